@@ -1,0 +1,23 @@
+"""Shared pytest configuration.
+
+``-m gpu`` marks tests that need a GB300 and the CUDA library; everything else
+runs on the CPU (oracle pins, host logic, library symbol checks)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
+
+
+@pytest.fixture(scope="session")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
