@@ -1,0 +1,374 @@
+"""Benchmark: 0.01 m integrate + segment, frames/s (and p50/p99 ms per frame).
+
+Workload (default): the paper-scale trajectory -- a 4 x 4 x 2 m map at 0.01 m
+(sparse 8^3 bricks), a 640 x 480 depth camera (87 x 58 deg, 0.3-4 m,
+sigma = 1 mm + 0.2 % of range) walking 300 frames over an 8-step open-tread
+stair, a desk with a 0.4 m overhang, a 15 deg ramp, floor and 20 boxes.
+One step = integrate one frame (307,200 points) + segment the accumulated map
+(normals, classification, clustering, RANSAC with I = 100, refit, hulls).
+The timed steps are the LAST K frames of the trajectory (the largest maps);
+earlier frames are integrated untimed first.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Multi-GPU (torchrun): every rank runs its own replica
+of the workload on its own GPU (no collective on the data path); value is the
+frames of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_FRAMES = 300
+METRIC = "0.01 m integrate+segment: frames/s, p50/p99 ms, batched/served vs plain GPU"
+WORKLOAD = ("paper-scale trajectory: 4x4x2 m map at 0.01 m (sparse 8^3 bricks), 640x480 depth camera "
+            "(87x58 deg, 0.3-4 m, sigma 1 mm + 0.2% range) over an 8-step open-tread stair, overhanging desk, "
+            "15 deg ramp, floor, 20 boxes; 300 frames; step = integrate 307,200 points + segment (I=100)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--ref-budget-s", type=float, default=150.0)
+    ap.add_argument("--stages", action="store_true", help="print the per-stage breakdown to stderr")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_frames(device):
+    """All 300 frames on the device (float32 [300, 307200, 3]) and their poses."""
+    import torch
+    import synth
+    scene = synth.config2_scene()
+    pts = torch.empty((N_FRAMES, 640 * 480, 3), dtype=torch.float32, device=device)
+    poses = []
+    for f in range(1, N_FRAMES + 1):
+        p, pose = synth.config2_frame(f, scene, device=device)
+        pts[f - 1].copy_(p)
+        poses.append(pose)
+    return pts, poses
+
+
+def frame_schedule(steps, warmup):
+    """Frame index (0-based) of every warm-up and timed step; the timed steps end
+    at the last frame.  Steps beyond one trajectory restart it on a reset map."""
+    total = steps + warmup
+    first = max(0, N_FRAMES - total)
+    sched = [(first + i) % N_FRAMES for i in range(total)]
+    return first, sched
+
+
+def seg_params(vm):
+    return vm.segment_params(n_hyp=100, seed=0)
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2510_01592_gb300 import vm
+    import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = synth.config2_spec()
+    pts, poses = make_frames(dev)
+    first, sched = frame_schedule(args.steps, args.warmup)
+    params = seg_params(vm)
+    stream = torch.cuda.Stream(device=dev)
+
+    def fresh_map(timing=False):
+        m = vm.VoxelMap(spec.dims, spec.origin, spec.voxel_size, stream=stream, stage_timing=timing)
+        for f in range(first):
+            m.integrate(pts[f], poses[f])
+        return m
+
+    # ---------------- device-resident inputs: the metric
+    m = fresh_map()
+    for i in range(args.warmup):
+        f = sched[i]
+        if f == 0 and i:
+            m.reset()
+        m.integrate(pts[f], poses[f])
+        m.segment(params)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = vm.launch_count()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    n_planes = []
+    for i in range(args.steps):
+        f = sched[args.warmup + i]
+        if f == 0 and (args.warmup + i):
+            m.reset()
+        m.integrate(pts[f], poses[f])
+        r = m.segment(params)
+        n_planes.append(len(r["planes"]))
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = vm.launch_count() - launches0
+    clocks = sampler.stop()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    st = m.stats()
+    m.close()
+    # ---------------- stage breakdown over the same frames (separate instrumented pass)
+    mt = fresh_map(timing=True)
+    for i in range(args.warmup):
+        f = sched[i]
+        mt.integrate(pts[f], poses[f])
+        mt.segment(params)
+    mt.stage_times()
+    for i in range(args.steps):
+        f = sched[args.warmup + i]
+        if f == 0 and (args.warmup + i):
+            mt.reset()
+        mt.integrate(pts[f], poses[f])
+        mt.segment(params)
+    stages = mt.stage_times()
+    mt.close()
+    # ---------------- end to end: host (pinned) inputs, host results
+    host_pts = [pts[f].cpu().pin_memory() for f in sorted(set(sched))]
+    host_of = {f: host_pts[j] for j, f in enumerate(sorted(set(sched)))}
+    me = fresh_map()
+    for i in range(args.warmup):
+        f = sched[i]
+        me.integrate(host_of[f].numpy(), poses[f])
+        me.segment(params)
+    torch.cuda.synchronize()
+    d2h = 0
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        f = sched[args.warmup + i]
+        if f == 0 and (args.warmup + i):
+            me.reset()
+        me.integrate(host_of[f].numpy(), poses[f])
+        r = me.segment(params)
+        d2h += r["planes"].nbytes + r["hull_xy"].nbytes + r["hull_xyz"].nbytes
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    me.close()
+
+    if ws > 1:
+        t = torch.tensor([total_ms, e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+    frames = args.steps * ws
+    value = frames / (total_ms / 1e3)
+    res = {
+        "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic (ray-cast scenes)",
+        "config": {"workload": WORKLOAD, "frames_timed": f"{first + args.warmup + 1}..{first + args.warmup + args.steps}"
+                   if first + args.warmup + args.steps <= N_FRAMES else "wrapping trajectory",
+                   "voxel_m": 0.01, "map_m": [4, 4, 2], "points_per_frame": 307200, "ransac_hypotheses": 100,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2: a distinct 3.7 MB frame per step from a 1.1 GB resident "
+                         "trajectory; per-step map state (pool + segmentation arrays) well above the 129 MB L2"},
+        "p50_ms": round(statistics.median(per_step), 4),
+        "p99_ms": round(sorted(per_step)[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)], 4),
+        "gpu_launches": int(launches),
+        "e2e": {"value": round(frames / e2e_s, 2), "unit": "frames/s", "h2d_bytes_per_step": 640 * 480 * 12,
+                "d2h_bytes_per_step": int(d2h / max(1, args.steps))},
+        "planes_per_frame": round(float(np.mean(n_planes)), 2),
+        "map": {"occupied_voxels": st["occupied_voxels"], "steppable_voxels": st["steppable_voxels"],
+                "bricks": st["bricks_allocated"], "device_bytes": st["device_bytes"]},
+    }
+    if clocks:
+        res["clocks"] = clocks
+    res["stages_ms_per_step"] = {k: round(v[0] / max(1, args.steps), 4) for k, v in stages.items() if v[1]}
+    res["roofline"] = roofline(stages, st, args.steps, spec)
+    return res, rank
+
+
+def roofline(stages, st, steps, spec):
+    """Dominant stage's achieved rate against the measured peak (see the design doc
+    for the algorithmic bytes / ops per unit of each kernel)."""
+    peaks = load_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    timed = {k: v[0] / max(1, v[1]) for k, v in stages.items() if v[1]}
+    if not timed:
+        return None
+    dom = max(timed, key=lambda k: stages[k][0])
+    occ = st["occupied_voxels"]
+    slots = st["bricks_allocated"] * 512
+    # algorithmic bytes per launch of each HBM-bound stage
+    algo = {
+        "finalize": slots * (4 + 1 + 12) + occ * 24,            # counts, status, means out; sums of occupied in
+        "normals": occ * (12 + 12 + 2) + slots * 1,             # means in, normals + status/N out, status probe
+        "ccl": occ * (24 + 4) + slots * (1 + 4 + 4),            # means+normals of vertices, parents init/compress
+        "order_bricks": 0,
+    }
+    ms = timed[dom]
+    if dom in algo and algo[dom]:
+        ach = algo[dom] / (ms / 1e3) / 1e9
+        return {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"
+                if peaks else "fallback 6800 GB/s", "avg_launch_ms": round(ms, 4)}
+    return {"kernel": dom, "bound": "latency", "avg_launch_ms": round(ms, 4), "achieved": None, "peak": None,
+            "unit": None, "frac": None, "traffic": None}
+
+
+def cpu_baseline(budget_s):
+    """The oracle as it stands, single-threaded on the host, over a bounded
+    sample: frames integrated untimed up to the timed window, then
+    integrate + segment per frame until the budget is spent."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    spec = synth.config2_spec()
+    scene = synth.config2_scene()
+    om = oracle.OracleMap(spec.dims, spec.origin, spec.voxel_size)
+    prm = oracle.make_params(n_hyp=100, seed=0)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    start = N_FRAMES - 30
+    for f in range(1, start + 1):
+        p, pose = synth.config2_frame(f, scene, device=dev)
+        om.integrate(p.cpu().numpy(), pose)
+    done, t_used = 0, 0.0
+    f = start + 1
+    while t_used < budget_s and f <= N_FRAMES:
+        p, pose = synth.config2_frame(f, scene, device=dev)
+        host = p.cpu().numpy()
+        t0 = time.perf_counter()
+        om.integrate(host, pose)
+        om.segment(prm)
+        t_used += time.perf_counter() - t0
+        done += 1
+        f += 1
+    om.close()
+    return {"value": round(done / t_used, 4), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"frames {start + 1}..{start + done} of the 300-frame trajectory (frames 1..{start} "
+                      f"integrated untimed first), integrate + segment each, single-threaded C oracle"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return None, rank
+    cb = cpu_baseline(args.ref_budget_s)
+    res = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "frames/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic (ray-cast scenes)",
+           "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+           "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return res, rank
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        res, rank = run_reference(args)
+        if res is not None and rank == 0:
+            print(json.dumps(res))
+        return
+    res, rank = run_gpu(args)
+    ws, _, _ = dist_env()
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(args.cpu_budget_s)
+        if args.stages:
+            print(json.dumps(res["stages_ms_per_step"], indent=1), file=sys.stderr)
+        print(json.dumps(res))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

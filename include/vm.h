@@ -1,0 +1,213 @@
+/*
+ * vm.h -- C ABI of the GB300 voxel-map / multi-plane-segmentation library
+ * (libvoxmps.so).  It implements the method of "Real-time Multi-Plane
+ * Segmentation Based on GPU Accelerated High-Resolution 3D Voxel Mapping for
+ * Legged Robot Locomotion" (arXiv 2510.01592): the voxel update of Sec. III.B
+ * (Eq. 1) and the multi-plane segmentation of Sec. III.C (Eq. 3, Eq. 4,
+ * Algorithm 1, cluster-parallel RANSAC, boundary polygons), every step as a
+ * hand-written CUDA kernel for sm_103a.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a vm_status.  Nothing aborts, traps or exits; on an
+ *    error vm_last_error() returns a thread-local message.
+ *  - Pointers are plain host or device pointers as stated per argument.  No
+ *    call takes ownership of caller memory.
+ *  - Work on one map is ordered on that map's CUDA stream.  Different maps may
+ *    run concurrently on different streams.
+ *  - Poses are row-major 3x4 [R | t] mapping sensor coordinates to map
+ *    coordinates; the map frame has z up (gravity along -z).
+ *  - Coordinates are metres, FP32.
+ */
+#ifndef VOXMPS_VM_H
+#define VOXMPS_VM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VM_OK = 0,
+    VM_ERR_INVALID_ARG = 1,    /* null pointer, zero/negative size, bad parameter        */
+    VM_ERR_OUT_OF_MEMORY = 2,  /* a device or host allocation failed                     */
+    VM_ERR_CAPACITY = 3,       /* the brick pool is full; points in new bricks dropped   */
+    VM_ERR_CUDA = 4,           /* a CUDA runtime call failed (message has the CUDA error) */
+    VM_ERR_TIMEOUT = 5,        /* a bounded device loop hit its iteration cap            */
+    VM_ERR_EXTENT = 6          /* the grid is too large for 32-bit voxel ids             */
+} vm_status;
+
+typedef struct vm_map vm_map; /* opaque, library-owned */
+
+/* Map geometry (Sec. III.B, 3D voxel map representation).  The grid has
+ * dims[0] x dims[1] x dims[2] voxels of edge voxel_size whose lowest corner is
+ * origin.  Storage is sparse: 8x8x8-voxel bricks are allocated on first touch
+ * from a pool of brick_capacity bricks (0 = enough bricks for the whole grid). */
+typedef struct {
+    float origin[3];
+    int32_t dims[3];
+    float voxel_size;          /* metres; 1/voxel_size is formed in double, then rounded to FP32 */
+    uint32_t brick_capacity;
+    uint32_t flags;            /* VM_MAP_* bits */
+} vm_map_params;
+
+#define VM_MAP_STAGE_TIMING 1u /* record CUDA-event time per pipeline stage (vm_stage_times) */
+
+/* Segmentation parameters (Sec. III.C).  Defaults from the paper:
+ * n_th = 3, theta 15 deg (cos_step = cos_ccl = 0.96592583f), d_th = 0.05 m,
+ * n_hyp = I = 100, eps = 0.01 m. */
+typedef struct {
+    uint32_t n_th;             /* Eq. 4: minimum occupied neighbours N_th                 */
+    float cos_step;            /* Eq. 4: steppable iff |n_z| >= cos_step                  */
+    float d_th2;               /* Algorithm 1: edge iff |mu_i - mu_j|^2 < d_th2           */
+    float cos_ccl;             /* Algorithm 1: edge iff |n_i . n_j| > cos_ccl             */
+    uint32_t min_cluster;      /* clusters smaller than this are discarded                */
+    uint32_t n_hyp;            /* RANSAC hypotheses per cluster (1..1024)                 */
+    float eps;                 /* RANSAC inlier threshold: |n.p + d| <= eps               */
+    uint64_t seed;             /* Philox4x64-10 key word 0                                */
+    uint32_t classify;         /* 1: cluster steppable voxels only (paper); 0: all occupied */
+    uint32_t reserved;
+} vm_segment_params;
+
+/* One output plane: one per cluster, clusters in ascending label order. */
+typedef struct {
+    float normal[3];           /* refit normal (total least squares on the inliers), n_z >= 0 */
+    float offset;              /* refit plane: normal . x + offset = 0                       */
+    uint32_t inlier_count;     /* inliers of the selected RANSAC hypothesis                  */
+    uint32_t label;            /* cluster label: smallest voxel id of the cluster / caller label */
+    float ransac_normal[3];    /* selected hypothesis (bit-exact to the reference reading)   */
+    float ransac_offset;
+    float basis_u[3];          /* in-plane basis from the RANSAC normal                      */
+    float basis_v[3];
+    float hull_origin[3];      /* the cluster's first point                                  */
+    uint32_t hull_offset;      /* first vertex in vm_planes.hull_xy / hull_xyz               */
+    uint32_t hull_count;       /* vertices, counter-clockwise from the lexicographic minimum */
+    uint32_t n_points;         /* points in the cluster                                      */
+    int32_t best_h;            /* selected hypothesis index; -1: no valid hypothesis, no plane */
+    uint32_t flags;            /* bit 0: refit ill-conditioned (lambda_mid < 10 lambda_min)  */
+} vm_plane;
+
+/* Result of vm_segment / vm_fit_planes; host memory owned by the library
+ * until vm_planes_free. */
+typedef struct {
+    vm_plane* planes;
+    uint32_t n_planes;
+    int32_t* hull_xy;          /* [n_hull][2] in-plane coordinates, units of 2^-16 m */
+    float* hull_xyz;           /* [n_hull][3] hull vertices lifted onto the refit plane, map frame */
+    uint32_t n_hull;
+} vm_planes;
+
+typedef struct {
+    uint64_t points_integrated;  /* points accumulated since creation / reset     */
+    uint64_t points_dropped;     /* NaN, Inf or outside the grid                  */
+    uint64_t points_no_capacity; /* dropped because the brick pool was full       */
+    uint32_t bricks_allocated;
+    uint32_t brick_capacity;
+    uint32_t occupied_voxels;    /* at the last segmentation                      */
+    uint32_t steppable_voxels;   /* at the last segmentation                      */
+    uint32_t clusters;           /* kept clusters at the last segmentation        */
+    uint32_t reserved;
+    uint64_t device_bytes;       /* device memory held by the map                 */
+} vm_stats;
+
+/* Create a map.  params: see vm_map_params.  cuda_stream: a cudaStream_t the
+ * map's work is ordered on, or NULL to let the library create one.  On
+ * success *out holds the map.  Errors: VM_ERR_INVALID_ARG (dims <= 0,
+ * voxel_size <= 0, an extent beyond 16 m per axis), VM_ERR_EXTENT (more than
+ * 2^32 voxel ids), VM_ERR_OUT_OF_MEMORY, VM_ERR_CUDA.  Sec. III.B. */
+vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out);
+
+/* Voxel information update (Sec. III.B, Eq. 1), one thread per point.
+ * xyz: n points, float32[n][3] (AoS), device memory if xyz_on_device != 0,
+ * otherwise host memory (copied on the map's stream; pinned memory makes the
+ * copy asynchronous).  pose3x4: host pointer to 12 floats, sensor->map.
+ * Each point is transformed, keyed to its voxel, and accumulated as exact
+ * fixed-point sums (2^-20 m units) plus a count; NaN/Inf points and points
+ * outside the grid are dropped and counted.  Asynchronous on the map's stream
+ * unless xyz is pageable host memory.  Errors: VM_ERR_INVALID_ARG,
+ * VM_ERR_CUDA; a full brick pool is reported by the next vm_segment /
+ * vm_get_stats as VM_ERR_CAPACITY. */
+vm_status vm_integrate(vm_map* map, const float* xyz, uint32_t n, const float pose3x4[12], int xyz_on_device);
+
+/* Multi-plane segmentation of the accumulated map (Sec. III.C): mean
+ * positions, normals and steppable classification (Eq. 3, Eq. 4), clustering
+ * (Algorithm 1, as union-find over the same adjacency), clusters of at least
+ * min_cluster voxels, per-cluster RANSAC (stages a-c), inlier refit and
+ * convex hull.  Synchronises the map's stream.  *out receives library-owned
+ * host arrays (free with vm_planes_free).  Errors: VM_ERR_INVALID_ARG,
+ * VM_ERR_CAPACITY (the pool overflowed since the last call; the result covers
+ * the points that fitted), VM_ERR_TIMEOUT, VM_ERR_OUT_OF_MEMORY, VM_ERR_CUDA. */
+vm_status vm_segment(vm_map* map, const vm_segment_params* params, vm_planes* out);
+
+/* Free the host arrays of a vm_planes and zero it.  NULL members are fine. */
+vm_status vm_planes_free(vm_planes* planes);
+
+/* Clear the map (every voxel free) without releasing memory. */
+vm_status vm_reset(vm_map* map);
+
+/* Destroy a map and release its device memory; waits for its stream. */
+vm_status vm_destroy(vm_map* map);
+
+/* Counters of the map; synchronises its stream. */
+vm_status vm_get_stats(vm_map* map, vm_stats* out);
+
+/* Batched plane fitting on caller-formed clusters (Sec. III.C multi-plane
+ * estimation and boundary polygons; the cluster-parallel form of Sec. IV-C):
+ * one persistent RANSAC launch over all clusters, then refit and hull.
+ * xyz: device float32[off[k]][3]; off: device uint32[k+1], cluster c holds
+ * points off[c]..off[c+1]-1; labels: device uint32[k] keying each cluster's
+ * Philox stream, or NULL for label = c.  stream: cudaStream_t or NULL (the
+ * legacy default stream).  Synchronises the stream.  Errors:
+ * VM_ERR_INVALID_ARG, VM_ERR_OUT_OF_MEMORY, VM_ERR_TIMEOUT, VM_ERR_CUDA. */
+vm_status vm_fit_planes(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
+                        const vm_segment_params* params, void* stream, vm_planes* out);
+
+/* Debug / parity export of the occupied voxels, in voxel-id order.  Voxel ids
+ * are brick-major: bricks of 8^3 voxels numbered x-fastest over the brick
+ * grid, voxels inside a brick x-fastest.  Host output arrays of capacity cap:
+ * vid[cap], sums[cap][3] (int64, 2^-20 m units relative to the origin),
+ * counts[cap]; *n receives the number of occupied voxels (if > cap only cap
+ * are written).  Any output pointer may be NULL.  Synchronises. */
+vm_status vm_export_voxels(vm_map* map, uint32_t* vid, int64_t* sums, uint32_t* counts, uint32_t cap, uint32_t* n);
+
+/* Debug / parity export of the last vm_segment's per-voxel state, in voxel-id
+ * order over the occupied voxels: normal[cap][3], status[cap] (1 occupied,
+ * 2 steppable), label[cap] (smallest voxel id of the voxel's component, or
+ * 0xFFFFFFFF when the voxel is not clustered), nbr[cap] (occupied neighbours
+ * N).  Host arrays; any may be NULL.  Synchronises. */
+vm_status vm_export_labels(vm_map* map, uint32_t* vid, float* normal, uint8_t* status, uint32_t* label,
+                           uint32_t* nbr, uint32_t cap, uint32_t* n);
+
+/* Debug / parity export of the last vm_segment's cluster points: pts[cap][3]
+ * (mean positions in cluster order), vid[cap] (their voxel ids) and
+ * inlier[cap] (1 if an inlier of the cluster's selected hypothesis).  Host
+ * arrays; any may be NULL; *n receives the point count.  Synchronises. */
+vm_status vm_export_clusters(vm_map* map, float* pts, uint32_t* vid, uint8_t* inlier, uint32_t cap, uint32_t* n);
+
+/* Diagnostics (no counterpart in the paper).  Stage timing records CUDA
+ * events around each pipeline stage on the stream it runs on: integrate,
+ * order_bricks, finalize, normals, ccl, clusters, ransac_hyp, ransac_score,
+ * extract, refit_hull, pack (vm_stage_name gives the names).
+ * vm_stage_timing: enable (1) or disable (0) for a map, or for this thread's
+ * vm_fit_planes calls when map is NULL.  vm_stage_times: device milliseconds
+ * and call counts per stage accumulated since the previous call (then reset);
+ * ms[cap], calls[cap] host arrays, either may be NULL; *n_stages receives the
+ * stage count.  Synchronises the map's stream. */
+vm_status vm_stage_timing(vm_map* map, int enable);
+vm_status vm_stage_times(vm_map* map, double* ms, uint64_t* calls, uint32_t cap, uint32_t* n_stages);
+const char* vm_stage_name(uint32_t stage);
+
+/* Number of CUDA kernel launches the library has issued in this process. */
+uint64_t vm_launch_count(void);
+
+/* Thread-local message describing the last error of this thread. */
+const char* vm_last_error(void);
+
+/* Library version string. */
+const char* vm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOXMPS_VM_H */

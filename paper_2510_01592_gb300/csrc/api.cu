@@ -1,0 +1,769 @@
+// api.cu -- the C ABI of libvoxmps.so (include/vm.h): map lifecycle, device
+// scratch management and the host-side ordering of the kernels of one call.
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "vm_internal.cuh"
+
+using namespace vmx;
+
+namespace vmx {
+
+static thread_local std::string g_err;
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "finalize", "normals", "ccl",
+                                              "clusters", "ransac_hyp", "ransac_score", "extract", "refit_hull",
+                                              "pack"};
+
+// CUDA-event stage timer: begin/end record events on the stream; elapsed times
+// are folded in once the events have completed (at the next sync point).
+struct Timer : StageHook {
+    bool on = false;
+    struct Rec {
+        int st;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> recs;
+    cudaEvent_t open[kNumStages] = {};
+    double ms[kNumStages] = {};
+    unsigned long long calls[kNumStages] = {};
+    cudaEvent_t get() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    void begin(int st, cudaStream_t s) override {
+        if (!on) return;
+        cudaEvent_t e = get();
+        if (e) cudaEventRecord(e, s);
+        open[st] = e;
+    }
+    void end(int st, cudaStream_t s) override {
+        if (!on || !open[st]) return;
+        cudaEvent_t e = get();
+        if (!e) return;
+        cudaEventRecord(e, s);
+        recs.push_back({st, open[st], e});
+        open[st] = nullptr;
+    }
+    void fold() {
+        for (auto& r : recs) {
+            float t = 0.0f;
+            cudaEventSynchronize(r.b);
+            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+                ms[r.st] += t;
+                calls[r.st] += 1;
+            }
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        recs.clear();
+    }
+    void release() {
+        fold();
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+    }
+    StageHook* hook() { return on ? this : nullptr; }
+};
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+vm_status cuda_status(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? VM_ERR_OUT_OF_MEMORY : VM_ERR_CUDA;
+}
+
+vm_status ensure(DevBuf& b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return VM_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 4 + 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e, "cudaMalloc");
+    }
+    b.bytes = want;
+    return VM_OK;
+}
+
+static void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Carves aligned sub-buffers out of one allocation.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+// Fit scratch owned by a map or by a calling thread.
+struct FitContext {
+    Timer timer;
+    DevBuf mem;
+    FitBuffers fb{};
+    size_t kcap = 0, npts = 0, items = 0;
+    int H = 0;
+    DevBuf out;          // device staging of planes / hull arrays
+    void* host = nullptr;  // pinned host staging
+    size_t host_bytes = 0;
+};
+
+static size_t fit_bytes(size_t kcap, size_t npts, size_t items, int H, Carver* c) {
+    Carver dry{nullptr};
+    Carver& k = c ? *c : dry;
+    FitBuffers fb{};
+    fb.hyp = k.take<float4>(kcap * H);
+    fb.hyp_valid = k.take<uint8_t>(kcap * H);
+    fb.counts = k.take<uint32_t>(kcap * H);
+    fb.cl = k.take<FitCluster>(kcap);
+    fb.item_off = k.take<uint32_t>(kcap + 1);
+    fb.queue = k.take<uint32_t>(4);
+    fb.inlier = k.take<uint8_t>(npts + 1);
+    fb.part = k.take<float>((items + 1) * 10);
+    fb.cen = k.take<double>(kcap * 3);
+    fb.surv = k.take<int2>(npts + 1);
+    fb.hull = k.take<int2>(npts + 1);
+    fb.hull_cnt = k.take<uint32_t>(kcap + 1);
+    size_t sw = scan_tmp_words(kcap + 1);
+    fb.scan_tmp = k.take<uint32_t>(sw);
+    fb.err = k.take<uint32_t>(4);
+    if (c) {
+        c->off = k.off;
+    }
+    return k.off + 256;
+}
+
+static vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile) {
+    const size_t items = npts / (size_t)tile + kcap + 1;
+    if (fc.mem.p && kcap <= fc.kcap && npts <= fc.npts && items <= fc.items && H <= fc.H) return VM_OK;
+    const size_t k2 = kcap + kcap / 4 + 16, n2 = npts + npts / 4 + 1024, i2 = n2 / (size_t)tile + k2 + 1;
+    const int H2 = H > fc.H ? H : fc.H;
+    const size_t bytes = fit_bytes(k2, n2, i2, H2, nullptr);
+    VM_TRY(ensure(fc.mem, bytes));
+    Carver c{static_cast<char*>(fc.mem.p)};
+    FitBuffers fb{};
+    fb.hyp = c.take<float4>(k2 * H2);
+    fb.hyp_valid = c.take<uint8_t>(k2 * H2);
+    fb.counts = c.take<uint32_t>(k2 * H2);
+    fb.cl = c.take<FitCluster>(k2);
+    fb.item_off = c.take<uint32_t>(k2 + 1);
+    fb.queue = c.take<uint32_t>(4);
+    fb.inlier = c.take<uint8_t>(n2 + 1);
+    fb.part = c.take<float>((i2 + 1) * 10);
+    fb.cen = c.take<double>(k2 * 3);
+    fb.surv = c.take<int2>(n2 + 1);
+    fb.hull = c.take<int2>(n2 + 1);
+    fb.hull_cnt = c.take<uint32_t>(k2 + 1);
+    fb.scan_tmp = c.take<uint32_t>(scan_tmp_words(k2 + 1));
+    fb.err = c.take<uint32_t>(4);
+    fb.kcap = k2;
+    fb.npts_cap = n2;
+    fb.items_cap = i2;
+    fb.H = H2;
+    fc.fb = fb;
+    fc.kcap = k2;
+    fc.npts = n2;
+    fc.items = i2;
+    fc.H = H2;
+    return VM_OK;
+}
+
+static void fit_release(FitContext& fc) {
+    fc.timer.release();
+    release(fc.mem);
+    release(fc.out);
+    if (fc.host) cudaFreeHost(fc.host);
+    fc.host = nullptr;
+    fc.host_bytes = 0;
+    fc.kcap = fc.npts = fc.items = 0;
+    fc.H = 0;
+}
+
+static int device_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+static vm_status check_params(const vm_segment_params* p) {
+    if (!p) {
+        set_error("null segment params");
+        return VM_ERR_INVALID_ARG;
+    }
+    if (p->n_hyp < 1 || p->n_hyp > 1024) {
+        set_error("n_hyp must be in [1, 1024]");
+        return VM_ERR_INVALID_ARG;
+    }
+    if (!(p->eps >= 0.0f) || !(p->d_th2 >= 0.0f)) {
+        set_error("eps and d_th2 must be non-negative");
+        return VM_ERR_INVALID_ARG;
+    }
+    return VM_OK;
+}
+
+// Runs the fit on k clusters and returns the packed result on the host.
+static vm_status fit_and_pack(FitContext& fc, const float* pts, const uint32_t* off, const uint32_t* labels,
+                              uint32_t k, uint32_t npts, const vm_segment_params& p, const FitTuning& tune,
+                              cudaStream_t s, vm_planes* out) {
+    memset(out, 0, sizeof(*out));
+    if (k == 0) return VM_OK;
+    VM_TRY(fit_prepare(fc, k, npts, (int)p.n_hyp, tune.tile));
+    FitBuffers& fb = fc.fb;
+    VM_CUDA(cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s));
+    StageHook* hk = fc.timer.hook();
+    VM_CUDA(launch_fit(pts, off, labels, k, npts, p, fb, tune, device_sms(), s, hk));
+    uint32_t hdr[2];
+    VM_CUDA(cudaMemcpyAsync(&hdr[0], fb.hull_cnt + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VM_CUDA(cudaMemcpyAsync(&hdr[1], fb.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VM_CUDA(cudaStreamSynchronize(s));
+    const uint32_t n_hull = hdr[0];
+    const size_t b_planes = (size_t)k * sizeof(vm_plane);
+    const size_t b_xy = (size_t)n_hull * 2 * sizeof(int32_t);
+    const size_t b_xyz = (size_t)n_hull * 3 * sizeof(float);
+    const size_t o_xy = (b_planes + 255) & ~(size_t)255;
+    const size_t o_xyz = (o_xy + b_xy + 255) & ~(size_t)255;
+    const size_t total = o_xyz + b_xyz + 256;
+    VM_TRY(ensure(fc.out, total));
+    char* d = static_cast<char*>(fc.out.p);
+    VM_STAGE_BEGIN(hk, kStPack, s);
+    VM_CUDA(launch_pack(fb, off, labels, k, reinterpret_cast<vm_plane*>(d), reinterpret_cast<int32_t*>(d + o_xy),
+                        reinterpret_cast<float*>(d + o_xyz), s));
+    if (fc.host_bytes < total) {
+        if (fc.host) cudaFreeHost(fc.host);
+        fc.host = nullptr;
+        fc.host_bytes = 0;
+        VM_CUDA(cudaMallocHost(&fc.host, total + total / 4));
+        fc.host_bytes = total + total / 4;
+    }
+    VM_CUDA(cudaMemcpyAsync(fc.host, d, total, cudaMemcpyDeviceToHost, s));
+    VM_STAGE_END(hk, kStPack, s);
+    VM_CUDA(cudaStreamSynchronize(s));
+    fc.timer.fold();
+    out->planes = static_cast<vm_plane*>(malloc(b_planes ? b_planes : 1));
+    out->hull_xy = static_cast<int32_t*>(malloc(b_xy ? b_xy : 1));
+    out->hull_xyz = static_cast<float*>(malloc(b_xyz ? b_xyz : 1));
+    if (!out->planes || !out->hull_xy || !out->hull_xyz) {
+        vm_planes_free(out);
+        set_error("host allocation of the result failed");
+        return VM_ERR_OUT_OF_MEMORY;
+    }
+    const char* h = static_cast<const char*>(fc.host);
+    memcpy(out->planes, h, b_planes);
+    memcpy(out->hull_xy, h + o_xy, b_xy);
+    memcpy(out->hull_xyz, h + o_xyz, b_xyz);
+    out->n_planes = k;
+    out->n_hull = n_hull;
+    if (hdr[1] & kErrTimeout) {
+        set_error("a bounded device loop reached its iteration cap during the plane fit");
+        return VM_ERR_TIMEOUT;
+    }
+    return VM_OK;
+}
+
+}  // namespace vmx
+
+struct vm_map {
+    vm_map_params prm{};
+    Grid g{};
+    uint32_t nb_total = 0;
+    uint32_t capacity = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // pool
+    int32_t* brick_table = nullptr;
+    int32_t* slot_key = nullptr;
+    unsigned long long* S = nullptr;
+    uint32_t* C = nullptr;
+    MapCounters* ctr = nullptr;
+    uint32_t* err = nullptr;  // segmentation error word
+    DevBuf pool;
+    DevBuf stage;             // host points staged on the device
+    // segmentation
+    DevBuf brick_mem;         // brick-level arrays (fixed size)
+    DevBuf vox_mem;           // rank-dense voxel arrays (grow with the brick count)
+    SegBuffers seg{};
+    size_t seg_nv = 0;
+    SegCounters* hctr = nullptr;  // pinned
+    SegCounters last{};
+    FitContext fit;
+    FitTuning tune = default_tuning();
+    bool segmented = false;
+};
+
+namespace {
+
+vm_status alloc_vox(vm_map* m, uint32_t n_sorted) {
+    const size_t need = (size_t)(n_sorted ? n_sorted : 1) * kBrickVox;
+    if (m->vox_mem.p && need <= m->seg_nv) return VM_OK;
+    size_t nv = need + need / 4;
+    const size_t cap_nv = (size_t)m->capacity * kBrickVox;
+    if (nv > cap_nv) nv = cap_nv > need ? cap_nv : need;
+    const size_t tmp_words = [&] {
+        size_t a = scan_tmp_words(nv + 1), b = sort_tmp_words(nv);
+        size_t c = scan_tmp_words((size_t)m->nb_total + 1);
+        size_t r = a > b ? a : b;
+        return r > c ? r : c;
+    }();
+    auto layout = [&](Carver& c, SegBuffers& b) {
+        b.M = c.take<int32_t>(3 * nv);
+        b.nrm = c.take<float>(3 * nv);
+        b.status = c.take<uint8_t>(nv);
+        b.nbr = c.take<uint8_t>(nv);
+        b.parent = c.take<uint32_t>(nv);
+        b.count = c.take<uint32_t>(nv);
+        b.cid = c.take<uint32_t>(nv + 1);
+        b.vert_flag = c.take<uint32_t>(nv + 1);
+        b.keys = c.take<uint32_t>(nv);
+        b.vals = c.take<uint32_t>(nv);
+        b.keys_alt = c.take<uint32_t>(nv);
+        b.vals_alt = c.take<uint32_t>(nv);
+        b.cl_size = c.take<uint32_t>(nv + 1);
+        b.cl_off = c.take<uint32_t>(nv + 1);
+        b.cl_label = c.take<uint32_t>(nv + 1);
+        b.pts = c.take<float>(3 * nv);
+        b.pt_vid = c.take<uint32_t>(nv);
+        b.scan_tmp = c.take<uint32_t>(tmp_words);
+    };
+    Carver dry{nullptr};
+    SegBuffers tmp{};
+    layout(dry, tmp);
+    VM_TRY(ensure(m->vox_mem, dry.off + 256));
+    Carver c{static_cast<char*>(m->vox_mem.p)};
+    layout(c, m->seg);
+    m->seg.nv = nv;
+    m->seg.kcap = nv;
+    m->seg_nv = nv;
+    return VM_OK;
+}
+
+vm_status check_map(vm_map* m) {
+    if (!m) {
+        set_error("null map");
+        return VM_ERR_INVALID_ARG;
+    }
+    return VM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vm_last_error(void) { return g_err.c_str(); }
+
+const char* vm_version(void) { return "voxmps 0.1 (sm_103a)"; }
+
+vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out) {
+    if (!params || !out) {
+        set_error("null argument");
+        return VM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    const vm_map_params& p = *params;
+    if (p.dims[0] <= 0 || p.dims[1] <= 0 || p.dims[2] <= 0 || !(p.voxel_size > 0.0f)) {
+        set_error("dims and voxel_size must be positive");
+        return VM_ERR_INVALID_ARG;
+    }
+    for (int a = 0; a < 3; ++a) {
+        if ((double)p.dims[a] * (double)p.voxel_size > 16.0 + 1e-9) {
+            set_error("map extent beyond 16 m on an axis");
+            return VM_ERR_INVALID_ARG;
+        }
+    }
+    vm_map* m = new (std::nothrow) vm_map();
+    if (!m) {
+        set_error("host allocation failed");
+        return VM_ERR_OUT_OF_MEMORY;
+    }
+    m->prm = p;
+    m->fit.timer.on = (p.flags & VM_MAP_STAGE_TIMING) != 0;
+    Grid& g = m->g;
+    g.nx = p.dims[0]; g.ny = p.dims[1]; g.nz = p.dims[2];
+    g.nbx = (g.nx + kBrick - 1) / kBrick;
+    g.nby = (g.ny + kBrick - 1) / kBrick;
+    g.nbz = (g.nz + kBrick - 1) / kBrick;
+    g.ox = p.origin[0]; g.oy = p.origin[1]; g.oz = p.origin[2];
+    g.inv_res = (float)(1.0 / (double)p.voxel_size);
+    const unsigned long long nb = (unsigned long long)g.nbx * g.nby * g.nbz;
+    if (nb * kBrickVox > 0xFFFFFFFFull) {
+        delete m;
+        set_error("more than 2^32 voxel ids");
+        return VM_ERR_EXTENT;
+    }
+    m->nb_total = (uint32_t)nb;
+    m->capacity = p.brick_capacity ? (p.brick_capacity < m->nb_total ? p.brick_capacity : m->nb_total) : m->nb_total;
+    cudaError_t e;
+    if (cuda_stream) {
+        m->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete m;
+            return cuda_status(e, "cudaStreamCreate");
+        }
+        m->own_stream = true;
+    }
+    // pool: table, slot keys, sums, counts, counters
+    Carver dry{nullptr};
+    dry.take<int32_t>(m->nb_total);
+    dry.take<int32_t>(m->capacity);
+    dry.take<unsigned long long>((size_t)m->capacity * 3 * kBrickVox);
+    dry.take<uint32_t>((size_t)m->capacity * kBrickVox);
+    dry.take<MapCounters>(1);
+    dry.take<uint32_t>(4);
+    vm_status st = ensure(m->pool, dry.off + 256);
+    if (st != VM_OK) {
+        vm_destroy(m);
+        return st;
+    }
+    Carver c{static_cast<char*>(m->pool.p)};
+    m->brick_table = c.take<int32_t>(m->nb_total);
+    m->slot_key = c.take<int32_t>(m->capacity);
+    m->S = c.take<unsigned long long>((size_t)m->capacity * 3 * kBrickVox);
+    m->C = c.take<uint32_t>((size_t)m->capacity * kBrickVox);
+    m->ctr = c.take<MapCounters>(1);
+    m->err = c.take<uint32_t>(4);
+    // brick-level segmentation arrays
+    Carver bd{nullptr};
+    bd.take<uint32_t>((size_t)m->nb_total + 1);
+    bd.take<int32_t>(m->nb_total);
+    bd.take<int32_t>(m->capacity);
+    bd.take<int32_t>(m->capacity);
+    bd.take<SegCounters>(1);
+    st = ensure(m->brick_mem, bd.off + 256);
+    if (st != VM_OK) {
+        vm_destroy(m);
+        return st;
+    }
+    Carver bc{static_cast<char*>(m->brick_mem.p)};
+    m->seg.flags = bc.take<uint32_t>((size_t)m->nb_total + 1);
+    m->seg.rank_table = bc.take<int32_t>(m->nb_total);
+    m->seg.sorted_slot = bc.take<int32_t>(m->capacity);
+    m->seg.sorted_key = bc.take<int32_t>(m->capacity);
+    m->seg.ctr = bc.take<SegCounters>(1);
+    e = cudaMallocHost(reinterpret_cast<void**>(&m->hctr), sizeof(SegCounters));
+    if (e != cudaSuccess) {
+        vm_destroy(m);
+        return cuda_status(e, "cudaMallocHost");
+    }
+    st = vm_reset(m);
+    if (st != VM_OK) {
+        vm_destroy(m);
+        return st;
+    }
+    *out = m;
+    return VM_OK;
+}
+
+vm_status vm_reset(vm_map* m) {
+    VM_TRY(check_map(m));
+    VM_CUDA(cudaMemsetAsync(m->brick_table, 0xFF, (size_t)m->nb_total * sizeof(int32_t), m->stream));
+    VM_CUDA(cudaMemsetAsync(m->S, 0, (size_t)m->capacity * 3 * kBrickVox * sizeof(unsigned long long), m->stream));
+    VM_CUDA(cudaMemsetAsync(m->C, 0, (size_t)m->capacity * kBrickVox * sizeof(uint32_t), m->stream));
+    VM_CUDA(cudaMemsetAsync(m->ctr, 0, sizeof(MapCounters), m->stream));
+    m->segmented = false;
+    return VM_OK;
+}
+
+vm_status vm_destroy(vm_map* m) {
+    if (!m) return VM_OK;
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    release(m->pool);
+    release(m->stage);
+    release(m->brick_mem);
+    release(m->vox_mem);
+    fit_release(m->fit);
+    if (m->hctr) cudaFreeHost(m->hctr);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+    return VM_OK;
+}
+
+vm_status vm_integrate(vm_map* m, const float* xyz, uint32_t n, const float pose3x4[12], int xyz_on_device) {
+    VM_TRY(check_map(m));
+    if ((!xyz && n) || !pose3x4) {
+        set_error("null points or pose");
+        return VM_ERR_INVALID_ARG;
+    }
+    if (n == 0) return VM_OK;
+    const float* d = xyz;
+    if (!xyz_on_device) {
+        VM_TRY(ensure(m->stage, (size_t)n * 3 * sizeof(float)));
+        VM_CUDA(cudaMemcpyAsync(m->stage.p, xyz, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+        d = static_cast<const float*>(m->stage.p);
+    }
+    Pose P;
+    memcpy(P.r, pose3x4, sizeof(P.r));
+    StageHook* hk = m->fit.timer.hook();
+    VM_STAGE_BEGIN(hk, kStIntegrate, m->stream);
+    VM_CUDA(launch_integrate(d, n, P, m->g, m->brick_table, m->slot_key, m->S, m->C, m->ctr, m->capacity, m->stream));
+    VM_STAGE_END(hk, kStIntegrate, m->stream);
+    return VM_OK;
+}
+
+vm_status vm_segment(vm_map* m, const vm_segment_params* params, vm_planes* out) {
+    VM_TRY(check_map(m));
+    VM_TRY(check_params(params));
+    if (!out) {
+        set_error("null output");
+        return VM_ERR_INVALID_ARG;
+    }
+    memset(out, 0, sizeof(*out));
+    const int sms = device_sms();
+    cudaStream_t s = m->stream;
+    SegBuffers& b = m->seg;
+    // 1. bricks in key order
+    if (!m->vox_mem.p) VM_TRY(alloc_vox(m, 1));
+    StageHook* hk = m->fit.timer.hook();
+    VM_CUDA(cudaMemsetAsync(m->err, 0, sizeof(uint32_t), s));
+    VM_STAGE_BEGIN(hk, kStOrder, s);
+    VM_CUDA(seg_order_bricks(m->brick_table, m->nb_total, b, sms, s));
+    VM_STAGE_END(hk, kStOrder, s);
+    VM_CUDA(cudaMemcpyAsync(m->hctr, b.ctr, sizeof(SegCounters), cudaMemcpyDeviceToHost, s));
+    VM_CUDA(cudaStreamSynchronize(s));
+    const uint32_t n_sorted = m->hctr->n_sorted;
+    VM_TRY(alloc_vox(m, n_sorted));
+    // 2. means, normals, classification, clustering, cluster numbering
+    VM_CUDA(seg_voxels(m->g, n_sorted, m->S, m->C, *params, b, m->err, sms, s, hk));
+    VM_CUDA(cudaMemcpyAsync(m->hctr, b.ctr, sizeof(SegCounters), cudaMemcpyDeviceToHost, s));
+    uint32_t map_err = 0, seg_err = 0;
+    VM_CUDA(cudaMemcpyAsync(&map_err, &m->ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VM_CUDA(cudaMemcpyAsync(&seg_err, m->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VM_CUDA(cudaStreamSynchronize(s));
+    m->last = *m->hctr;
+    const uint32_t K = m->last.k, n_kept = m->last.n_kept;
+    // 3. cluster point lists in cluster order
+    VM_STAGE_BEGIN(hk, kStClusters, s);
+    VM_CUDA(seg_clusters(m->g, K, n_kept, b, sms, s));
+    VM_STAGE_END(hk, kStClusters, s);
+    m->segmented = true;
+    // 4. RANSAC, refit, hull, pack
+    vm_status st = fit_and_pack(m->fit, b.pts, b.cl_off, b.cl_label, K, n_kept, *params, m->tune, s, out);
+    if (st != VM_OK) return st;
+    if (seg_err & kErrTimeout) {
+        set_error("union-find reached its iteration cap");
+        return VM_ERR_TIMEOUT;
+    }
+    if (map_err & kErrCapacity) {
+        set_error("brick pool full: points in unallocated bricks were dropped");
+        return VM_ERR_CAPACITY;
+    }
+    return VM_OK;
+}
+
+vm_status vm_planes_free(vm_planes* p) {
+    if (!p) return VM_OK;
+    free(p->planes);
+    free(p->hull_xy);
+    free(p->hull_xyz);
+    memset(p, 0, sizeof(*p));
+    return VM_OK;
+}
+
+vm_status vm_get_stats(vm_map* m, vm_stats* out) {
+    VM_TRY(check_map(m));
+    if (!out) {
+        set_error("null output");
+        return VM_ERR_INVALID_ARG;
+    }
+    MapCounters c;
+    VM_CUDA(cudaMemcpyAsync(&c, m->ctr, sizeof(c), cudaMemcpyDeviceToHost, m->stream));
+    VM_CUDA(cudaStreamSynchronize(m->stream));
+    memset(out, 0, sizeof(*out));
+    out->points_integrated = c.integrated;
+    out->points_dropped = c.dropped;
+    out->points_no_capacity = c.no_capacity;
+    out->bricks_allocated = c.n_bricks < m->capacity ? c.n_bricks : m->capacity;
+    out->brick_capacity = m->capacity;
+    out->occupied_voxels = m->last.n_occ;
+    out->steppable_voxels = m->last.n_vert;
+    out->clusters = m->last.k;
+    out->device_bytes = m->pool.bytes + m->stage.bytes + m->brick_mem.bytes + m->vox_mem.bytes + m->fit.mem.bytes +
+                        m->fit.out.bytes;
+    if (c.err & kErrCapacity) {
+        set_error("brick pool full");
+        return VM_ERR_CAPACITY;
+    }
+    return VM_OK;
+}
+
+vm_status vm_export_voxels(vm_map* m, uint32_t* vid, int64_t* sums, uint32_t* counts, uint32_t cap, uint32_t* n) {
+    VM_TRY(check_map(m));
+    if (!n) {
+        set_error("null count output");
+        return VM_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = m->stream;
+    if (!m->vox_mem.p) VM_TRY(alloc_vox(m, 1));  // scan scratch
+    VM_CUDA(seg_order_bricks(m->brick_table, m->nb_total, m->seg, device_sms(), s));
+    VM_CUDA(cudaMemcpyAsync(m->hctr, m->seg.ctr, sizeof(SegCounters), cudaMemcpyDeviceToHost, s));
+    VM_CUDA(cudaStreamSynchronize(s));
+    const uint32_t nb = m->hctr->n_sorted;
+    std::vector<int32_t> slot(nb), key(nb);
+    std::vector<unsigned long long> S((size_t)m->capacity * 3 * kBrickVox);
+    std::vector<uint32_t> C((size_t)m->capacity * kBrickVox);
+    if (nb) {
+        VM_CUDA(cudaMemcpyAsync(slot.data(), m->seg.sorted_slot, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaMemcpyAsync(key.data(), m->seg.sorted_key, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaMemcpyAsync(S.data(), m->S, S.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaMemcpyAsync(C.data(), m->C, C.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    }
+    VM_CUDA(cudaStreamSynchronize(s));
+    uint32_t k = 0;
+    for (uint32_t r = 0; r < nb; ++r) {
+        for (int l = 0; l < kBrickVox; ++l) {
+            const size_t sv = (size_t)slot[r] * kBrickVox + l;
+            if (!C[sv]) continue;
+            if (k < cap) {
+                if (vid) vid[k] = (uint32_t)key[r] * kBrickVox + l;
+                if (counts) counts[k] = C[sv];
+                if (sums)
+                    for (int a = 0; a < 3; ++a)
+                        sums[3 * (size_t)k + a] = (int64_t)S[((size_t)slot[r] * 3 + a) * kBrickVox + l];
+            }
+            ++k;
+        }
+    }
+    *n = k;
+    return VM_OK;
+}
+
+vm_status vm_export_labels(vm_map* m, uint32_t* vid, float* normal, uint8_t* status, uint32_t* label, uint32_t* nbr,
+                           uint32_t cap, uint32_t* n) {
+    VM_TRY(check_map(m));
+    if (!n) {
+        set_error("null count output");
+        return VM_ERR_INVALID_ARG;
+    }
+    *n = 0;
+    if (!m->segmented) return VM_OK;
+    cudaStream_t s = m->stream;
+    const uint32_t nb = m->last.n_sorted;
+    const size_t nv = (size_t)nb * kBrickVox;
+    std::vector<int32_t> key(nb);
+    std::vector<uint8_t> st(nv), nb8(nv);
+    std::vector<float> nrm(3 * nv);
+    std::vector<uint32_t> par(nv);
+    if (nb) {
+        VM_CUDA(cudaMemcpyAsync(key.data(), m->seg.sorted_key, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaMemcpyAsync(st.data(), m->seg.status, nv, cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaMemcpyAsync(nb8.data(), m->seg.nbr, nv, cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaMemcpyAsync(par.data(), m->seg.parent, nv * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        for (int a = 0; a < 3; ++a)
+            VM_CUDA(cudaMemcpyAsync(nrm.data() + a * nv, m->seg.nrm + a * m->seg.nv, nv * sizeof(float),
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    VM_CUDA(cudaStreamSynchronize(s));
+    uint32_t k = 0;
+    for (size_t i = 0; i < nv; ++i) {
+        if (!st[i]) continue;
+        if (k < cap) {
+            const uint32_t v = (uint32_t)key[i / kBrickVox] * kBrickVox + (uint32_t)(i % kBrickVox);
+            if (vid) vid[k] = v;
+            if (normal)
+                for (int a = 0; a < 3; ++a) normal[3 * (size_t)k + a] = nrm[a * nv + i];
+            if (status) status[k] = st[i];
+            if (nbr) nbr[k] = nb8[i];
+            if (label) {
+                const uint32_t p = par[i];
+                label[k] = (p == kNone) ? kNone : (uint32_t)key[p / kBrickVox] * kBrickVox + p % kBrickVox;
+            }
+        }
+        ++k;
+    }
+    *n = k;
+    return VM_OK;
+}
+
+vm_status vm_export_clusters(vm_map* m, float* pts, uint32_t* vid, uint8_t* inlier, uint32_t cap, uint32_t* n) {
+    VM_TRY(check_map(m));
+    if (!n) {
+        set_error("null count output");
+        return VM_ERR_INVALID_ARG;
+    }
+    *n = 0;
+    if (!m->segmented) return VM_OK;
+    const uint32_t np = m->last.n_kept;
+    const uint32_t w = np < cap ? np : cap;
+    cudaStream_t s = m->stream;
+    if (w) {
+        if (pts) VM_CUDA(cudaMemcpyAsync(pts, m->seg.pts, (size_t)w * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (vid) VM_CUDA(cudaMemcpyAsync(vid, m->seg.pt_vid, (size_t)w * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        if (inlier && m->last.k)
+            VM_CUDA(cudaMemcpyAsync(inlier, m->fit.fb.inlier, (size_t)w, cudaMemcpyDeviceToHost, s));
+    }
+    VM_CUDA(cudaStreamSynchronize(s));
+    *n = np;
+    return VM_OK;
+}
+
+static thread_local FitContext tl_fit;
+
+vm_status vm_stage_timing(vm_map* map, int enable) {
+    FitContext& fc = map ? map->fit : tl_fit;
+    fc.timer.fold();
+    fc.timer.on = enable != 0;
+    return VM_OK;
+}
+
+vm_status vm_stage_times(vm_map* map, double* ms, uint64_t* calls, uint32_t cap, uint32_t* n_stages) {
+    FitContext& fc = map ? map->fit : tl_fit;
+    if (map && map->stream) VM_CUDA(cudaStreamSynchronize(map->stream));
+    fc.timer.fold();
+    for (uint32_t i = 0; i < (uint32_t)kNumStages && i < cap; ++i) {
+        if (ms) ms[i] = fc.timer.ms[i];
+        if (calls) calls[i] = fc.timer.calls[i];
+        fc.timer.ms[i] = 0.0;
+        fc.timer.calls[i] = 0;
+    }
+    if (n_stages) *n_stages = kNumStages;
+    return VM_OK;
+}
+
+const char* vm_stage_name(uint32_t stage) { return stage < (uint32_t)kNumStages ? kStageNames[stage] : ""; }
+
+uint64_t vm_launch_count(void) { return g_launches.load(); }
+
+vm_status vm_fit_planes(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
+                        const vm_segment_params* params, void* stream, vm_planes* out) {
+    VM_TRY(check_params(params));
+    if (!out || (k && (!xyz || !off))) {
+        set_error("null argument");
+        return VM_ERR_INVALID_ARG;
+    }
+    memset(out, 0, sizeof(*out));
+    if (k == 0) return VM_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t npts = 0;
+    VM_CUDA(cudaMemcpyAsync(&npts, off + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    VM_CUDA(cudaStreamSynchronize(s));
+    return fit_and_pack(tl_fit, xyz, off, labels, k, npts, *params, default_tuning(), s, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,788 @@
+// fit.cu -- cluster-parallel plane estimation (Sec. III.C, multi-plane
+// estimation stages a-c), inlier refit and boundary polygons (Sec. III.C,
+// boundary polygon generation), for all clusters of a batch at once.
+//
+//  k_hyp     stage a: one thread per (cluster, hypothesis): three sample
+//            indices from Philox4x64-10, plane through the samples.
+//  k_score   stage b: a persistent kernel; CTAs pull (cluster, point tile)
+//            work items from an atomic queue, stage the tile in shared memory
+//            and test every point against every hypothesis held in registers;
+//            integer counts are summed in shared memory and added to global
+//            memory with integer atomics (order-free, hence exact).
+//  k_select  stage c: max count, lowest hypothesis index on ties; in-plane
+//            basis and hull origin.
+//  k_extract inliers of the selected plane, centroid partial sums and the
+//            octagon of extreme points (exact integer keys).
+//  k_filter  covariance partial sums; points strictly inside the octagon
+//            cannot be hull vertices and are dropped (the GPU filtering step
+//            of the cited convex-hull method), the rest are appended.
+//  k_hull    per cluster: TLS refit in double from the partial sums; sort of
+//            the surviving quantised points in shared memory (bitonic), then
+//            Andrew's monotone chain with exact int64 orientation tests; a
+//            gift-wrapping pass over global memory when the survivors exceed
+//            shared memory.
+#include <climits>
+
+#include "vm_internal.cuh"
+
+namespace vmx {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kHullCap = 4096;  // survivors sorted in shared memory
+
+// ---------------------------------------------------------------- Philox
+__device__ __forceinline__ void philox4x64_10(const unsigned long long ctr[4], const unsigned long long key[2],
+                                              unsigned long long out[4]) {
+    unsigned long long x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    unsigned long long k0 = key[0], k1 = key[1];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B97F4A7C15ull;
+            k1 += 0xBB67AE8584CAA73Bull;
+        }
+        const unsigned long long m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+        const unsigned long long hi0 = __umul64hi(m0, x0), lo0 = m0 * x0;
+        const unsigned long long hi1 = __umul64hi(m1, x2), lo1 = m1 * x2;
+        x0 = hi1 ^ x1 ^ k0;
+        x1 = lo1;
+        x2 = hi0 ^ x3 ^ k1;
+        x3 = lo0;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+__device__ __forceinline__ float plane_dist(float nx, float ny, float nz, float d, float px, float py, float pz) {
+    return fabsf(__fmaf_rn(nz, pz, __fmaf_rn(ny, py, __fmaf_rn(nx, px, d))));
+}
+
+__device__ __forceinline__ uint32_t find_cluster(const uint32_t* __restrict__ item_off, uint32_t k, uint32_t it) {
+    uint32_t lo = 0, hi = k;  // largest c with item_off[c] <= it
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (item_off[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- stage a
+__global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                      const uint32_t* __restrict__ labels, uint32_t k, int H, unsigned long long seed,
+                      float4* __restrict__ hyp, uint8_t* __restrict__ valid, uint32_t* __restrict__ counts) {
+    const size_t total = (size_t)k * H;
+    for (size_t t = (size_t)blockIdx.x * kT + threadIdx.x; t < total; t += (size_t)gridDim.x * kT) {
+        const uint32_t c = (uint32_t)(t / H), h = (uint32_t)(t % H);
+        const uint32_t base = off[c], n = off[c + 1] - base;
+        const uint32_t label = labels ? labels[c] : c;
+        const unsigned long long ctr[4] = {label, h, 0ull, 0ull}, key[2] = {seed, 0ull};
+        unsigned long long r[4];
+        philox4x64_10(ctr, key, r);
+        const uint32_t i0 = (uint32_t)__umul64hi(r[0], n), i1 = (uint32_t)__umul64hi(r[1], n),
+                       i2 = (uint32_t)__umul64hi(r[2], n);
+        counts[t] = 0;
+        uint8_t ok = (i0 != i1) && (i0 != i2) && (i1 != i2);
+        float4 pl = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0x7f800000));  // never an inlier
+        if (ok) {
+            const float* p0 = pts + 3 * ((size_t)base + i0);
+            const float* p1 = pts + 3 * ((size_t)base + i1);
+            const float* p2 = pts + 3 * ((size_t)base + i2);
+            const float e1x = __fsub_rn(p1[0], p0[0]), e1y = __fsub_rn(p1[1], p0[1]), e1z = __fsub_rn(p1[2], p0[2]);
+            const float e2x = __fsub_rn(p2[0], p0[0]), e2y = __fsub_rn(p2[1], p0[1]), e2z = __fsub_rn(p2[2], p0[2]);
+            const float cx = __fmaf_rn(e1y, e2z, -__fmul_rn(e1z, e2y));
+            const float cy = __fmaf_rn(e1z, e2x, -__fmul_rn(e1x, e2z));
+            const float cz = __fmaf_rn(e1x, e2y, -__fmul_rn(e1y, e2x));
+            const float nn = __fmaf_rn(cz, cz, __fmaf_rn(cy, cy, __fmul_rn(cx, cx)));
+            if (nn > 0.0f) {
+                const float inv = __fdiv_rn(1.0f, __fsqrt_rn(nn));
+                const float nx = __fmul_rn(cx, inv), ny = __fmul_rn(cy, inv), nz = __fmul_rn(cz, inv);
+                const float d = -__fmaf_rn(nz, p0[2], __fmaf_rn(ny, p0[1], __fmul_rn(nx, p0[0])));
+                pl = make_float4(nx, ny, nz, d);
+            } else {
+                ok = 0;
+            }
+        }
+        hyp[t] = pl;
+        valid[t] = ok;
+    }
+}
+
+// ---------------------------------------------------------------- stage b
+template <int R>
+__global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                                              const uint32_t* __restrict__ item_off, uint32_t k, int H, int T,
+                                              const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
+                                              uint32_t* __restrict__ queue, float eps) {
+    extern __shared__ float4 sp[];                // T staged points
+    uint32_t* red = reinterpret_cast<uint32_t*>(sp + T);  // [P][G*R]
+    __shared__ uint32_t s_item;
+    const int G = (H + R - 1) / R;                // threads per point subset
+    const int P = kT / G;                         // point subsets
+    const int g = threadIdx.x / G, j = threadIdx.x % G;
+    const bool active = g < P;
+    const uint32_t n_items = item_off[k];
+    for (int guard = 0; guard < kLoopCap; ++guard) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= n_items) break;
+        const uint32_t c = find_cluster(item_off, k, it);
+        const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
+        const uint32_t end = min(off[c + 1], start + (uint32_t)T);
+        const int cnt = (int)(end - start);
+        for (int q = threadIdx.x; q < cnt; q += kT) {
+            const float* p = pts + 3 * ((size_t)start + q);
+            sp[q] = make_float4(p[0], p[1], p[2], 0.0f);
+        }
+        float4 pl[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int h = j * R + r;
+            pl[r] = (active && h < H) ? hyp[(size_t)c * H + h]
+                                      : make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0x7f800000));
+        }
+        __syncthreads();
+        uint32_t acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0;
+        if (active) {
+            for (int q = g; q < cnt; q += P) {
+                const float4 p = sp[q];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    acc[r] += plane_dist(pl[r].x, pl[r].y, pl[r].z, pl[r].w, p.x, p.y, p.z) <= eps;
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) red[g * (G * R) + j * R + r] = acc[r];
+        }
+        __syncthreads();
+        for (int h = threadIdx.x; h < H; h += kT) {
+            uint32_t s = 0;
+            for (int q = 0; q < P; ++q) s += red[q * (G * R) + h];
+            if (s) atomicAdd(&counts[(size_t)c * H + h], s);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- stage c
+__global__ void k_select(const float* __restrict__ pts, const uint32_t* __restrict__ off, uint32_t k, int H,
+                         const float4* __restrict__ hyp, const uint8_t* __restrict__ valid,
+                         const uint32_t* __restrict__ counts, FitCluster* __restrict__ cl) {
+    __shared__ unsigned long long wbest[kT / 32];
+    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
+        unsigned long long best = 0;  // (count << 32) | ~h ; 0 = none
+        for (int h = threadIdx.x; h < H; h += kT) {
+            const size_t t = (size_t)c * H + h;
+            if (valid[t]) {
+                const unsigned long long key = ((unsigned long long)counts[t] << 32) | (uint32_t)(~(uint32_t)h);
+                best = key > best ? key : best;
+            }
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, s);
+            best = o > best ? o : best;
+        }
+        if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < kT / 32; ++w) best = wbest[w] > best ? wbest[w] : best;
+            FitCluster f;
+            memset(&f, 0, sizeof(f));
+            const uint32_t n = off[c + 1] - off[c];
+            if (best != 0) {
+                const int h = (int)(~(uint32_t)(best & 0xffffffffu));
+                const float4 pl = hyp[(size_t)c * H + h];
+                f.best_h = h;
+                f.n[0] = pl.x; f.n[1] = pl.y; f.n[2] = pl.z; f.d = pl.w;
+                f.inliers = (uint32_t)(best >> 32);
+                const float nx = pl.x, ny = pl.y, nz = pl.z;
+                float ux, uy, uz;
+                if (fabsf(nx) < 0.9f) { ux = 0.0f; uy = -nz; uz = ny; }  // e_x cross n
+                else { ux = nz; uy = 0.0f; uz = -nx; }                   // e_y cross n
+                const float ul = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
+                const float ui = __fdiv_rn(1.0f, __fsqrt_rn(ul));
+                ux = __fmul_rn(ux, ui); uy = __fmul_rn(uy, ui); uz = __fmul_rn(uz, ui);
+                f.u[0] = ux; f.u[1] = uy; f.u[2] = uz;
+                f.v[0] = __fmaf_rn(ny, uz, -__fmul_rn(nz, uy));
+                f.v[1] = __fmaf_rn(nz, ux, -__fmul_rn(nx, uz));
+                f.v[2] = __fmaf_rn(nx, uy, -__fmul_rn(ny, ux));
+            } else {
+                f.best_h = -1;
+            }
+            if (n) {
+                const float* p = pts + 3 * (size_t)off[c];
+                f.o[0] = p[0]; f.o[1] = p[1]; f.o[2] = p[2];
+            }
+            cl[c] = f;
+        }
+        __syncthreads();
+    }
+}
+
+// Quantised in-plane coordinates (units of 2^-16 m) relative to the origin.
+__device__ __forceinline__ int2 quantise(const FitCluster& f, float px, float py, float pz) {
+    const float qx = __fsub_rn(px, f.o[0]), qy = __fsub_rn(py, f.o[1]), qz = __fsub_rn(pz, f.o[2]);
+    const float a = __fmaf_rn(qz, f.u[2], __fmaf_rn(qy, f.u[1], __fmul_rn(qx, f.u[0])));
+    const float b = __fmaf_rn(qz, f.v[2], __fmaf_rn(qy, f.v[1], __fmul_rn(qx, f.v[0])));
+    return make_int2(__float2int_rn(__fmul_rn(a, 65536.0f)), __float2int_rn(__fmul_rn(b, 65536.0f)));
+}
+
+// Directions of the octagon, counter-clockwise: (1,0) (1,1) (0,1) (-1,1) (-1,0) (-1,-1) (0,-1) (1,-1).
+__device__ __forceinline__ int32_t dir_value(int dir, int2 p) {
+    switch (dir) {
+        case 0: return p.x;
+        case 1: return p.x + p.y;
+        case 2: return p.y;
+        case 3: return p.y - p.x;
+        case 4: return -p.x;
+        case 5: return -p.x - p.y;
+        case 6: return -p.y;
+        default: return p.x - p.y;
+    }
+}
+
+__device__ __forceinline__ unsigned long long ext_key(int32_t v, uint32_t idx) {
+    return ((unsigned long long)((uint32_t)v ^ 0x80000000u) << 32) | idx;
+}
+
+template <typename Tv>
+__device__ __forceinline__ Tv block_sum(Tv v, Tv* sh) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    Tv t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kT / 32; ++w) t += sh[w];
+    return t;  // valid in thread 0
+}
+
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, s);
+        v = o > v ? o : v;
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kT / 32; ++w) t = sh[w] > t ? sh[w] : t;
+    return t;
+}
+
+// Inliers, centroid partials (relative to the origin) and octagon extremes.
+__global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                                                const uint32_t* __restrict__ item_off, uint32_t k, int T,
+                                                FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
+                                                float* __restrict__ part, float eps) {
+    __shared__ float shf[kT / 32];
+    __shared__ uint32_t shu[kT / 32];
+    __shared__ unsigned long long shm[kT / 32];
+    const uint32_t n_items = item_off[k];
+    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const uint32_t c = find_cluster(item_off, k, it);
+        const FitCluster f = cl[c];
+        const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
+        const uint32_t end = min(off[c + 1], start + (uint32_t)T);
+        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+        uint32_t cnt = 0;
+        unsigned long long ext[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) ext[d] = 0;
+        for (uint32_t q = start + threadIdx.x; q < end; q += kT) {
+            const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
+            const bool in = f.best_h >= 0 && plane_dist(f.n[0], f.n[1], f.n[2], f.d, px, py, pz) <= eps;
+            inlier[q] = in;
+            if (!in) continue;
+            ++cnt;
+            sx += __fsub_rn(px, f.o[0]);
+            sy += __fsub_rn(py, f.o[1]);
+            sz += __fsub_rn(pz, f.o[2]);
+            const int2 xy = quantise(f, px, py, pz);
+            const uint32_t idx = q - off[c];
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                const unsigned long long key = ext_key(dir_value(d, xy), idx);
+                ext[d] = key > ext[d] ? key : ext[d];
+            }
+        }
+        const float tx = block_sum(sx, shf), ty = block_sum(sy, shf), tz = block_sum(sz, shf);
+        const uint32_t tc = block_sum(cnt, shu);
+        if (threadIdx.x == 0) {
+            float* pp = part + (size_t)it * 10;
+            pp[0] = __uint_as_float(tc);
+            pp[1] = tx; pp[2] = ty; pp[3] = tz;
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const unsigned long long m = block_max_u64(ext[d], shm);
+            if (threadIdx.x == 0 && m) atomicMax(&cl[c].ext[d], m);
+        }
+        __syncthreads();
+    }
+}
+
+// Per cluster: inlier count and centroid (double over the per-item partials).
+__global__ void k_centroid(const uint32_t* __restrict__ item_off, uint32_t k, const float* __restrict__ part,
+                           FitCluster* __restrict__ cl, double* __restrict__ cen) {
+    for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT) {
+        double sx = 0, sy = 0, sz = 0;
+        uint32_t n = 0;
+        for (uint32_t it = item_off[c]; it < item_off[c + 1]; ++it) {
+            const float* pp = part + (size_t)it * 10;
+            n += __float_as_uint(pp[0]);
+            sx += pp[1]; sy += pp[2]; sz += pp[3];
+        }
+        FitCluster& f = cl[c];
+        f.inliers = n;
+        double cx = f.o[0], cy = f.o[1], cz = f.o[2];
+        if (n) { cx += sx / n; cy += sy / n; cz += sz / n; }
+        cen[3 * c] = cx; cen[3 * c + 1] = cy; cen[3 * c + 2] = cz;
+        f.c[0] = (float)cx; f.c[1] = (float)cy; f.c[2] = (float)cz;
+    }
+}
+
+__device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b) {
+    return (long long)(a.x - o.x) * (long long)(b.y - o.y) - (long long)(a.y - o.y) * (long long)(b.x - o.x);
+}
+
+// Covariance partials about the centroid and the octagon filter.
+__global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                                               const uint32_t* __restrict__ item_off, uint32_t k, int T,
+                                               FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
+                                               const double* __restrict__ cen, float* __restrict__ part,
+                                               int2* __restrict__ surv) {
+    __shared__ float shf[kT / 32];
+    __shared__ int2 poly[9];
+    __shared__ int npoly;
+    const uint32_t n_items = item_off[k];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const uint32_t c = find_cluster(item_off, k, it);
+        const FitCluster f = cl[c];
+        const uint32_t base = off[c];
+        const uint32_t start = base + (it - item_off[c]) * (uint32_t)T;
+        const uint32_t end = min(off[c + 1], start + (uint32_t)T);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // octagon through the extreme points, counter-clockwise, duplicates removed
+            int m = 0;
+            for (int d = 0; d < 8; ++d) {
+                if (!f.ext[d]) continue;
+                const uint32_t idx = (uint32_t)(f.ext[d] & 0xffffffffu);
+                const float* p = pts + 3 * ((size_t)base + idx);
+                const int2 xy = quantise(f, p[0], p[1], p[2]);
+                if (m && poly[m - 1].x == xy.x && poly[m - 1].y == xy.y) continue;
+                poly[m++] = xy;
+            }
+            if (m > 1 && poly[m - 1].x == poly[0].x && poly[m - 1].y == poly[0].y) --m;
+            // a degenerate (zero-area) polygon filters nothing
+            long long area2 = 0;
+            for (int i = 0; i < m; ++i) {
+                const int2 a = poly[i], b = poly[(i + 1) % m];
+                area2 += (long long)a.x * b.y - (long long)a.y * b.x;
+            }
+            npoly = (m >= 3 && area2 > 0) ? m : 0;
+        }
+        __syncthreads();
+        const int m = npoly;
+        const float cx = (float)cen[3 * c], cy = (float)cen[3 * c + 1], cz = (float)cen[3 * c + 2];
+        float a00 = 0, a11 = 0, a22 = 0, a01 = 0, a02 = 0, a12 = 0;
+        for (uint32_t q0 = start; q0 < end; q0 += kT) {
+            const uint32_t q = q0 + threadIdx.x;
+            bool keep = false;
+            int2 xy = make_int2(0, 0);
+            if (q < end && inlier[q]) {
+                const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
+                const float rx = __fsub_rn(px, cx), ry = __fsub_rn(py, cy), rz = __fsub_rn(pz, cz);
+                a00 = __fmaf_rn(rx, rx, a00); a11 = __fmaf_rn(ry, ry, a11); a22 = __fmaf_rn(rz, rz, a22);
+                a01 = __fmaf_rn(rx, ry, a01); a02 = __fmaf_rn(rx, rz, a02); a12 = __fmaf_rn(ry, rz, a12);
+                xy = quantise(f, px, py, pz);
+                keep = true;
+                for (int i = 0; i < m; ++i) {  // strictly inside every edge -> not a hull vertex
+                    if (cross3(poly[i], poly[(i + 1) % m], xy) <= 0) break;
+                    if (i == m - 1) keep = false;
+                }
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, keep);
+            uint32_t pos = 0;
+            if (lane == 0 && b) pos = atomicAdd(&cl[c].n_surv, (uint32_t)__popc(b));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (keep) surv[base + pos + __popc(b & ((1u << lane) - 1u))] = xy;
+        }
+        const float s0 = block_sum(a00, shf), s1 = block_sum(a11, shf), s2 = block_sum(a22, shf);
+        const float s3 = block_sum(a01, shf), s4 = block_sum(a02, shf), s5 = block_sum(a12, shf);
+        if (threadIdx.x == 0) {
+            float* pp = part + (size_t)it * 10 + 4;
+            pp[0] = s0; pp[1] = s1; pp[2] = s2; pp[3] = s3; pp[4] = s4; pp[5] = s5;
+        }
+    }
+}
+
+// Double-precision cyclic Jacobi for the refit (same rotation as the FP32 one).
+__device__ void jacobi3_d(double A[6], int sweeps, double v[3][3], double d[3]) {
+    double a[3][3] = {{A[0], A[3], A[4]}, {A[3], A[1], A[5]}, {A[4], A[5], A[2]}};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) v[r][c] = (r == c) ? 1.0 : 0.0;
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int k = 0; k < 3; ++k) {
+            const int p = (k == 2) ? 1 : 0, q = (k == 0) ? 1 : 2, r = 2 - k;
+            const double apq = a[p][q];
+            if (apq == 0.0) continue;
+            const double app = a[p][p], aqq = a[q][q];
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double cc = 1.0 / sqrt(1.0 + t * t), s = t * cc;
+            a[p][p] = app - t * apq;
+            a[q][q] = aqq + t * apq;
+            a[p][q] = a[q][p] = 0.0;
+            const double arp = a[r][p], arq = a[r][q];
+            a[r][p] = a[p][r] = cc * arp - s * arq;
+            a[r][q] = a[q][r] = s * arp + cc * arq;
+            for (int i = 0; i < 3; ++i) {
+                const double vip = v[i][p], viq = v[i][q];
+                v[i][p] = cc * vip - s * viq;
+                v[i][q] = s * vip + cc * viq;
+            }
+        }
+    }
+    d[0] = a[0][0]; d[1] = a[1][1]; d[2] = a[2][2];
+}
+
+__device__ __forceinline__ unsigned long long xy_key(int2 p) {
+    return ((unsigned long long)((uint32_t)p.x ^ 0x80000000u) << 32) | ((uint32_t)p.y ^ 0x80000000u);
+}
+__device__ __forceinline__ int2 key_xy(unsigned long long k) {
+    return make_int2((int32_t)((uint32_t)(k >> 32) ^ 0x80000000u), (int32_t)((uint32_t)k ^ 0x80000000u));
+}
+
+// Monotone chain over sorted unique points; one thread builds a chain.
+__device__ int chain(const unsigned long long* P, int u, bool upper, uint32_t* st) {
+    int kk = 0;
+    for (int s = 0; s < u; ++s) {
+        const int i = upper ? (u - 1 - s) : s;
+        const int2 p = key_xy(P[i]);
+        while (kk >= 2 && cross3(key_xy(P[st[kk - 2]]), key_xy(P[st[kk - 1]]), p) <= 0) --kk;
+        st[kk++] = (uint32_t)i;
+    }
+    return kk;
+}
+
+// "Better next vertex" from cur: more clockwise, or collinear and farther.
+__device__ __forceinline__ bool jarvis_better(int2 cur, int2 a, bool a_ok, int2 b, bool b_ok) {
+    if (!b_ok) return false;
+    if (!a_ok) return true;
+    const long long cr = cross3(cur, a, b);
+    if (cr < 0) return true;
+    if (cr > 0) return false;
+    const long long da = (long long)(a.x - cur.x) * (a.x - cur.x) + (long long)(a.y - cur.y) * (a.y - cur.y);
+    const long long db = (long long)(b.x - cur.x) * (b.x - cur.x) + (long long)(b.y - cur.y) * (b.y - cur.y);
+    return db > da;
+}
+
+__global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
+                                             uint32_t k, const float* __restrict__ part,
+                                             const double* __restrict__ cen, FitCluster* __restrict__ cl,
+                                             const int2* __restrict__ surv, int2* __restrict__ hull,
+                                             uint32_t* __restrict__ hull_cnt, uint32_t* __restrict__ err) {
+    extern __shared__ unsigned long long sk[];              // kHullCap keys, then kHullCap unique
+    unsigned long long* uq = sk + kHullCap;
+    uint32_t* st_lo = reinterpret_cast<uint32_t*>(uq + kHullCap);
+    uint32_t* st_hi = st_lo + kHullCap;
+    __shared__ uint32_t wsum[kT / 32];
+    __shared__ int s_u, s_klo, s_khi;
+    __shared__ int2 jcand[kT];
+    __shared__ int jok[kT];
+    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
+        __syncthreads();
+        const FitCluster f = cl[c];
+        const uint32_t base = off[c];
+        if (threadIdx.x == 0) {
+            // refit: total least squares on the inliers, covariance summed in double
+            uint32_t flags = 0;
+            float rn[3] = {0.0f, 0.0f, 0.0f}, rd = 0.0f;
+            if (f.best_h >= 0 && f.inliers > 0) {
+                double A[6] = {0, 0, 0, 0, 0, 0};
+                for (uint32_t it = item_off[c]; it < item_off[c + 1]; ++it)
+                    for (int e = 0; e < 6; ++e) A[e] += part[(size_t)it * 10 + 4 + e];
+                double V[3][3], D[3];
+                jacobi3_d(A, 10, V, D);
+                int m = 0;
+                if (D[1] < D[m]) m = 1;
+                if (D[2] < D[m]) m = 2;
+                double x = V[0][m], y = V[1][m], z = V[2][m];
+                const double l = sqrt(x * x + y * y + z * z);
+                x /= l; y /= l; z /= l;
+                if (z < 0.0 || (z == 0.0 && (y < 0.0 || (y == 0.0 && x < 0.0)))) { x = -x; y = -y; z = -z; }
+                double e0 = D[0], e1 = D[1], e2 = D[2], t;
+                if (e1 < e0) { t = e0; e0 = e1; e1 = t; }
+                if (e2 < e1) { t = e1; e1 = e2; e2 = t; }
+                if (e1 < e0) { t = e0; e0 = e1; e1 = t; }
+                if (!(e1 >= 10.0 * e0)) flags |= 1u;
+                rn[0] = (float)x; rn[1] = (float)y; rn[2] = (float)z;
+                rd = (float)(-(x * cen[3 * c] + y * cen[3 * c + 1] + z * cen[3 * c + 2]));
+            }
+            cl[c].refit_n[0] = rn[0]; cl[c].refit_n[1] = rn[1]; cl[c].refit_n[2] = rn[2];
+            cl[c].refit_d = rd;
+            cl[c].flags = flags;
+        }
+        const int s = (int)f.n_surv;
+        int2* out = hull + base;
+        if (s <= kHullCap) {
+            int n2 = 1;
+            while (n2 < s) n2 <<= 1;
+            for (int i = threadIdx.x; i < n2; i += kT) sk[i] = (i < s) ? xy_key(surv[base + i]) : ~0ull;
+            __syncthreads();
+            // bitonic sort, ascending
+            for (int size = 2; size <= n2; size <<= 1) {
+                for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                    for (int i = threadIdx.x; i < n2; i += kT) {
+                        const int jdx = i ^ stride;
+                        if (jdx > i) {
+                            const bool up = (i & size) == 0;
+                            const unsigned long long a = sk[i], b = sk[jdx];
+                            if ((a > b) == up) { sk[i] = b; sk[jdx] = a; }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            // unique (order-preserving compaction by a block scan in chunks)
+            int u = 0;
+            for (int c0 = 0; c0 < s; c0 += kT) {
+                const int i = c0 + threadIdx.x;
+                const uint32_t fl = (i < s) && (i == 0 || sk[i] != sk[i - 1]);
+                uint32_t inc = fl;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+                    if ((threadIdx.x & 31) >= o) inc += t;
+                }
+                if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = inc;
+                __syncthreads();
+                uint32_t wpre = 0, tot = 0;
+                for (int w = 0; w < kT / 32; ++w) {
+                    if (w < (int)(threadIdx.x >> 5)) wpre += wsum[w];
+                    tot += wsum[w];
+                }
+                if (fl) uq[u + wpre + inc - 1] = sk[i];
+                u += (int)tot;
+                __syncthreads();
+            }
+            if (u < 3) {
+                for (int i = threadIdx.x; i < u; i += kT) out[i] = key_xy(uq[i]);
+                if (threadIdx.x == 0) hull_cnt[c] = (uint32_t)u;
+            } else {
+                if (threadIdx.x == 0) s_klo = chain(uq, u, false, st_lo);
+                if (threadIdx.x == 32) s_khi = chain(uq, u, true, st_hi);
+                __syncthreads();
+                const int klo = s_klo - 1, khi = s_khi - 1;
+                for (int i = threadIdx.x; i < klo + khi; i += kT)
+                    out[i] = key_xy(uq[i < klo ? st_lo[i] : st_hi[i - klo]]);
+                if (threadIdx.x == 0) hull_cnt[c] = (uint32_t)(klo + khi);
+            }
+        } else {
+            // gift wrapping over the survivors in global memory
+            int2 best = make_int2(INT_MAX, INT_MAX);
+            unsigned long long bk = ~0ull;
+            for (int i = threadIdx.x; i < s; i += kT) {
+                const unsigned long long key = xy_key(surv[base + i]);
+                bk = key < bk ? key : bk;
+            }
+            // block min
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, bk, o);
+                bk = t < bk ? t : bk;
+            }
+            __shared__ unsigned long long wmin[kT / 32];
+            if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = bk;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < kT / 32; ++w) bk = wmin[w] < bk ? wmin[w] : bk;
+                wmin[0] = bk;
+            }
+            __syncthreads();
+            const int2 start = key_xy(wmin[0]);
+            int2 cur = start;
+            int h = 0;
+            if (threadIdx.x == 0) out[h] = cur;
+            ++h;
+            for (int guard = 0; guard <= s; ++guard) {
+                int2 cand = make_int2(0, 0);
+                bool ok = false;
+                for (int i = threadIdx.x; i < s; i += kT) {
+                    const int2 p = surv[base + i];
+                    const bool pok = !(p.x == cur.x && p.y == cur.y);
+                    if (jarvis_better(cur, cand, ok, p, pok)) { cand = p; ok = true; }
+                }
+                jcand[threadIdx.x] = cand;
+                jok[threadIdx.x] = ok;
+                __syncthreads();
+                for (int w = kT / 2; w > 0; w >>= 1) {
+                    if ((int)threadIdx.x < w) {
+                        const int o = threadIdx.x + w;
+                        if (jarvis_better(cur, jcand[threadIdx.x], jok[threadIdx.x], jcand[o], jok[o])) {
+                            jcand[threadIdx.x] = jcand[o];
+                            jok[threadIdx.x] = 1;
+                        }
+                    }
+                    __syncthreads();
+                }
+                const int2 nxt = jcand[0];
+                const bool nok = jok[0];
+                __syncthreads();
+                if (!nok || (nxt.x == start.x && nxt.y == start.y)) break;
+                if (h >= s) {  // more vertices than points: only a broken invariant gets here
+                    if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+                    break;
+                }
+                if (threadIdx.x == 0) out[h] = nxt;
+                ++h;
+                cur = nxt;
+                if (guard == s && threadIdx.x == 0) atomicOr(err, kErrTimeout);
+            }
+            if (threadIdx.x == 0) hull_cnt[c] = (uint32_t)h;
+        }
+    }
+}
+
+__global__ void k_items(const uint32_t* __restrict__ off, uint32_t k, int T, uint32_t* __restrict__ item_cnt) {
+    for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT)
+        item_cnt[c] = (off[c + 1] - off[c] + (uint32_t)T - 1) / (uint32_t)T;
+}
+
+__global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restrict__ labels, uint32_t k,
+                       const FitCluster* __restrict__ cl, const int2* __restrict__ hull,
+                       const uint32_t* __restrict__ hull_off, vm_plane* __restrict__ planes,
+                       int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz) {
+    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
+        const FitCluster f = cl[c];
+        const uint32_t ho = hull_off[c], hn = hull_off[c + 1] - ho;
+        if (threadIdx.x == 0) {
+            vm_plane p;
+            for (int a = 0; a < 3; ++a) {
+                p.normal[a] = f.refit_n[a];
+                p.ransac_normal[a] = f.n[a];
+                p.basis_u[a] = f.u[a];
+                p.basis_v[a] = f.v[a];
+                p.hull_origin[a] = f.o[a];
+            }
+            p.offset = f.refit_d;
+            p.ransac_offset = f.d;
+            p.inlier_count = f.inliers;
+            p.label = labels ? labels[c] : c;
+            p.hull_offset = ho;
+            p.hull_count = hn;
+            p.n_points = off[c + 1] - off[c];
+            p.best_h = f.best_h;
+            p.flags = f.flags;
+            planes[c] = p;
+        }
+        for (uint32_t i = threadIdx.x; i < hn; i += blockDim.x) {
+            const int2 q = hull[off[c] + i];
+            hull_xy[2 * (ho + i)] = q.x;
+            hull_xy[2 * (ho + i) + 1] = q.y;
+            const float a = q.x * (1.0f / 65536.0f), b = q.y * (1.0f / 65536.0f);
+            float x = f.o[0] + a * f.u[0] + b * f.v[0];
+            float y = f.o[1] + a * f.u[1] + b * f.v[1];
+            float z = f.o[2] + a * f.u[2] + b * f.v[2];
+            const float e = f.refit_n[0] * x + f.refit_n[1] * y + f.refit_n[2] * z + f.refit_d;
+            hull_xyz[3 * (ho + i)] = x - e * f.refit_n[0];
+            hull_xyz[3 * (ho + i) + 1] = y - e * f.refit_n[1];
+            hull_xyz[3 * (ho + i) + 2] = z - e * f.refit_n[2];
+        }
+    }
+}
+
+template <int R>
+cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* item_off, uint32_t k, int H, int T,
+                         const float4* hyp, uint32_t* counts, uint32_t* queue, float eps, int grid, cudaStream_t s) {
+    const int G = (H + R - 1) / R;
+    const int P = kT / G;
+    const size_t smem = (size_t)T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_score<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    k_score<R><<<grid, kT, smem, s>>>(pts, off, item_off, k, H, T, hyp, counts, queue, eps);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+FitTuning default_tuning() { return FitTuning{2048, 4, 4}; }
+
+size_t fit_hull_smem() { return (size_t)kHullCap * (2 * sizeof(unsigned long long) + 2 * sizeof(uint32_t)); }
+
+cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, uint32_t k, uint32_t npts,
+                       const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int sms, cudaStream_t s,
+                       StageHook* hk) {
+    (void)npts;
+    if (k == 0) return cudaSuccess;
+    const int H = (int)p.n_hyp;
+    const int T = t.tile;
+    cudaError_t e;
+    VM_STAGE_BEGIN(hk, kStHyp, s);
+    k_items<<<(k + kT - 1) / kT, kT, 0, s>>>(off, k, T, fb.item_off);
+    e = exclusive_scan_u32(fb.item_off, fb.item_off, fb.item_off + k, k, fb.scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(fb.queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    const size_t kh = (size_t)k * H;
+    const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
+    k_hyp<<<hgrid, kT, 0, s>>>(pts, off, labels, k, H, p.seed, fb.hyp, fb.hyp_valid, fb.counts);
+    VM_STAGE_END(hk, kStHyp, s);
+    count_launch(2);
+    const int grid = sms * t.ctas_per_sm;
+    int R = t.hyp_per_thread;
+    while (R < 8 && (H + R - 1) / R > kT) R <<= 1;  // at most one subset row of kT threads
+    VM_STAGE_BEGIN(hk, kStScore, s);
+    switch (R) {
+        case 1: e = launch_score<1>(pts, off, fb.item_off, k, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        case 2: e = launch_score<2>(pts, off, fb.item_off, k, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        case 8: e = launch_score<8>(pts, off, fb.item_off, k, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        default: e = launch_score<4>(pts, off, fb.item_off, k, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    VM_STAGE_END(hk, kStScore, s);
+    count_launch(1);
+    const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;
+    VM_STAGE_BEGIN(hk, kStExtract, s);
+    k_select<<<cgrid, kT, 0, s>>>(pts, off, k, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
+    const unsigned igrid = (unsigned)sms * 8;
+    k_extract<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, k, T, fb.cl, fb.inlier, fb.part, p.eps);
+    k_centroid<<<(k + kT - 1) / kT, kT, 0, s>>>(fb.item_off, k, fb.part, fb.cl, fb.cen);
+    k_filter<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, k, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
+    VM_STAGE_END(hk, kStExtract, s);
+    count_launch(4);
+    VM_STAGE_BEGIN(hk, kStHull, s);
+    static bool hull_attr = false;
+    if (!hull_attr) {
+        cudaFuncSetAttribute(k_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_hull_smem());
+        hull_attr = true;
+    }
+    k_hull<<<cgrid, kT, fit_hull_smem(), s>>>(off, fb.item_off, k, fb.part, fb.cen, fb.cl, fb.surv, fb.hull,
+                                             fb.hull_cnt, fb.err);
+    e = exclusive_scan_u32(fb.hull_cnt, fb.hull_cnt, fb.hull_cnt + k, k, fb.scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    VM_STAGE_END(hk, kStHull, s);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, uint32_t k,
+                        vm_plane* planes, int32_t* hull_xy, float* hull_xyz, cudaStream_t s) {
+    if (k == 0) return cudaSuccess;
+    k_pack<<<k < 4096 ? k : 4096, 128, 0, s>>>(off, labels, k, fb.cl, fb.hull, fb.hull_cnt, planes, hull_xy,
+                                              hull_xyz);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace vmx

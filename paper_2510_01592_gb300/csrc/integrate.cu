@@ -1,0 +1,161 @@
+// integrate.cu -- voxel information update (Sec. III.B, Eq. 1), one thread per
+// sensor point.
+//
+// Storage: a direct-indexed brick table (one int32 per 8^3-voxel brick of the
+// grid) maps a brick to a slot of a pool allocated on first touch.  A slot
+// holds, per voxel, the exact fixed-point coordinate sums S (int64, 2^-20 m
+// units relative to the map origin) and the point count C.  Eq. 1's running
+// mean is the ratio S / C, independent of the order the points arrive in, so
+// concurrent updates need only integer atomics.
+//
+// Two launches per frame, both reading the frame's points (the second read is
+// served from L2):
+//  1. k_claim: a point whose brick is unallocated claims it with a CAS on the
+//     table entry; the winner takes a pool slot.  No thread ever waits on
+//     another.
+//  2. k_accum: each warp reduces runs of consecutive points that fall in the
+//     same voxel (a segmented shuffle scan) and the last lane of each run
+//     issues one 64-bit atomic per axis plus one 32-bit count atomic.
+#include "vm_internal.cuh"
+
+namespace vmx {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Keyed {
+    int ok;
+    uint32_t brick;   // linear brick key
+    uint32_t local;   // voxel index inside the brick
+    int32_t F[3];     // rint(d * 2^20), d = offset from the map origin
+};
+
+// Transform, key and quantise one point.  The op sequence is the reading of
+// Sec. III.B: fma chain for R p + t, subtract the origin, floor(d * inv_res).
+__device__ __forceinline__ Keyed key_point(const float* __restrict__ xyz, uint32_t i, const Pose& P, const Grid& g) {
+    Keyed k;
+    const float x = xyz[3 * (size_t)i + 0], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
+    const float wx = __fmaf_rn(P.r[2], z, __fmaf_rn(P.r[1], y, __fmaf_rn(P.r[0], x, P.r[3])));
+    const float wy = __fmaf_rn(P.r[6], z, __fmaf_rn(P.r[5], y, __fmaf_rn(P.r[4], x, P.r[7])));
+    const float wz = __fmaf_rn(P.r[10], z, __fmaf_rn(P.r[9], y, __fmaf_rn(P.r[8], x, P.r[11])));
+    const float dx = __fsub_rn(wx, g.ox), dy = __fsub_rn(wy, g.oy), dz = __fsub_rn(wz, g.oz);
+    const float fx = floorf(__fmul_rn(dx, g.inv_res));
+    const float fy = floorf(__fmul_rn(dy, g.inv_res));
+    const float fz = floorf(__fmul_rn(dz, g.inv_res));
+    k.ok = (fx >= 0.0f) & (fx < (float)g.nx) & (fy >= 0.0f) & (fy < (float)g.ny) & (fz >= 0.0f) &
+           (fz < (float)g.nz);
+    if (k.ok) {
+        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+        k.brick = ((uint32_t)(iz >> 3) * (uint32_t)g.nby + (uint32_t)(iy >> 3)) * (uint32_t)g.nbx + (uint32_t)(ix >> 3);
+        k.local = (uint32_t)((((iz & 7) << 3) | (iy & 7)) << 3 | (ix & 7));
+        k.F[0] = (int32_t)__float2ll_rn(__fmul_rn(dx, 1048576.0f));
+        k.F[1] = (int32_t)__float2ll_rn(__fmul_rn(dy, 1048576.0f));
+        k.F[2] = (int32_t)__float2ll_rn(__fmul_rn(dz, 1048576.0f));
+    } else {
+        k.brick = kNone;
+        k.local = 0;
+        k.F[0] = k.F[1] = k.F[2] = 0;
+    }
+    return k;
+}
+
+__global__ void __launch_bounds__(kThreads) k_claim(const float* __restrict__ xyz, uint32_t n, Pose P, Grid g,
+                                                   int32_t* __restrict__ table, int32_t* __restrict__ slot_key,
+                                                   MapCounters* __restrict__ ctr, uint32_t capacity) {
+    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+        Keyed k = key_point(xyz, i, P, g);
+        if (!k.ok) continue;
+        if (table[k.brick] != -1) continue;  // allocated, being claimed, or refused
+        if (atomicCAS(&table[k.brick], -1, -2) != -1) continue;
+        const uint32_t slot = atomicAdd(&ctr->n_bricks, 1u);
+        if (slot < capacity) {
+            slot_key[slot] = (int32_t)k.brick;
+            table[k.brick] = (int32_t)slot;
+        } else {
+            table[k.brick] = -3;  // pool full: the brick's points are dropped and counted
+            atomicOr(&ctr->err, kErrCapacity);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_accum(const float* __restrict__ xyz, uint32_t n, Pose P, Grid g,
+                                                   const int32_t* __restrict__ table,
+                                                   unsigned long long* __restrict__ S, uint32_t* __restrict__ C,
+                                                   MapCounters* __restrict__ ctr) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp_global = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * kThreads) >> 5;
+    uint32_t n_ok = 0, n_bad = 0, n_full = 0;
+    for (uint32_t base = warp_global * 32u; base < n; base += n_warps * 32u) {
+        const uint32_t i = base + lane;
+        uint32_t key = kNone;
+        int32_t v0 = 0, v1 = 0, v2 = 0;
+        if (i < n) {
+            Keyed k = key_point(xyz, i, P, g);
+            if (k.ok) {
+                const int32_t slot = table[k.brick];
+                if (slot >= 0) {
+                    key = (uint32_t)slot * kBrickVox + k.local;
+                    v0 = k.F[0]; v1 = k.F[1]; v2 = k.F[2];
+                    ++n_ok;
+                } else {
+                    ++n_full;
+                }
+            } else {
+                ++n_bad;
+            }
+        }
+        // segmented inclusive scan over runs of equal keys in consecutive lanes
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool head = (lane == 0) || (key != prev);
+        const uint32_t heads = __ballot_sync(0xffffffffu, head);
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t0 = __shfl_up_sync(0xffffffffu, v0, o);
+            const int32_t t1 = __shfl_up_sync(0xffffffffu, v1, o);
+            const int32_t t2 = __shfl_up_sync(0xffffffffu, v2, o);
+            if (lane - o >= start) { v0 += t0; v1 += t1; v2 += t2; }
+        }
+        const bool tail = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+        if (tail && key != kNone) {
+            const uint32_t slot = key / kBrickVox, l = key % kBrickVox;
+            unsigned long long* s = S + (size_t)slot * 3 * kBrickVox + l;
+            atomicAdd(s, (unsigned long long)(uint32_t)v0);
+            atomicAdd(s + kBrickVox, (unsigned long long)(uint32_t)v1);
+            atomicAdd(s + 2 * kBrickVox, (unsigned long long)(uint32_t)v2);
+            atomicAdd(C + key, (uint32_t)(lane - start + 1));
+        }
+    }
+    // per-warp totals of accepted / dropped points
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_ok += __shfl_xor_sync(0xffffffffu, n_ok, o);
+        n_bad += __shfl_xor_sync(0xffffffffu, n_bad, o);
+        n_full += __shfl_xor_sync(0xffffffffu, n_full, o);
+    }
+    if (lane == 0) {
+        if (n_ok) atomicAdd(&ctr->integrated, (unsigned long long)n_ok);
+        if (n_bad) atomicAdd(&ctr->dropped, (unsigned long long)n_bad);
+        if (n_full) atomicAdd(&ctr->no_capacity, (unsigned long long)n_full);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, int32_t* brick_table,
+                             int32_t* slot_key, unsigned long long* S, uint32_t* C, MapCounters* ctr,
+                             uint32_t capacity, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t want = (n + kThreads - 1) / kThreads;
+    const uint32_t grid = want < (uint32_t)(sms * 8) ? want : (uint32_t)(sms * 8);
+    k_claim<<<grid, kThreads, 0, s>>>(xyz, n, pose, g, brick_table, slot_key, ctr, capacity);
+    k_accum<<<grid, kThreads, 0, s>>>(xyz, n, pose, g, brick_table, S, C, ctr);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+}  // namespace vmx

@@ -1,0 +1,227 @@
+// scan.cu -- device-wide exclusive prefix sum and a stable LSD radix sort of
+// (uint32 key, uint32 value) pairs.  These order the bricks and voxels by id,
+// number the kept clusters and lay the cluster members out contiguously in
+// voxel-id order (Sec. III.C: points sharing a label are grouped as clusters).
+#include "vm_internal.cuh"
+
+namespace vmx {
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 2048
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x == kScanThreads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_sums, uint32_t* block_total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) warp_sums[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = (lane < kScanThreads / 32) ? warp_sums[lane] : 0u;
+        uint32_t si = warp_incl_scan(s);
+        if (lane < kScanThreads / 32) warp_sums[lane] = si - s;
+        if (lane == kScanThreads / 32 - 1) *block_total = si;
+    }
+    __syncthreads();
+    return inc - v + warp_sums[w];
+}
+
+__global__ void k_tile_reduce(const uint32_t* __restrict__ in, size_t n, uint32_t* __restrict__ tile_sum) {
+    __shared__ uint32_t ws[kScanThreads / 32];
+    const size_t base = (size_t)blockIdx.x * kScanTile;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        size_t j = base + (size_t)i * kScanThreads + threadIdx.x;
+        if (j < n) s += in[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
+        tile_sum[blockIdx.x] = t;
+    }
+}
+
+// One block scans the tile sums in place (exclusive), carrying across chunks.
+__global__ void k_scan_sums(uint32_t* __restrict__ sums, size_t nt, uint32_t* __restrict__ total) {
+    __shared__ uint32_t ws[kScanThreads / 32];
+    __shared__ uint32_t chunk_total;
+    uint32_t carry = 0;
+    for (size_t base = 0; base < nt; base += kScanThreads) {
+        size_t j = base + threadIdx.x;
+        uint32_t v = (j < nt) ? sums[j] : 0u;
+        uint32_t ex = block_excl_scan(v, ws, &chunk_total);
+        if (j < nt) sums[j] = ex + carry;
+        __syncthreads();
+        carry += chunk_total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_tile_scan(const uint32_t* in, uint32_t* out, size_t n, const uint32_t* __restrict__ tile_off) {
+    __shared__ uint32_t buf[kScanTile];
+    __shared__ uint32_t ws[kScanThreads / 32];
+    __shared__ uint32_t tot;
+    const size_t base = (size_t)blockIdx.x * kScanTile;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int t = i * kScanThreads + threadIdx.x;
+        size_t j = base + t;
+        buf[t] = (j < n) ? in[j] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = buf[threadIdx.x * kScanItems + i];
+        s += v[i];
+    }
+    uint32_t ex = block_excl_scan(s, ws, &tot) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        buf[threadIdx.x * kScanItems + i] = ex;
+        ex += v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        int t = i * kScanThreads + threadIdx.x;
+        size_t j = base + t;
+        if (j < n) out[j] = buf[t];
+    }
+}
+
+// ------------------------------------------------------------------ radix sort
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortIters = 8;                               // 32-item rounds per warp
+constexpr int kSortTile = kSortThreads * kSortIters;        // 2048
+
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t n, int shift, uint32_t* __restrict__ ghist,
+                          size_t nt) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * kSortTile;
+    for (int i = 0; i < kSortIters; ++i) {
+        size_t j = base + (size_t)i * kSortThreads + threadIdx.x;
+        if (j < n) atomicAdd(&h[(keys[j] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    ghist[(size_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: warp w owns items [w*256, w*256+256) of the tile, in order.
+__global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t n, int shift,
+                             const uint32_t* __restrict__ goff, size_t nt) {
+    __shared__ uint32_t wc[kSortWarps][256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wc[0][0])[d] = 0;
+    __syncthreads();
+    const size_t base = (size_t)blockIdx.x * kSortTile + (size_t)w * (32 * kSortIters);
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t rank[kSortIters], dig[kSortIters];
+#pragma unroll
+    for (int i = 0; i < kSortIters; ++i) {
+        size_t j = base + (size_t)i * 32 + lane;
+        uint32_t d = (j < n) ? ((kin[j] >> shift) & 255u) : 256u;
+        dig[i] = d;
+        uint32_t m = __match_any_sync(0xffffffffu, d);
+        uint32_t r = __popc(m & lt);
+        uint32_t b = (d < 256u) ? wc[w][d] : 0u;
+        __syncwarp();
+        if (d < 256u && r == 0) wc[w][d] = b + __popc(m);
+        __syncwarp();
+        rank[i] = b + r;
+    }
+    __syncthreads();
+    {   // exclusive offsets of each warp per digit
+        const int d = threadIdx.x;  // kSortThreads == 256 digits
+        uint32_t run = 0;
+        for (int q = 0; q < kSortWarps; ++q) {
+            uint32_t t = wc[q][d];
+            wc[q][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortIters; ++i) {
+        size_t j = base + (size_t)i * 32 + lane;
+        if (j < n) {
+            uint32_t d = dig[i];
+            uint32_t pos = goff[(size_t)d * nt + blockIdx.x] + wc[w][d] + rank[i];
+            kout[pos] = kin[j];
+            vout[pos] = vin[j];
+        }
+    }
+}
+
+}  // namespace
+
+size_t scan_tmp_words(size_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total, size_t n, uint32_t* tmp,
+                               cudaStream_t s) {
+    if (n == 0) {
+        if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+        return cudaSuccess;
+    }
+    const size_t nt = (n + kScanTile - 1) / kScanTile;
+    k_tile_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tmp);
+    k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp, nt, total);
+    k_tile_scan<<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, n, tmp);
+    count_launch(3);
+    return cudaGetLastError();
+}
+
+size_t sort_tmp_words(size_t n) {
+    const size_t nt = (n + kSortTile - 1) / kSortTile;
+    return 256 * nt + scan_tmp_words(256 * nt) + 1;
+}
+
+cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
+                                  int bits, uint32_t* tmp, cudaStream_t s) {
+    if (n == 0 || bits <= 0) return cudaSuccess;
+    const size_t nt = (n + kSortTile - 1) / kSortTile;
+    uint32_t* ghist = tmp;
+    uint32_t* stmp = tmp + 256 * nt;
+    uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_rs_hist<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, n, shift, ghist, nt);
+        cudaError_t e = exclusive_scan_u32(ghist, ghist, nullptr, 256 * nt, stmp, s);
+        if (e != cudaSuccess) return e;
+        k_rs_scatter<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, ghist, nt);
+        count_launch(2);
+        uint32_t* t;
+        t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    if (ki != keys) {
+        cudaMemcpyAsync(keys, ki, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, vi, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace vmx

@@ -1,0 +1,500 @@
+// segment.cu -- multi-plane segmentation up to the cluster point lists
+// (Sec. III.C): mean positions from the exact sums, normals and steppable
+// classification (Eq. 3, Eq. 4), clustering (Algorithm 1) and cluster
+// formation.
+//
+// Layout.  After ordering the allocated bricks by brick key, every per-voxel
+// array is "rank-dense": voxel (brick rank r, local index l) lives at
+// r * 512 + l.  Because bricks are ranked by key and voxel ids are
+// brick-major (key * 512 + l), index order equals voxel-id order, so the
+// union-find root with the smallest index is the component's smallest voxel
+// id -- the fixed point of Algorithm 1's min-label propagation.
+//
+// Normals and clustering run one CTA per brick (512 threads, a thread per
+// voxel) with the brick and a one-voxel halo from its 26 neighbours staged in
+// shared memory.
+#include <climits>
+
+#include "vm_internal.cuh"
+
+namespace vmx {
+namespace {
+
+constexpr int kT = 256;
+constexpr float kInvQ = 9.5367431640625e-07f;  // 2^-20
+
+__device__ __forceinline__ void brick_coords(int32_t key, const Grid& g, int& bx, int& by, int& bz) {
+    bx = key % g.nbx;
+    by = (key / g.nbx) % g.nby;
+    bz = key / (g.nbx * g.nby);
+}
+
+__global__ void k_brick_flags(const int32_t* __restrict__ table, uint32_t nb, uint32_t* __restrict__ flags) {
+    for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < nb; i += gridDim.x * kT) flags[i] = table[i] >= 0;
+}
+
+__global__ void k_brick_compact(const int32_t* __restrict__ table, uint32_t nb, const uint32_t* __restrict__ flags,
+                                int32_t* __restrict__ rank_table, int32_t* __restrict__ sorted_slot,
+                                int32_t* __restrict__ sorted_key) {
+    for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < nb; i += gridDim.x * kT) {
+        const int32_t t = table[i];
+        if (t >= 0) {
+            const uint32_t r = flags[i];
+            sorted_slot[r] = t;
+            sorted_key[r] = (int32_t)i;
+            rank_table[i] = (int32_t)r;
+        } else {
+            rank_table[i] = -1;
+        }
+    }
+}
+
+// Mean of each voxel: M = floor((2 S + c) / (2 c)), the exact integer mean in
+// 2^-20 m units rounded half up (Eq. 1's mu up to that quantum).
+__global__ void __launch_bounds__(kT) k_finalize(uint32_t n_sorted, const int32_t* __restrict__ sorted_slot,
+                                                 const unsigned long long* __restrict__ S,
+                                                 const uint32_t* __restrict__ C, int32_t* __restrict__ M,
+                                                 uint8_t* __restrict__ status, size_t stride,
+                                                 SegCounters* __restrict__ ctr) {
+    uint32_t occ = 0;
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        const int32_t slot = sorted_slot[r];
+        for (int l = threadIdx.x; l < kBrickVox; l += kT) {
+            const uint32_t c = C[(size_t)slot * kBrickVox + l];
+            const size_t o = (size_t)r * kBrickVox + l;
+            if (c) {
+                const long long c2 = 2ll * (long long)c;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const long long s = (long long)S[((size_t)slot * 3 + a) * kBrickVox + l];
+                    M[a * stride + o] = (int32_t)((2ll * s + (long long)c) / c2);
+                }
+                status[o] = 1;
+                ++occ;
+            } else {
+                M[o] = INT_MIN;
+                M[stride + o] = INT_MIN;
+                M[2 * stride + o] = INT_MIN;
+                status[o] = 0;
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) occ += __shfl_xor_sync(0xffffffffu, occ, s);
+    if ((threadIdx.x & 31) == 0 && occ) atomicAdd(&ctr->n_occ, occ);
+}
+
+// ---------------------------------------------------------------- Jacobi (FP32)
+// Cyclic Jacobi (Golub & Van Loan Sec. 8.5) on a symmetric 3x3 matrix, pairs
+// (0,1), (0,2), (1,2), a fixed number of sweeps, pairs with a_pq == 0 skipped;
+// tau = (a_qq - a_pp) / (2 a_pq), t = sgn(tau) / (|tau| + sqrt(1 + tau^2)),
+// c = 1 / sqrt(1 + t^2), s = t c.  Every operation is an explicit IEEE
+// round-to-nearest intrinsic.
+__device__ __forceinline__ void jacobi3(float a00, float a11, float a22, float a01, float a02, float a12, int sweeps,
+                                        float v[3][3], float d[3]) {
+    float a[3][3] = {{a00, a01, a02}, {a01, a11, a12}, {a02, a12, a22}};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[r][c] = (r == c) ? 1.0f : 0.0f;
+    for (int sw = 0; sw < sweeps; ++sw) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int p = (k == 2) ? 1 : 0, q = (k == 0) ? 1 : 2, r = 2 - k;
+            const float apq = a[p][q];
+            if (apq == 0.0f) continue;
+            const float app = a[p][p], aqq = a[q][q];
+            const float tau = __fdiv_rn(__fsub_rn(aqq, app), __fmul_rn(2.0f, apq));
+            const float sg = (tau >= 0.0f) ? 1.0f : -1.0f;
+            const float t = __fdiv_rn(sg, __fadd_rn(fabsf(tau), __fsqrt_rn(__fmaf_rn(tau, tau, 1.0f))));
+            const float c = __fdiv_rn(1.0f, __fsqrt_rn(__fmaf_rn(t, t, 1.0f)));
+            const float s = __fmul_rn(t, c);
+            a[p][p] = __fmaf_rn(-t, apq, app);
+            a[q][q] = __fmaf_rn(t, apq, aqq);
+            a[p][q] = 0.0f;
+            a[q][p] = 0.0f;
+            const float arp = a[r][p], arq = a[r][q];
+            const float nrp = __fmaf_rn(c, arp, -__fmul_rn(s, arq));
+            const float nrq = __fmaf_rn(s, arp, __fmul_rn(c, arq));
+            a[r][p] = nrp; a[p][r] = nrp;
+            a[r][q] = nrq; a[q][r] = nrq;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float vip = v[i][p], viq = v[i][q];
+                v[i][p] = __fmaf_rn(c, vip, -__fmul_rn(s, viq));
+                v[i][q] = __fmaf_rn(s, vip, __fmul_rn(c, viq));
+            }
+        }
+    }
+    d[0] = a[0][0]; d[1] = a[1][1]; d[2] = a[2][2];
+}
+
+// Column of the smallest diagonal entry (lowest index on ties), scaled by
+// 1/sqrt(n.n), oriented n_z >= 0 (then n_y, then n_x when zero).
+__device__ __forceinline__ void pick_normal(float v[3][3], const float d[3], float n[3]) {
+    int m = 0;
+    if (d[1] < d[m]) m = 1;
+    if (d[2] < d[m]) m = 2;
+    float x = (m == 0) ? v[0][0] : (m == 1) ? v[0][1] : v[0][2];
+    float y = (m == 0) ? v[1][0] : (m == 1) ? v[1][1] : v[1][2];
+    float z = (m == 0) ? v[2][0] : (m == 1) ? v[2][1] : v[2][2];
+    const float nn = __fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x)));
+    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(nn));
+    x = __fmul_rn(x, inv); y = __fmul_rn(y, inv); z = __fmul_rn(z, inv);
+    const bool flip = (z < 0.0f) || (z == 0.0f && (y < 0.0f || (y == 0.0f && x < 0.0f)));
+    if (flip) { x = -x; y = -y; z = -z; }
+    n[0] = x; n[1] = y; n[2] = z;
+}
+
+// Rank of each of the 27 bricks around brick r (-1: none).
+__device__ __forceinline__ void load_neighbour_ranks(int32_t key, const Grid& g, const int32_t* __restrict__ rank_table,
+                                                     int32_t* nb) {
+    if (threadIdx.x < 27) {
+        int bx, by, bz;
+        brick_coords(key, g, bx, by, bz);
+        const int dz = (int)threadIdx.x / 9 - 1, dy = ((int)threadIdx.x / 3) % 3 - 1, dx = (int)threadIdx.x % 3 - 1;
+        const int x = bx + dx, y = by + dy, z = bz + dz;
+        nb[threadIdx.x] = (x >= 0 && y >= 0 && z >= 0 && x < g.nbx && y < g.nby && z < g.nbz)
+                              ? rank_table[(z * g.nby + y) * g.nbx + x] : -1;
+    }
+}
+
+// Rank-dense index of halo cell c of a 10^3 halo, or -1.
+__device__ __forceinline__ int32_t halo_index(int c, const int32_t* nb) {
+    const int hx = c % 10, hy = (c / 10) % 10, hz = c / 100;
+    const int gx = hx - 1, gy = hy - 1, gz = hz - 1;
+    const int bdx = gx < 0 ? -1 : (gx > 7 ? 1 : 0);
+    const int bdy = gy < 0 ? -1 : (gy > 7 ? 1 : 0);
+    const int bdz = gz < 0 ? -1 : (gz > 7 ? 1 : 0);
+    const int32_t rk = nb[(bdz + 1) * 9 + (bdy + 1) * 3 + (bdx + 1)];
+    if (rk < 0) return -1;
+    const int lx = gx - 8 * bdx, ly = gy - 8 * bdy, lz = gz - 8 * bdz;
+    return rk * kBrickVox + ((lz * 8 + ly) * 8 + lx);
+}
+
+// Eq. 3 / Eq. 4: covariance of the 3x3x3 window of mean positions (self
+// included) as an exact integer matrix N' sum(dd^T) - (sum d)(sum d)^T of
+// offsets d = M_j - M_i, rounded to FP32; normal by Jacobi (6 sweeps);
+// steppable iff N >= n_th and |n_z| >= cos_step.
+__global__ void __launch_bounds__(512) k_normals(uint32_t n_sorted, Grid g, const int32_t* __restrict__ sorted_key,
+                                                 const int32_t* __restrict__ rank_table,
+                                                 const int32_t* __restrict__ M, float* __restrict__ nrm,
+                                                 uint8_t* __restrict__ status, uint8_t* __restrict__ nbr,
+                                                 size_t stride, uint32_t n_th, float cos_step) {
+    __shared__ int32_t sM[3][1000];
+    __shared__ int32_t nb[27];
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        __syncthreads();
+        load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
+        __syncthreads();
+        for (int c = threadIdx.x; c < 1000; c += 512) {
+            const int32_t idx = halo_index(c, nb);
+            if (idx >= 0) {
+                sM[0][c] = M[idx];
+                sM[1][c] = M[stride + idx];
+                sM[2][c] = M[2 * stride + idx];
+            } else {
+                sM[0][c] = INT_MIN;
+            }
+        }
+        __syncthreads();
+        const int l = threadIdx.x;
+        const int c0 = (((l >> 6) + 1) * 10 + ((l >> 3) & 7) + 1) * 10 + (l & 7) + 1;
+        const int32_t m0 = sM[0][c0], m1 = sM[1][c0], m2 = sM[2][c0];
+        if (m0 == INT_MIN) continue;
+        int32_t s1x = 0, s1y = 0, s1z = 0;
+        long long sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+        int cnt = 0;
+#pragma unroll
+        for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int c = c0 + dz * 100 + dy * 10 + dx;
+                    const int32_t a0 = sM[0][c];
+                    if (a0 == INT_MIN) continue;
+                    const int32_t ex = a0 - m0, ey = sM[1][c] - m1, ez = sM[2][c] - m2;
+                    s1x += ex; s1y += ey; s1z += ez;
+                    sxx += (long long)ex * ex; syy += (long long)ey * ey; szz += (long long)ez * ez;
+                    sxy += (long long)ex * ey; sxz += (long long)ex * ez; syz += (long long)ey * ez;
+                    ++cnt;
+                }
+        const long long N = cnt;
+        const float A00 = __ll2float_rn(N * sxx - (long long)s1x * s1x);
+        const float A11 = __ll2float_rn(N * syy - (long long)s1y * s1y);
+        const float A22 = __ll2float_rn(N * szz - (long long)s1z * s1z);
+        const float A01 = __ll2float_rn(N * sxy - (long long)s1x * s1y);
+        const float A02 = __ll2float_rn(N * sxz - (long long)s1x * s1z);
+        const float A12 = __ll2float_rn(N * syz - (long long)s1y * s1z);
+        float v[3][3], d[3], n[3];
+        jacobi3(A00, A11, A22, A01, A02, A12, 6, v, d);
+        pick_normal(v, d, n);
+        const size_t o = (size_t)r * kBrickVox + l;
+        nrm[o] = n[0];
+        nrm[stride + o] = n[1];
+        nrm[2 * stride + o] = n[2];
+        const uint32_t N_nb = (uint32_t)(cnt - 1);
+        nbr[o] = (uint8_t)N_nb;
+        status[o] = (N_nb >= n_th && fabsf(n[2]) >= cos_step) ? 2 : 1;
+    }
+}
+
+// ---------------------------------------------------------------- union-find
+__device__ __forceinline__ uint32_t uf_find(uint32_t* P, uint32_t x, uint32_t* err) {
+    for (int it = 0; it < kLoopCap; ++it) {
+        const uint32_t p = __ldcg(P + x);
+        if (p == x) return x;
+        const uint32_t gp = __ldcg(P + p);
+        if (gp != p) P[x] = gp;  // path halving: gp is an ancestor of x
+        x = gp;
+    }
+    atomicOr(err, kErrTimeout);
+    return x;
+}
+
+// Hook the larger root under the smaller, so every root is the smallest index
+// of its tree.
+__device__ __forceinline__ void uf_union(uint32_t* P, uint32_t a, uint32_t b, uint32_t* err) {
+    for (int it = 0; it < kLoopCap; ++it) {
+        a = uf_find(P, a, err);
+        b = uf_find(P, b, err);
+        if (a == b) return;
+        const uint32_t hi = a > b ? a : b, lo = a > b ? b : a;
+        const uint32_t old = atomicCAS(P + hi, hi, lo);
+        if (old == hi) return;
+        a = old;  // hi was hooked meanwhile: continue from its new parent
+        b = lo;
+    }
+    atomicOr(err, kErrTimeout);
+}
+
+__global__ void k_ccl_init(size_t nv, const uint8_t* __restrict__ status, uint32_t* __restrict__ parent,
+                           uint32_t* __restrict__ count, uint8_t want) {
+    for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
+        parent[i] = (status[i] >= want) ? (uint32_t)i : kNone;
+        count[i] = 0;
+    }
+}
+
+// Algorithm 1's adjacency: two vertices that are 26-neighbours are joined
+// iff |mu_i - mu_j|^2 < d_th^2 and |n_i . n_j| > cos_ccl.  Each vertex tests
+// its 13 forward neighbours; the test is symmetric.
+__global__ void __launch_bounds__(512) k_ccl_link(uint32_t n_sorted, Grid g, const int32_t* __restrict__ sorted_key,
+                                                  const int32_t* __restrict__ rank_table,
+                                                  const int32_t* __restrict__ M, const float* __restrict__ nrm,
+                                                  const uint8_t* __restrict__ status, uint32_t* parent, size_t stride,
+                                                  uint8_t want, float d_th2, float cos_ccl, uint32_t* err) {
+    __shared__ float sMu[3][1000];
+    __shared__ float sN[3][1000];
+    __shared__ int32_t sIdx[1000];
+    __shared__ int32_t nb[27];
+    __shared__ int any_vertex;
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) any_vertex = 0;
+        load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
+        __syncthreads();
+        // warp vote: skip bricks without a vertex
+        {
+            const size_t o = (size_t)r * kBrickVox + threadIdx.x;
+            const bool v = status[o] >= want;
+            if (__any_sync(0xffffffffu, v) && (threadIdx.x & 31) == 0) any_vertex = 1;
+        }
+        __syncthreads();
+        if (!any_vertex) continue;
+        for (int c = threadIdx.x; c < 1000; c += 512) {
+            int32_t idx = halo_index(c, nb);
+            if (idx >= 0 && status[idx] >= want) {
+                sMu[0][c] = __fadd_rn(g.ox, __fmul_rn(__int2float_rn(M[idx]), kInvQ));
+                sMu[1][c] = __fadd_rn(g.oy, __fmul_rn(__int2float_rn(M[stride + idx]), kInvQ));
+                sMu[2][c] = __fadd_rn(g.oz, __fmul_rn(__int2float_rn(M[2 * stride + idx]), kInvQ));
+                sN[0][c] = nrm[idx];
+                sN[1][c] = nrm[stride + idx];
+                sN[2][c] = nrm[2 * stride + idx];
+            } else {
+                idx = -1;
+            }
+            sIdx[c] = idx;
+        }
+        __syncthreads();
+        const int l = threadIdx.x;
+        const int c0 = (((l >> 6) + 1) * 10 + ((l >> 3) & 7) + 1) * 10 + (l & 7) + 1;
+        const int32_t me = sIdx[c0];
+        if (me < 0) continue;
+        const float mx = sMu[0][c0], my = sMu[1][c0], mz = sMu[2][c0];
+        const float nx = sN[0][c0], ny = sN[1][c0], nz = sN[2][c0];
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            // forward offsets: (dz, dy, dx) lexicographically after (0, 0, 0)
+            const int dz = (k < 9) ? 1 : 0;
+            const int dy = (k < 9) ? (k / 3 - 1) : ((k < 12) ? 1 : 0);
+            const int dx = (k < 9) ? (k % 3 - 1) : ((k < 12) ? (k - 9 - 1) : 1);
+            const int c = c0 + dz * 100 + dy * 10 + dx;
+            const int32_t j = sIdx[c];
+            if (j < 0) continue;
+            const float ex = __fsub_rn(mx, sMu[0][c]), ey = __fsub_rn(my, sMu[1][c]), ez = __fsub_rn(mz, sMu[2][c]);
+            const float d2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
+            const float cs = __fmaf_rn(nz, sN[2][c], __fmaf_rn(ny, sN[1][c], __fmul_rn(nx, sN[0][c])));
+            if (d2 < d_th2 && fabsf(cs) > cos_ccl) uf_union(parent, (uint32_t)me, (uint32_t)j, err);
+        }
+    }
+}
+
+// Read-only walk to the root.  Used once linking is over: every thread writes
+// only its own entry, so a finished entry is never overwritten by another
+// thread's path shortcut (which could leave it on an intermediate node).
+__device__ __forceinline__ uint32_t uf_root(const uint32_t* P, uint32_t x, uint32_t* err) {
+    for (int it = 0; it < kLoopCap; ++it) {
+        const uint32_t p = __ldcg(P + x);
+        if (p == x) return x;
+        x = p;
+    }
+    atomicOr(err, kErrTimeout);
+    return x;
+}
+
+// Pointer jumping to the root: afterwards parent[i] is the component's
+// smallest index (its label) for every vertex.
+__global__ void k_ccl_compress(size_t nv, uint32_t* parent, uint32_t* err) {
+    for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
+        if (parent[i] != kNone) parent[i] = uf_root(parent, (uint32_t)i, err);
+    }
+}
+
+// Component sizes: warps aggregate equal roots before the atomic.
+__global__ void k_count(size_t nv, const uint32_t* __restrict__ parent, uint32_t* __restrict__ count,
+                        SegCounters* __restrict__ ctr) {
+    uint32_t nvert = 0;
+    for (size_t base = ((size_t)blockIdx.x * kT + threadIdx.x) & ~(size_t)31; base < nv;
+         base += (size_t)gridDim.x * kT) {
+        const size_t i = base + (threadIdx.x & 31);
+        const uint32_t root = (i < nv) ? parent[i] : kNone;
+        const uint32_t m = __match_any_sync(0xffffffffu, root);
+        if (root != kNone) {
+            ++nvert;
+            if ((threadIdx.x & 31) == (uint32_t)(__ffs(m) - 1)) atomicAdd(&count[root], (uint32_t)__popc(m));
+        }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) nvert += __shfl_xor_sync(0xffffffffu, nvert, s);
+    if ((threadIdx.x & 31) == 0 && nvert) atomicAdd(&ctr->n_vert, nvert);
+}
+
+__global__ void k_keep_flags(size_t nv, const uint32_t* __restrict__ parent, const uint32_t* __restrict__ count,
+                             uint32_t min_cluster, uint32_t* __restrict__ root_flag, uint32_t* __restrict__ vert_flag) {
+    for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
+        const uint32_t p = parent[i];
+        const bool kept = (p != kNone) && count[p] >= min_cluster;
+        vert_flag[i] = kept;
+        root_flag[i] = kept && p == (uint32_t)i;
+    }
+}
+
+__device__ __forceinline__ uint32_t vid_of(size_t idx, const int32_t* __restrict__ sorted_key) {
+    return (uint32_t)sorted_key[idx / kBrickVox] * kBrickVox + (uint32_t)(idx % kBrickVox);
+}
+
+__global__ void k_compact(size_t nv, const uint32_t* __restrict__ parent, const uint32_t* __restrict__ count,
+                          uint32_t min_cluster, const uint32_t* __restrict__ cid, const uint32_t* __restrict__ vpos,
+                          const int32_t* __restrict__ sorted_key, uint32_t* __restrict__ keys,
+                          uint32_t* __restrict__ vals, uint32_t* __restrict__ cl_size,
+                          uint32_t* __restrict__ cl_label) {
+    for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
+        const uint32_t p = parent[i];
+        if (p == kNone || count[p] < min_cluster) continue;
+        const uint32_t c = cid[p];
+        keys[vpos[i]] = c;
+        vals[vpos[i]] = (uint32_t)i;
+        if (p == (uint32_t)i) {
+            cl_size[c] = count[i];
+            cl_label[c] = vid_of(i, sorted_key);
+        }
+    }
+}
+
+// Cluster points in cluster order: mean positions and voxel ids.
+__global__ void k_gather(uint32_t n, const uint32_t* __restrict__ vals, const int32_t* __restrict__ M, size_t stride,
+                         const int32_t* __restrict__ sorted_key, Grid g, float* __restrict__ pts,
+                         uint32_t* __restrict__ pt_vid) {
+    for (uint32_t p = blockIdx.x * kT + threadIdx.x; p < n; p += gridDim.x * kT) {
+        const uint32_t i = vals[p];
+        pts[3 * (size_t)p + 0] = __fadd_rn(g.ox, __fmul_rn(__int2float_rn(M[i]), kInvQ));
+        pts[3 * (size_t)p + 1] = __fadd_rn(g.oy, __fmul_rn(__int2float_rn(M[stride + i]), kInvQ));
+        pts[3 * (size_t)p + 2] = __fadd_rn(g.oz, __fmul_rn(__int2float_rn(M[2 * stride + i]), kInvQ));
+        pt_vid[p] = vid_of(i, sorted_key);
+    }
+}
+
+inline unsigned grid_for(size_t n, int sms, int per_sm = 8) {
+    size_t want = (n + kT - 1) / kT;
+    size_t cap = (size_t)sms * per_sm;
+    if (want < 1) want = 1;
+    return (unsigned)(want < cap ? want : cap);
+}
+
+}  // namespace
+
+cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.ctr, 0, sizeof(SegCounters), s);
+    if (e != cudaSuccess) return e;
+    k_brick_flags<<<grid_for(nb_total, sms), kT, 0, s>>>(brick_table, nb_total, b.flags);
+    e = exclusive_scan_u32(b.flags, b.flags, &b.ctr->n_sorted, nb_total, b.scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    k_brick_compact<<<grid_for(nb_total, sms), kT, 0, s>>>(brick_table, nb_total, b.flags, b.rank_table,
+                                                             b.sorted_slot, b.sorted_key);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_voxels(const Grid& g, uint32_t n_sorted, const unsigned long long* S, const uint32_t* C,
+                       const vm_segment_params& p, SegBuffers& b, uint32_t* err, int sms, cudaStream_t s,
+                       StageHook* hk) {
+    if (n_sorted == 0) return cudaSuccess;
+    const size_t nv = (size_t)n_sorted * kBrickVox;
+    const size_t stride = b.nv;
+    const unsigned bricks_grid = (unsigned)(n_sorted < (uint32_t)sms * 4 ? n_sorted : (uint32_t)sms * 4);
+    VM_STAGE_BEGIN(hk, kStFinalize, s);
+    k_finalize<<<bricks_grid, kT, 0, s>>>(n_sorted, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
+    VM_STAGE_END(hk, kStFinalize, s);
+    VM_STAGE_BEGIN(hk, kStNormals, s);
+    k_normals<<<bricks_grid, 512, 0, s>>>(n_sorted, g, b.sorted_key, b.rank_table, b.M, b.nrm, b.status, b.nbr,
+                                          stride, p.n_th, p.cos_step);
+    VM_STAGE_END(hk, kStNormals, s);
+    const uint8_t want = p.classify ? 2 : 1;
+    VM_STAGE_BEGIN(hk, kStCcl, s);
+    k_ccl_init<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.status, b.parent, b.count, want);
+    k_ccl_link<<<bricks_grid, 512, 0, s>>>(n_sorted, g, b.sorted_key, b.rank_table, b.M, b.nrm, b.status, b.parent,
+                                           stride, want, p.d_th2, p.cos_ccl, err);
+    k_ccl_compress<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, err);
+    VM_STAGE_END(hk, kStCcl, s);
+    count_launch(5);
+    VM_STAGE_BEGIN(hk, kStClusters, s);
+    k_count<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, b.count, b.ctr);
+    const uint32_t min_cl = p.min_cluster ? p.min_cluster : 1u;
+    k_keep_flags<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, b.count, min_cl, b.cid, b.vert_flag);
+    cudaError_t e = exclusive_scan_u32(b.cid, b.cid, &b.ctr->k, nv, b.scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan_u32(b.vert_flag, b.vert_flag, &b.ctr->n_kept, nv, b.scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    k_compact<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, b.count, min_cl, b.cid, b.vert_flag, b.sorted_key,
+                                               b.keys, b.vals, b.cl_size, b.cl_label);
+    VM_STAGE_END(hk, kStClusters, s);
+    count_launch(3);
+    return cudaGetLastError();
+}
+
+cudaError_t seg_clusters(const Grid& g, uint32_t k, uint32_t n_kept, SegBuffers& b, int sms, cudaStream_t s) {
+    if (k == 0) return cudaSuccess;
+    int bits = 1;
+    while ((1u << bits) < k && bits < 32) ++bits;
+    cudaError_t e = stable_sort_pairs_u32(b.keys, b.vals, b.keys_alt, b.vals_alt, n_kept, bits, b.scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan_u32(b.cl_size, b.cl_off, b.cl_off + k, k, b.scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    k_gather<<<grid_for(n_kept, sms), kT, 0, s>>>(n_kept, b.vals, b.M, b.nv, b.sorted_key, g, b.pts, b.pt_vid);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace vmx

@@ -1,0 +1,241 @@
+// vm_internal.cuh -- internal declarations shared by the CUDA translation units
+// of libvoxmps.so (not installed, not part of the C ABI).
+//
+// Numerics: every floating-point operation whose result decides an integer
+// (a voxel index, a classification, an edge, an inlier) is written with an
+// explicit IEEE round-to-nearest intrinsic (__fmaf_rn, __fmul_rn, __fadd_rn,
+// __fsub_rn, __fdiv_rn, __fsqrt_rn) so the op sequence is fixed regardless of
+// compiler contraction; the library is also built with --fmad=false.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/vm.h"
+
+namespace vmx {
+
+constexpr int kBrick = 8;
+constexpr int kBrickVox = 512;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// Device error word bits.
+constexpr uint32_t kErrCapacity = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr uint32_t kErrOverflow = 4u;
+
+// Iteration cap of every device retry loop (union-find, work queues).
+constexpr int kLoopCap = 1 << 22;
+
+struct Pose {
+    float r[12];
+};
+
+// Grid geometry passed to kernels by value.
+struct Grid {
+    int nx, ny, nz;
+    int nbx, nby, nbz;
+    float ox, oy, oz;
+    float inv_res;
+};
+
+// Counters kept in device memory per map.
+struct MapCounters {
+    unsigned long long integrated;
+    unsigned long long dropped;
+    unsigned long long no_capacity;
+    uint32_t n_bricks;   // bricks allocated (may exceed capacity on overflow)
+    uint32_t err;        // error bits
+};
+
+// Counters produced by one segmentation, read back by the host.
+struct SegCounters {
+    uint32_t n_sorted;   // bricks in key order
+    uint32_t n_occ;      // occupied voxels
+    uint32_t n_vert;     // clustered vertices (steppable or all occupied)
+    uint32_t n_kept;     // clustered vertices in kept clusters
+    uint32_t k;          // kept clusters
+    uint32_t n_hull;     // hull vertices
+    uint32_t err;        // error bits
+    uint32_t pad;
+};
+
+// Per-cluster fit state on the device.
+struct FitCluster {
+    float n[3];          // selected RANSAC plane
+    float d;
+    float u[3], v[3];    // in-plane basis
+    float o[3];          // hull origin = first point of the cluster
+    float c[3];          // inlier centroid
+    int32_t best_h;
+    uint32_t inliers;
+    uint32_t n_surv;     // hull candidates after the octagon filter
+    uint32_t hull_n;
+    uint32_t hull_off;
+    uint32_t flags;
+    float refit_n[3];
+    float refit_d;
+    unsigned long long ext[8];  // octagon extremes: (biased value << 32) | point index
+};
+
+// ---------------------------------------------------------------- diagnostics
+// Pipeline stages timed by the optional stage timer.
+enum Stage {
+    kStIntegrate = 0,  // claim + accumulate
+    kStOrder,          // bricks in key order
+    kStFinalize,       // integer means
+    kStNormals,        // Eq. 3 / Eq. 4
+    kStCcl,            // Algorithm 1 (init, link, compress)
+    kStClusters,       // sizes, numbering, compaction, sort, gather
+    kStHyp,            // stage a
+    kStScore,          // stage b
+    kStExtract,        // stage c, inliers, centroid, filter
+    kStHull,           // refit + hull
+    kStPack,           // output records
+    kNumStages
+};
+
+// Records device time of stages on a stream (events); null = disabled.
+struct StageHook {
+    virtual void begin(int stage, cudaStream_t s) = 0;
+    virtual void end(int stage, cudaStream_t s) = 0;
+    virtual ~StageHook() {}
+};
+#define VM_STAGE_BEGIN(hk, st, s) \
+    do {                          \
+        if (hk) (hk)->begin((st), (s)); \
+    } while (0)
+#define VM_STAGE_END(hk, st, s) \
+    do {                        \
+        if (hk) (hk)->end((st), (s)); \
+    } while (0)
+
+// Kernel launches issued by the library in this process.
+void count_launch(int n = 1);
+
+// ---------------------------------------------------------------- scratch
+// A device buffer that grows on demand (never shrinks).
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Host-side helpers (api.cu).
+void set_error(const std::string& msg);
+vm_status cuda_status(cudaError_t e, const char* what);
+vm_status ensure(DevBuf& b, size_t bytes);
+#define VM_CUDA(call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return ::vmx::cuda_status(_e, #call);    \
+    } while (0)
+#define VM_TRY(expr)                                \
+    do {                                            \
+        vm_status _s = (expr);                      \
+        if (_s != VM_OK) return _s;                 \
+    } while (0)
+
+// ---------------------------------------------------------------- scan.cu
+// Exclusive prefix sum of n uint32 values: out[i] = sum(in[0..i-1]); *total
+// (device) receives the sum.  in and out may alias.  tmp must hold
+// scan_tmp_words(n) words.
+size_t scan_tmp_words(size_t n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total, size_t n, uint32_t* tmp,
+                               cudaStream_t s);
+// Stable sort of (key, value) pairs by key, key < 2^bits (bits <= 32), LSD
+// 8-bit digits.  keys/vals are sorted in place using the alt buffers.
+size_t sort_tmp_words(size_t n);
+cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
+                                  int bits, uint32_t* tmp, cudaStream_t s);
+
+// ---------------------------------------------------------------- integrate.cu
+cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, int32_t* brick_table,
+                             int32_t* slot_key, unsigned long long* S, uint32_t* C, MapCounters* ctr,
+                             uint32_t capacity, cudaStream_t s);
+
+// ---------------------------------------------------------------- segment.cu
+struct SegBuffers {
+    // brick order
+    uint32_t* flags;        // [nb_total + 1] scan scratch
+    int32_t* rank_table;    // [nb_total]   brick key -> rank or -1
+    int32_t* sorted_slot;   // [cap]        rank -> pool slot
+    int32_t* sorted_key;    // [cap]        rank -> brick key
+    // rank-dense voxel arrays, index = rank * 512 + local
+    int32_t* M;             // [3][nv]  exact integer means (2^-20 m), INT32_MIN when empty
+    float* nrm;             // [3][nv]
+    uint8_t* status;        // [nv]     0 free, 1 occupied, 2 steppable
+    uint8_t* nbr;           // [nv]     occupied neighbours N
+    uint32_t* parent;       // [nv]     union-find parent, kNone when not a vertex
+    uint32_t* count;        // [nv]     component sizes at roots
+    uint32_t* cid;          // [nv + 1] kept-root flags -> cluster index (scan)
+    uint32_t* vert_flag;    // [nv + 1] kept-vertex flags -> compact position (scan)
+    // compact kept vertices
+    uint32_t* keys;         // [nv] cluster index
+    uint32_t* vals;         // [nv] rank-dense voxel index
+    uint32_t* keys_alt;
+    uint32_t* vals_alt;
+    // clusters
+    uint32_t* cl_size;      // [kcap + 1]
+    uint32_t* cl_off;       // [kcap + 1]
+    uint32_t* cl_label;     // [kcap]
+    float* pts;             // [nv][3]  cluster points in cluster order
+    uint32_t* pt_vid;       // [nv]
+    uint32_t* scan_tmp;
+    SegCounters* ctr;       // device
+    size_t nv, kcap;
+};
+
+// Orders the allocated bricks by key (rank table, sorted slots/keys); the
+// brick count lands in b.ctr->n_sorted.
+cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s);
+// Means, normals, classification, union-find clustering, cluster numbering and
+// compaction of kept vertices for n_sorted bricks.
+cudaError_t seg_voxels(const Grid& g, uint32_t n_sorted, const unsigned long long* S, const uint32_t* C,
+                       const vm_segment_params& p, SegBuffers& b, uint32_t* err, int sms, cudaStream_t s,
+                       StageHook* hk);
+// Stable sort of kept vertices by cluster, cluster offsets, point gather.
+cudaError_t seg_clusters(const Grid& g, uint32_t k, uint32_t n_kept, SegBuffers& b, int sms, cudaStream_t s);
+
+// ---------------------------------------------------------------- fit.cu
+struct FitBuffers {
+    float4* hyp;            // [kcap * H]
+    uint8_t* hyp_valid;     // [kcap * H]
+    uint32_t* counts;       // [kcap * H]
+    FitCluster* cl;         // [kcap]
+    uint32_t* item_off;     // [kcap + 1] work-item offsets (scan)
+    uint32_t* queue;        // [4] work-queue heads
+    uint8_t* inlier;        // [npts]
+    float* part;            // [items][10] per-item partial sums
+    double* cen;            // [kcap][3] inlier centroids
+    int2* surv;             // [npts] hull candidates (per-cluster segments at cluster offsets)
+    int2* hull;             // [npts] hull vertices (per-cluster segments at cluster offsets)
+    uint32_t* hull_cnt;     // [kcap + 1] -> hull offsets (scan)
+    uint32_t* scan_tmp;
+    uint32_t* err;          // device error word
+    size_t kcap, npts_cap, items_cap;
+    int H;
+};
+
+struct FitTuning {
+    int tile;               // points per scoring work item
+    int hyp_per_thread;     // hypotheses held in registers per thread
+    int ctas_per_sm;        // persistent CTAs per SM
+};
+FitTuning default_tuning();
+size_t fit_hull_smem();
+
+// Runs RANSAC, selection, extraction, refit and hull for k clusters whose
+// points are pts[off[c]..off[c+1]) (device), labels (device, or nullptr for
+// label = c).  k and npts are host values.  Produces per-cluster records in
+// fb.cl and hull vertices in fb.hull / fb.hull_cnt (offsets after the scan).
+cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, uint32_t k, uint32_t npts,
+                       const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int num_sms, cudaStream_t s,
+                       StageHook* hk);
+
+// Packs vm_plane records, hull_xy and hull_xyz into device staging buffers.
+cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, uint32_t k,
+                        vm_plane* planes, int32_t* hull_xy, float* hull_xyz, cudaStream_t s);
+
+}  // namespace vmx

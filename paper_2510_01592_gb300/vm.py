@@ -1,0 +1,299 @@
+"""ctypes binding of libvoxmps.so (include/vm.h).
+
+Argument marshalling only: every step of integration and segmentation runs in
+the library's CUDA kernels.  There is no CPU fallback -- if the library is not
+built or cannot load, every call raises.
+
+The low-level functions carry the C names (``vm_create``, ``vm_integrate``,
+``vm_segment``, ``vm_fit_planes`` ...).  ``VoxelMap`` wraps a map handle;
+torch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+VM_MAP_STAGE_TIMING = 1
+N_STAGES = 16  # upper bound of the library's stage count
+
+VM_OK, VM_ERR_INVALID_ARG, VM_ERR_OUT_OF_MEMORY, VM_ERR_CAPACITY, VM_ERR_CUDA, VM_ERR_TIMEOUT, VM_ERR_EXTENT = range(7)
+STATUS_NAMES = {0: "VM_OK", 1: "VM_ERR_INVALID_ARG", 2: "VM_ERR_OUT_OF_MEMORY", 3: "VM_ERR_CAPACITY",
+                4: "VM_ERR_CUDA", 5: "VM_ERR_TIMEOUT", 6: "VM_ERR_EXTENT"}
+
+
+class VmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vm_map_params(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("dims", C.c_int32 * 3), ("voxel_size", C.c_float),
+                ("brick_capacity", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class vm_segment_params(C.Structure):
+    _fields_ = [("n_th", C.c_uint32), ("cos_step", C.c_float), ("d_th2", C.c_float), ("cos_ccl", C.c_float),
+                ("min_cluster", C.c_uint32), ("n_hyp", C.c_uint32), ("eps", C.c_float), ("seed", C.c_uint64),
+                ("classify", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class vm_plane(C.Structure):
+    _fields_ = [("normal", C.c_float * 3), ("offset", C.c_float), ("inlier_count", C.c_uint32),
+                ("label", C.c_uint32), ("ransac_normal", C.c_float * 3), ("ransac_offset", C.c_float),
+                ("basis_u", C.c_float * 3), ("basis_v", C.c_float * 3), ("hull_origin", C.c_float * 3),
+                ("hull_offset", C.c_uint32), ("hull_count", C.c_uint32), ("n_points", C.c_uint32),
+                ("best_h", C.c_int32), ("flags", C.c_uint32)]
+
+
+class vm_planes(C.Structure):
+    _fields_ = [("planes", C.POINTER(vm_plane)), ("n_planes", C.c_uint32), ("hull_xy", C.POINTER(C.c_int32)),
+                ("hull_xyz", C.POINTER(C.c_float)), ("n_hull", C.c_uint32)]
+
+
+class vm_stats(C.Structure):
+    _fields_ = [("points_integrated", C.c_uint64), ("points_dropped", C.c_uint64),
+                ("points_no_capacity", C.c_uint64), ("bricks_allocated", C.c_uint32),
+                ("brick_capacity", C.c_uint32), ("occupied_voxels", C.c_uint32), ("steppable_voxels", C.c_uint32),
+                ("clusters", C.c_uint32), ("reserved", C.c_uint32), ("device_bytes", C.c_uint64)]
+
+
+# name -> (restype, argtypes); every name is declared in include/vm.h
+_SIGS = {
+    "vm_create": (C.c_int, [C.POINTER(vm_map_params), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vm_integrate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_float), C.c_int]),
+    "vm_segment": (C.c_int, [C.c_void_p, C.POINTER(vm_segment_params), C.POINTER(vm_planes)]),
+    "vm_planes_free": (C.c_int, [C.POINTER(vm_planes)]),
+    "vm_reset": (C.c_int, [C.c_void_p]),
+    "vm_destroy": (C.c_int, [C.c_void_p]),
+    "vm_get_stats": (C.c_int, [C.c_void_p, C.POINTER(vm_stats)]),
+    "vm_fit_planes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(vm_segment_params),
+                                C.c_void_p, C.POINTER(vm_planes)]),
+    "vm_export_voxels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32,
+                                   C.POINTER(C.c_uint32)]),
+    "vm_export_labels": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_uint32, C.POINTER(C.c_uint32)]),
+    "vm_export_clusters": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32,
+                                     C.POINTER(C.c_uint32)]),
+    "vm_stage_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "vm_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32)]),
+    "vm_stage_name": (C.c_char_p, [C.c_uint32]),
+    "vm_launch_count": (C.c_uint64, []),
+    "vm_last_error": (C.c_char_p, []),
+    "vm_version": (C.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libvoxmps.so (building it first if needed).  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libvoxmps.so is missing at {path}; run paper_2510_01592_gb300.build.build()")
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != VM_OK:
+        raise VmError(st, load().vm_last_error().decode(errors="replace"))
+
+
+def segment_params(n_th=3, theta_step_deg=15.0, d_th=0.05, theta_ccl_deg=15.0, min_cluster=50, n_hyp=100, eps=0.01,
+                   seed=0, classify=1) -> vm_segment_params:
+    """Paper defaults (Sec. III.C, Sec. IV-A); cosines and d_th^2 in double, then FP32."""
+    return vm_segment_params(n_th, np.float32(math.cos(math.radians(theta_step_deg))), np.float32(d_th * d_th),
+                             np.float32(math.cos(math.radians(theta_ccl_deg))), min_cluster, n_hyp,
+                             np.float32(eps), seed, classify, 0)
+
+
+def _planes_to_numpy(out: vm_planes):
+    n = out.n_planes
+    dt = np.dtype([("normal", np.float32, 3), ("offset", np.float32), ("inlier_count", np.uint32),
+                   ("label", np.uint32), ("ransac_normal", np.float32, 3), ("ransac_offset", np.float32),
+                   ("basis_u", np.float32, 3), ("basis_v", np.float32, 3), ("hull_origin", np.float32, 3),
+                   ("hull_offset", np.uint32), ("hull_count", np.uint32), ("n_points", np.uint32),
+                   ("best_h", np.int32), ("flags", np.uint32)])
+    assert dt.itemsize == C.sizeof(vm_plane)
+    if n:
+        raw = C.string_at(out.planes, n * C.sizeof(vm_plane))
+        planes = np.frombuffer(raw, dtype=dt).copy()
+    else:
+        planes = np.zeros(0, dtype=dt)
+    nh = out.n_hull
+    hull_xy = np.ctypeslib.as_array(out.hull_xy, shape=(nh, 2)).copy() if nh else np.zeros((0, 2), np.int32)
+    hull_xyz = np.ctypeslib.as_array(out.hull_xyz, shape=(nh, 3)).copy() if nh else np.zeros((0, 3), np.float32)
+    return {"planes": planes, "hull_xy": hull_xy, "hull_xyz": hull_xyz}
+
+
+def _ptr(x):
+    """Device or host data pointer of a torch tensor / numpy array (or None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class VoxelMap:
+    """A device-resident voxel map (Sec. III.B) with multi-plane segmentation (Sec. III.C)."""
+
+    def __init__(self, dims, origin, voxel_size, brick_capacity=0, stream=None, stage_timing=False):
+        L = load()
+        p = vm_map_params((C.c_float * 3)(*[float(o) for o in origin]), (C.c_int32 * 3)(*[int(d) for d in dims]),
+                          float(voxel_size), int(brick_capacity), VM_MAP_STAGE_TIMING if stage_timing else 0)
+        h = C.c_void_p()
+        self._stream = stream
+        _check(L.vm_create(C.byref(p), _stream_handle(stream), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def integrate(self, xyz, pose):
+        """xyz: float32 [n, 3] torch tensor (CUDA or CPU) or numpy array; pose: 12 floats, sensor->map."""
+        pose = np.ascontiguousarray(pose, np.float32).reshape(12)
+        on_dev = 1 if (hasattr(xyz, "is_cuda") and xyz.is_cuda) else 0
+        if hasattr(xyz, "is_contiguous"):
+            assert xyz.dtype.is_floating_point and xyz.element_size() == 4 and xyz.is_contiguous()
+            n = xyz.numel() // 3
+        else:
+            xyz = np.ascontiguousarray(xyz, np.float32)
+            n = xyz.size // 3
+        _check(load().vm_integrate(self._h, _ptr(xyz), n, pose.ctypes.data_as(C.POINTER(C.c_float)), on_dev))
+
+    def segment(self, params: vm_segment_params | None = None):
+        params = params or segment_params()
+        out = vm_planes()
+        st = load().vm_segment(self._h, C.byref(params), C.byref(out))
+        try:
+            if st not in (VM_OK, VM_ERR_CAPACITY):
+                _check(st)
+            res = _planes_to_numpy(out)
+            res["status"] = st
+        finally:
+            load().vm_planes_free(C.byref(out))
+        return res
+
+    def reset(self):
+        _check(load().vm_reset(self._h))
+
+    def stats(self):
+        s = vm_stats()
+        st = load().vm_get_stats(self._h, C.byref(s))
+        if st not in (VM_OK, VM_ERR_CAPACITY):
+            _check(st)
+        return {f: getattr(s, f) for f, _ in vm_stats._fields_} | {"status": st}
+
+    def stage_times(self):
+        """{stage: (ms, calls)} accumulated since the previous call."""
+        return stage_times(self._h)
+
+    def export_voxels(self):
+        L = load()
+        n = C.c_uint32()
+        _check(L.vm_export_voxels(self._h, None, None, None, 0, C.byref(n)))
+        k = n.value
+        vid = np.zeros(k, np.uint32)
+        S = np.zeros((k, 3), np.int64)
+        c = np.zeros(k, np.uint32)
+        _check(L.vm_export_voxels(self._h, _ptr(vid), _ptr(S), _ptr(c), k, C.byref(n)))
+        return vid, S, c
+
+    def export_labels(self):
+        L = load()
+        n = C.c_uint32()
+        _check(L.vm_export_labels(self._h, None, None, None, None, None, 0, C.byref(n)))
+        k = n.value
+        vid = np.zeros(k, np.uint32)
+        nrm = np.zeros((k, 3), np.float32)
+        st = np.zeros(k, np.uint8)
+        lab = np.zeros(k, np.uint32)
+        nbr = np.zeros(k, np.uint32)
+        _check(L.vm_export_labels(self._h, _ptr(vid), _ptr(nrm), _ptr(st), _ptr(lab), _ptr(nbr), k, C.byref(n)))
+        return {"vid": vid, "n": nrm, "status": st, "label": lab, "nbr": nbr}
+
+    def export_clusters(self):
+        L = load()
+        n = C.c_uint32()
+        _check(L.vm_export_clusters(self._h, None, None, None, 0, C.byref(n)))
+        k = n.value
+        pts = np.zeros((k, 3), np.float32)
+        vid = np.zeros(k, np.uint32)
+        inl = np.zeros(k, np.uint8)
+        _check(L.vm_export_clusters(self._h, _ptr(pts), _ptr(vid), _ptr(inl), k, C.byref(n)))
+        return {"pts": pts, "pt_vid": vid, "inlier": inl}
+
+
+def fit_planes(xyz, off, params: vm_segment_params | None = None, labels=None, stream=None):
+    """Batched RANSAC + refit + hull on caller clusters; xyz, off, labels are CUDA tensors."""
+    params = params or segment_params()
+    k = int(off.numel()) - 1
+    out = vm_planes()
+    _check(load().vm_fit_planes(_ptr(xyz), _ptr(off), _ptr(labels), k, C.byref(params), _stream_handle(stream),
+                                C.byref(out)))
+    try:
+        return _planes_to_numpy(out)
+    finally:
+        load().vm_planes_free(C.byref(out))
+
+
+def stage_times(handle=None):
+    L = load()
+    ms = (C.c_double * N_STAGES)()
+    calls = (C.c_uint64 * N_STAGES)()
+    n = C.c_uint32()
+    _check(L.vm_stage_times(handle, ms, calls, N_STAGES, C.byref(n)))
+    return {L.vm_stage_name(i).decode(): (ms[i], int(calls[i])) for i in range(n.value)}
+
+
+def set_fit_stage_timing(enable: bool):
+    """Stage timing of this thread's fit_planes calls."""
+    _check(load().vm_stage_timing(None, 1 if enable else 0))
+
+
+def launch_count() -> int:
+    return int(load().vm_launch_count())
+
+
+# C-ABI names re-exported for callers who want the raw entry points.
+def __getattr__(name):
+    if name in _SIGS:
+        return getattr(load(), name)
+    raise AttributeError(name)

@@ -1,0 +1,86 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/vm.h declares; without a GPU its calls fail with a status (no crash,
+no CPU fallback).  The Python binding's structs match the header's sizes."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "vm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(vm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("vm_create", "vm_integrate", "vm_segment", "vm_destroy", "vm_fit_planes", "vm_planes_free",
+              "vm_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2510_01592_gb300 import vm
+    L = vm.load()
+    for n in _declared():
+        assert hasattr(L, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", vm.lib_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (vm_[a-z_0-9]+)\b", out))
+    assert set(_declared()) <= exported
+    assert L.vm_version().startswith(b"voxmps")
+
+
+def test_binding_struct_sizes_match_header():
+    """Compile a probe against include/vm.h with the host compiler and compare sizeof."""
+    from paper_2510_01592_gb300 import vm
+    probe = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "vm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(vm_map_params), sizeof(vm_segment_params), sizeof(vm_plane),
+         sizeof(vm_planes), sizeof(vm_stats), offsetof(vm_plane, hull_offset), offsetof(vm_segment_params, seed));
+  return 0;
+}
+'''
+    d = os.path.join(ROOT, "paper_2510_01592_gb300", "_build")
+    os.makedirs(d, exist_ok=True)
+    src = os.path.join(d, "abi_probe.c")
+    exe = os.path.join(d, "abi_probe")
+    open(src, "w").write(probe)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+    got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    want = [C.sizeof(vm.vm_map_params), C.sizeof(vm.vm_segment_params), C.sizeof(vm.vm_plane),
+            C.sizeof(vm.vm_planes), C.sizeof(vm.vm_stats), vm.vm_plane.hull_offset.offset,
+            vm.vm_segment_params.seed.offset]
+    assert got == want
+
+
+def test_calls_fail_with_a_status_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2510_01592_gb300 import vm
+    with pytest.raises(vm.VmError) as ei:
+        vm.VoxelMap((8, 8, 8), (0, 0, 0), 0.05)
+    assert ei.value.status in (vm.VM_ERR_CUDA, vm.VM_ERR_OUT_OF_MEMORY)
+
+
+def test_invalid_arguments_rejected_before_any_device_work():
+    from paper_2510_01592_gb300 import vm
+    L = vm.load()
+    h = C.c_void_p()
+    bad = vm.vm_map_params((C.c_float * 3)(0, 0, 0), (C.c_int32 * 3)(0, 8, 8), 0.05, 0, 0)
+    assert L.vm_create(C.byref(bad), None, C.byref(h)) == vm.VM_ERR_INVALID_ARG
+    huge = vm.vm_map_params((C.c_float * 3)(0, 0, 0), (C.c_int32 * 3)(2000, 8, 8), 0.01, 0, 0)
+    assert L.vm_create(C.byref(huge), None, C.byref(h)) == vm.VM_ERR_INVALID_ARG  # 20 m > 16 m
+    assert L.vm_segment(None, None, None) == vm.VM_ERR_INVALID_ARG
+    p = vm.segment_params(n_hyp=0)
+    out = vm.vm_planes()
+    assert L.vm_fit_planes(None, None, None, 1, C.byref(p), None, C.byref(out)) == vm.VM_ERR_INVALID_ARG
+    assert b"n_hyp" in L.vm_last_error()

@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU oracle
+on the same seeded inputs.  Exact fields bit for bit; the refit within
+1e-4 rad / 1e-5 m (see tests/parity.py)."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from parity import compare_labels, compare_planes, compare_sums
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vmmod():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2510_01592_gb300 import vm
+    vm.load()
+    return vm
+
+
+def _params_pair(orc, vm, **kw):
+    return orc.make_params(**kw), vm.segment_params(**kw)
+
+
+def _run_both(orc, vm, spec, frames, seg_kw, brick_capacity=0):
+    """frames: list of (points float32[n,3] numpy, pose[12])."""
+    gm = vm.VoxelMap(spec.dims, spec.origin, spec.voxel_size, brick_capacity=brick_capacity)
+    om = orc.OracleMap(spec.dims, spec.origin, spec.voxel_size)
+    for pts, pose in frames:
+        gm.integrate(pts, pose)
+        om.integrate(pts, pose)
+    op, gpm = _params_pair(orc, vm, **seg_kw)
+    return gm, om, op, gpm
+
+
+def _check_segment(orc, vm, gm, om, op, gpm):
+    compare_sums(gm, om)
+    ores = om.segment(op)
+    gres = gm.segment(gpm)
+    assert gres["status"] == vm.VM_OK
+    compare_labels(gm.export_labels(), ores["voxels"])
+    return compare_planes(gres, ores, gm.export_clusters()), gres, ores
+
+
+def test_config1_integrate_and_segment(orc, vmmod):
+    spec, pts, pose = synth.config1()
+    gm, om, op, gp = _run_both(orc, vmmod, spec, [(pts, pose)], dict(n_hyp=64))
+    (wa, wd), gres, _ = _check_segment(orc, vmmod, gm, om, op, gp)
+    assert len(gres["planes"]) >= 4
+    st = gm.stats()
+    assert st["points_integrated"] + st["points_dropped"] == len(pts)
+
+
+@pytest.mark.parametrize("res", [0.01, 0.02, 0.05])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_random_plane_scenes(orc, vmmod, res, seed):
+    rng = np.random.default_rng(seed)
+    pts = []
+    for _ in range(8):
+        t = math.radians(rng.uniform(0, 25))
+        a = rng.uniform(0, 2 * math.pi)
+        n = np.array([math.sin(t) * math.cos(a), math.sin(t) * math.sin(a), math.cos(t)])
+        c = rng.uniform([0.1, 0.1, 0.05], [0.9, 0.9, 0.5])
+        u = np.cross([1.0, 0, 0], n)
+        u /= np.linalg.norm(u)
+        w = np.cross(n, u)
+        s = rng.uniform(-0.2, 0.2, size=(6000, 2))
+        pts.append(c + s[:, :1] * u + s[:, 1:] * w + rng.normal(0, 0.002, size=(6000, 1)) * n)
+    pts = np.concatenate(pts).astype(np.float32)
+    spec = synth.MapSpec((int(round(1.0 / res)),) * 2 + (int(round(0.6 / res)),), (0.0, 0.0, 0.0), res)
+    theta = 8.0 if seed else 15.0
+    gm, om, op, gp = _run_both(orc, vmmod, spec, [(pts, synth.identity_pose())],
+                               dict(n_hyp=48, theta_ccl_deg=theta, min_cluster=20, seed=seed))
+    _check_segment(orc, vmmod, gm, om, op, gp)
+
+
+def test_all_occupied_clustering_and_rotated_pose(orc, vmmod):
+    """classify = 0 (every occupied voxel is a vertex) with a rotated, translated pose."""
+    spec, pts, _ = synth.config1()
+    c, s = math.cos(0.3), math.sin(0.3)
+    pose = np.array([c, -s, 0, 0.02, s, c, 0, -0.01, 0, 0, 1, 0.005], np.float32)
+    gm, om, op, gp = _run_both(orc, vmmod, spec, [(pts, pose)], dict(n_hyp=32, classify=0, min_cluster=30))
+    _check_segment(orc, vmmod, gm, om, op, gp)
+
+
+def test_config2_frames(orc, vmmod):
+    """Paper-scale map (4 x 4 x 2 m at 0.01 m): the first frames of the trajectory,
+    segmented after frame 4 and after frame 10."""
+    spec = synth.config2_spec()
+    scene = synth.config2_scene()
+    gm = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size)
+    om = orc.OracleMap(spec.dims, spec.origin, spec.voxel_size)
+    op, gp = _params_pair(orc, vmmod, n_hyp=100)
+    for f in range(1, 11):
+        pts, pose = synth.config2_frame(f, scene, device="cuda")
+        gm.integrate(pts, pose)                # device pointer
+        om.integrate(pts.cpu().numpy(), pose)
+        if f in (4, 10):
+            _check_segment(orc, vmmod, gm, om, op, gp)
+
+
+def test_host_and_device_inputs_agree(vmmod):
+    spec, pts, pose = synth.config1()
+    import torch
+    a = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size)
+    a.integrate(pts, pose)  # host memory, copied by the library
+    b = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size)
+    b.integrate(torch.from_numpy(pts).cuda(), pose)
+    for x, y in zip(a.export_voxels(), b.export_voxels()):
+        assert np.array_equal(x, y)
+
+
+def test_degenerate_inputs(orc, vmmod):
+    spec = synth.MapSpec((40, 40, 20), (0, 0, 0), 0.02)
+    m = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size)
+    # empty map
+    r = m.segment(vmmod.segment_params())
+    assert len(r["planes"]) == 0 and r["status"] == vmmod.VM_OK
+    # NaN / Inf / out-of-extent points only
+    bad = np.array([[np.nan, 0, 0], [np.inf, 0.1, 0.1], [5, 5, 5], [-1, 0.1, 0.1]], np.float32)
+    m.integrate(bad, synth.identity_pose())
+    st = m.stats()
+    assert st["points_integrated"] == 0 and st["points_dropped"] == 4
+    assert len(m.segment(vmmod.segment_params())["planes"]) == 0
+    # a single voxel, a line of voxels: no steppable clusters
+    line = np.stack([np.linspace(0.01, 0.7, 200), np.full(200, 0.3), np.full(200, 0.1)], 1).astype(np.float32)
+    m.integrate(line, synth.identity_pose())
+    om = orc.OracleMap(spec.dims, spec.origin, spec.voxel_size)
+    om.integrate(np.concatenate([bad, line]), synth.identity_pose())
+    compare_sums(m, om)
+    op, gp = _params_pair(orc, vmmod, min_cluster=1, n_hyp=16)
+    ores, gres = om.segment(op), m.segment(gp)
+    compare_labels(m.export_labels(), ores["voxels"])
+    compare_planes(gres, ores, m.export_clusters())
+
+
+def test_capacity_overflow_reports_and_keeps_going(vmmod):
+    spec, pts, pose = synth.config1()
+    m = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size, brick_capacity=8)
+    m.integrate(pts, pose)
+    st = m.stats()
+    assert st["status"] == vmmod.VM_ERR_CAPACITY
+    assert st["bricks_allocated"] == 8 and st["points_no_capacity"] > 0
+    assert st["points_integrated"] + st["points_dropped"] + st["points_no_capacity"] == len(pts)
+    r = m.segment(vmmod.segment_params(n_hyp=16))
+    assert r["status"] == vmmod.VM_ERR_CAPACITY
+
+
+def _clusters_for_fit(seed, n_clusters, hi):
+    xyz, off, _ = synth.config3_clusters(n_clusters=n_clusters, seed=seed, size_hi=hi)
+    return xyz, off
+
+
+def test_fit_planes_batch(orc, vmmod):
+    import torch
+    xyz, off = _clusters_for_fit(3, 60, 20000)
+    # edge clusters: empty, 1, 2, 3 points, collinear
+    extra = [np.zeros((0, 3)), np.array([[1, 1, 1.0]]), np.array([[0, 0, 0], [1, 0, 0.0]]),
+             np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0.0]]),
+             np.stack([np.arange(80) * 0.01, np.zeros(80), np.zeros(80)], 1)]
+    pts = [xyz] + [e.astype(np.float32) for e in extra]
+    sizes = list(np.diff(off.astype(np.int64))) + [len(e) for e in extra]
+    allp = np.concatenate(pts).astype(np.float32)
+    offs = np.zeros(len(sizes) + 1, np.uint32)
+    offs[1:] = np.cumsum(sizes)
+    labels = (np.arange(len(sizes), dtype=np.uint32) * 7919 + 13).astype(np.uint32)
+    op, gp = _params_pair(orc, vmmod, n_hyp=256, seed=7)
+    ores = orc.fit_planes(allp, offs, op, labels=labels)
+    gres = vmmod.fit_planes(torch.from_numpy(allp).cuda(), torch.from_numpy(offs).cuda(), gp,
+                            labels=torch.from_numpy(labels).cuda())
+    compare_planes(gres, ores)
+
+
+def test_fit_planes_hull_beyond_shared_memory(orc, vmmod):
+    """A dense disc leaves more octagon survivors than the shared-memory sort
+    holds; the gift-wrapping path must give the same hull."""
+    import torch
+    rng = np.random.default_rng(5)
+    r = np.sqrt(rng.uniform(0, 1, 150000)) * 1.5
+    a = rng.uniform(0, 2 * math.pi, 150000)
+    pts = np.stack([r * np.cos(a), r * np.sin(a), rng.normal(0, 0.001, 150000)], 1).astype(np.float32)
+    off = np.array([0, len(pts)], np.uint32)
+    op, gp = _params_pair(orc, vmmod, n_hyp=32, seed=1)
+    ores = orc.fit_planes(pts, off, op)
+    gres = vmmod.fit_planes(torch.from_numpy(pts).cuda(), torch.from_numpy(off).cuda(), gp)
+    compare_planes(gres, ores)
+    assert gres["planes"]["hull_count"][0] > 50
