@@ -162,6 +162,35 @@ vm_status vm_get_stats(vm_map* map, vm_stats* out);
 vm_status vm_fit_planes(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
                         const vm_segment_params* params, void* stream, vm_planes* out);
 
+/* RANSAC without allocation.  The paper has no counterpart: this entry point
+ * serves callers that must not allocate device memory while they run -- a
+ * robot control loop with a hard deadline (cudaMalloc can stall on
+ * device-wide synchronisation for an unbounded time) or a host program whose
+ * device memory is owned up front by another allocator.  It runs the same
+ * hypothesis, scoring and selection kernels as vm_fit_planes (Sec. III.C
+ * stages a-c) on caller-formed clusters, with all scratch in one array
+ * compiled into the library (about 11 MiB per GPU that loads it, held until
+ * the process exits); it calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ * Limits: k <= 4096 clusters and k * n_hyp <= 524288; larger requests return
+ * VM_ERR_CAPACITY with a message and launch nothing.
+ * Inputs (device): xyz float32[off[k]][3]; off uint32[k+1]; labels uint32[k]
+ * or NULL (label = cluster index).  Outputs (device, caller-owned):
+ * planes_out float32[k][4] = (n_x, n_y, n_z, d) of the selected hypothesis,
+ * best_h_out int32[k] (-1: no valid hypothesis), inliers_out uint32[k].
+ * Results equal vm_fit_planes' ransac_normal / ransac_offset / best_h /
+ * inlier_count bit for bit.  Asynchronous on stream (NULL: legacy default
+ * stream); outputs are ready once the stream has synchronised.
+ * Every call on a device shares the one scratch array, which keeps the last
+ * call's contents (the work queue and counters are cleared at the start of
+ * each call): calls whose work overlaps on the GPU race, so serialise them
+ * (one stream, or events).  The first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture. */
+vm_status vm_ransac_static(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
+                           const vm_segment_params* params, void* stream, float* planes_out, int32_t* best_h_out,
+                           uint32_t* inliers_out);
+
 /* Debug / parity export of the occupied voxels, in voxel-id order.  Voxel ids
  * are brick-major: bricks of 8^3 voxels numbered x-fastest over the brick
  * grid, voxels inside a brick x-fastest.  Host output arrays of capacity cap:

@@ -22,6 +22,8 @@
 //            gift-wrapping pass over global memory when the survivors exceed
 //            shared memory.
 #include <climits>
+#include <mutex>
+#include <string>
 
 #include "vm_internal.cuh"
 
@@ -786,3 +788,134 @@ cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_
 }
 
 }  // namespace vmx
+
+// ---------------------------------------------------------------- no-allocation RANSAC
+// vm_ransac_static runs the same hypothesis / scoring / selection kernels as
+// vm_fit_planes, but every scratch buffer lives in one file-scope device array
+// instead of memory obtained from cudaMalloc.  It exists for callers that may
+// not allocate device memory once they are running -- a control loop with a
+// hard deadline (cudaMalloc can block on device-wide synchronisation for an
+// unbounded time), or a host program whose device memory is owned up front by
+// another allocator.  The array is sized for at most kStaticMaxClusters
+// clusters and kStaticMaxSlots (clusters x hypotheses); every GPU that loads
+// the library holds it (about 11 MiB) until the process exits.
+namespace vmx {
+namespace {
+
+constexpr uint32_t kStaticMaxClusters = 4096;
+constexpr uint32_t kStaticMaxSlots = 524288;  // clusters x hypotheses
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr size_t kOffHyp = 0;
+constexpr size_t kOffCounts = kOffHyp + align256((size_t)kStaticMaxSlots * sizeof(float4));
+constexpr size_t kOffValid = kOffCounts + align256((size_t)kStaticMaxSlots * sizeof(uint32_t));
+constexpr size_t kOffCl = kOffValid + align256((size_t)kStaticMaxSlots);
+constexpr size_t kOffItems = kOffCl + align256((size_t)kStaticMaxClusters * sizeof(FitCluster));
+constexpr size_t kOffQueue = kOffItems + align256((size_t)(kStaticMaxClusters + 1) * sizeof(uint32_t));
+constexpr size_t kOffScan = kOffQueue + 256;
+constexpr size_t kScanWords = 64;  // >= scan_tmp_words(kStaticMaxClusters + 1)
+constexpr size_t kStaticBytes = kOffScan + align256(kScanWords * sizeof(uint32_t));
+
+// Copies the selected plane, hypothesis index and inlier count of each cluster
+// to the caller's arrays.
+__global__ void k_static_out(const FitCluster* __restrict__ cl, uint32_t k, float* __restrict__ planes,
+                             int32_t* __restrict__ best_h, uint32_t* __restrict__ inliers) {
+    for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT) {
+        const FitCluster f = cl[c];
+        planes[4 * c + 0] = f.n[0];
+        planes[4 * c + 1] = f.n[1];
+        planes[4 * c + 2] = f.n[2];
+        planes[4 * c + 3] = f.d;
+        best_h[c] = f.best_h;
+        inliers[c] = f.best_h >= 0 ? f.inliers : 0u;
+    }
+}
+
+}  // namespace
+}  // namespace vmx
+
+static __device__ __align__(256) unsigned char g_ransac_scratch[vmx::kStaticBytes];
+
+namespace {
+// Device address of g_ransac_scratch per device ordinal, looked up once per
+// device (with that device current) by the first call made on it.
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
+                                      const vm_segment_params* params, void* stream, float* planes_out,
+                                      int32_t* best_h_out, uint32_t* inliers_out) {
+    using namespace vmx;
+    if (!params || (k && (!xyz || !off || !planes_out || !best_h_out || !inliers_out))) {
+        set_error("vm_ransac_static: null argument");
+        return VM_ERR_INVALID_ARG;
+    }
+    if (params->n_hyp < 1 || params->n_hyp > 1024 || !(params->eps >= 0.0f)) {
+        set_error("vm_ransac_static: n_hyp must be in [1, 1024] and eps >= 0");
+        return VM_ERR_INVALID_ARG;
+    }
+    if (k == 0) return VM_OK;
+    if (k > kStaticMaxClusters || (uint64_t)k * params->n_hyp > kStaticMaxSlots) {
+        set_error("vm_ransac_static: " + std::to_string(k) + " clusters x " + std::to_string(params->n_hyp) +
+                  " hypotheses exceed the static scratch (at most " + std::to_string(kStaticMaxClusters) +
+                  " clusters and " + std::to_string(kStaticMaxSlots) + " cluster-hypothesis pairs)");
+        return VM_ERR_CAPACITY;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("vm_ransac_static: device ordinal out of range");
+        return VM_ERR_INVALID_ARG;
+    }
+    char* base;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_ransac_scratch);
+            if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_ransac_scratch)");
+            g_static_addr[dev] = p;
+        }
+        base = static_cast<char*>(g_static_addr[dev]);
+    }
+    const int H = (int)params->n_hyp;
+    const FitTuning t = default_tuning();
+    float4* hyp = reinterpret_cast<float4*>(base + kOffHyp);
+    uint32_t* counts = reinterpret_cast<uint32_t*>(base + kOffCounts);
+    uint8_t* valid = reinterpret_cast<uint8_t*>(base + kOffValid);
+    FitCluster* cl = reinterpret_cast<FitCluster*>(base + kOffCl);
+    uint32_t* item_off = reinterpret_cast<uint32_t*>(base + kOffItems);
+    uint32_t* queue = reinterpret_cast<uint32_t*>(base + kOffQueue);
+    uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(base + kOffScan);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    // the work queue starts at zero every call; counts are zeroed by k_hyp
+    if ((e = cudaMemsetAsync(queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess)
+        return cuda_status(e, "cudaMemsetAsync");
+    k_items<<<(k + kT - 1) / kT, kT, 0, s>>>(off, k, t.tile, item_off);
+    if ((e = exclusive_scan_u32(item_off, item_off, item_off + k, k, scan_tmp, s)) != cudaSuccess)
+        return cuda_status(e, "scan");
+    const size_t kh = (size_t)k * H;
+    const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
+    k_hyp<<<hgrid, kT, 0, s>>>(xyz, off, labels, k, H, params->seed, hyp, valid, counts);
+    int R = t.hyp_per_thread;
+    while (R < 8 && (H + R - 1) / R > kT) R <<= 1;
+    const int grid = sms * t.ctas_per_sm;
+    switch (R) {
+        case 8: e = launch_score<8>(xyz, off, item_off, k, H, t.tile, hyp, counts, queue, params->eps, grid, s); break;
+        default: e = launch_score<4>(xyz, off, item_off, k, H, t.tile, hyp, counts, queue, params->eps, grid, s); break;
+    }
+    if (e != cudaSuccess) return cuda_status(e, "k_score");
+    const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;
+    k_select<<<cgrid, kT, 0, s>>>(xyz, off, k, H, hyp, valid, counts, cl);
+    k_static_out<<<(k + kT - 1) / kT, kT, 0, s>>>(cl, k, planes_out, best_h_out, inliers_out);
+    count_launch(5);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "vm_ransac_static launch");
+    return VM_OK;
+}
