@@ -48,7 +48,30 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--stages", action="store_true", help="print the per-stage breakdown to stderr")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="F",
+                    help="profiling driver: integrate frames 1..F, segment --profile-segments times, no timing")
+    ap.add_argument("--profile-segments", type=int, default=3)
     return ap.parse_args()
+
+
+def profile_case(frames, segments):
+    """A small, fixed invocation of the path for profiler captures: frames
+    1..F of the paper-scale trajectory integrated, then `segments` segment
+    calls (the first warms the scratch; capture the later ones)."""
+    import torch
+    from paper_2510_01592_gb300 import vm
+    import synth
+    spec = synth.config2_spec()
+    scene = synth.config2_scene()
+    m = vm.VoxelMap(spec.dims, spec.origin, spec.voxel_size)
+    for f in range(1, frames + 1):
+        p, pose = synth.config2_frame(f, scene, device="cuda")
+        m.integrate(p, pose)
+    for _ in range(segments):
+        r = m.segment(seg_params(vm))
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": frames, "segments": segments, "planes": int(len(r["planes"])),
+                      "stats": {k: v for k, v in m.stats().items() if isinstance(v, int)}}))
 
 
 def dist_env():
@@ -352,6 +375,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args.profile_case, args.profile_segments)
+        return
     if args.impl == "reference":
         res, rank = run_reference(args)
         if res is not None and rank == 0:

@@ -284,6 +284,10 @@ static vm_status fit_and_pack(FitContext& fc, const float* pts, const uint32_t* 
         set_error("a bounded device loop reached its iteration cap during the plane fit");
         return VM_ERR_TIMEOUT;
     }
+    if (hdr[1] & kErrOverflow) {
+        set_error("a cluster spans more than 2^28 hull quanta (4096 m) in its plane; its hull is not exact");
+        return VM_ERR_EXTENT;
+    }
     return VM_OK;
 }
 
@@ -336,6 +340,7 @@ vm_status alloc_vox(vm_map* m, uint32_t n_sorted) {
         b.nrm = c.take<float>(3 * nv);
         b.status = c.take<uint8_t>(nv);
         b.nbr = c.take<uint8_t>(nv);
+        b.rec = c.take<float4>(2 * nv);
         b.parent = c.take<uint32_t>(nv);
         b.count = c.take<uint32_t>(nv);
         b.cid = c.take<uint32_t>(nv + 1);

@@ -12,15 +12,16 @@
 //  k_select  stage c: max count, lowest hypothesis index on ties; in-plane
 //            basis and hull origin.
 //  k_extract inliers of the selected plane, centroid partial sums and the
-//            octagon of extreme points (exact integer keys).
-//  k_filter  covariance partial sums; points strictly inside the octagon
-//            cannot be hull vertices and are dropped (the GPU filtering step
-//            of the cited convex-hull method), the rest are appended.
-//  k_hull    per cluster: TLS refit in double from the partial sums; sort of
-//            the surviving quantised points in shared memory (bitonic), then
-//            Andrew's monotone chain with exact int64 orientation tests; a
-//            gift-wrapping pass over global memory when the survivors exceed
-//            shared memory.
+//            extreme inliers along 16 integer directions (exact integer keys).
+//  k_filter  covariance partial sums; points strictly inside the 16-gon of
+//            extreme points cannot be hull vertices and are dropped (the GPU
+//            filtering step of the cited convex-hull method), the rest are
+//            appended.
+//  k_refit   per cluster: TLS refit in double from the partial sums.
+//  k_hull    per cluster: a second, 32-direction filter, then a bitonic sort
+//            of the remaining quantised points in shared memory and Andrew's
+//            monotone chain with exact int64 orientation tests; gift wrapping
+//            over global memory when too many remain for shared memory.
 #include <climits>
 #include <mutex>
 #include <string>
@@ -31,7 +32,8 @@ namespace vmx {
 namespace {
 
 constexpr int kT = 256;
-constexpr int kHullCap = 4096;  // survivors sorted in shared memory
+constexpr int kHullCap = 2048;   // hull candidates sorted in shared memory
+constexpr int kSurvCap = 12288;  // first-filter survivors staged in shared memory
 
 // ---------------------------------------------------------------- Philox
 __device__ __forceinline__ void philox4x64_10(const unsigned long long ctr[4], const unsigned long long key[2],
@@ -231,18 +233,20 @@ __device__ __forceinline__ int2 quantise(const FitCluster& f, float px, float py
     return make_int2(__float2int_rn(__fmul_rn(a, 65536.0f)), __float2int_rn(__fmul_rn(b, 65536.0f)));
 }
 
-// Directions of the octagon, counter-clockwise: (1,0) (1,1) (0,1) (-1,1) (-1,0) (-1,-1) (0,-1) (1,-1).
+// The 16 filter directions, counter-clockwise: (1,0) (2,1) (1,1) (1,2) (0,1)
+// (-1,2) (-1,1) (-2,1) (-1,0) (-2,-1) (-1,-1) (-1,-2) (0,-1) (1,-2) (1,-1) (2,-1).
+// With |X|, |Y| < 2^28 every value fits in int32.
+constexpr int kFiltDirs = 16;
 __device__ __forceinline__ int32_t dir_value(int dir, int2 p) {
-    switch (dir) {
-        case 0: return p.x;
-        case 1: return p.x + p.y;
-        case 2: return p.y;
-        case 3: return p.y - p.x;
-        case 4: return -p.x;
-        case 5: return -p.x - p.y;
-        case 6: return -p.y;
-        default: return p.x - p.y;
-    }
+    const int a = (dir == 0 || dir == 2 || dir == 3 || dir == 14 || dir == 13) ? 1
+                : (dir == 1 || dir == 15) ? 2
+                : (dir == 4 || dir == 12) ? 0
+                : (dir == 7 || dir == 9) ? -2 : -1;
+    const int b = (dir == 0 || dir == 8) ? 0
+                : (dir == 1 || dir == 2 || dir == 4 || dir == 6 || dir == 7) ? 1
+                : (dir == 3 || dir == 5) ? 2
+                : (dir == 11 || dir == 13) ? -2 : -1;
+    return a * p.x + b * p.y;
 }
 
 __device__ __forceinline__ unsigned long long ext_key(int32_t v, uint32_t idx) {
@@ -262,29 +266,14 @@ __device__ __forceinline__ Tv block_sum(Tv v, Tv* sh) {
     return t;  // valid in thread 0
 }
 
-__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long* sh) {
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, s);
-        v = o > v ? o : v;
-    }
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    unsigned long long t = 0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kT / 32; ++w) t = sh[w] > t ? sh[w] : t;
-    return t;
-}
-
-// Inliers, centroid partials (relative to the origin) and octagon extremes.
+// Inliers, centroid partials (relative to the origin) and the extreme inliers
+// along the 16 filter directions (reduced per warp, then atomicMax).
 __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                                 const uint32_t* __restrict__ item_off, uint32_t k, int T,
                                                 FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
-                                                float* __restrict__ part, float eps) {
+                                                float* __restrict__ part, float eps, uint32_t* __restrict__ err) {
     __shared__ float shf[kT / 32];
     __shared__ uint32_t shu[kT / 32];
-    __shared__ unsigned long long shm[kT / 32];
     const uint32_t n_items = item_off[k];
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         const uint32_t c = find_cluster(item_off, k, it);
@@ -293,9 +282,10 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
         const uint32_t end = min(off[c + 1], start + (uint32_t)T);
         float sx = 0.0f, sy = 0.0f, sz = 0.0f;
         uint32_t cnt = 0;
-        unsigned long long ext[8];
+        unsigned long long ext[kFiltDirs];
 #pragma unroll
-        for (int d = 0; d < 8; ++d) ext[d] = 0;
+        for (int d = 0; d < kFiltDirs; ++d) ext[d] = 0;
+        bool big = false;
         for (uint32_t q = start + threadIdx.x; q < end; q += kT) {
             const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
             const bool in = f.best_h >= 0 && plane_dist(f.n[0], f.n[1], f.n[2], f.d, px, py, pz) <= eps;
@@ -306,13 +296,15 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
             sy += __fsub_rn(py, f.o[1]);
             sz += __fsub_rn(pz, f.o[2]);
             const int2 xy = quantise(f, px, py, pz);
+            big |= (abs(xy.x) >= (1 << 28)) | (abs(xy.y) >= (1 << 28));
             const uint32_t idx = q - off[c];
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
+            for (int d = 0; d < kFiltDirs; ++d) {
                 const unsigned long long key = ext_key(dir_value(d, xy), idx);
                 ext[d] = key > ext[d] ? key : ext[d];
             }
         }
+        if (big) atomicOr(err, kErrOverflow);
         const float tx = block_sum(sx, shf), ty = block_sum(sy, shf), tz = block_sum(sz, shf);
         const uint32_t tc = block_sum(cnt, shu);
         if (threadIdx.x == 0) {
@@ -321,31 +313,49 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
             pp[1] = tx; pp[2] = ty; pp[3] = tz;
         }
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            const unsigned long long m = block_max_u64(ext[d], shm);
-            if (threadIdx.x == 0 && m) atomicMax(&cl[c].ext[d], m);
+        for (int d = 0; d < kFiltDirs; ++d) {
+            unsigned long long m = ext[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+                m = t > m ? t : m;
+            }
+            if ((threadIdx.x & 31) == 0 && m) atomicMax(&cl[c].ext[d], m);
         }
         __syncthreads();
     }
 }
 
-// Per cluster: inlier count and centroid (double over the per-item partials).
+// Per cluster (one warp each): inlier count and centroid, the per-item
+// partial sums added in double in a fixed order (lane-strided, then a shuffle
+// tree), so the result does not depend on scheduling.
 __global__ void k_centroid(const uint32_t* __restrict__ item_off, uint32_t k, const float* __restrict__ part,
                            FitCluster* __restrict__ cl, double* __restrict__ cen) {
-    for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (kT / 32);
+    for (uint32_t c = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); c < k; c += warps) {
         double sx = 0, sy = 0, sz = 0;
         uint32_t n = 0;
-        for (uint32_t it = item_off[c]; it < item_off[c + 1]; ++it) {
+        for (uint32_t it = item_off[c] + lane; it < item_off[c + 1]; it += 32) {
             const float* pp = part + (size_t)it * 10;
             n += __float_as_uint(pp[0]);
             sx += pp[1]; sy += pp[2]; sz += pp[3];
         }
-        FitCluster& f = cl[c];
-        f.inliers = n;
-        double cx = f.o[0], cy = f.o[1], cz = f.o[2];
-        if (n) { cx += sx / n; cy += sy / n; cz += sz / n; }
-        cen[3 * c] = cx; cen[3 * c + 1] = cy; cen[3 * c + 2] = cz;
-        f.c[0] = (float)cx; f.c[1] = (float)cy; f.c[2] = (float)cz;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            n += __shfl_xor_sync(0xffffffffu, n, o);
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        if (lane == 0) {
+            FitCluster& f = cl[c];
+            f.inliers = n;
+            double cx = f.o[0], cy = f.o[1], cz = f.o[2];
+            if (n) { cx += sx / n; cy += sy / n; cz += sz / n; }
+            cen[3 * c] = cx; cen[3 * c + 1] = cy; cen[3 * c + 2] = cz;
+            f.c[0] = (float)cx; f.c[1] = (float)cy; f.c[2] = (float)cz;
+        }
     }
 }
 
@@ -353,14 +363,16 @@ __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b) {
     return (long long)(a.x - o.x) * (long long)(b.y - o.y) - (long long)(a.y - o.y) * (long long)(b.x - o.x);
 }
 
-// Covariance partials about the centroid and the octagon filter.
+// Covariance partials about the centroid, and the 16-gon filter: inliers
+// strictly inside the polygon through the 16 extreme inliers cannot be hull
+// vertices; the others are appended to the cluster's survivor list.
 __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                                const uint32_t* __restrict__ item_off, uint32_t k, int T,
                                                FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
                                                const double* __restrict__ cen, float* __restrict__ part,
                                                int2* __restrict__ surv) {
     __shared__ float shf[kT / 32];
-    __shared__ int2 poly[9];
+    __shared__ int2 poly[kFiltDirs + 1];
     __shared__ int npoly;
     const uint32_t n_items = item_off[k];
     const int lane = threadIdx.x & 31;
@@ -372,9 +384,9 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
         const uint32_t end = min(off[c + 1], start + (uint32_t)T);
         __syncthreads();
         if (threadIdx.x == 0) {
-            // octagon through the extreme points, counter-clockwise, duplicates removed
+            // polygon through the extreme points, counter-clockwise, duplicates removed
             int m = 0;
-            for (int d = 0; d < 8; ++d) {
+            for (int d = 0; d < kFiltDirs; ++d) {
                 if (!f.ext[d]) continue;
                 const uint32_t idx = (uint32_t)(f.ext[d] & 0xffffffffu);
                 const float* p = pts + 3 * ((size_t)base + idx);
@@ -426,34 +438,76 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
     }
 }
 
-// Double-precision cyclic Jacobi for the refit (same rotation as the FP32 one).
-__device__ void jacobi3_d(double A[6], int sweeps, double v[3][3], double d[3]) {
-    double a[3][3] = {{A[0], A[3], A[4]}, {A[3], A[1], A[5]}, {A[4], A[5], A[2]}};
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) v[r][c] = (r == c) ? 1.0 : 0.0;
-    for (int sw = 0; sw < sweeps; ++sw) {
-        for (int k = 0; k < 3; ++k) {
-            const int p = (k == 2) ? 1 : 0, q = (k == 0) ? 1 : 2, r = 2 - k;
-            const double apq = a[p][q];
-            if (apq == 0.0) continue;
-            const double app = a[p][p], aqq = a[q][q];
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            const double cc = 1.0 / sqrt(1.0 + t * t), s = t * cc;
-            a[p][p] = app - t * apq;
-            a[q][q] = aqq + t * apq;
-            a[p][q] = a[q][p] = 0.0;
-            const double arp = a[r][p], arq = a[r][q];
-            a[r][p] = a[p][r] = cc * arp - s * arq;
-            a[r][q] = a[q][r] = s * arp + cc * arq;
-            for (int i = 0; i < 3; ++i) {
-                const double vip = v[i][p], viq = v[i][q];
-                v[i][p] = cc * vip - s * viq;
-                v[i][q] = s * vip + cc * viq;
+// 1/sqrt(x) in double from an FP32 estimate and two Newton steps (double
+// division and square root are slow on this part).
+__device__ __forceinline__ double rsqrt_d(double x) {
+    double y = (double)rsqrtf((float)x);
+    y = y * (1.5 - 0.5 * x * y * y);
+    return y * (1.5 - 0.5 * x * y * y);
+}
+
+// Refit (one warp per cluster): total least squares on the inliers.  The
+// covariance A about the centroid is summed in double over the per-item
+// partials.  Its smallest eigenvector is the dominant eigenvector of the
+// adjugate adj(A) (eigenvalues lambda_j lambda_k), so power iteration on adj(A)
+// from the selected RANSAC normal converges by lambda_min / lambda_mid per
+// step; six steps in double, multiplies and adds only.  n_z >= 0,
+// d = -n . centroid; lambda_mid < 10 lambda_min (from the trace, the Rayleigh
+// quotient and x^T adj(A) x = lambda_1 lambda_2) flags the plane ill-conditioned.
+__global__ void k_refit(const uint32_t* __restrict__ item_off, uint32_t k, const float* __restrict__ part,
+                        const double* __restrict__ cen, FitCluster* __restrict__ cl) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warps = gridDim.x * (kT / 32);
+    for (uint32_t c = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); c < k; c += warps) {
+        double A[6] = {0, 0, 0, 0, 0, 0};
+        for (uint32_t it = item_off[c] + lane; it < item_off[c + 1]; it += 32)
+            for (int e = 0; e < 6; ++e) A[e] += part[(size_t)it * 10 + 4 + e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int e = 0; e < 6; ++e) A[e] += __shfl_xor_sync(0xffffffffu, A[e], o);
+        if (lane) continue;
+        FitCluster& f = cl[c];
+        uint32_t flags = 0;
+        float rn[3] = {0.0f, 0.0f, 0.0f}, rd = 0.0f;
+        if (f.best_h >= 0 && f.inliers > 0) {
+            const double a = A[0], b = A[1], cc = A[2], d = A[3], e = A[4], g = A[5];
+            // symmetric adjugate (cofactors) of [[a d e] [d b g] [e g cc]]
+            const double m00 = b * cc - g * g, m11 = a * cc - e * e, m22 = a * b - d * d;
+            const double m01 = e * g - d * cc, m02 = d * g - e * b, m12 = d * e - a * g;
+            double x = f.n[0], y = f.n[1], z = f.n[2];
+            bool ok = true;
+            for (int it = 0; it < 6; ++it) {
+                const double nx = m00 * x + m01 * y + m02 * z;
+                const double ny = m01 * x + m11 * y + m12 * z;
+                const double nz = m02 * x + m12 * y + m22 * z;
+                const double q = nx * nx + ny * ny + nz * nz;
+                if (!(q > 0.0) || !(q < 1e300)) { ok = false; break; }  // rank <= 1: keep the RANSAC normal
+                const double s = rsqrt_d(q);
+                x = nx * s; y = ny * s; z = nz * s;
             }
+            if (!ok) {
+                const double s = rsqrt_d((double)f.n[0] * f.n[0] + (double)f.n[1] * f.n[1] + (double)f.n[2] * f.n[2]);
+                x = f.n[0] * s; y = f.n[1] * s; z = f.n[2] * s;
+                flags |= 1u;
+            }
+            if (z < 0.0 || (z == 0.0 && (y < 0.0 || (y == 0.0 && x < 0.0)))) { x = -x; y = -y; z = -z; }
+            // eigenvalues for the conditioning flag
+            const double lmin = x * (a * x + d * y + e * z) + y * (d * x + b * y + g * z) + z * (e * x + g * y + cc * z);
+            const double p12 = x * (m00 * x + m01 * y + m02 * z) + y * (m01 * x + m11 * y + m12 * z) +
+                               z * (m02 * x + m12 * y + m22 * z);
+            const float S = (float)(a + b + cc - lmin);
+            const float disc = fmaxf(S * S - 4.0f * (float)p12, 0.0f);
+            const float lmax = 0.5f * (S + sqrtf(disc));
+            const float lmid = lmax > 0.0f ? (float)p12 / lmax : 0.0f;  // no cancellation
+            if (!(lmid >= 10.0f * (float)lmin)) flags |= 1u;
+            rn[0] = (float)x; rn[1] = (float)y; rn[2] = (float)z;
+            rd = (float)(-(x * cen[3 * c] + y * cen[3 * c + 1] + z * cen[3 * c + 2]));
         }
+        f.refit_n[0] = rn[0]; f.refit_n[1] = rn[1]; f.refit_n[2] = rn[2];
+        f.refit_d = rd;
+        f.flags = flags;
     }
-    d[0] = a[0][0]; d[1] = a[1][1]; d[2] = a[2][2];
 }
 
 __device__ __forceinline__ unsigned long long xy_key(int2 p) {
@@ -463,14 +517,23 @@ __device__ __forceinline__ int2 key_xy(unsigned long long k) {
     return make_int2((int32_t)((uint32_t)(k >> 32) ^ 0x80000000u), (int32_t)((uint32_t)k ^ 0x80000000u));
 }
 
-// Monotone chain over sorted unique points; one thread builds a chain.
+// Monotone chain over sorted unique points; one thread builds a chain.  The
+// two top entries stay in registers so a pop costs one shared-memory load.
 __device__ int chain(const unsigned long long* P, int u, bool upper, uint32_t* st) {
     int kk = 0;
+    int2 t1 = make_int2(0, 0), t0 = make_int2(0, 0);  // top, second
     for (int s = 0; s < u; ++s) {
         const int i = upper ? (u - 1 - s) : s;
         const int2 p = key_xy(P[i]);
-        while (kk >= 2 && cross3(key_xy(P[st[kk - 2]]), key_xy(P[st[kk - 1]]), p) <= 0) --kk;
-        st[kk++] = (uint32_t)i;
+        while (kk >= 2 && cross3(t0, t1, p) <= 0) {
+            --kk;
+            t1 = t0;
+            if (kk >= 2) t0 = key_xy(P[st[kk - 2]]);
+        }
+        st[kk] = (uint32_t)i;
+        t0 = t1;
+        t1 = p;
+        ++kk;
     }
     return kk;
 }
@@ -487,60 +550,127 @@ __device__ __forceinline__ bool jarvis_better(int2 cur, int2 a, bool a_ok, int2 
     return db > da;
 }
 
-__global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
-                                             uint32_t k, const float* __restrict__ part,
-                                             const double* __restrict__ cen, FitCluster* __restrict__ cl,
-                                             const int2* __restrict__ surv, int2* __restrict__ hull,
-                                             uint32_t* __restrict__ hull_cnt, uint32_t* __restrict__ err) {
+// Directions of the second hull filter: kHullDirs integer vectors
+// (rint(1024 cos), rint(1024 sin)) of multiples of 360/kHullDirs degrees, in
+// counter-clockwise order.  Any closed polygon through input points serves
+// the filter (a point strictly left of every edge has winding number >= 1, so
+// it lies in the convex hull of the polygon's vertices and is not an extreme
+// point); the directions only decide how much it removes.
+constexpr int kHullDirs = 128;
+
+// Per cluster hull of the first filter's survivors: (1) extreme survivors along
+// kHullDirs directions; (2) survivors strictly inside the polygon they span
+// are dropped (none of them can be a hull vertex), the rest gathered in shared
+// memory;
+// (3) bitonic sort by (X, Y), duplicates removed; (4) monotone chain, lower
+// and upper halves built concurrently by two threads.  If more than
+// kHullCap points remain, gift wrapping runs over the survivors instead.
+__global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, uint32_t k,
+                                             const FitCluster* __restrict__ cl, const int2* __restrict__ surv,
+                                             int2* __restrict__ hull, uint32_t* __restrict__ hull_cnt,
+                                             uint32_t* __restrict__ err) {
     extern __shared__ unsigned long long sk[];              // kHullCap keys, then kHullCap unique
     unsigned long long* uq = sk + kHullCap;
     uint32_t* st_lo = reinterpret_cast<uint32_t*>(uq + kHullCap);
     uint32_t* st_hi = st_lo + kHullCap;
+    int2* ssv = reinterpret_cast<int2*>(st_hi + kHullCap);  // kSurvCap staged survivors
     __shared__ uint32_t wsum[kT / 32];
-    __shared__ int s_u, s_klo, s_khi;
+    __shared__ int s_klo, s_khi, s_m, s_cnt;
+    __shared__ int2 poly[kHullDirs + 1];
+    __shared__ int2 sdir[kHullDirs];
     __shared__ int2 jcand[kT];
     __shared__ int jok[kT];
+    __shared__ unsigned long long wmin[kT / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < kHullDirs; j += kT) {
+        const float t = (float)j * (2.0f / kHullDirs);
+        sdir[j] = make_int2(__float2int_rn(1024.0f * cospif(t)), __float2int_rn(1024.0f * sinpif(t)));
+    }
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
         __syncthreads();
-        const FitCluster f = cl[c];
         const uint32_t base = off[c];
-        if (threadIdx.x == 0) {
-            // refit: total least squares on the inliers, covariance summed in double
-            uint32_t flags = 0;
-            float rn[3] = {0.0f, 0.0f, 0.0f}, rd = 0.0f;
-            if (f.best_h >= 0 && f.inliers > 0) {
-                double A[6] = {0, 0, 0, 0, 0, 0};
-                for (uint32_t it = item_off[c]; it < item_off[c + 1]; ++it)
-                    for (int e = 0; e < 6; ++e) A[e] += part[(size_t)it * 10 + 4 + e];
-                double V[3][3], D[3];
-                jacobi3_d(A, 10, V, D);
-                int m = 0;
-                if (D[1] < D[m]) m = 1;
-                if (D[2] < D[m]) m = 2;
-                double x = V[0][m], y = V[1][m], z = V[2][m];
-                const double l = sqrt(x * x + y * y + z * z);
-                x /= l; y /= l; z /= l;
-                if (z < 0.0 || (z == 0.0 && (y < 0.0 || (y == 0.0 && x < 0.0)))) { x = -x; y = -y; z = -z; }
-                double e0 = D[0], e1 = D[1], e2 = D[2], t;
-                if (e1 < e0) { t = e0; e0 = e1; e1 = t; }
-                if (e2 < e1) { t = e1; e1 = e2; e2 = t; }
-                if (e1 < e0) { t = e0; e0 = e1; e1 = t; }
-                if (!(e1 >= 10.0 * e0)) flags |= 1u;
-                rn[0] = (float)x; rn[1] = (float)y; rn[2] = (float)z;
-                rd = (float)(-(x * cen[3 * c] + y * cen[3 * c + 1] + z * cen[3 * c + 2]));
-            }
-            cl[c].refit_n[0] = rn[0]; cl[c].refit_n[1] = rn[1]; cl[c].refit_n[2] = rn[2];
-            cl[c].refit_d = rd;
-            cl[c].flags = flags;
-        }
-        const int s = (int)f.n_surv;
+        const int s = (int)cl[c].n_surv;
         int2* out = hull + base;
-        if (s <= kHullCap) {
-            int n2 = 1;
-            while (n2 < s) n2 <<= 1;
-            for (int i = threadIdx.x; i < n2; i += kT) sk[i] = (i < s) ? xy_key(surv[base + i]) : ~0ull;
+        if (threadIdx.x == 0) s_cnt = 0;
+        // stage the survivors (when they fit) so the scans below read shared memory
+        const int2* sv = surv + base;
+        if (s <= kSurvCap) {
+            for (int i = threadIdx.x; i < s; i += kT) ssv[i] = sv[i];
+            sv = ssv;
             __syncthreads();
-            // bitonic sort, ascending
+        }
+        // (1) extreme points along kHullDirs directions: warp w takes 16 of them
+        {
+            constexpr int kPer = kHullDirs / (kT / 32);
+            long long bv[kPer];
+            int bi[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) { bv[q] = LLONG_MIN; bi[q] = -1; }
+            for (int i = lane; i < s; i += 32) {
+                const int2 p = sv[i];
+#pragma unroll
+                for (int q = 0; q < kPer; ++q) {
+                    const int2 dv = sdir[kPer * w + q];
+                    const long long v = (long long)dv.x * p.x + (long long)dv.y * p.y;
+                    if (v > bv[q]) { bv[q] = v; bi[q] = i; }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const long long ov = __shfl_xor_sync(0xffffffffu, bv[q], o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
+                    if (ov > bv[q] || (ov == bv[q] && oi < bi[q])) { bv[q] = ov; bi[q] = oi; }
+                }
+                if (lane == 0) poly[kPer * w + q] = (bi[q] >= 0) ? sv[bi[q]] : make_int2(INT_MIN, INT_MIN);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {  // polygon through the extremes, consecutive duplicates removed
+            int m = 0;
+            for (int j = 0; j < kHullDirs; ++j) {
+                const int2 p = poly[j];
+                if (p.x == INT_MIN && p.y == INT_MIN) continue;
+                if (m && poly[m - 1].x == p.x && poly[m - 1].y == p.y) continue;
+                poly[m++] = p;
+            }
+            if (m > 1 && poly[m - 1].x == poly[0].x && poly[m - 1].y == poly[0].y) --m;
+            long long area2 = 0;
+            for (int i = 0; i < m; ++i) {
+                const int2 a = poly[i], b = poly[(i + 1) % m];
+                area2 += (long long)a.x * b.y - (long long)a.y * b.x;
+            }
+            s_m = (m >= 3 && area2 > 0) ? m : 0;
+        }
+        __syncthreads();
+        const int m = s_m;
+        // (2) drop survivors strictly inside the polygon
+        for (int i0 = 0; i0 < s; i0 += kT) {
+            const int i = i0 + threadIdx.x;
+            bool keep = false;
+            int2 p = make_int2(0, 0);
+            if (i < s) {
+                p = sv[i];
+                keep = (m == 0);
+                for (int e = 0; e < m; ++e) {
+                    if (cross3(poly[e], poly[e + 1 < m ? e + 1 : 0], p) <= 0) { keep = true; break; }
+                }
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, keep);
+            int pos = 0;
+            if (lane == 0 && b) pos = atomicAdd(&s_cnt, __popc(b));
+            pos = __shfl_sync(0xffffffffu, pos, 0) + __popc(b & ((1u << lane) - 1u));
+            if (keep && pos < kHullCap) sk[pos] = xy_key(p);
+        }
+        __syncthreads();
+        const int s2 = s_cnt;
+        if (s2 <= kHullCap) {
+            int n2 = 1;
+            while (n2 < s2) n2 <<= 1;
+            for (int i = s2 + threadIdx.x; i < n2; i += kT) sk[i] = ~0ull;
+            __syncthreads();
+            // (3) bitonic sort, ascending
             for (int size = 2; size <= n2; size <<= 1) {
                 for (int stride = size >> 1; stride > 0; stride >>= 1) {
                     for (int i = threadIdx.x; i < n2; i += kT) {
@@ -554,28 +684,29 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
                     __syncthreads();
                 }
             }
-            // unique (order-preserving compaction by a block scan in chunks)
+            // unique, order-preserving (block scan in chunks)
             int u = 0;
-            for (int c0 = 0; c0 < s; c0 += kT) {
+            for (int c0 = 0; c0 < s2; c0 += kT) {
                 const int i = c0 + threadIdx.x;
-                const uint32_t fl = (i < s) && (i == 0 || sk[i] != sk[i - 1]);
+                const uint32_t fl = (i < s2) && (i == 0 || sk[i] != sk[i - 1]);
                 uint32_t inc = fl;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-                    if ((threadIdx.x & 31) >= o) inc += t;
+                    if (lane >= o) inc += t;
                 }
-                if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = inc;
+                if (lane == 31) wsum[w] = inc;
                 __syncthreads();
                 uint32_t wpre = 0, tot = 0;
-                for (int w = 0; w < kT / 32; ++w) {
-                    if (w < (int)(threadIdx.x >> 5)) wpre += wsum[w];
-                    tot += wsum[w];
+                for (int q = 0; q < kT / 32; ++q) {
+                    if (q < w) wpre += wsum[q];
+                    tot += wsum[q];
                 }
                 if (fl) uq[u + wpre + inc - 1] = sk[i];
                 u += (int)tot;
                 __syncthreads();
             }
+            // (4) monotone chain
             if (u < 3) {
                 for (int i = threadIdx.x; i < u; i += kT) out[i] = key_xy(uq[i]);
                 if (threadIdx.x == 0) hull_cnt[c] = (uint32_t)u;
@@ -589,24 +720,21 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
                 if (threadIdx.x == 0) hull_cnt[c] = (uint32_t)(klo + khi);
             }
         } else {
-            // gift wrapping over the survivors in global memory
-            int2 best = make_int2(INT_MAX, INT_MAX);
+            // gift wrapping over all survivors in global memory
             unsigned long long bk = ~0ull;
             for (int i = threadIdx.x; i < s; i += kT) {
-                const unsigned long long key = xy_key(surv[base + i]);
+                const unsigned long long key = xy_key(sv[i]);
                 bk = key < bk ? key : bk;
             }
-            // block min
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const unsigned long long t = __shfl_xor_sync(0xffffffffu, bk, o);
                 bk = t < bk ? t : bk;
             }
-            __shared__ unsigned long long wmin[kT / 32];
-            if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = bk;
+            if (lane == 0) wmin[w] = bk;
             __syncthreads();
             if (threadIdx.x == 0) {
-                for (int w = 1; w < kT / 32; ++w) bk = wmin[w] < bk ? wmin[w] : bk;
+                for (int q = 1; q < kT / 32; ++q) bk = wmin[q] < bk ? wmin[q] : bk;
                 wmin[0] = bk;
             }
             __syncthreads();
@@ -619,16 +747,16 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
                 int2 cand = make_int2(0, 0);
                 bool ok = false;
                 for (int i = threadIdx.x; i < s; i += kT) {
-                    const int2 p = surv[base + i];
+                    const int2 p = sv[i];
                     const bool pok = !(p.x == cur.x && p.y == cur.y);
                     if (jarvis_better(cur, cand, ok, p, pok)) { cand = p; ok = true; }
                 }
                 jcand[threadIdx.x] = cand;
                 jok[threadIdx.x] = ok;
                 __syncthreads();
-                for (int w = kT / 2; w > 0; w >>= 1) {
-                    if ((int)threadIdx.x < w) {
-                        const int o = threadIdx.x + w;
+                for (int r = kT / 2; r > 0; r >>= 1) {
+                    if ((int)threadIdx.x < r) {
+                        const int o = threadIdx.x + r;
                         if (jarvis_better(cur, jcand[threadIdx.x], jok[threadIdx.x], jcand[o], jok[o])) {
                             jcand[threadIdx.x] = jcand[o];
                             jok[threadIdx.x] = 1;
@@ -647,7 +775,6 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
                 if (threadIdx.x == 0) out[h] = nxt;
                 ++h;
                 cur = nxt;
-                if (guard == s && threadIdx.x == 0) atomicOr(err, kErrTimeout);
             }
             if (threadIdx.x == 0) hull_cnt[c] = (uint32_t)h;
         }
@@ -721,7 +848,9 @@ cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* 
 
 FitTuning default_tuning() { return FitTuning{2048, 4, 4}; }
 
-size_t fit_hull_smem() { return (size_t)kHullCap * (2 * sizeof(unsigned long long) + 2 * sizeof(uint32_t)); }
+size_t fit_hull_smem() {
+    return (size_t)kHullCap * (2 * sizeof(unsigned long long) + 2 * sizeof(uint32_t)) + (size_t)kSurvCap * sizeof(int2);
+}
 
 cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, uint32_t k, uint32_t npts,
                        const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int sms, cudaStream_t s,
@@ -758,8 +887,9 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_BEGIN(hk, kStExtract, s);
     k_select<<<cgrid, kT, 0, s>>>(pts, off, k, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
     const unsigned igrid = (unsigned)sms * 8;
-    k_extract<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, k, T, fb.cl, fb.inlier, fb.part, p.eps);
-    k_centroid<<<(k + kT - 1) / kT, kT, 0, s>>>(fb.item_off, k, fb.part, fb.cl, fb.cen);
+    k_extract<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, k, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
+    const unsigned wgrid = (k + kT / 32 - 1) / (kT / 32);
+    k_centroid<<<wgrid, kT, 0, s>>>(fb.item_off, k, fb.part, fb.cl, fb.cen);
     k_filter<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, k, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
     VM_STAGE_END(hk, kStExtract, s);
     count_launch(4);
@@ -769,12 +899,12 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
         cudaFuncSetAttribute(k_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_hull_smem());
         hull_attr = true;
     }
-    k_hull<<<cgrid, kT, fit_hull_smem(), s>>>(off, fb.item_off, k, fb.part, fb.cen, fb.cl, fb.surv, fb.hull,
-                                             fb.hull_cnt, fb.err);
+    k_refit<<<wgrid, kT, 0, s>>>(fb.item_off, k, fb.part, fb.cen, fb.cl);
+    k_hull<<<cgrid, kT, fit_hull_smem(), s>>>(off, k, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
     e = exclusive_scan_u32(fb.hull_cnt, fb.hull_cnt, fb.hull_cnt + k, k, fb.scan_tmp, s);
     if (e != cudaSuccess) return e;
     VM_STAGE_END(hk, kStHull, s);
-    count_launch(1);
+    count_launch(2);
     return cudaGetLastError();
 }
 

@@ -172,75 +172,9 @@ __device__ __forceinline__ int32_t halo_index(int c, const int32_t* nb) {
     return rk * kBrickVox + ((lz * 8 + ly) * 8 + lx);
 }
 
-// Eq. 3 / Eq. 4: covariance of the 3x3x3 window of mean positions (self
-// included) as an exact integer matrix N' sum(dd^T) - (sum d)(sum d)^T of
-// offsets d = M_j - M_i, rounded to FP32; normal by Jacobi (6 sweeps);
-// steppable iff N >= n_th and |n_z| >= cos_step.
-__global__ void __launch_bounds__(512) k_normals(uint32_t n_sorted, Grid g, const int32_t* __restrict__ sorted_key,
-                                                 const int32_t* __restrict__ rank_table,
-                                                 const int32_t* __restrict__ M, float* __restrict__ nrm,
-                                                 uint8_t* __restrict__ status, uint8_t* __restrict__ nbr,
-                                                 size_t stride, uint32_t n_th, float cos_step) {
-    __shared__ int32_t sM[3][1000];
-    __shared__ int32_t nb[27];
-    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
-        __syncthreads();
-        load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
-        __syncthreads();
-        for (int c = threadIdx.x; c < 1000; c += 512) {
-            const int32_t idx = halo_index(c, nb);
-            if (idx >= 0) {
-                sM[0][c] = M[idx];
-                sM[1][c] = M[stride + idx];
-                sM[2][c] = M[2 * stride + idx];
-            } else {
-                sM[0][c] = INT_MIN;
-            }
-        }
-        __syncthreads();
-        const int l = threadIdx.x;
-        const int c0 = (((l >> 6) + 1) * 10 + ((l >> 3) & 7) + 1) * 10 + (l & 7) + 1;
-        const int32_t m0 = sM[0][c0], m1 = sM[1][c0], m2 = sM[2][c0];
-        if (m0 == INT_MIN) continue;
-        int32_t s1x = 0, s1y = 0, s1z = 0;
-        long long sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
-        int cnt = 0;
-#pragma unroll
-        for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-            for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int c = c0 + dz * 100 + dy * 10 + dx;
-                    const int32_t a0 = sM[0][c];
-                    if (a0 == INT_MIN) continue;
-                    const int32_t ex = a0 - m0, ey = sM[1][c] - m1, ez = sM[2][c] - m2;
-                    s1x += ex; s1y += ey; s1z += ez;
-                    sxx += (long long)ex * ex; syy += (long long)ey * ey; szz += (long long)ez * ez;
-                    sxy += (long long)ex * ey; sxz += (long long)ex * ez; syz += (long long)ey * ez;
-                    ++cnt;
-                }
-        const long long N = cnt;
-        const float A00 = __ll2float_rn(N * sxx - (long long)s1x * s1x);
-        const float A11 = __ll2float_rn(N * syy - (long long)s1y * s1y);
-        const float A22 = __ll2float_rn(N * szz - (long long)s1z * s1z);
-        const float A01 = __ll2float_rn(N * sxy - (long long)s1x * s1y);
-        const float A02 = __ll2float_rn(N * sxz - (long long)s1x * s1z);
-        const float A12 = __ll2float_rn(N * syz - (long long)s1y * s1z);
-        float v[3][3], d[3], n[3];
-        jacobi3(A00, A11, A22, A01, A02, A12, 6, v, d);
-        pick_normal(v, d, n);
-        const size_t o = (size_t)r * kBrickVox + l;
-        nrm[o] = n[0];
-        nrm[stride + o] = n[1];
-        nrm[2 * stride + o] = n[2];
-        const uint32_t N_nb = (uint32_t)(cnt - 1);
-        nbr[o] = (uint8_t)N_nb;
-        status[o] = (N_nb >= n_th && fabsf(n[2]) >= cos_step) ? 2 : 1;
-    }
-}
-
 // ---------------------------------------------------------------- union-find
+// Global forest over rank-dense indices.  Hooking always puts the larger root
+// under the smaller, so every root is the smallest index of its tree.
 __device__ __forceinline__ uint32_t uf_find(uint32_t* P, uint32_t x, uint32_t* err) {
     for (int it = 0; it < kLoopCap; ++it) {
         const uint32_t p = __ldcg(P + x);
@@ -253,8 +187,6 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t* P, uint32_t x, uint32_t* e
     return x;
 }
 
-// Hook the larger root under the smaller, so every root is the smallest index
-// of its tree.
 __device__ __forceinline__ void uf_union(uint32_t* P, uint32_t a, uint32_t b, uint32_t* err) {
     for (int it = 0; it < kLoopCap; ++it) {
         a = uf_find(P, a, err);
@@ -269,74 +201,238 @@ __device__ __forceinline__ void uf_union(uint32_t* P, uint32_t a, uint32_t b, ui
     atomicOr(err, kErrTimeout);
 }
 
-__global__ void k_ccl_init(size_t nv, const uint8_t* __restrict__ status, uint32_t* __restrict__ parent,
-                           uint32_t* __restrict__ count, uint8_t want) {
-    for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
-        parent[i] = (status[i] >= want) ? (uint32_t)i : kNone;
-        count[i] = 0;
+// The same forest in shared memory, over the 512 voxels of one brick.
+__device__ __forceinline__ uint32_t lf_find(volatile uint32_t* P, uint32_t x) {
+    for (int it = 0; it < 1024; ++it) {
+        const uint32_t p = P[x];
+        if (p == x) return x;
+        const uint32_t gp = P[p];
+        if (gp != p) P[x] = gp;
+        x = gp;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void lf_union(uint32_t* P, uint32_t a, uint32_t b, uint32_t* err) {
+    for (int it = 0; it < 4096; ++it) {
+        a = lf_find(P, a);
+        b = lf_find(P, b);
+        if (a == b) return;
+        const uint32_t hi = a > b ? a : b, lo = a > b ? b : a;
+        const uint32_t old = atomicCAS(P + hi, hi, lo);
+        if (old == hi) return;
+        a = old;
+        b = lo;
+    }
+    atomicOr(err, kErrTimeout);
+}
+
+// Algorithm 1's edge test: |mu_i - mu_j|^2 < d_th^2 and |n_i . n_j| > cos_ccl
+// (symmetric in i and j).
+__device__ __forceinline__ bool ccl_edge(float ax, float ay, float az, float anx, float any, float anz, float bx,
+                                         float by, float bz, float bnx, float bny, float bnz, float d_th2,
+                                         float cos_ccl) {
+    const float ex = __fsub_rn(ax, bx), ey = __fsub_rn(ay, by), ez = __fsub_rn(az, bz);
+    const float d2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
+    const float cs = __fmaf_rn(anz, bnz, __fmaf_rn(any, bny, __fmul_rn(anx, bnx)));
+    return d2 < d_th2 && fabsf(cs) > cos_ccl;
+}
+
+__device__ __forceinline__ float mean_pos(float o, int32_t m) {
+    return __fadd_rn(o, __fmul_rn(__int2float_rn(m), kInvQ));
+}
+
+// Forward neighbour k of 13: (dz, dy, dx) lexicographically after (0, 0, 0).
+__device__ __forceinline__ void fwd_offset(int k, int& dz, int& dy, int& dx) {
+    dz = (k < 9) ? 1 : 0;
+    dy = (k < 9) ? (k / 3 - 1) : ((k < 12) ? 1 : 0);
+    dx = (k < 9) ? (k % 3 - 1) : ((k < 12) ? (k - 9 - 1) : 1);
+}
+
+// Eq. 3 / Eq. 4 and the intra-brick half of Algorithm 1, one 128-thread CTA
+// per brick.  The brick and a one-voxel halo of integer means are staged in
+// shared memory; the brick's occupied voxels are compacted into a list so
+// their work is spread over all four warps.
+// Normals: covariance of the 3x3x3 window of mean positions (self included)
+// as the exact integer matrix N' sum(dd^T) - (sum d)(sum d)^T of offsets
+// d = M_j - M_i, rounded to FP32; normal by Jacobi (6 sweeps); steppable iff
+// N >= n_th and |n_z| >= cos_step.  Clustering: the brick's vertices are
+// joined over edges inside the brick with a union-find in shared memory; the
+// global parent of each vertex is set to its local root (the smallest index of
+// its in-brick component).  Edges that leave the brick follow in k_ccl_cross.
+constexpr int kNormT = 128;
+__global__ void __launch_bounds__(kNormT) k_normals(uint32_t n_sorted, Grid g, const int32_t* __restrict__ sorted_key,
+                                                    const int32_t* __restrict__ rank_table,
+                                                    const int32_t* __restrict__ M, float* __restrict__ nrm,
+                                                    uint8_t* __restrict__ status, uint8_t* __restrict__ nbr,
+                                                    uint32_t* __restrict__ parent, uint32_t* __restrict__ count,
+                                                    float4* __restrict__ rec, size_t stride, uint32_t n_th,
+                                                    float cos_step, uint8_t want, float d_th2, float cos_ccl,
+                                                    uint32_t* err) {
+    __shared__ int32_t sM[3][1000];
+    __shared__ float sMu[3][512];
+    __shared__ float sN[3][512];
+    __shared__ uint32_t lpar[512];
+    __shared__ uint16_t list[512];
+    __shared__ uint8_t sSt[512];
+    __shared__ int32_t nb[27];
+    __shared__ int n_list;
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) n_list = 0;
+        load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
+        __syncthreads();
+        for (int c = threadIdx.x; c < 1000; c += kNormT) {
+            const int32_t idx = halo_index(c, nb);
+            if (idx >= 0) {
+                sM[0][c] = M[idx];
+                sM[1][c] = M[stride + idx];
+                sM[2][c] = M[2 * stride + idx];
+            } else {
+                sM[0][c] = INT_MIN;
+            }
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
+            const int c0 = (((l >> 6) + 1) * 10 + ((l >> 3) & 7) + 1) * 10 + (l & 7) + 1;
+            sSt[l] = 0;
+            if (sM[0][c0] != INT_MIN) list[atomicAdd(&n_list, 1)] = (uint16_t)l;
+        }
+        __syncthreads();
+        const int nl = n_list;
+        for (int q = threadIdx.x; q < nl; q += kNormT) {
+            const int l = list[q];
+            const int c0 = (((l >> 6) + 1) * 10 + ((l >> 3) & 7) + 1) * 10 + (l & 7) + 1;
+            const int32_t m0 = sM[0][c0], m1 = sM[1][c0], m2 = sM[2][c0];
+            int32_t s1x = 0, s1y = 0, s1z = 0;
+            long long sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+            int cnt = 0;
+#pragma unroll
+            for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int c = c0 + dz * 100 + dy * 10 + dx;
+                        const int32_t a0 = sM[0][c];
+                        if (a0 == INT_MIN) continue;
+                        const int32_t ex = a0 - m0, ey = sM[1][c] - m1, ez = sM[2][c] - m2;
+                        s1x += ex; s1y += ey; s1z += ez;
+                        sxx += (long long)ex * ex; syy += (long long)ey * ey; szz += (long long)ez * ez;
+                        sxy += (long long)ex * ey; sxz += (long long)ex * ez; syz += (long long)ey * ez;
+                        ++cnt;
+                    }
+            const long long N = cnt;
+            const float A00 = __ll2float_rn(N * sxx - (long long)s1x * s1x);
+            const float A11 = __ll2float_rn(N * syy - (long long)s1y * s1y);
+            const float A22 = __ll2float_rn(N * szz - (long long)s1z * s1z);
+            const float A01 = __ll2float_rn(N * sxy - (long long)s1x * s1y);
+            const float A02 = __ll2float_rn(N * sxz - (long long)s1x * s1z);
+            const float A12 = __ll2float_rn(N * syz - (long long)s1y * s1z);
+            float v[3][3], d[3], n[3];
+            jacobi3(A00, A11, A22, A01, A02, A12, 6, v, d);
+            pick_normal(v, d, n);
+            const size_t o = (size_t)r * kBrickVox + l;
+            nrm[o] = n[0];
+            nrm[stride + o] = n[1];
+            nrm[2 * stride + o] = n[2];
+            const uint32_t N_nb = (uint32_t)(cnt - 1);
+            nbr[o] = (uint8_t)N_nb;
+            const uint8_t st = (N_nb >= n_th && fabsf(n[2]) >= cos_step) ? 2 : 1;
+            status[o] = st;
+            sSt[l] = st;
+            const float mx = mean_pos(g.ox, m0), my = mean_pos(g.oy, m1), mz = mean_pos(g.oz, m2);
+            sMu[0][l] = mx; sMu[1][l] = my; sMu[2][l] = mz;
+            sN[0][l] = n[0]; sN[1][l] = n[1]; sN[2][l] = n[2];
+            rec[o] = make_float4(mx, my, mz, __int_as_float((int)st));
+            rec[stride + o] = make_float4(n[0], n[1], n[2], 0.0f);
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) lpar[l] = (sSt[l] >= want) ? (uint32_t)l : kNone;
+        __syncthreads();
+        for (int q = threadIdx.x; q < nl; q += kNormT) {
+            const int l = list[q];
+            if (sSt[l] < want) continue;
+            const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+#pragma unroll
+            for (int k = 0; k < 13; ++k) {
+                int dz, dy, dx;
+                fwd_offset(k, dz, dy, dx);
+                const int x = lx + dx, y = ly + dy, z = lz + dz;
+                if (x < 0 || x > 7 || y < 0 || y > 7 || z > 7) continue;
+                const int j = (z * 8 + y) * 8 + x;
+                if (sSt[j] < want) continue;
+                if (ccl_edge(sMu[0][l], sMu[1][l], sMu[2][l], sN[0][l], sN[1][l], sN[2][l], sMu[0][j], sMu[1][j],
+                             sMu[2][j], sN[0][j], sN[1][j], sN[2][j], d_th2, cos_ccl))
+                    lf_union(lpar, (uint32_t)l, (uint32_t)j, err);
+            }
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
+            const size_t o = (size_t)r * kBrickVox + l;
+            uint32_t root = kNone;
+            if (sSt[l] >= want) {  // read-only walk: entries are final once every union is done
+                uint32_t x = (uint32_t)l;
+                for (int it = 0; it < 1024; ++it) {
+                    const uint32_t p = lpar[x];
+                    if (p == x) break;
+                    x = p;
+                }
+                root = (uint32_t)r * kBrickVox + x;
+            }
+            parent[o] = root;
+            count[o] = 0;
+            if (sSt[l] == 0) rec[o] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
+        }
     }
 }
 
-// Algorithm 1's adjacency: two vertices that are 26-neighbours are joined
-// iff |mu_i - mu_j|^2 < d_th^2 and |n_i . n_j| > cos_ccl.  Each vertex tests
-// its 13 forward neighbours; the test is symmetric.
-__global__ void __launch_bounds__(512) k_ccl_link(uint32_t n_sorted, Grid g, const int32_t* __restrict__ sorted_key,
-                                                  const int32_t* __restrict__ rank_table,
-                                                  const int32_t* __restrict__ M, const float* __restrict__ nrm,
-                                                  const uint8_t* __restrict__ status, uint32_t* parent, size_t stride,
-                                                  uint8_t want, float d_th2, float cos_ccl, uint32_t* err) {
-    __shared__ float sMu[3][1000];
-    __shared__ float sN[3][1000];
-    __shared__ int32_t sIdx[1000];
-    __shared__ int32_t nb[27];
-    __shared__ int any_vertex;
-    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
-        __syncthreads();
-        if (threadIdx.x == 0) any_vertex = 0;
-        load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
-        __syncthreads();
-        // warp vote: skip bricks without a vertex
-        {
-            const size_t o = (size_t)r * kBrickVox + threadIdx.x;
-            const bool v = status[o] >= want;
-            if (__any_sync(0xffffffffu, v) && (threadIdx.x & 31) == 0) any_vertex = 1;
+// The inter-brick half of Algorithm 1, one warp per brick: a vertex whose
+// forward neighbours can lie in another brick tests those neighbours and joins
+// the global forest over the edges that pass.  Forward offsets have dz in
+// {0, 1}, dy in {-1, 0, 1} (-1 only with dz = 1) and dx in {-1, 0, 1}, so they
+// leave the brick through the +z face, either y face or either x face.
+__global__ void __launch_bounds__(256) k_ccl_cross(uint32_t n_sorted, Grid g, const int32_t* __restrict__ sorted_key,
+                                                   const int32_t* __restrict__ rank_table,
+                                                   const float4* __restrict__ rec, uint32_t* parent, size_t stride,
+                                                   uint8_t want, float d_th2, float cos_ccl, uint32_t* err) {
+    __shared__ int32_t nbs[8][27];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t* nb = nbs[w];
+    const uint32_t warps = gridDim.x * 8;
+    for (uint32_t r = blockIdx.x * 8 + w; r < n_sorted; r += warps) {
+        __syncwarp();
+        if (lane < 27) {
+            int bx, by, bz;
+            brick_coords(sorted_key[r], g, bx, by, bz);
+            const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+            const int x = bx + dx, y = by + dy, z = bz + dz;
+            nb[lane] = (x >= 0 && y >= 0 && z >= 0 && x < g.nbx && y < g.nby && z < g.nbz)
+                           ? rank_table[(z * g.nby + y) * g.nbx + x] : -1;
         }
-        __syncthreads();
-        if (!any_vertex) continue;
-        for (int c = threadIdx.x; c < 1000; c += 512) {
-            int32_t idx = halo_index(c, nb);
-            if (idx >= 0 && status[idx] >= want) {
-                sMu[0][c] = __fadd_rn(g.ox, __fmul_rn(__int2float_rn(M[idx]), kInvQ));
-                sMu[1][c] = __fadd_rn(g.oy, __fmul_rn(__int2float_rn(M[stride + idx]), kInvQ));
-                sMu[2][c] = __fadd_rn(g.oz, __fmul_rn(__int2float_rn(M[2 * stride + idx]), kInvQ));
-                sN[0][c] = nrm[idx];
-                sN[1][c] = nrm[stride + idx];
-                sN[2][c] = nrm[2 * stride + idx];
-            } else {
-                idx = -1;
+        __syncwarp();
+        for (int l = lane; l < kBrickVox; l += 32) {
+            const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+            if (!((lx == 0) | (lx == 7) | (ly == 0) | (ly == 7) | (lz == 7))) continue;
+            const size_t o = (size_t)r * kBrickVox + l;
+            const float4 a = rec[o];
+            if (__float_as_int(a.w) < want) continue;
+            const float4 an = rec[stride + o];
+            for (int k = 0; k < 13; ++k) {
+                int dz, dy, dx;
+                fwd_offset(k, dz, dy, dx);
+                const int x = lx + dx, y = ly + dy, z = lz + dz;
+                if (x >= 0 && x <= 7 && y >= 0 && y <= 7 && z <= 7) continue;  // inside the brick: done already
+                const int bdx = x < 0 ? -1 : (x > 7 ? 1 : 0), bdy = y < 0 ? -1 : (y > 7 ? 1 : 0), bdz = z > 7 ? 1 : 0;
+                const int32_t rk = nb[(bdz + 1) * 9 + (bdy + 1) * 3 + (bdx + 1)];
+                if (rk < 0) continue;
+                const size_t j = (size_t)rk * kBrickVox + (((z - 8 * bdz) * 8 + (y - 8 * bdy)) * 8 + (x - 8 * bdx));
+                const float4 b = rec[j];
+                if (__float_as_int(b.w) < want) continue;
+                const float4 bn = rec[stride + j];
+                if (ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
+                    uf_union(parent, (uint32_t)o, (uint32_t)j, err);
             }
-            sIdx[c] = idx;
-        }
-        __syncthreads();
-        const int l = threadIdx.x;
-        const int c0 = (((l >> 6) + 1) * 10 + ((l >> 3) & 7) + 1) * 10 + (l & 7) + 1;
-        const int32_t me = sIdx[c0];
-        if (me < 0) continue;
-        const float mx = sMu[0][c0], my = sMu[1][c0], mz = sMu[2][c0];
-        const float nx = sN[0][c0], ny = sN[1][c0], nz = sN[2][c0];
-#pragma unroll
-        for (int k = 0; k < 13; ++k) {
-            // forward offsets: (dz, dy, dx) lexicographically after (0, 0, 0)
-            const int dz = (k < 9) ? 1 : 0;
-            const int dy = (k < 9) ? (k / 3 - 1) : ((k < 12) ? 1 : 0);
-            const int dx = (k < 9) ? (k % 3 - 1) : ((k < 12) ? (k - 9 - 1) : 1);
-            const int c = c0 + dz * 100 + dy * 10 + dx;
-            const int32_t j = sIdx[c];
-            if (j < 0) continue;
-            const float ex = __fsub_rn(mx, sMu[0][c]), ey = __fsub_rn(my, sMu[1][c]), ez = __fsub_rn(mz, sMu[2][c]);
-            const float d2 = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
-            const float cs = __fmaf_rn(nz, sN[2][c], __fmaf_rn(ny, sN[1][c], __fmul_rn(nx, sN[0][c])));
-            if (d2 < d_th2 && fabsf(cs) > cos_ccl) uf_union(parent, (uint32_t)me, (uint32_t)j, err);
         }
     }
 }
@@ -457,18 +553,20 @@ cudaError_t seg_voxels(const Grid& g, uint32_t n_sorted, const unsigned long lon
     VM_STAGE_BEGIN(hk, kStFinalize, s);
     k_finalize<<<bricks_grid, kT, 0, s>>>(n_sorted, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
     VM_STAGE_END(hk, kStFinalize, s);
-    VM_STAGE_BEGIN(hk, kStNormals, s);
-    k_normals<<<bricks_grid, 512, 0, s>>>(n_sorted, g, b.sorted_key, b.rank_table, b.M, b.nrm, b.status, b.nbr,
-                                          stride, p.n_th, p.cos_step);
-    VM_STAGE_END(hk, kStNormals, s);
     const uint8_t want = p.classify ? 2 : 1;
+    VM_STAGE_BEGIN(hk, kStNormals, s);
+    const unsigned norm_grid = (unsigned)(n_sorted < (uint32_t)sms * 8 ? n_sorted : (uint32_t)sms * 8);
+    k_normals<<<norm_grid, kNormT, 0, s>>>(n_sorted, g, b.sorted_key, b.rank_table, b.M, b.nrm, b.status, b.nbr,
+                                          b.parent, b.count, b.rec, stride, p.n_th, p.cos_step, want, p.d_th2,
+                                          p.cos_ccl, err);
+    VM_STAGE_END(hk, kStNormals, s);
     VM_STAGE_BEGIN(hk, kStCcl, s);
-    k_ccl_init<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.status, b.parent, b.count, want);
-    k_ccl_link<<<bricks_grid, 512, 0, s>>>(n_sorted, g, b.sorted_key, b.rank_table, b.M, b.nrm, b.status, b.parent,
-                                           stride, want, p.d_th2, p.cos_ccl, err);
+    const unsigned cross_grid = (unsigned)((n_sorted + 7) / 8 < (uint32_t)sms * 8 ? (n_sorted + 7) / 8 : (uint32_t)sms * 8);
+    k_ccl_cross<<<cross_grid, 256, 0, s>>>(n_sorted, g, b.sorted_key, b.rank_table, b.rec, b.parent, stride, want,
+                                            p.d_th2, p.cos_ccl, err);
     k_ccl_compress<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, err);
     VM_STAGE_END(hk, kStCcl, s);
-    count_launch(5);
+    count_launch(4);
     VM_STAGE_BEGIN(hk, kStClusters, s);
     k_count<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, b.count, b.ctr);
     const uint32_t min_cl = p.min_cluster ? p.min_cluster : 1u;

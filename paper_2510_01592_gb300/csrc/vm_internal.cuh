@@ -77,7 +77,7 @@ struct FitCluster {
     uint32_t flags;
     float refit_n[3];
     float refit_d;
-    unsigned long long ext[8];  // octagon extremes: (biased value << 32) | point index
+    unsigned long long ext[16]; // filter extremes: (biased value << 32) | point index
 };
 
 // ---------------------------------------------------------------- diagnostics
@@ -167,6 +167,7 @@ struct SegBuffers {
     float* nrm;             // [3][nv]
     uint8_t* status;        // [nv]     0 free, 1 occupied, 2 steppable
     uint8_t* nbr;           // [nv]     occupied neighbours N
+    float4* rec;            // [2][nv]  packed (mu, status bits) and (normal, 0) per voxel
     uint32_t* parent;       // [nv]     union-find parent, kNone when not a vertex
     uint32_t* count;        // [nv]     component sizes at roots
     uint32_t* cid;          // [nv + 1] kept-root flags -> cluster index (scan)

@@ -188,3 +188,20 @@ def test_fit_planes_hull_beyond_shared_memory(orc, vmmod):
     gres = vmmod.fit_planes(torch.from_numpy(pts).cuda(), torch.from_numpy(off).cuda(), gp)
     compare_planes(gres, ores)
     assert gres["planes"]["hull_count"][0] > 50
+
+
+def test_fit_planes_hull_gift_wrapping_path(orc, vmmod):
+    """Points on a circle all lie on the hull boundary, so more candidates than
+    the shared-memory sort holds survive both filters and the gift-wrapping
+    pass runs; it must give the monotone chain's hull."""
+    import torch
+    rng = np.random.default_rng(8)
+    n = 6000
+    a = np.sort(rng.uniform(0, 2 * math.pi, n))
+    pts = np.stack([0.8 * np.cos(a) + 1.0, 0.8 * np.sin(a) - 0.5, np.full(n, 0.25)], 1).astype(np.float32)
+    off = np.array([0, n], np.uint32)
+    op, gp = _params_pair(orc, vmmod, n_hyp=16, seed=3)
+    ores = orc.fit_planes(pts, off, op)
+    gres = vmmod.fit_planes(torch.from_numpy(pts).cuda(), torch.from_numpy(off).cuda(), gp)
+    compare_planes(gres, ores)
+    assert gres["planes"]["hull_count"][0] > 1000  # ~6000 candidates: beyond the 2048-entry sort
