@@ -51,7 +51,8 @@ typedef struct {
     uint32_t flags;            /* VM_MAP_* bits */
 } vm_map_params;
 
-#define VM_MAP_STAGE_TIMING 1u /* record CUDA-event time per pipeline stage (vm_stage_times) */
+#define VM_MAP_STAGE_TIMING 1u /* record CUDA-event time per pipeline stage (vm_stage_times); implies VM_MAP_EAGER */
+#define VM_MAP_EAGER 2u        /* launch the segmentation kernel by kernel instead of replaying a captured CUDA graph */
 
 /* Segmentation parameters (Sec. III.C).  Defaults from the paper:
  * n_th = 3, theta 15 deg (cos_step = cos_ccl = 0.96592583f), d_th = 0.05 m,

@@ -125,6 +125,7 @@ struct Carver {
 // Fit scratch owned by a map or by a calling thread.
 struct FitContext {
     Timer timer;
+    uint64_t gen = 0;      // bumps whenever the scratch moves
     DevBuf mem;
     FitBuffers fb{};
     size_t kcap = 0, npts = 0, items = 0;
@@ -153,6 +154,8 @@ static size_t fit_bytes(size_t kcap, size_t npts, size_t items, int H, Carver* c
     size_t sw = scan_tmp_words(kcap + 1);
     fb.scan_tmp = k.take<uint32_t>(sw);
     fb.err = k.take<uint32_t>(4);
+    fb.tot = k.take<uint32_t>(4);
+    fb.kdev = k.take<uint32_t>(4);
     if (c) {
         c->off = k.off;
     }
@@ -182,11 +185,14 @@ static vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, in
     fb.hull_cnt = c.take<uint32_t>(k2 + 1);
     fb.scan_tmp = c.take<uint32_t>(scan_tmp_words(k2 + 1));
     fb.err = c.take<uint32_t>(4);
+    fb.tot = c.take<uint32_t>(4);
+    fb.kdev = c.take<uint32_t>(4);
     fb.kcap = k2;
     fb.npts_cap = n2;
     fb.items_cap = i2;
     fb.H = H2;
     fc.fb = fb;
+    fc.gen++;
     fc.kcap = k2;
     fc.npts = n2;
     fc.items = i2;
@@ -238,7 +244,8 @@ static vm_status fit_and_pack(FitContext& fc, const float* pts, const uint32_t* 
     FitBuffers& fb = fc.fb;
     VM_CUDA(cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s));
     StageHook* hk = fc.timer.hook();
-    VM_CUDA(launch_fit(pts, off, labels, k, npts, p, fb, tune, device_sms(), s, hk));
+    VM_CUDA(fit_set_count(fb.kdev, k, s));
+    VM_CUDA(launch_fit(pts, off, labels, fb.kdev, k, p, fb, tune, device_sms(), s, hk));
     uint32_t hdr[2];
     VM_CUDA(cudaMemcpyAsync(&hdr[0], fb.hull_cnt + k, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     VM_CUDA(cudaMemcpyAsync(&hdr[1], fb.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -253,8 +260,8 @@ static vm_status fit_and_pack(FitContext& fc, const float* pts, const uint32_t* 
     VM_TRY(ensure(fc.out, total));
     char* d = static_cast<char*>(fc.out.p);
     VM_STAGE_BEGIN(hk, kStPack, s);
-    VM_CUDA(launch_pack(fb, off, labels, k, reinterpret_cast<vm_plane*>(d), reinterpret_cast<int32_t*>(d + o_xy),
-                        reinterpret_cast<float*>(d + o_xyz), s));
+    VM_CUDA(launch_pack(fb, off, labels, fb.kdev, k, reinterpret_cast<vm_plane*>(d),
+                        reinterpret_cast<int32_t*>(d + o_xy), reinterpret_cast<float*>(d + o_xyz), n_hull, s));
     if (fc.host_bytes < total) {
         if (fc.host) cudaFreeHost(fc.host);
         fc.host = nullptr;
@@ -319,16 +326,31 @@ struct vm_map {
     FitContext fit;
     FitTuning tune = default_tuning();
     bool segmented = false;
+    // results: mapped pinned host memory written by the kernels
+    void* out_host = nullptr;
+    char* out_dev = nullptr;
+    size_t out_bytes = 0;
+    uint32_t out_kcap = 0, out_hcap = 0;
+    uint32_t kcap = 0;            // kept-cluster capacity of the scratch
+    uint32_t brick_hint = 0, k_hint = 0, hull_hint = 0;
+    uint64_t gen = 0;             // bumps whenever scratch or outputs move
+    // captured segmentation (one CUDA graph, replayed per call)
+    bool use_graph = true;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t ggen = ~0ull;
+    vm_segment_params gprm{};
+    unsigned long long glaunches = 0;
 };
 
 namespace {
 
-vm_status alloc_vox(vm_map* m, uint32_t n_sorted) {
-    const size_t need = (size_t)(n_sorted ? n_sorted : 1) * kBrickVox;
+vm_status alloc_vox(vm_map* m, uint32_t n_bricks) {
+    const size_t need = (size_t)(n_bricks ? n_bricks : 1) * kBrickVox;
     if (m->vox_mem.p && need <= m->seg_nv) return VM_OK;
-    size_t nv = need + need / 4;
+    size_t nv = need;
     const size_t cap_nv = (size_t)m->capacity * kBrickVox;
-    if (nv > cap_nv) nv = cap_nv > need ? cap_nv : need;
+    if (nv > cap_nv) nv = cap_nv;
+    m->gen++;
     const size_t tmp_words = [&] {
         size_t a = scan_tmp_words(nv + 1), b = sort_tmp_words(nv);
         size_t c = scan_tmp_words((size_t)m->nb_total + 1);
@@ -365,6 +387,129 @@ vm_status alloc_vox(vm_map* m, uint32_t n_sorted) {
     m->seg.nv = nv;
     m->seg.kcap = nv;
     m->seg_nv = nv;
+    return VM_OK;
+}
+
+// Result block in mapped pinned host memory: the counters, then kcap plane
+// records, then hcap hull vertices (xy int32 pairs, then xyz floats).
+size_t out_planes_off() { return 256; }
+size_t out_xy_off(uint32_t kcap) { return (256 + (size_t)kcap * sizeof(vm_plane) + 255) & ~(size_t)255; }
+size_t out_xyz_off(uint32_t kcap, uint32_t hcap) { return (out_xy_off(kcap) + (size_t)hcap * 8 + 255) & ~(size_t)255; }
+
+vm_status ensure_out(vm_map* m, uint32_t kcap, uint32_t hcap) {
+    if (m->out_host && kcap <= m->out_kcap && hcap <= m->out_hcap) return VM_OK;
+    if (m->out_host) cudaFreeHost(m->out_host);
+    m->out_host = nullptr;
+    m->out_dev = nullptr;
+    const size_t bytes = out_xyz_off(kcap, hcap) + (size_t)hcap * 12 + 256;
+    cudaError_t e = cudaHostAlloc(&m->out_host, bytes, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        m->out_host = nullptr;
+        return cuda_status(e, "cudaHostAlloc(mapped)");
+    }
+    void* d = nullptr;
+    e = cudaHostGetDevicePointer(&d, m->out_host, 0);
+    if (e != cudaSuccess) return cuda_status(e, "cudaHostGetDevicePointer");
+    memset(m->out_host, 0, 256);
+    m->out_dev = static_cast<char*>(d);
+    m->out_bytes = bytes;
+    m->out_kcap = kcap;
+    m->out_hcap = hcap;
+    m->gen++;
+    return VM_OK;
+}
+
+// Sizes the scratch from the last known counts with headroom; a launch whose
+// counts still do not fit raises kErrScratch and the caller retries.
+vm_status plan_capacity(vm_map* m, const vm_segment_params& p) {
+    const uint32_t want_b = m->brick_hint + m->brick_hint / 4 + 64;
+    const uint32_t cap_b = want_b < m->capacity ? want_b : m->capacity;
+    if (!m->vox_mem.p || (size_t)cap_b * kBrickVox > m->seg_nv) VM_TRY(alloc_vox(m, cap_b));
+    const size_t nv = m->seg_nv;
+    const uint32_t mc = p.min_cluster > 16 ? p.min_cluster : 16;
+    size_t kcap = nv / mc;
+    const size_t kh = (size_t)m->k_hint + m->k_hint / 4 + 64;
+    if (kcap < kh) kcap = kh;
+    if (kcap < 256) kcap = 256;
+    if (kcap > nv) kcap = nv;
+    if (kcap < m->kcap) kcap = m->kcap;  // never shrink: keeps the captured graph valid
+    m->kcap = (uint32_t)kcap;
+    const uint64_t g0 = m->fit.gen;
+    VM_TRY(fit_prepare(m->fit, kcap, nv, (int)p.n_hyp, m->tune.tile));
+    if (m->fit.gen != g0) m->gen++;
+    uint32_t hcap = m->hull_hint + m->hull_hint / 2 + 4096;
+    if (hcap < 65536) hcap = 65536;
+    if (hcap < m->out_hcap) hcap = m->out_hcap;
+    return ensure_out(m, (uint32_t)kcap, hcap);
+}
+
+__global__ void k_header(const SegCounters* __restrict__ ctr, const uint32_t* __restrict__ hull_off,
+                         const uint32_t* __restrict__ fit_err, const MapCounters* __restrict__ mc,
+                         const uint32_t* __restrict__ seg_err, SegCounters* __restrict__ out) {
+    SegCounters h = *ctr;
+    h.n_hull = hull_off[h.k];
+    h.fit_err = *fit_err;
+    h.n_bricks = mc->n_bricks;
+    h.map_err = mc->err;
+    h.err |= *seg_err;
+    *out = h;
+}
+
+// The whole segmentation as one fixed launch sequence (every count is read on
+// the device): order bricks, means, normals, clustering, clusters, RANSAC,
+// refit, hull, pack into the mapped result block, header.
+cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk) {
+    cudaStream_t s = m->stream;
+    const int sms = device_sms();
+    SegBuffers& b = m->seg;
+    FitBuffers& fb = m->fit.fb;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(m->err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    VM_STAGE_BEGIN(hk, kStOrder, s);
+    if ((e = seg_order_bricks(m->brick_table, m->nb_total, b, sms, s)) != cudaSuccess) return e;
+    VM_STAGE_END(hk, kStOrder, s);
+    if ((e = seg_run(m->g, m->S, m->C, p, b, m->kcap, m->err, sms, s, hk)) != cudaSuccess) return e;
+    if ((e = launch_fit(b.pts, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, p, fb, m->tune, sms, s, hk)) != cudaSuccess)
+        return e;
+    char* d = m->out_dev;
+    VM_STAGE_BEGIN(hk, kStPack, s);
+    e = launch_pack(fb, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, reinterpret_cast<vm_plane*>(d + out_planes_off()),
+                    reinterpret_cast<int32_t*>(d + out_xy_off(m->out_kcap)),
+                    reinterpret_cast<float*>(d + out_xyz_off(m->out_kcap, m->out_hcap)), m->out_hcap, s);
+    if (e != cudaSuccess) return e;
+    k_header<<<1, 1, 0, s>>>(b.ctr, fb.hull_cnt, fb.err, m->ctr, m->err, reinterpret_cast<SegCounters*>(d));
+    count_launch(1);
+    VM_STAGE_END(hk, kStPack, s);
+    return cudaGetLastError();
+}
+
+vm_status capture_segment(vm_map* m, const vm_segment_params& p) {
+    if (m->gexec) {
+        cudaGraphExecDestroy(m->gexec);
+        m->gexec = nullptr;
+    }
+    fit_init_attributes();
+    cudaGraph_t graph = nullptr;
+    const unsigned long long l0 = g_launches.load();
+    VM_CUDA(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_segment(m, p, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(m->stream, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_status(e, "segment capture");
+    }
+    if (e2 != cudaSuccess) return cuda_status(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&m->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        m->gexec = nullptr;
+        return cuda_status(e, "cudaGraphInstantiate");
+    }
+    m->glaunches = g_launches.load() - l0;
+    g_launches.fetch_sub(m->glaunches);  // counted when replayed, not when captured
+    m->ggen = m->gen;
+    m->gprm = p;
     return VM_OK;
 }
 
@@ -408,6 +553,7 @@ vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out
     }
     m->prm = p;
     m->fit.timer.on = (p.flags & VM_MAP_STAGE_TIMING) != 0;
+    m->use_graph = (p.flags & VM_MAP_EAGER) == 0;
     Grid& g = m->g;
     g.nx = p.dims[0]; g.ny = p.dims[1]; g.nz = p.dims[2];
     g.nbx = (g.nx + kBrick - 1) / kBrick;
@@ -504,6 +650,8 @@ vm_status vm_destroy(vm_map* m) {
     release(m->brick_mem);
     release(m->vox_mem);
     fit_release(m->fit);
+    if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    if (m->out_host) cudaFreeHost(m->out_host);
     if (m->hctr) cudaFreeHost(m->hctr);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
     delete m;
@@ -540,42 +688,70 @@ vm_status vm_segment(vm_map* m, const vm_segment_params* params, vm_planes* out)
         return VM_ERR_INVALID_ARG;
     }
     memset(out, 0, sizeof(*out));
-    const int sms = device_sms();
+    const vm_segment_params& p = *params;
     cudaStream_t s = m->stream;
-    SegBuffers& b = m->seg;
-    // 1. bricks in key order
-    if (!m->vox_mem.p) VM_TRY(alloc_vox(m, 1));
-    StageHook* hk = m->fit.timer.hook();
-    VM_CUDA(cudaMemsetAsync(m->err, 0, sizeof(uint32_t), s));
-    VM_STAGE_BEGIN(hk, kStOrder, s);
-    VM_CUDA(seg_order_bricks(m->brick_table, m->nb_total, b, sms, s));
-    VM_STAGE_END(hk, kStOrder, s);
-    VM_CUDA(cudaMemcpyAsync(m->hctr, b.ctr, sizeof(SegCounters), cudaMemcpyDeviceToHost, s));
-    VM_CUDA(cudaStreamSynchronize(s));
-    const uint32_t n_sorted = m->hctr->n_sorted;
-    VM_TRY(alloc_vox(m, n_sorted));
-    // 2. means, normals, classification, clustering, cluster numbering
-    VM_CUDA(seg_voxels(m->g, n_sorted, m->S, m->C, *params, b, m->err, sms, s, hk));
-    VM_CUDA(cudaMemcpyAsync(m->hctr, b.ctr, sizeof(SegCounters), cudaMemcpyDeviceToHost, s));
-    uint32_t map_err = 0, seg_err = 0;
-    VM_CUDA(cudaMemcpyAsync(&map_err, &m->ctr->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    VM_CUDA(cudaMemcpyAsync(&seg_err, m->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    VM_CUDA(cudaStreamSynchronize(s));
-    m->last = *m->hctr;
-    const uint32_t K = m->last.k, n_kept = m->last.n_kept;
-    // 3. cluster point lists in cluster order
-    VM_STAGE_BEGIN(hk, kStClusters, s);
-    VM_CUDA(seg_clusters(m->g, K, n_kept, b, sms, s));
-    VM_STAGE_END(hk, kStClusters, s);
+    if (!m->vox_mem.p) {  // first call: size the scratch from the pool's brick count (one read)
+        MapCounters c;
+        VM_CUDA(cudaMemcpyAsync(&c, m->ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaStreamSynchronize(s));
+        m->brick_hint = c.n_bricks < m->capacity ? c.n_bricks : m->capacity;
+    }
+    const SegCounters* hdr = nullptr;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        VM_TRY(plan_capacity(m, p));
+        StageHook* hk = m->fit.timer.hook();
+        if (m->use_graph && !hk && (!m->gexec || m->ggen != m->gen || memcmp(&m->gprm, &p, sizeof(p)) != 0)) {
+            if (capture_segment(m, p) != VM_OK) {  // e.g. a stream that cannot be captured: launch eagerly
+                cudaGetLastError();
+                m->use_graph = false;
+            }
+        }
+        if (m->use_graph && !hk) {
+            VM_CUDA(cudaGraphLaunch(m->gexec, s));
+            count_launch((int)m->glaunches);
+        } else {
+            VM_CUDA(enqueue_segment(m, p, hk));
+        }
+        VM_CUDA(cudaStreamSynchronize(s));
+        m->fit.timer.fold();
+        hdr = static_cast<const SegCounters*>(m->out_host);
+        m->brick_hint = hdr->n_bricks < m->capacity ? hdr->n_bricks : m->capacity;
+        m->k_hint = hdr->k;
+        m->hull_hint = hdr->n_hull;
+        const bool retry = (hdr->err & kErrScratch) || hdr->n_hull > m->out_hcap;
+        if (!retry) break;
+        if (attempt == 3) {
+            set_error("segmentation scratch could not be sized for this map");
+            return VM_ERR_OUT_OF_MEMORY;
+        }
+    }
+    m->last = *hdr;
     m->segmented = true;
-    // 4. RANSAC, refit, hull, pack
-    vm_status st = fit_and_pack(m->fit, b.pts, b.cl_off, b.cl_label, K, n_kept, *params, m->tune, s, out);
-    if (st != VM_OK) return st;
-    if (seg_err & kErrTimeout) {
-        set_error("union-find reached its iteration cap");
+    const uint32_t K = hdr->k, n_hull = hdr->n_hull;
+    const size_t b_planes = (size_t)K * sizeof(vm_plane);
+    out->planes = static_cast<vm_plane*>(malloc(b_planes ? b_planes : 1));
+    out->hull_xy = static_cast<int32_t*>(malloc(n_hull ? (size_t)n_hull * 8 : 1));
+    out->hull_xyz = static_cast<float*>(malloc(n_hull ? (size_t)n_hull * 12 : 1));
+    if (!out->planes || !out->hull_xy || !out->hull_xyz) {
+        vm_planes_free(out);
+        set_error("host allocation of the result failed");
+        return VM_ERR_OUT_OF_MEMORY;
+    }
+    const char* h = static_cast<const char*>(m->out_host);
+    memcpy(out->planes, h + out_planes_off(), b_planes);
+    memcpy(out->hull_xy, h + out_xy_off(m->out_kcap), (size_t)n_hull * 8);
+    memcpy(out->hull_xyz, h + out_xyz_off(m->out_kcap, m->out_hcap), (size_t)n_hull * 12);
+    out->n_planes = K;
+    out->n_hull = n_hull;
+    if ((hdr->err | hdr->fit_err) & kErrTimeout) {
+        set_error("a bounded device loop reached its iteration cap");
         return VM_ERR_TIMEOUT;
     }
-    if (map_err & kErrCapacity) {
+    if (hdr->fit_err & kErrOverflow) {
+        set_error("a cluster spans more than 2^28 hull quanta (4096 m) in its plane; its hull is not exact");
+        return VM_ERR_EXTENT;
+    }
+    if (hdr->map_err & kErrCapacity) {
         set_error("brick pool full: points in unallocated bricks were dropped");
         return VM_ERR_CAPACITY;
     }
@@ -611,6 +787,7 @@ vm_status vm_get_stats(vm_map* m, vm_stats* out) {
     out->clusters = m->last.k;
     out->device_bytes = m->pool.bytes + m->stage.bytes + m->brick_mem.bytes + m->vox_mem.bytes + m->fit.mem.bytes +
                         m->fit.out.bytes;
+    (void)0;
     if (c.err & kErrCapacity) {
         set_error("brick pool full");
         return VM_ERR_CAPACITY;

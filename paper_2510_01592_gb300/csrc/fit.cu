@@ -72,8 +72,9 @@ __device__ __forceinline__ uint32_t find_cluster(const uint32_t* __restrict__ it
 
 // ---------------------------------------------------------------- stage a
 __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                      const uint32_t* __restrict__ labels, uint32_t k, int H, unsigned long long seed,
+                      const uint32_t* __restrict__ labels, const uint32_t* __restrict__ kp, int H, unsigned long long seed,
                       float4* __restrict__ hyp, uint8_t* __restrict__ valid, uint32_t* __restrict__ counts) {
+    const uint32_t k = *kp;
     const size_t total = (size_t)k * H;
     for (size_t t = (size_t)blockIdx.x * kT + threadIdx.x; t < total; t += (size_t)gridDim.x * kT) {
         const uint32_t c = (uint32_t)(t / H), h = (uint32_t)(t % H);
@@ -114,9 +115,10 @@ __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict_
 // ---------------------------------------------------------------- stage b
 template <int R>
 __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                              const uint32_t* __restrict__ item_off, uint32_t k, int H, int T,
+                                              const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int H, int T,
                                               const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
                                               uint32_t* __restrict__ queue, float eps) {
+    const uint32_t k = *kp;
     extern __shared__ float4 sp[];                // T staged points
     uint32_t* red = reinterpret_cast<uint32_t*>(sp + T);  // [P][G*R]
     __shared__ uint32_t s_item;
@@ -170,9 +172,10 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
 }
 
 // ---------------------------------------------------------------- stage c
-__global__ void k_select(const float* __restrict__ pts, const uint32_t* __restrict__ off, uint32_t k, int H,
+__global__ void k_select(const float* __restrict__ pts, const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int H,
                          const float4* __restrict__ hyp, const uint8_t* __restrict__ valid,
                          const uint32_t* __restrict__ counts, FitCluster* __restrict__ cl) {
+    const uint32_t k = *kp;
     __shared__ unsigned long long wbest[kT / 32];
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
         unsigned long long best = 0;  // (count << 32) | ~h ; 0 = none
@@ -269,9 +272,10 @@ __device__ __forceinline__ Tv block_sum(Tv v, Tv* sh) {
 // Inliers, centroid partials (relative to the origin) and the extreme inliers
 // along the 16 filter directions (reduced per warp, then atomicMax).
 __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                                const uint32_t* __restrict__ item_off, uint32_t k, int T,
+                                                const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int T,
                                                 FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
                                                 float* __restrict__ part, float eps, uint32_t* __restrict__ err) {
+    const uint32_t k = *kp;
     __shared__ float shf[kT / 32];
     __shared__ uint32_t shu[kT / 32];
     const uint32_t n_items = item_off[k];
@@ -329,8 +333,9 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
 // Per cluster (one warp each): inlier count and centroid, the per-item
 // partial sums added in double in a fixed order (lane-strided, then a shuffle
 // tree), so the result does not depend on scheduling.
-__global__ void k_centroid(const uint32_t* __restrict__ item_off, uint32_t k, const float* __restrict__ part,
+__global__ void k_centroid(const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, const float* __restrict__ part,
                            FitCluster* __restrict__ cl, double* __restrict__ cen) {
+    const uint32_t k = *kp;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kT / 32);
     for (uint32_t c = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); c < k; c += warps) {
@@ -367,10 +372,11 @@ __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b) {
 // strictly inside the polygon through the 16 extreme inliers cannot be hull
 // vertices; the others are appended to the cluster's survivor list.
 __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                               const uint32_t* __restrict__ item_off, uint32_t k, int T,
+                                               const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int T,
                                                FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
                                                const double* __restrict__ cen, float* __restrict__ part,
                                                int2* __restrict__ surv) {
+    const uint32_t k = *kp;
     __shared__ float shf[kT / 32];
     __shared__ int2 poly[kFiltDirs + 1];
     __shared__ int npoly;
@@ -454,8 +460,9 @@ __device__ __forceinline__ double rsqrt_d(double x) {
 // step; six steps in double, multiplies and adds only.  n_z >= 0,
 // d = -n . centroid; lambda_mid < 10 lambda_min (from the trace, the Rayleigh
 // quotient and x^T adj(A) x = lambda_1 lambda_2) flags the plane ill-conditioned.
-__global__ void k_refit(const uint32_t* __restrict__ item_off, uint32_t k, const float* __restrict__ part,
+__global__ void k_refit(const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, const float* __restrict__ part,
                         const double* __restrict__ cen, FitCluster* __restrict__ cl) {
+    const uint32_t k = *kp;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kT / 32);
     for (uint32_t c = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); c < k; c += warps) {
@@ -565,10 +572,11 @@ constexpr int kHullDirs = 128;
 // (3) bitonic sort by (X, Y), duplicates removed; (4) monotone chain, lower
 // and upper halves built concurrently by two threads.  If more than
 // kHullCap points remain, gift wrapping runs over the survivors instead.
-__global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, uint32_t k,
+__global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp,
                                              const FitCluster* __restrict__ cl, const int2* __restrict__ surv,
                                              int2* __restrict__ hull, uint32_t* __restrict__ hull_cnt,
                                              uint32_t* __restrict__ err) {
+    const uint32_t k = *kp;
     extern __shared__ unsigned long long sk[];              // kHullCap keys, then kHullCap unique
     unsigned long long* uq = sk + kHullCap;
     uint32_t* st_lo = reinterpret_cast<uint32_t*>(uq + kHullCap);
@@ -781,15 +789,17 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, u
     }
 }
 
-__global__ void k_items(const uint32_t* __restrict__ off, uint32_t k, int T, uint32_t* __restrict__ item_cnt) {
+__global__ void k_items(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int T, uint32_t* __restrict__ item_cnt) {
+    const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT)
         item_cnt[c] = (off[c + 1] - off[c] + (uint32_t)T - 1) / (uint32_t)T;
 }
 
-__global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restrict__ labels, uint32_t k,
+__global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restrict__ labels, const uint32_t* __restrict__ kp,
                        const FitCluster* __restrict__ cl, const int2* __restrict__ hull,
                        const uint32_t* __restrict__ hull_off, vm_plane* __restrict__ planes,
-                       int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz) {
+                       int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz, uint32_t hull_cap) {
+    const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
         const FitCluster f = cl[c];
         const uint32_t ho = hull_off[c], hn = hull_off[c + 1] - ho;
@@ -813,7 +823,7 @@ __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restr
             p.flags = f.flags;
             planes[c] = p;
         }
-        for (uint32_t i = threadIdx.x; i < hn; i += blockDim.x) {
+        for (uint32_t i = threadIdx.x; i < hn && ho + i < hull_cap; i += blockDim.x) {
             const int2 q = hull[off[c] + i];
             hull_xy[2 * (ho + i)] = q.x;
             hull_xy[2 * (ho + i) + 1] = q.y;
@@ -830,19 +840,21 @@ __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restr
 }
 
 template <int R>
-cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* item_off, uint32_t k, int H, int T,
-                         const float4* hyp, uint32_t* counts, uint32_t* queue, float eps, int grid, cudaStream_t s) {
+cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* kp, int H,
+                         int T, const float4* hyp, uint32_t* counts, uint32_t* queue, float eps, int grid,
+                         cudaStream_t s) {
     const int G = (H + R - 1) / R;
     const int P = kT / G;
     const size_t smem = (size_t)T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_score<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
-    k_score<R><<<grid, kT, smem, s>>>(pts, off, item_off, k, H, T, hyp, counts, queue, eps);
+    k_score<R><<<grid, kT, smem, s>>>(pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
     return cudaGetLastError();
 }
+
+__global__ void k_set_end(uint32_t* __restrict__ arr, const uint32_t* __restrict__ kp, const uint32_t* __restrict__ v) {
+    arr[*kp] = *v;
+}
+
+__global__ void k_set_u32(uint32_t* __restrict__ p, uint32_t v) { *p = v; }
 
 }  // namespace
 
@@ -852,67 +864,84 @@ size_t fit_hull_smem() {
     return (size_t)kHullCap * (2 * sizeof(unsigned long long) + 2 * sizeof(uint32_t)) + (size_t)kSurvCap * sizeof(int2);
 }
 
-cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, uint32_t k, uint32_t npts,
-                       const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int sms, cudaStream_t s,
-                       StageHook* hk) {
-    (void)npts;
-    if (k == 0) return cudaSuccess;
+void fit_init_attributes() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_hull_smem());
+    cudaFuncSetAttribute(k_score<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_score<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_score<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_score<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    done = true;
+}
+
+cudaError_t fit_set_count(uint32_t* kdev, uint32_t k, cudaStream_t s) {
+    k_set_u32<<<1, 1, 0, s>>>(kdev, k);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
+                       uint32_t kcap, const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int sms,
+                       cudaStream_t s, StageHook* hk) {
+    if (kcap == 0) return cudaSuccess;
+    fit_init_attributes();
     const int H = (int)p.n_hyp;
     const int T = t.tile;
     cudaError_t e;
     VM_STAGE_BEGIN(hk, kStHyp, s);
-    k_items<<<(k + kT - 1) / kT, kT, 0, s>>>(off, k, T, fb.item_off);
-    e = exclusive_scan_u32(fb.item_off, fb.item_off, fb.item_off + k, k, fb.scan_tmp, s);
+    const unsigned kgrid = (kcap + kT - 1) / kT < (uint32_t)sms * 8 ? (kcap + kT - 1) / kT : (uint32_t)sms * 8;
+    k_items<<<kgrid, kT, 0, s>>>(off, kp, T, fb.item_off);
+    e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s);
     if (e != cudaSuccess) return e;
+    k_set_end<<<1, 1, 0, s>>>(fb.item_off, kp, fb.tot);
     if ((e = cudaMemsetAsync(fb.queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
-    const size_t kh = (size_t)k * H;
+    const size_t kh = (size_t)kcap * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    k_hyp<<<hgrid, kT, 0, s>>>(pts, off, labels, k, H, p.seed, fb.hyp, fb.hyp_valid, fb.counts);
+    k_hyp<<<hgrid, kT, 0, s>>>(pts, off, labels, kp, H, p.seed, fb.hyp, fb.hyp_valid, fb.counts);
     VM_STAGE_END(hk, kStHyp, s);
-    count_launch(2);
+    count_launch(3);
     const int grid = sms * t.ctas_per_sm;
     int R = t.hyp_per_thread;
     while (R < 8 && (H + R - 1) / R > kT) R <<= 1;  // at most one subset row of kT threads
     VM_STAGE_BEGIN(hk, kStScore, s);
     switch (R) {
-        case 1: e = launch_score<1>(pts, off, fb.item_off, k, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-        case 2: e = launch_score<2>(pts, off, fb.item_off, k, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-        case 8: e = launch_score<8>(pts, off, fb.item_off, k, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-        default: e = launch_score<4>(pts, off, fb.item_off, k, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        case 1: e = launch_score<1>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        case 2: e = launch_score<2>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        case 8: e = launch_score<8>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        default: e = launch_score<4>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
     }
     if (e != cudaSuccess) return e;
     VM_STAGE_END(hk, kStScore, s);
     count_launch(1);
-    const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;
+    const unsigned cgrid = kcap < (uint32_t)sms * 8 ? kcap : (uint32_t)sms * 8;
     VM_STAGE_BEGIN(hk, kStExtract, s);
-    k_select<<<cgrid, kT, 0, s>>>(pts, off, k, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
+    k_select<<<cgrid, kT, 0, s>>>(pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
     const unsigned igrid = (unsigned)sms * 8;
-    k_extract<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, k, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
-    const unsigned wgrid = (k + kT / 32 - 1) / (kT / 32);
-    k_centroid<<<wgrid, kT, 0, s>>>(fb.item_off, k, fb.part, fb.cl, fb.cen);
-    k_filter<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, k, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
+    k_extract<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
+    const unsigned wgrid0 = (kcap + kT / 32 - 1) / (kT / 32);
+    const unsigned wgrid = wgrid0 < (uint32_t)sms * 8 ? wgrid0 : (uint32_t)sms * 8;
+    k_centroid<<<wgrid, kT, 0, s>>>(fb.item_off, kp, fb.part, fb.cl, fb.cen);
+    k_filter<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
     VM_STAGE_END(hk, kStExtract, s);
     count_launch(4);
     VM_STAGE_BEGIN(hk, kStHull, s);
-    static bool hull_attr = false;
-    if (!hull_attr) {
-        cudaFuncSetAttribute(k_hull, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fit_hull_smem());
-        hull_attr = true;
-    }
-    k_refit<<<wgrid, kT, 0, s>>>(fb.item_off, k, fb.part, fb.cen, fb.cl);
-    k_hull<<<cgrid, kT, fit_hull_smem(), s>>>(off, k, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
-    e = exclusive_scan_u32(fb.hull_cnt, fb.hull_cnt, fb.hull_cnt + k, k, fb.scan_tmp, s);
+    k_refit<<<wgrid, kT, 0, s>>>(fb.item_off, kp, fb.part, fb.cen, fb.cl);
+    k_hull<<<cgrid, kT, fit_hull_smem(), s>>>(off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
+    e = exclusive_scan_dev(fb.hull_cnt, fb.hull_cnt, fb.tot + 1, kp, kcap, fb.scan_tmp, s);
     if (e != cudaSuccess) return e;
+    k_set_end<<<1, 1, 0, s>>>(fb.hull_cnt, kp, fb.tot + 1);
     VM_STAGE_END(hk, kStHull, s);
-    count_launch(2);
+    count_launch(3);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, uint32_t k,
-                        vm_plane* planes, int32_t* hull_xy, float* hull_xyz, cudaStream_t s) {
-    if (k == 0) return cudaSuccess;
-    k_pack<<<k < 4096 ? k : 4096, 128, 0, s>>>(off, labels, k, fb.cl, fb.hull, fb.hull_cnt, planes, hull_xy,
-                                              hull_xyz);
+cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
+                        uint32_t kcap, vm_plane* planes, int32_t* hull_xy, float* hull_xyz, uint32_t hull_cap,
+                        cudaStream_t s) {
+    if (kcap == 0) return cudaSuccess;
+    k_pack<<<kcap < 4096 ? kcap : 4096, 128, 0, s>>>(off, labels, kp, fb.cl, fb.hull, fb.hull_cnt, planes, hull_xy,
+                                                    hull_xyz, hull_cap);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -942,14 +971,15 @@ constexpr size_t kOffValid = kOffCounts + align256((size_t)kStaticMaxSlots * siz
 constexpr size_t kOffCl = kOffValid + align256((size_t)kStaticMaxSlots);
 constexpr size_t kOffItems = kOffCl + align256((size_t)kStaticMaxClusters * sizeof(FitCluster));
 constexpr size_t kOffQueue = kOffItems + align256((size_t)(kStaticMaxClusters + 1) * sizeof(uint32_t));
-constexpr size_t kOffScan = kOffQueue + 256;
+constexpr size_t kOffScan = kOffQueue + 256;  // the queue area also holds the count and a scan total
 constexpr size_t kScanWords = 64;  // >= scan_tmp_words(kStaticMaxClusters + 1)
 constexpr size_t kStaticBytes = kOffScan + align256(kScanWords * sizeof(uint32_t));
 
 // Copies the selected plane, hypothesis index and inlier count of each cluster
 // to the caller's arrays.
-__global__ void k_static_out(const FitCluster* __restrict__ cl, uint32_t k, float* __restrict__ planes,
+__global__ void k_static_out(const FitCluster* __restrict__ cl, const uint32_t* __restrict__ kp, float* __restrict__ planes,
                              int32_t* __restrict__ best_h, uint32_t* __restrict__ inliers) {
+    const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT) {
         const FitCluster f = cl[c];
         planes[4 * c + 0] = f.n[0];
@@ -1019,32 +1049,37 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     FitCluster* cl = reinterpret_cast<FitCluster*>(base + kOffCl);
     uint32_t* item_off = reinterpret_cast<uint32_t*>(base + kOffItems);
     uint32_t* queue = reinterpret_cast<uint32_t*>(base + kOffQueue);
+    uint32_t* kdev = queue + 8;
+    uint32_t* total = queue + 9;
     uint32_t* scan_tmp = reinterpret_cast<uint32_t*>(base + kOffScan);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
+    fit_init_attributes();
     // the work queue starts at zero every call; counts are zeroed by k_hyp
     if ((e = cudaMemsetAsync(queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_status(e, "cudaMemsetAsync");
-    k_items<<<(k + kT - 1) / kT, kT, 0, s>>>(off, k, t.tile, item_off);
-    if ((e = exclusive_scan_u32(item_off, item_off, item_off + k, k, scan_tmp, s)) != cudaSuccess)
+    k_set_u32<<<1, 1, 0, s>>>(kdev, k);
+    k_items<<<(k + kT - 1) / kT, kT, 0, s>>>(off, kdev, t.tile, item_off);
+    if ((e = exclusive_scan_dev(item_off, item_off, total, kdev, k, scan_tmp, s)) != cudaSuccess)
         return cuda_status(e, "scan");
+    k_set_end<<<1, 1, 0, s>>>(item_off, kdev, total);
     const size_t kh = (size_t)k * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    k_hyp<<<hgrid, kT, 0, s>>>(xyz, off, labels, k, H, params->seed, hyp, valid, counts);
+    k_hyp<<<hgrid, kT, 0, s>>>(xyz, off, labels, kdev, H, params->seed, hyp, valid, counts);
     int R = t.hyp_per_thread;
     while (R < 8 && (H + R - 1) / R > kT) R <<= 1;
     const int grid = sms * t.ctas_per_sm;
     switch (R) {
-        case 8: e = launch_score<8>(xyz, off, item_off, k, H, t.tile, hyp, counts, queue, params->eps, grid, s); break;
-        default: e = launch_score<4>(xyz, off, item_off, k, H, t.tile, hyp, counts, queue, params->eps, grid, s); break;
+        case 8: e = launch_score<8>(xyz, off, item_off, kdev, H, t.tile, hyp, counts, queue, params->eps, grid, s); break;
+        default: e = launch_score<4>(xyz, off, item_off, kdev, H, t.tile, hyp, counts, queue, params->eps, grid, s); break;
     }
     if (e != cudaSuccess) return cuda_status(e, "k_score");
     const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;
-    k_select<<<cgrid, kT, 0, s>>>(xyz, off, k, H, hyp, valid, counts, cl);
-    k_static_out<<<(k + kT - 1) / kT, kT, 0, s>>>(cl, k, planes_out, best_h_out, inliers_out);
-    count_launch(5);
+    k_select<<<cgrid, kT, 0, s>>>(xyz, off, kdev, H, hyp, valid, counts, cl);
+    k_static_out<<<(k + kT - 1) / kT, kT, 0, s>>>(cl, kdev, planes_out, best_h_out, inliers_out);
+    count_launch(7);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "vm_ransac_static launch");
     return VM_OK;

@@ -37,8 +37,17 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_s
     return inc - v + warp_sums[w];
 }
 
-__global__ void k_tile_reduce(const uint32_t* __restrict__ in, size_t n, uint32_t* __restrict__ tile_sum) {
+// n_dev (optional): the element count read on the device, clamped to n.
+__device__ __forceinline__ size_t dev_count(size_t n, const uint32_t* n_dev) {
+    if (!n_dev) return n;
+    const size_t d = *n_dev;
+    return d < n ? d : n;
+}
+
+__global__ void k_tile_reduce(const uint32_t* __restrict__ in, size_t n_cap, const uint32_t* __restrict__ n_dev,
+                              uint32_t* __restrict__ tile_sum) {
     __shared__ uint32_t ws[kScanThreads / 32];
+    const size_t n = dev_count(n_cap, n_dev);
     const size_t base = (size_t)blockIdx.x * kScanTile;
     uint32_t s = 0;
 #pragma unroll
@@ -74,11 +83,14 @@ __global__ void k_scan_sums(uint32_t* __restrict__ sums, size_t nt, uint32_t* __
     if (threadIdx.x == 0 && total) *total = carry;
 }
 
-__global__ void k_tile_scan(const uint32_t* in, uint32_t* out, size_t n, const uint32_t* __restrict__ tile_off) {
+__global__ void k_tile_scan(const uint32_t* in, uint32_t* out, size_t n_cap, const uint32_t* __restrict__ n_dev,
+                            const uint32_t* __restrict__ tile_off) {
     __shared__ uint32_t buf[kScanTile];
     __shared__ uint32_t ws[kScanThreads / 32];
     __shared__ uint32_t tot;
+    const size_t n = dev_count(n_cap, n_dev);
     const size_t base = (size_t)blockIdx.x * kScanTile;
+    if (base >= n) return;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         int t = i * kScanThreads + threadIdx.x;
@@ -114,9 +126,10 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortIters = 8;                               // 32-item rounds per warp
 constexpr int kSortTile = kSortThreads * kSortIters;        // 2048
 
-__global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t n, int shift, uint32_t* __restrict__ ghist,
-                          size_t nt) {
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t n_cap, const uint32_t* __restrict__ n_dev, int shift,
+                          uint32_t* __restrict__ ghist, size_t nt) {
     __shared__ uint32_t h[256];
+    const size_t n = dev_count(n_cap, n_dev);
     h[threadIdx.x] = 0;
     __syncthreads();
     const size_t base = (size_t)blockIdx.x * kSortTile;
@@ -130,9 +143,12 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t n, int shift
 
 // Stable scatter: warp w owns items [w*256, w*256+256) of the tile, in order.
 __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t n, int shift,
-                             const uint32_t* __restrict__ goff, size_t nt) {
+                             uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t n_cap,
+                             const uint32_t* __restrict__ n_dev, int shift, const uint32_t* __restrict__ goff,
+                             size_t nt) {
     __shared__ uint32_t wc[kSortWarps][256];
+    const size_t n = dev_count(n_cap, n_dev);
+    if ((size_t)blockIdx.x * kSortTile >= n) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wc[0][0])[d] = 0;
     __syncthreads();
@@ -175,22 +191,75 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* _
     }
 }
 
+// Small inputs: one 1024-thread CTA scans everything, four items per thread
+// per round, carrying the running total across rounds.
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallItems = 4;
+constexpr size_t kSmallMax = 16384;
+
+__global__ void __launch_bounds__(kSmallThreads) k_scan_small(const uint32_t* in, uint32_t* out, size_t n_cap,
+                                                              const uint32_t* __restrict__ n_dev, uint32_t* total) {
+    __shared__ uint32_t ws[kSmallThreads / 32];
+    __shared__ uint32_t round_total;
+    const size_t n = dev_count(n_cap, n_dev);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (size_t base = 0; base < n; base += (size_t)kSmallThreads * kSmallItems) {
+        const size_t j0 = base + (size_t)threadIdx.x * kSmallItems;
+        uint32_t v[kSmallItems], sum = 0;
+#pragma unroll
+        for (int i = 0; i < kSmallItems; ++i) {
+            v[i] = (j0 + i < n) ? in[j0 + i] : 0u;
+            sum += v[i];
+        }
+        const uint32_t inc = warp_incl_scan(sum);
+        if (lane == 31) ws[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t t = ws[lane];
+            const uint32_t ti = warp_incl_scan(t);
+            ws[lane] = ti - t;
+            if (lane == 31) round_total = ti;
+        }
+        __syncthreads();
+        uint32_t ex = carry + ws[w] + (inc - sum);
+#pragma unroll
+        for (int i = 0; i < kSmallItems; ++i) {
+            if (j0 + i < n) out[j0 + i] = ex;
+            ex += v[i];
+        }
+        carry += round_total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
 }  // namespace
 
 size_t scan_tmp_words(size_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
-cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total, size_t n, uint32_t* tmp,
-                               cudaStream_t s) {
-    if (n == 0) {
+cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
+                               uint32_t* tmp, cudaStream_t s) {
+    if (n_cap == 0) {
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
         return cudaSuccess;
     }
-    const size_t nt = (n + kScanTile - 1) / kScanTile;
-    k_tile_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tmp);
+    if (n_cap <= kSmallMax) {
+        k_scan_small<<<1, kSmallThreads, 0, s>>>(in, out, n_cap, n_dev, total);
+        count_launch(1);
+        return cudaGetLastError();
+    }
+    const size_t nt = (n_cap + kScanTile - 1) / kScanTile;
+    k_tile_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n_cap, n_dev, tmp);
     k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp, nt, total);
-    k_tile_scan<<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, n, tmp);
+    k_tile_scan<<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, n_cap, n_dev, tmp);
     count_launch(3);
     return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total, size_t n, uint32_t* tmp,
+                               cudaStream_t s) {
+    return exclusive_scan_dev(in, out, total, nullptr, n, tmp, s);
 }
 
 size_t sort_tmp_words(size_t n) {
@@ -198,30 +267,35 @@ size_t sort_tmp_words(size_t n) {
     return 256 * nt + scan_tmp_words(256 * nt) + 1;
 }
 
-cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
-                                  int bits, uint32_t* tmp, cudaStream_t s) {
-    if (n == 0 || bits <= 0) return cudaSuccess;
-    const size_t nt = (n + kSortTile - 1) / kSortTile;
+cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                                  const uint32_t* n_dev, size_t n_cap, int bits, uint32_t* tmp, cudaStream_t s) {
+    if (n_cap == 0 || bits <= 0) return cudaSuccess;
+    const size_t nt = (n_cap + kSortTile - 1) / kSortTile;
     uint32_t* ghist = tmp;
     uint32_t* stmp = tmp + 256 * nt;
     uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
-    int passes = (bits + 7) / 8;
+    const int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; ++p) {
-        int shift = 8 * p;
-        k_rs_hist<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, n, shift, ghist, nt);
-        cudaError_t e = exclusive_scan_u32(ghist, ghist, nullptr, 256 * nt, stmp, s);
+        const int shift = 8 * p;
+        k_rs_hist<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, ghist, nt);
+        cudaError_t e = exclusive_scan_dev(ghist, ghist, nullptr, nullptr, 256 * nt, stmp, s);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, vi, ko, vo, n, shift, ghist, nt);
+        k_rs_scatter<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, ghist, nt);
         count_launch(2);
         uint32_t* t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
     }
-    if (ki != keys) {
-        cudaMemcpyAsync(keys, ki, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(vals, vi, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    if (ki != keys) {  // odd number of passes: copy back (n_cap elements; the tail is scratch)
+        cudaMemcpyAsync(keys, ki, n_cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(vals, vi, n_cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     }
     return cudaGetLastError();
+}
+
+cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
+                                  int bits, uint32_t* tmp, cudaStream_t s) {
+    return stable_sort_pairs_dev(keys, vals, keys_alt, vals_alt, nullptr, n, bits, tmp, s);
 }
 
 }  // namespace vmx

@@ -51,11 +51,12 @@ __global__ void k_brick_compact(const int32_t* __restrict__ table, uint32_t nb, 
 
 // Mean of each voxel: M = floor((2 S + c) / (2 c)), the exact integer mean in
 // 2^-20 m units rounded half up (Eq. 1's mu up to that quantum).
-__global__ void __launch_bounds__(kT) k_finalize(uint32_t n_sorted, const int32_t* __restrict__ sorted_slot,
+__global__ void __launch_bounds__(kT) k_finalize(const uint32_t* __restrict__ nsp, uint32_t cap_b, const int32_t* __restrict__ sorted_slot,
                                                  const unsigned long long* __restrict__ S,
                                                  const uint32_t* __restrict__ C, int32_t* __restrict__ M,
                                                  uint8_t* __restrict__ status, size_t stride,
                                                  SegCounters* __restrict__ ctr) {
+    const uint32_t n_sorted = min(*nsp, cap_b);
     uint32_t occ = 0;
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
         const int32_t slot = sorted_slot[r];
@@ -261,7 +262,7 @@ __device__ __forceinline__ void fwd_offset(int k, int& dz, int& dy, int& dx) {
 // global parent of each vertex is set to its local root (the smallest index of
 // its in-brick component).  Edges that leave the brick follow in k_ccl_cross.
 constexpr int kNormT = 128;
-__global__ void __launch_bounds__(kNormT) k_normals(uint32_t n_sorted, Grid g, const int32_t* __restrict__ sorted_key,
+__global__ void __launch_bounds__(kNormT) k_normals(const uint32_t* __restrict__ nsp, uint32_t cap_b, Grid g, const int32_t* __restrict__ sorted_key,
                                                     const int32_t* __restrict__ rank_table,
                                                     const int32_t* __restrict__ M, float* __restrict__ nrm,
                                                     uint8_t* __restrict__ status, uint8_t* __restrict__ nbr,
@@ -269,6 +270,7 @@ __global__ void __launch_bounds__(kNormT) k_normals(uint32_t n_sorted, Grid g, c
                                                     float4* __restrict__ rec, size_t stride, uint32_t n_th,
                                                     float cos_step, uint8_t want, float d_th2, float cos_ccl,
                                                     uint32_t* err) {
+    const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ int32_t sM[3][1000];
     __shared__ float sMu[3][512];
     __shared__ float sN[3][512];
@@ -387,51 +389,88 @@ __global__ void __launch_bounds__(kNormT) k_normals(uint32_t n_sorted, Grid g, c
     }
 }
 
-// The inter-brick half of Algorithm 1, one warp per brick: a vertex whose
-// forward neighbours can lie in another brick tests those neighbours and joins
-// the global forest over the edges that pass.  Forward offsets have dz in
-// {0, 1}, dy in {-1, 0, 1} (-1 only with dz = 1) and dx in {-1, 0, 1}, so they
-// leave the brick through the +z face, either y face or either x face.
-__global__ void __launch_bounds__(256) k_ccl_cross(uint32_t n_sorted, Grid g, const int32_t* __restrict__ sorted_key,
-                                                   const int32_t* __restrict__ rank_table,
-                                                   const float4* __restrict__ rec, uint32_t* parent, size_t stride,
-                                                   uint8_t want, float d_th2, float cos_ccl, uint32_t* err) {
-    __shared__ int32_t nbs[8][27];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int32_t* nb = nbs[w];
-    const uint32_t warps = gridDim.x * 8;
-    for (uint32_t r = blockIdx.x * 8 + w; r < n_sorted; r += warps) {
-        __syncwarp();
-        if (lane < 27) {
-            int bx, by, bz;
-            brick_coords(sorted_key[r], g, bx, by, bz);
-            const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
-            const int x = bx + dx, y = by + dy, z = bz + dz;
-            nb[lane] = (x >= 0 && y >= 0 && z >= 0 && x < g.nbx && y < g.nby && z < g.nbz)
-                           ? rank_table[(z * g.nby + y) * g.nbx + x] : -1;
+// The inter-brick half of Algorithm 1, one 128-thread CTA per brick.  The
+// brick's 10^3 halo of packed voxel records and current parents is staged in
+// shared memory with independent loads; then every vertex whose forward
+// neighbours can lie in another brick tests those neighbours from shared
+// memory.  Forward offsets have dz in {0, 1}, dy in {-1, 0, 1} (-1 only with
+// dz = 1) and dx in {-1, 0, 1}, so they leave the brick through the +z face,
+// either y face or either x face.  An edge (i, j) that passes is recorded as
+// the pair of their staged parents (ancestors of i and j, so joining them
+// joins i and j) in a hash set in shared memory, and each distinct pair is
+// joined once in the global forest: most of a brick's edges lead to the same
+// few pairs.
+constexpr int kCrossT = 128;
+constexpr int kPairSlots = 256;
+__global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restrict__ nsp, uint32_t cap_b, Grid g, const int32_t* __restrict__ sorted_key,
+                                                       const int32_t* __restrict__ rank_table,
+                                                       const float4* __restrict__ rec, uint32_t* parent,
+                                                       size_t stride, uint8_t want, float d_th2, float cos_ccl,
+                                                       uint32_t* err) {
+    const uint32_t n_sorted = min(*nsp, cap_b);
+    __shared__ float4 sA[1000];
+    __shared__ float4 sB[1000];
+    __shared__ uint32_t sP[1000];
+    __shared__ unsigned long long set[kPairSlots];
+    __shared__ int32_t nb[27];
+    for (int q = threadIdx.x; q < kPairSlots; q += kCrossT) set[q] = ~0ull;
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        __syncthreads();
+        load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
+        __syncthreads();
+        for (int c = threadIdx.x; c < 1000; c += kCrossT) {
+            const int32_t idx = halo_index(c, nb);
+            uint32_t pc = kNone;
+            if (idx >= 0) {
+                const float4 a = rec[idx];
+                if (__float_as_int(a.w) >= want) {
+                    sA[c] = a;
+                    sB[c] = rec[stride + idx];
+                    pc = __ldcg(parent + idx);
+                }
+            }
+            sP[c] = pc;
         }
-        __syncwarp();
-        for (int l = lane; l < kBrickVox; l += 32) {
+        __syncthreads();
+        unsigned long long last = ~0ull;
+        for (int l = threadIdx.x; l < kBrickVox; l += kCrossT) {
             const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
             if (!((lx == 0) | (lx == 7) | (ly == 0) | (ly == 7) | (lz == 7))) continue;
-            const size_t o = (size_t)r * kBrickVox + l;
-            const float4 a = rec[o];
-            if (__float_as_int(a.w) < want) continue;
-            const float4 an = rec[stride + o];
+            const int c0 = ((lz + 1) * 10 + ly + 1) * 10 + lx + 1;
+            const uint32_t pa = sP[c0];
+            if (pa == kNone) continue;
+            const float4 a = sA[c0], an = sB[c0];
             for (int k = 0; k < 13; ++k) {
                 int dz, dy, dx;
                 fwd_offset(k, dz, dy, dx);
                 const int x = lx + dx, y = ly + dy, z = lz + dz;
                 if (x >= 0 && x <= 7 && y >= 0 && y <= 7 && z <= 7) continue;  // inside the brick: done already
-                const int bdx = x < 0 ? -1 : (x > 7 ? 1 : 0), bdy = y < 0 ? -1 : (y > 7 ? 1 : 0), bdz = z > 7 ? 1 : 0;
-                const int32_t rk = nb[(bdz + 1) * 9 + (bdy + 1) * 3 + (bdx + 1)];
-                if (rk < 0) continue;
-                const size_t j = (size_t)rk * kBrickVox + (((z - 8 * bdz) * 8 + (y - 8 * bdy)) * 8 + (x - 8 * bdx));
-                const float4 b = rec[j];
-                if (__float_as_int(b.w) < want) continue;
-                const float4 bn = rec[stride + j];
-                if (ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
-                    uf_union(parent, (uint32_t)o, (uint32_t)j, err);
+                const int c = c0 + dz * 100 + dy * 10 + dx;
+                const uint32_t pb = sP[c];
+                if (pb == kNone || pb == pa) continue;
+                const float4 b = sA[c], bn = sB[c];
+                if (!ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
+                    continue;
+                const uint32_t lo = pa < pb ? pa : pb, hi = pa < pb ? pb : pa;
+                const unsigned long long key = ((unsigned long long)lo << 32) | hi;
+                if (key == last) continue;
+                last = key;
+                uint32_t h = (lo * 2654435761u ^ hi * 40503u) & (kPairSlots - 1);
+                bool placed = false;
+                for (int probe = 0; probe < kPairSlots; ++probe) {
+                    const unsigned long long prev = atomicCAS(&set[h], ~0ull, key);
+                    if (prev == ~0ull || prev == key) { placed = true; break; }
+                    h = (h + 1) & (kPairSlots - 1);
+                }
+                if (!placed) uf_union(parent, lo, hi, err);  // set full: join directly
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < kPairSlots; q += kCrossT) {
+            const unsigned long long key = set[q];
+            if (key != ~0ull) {
+                uf_union(parent, (uint32_t)(key >> 32), (uint32_t)key, err);
+                set[q] = ~0ull;
             }
         }
     }
@@ -452,15 +491,17 @@ __device__ __forceinline__ uint32_t uf_root(const uint32_t* P, uint32_t x, uint3
 
 // Pointer jumping to the root: afterwards parent[i] is the component's
 // smallest index (its label) for every vertex.
-__global__ void k_ccl_compress(size_t nv, uint32_t* parent, uint32_t* err) {
+__global__ void k_ccl_compress(const uint32_t* __restrict__ nsp, uint32_t cap_b, uint32_t* parent, uint32_t* err) {
+    const size_t nv = (size_t)min(*nsp, cap_b) * kBrickVox;
     for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
         if (parent[i] != kNone) parent[i] = uf_root(parent, (uint32_t)i, err);
     }
 }
 
 // Component sizes: warps aggregate equal roots before the atomic.
-__global__ void k_count(size_t nv, const uint32_t* __restrict__ parent, uint32_t* __restrict__ count,
+__global__ void k_count(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent, uint32_t* __restrict__ count,
                         SegCounters* __restrict__ ctr) {
+    const size_t nv = (size_t)min(*nsp, cap_b) * kBrickVox;
     uint32_t nvert = 0;
     for (size_t base = ((size_t)blockIdx.x * kT + threadIdx.x) & ~(size_t)31; base < nv;
          base += (size_t)gridDim.x * kT) {
@@ -477,42 +518,100 @@ __global__ void k_count(size_t nv, const uint32_t* __restrict__ parent, uint32_t
     if ((threadIdx.x & 31) == 0 && nvert) atomicAdd(&ctr->n_vert, nvert);
 }
 
-__global__ void k_keep_flags(size_t nv, const uint32_t* __restrict__ parent, const uint32_t* __restrict__ count,
-                             uint32_t min_cluster, uint32_t* __restrict__ root_flag, uint32_t* __restrict__ vert_flag) {
-    for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
-        const uint32_t p = parent[i];
-        const bool kept = (p != kNone) && count[p] >= min_cluster;
-        vert_flag[i] = kept;
-        root_flag[i] = kept && p == (uint32_t)i;
-    }
-}
-
 __device__ __forceinline__ uint32_t vid_of(size_t idx, const int32_t* __restrict__ sorted_key) {
     return (uint32_t)sorted_key[idx / kBrickVox] * kBrickVox + (uint32_t)(idx % kBrickVox);
 }
 
-__global__ void k_compact(size_t nv, const uint32_t* __restrict__ parent, const uint32_t* __restrict__ count,
-                          uint32_t min_cluster, const uint32_t* __restrict__ cid, const uint32_t* __restrict__ vpos,
-                          const int32_t* __restrict__ sorted_key, uint32_t* __restrict__ keys,
-                          uint32_t* __restrict__ vals, uint32_t* __restrict__ cl_size,
-                          uint32_t* __restrict__ cl_label) {
-    for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
+// Cluster formation, one 512-thread CTA per brick, one voxel per thread in
+// index order.  A vertex is kept when its component has at least min_cluster
+// vertices; its root is the component's smallest index.
+// Block-wide exclusive count of a per-thread flag (thread order = index order).
+__device__ __forceinline__ uint32_t brick_rank(bool f, uint32_t* wcnt, uint32_t* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wcnt[w] = __popc(bal);
+    __syncthreads();
+    uint32_t pre = 0, tot = 0;
+    for (int q = 0; q < kBrickVox / 32; ++q) {
+        const uint32_t c = wcnt[q];
+        pre += (q < w) ? c : 0u;
+        tot += c;
+    }
+    __syncthreads();
+    *total = tot;
+    return pre + __popc(bal & ((1u << lane) - 1u));
+}
+
+// (1) per-brick counts of kept vertices and of kept roots;
+__global__ void __launch_bounds__(kBrickVox) k_brick_tally(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent,
+                                                           const uint32_t* __restrict__ count, uint32_t min_cluster,
+                                                           uint32_t* __restrict__ nvert, uint32_t* __restrict__ nroot) {
+    const uint32_t n_sorted = min(*nsp, cap_b);
+    __shared__ uint32_t wc[kBrickVox / 32];
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        const size_t i = (size_t)r * kBrickVox + threadIdx.x;
         const uint32_t p = parent[i];
-        if (p == kNone || count[p] < min_cluster) continue;
-        const uint32_t c = cid[p];
-        keys[vpos[i]] = c;
-        vals[vpos[i]] = (uint32_t)i;
-        if (p == (uint32_t)i) {
-            cl_size[c] = count[i];
-            cl_label[c] = vid_of(i, sorted_key);
+        const bool kept = p != kNone && count[p] >= min_cluster;
+        uint32_t tv, tr;
+        brick_rank(kept, wc, &tv);
+        brick_rank(kept && p == (uint32_t)i, wc, &tr);
+        if (threadIdx.x == 0) { nvert[r] = tv; nroot[r] = tr; }
+    }
+}
+
+// (2) kept roots numbered in index order (= label order): cluster sizes and labels;
+__global__ void __launch_bounds__(kBrickVox) k_brick_roots(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent,
+                                                           const uint32_t* __restrict__ count, uint32_t min_cluster,
+                                                           const uint32_t* __restrict__ rbase,
+                                                           const int32_t* __restrict__ sorted_key,
+                                                           uint32_t* __restrict__ cid, uint32_t* __restrict__ cl_size,
+                                                           uint32_t* __restrict__ cl_label, uint32_t kcap) {
+    const uint32_t n_sorted = min(*nsp, cap_b);
+    __shared__ uint32_t wc[kBrickVox / 32];
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        const size_t i = (size_t)r * kBrickVox + threadIdx.x;
+        const uint32_t p = parent[i];
+        const bool root = p == (uint32_t)i && count[p] >= min_cluster;
+        uint32_t t;
+        const uint32_t rank = brick_rank(root, wc, &t);
+        if (root) {
+            const uint32_t c = rbase[r] + rank;
+            cid[i] = c;
+            if (c < kcap) {
+                cl_size[c] = count[i];
+                cl_label[c] = vid_of(i, sorted_key);
+            }
+        }
+    }
+}
+
+// (3) kept vertices compacted in index order as (cluster, index) pairs.
+__global__ void __launch_bounds__(kBrickVox) k_brick_verts(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent,
+                                                           const uint32_t* __restrict__ count, uint32_t min_cluster,
+                                                           const uint32_t* __restrict__ vbase,
+                                                           const uint32_t* __restrict__ cid,
+                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const uint32_t n_sorted = min(*nsp, cap_b);
+    __shared__ uint32_t wc[kBrickVox / 32];
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        const size_t i = (size_t)r * kBrickVox + threadIdx.x;
+        const uint32_t p = parent[i];
+        const bool kept = p != kNone && count[p] >= min_cluster;
+        uint32_t t;
+        const uint32_t rank = brick_rank(kept, wc, &t);
+        if (kept) {
+            const uint32_t pos = vbase[r] + rank;
+            keys[pos] = cid[p];
+            vals[pos] = (uint32_t)i;
         }
     }
 }
 
 // Cluster points in cluster order: mean positions and voxel ids.
-__global__ void k_gather(uint32_t n, const uint32_t* __restrict__ vals, const int32_t* __restrict__ M, size_t stride,
+__global__ void k_gather(const uint32_t* __restrict__ np, const uint32_t* __restrict__ vals, const int32_t* __restrict__ M, size_t stride,
                          const int32_t* __restrict__ sorted_key, Grid g, float* __restrict__ pts,
                          uint32_t* __restrict__ pt_vid) {
+    const uint32_t n = *np;
     for (uint32_t p = blockIdx.x * kT + threadIdx.x; p < n; p += gridDim.x * kT) {
         const uint32_t i = vals[p];
         pts[3 * (size_t)p + 0] = __fadd_rn(g.ox, __fmul_rn(__int2float_rn(M[i]), kInvQ));
@@ -543,55 +642,69 @@ cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegB
     return cudaGetLastError();
 }
 
-cudaError_t seg_voxels(const Grid& g, uint32_t n_sorted, const unsigned long long* S, const uint32_t* C,
-                       const vm_segment_params& p, SegBuffers& b, uint32_t* err, int sms, cudaStream_t s,
-                       StageHook* hk) {
-    if (n_sorted == 0) return cudaSuccess;
-    const size_t nv = (size_t)n_sorted * kBrickVox;
+// Flags a segmentation whose brick or cluster count exceeds the scratch it was
+// launched with; the kernels clamp to the scratch, the host regrows and reruns.
+__global__ void k_seg_guard(SegCounters* __restrict__ ctr, uint32_t cap_b) {
+    if (ctr->n_sorted > cap_b) ctr->err |= kErrScratch;
+}
+__global__ void k_seg_guard_k(SegCounters* __restrict__ ctr, uint32_t kcap) {
+    if (ctr->k > kcap) {
+        ctr->err |= kErrScratch;
+        ctr->k = kcap;
+    }
+}
+__global__ void k_set_end_u32(uint32_t* __restrict__ arr, const uint32_t* __restrict__ kp,
+                              const uint32_t* __restrict__ v) {
+    arr[*kp] = *v;
+}
+
+cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* C, const vm_segment_params& p,
+                    SegBuffers& b, uint32_t kcap, uint32_t* err, int sms, cudaStream_t s, StageHook* hk) {
+    const uint32_t cap_b = (uint32_t)(b.nv / kBrickVox);
     const size_t stride = b.nv;
-    const unsigned bricks_grid = (unsigned)(n_sorted < (uint32_t)sms * 4 ? n_sorted : (uint32_t)sms * 4);
+    const uint32_t* nsp = &b.ctr->n_sorted;
+    const auto clampg = [&](uint32_t want, uint32_t mx) { return want < mx ? (want ? want : 1u) : mx; };
+    k_seg_guard<<<1, 1, 0, s>>>(b.ctr, cap_b);
     VM_STAGE_BEGIN(hk, kStFinalize, s);
-    k_finalize<<<bricks_grid, kT, 0, s>>>(n_sorted, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
+    k_finalize<<<clampg(cap_b, sms * 4), kT, 0, s>>>(nsp, cap_b, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
     VM_STAGE_END(hk, kStFinalize, s);
     const uint8_t want = p.classify ? 2 : 1;
     VM_STAGE_BEGIN(hk, kStNormals, s);
-    const unsigned norm_grid = (unsigned)(n_sorted < (uint32_t)sms * 8 ? n_sorted : (uint32_t)sms * 8);
-    k_normals<<<norm_grid, kNormT, 0, s>>>(n_sorted, g, b.sorted_key, b.rank_table, b.M, b.nrm, b.status, b.nbr,
-                                          b.parent, b.count, b.rec, stride, p.n_th, p.cos_step, want, p.d_th2,
-                                          p.cos_ccl, err);
+    k_normals<<<clampg(cap_b, sms * 8), kNormT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.M, b.nrm, b.status,
+                                                         b.nbr, b.parent, b.count, b.rec, stride, p.n_th, p.cos_step,
+                                                         want, p.d_th2, p.cos_ccl, err);
     VM_STAGE_END(hk, kStNormals, s);
     VM_STAGE_BEGIN(hk, kStCcl, s);
-    const unsigned cross_grid = (unsigned)((n_sorted + 7) / 8 < (uint32_t)sms * 8 ? (n_sorted + 7) / 8 : (uint32_t)sms * 8);
-    k_ccl_cross<<<cross_grid, 256, 0, s>>>(n_sorted, g, b.sorted_key, b.rank_table, b.rec, b.parent, stride, want,
-                                            p.d_th2, p.cos_ccl, err);
-    k_ccl_compress<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, err);
+    k_ccl_cross<<<clampg(cap_b, sms * 8), kCrossT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.rec, b.parent,
+                                                            stride, want, p.d_th2, p.cos_ccl, err);
+    k_ccl_compress<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, err);
     VM_STAGE_END(hk, kStCcl, s);
-    count_launch(4);
+    count_launch(5);
     VM_STAGE_BEGIN(hk, kStClusters, s);
-    k_count<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, b.count, b.ctr);
+    k_count<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, b.count, b.ctr);
     const uint32_t min_cl = p.min_cluster ? p.min_cluster : 1u;
-    k_keep_flags<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, b.count, min_cl, b.cid, b.vert_flag);
-    cudaError_t e = exclusive_scan_u32(b.cid, b.cid, &b.ctr->k, nv, b.scan_tmp, s);
+    uint32_t* nvert = b.flags;      // per-brick tallies: flags reused for kept vertices,
+    uint32_t* nroot = b.vert_flag;  // vert_flag for kept roots
+    const unsigned bgrid = clampg(cap_b, sms * 4);
+    k_brick_tally<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot);
+    cudaError_t e = exclusive_scan_dev(nroot, nroot, &b.ctr->k, nsp, cap_b, b.scan_tmp, s);
     if (e != cudaSuccess) return e;
-    e = exclusive_scan_u32(b.vert_flag, b.vert_flag, &b.ctr->n_kept, nv, b.scan_tmp, s);
+    e = exclusive_scan_dev(nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp, s);
     if (e != cudaSuccess) return e;
-    k_compact<<<grid_for(nv, sms), kT, 0, s>>>(nv, b.parent, b.count, min_cl, b.cid, b.vert_flag, b.sorted_key,
-                                               b.keys, b.vals, b.cl_size, b.cl_label);
-    VM_STAGE_END(hk, kStClusters, s);
-    count_launch(3);
-    return cudaGetLastError();
-}
-
-cudaError_t seg_clusters(const Grid& g, uint32_t k, uint32_t n_kept, SegBuffers& b, int sms, cudaStream_t s) {
-    if (k == 0) return cudaSuccess;
+    k_brick_roots<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nroot, b.sorted_key, b.cid,
+                                               b.cl_size, b.cl_label, kcap);
+    k_seg_guard_k<<<1, 1, 0, s>>>(b.ctr, kcap);
+    k_brick_verts<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nvert, b.cid, b.keys, b.vals);
     int bits = 1;
-    while ((1u << bits) < k && bits < 32) ++bits;
-    cudaError_t e = stable_sort_pairs_u32(b.keys, b.vals, b.keys_alt, b.vals_alt, n_kept, bits, b.scan_tmp, s);
+    while ((1ull << bits) < kcap && bits < 32) ++bits;
+    e = stable_sort_pairs_dev(b.keys, b.vals, b.keys_alt, b.vals_alt, &b.ctr->n_kept, b.nv, bits, b.scan_tmp, s);
     if (e != cudaSuccess) return e;
-    e = exclusive_scan_u32(b.cl_size, b.cl_off, b.cl_off + k, k, b.scan_tmp, s);
+    e = exclusive_scan_dev(b.cl_size, b.cl_off, &b.ctr->tot, &b.ctr->k, kcap, b.scan_tmp, s);
     if (e != cudaSuccess) return e;
-    k_gather<<<grid_for(n_kept, sms), kT, 0, s>>>(n_kept, b.vals, b.M, b.nv, b.sorted_key, g, b.pts, b.pt_vid);
-    count_launch(1);
+    k_set_end_u32<<<1, 1, 0, s>>>(b.cl_off, &b.ctr->k, &b.ctr->tot);
+    k_gather<<<grid_for(b.nv, sms), kT, 0, s>>>(&b.ctr->n_kept, b.vals, b.M, b.nv, b.sorted_key, g, b.pts, b.pt_vid);
+    VM_STAGE_END(hk, kStClusters, s);
+    count_launch(9);
     return cudaGetLastError();
 }
 

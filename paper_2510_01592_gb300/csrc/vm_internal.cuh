@@ -25,6 +25,7 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kErrCapacity = 1u;
 constexpr uint32_t kErrTimeout = 2u;
 constexpr uint32_t kErrOverflow = 4u;
+constexpr uint32_t kErrScratch = 8u;   // counts exceeded the scratch the work was launched with
 
 // Iteration cap of every device retry loop (union-find, work queues).
 constexpr int kLoopCap = 1 << 22;
@@ -59,7 +60,11 @@ struct SegCounters {
     uint32_t k;          // kept clusters
     uint32_t n_hull;     // hull vertices
     uint32_t err;        // error bits
-    uint32_t pad;
+    uint32_t tot;        // scan total scratch
+    uint32_t n_bricks;   // bricks allocated in the pool (copied at the end)
+    uint32_t map_err;    // map error bits (copied at the end)
+    uint32_t fit_err;    // fit error bits (copied at the end)
+    uint32_t pad[5];
 };
 
 // Per-cluster fit state on the device.
@@ -146,6 +151,12 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* tota
                                cudaStream_t s);
 // Stable sort of (key, value) pairs by key, key < 2^bits (bits <= 32), LSD
 // 8-bit digits.  keys/vals are sorted in place using the alt buffers.
+// Variants whose element count is read on the device from n_dev (clamped to
+// the host bound n_cap, which sizes the grids): usable inside a CUDA graph.
+cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
+                               uint32_t* tmp, cudaStream_t s);
+cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                                  const uint32_t* n_dev, size_t n_cap, int bits, uint32_t* tmp, cudaStream_t s);
 size_t sort_tmp_words(size_t n);
 cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
                                   int bits, uint32_t* tmp, cudaStream_t s);
@@ -191,13 +202,14 @@ struct SegBuffers {
 // Orders the allocated bricks by key (rank table, sorted slots/keys); the
 // brick count lands in b.ctr->n_sorted.
 cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s);
-// Means, normals, classification, union-find clustering, cluster numbering and
-// compaction of kept vertices for n_sorted bricks.
-cudaError_t seg_voxels(const Grid& g, uint32_t n_sorted, const unsigned long long* S, const uint32_t* C,
-                       const vm_segment_params& p, SegBuffers& b, uint32_t* err, int sms, cudaStream_t s,
-                       StageHook* hk);
-// Stable sort of kept vertices by cluster, cluster offsets, point gather.
-cudaError_t seg_clusters(const Grid& g, uint32_t k, uint32_t n_kept, SegBuffers& b, int sms, cudaStream_t s);
+// Means, normals, classification, clustering, cluster numbering, the cluster
+// point lists in cluster order and their offsets, for the bricks ordered by
+// seg_order_bricks.  Every count is read on the device (clamped to the
+// scratch, with kErrScratch raised when it does not fit), so the launch
+// sequence is fixed and can be captured in a CUDA graph.  kcap bounds the
+// kept clusters.
+cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* C, const vm_segment_params& p,
+                    SegBuffers& b, uint32_t kcap, uint32_t* err, int sms, cudaStream_t s, StageHook* hk);
 
 // ---------------------------------------------------------------- fit.cu
 struct FitBuffers {
@@ -215,6 +227,8 @@ struct FitBuffers {
     uint32_t* hull_cnt;     // [kcap + 1] -> hull offsets (scan)
     uint32_t* scan_tmp;
     uint32_t* err;          // device error word
+    uint32_t* tot;          // [4] scan totals
+    uint32_t* kdev;         // cluster count when the caller supplies it
     size_t kcap, npts_cap, items_cap;
     int H;
 };
@@ -227,16 +241,22 @@ struct FitTuning {
 FitTuning default_tuning();
 size_t fit_hull_smem();
 
-// Runs RANSAC, selection, extraction, refit and hull for k clusters whose
+// Runs RANSAC, selection, extraction, refit and hull for the clusters whose
 // points are pts[off[c]..off[c+1]) (device), labels (device, or nullptr for
-// label = c).  k and npts are host values.  Produces per-cluster records in
-// fb.cl and hull vertices in fb.hull / fb.hull_cnt (offsets after the scan).
-cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, uint32_t k, uint32_t npts,
-                       const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int num_sms, cudaStream_t s,
-                       StageHook* hk);
+// label = c).  The cluster count is read on the device from *kp (at most
+// kcap, which sizes the grids), so the launch sequence is fixed and can be
+// captured in a CUDA graph.  Per-cluster records land in fb.cl, hull vertices
+// in fb.hull at each cluster's point offset and their offsets in fb.hull_cnt.
+void fit_init_attributes();
+cudaError_t fit_set_count(uint32_t* kdev, uint32_t k, cudaStream_t s);
+cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
+                       uint32_t kcap, const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int num_sms,
+                       cudaStream_t s, StageHook* hk);
 
-// Packs vm_plane records, hull_xy and hull_xyz into device staging buffers.
-cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, uint32_t k,
-                        vm_plane* planes, int32_t* hull_xy, float* hull_xyz, cudaStream_t s);
+// Packs vm_plane records and hull arrays (at most hull_cap vertices) for the
+// *kp clusters; the destinations may be mapped host memory.
+cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
+                        uint32_t kcap, vm_plane* planes, int32_t* hull_xy, float* hull_xyz, uint32_t hull_cap,
+                        cudaStream_t s);
 
 }  // namespace vmx

@@ -23,6 +23,7 @@ _lock = threading.Lock()
 _lib = None
 
 VM_MAP_STAGE_TIMING = 1
+VM_MAP_EAGER = 2
 N_STAGES = 16  # upper bound of the library's stage count
 
 VM_OK, VM_ERR_INVALID_ARG, VM_ERR_OUT_OF_MEMORY, VM_ERR_CAPACITY, VM_ERR_CUDA, VM_ERR_TIMEOUT, VM_ERR_EXTENT = range(7)
@@ -166,10 +167,13 @@ def _stream_handle(stream):
 class VoxelMap:
     """A device-resident voxel map (Sec. III.B) with multi-plane segmentation (Sec. III.C)."""
 
-    def __init__(self, dims, origin, voxel_size, brick_capacity=0, stream=None, stage_timing=False):
+    def __init__(self, dims, origin, voxel_size, brick_capacity=0, stream=None, stage_timing=False, eager=False):
+        """eager: launch the segmentation kernel by kernel instead of replaying a
+        captured CUDA graph (stage timing implies eager launches)."""
         L = load()
+        flags = (VM_MAP_STAGE_TIMING if stage_timing else 0) | (VM_MAP_EAGER if eager else 0)
         p = vm_map_params((C.c_float * 3)(*[float(o) for o in origin]), (C.c_int32 * 3)(*[int(d) for d in dims]),
-                          float(voxel_size), int(brick_capacity), VM_MAP_STAGE_TIMING if stage_timing else 0)
+                          float(voxel_size), int(brick_capacity), flags)
         h = C.c_void_p()
         self._stream = stream
         _check(L.vm_create(C.byref(p), _stream_handle(stream), C.byref(h)))

@@ -205,3 +205,24 @@ def test_fit_planes_hull_gift_wrapping_path(orc, vmmod):
     gres = vmmod.fit_planes(torch.from_numpy(pts).cuda(), torch.from_numpy(off).cuda(), gp)
     compare_planes(gres, ores)
     assert gres["planes"]["hull_count"][0] > 1000  # ~6000 candidates: beyond the 2048-entry sort
+
+
+def test_graph_and_eager_launches_agree_on_a_growing_map(orc, vmmod):
+    """The captured-graph segmentation and the kernel-by-kernel one give the same
+    result frame after frame while the map grows past the scratch it was sized
+    for (the regrow-and-retry path), and both match the oracle."""
+    spec = synth.config2_spec()
+    scene = synth.config2_scene()
+    mg = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size)
+    me = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size, eager=True)
+    om = orc.OracleMap(spec.dims, spec.origin, spec.voxel_size)
+    op, gp = _params_pair(orc, vmmod, n_hyp=64, seed=3)
+    for f in range(20, 40, 2):
+        pts, pose = synth.config2_frame(f, scene, device="cuda")
+        mg.integrate(pts, pose)
+        me.integrate(pts, pose)
+        om.integrate(pts.cpu().numpy(), pose)
+        rg, re_ = mg.segment(gp), me.segment(gp)
+        for key in ("planes", "hull_xy", "hull_xyz"):
+            assert np.array_equal(rg[key], re_[key]), key
+    compare_planes(rg, om.segment(op), mg.export_clusters())
