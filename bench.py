@@ -32,6 +32,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N_FRAMES = 300
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per allocated
+# brick, from one ncu capture of each kernel as it stands on the 60-frame case
+# of the trajectory (1,498 bricks; profiles/segment_kernels_60frames.md).  A
+# launch stages a fixed halo per brick, so traffic is scaled to the timed map by
+# its brick count.  Remove a kernel's entry when the kernel changes.
+TRAFFIC_PER_BRICK = {
+    "moments": 9288192.0 / 1498,
+    "eigen": (4122112.0 + 47872.0) / 1498,
+    "ccl_cross": (15159040.0 + 256.0) / 1498,
+}
 METRIC = "0.01 m integrate+segment: frames/s, p50/p99 ms, batched/served vs plain GPU"
 WORKLOAD = ("paper-scale trajectory: 4x4x2 m map at 0.01 m (sparse 8^3 bricks), 640x480 depth camera "
             "(87x58 deg, 0.3-4 m, sigma 1 mm + 0.2% range) over an 8-step open-tread stair, overhanging desk, "
@@ -312,41 +322,71 @@ def run_gpu(args):
                      "note": "graph: each segment call replays one captured CUDA graph of the whole device-driven "
                              "pipeline; plain: the same kernels launched one by one"},
         "map": {"occupied_voxels": st["occupied_voxels"], "steppable_voxels": st["steppable_voxels"],
+                "clustered_points": st["clustered_points"], "clusters": st["clusters"],
                 "bricks": st["bricks_allocated"], "device_bytes": st["device_bytes"]},
     }
     if clocks:
         res["clocks"] = clocks
     res["stages_ms_per_step"] = {k: round(v[0] / max(1, args.steps), 4) for k, v in stages.items() if v[1]}
-    res["roofline"] = roofline(stages, st, args.steps, spec)
+    table = kernel_table(stages, st, load_peaks(), st["clustered_points"])
+    res["kernels"] = table
+    res["roofline"] = roofline(table, {k: v * st["bricks_allocated"] for k, v in TRAFFIC_PER_BRICK.items()})
     return res, rank
 
 
-def roofline(stages, st, steps, spec):
-    """Dominant stage's achieved rate against the measured peak (see the design doc
-    for the algorithmic bytes / ops per unit of each kernel)."""
-    peaks = load_peaks()
+# FP32 lanes x clock: one instruction per lane per cycle on 152 SMs x 128 lanes
+SM_COUNT, FP32_LANES = 152, 128
+
+
+def kernel_table(stages, st, peaks, n_points_segment):
+    """Per-stage average launch time and, for single-kernel stages, the achieved
+    rate against the measured peak.  Algorithmic bytes / ops per unit:
+    slots = allocated bricks x 512 voxels, occ = occupied voxels."""
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    timed = {k: v[0] / max(1, v[1]) for k, v in stages.items() if v[1]}
-    if not timed:
-        return None
-    dom = max(timed, key=lambda k: stages[k][0])
+    clk = (peaks or {}).get("sm_max_mhz", 2070.0) * 1e6
+    alu_peak = SM_COUNT * FP32_LANES * clk / 1e12  # T instructions/s
     occ = st["occupied_voxels"]
     slots = st["bricks_allocated"] * 512
-    # algorithmic bytes per launch of each HBM-bound stage
-    algo = {
-        "finalize": slots * (4 + 1 + 12) + occ * 24,            # counts, status, means out; sums of occupied in
-        "normals": occ * (12 + 12 + 2) + slots * 1,             # means in, normals + status/N out, status probe
-        "ccl": occ * (24 + 4) + slots * (1 + 4 + 4),            # means+normals of vertices, parents init/compress
-        "order_bricks": 0,
+    model = {
+        "finalize": ("hbm", slots * (4 + 1 + 12) + occ * 24),
+        "moments": ("hbm", slots * (12 + 16) + occ * (4 + 24 + 1)),
+        "eigen": ("alu", occ * 520),
+        "ccl_local": ("hbm", slots * (16 + 8) + occ * 16),
+        "ccl_cross": ("hbm", slots * (16 + 4) + occ * 16),
+        "ransac_score": ("alu", n_points_segment * 100 * 5),
     }
-    ms = timed[dom]
-    if dom in algo and algo[dom]:
-        ach = algo[dom] / (ms / 1e3) / 1e9
-        return {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"
-                if peaks else "fallback 6800 GB/s", "avg_launch_ms": round(ms, 4)}
-    return {"kernel": dom, "bound": "latency", "avg_launch_ms": round(ms, 4), "achieved": None, "peak": None,
-            "unit": None, "frac": None, "traffic": None}
+    out = {}
+    for name, (ms_tot, calls) in stages.items():
+        if not calls:
+            continue
+        ms = ms_tot / calls
+        row = {"avg_launch_ms": round(ms, 4)}
+        if name in model:
+            bound, amount = model[name]
+            if bound == "hbm":
+                ach = amount / (ms / 1e3) / 1e9
+                row.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s", frac=round(ach / hbm, 4),
+                           algorithmic=int(amount))
+            else:
+                ach = amount / (ms / 1e3) / 1e12
+                row.update(bound="alu", achieved=round(ach, 3), peak=round(alu_peak, 1), unit="T instr/s",
+                           frac=round(ach / alu_peak, 4), algorithmic=int(amount))
+        out[name] = row
+    return out
+
+
+def roofline(table, traffic=None):
+    """The dominant single-kernel stage's row (a stage of one kernel)."""
+    single = {k: v for k, v in table.items() if "bound" in v}
+    if not single:
+        return None
+    dom = max(single, key=lambda k: single[k]["avg_launch_ms"])
+    r = dict(single[dom])
+    r["kernel"] = dom
+    t = (traffic or {}).get(dom)
+    r["traffic"] = None if t is None else int(t)
+    r["peak_source"] = "MEASURED_PEAKS.json" if load_peaks() else "fallback"
+    return r
 
 
 def cpu_baseline(budget_s):

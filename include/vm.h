@@ -107,7 +107,7 @@ typedef struct {
     uint32_t occupied_voxels;    /* at the last segmentation                      */
     uint32_t steppable_voxels;   /* at the last segmentation                      */
     uint32_t clusters;           /* kept clusters at the last segmentation        */
-    uint32_t reserved;
+    uint32_t clustered_points;   /* points in kept clusters at the last segmentation */
     uint64_t device_bytes;       /* device memory held by the map                 */
 } vm_stats;
 
@@ -216,8 +216,9 @@ vm_status vm_export_clusters(vm_map* map, float* pts, uint32_t* vid, uint8_t* in
 
 /* Diagnostics (no counterpart in the paper).  Stage timing records CUDA
  * events around each pipeline stage on the stream it runs on: integrate,
- * order_bricks, finalize, normals, ccl, clusters, ransac_hyp, ransac_score,
- * extract, refit_hull, pack (vm_stage_name gives the names).
+ * order_bricks, finalize, moments, eigen, ccl_local, ccl_cross, clusters,
+ * ransac_hyp, ransac_score, extract, refit_hull, pack (vm_stage_name gives the
+ * names).
  * vm_stage_timing: enable (1) or disable (0) for a map, or for this thread's
  * vm_fit_planes calls when map is NULL.  vm_stage_times: device milliseconds
  * and call counts per stage accumulated since the previous call (then reset);

@@ -19,9 +19,9 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
-static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "finalize", "normals", "ccl",
-                                              "clusters", "ransac_hyp", "ransac_score", "extract", "refit_hull",
-                                              "pack"};
+static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "finalize", "moments", "eigen",
+                                              "ccl_local", "ccl_cross", "clusters", "ransac_hyp", "ransac_score",
+                                              "extract", "refit_hull", "pack"};
 
 // CUDA-event stage timer: begin/end record events on the stream; elapsed times
 // are folded in once the events have completed (at the next sync point).
@@ -363,6 +363,8 @@ vm_status alloc_vox(vm_map* m, uint32_t n_bricks) {
         b.status = c.take<uint8_t>(nv);
         b.nbr = c.take<uint8_t>(nv);
         b.rec = c.take<float4>(2 * nv);
+        b.list_idx = c.take<uint32_t>(nv);
+        b.list_A = c.take<float>(6 * nv);
         b.parent = c.take<uint32_t>(nv);
         b.count = c.take<uint32_t>(nv);
         b.cid = c.take<uint32_t>(nv + 1);
@@ -785,6 +787,7 @@ vm_status vm_get_stats(vm_map* m, vm_stats* out) {
     out->occupied_voxels = m->last.n_occ;
     out->steppable_voxels = m->last.n_vert;
     out->clusters = m->last.k;
+    out->clustered_points = m->last.n_kept;
     out->device_bytes = m->pool.bytes + m->stage.bytes + m->brick_mem.bytes + m->vox_mem.bytes + m->fit.mem.bytes +
                         m->fit.out.bytes;
     (void)0;

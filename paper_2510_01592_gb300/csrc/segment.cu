@@ -250,35 +250,28 @@ __device__ __forceinline__ void fwd_offset(int k, int& dz, int& dy, int& dx) {
     dx = (k < 9) ? (k % 3 - 1) : ((k < 12) ? (k - 9 - 1) : 1);
 }
 
-// Eq. 3 / Eq. 4 and the intra-brick half of Algorithm 1, one 128-thread CTA
-// per brick.  The brick and a one-voxel halo of integer means are staged in
-// shared memory; the brick's occupied voxels are compacted into a list so
-// their work is spread over all four warps.
-// Normals: covariance of the 3x3x3 window of mean positions (self included)
-// as the exact integer matrix N' sum(dd^T) - (sum d)(sum d)^T of offsets
-// d = M_j - M_i, rounded to FP32; normal by Jacobi (6 sweeps); steppable iff
-// N >= n_th and |n_z| >= cos_step.  Clustering: the brick's vertices are
-// joined over edges inside the brick with a union-find in shared memory; the
-// global parent of each vertex is set to its local root (the smallest index of
-// its in-brick component).  Edges that leave the brick follow in k_ccl_cross.
+// Eq. 3 / Eq. 4 in two kernels.
+// k_moments, one 128-thread CTA per brick: the brick and a one-voxel halo of
+// integer means are staged in shared memory; for every occupied voxel the
+// window moments give the covariance of the 3x3x3 window of mean positions
+// (self included) as the exact integer matrix N' sum(dd^T) - (sum d)(sum d)^T
+// of offsets d = M_j - M_i, rounded to FP32.  Occupied voxels go to a flat
+// list (A, N, voxel index) for k_eigen; every voxel's record gets its mean
+// (status filled in by k_eigen; zero for free voxels).
 constexpr int kNormT = 128;
-__global__ void __launch_bounds__(kNormT) k_normals(const uint32_t* __restrict__ nsp, uint32_t cap_b, Grid g, const int32_t* __restrict__ sorted_key,
+__global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__ nsp, uint32_t cap_b, Grid g,
+                                                    const int32_t* __restrict__ sorted_key,
                                                     const int32_t* __restrict__ rank_table,
-                                                    const int32_t* __restrict__ M, float* __restrict__ nrm,
-                                                    uint8_t* __restrict__ status, uint8_t* __restrict__ nbr,
-                                                    uint32_t* __restrict__ parent, uint32_t* __restrict__ count,
-                                                    float4* __restrict__ rec, size_t stride, uint32_t n_th,
-                                                    float cos_step, uint8_t want, float d_th2, float cos_ccl,
-                                                    uint32_t* err) {
+                                                    const int32_t* __restrict__ M, float4* __restrict__ rec,
+                                                    uint32_t* __restrict__ list_idx, float* __restrict__ list_A,
+                                                    uint8_t* __restrict__ nbr, size_t stride,
+                                                    SegCounters* __restrict__ ctr) {
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ int32_t sM[3][1000];
-    __shared__ float sMu[3][512];
-    __shared__ float sN[3][512];
-    __shared__ uint32_t lpar[512];
     __shared__ uint16_t list[512];
-    __shared__ uint8_t sSt[512];
     __shared__ int32_t nb[27];
     __shared__ int n_list;
+    __shared__ uint32_t gbase;
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
         __syncthreads();
         if (threadIdx.x == 0) n_list = 0;
@@ -297,11 +290,19 @@ __global__ void __launch_bounds__(kNormT) k_normals(const uint32_t* __restrict__
         __syncthreads();
         for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
             const int c0 = (((l >> 6) + 1) * 10 + ((l >> 3) & 7) + 1) * 10 + (l & 7) + 1;
-            sSt[l] = 0;
-            if (sM[0][c0] != INT_MIN) list[atomicAdd(&n_list, 1)] = (uint16_t)l;
+            const size_t o = (size_t)r * kBrickVox + l;
+            if (sM[0][c0] != INT_MIN) {
+                list[atomicAdd(&n_list, 1)] = (uint16_t)l;
+                rec[o] = make_float4(mean_pos(g.ox, sM[0][c0]), mean_pos(g.oy, sM[1][c0]), mean_pos(g.oz, sM[2][c0]),
+                                     __int_as_float(0));
+            } else {
+                rec[o] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
+            }
         }
         __syncthreads();
         const int nl = n_list;
+        if (threadIdx.x == 0) gbase = atomicAdd(&ctr->n_list, (uint32_t)nl);
+        __syncthreads();
         for (int q = threadIdx.x; q < nl; q += kNormT) {
             const int l = list[q];
             const int c0 = (((l >> 6) + 1) * 10 + ((l >> 3) & 7) + 1) * 10 + (l & 7) + 1;
@@ -325,37 +326,73 @@ __global__ void __launch_bounds__(kNormT) k_normals(const uint32_t* __restrict__
                         ++cnt;
                     }
             const long long N = cnt;
-            const float A00 = __ll2float_rn(N * sxx - (long long)s1x * s1x);
-            const float A11 = __ll2float_rn(N * syy - (long long)s1y * s1y);
-            const float A22 = __ll2float_rn(N * szz - (long long)s1z * s1z);
-            const float A01 = __ll2float_rn(N * sxy - (long long)s1x * s1y);
-            const float A02 = __ll2float_rn(N * sxz - (long long)s1x * s1z);
-            const float A12 = __ll2float_rn(N * syz - (long long)s1y * s1z);
-            float v[3][3], d[3], n[3];
-            jacobi3(A00, A11, A22, A01, A02, A12, 6, v, d);
-            pick_normal(v, d, n);
+            const size_t slot = gbase + q;
             const size_t o = (size_t)r * kBrickVox + l;
-            nrm[o] = n[0];
-            nrm[stride + o] = n[1];
-            nrm[2 * stride + o] = n[2];
-            const uint32_t N_nb = (uint32_t)(cnt - 1);
-            nbr[o] = (uint8_t)N_nb;
-            const uint8_t st = (N_nb >= n_th && fabsf(n[2]) >= cos_step) ? 2 : 1;
-            status[o] = st;
-            sSt[l] = st;
-            const float mx = mean_pos(g.ox, m0), my = mean_pos(g.oy, m1), mz = mean_pos(g.oz, m2);
-            sMu[0][l] = mx; sMu[1][l] = my; sMu[2][l] = mz;
-            sN[0][l] = n[0]; sN[1][l] = n[1]; sN[2][l] = n[2];
-            rec[o] = make_float4(mx, my, mz, __int_as_float((int)st));
-            rec[stride + o] = make_float4(n[0], n[1], n[2], 0.0f);
+            list_idx[slot] = (uint32_t)o;
+            list_A[slot] = __ll2float_rn(N * sxx - (long long)s1x * s1x);
+            list_A[stride + slot] = __ll2float_rn(N * syy - (long long)s1y * s1y);
+            list_A[2 * stride + slot] = __ll2float_rn(N * szz - (long long)s1z * s1z);
+            list_A[3 * stride + slot] = __ll2float_rn(N * sxy - (long long)s1x * s1y);
+            list_A[4 * stride + slot] = __ll2float_rn(N * sxz - (long long)s1x * s1z);
+            list_A[5 * stride + slot] = __ll2float_rn(N * syz - (long long)s1y * s1z);
+            nbr[o] = (uint8_t)(cnt - 1);
+        }
+    }
+}
+
+// k_eigen, one thread per occupied voxel: normal = eigenvector of the smallest
+// eigenvalue by FP32 Jacobi (6 sweeps); steppable iff N >= n_th and
+// |n_z| >= cos_step (status 2, else 1).
+__global__ void __launch_bounds__(256) k_eigen(const SegCounters* __restrict__ ctr, const uint32_t* __restrict__ list_idx,
+                                               const float* __restrict__ list_A, const uint8_t* __restrict__ nbr,
+                                               float* __restrict__ nrm, uint8_t* __restrict__ status,
+                                               float4* __restrict__ rec, size_t stride, uint32_t n_th,
+                                               float cos_step) {
+    const uint32_t n = ctr->n_list;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        float v[3][3], d[3], nv[3];
+        jacobi3(list_A[q], list_A[stride + q], list_A[2 * stride + q], list_A[3 * stride + q],
+                list_A[4 * stride + q], list_A[5 * stride + q], 6, v, d);
+        pick_normal(v, d, nv);
+        const uint32_t o = list_idx[q];
+        nrm[o] = nv[0];
+        nrm[stride + o] = nv[1];
+        nrm[2 * stride + o] = nv[2];
+        const uint8_t st = (nbr[o] >= n_th && fabsf(nv[2]) >= cos_step) ? 2 : 1;
+        status[o] = st;
+        reinterpret_cast<int*>(rec + o)[3] = (int)st;
+        rec[stride + o] = make_float4(nv[0], nv[1], nv[2], 0.0f);
+    }
+}
+
+// The intra-brick half of Algorithm 1, one 128-thread CTA per brick: the
+// brick's records staged in shared memory, its vertices joined over edges
+// inside the brick with a union-find in shared memory; the global parent of
+// each vertex is set to its local root (the smallest index of its in-brick
+// component).  Edges that leave the brick follow in k_ccl_cross.
+__global__ void __launch_bounds__(kNormT) k_ccl_local(const uint32_t* __restrict__ nsp, uint32_t cap_b,
+                                                      const float4* __restrict__ rec, uint32_t* __restrict__ parent,
+                                                      uint32_t* __restrict__ count, size_t stride, uint8_t want,
+                                                      float d_th2, float cos_ccl, uint32_t* err) {
+    const uint32_t n_sorted = min(*nsp, cap_b);
+    __shared__ float4 sA[512];
+    __shared__ float4 sB[512];
+    __shared__ uint32_t lpar[512];
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        __syncthreads();
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
+            const size_t o = (size_t)r * kBrickVox + l;
+            const float4 a = rec[o];
+            sA[l] = a;
+            const bool vert = __float_as_int(a.w) >= want;
+            if (vert) sB[l] = rec[stride + o];
+            lpar[l] = vert ? (uint32_t)l : kNone;
         }
         __syncthreads();
-        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) lpar[l] = (sSt[l] >= want) ? (uint32_t)l : kNone;
-        __syncthreads();
-        for (int q = threadIdx.x; q < nl; q += kNormT) {
-            const int l = list[q];
-            if (sSt[l] < want) continue;
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
+            if (lpar[l] == kNone) continue;
             const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+            const float4 a = sA[l], an = sB[l];
 #pragma unroll
             for (int k = 0; k < 13; ++k) {
                 int dz, dy, dx;
@@ -363,9 +400,9 @@ __global__ void __launch_bounds__(kNormT) k_normals(const uint32_t* __restrict__
                 const int x = lx + dx, y = ly + dy, z = lz + dz;
                 if (x < 0 || x > 7 || y < 0 || y > 7 || z > 7) continue;
                 const int j = (z * 8 + y) * 8 + x;
-                if (sSt[j] < want) continue;
-                if (ccl_edge(sMu[0][l], sMu[1][l], sMu[2][l], sN[0][l], sN[1][l], sN[2][l], sMu[0][j], sMu[1][j],
-                             sMu[2][j], sN[0][j], sN[1][j], sN[2][j], d_th2, cos_ccl))
+                if (__float_as_int(sA[j].w) < want) continue;
+                const float4 b = sA[j], bn = sB[j];
+                if (ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
                     lf_union(lpar, (uint32_t)l, (uint32_t)j, err);
             }
         }
@@ -373,7 +410,7 @@ __global__ void __launch_bounds__(kNormT) k_normals(const uint32_t* __restrict__
         for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
             const size_t o = (size_t)r * kBrickVox + l;
             uint32_t root = kNone;
-            if (sSt[l] >= want) {  // read-only walk: entries are final once every union is done
+            if (__float_as_int(sA[l].w) >= want) {  // read-only walk: entries are final once every union is done
                 uint32_t x = (uint32_t)l;
                 for (int it = 0; it < 1024; ++it) {
                     const uint32_t p = lpar[x];
@@ -384,7 +421,6 @@ __global__ void __launch_bounds__(kNormT) k_normals(const uint32_t* __restrict__
             }
             parent[o] = root;
             count[o] = 0;
-            if (sSt[l] == 0) rec[o] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
         }
     }
 }
@@ -670,17 +706,25 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     VM_STAGE_END(hk, kStFinalize, s);
     const uint8_t want = p.classify ? 2 : 1;
     VM_STAGE_BEGIN(hk, kStNormals, s);
-    k_normals<<<clampg(cap_b, sms * 8), kNormT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.M, b.nrm, b.status,
-                                                         b.nbr, b.parent, b.count, b.rec, stride, p.n_th, p.cos_step,
-                                                         want, p.d_th2, p.cos_ccl, err);
+    k_moments<<<clampg(cap_b, sms * 8), kNormT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.M, b.rec,
+                                                         b.list_idx, b.list_A, b.nbr, stride, b.ctr);
     VM_STAGE_END(hk, kStNormals, s);
+    VM_STAGE_BEGIN(hk, kStEigen, s);
+    k_eigen<<<clampg((uint32_t)((b.nv + 255) / 256), sms * 16), 256, 0, s>>>(b.ctr, b.list_idx, b.list_A, b.nbr, b.nrm,
+                                                                            b.status, b.rec, stride, p.n_th,
+                                                                            p.cos_step);
+    VM_STAGE_END(hk, kStEigen, s);
+    VM_STAGE_BEGIN(hk, kStCclLocal, s);
+    k_ccl_local<<<clampg(cap_b, sms * 8), kNormT, 0, s>>>(nsp, cap_b, b.rec, b.parent, b.count, stride, want, p.d_th2,
+                                                           p.cos_ccl, err);
+    VM_STAGE_END(hk, kStCclLocal, s);
     VM_STAGE_BEGIN(hk, kStCcl, s);
     k_ccl_cross<<<clampg(cap_b, sms * 8), kCrossT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.rec, b.parent,
                                                             stride, want, p.d_th2, p.cos_ccl, err);
-    k_ccl_compress<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, err);
     VM_STAGE_END(hk, kStCcl, s);
-    count_launch(5);
+    count_launch(7);
     VM_STAGE_BEGIN(hk, kStClusters, s);
+    k_ccl_compress<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, err);
     k_count<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, b.count, b.ctr);
     const uint32_t min_cl = p.min_cluster ? p.min_cluster : 1u;
     uint32_t* nvert = b.flags;      // per-brick tallies: flags reused for kept vertices,

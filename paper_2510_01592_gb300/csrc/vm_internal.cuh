@@ -64,7 +64,8 @@ struct SegCounters {
     uint32_t n_bricks;   // bricks allocated in the pool (copied at the end)
     uint32_t map_err;    // map error bits (copied at the end)
     uint32_t fit_err;    // fit error bits (copied at the end)
-    uint32_t pad[5];
+    uint32_t n_list;     // occupied voxels listed for the eigen-solve
+    uint32_t pad[4];
 };
 
 // Per-cluster fit state on the device.
@@ -91,8 +92,10 @@ enum Stage {
     kStIntegrate = 0,  // claim + accumulate
     kStOrder,          // bricks in key order
     kStFinalize,       // integer means
-    kStNormals,        // Eq. 3 / Eq. 4
-    kStCcl,            // Algorithm 1 (init, link, compress)
+    kStNormals,        // Eq. 3 window moments (k_moments)
+    kStEigen,          // Eq. 3 eigen-solve + Eq. 4 (k_eigen)
+    kStCclLocal,       // Algorithm 1 inside bricks (k_ccl_local)
+    kStCcl,            // Algorithm 1 across bricks (k_ccl_cross, k_ccl_compress)
     kStClusters,       // sizes, numbering, compaction, sort, gather
     kStHyp,            // stage a
     kStScore,          // stage b
@@ -179,6 +182,8 @@ struct SegBuffers {
     uint8_t* status;        // [nv]     0 free, 1 occupied, 2 steppable
     uint8_t* nbr;           // [nv]     occupied neighbours N
     float4* rec;            // [2][nv]  packed (mu, status bits) and (normal, 0) per voxel
+    uint32_t* list_idx;     // [nv]     occupied voxels (rank-dense index), in no particular order
+    float* list_A;          // [6][nv]  their window covariances (FP32, rounded from exact integers)
     uint32_t* parent;       // [nv]     union-find parent, kNone when not a vertex
     uint32_t* count;        // [nv]     component sizes at roots
     uint32_t* cid;          // [nv + 1] kept-root flags -> cluster index (scan)

@@ -65,7 +65,7 @@ class vm_stats(C.Structure):
     _fields_ = [("points_integrated", C.c_uint64), ("points_dropped", C.c_uint64),
                 ("points_no_capacity", C.c_uint64), ("bricks_allocated", C.c_uint32),
                 ("brick_capacity", C.c_uint32), ("occupied_voxels", C.c_uint32), ("steppable_voxels", C.c_uint32),
-                ("clusters", C.c_uint32), ("reserved", C.c_uint32), ("device_bytes", C.c_uint64)]
+                ("clusters", C.c_uint32), ("clustered_points", C.c_uint32), ("device_bytes", C.c_uint64)]
 
 
 # name -> (restype, argtypes); every name is declared in include/vm.h
