@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--profile-case", type=int, default=0, metavar="F",
                     help="profiling driver: integrate frames 1..F, segment --profile-segments times, no timing")
     ap.add_argument("--profile-segments", type=int, default=3)
+    ap.add_argument("--no-batching", action="store_true", help="skip the batched-fit and cluster-parallel variants")
+    ap.add_argument("--profile-fit", type=int, default=0, metavar="K",
+                    help="profiling driver: K config-3 clusters (sizes log-uniform in [50, 200000]), "
+                         "3 fits with the default schedule, no timing")
     return ap.parse_args()
 
 
@@ -82,6 +86,135 @@ def profile_case(frames, segments):
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": frames, "segments": segments, "planes": int(len(r["planes"])),
                       "stats": {k: v for k, v in m.stats().items() if isinstance(v, int)}}))
+
+
+def profile_fit(k):
+    """A small, fixed batched fit for profiler captures: the first k clusters of
+    the config-3 recipe, H = 256, three runs of one plan (default schedule)."""
+    import torch
+    from paper_2510_01592_gb300 import vm
+    import synth
+    xyz, off, _ = synth.config3_clusters_device(n_clusters=k, device="cuda")
+    plan = vm.FitPlan(k, xyz.shape[0], vm.segment_params(n_hyp=256, seed=7))
+    for _ in range(3):
+        r = plan.run(xyz, off)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_fit": k, "points": int(xyz.shape[0]), "planes": int((r["planes"]["best_h"] >= 0).sum()),
+                      "tuning": plan.tuning}))
+
+
+def batching_variant(dev, stream, alu_peak):
+    """Config 3: one batch of 2,000 caller-formed clusters (sizes log-uniform in
+    [50, 200,000], 47.7 M points, H = 256) fitted per frame.  Plain: vm_fit_planes
+    (default schedule, kernels launched one by one, one host round trip for the
+    point count).  Batched: a FitPlan with the autotuned schedule, the whole fit
+    replayed as one CUDA graph.  Both read the same device-resident batch."""
+    import torch
+    from paper_2510_01592_gb300 import vm
+    import synth
+    xyz, off, _ = synth.config3_clusters_device(device=dev)
+    k, n = off.numel() - 1, int(xyz.shape[0])
+    H = 256
+    p = vm.segment_params(n_hyp=H, seed=7)
+    reps = 5
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    plain_ms = timed(lambda: vm.fit_planes(xyz, off, p, stream=stream))
+    plan = vm.FitPlan(k, n, p, stream=stream)
+    t0 = time.perf_counter()
+    best, tune_ms, n_tried = plan.autotune(xyz, off, reps=1)
+    tune_s = time.perf_counter() - t0
+    res = plan.run(xyz, off)
+    batched_ms = timed(lambda: plan.run(xyz, off))
+    plan.close()
+    pt = vm.FitPlan(k, n, p, stream=stream, stage_timing=True)
+    pt.set_tuning(best["tile"], best["hyp_per_thread"], best["ctas_per_sm"], best["schedule"])
+    pt.run(xyz, off)
+    pt.stage_times()
+    pt.run(xyz, off)
+    st = pt.stage_times()
+    pt.close()
+    score_ms = st["ransac_score"][0]
+    instr = 5.0 * H * n  # 3 FFMA + FSETP(|.|) + IADD per point-hypothesis test
+    ach = instr / (score_ms / 1e3) / 1e12
+    del xyz, off
+    torch.cuda.empty_cache()
+    return {
+        "workload": "2,000 clusters, sizes log-uniform in [50, 200,000] (47.7 M points), tilts U[0, 35 deg], "
+                    "5% outliers, H = 256, seed 7",
+        "points": n, "planes": int((res["planes"]["best_h"] >= 0).sum()),
+        "plain_fits_per_s": round(1e3 / plain_ms, 2), "plain_ms": round(plain_ms, 3),
+        "batched_fits_per_s": round(1e3 / batched_ms, 2), "batched_ms": round(batched_ms, 3),
+        "speedup": round(plain_ms / batched_ms, 3),
+        "tuning": best, "autotune": {"candidates": n_tried, "seconds": round(tune_s, 2)},
+        "stages_ms": {kk: round(v[0], 4) for kk, v in st.items()},
+        "ransac_score_roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 2),
+                                  "unit": "T instr/s", "frac": round(ach / alu_peak, 4),
+                                  "point_tests_per_s": round(H * n / (score_ms / 1e3), 1)},
+    }
+
+
+def e5_variant(stream, runs=1000):
+    """The paper's cluster-parallel ablation: m in {1, 2, 4, 8, 16} clusters of
+    M ~ U[10k, 30k] points, H = 100.  Cluster-parallel: one plan over all m
+    clusters.  One at a time: m plans of one cluster each, launched back to back
+    on the same stream (no host round trip between them).  Graph replays."""
+    import numpy as np
+    import torch
+    from paper_2510_01592_gb300 import vm
+    import synth
+    p = vm.segment_params(n_hyp=100, seed=0)
+    out = {}
+    for m in (1, 2, 4, 8, 16):
+        xyz_np, off_np = synth.e5_clusters(m, seed=m)
+        M = int(off_np[1])
+        xyz = torch.from_numpy(xyz_np).to("cuda")
+        off = torch.from_numpy(off_np.astype(np.int32)).to("cuda")
+        singles = [(xyz[c * M:(c + 1) * M], torch.tensor([0, M], dtype=torch.int32, device="cuda"))
+                   for c in range(m)]  # int32 offsets: the uint32 bits of values below 2^31
+        labels = [torch.tensor([c], dtype=torch.int32, device="cuda") for c in range(m)]
+        allp = vm.FitPlan(m, m * M, p, stream=stream)
+        ones = [vm.FitPlan(1, M, p, stream=stream) for _ in range(m)]
+
+        def par():
+            allp.launch(xyz, off)
+            allp.wait()
+
+        def seq():
+            for c in range(m):
+                ones[c].launch(singles[c][0], singles[c][1], labels[c])
+            for c in range(m):
+                ones[c].wait()
+
+        res = {}
+        for name, fn in (("parallel", par), ("one_at_a_time", seq)):
+            for _ in range(5):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(runs):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1) / runs
+        out[str(m)] = {"M": M, "parallel_ms": round(res["parallel"], 4),
+                       "one_at_a_time_ms": round(res["one_at_a_time"], 4),
+                       "speedup": round(res["one_at_a_time"] / res["parallel"], 3)}
+        allp.close()
+        for o in ones:
+            o.close()
+    return {"runs": runs, "n_hyp": 100, "by_clusters": out}
 
 
 def dist_env():
@@ -327,6 +460,11 @@ def run_gpu(args):
     }
     if clocks:
         res["clocks"] = clocks
+    if not args.no_batching and rank == 0:
+        peaks = load_peaks() or {}
+        alu_peak = SM_COUNT * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        res["variants"]["batching_config3"] = batching_variant(dev, stream, alu_peak)
+        res["variants"]["cluster_parallel_e5"] = e5_variant(stream)
     res["stages_ms_per_step"] = {k: round(v[0] / max(1, args.steps), 4) for k, v in stages.items() if v[1]}
     table = kernel_table(stages, st, load_peaks(), st["clustered_points"])
     res["kernels"] = table
@@ -442,6 +580,9 @@ def main():
     args = parse()
     if args.profile_case:
         profile_case(args.profile_case, args.profile_segments)
+        return
+    if args.profile_fit:
+        profile_fit(args.profile_fit)
         return
     if args.impl == "reference":
         res, rank = run_reference(args)

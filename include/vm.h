@@ -163,6 +163,66 @@ vm_status vm_get_stats(vm_map* map, vm_stats* out);
 vm_status vm_fit_planes(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
                         const vm_segment_params* params, void* stream, vm_planes* out);
 
+/* ---- Reusable batched fit ------------------------------------------------
+ * The cluster-parallel plane fit of vm_fit_planes (Sec. III.C multi-plane
+ * estimation stages a-c, refit, boundary polygons) as a reusable plan: the
+ * plan owns every device buffer a batch needs, a result block in mapped
+ * pinned host memory and one CUDA graph of the whole fit (hypotheses,
+ * persistent scoring, selection, extraction, refit, hull, pack), so a run
+ * with the same input pointers replays one graph and allocates nothing.
+ * A batch larger than any seen so far (more clusters, points or hull
+ * vertices) grows the buffers, captures again and re-runs.  Results are
+ * identical to vm_fit_planes for every tuning except the refit's double
+ * rounding (its partial sums follow the tile split), well inside the refit
+ * tolerance; integer results (best_h, inlier counts, hulls) are bit-exact. */
+typedef struct vm_fit_plan vm_fit_plan; /* opaque, library-owned */
+
+typedef struct {
+    uint32_t tile;           /* points per scoring / extraction work item, 64..16384       */
+    uint32_t hyp_per_thread; /* hypotheses each thread holds in registers: 1, 2, 4 or 8    */
+    uint32_t ctas_per_sm;    /* persistent scoring CTAs per SM, 1..16                      */
+    uint32_t schedule;       /* 0: a 256-thread CTA per work item; 1: a warp per work item  */
+} vm_fit_tuning;
+
+#define VM_FIT_STAGE_TIMING 1u /* CUDA-event time per stage (vm_fit_plan_stage_times); implies VM_FIT_EAGER */
+#define VM_FIT_EAGER 2u        /* launch kernel by kernel instead of replaying the graph */
+
+/* Creates a plan sized for k_cap clusters and n_cap points with params
+ * (n_hyp, eps, seed are used).  stream: cudaStream_t or NULL (the library
+ * creates one).  flags: 0, VM_FIT_EAGER or VM_FIT_STAGE_TIMING.  Errors: VM_ERR_INVALID_ARG,
+ * VM_ERR_OUT_OF_MEMORY, VM_ERR_CUDA. */
+vm_status vm_fit_plan_create(uint32_t k_cap, uint32_t n_cap, const vm_segment_params* params, void* stream,
+                             uint32_t flags, vm_fit_plan** out);
+/* Fits k clusters: xyz device float32[off[k]][3]; off device uint32[k+1];
+ * labels device uint32[k] or NULL (label = index); the pointers must stay
+ * valid until the call returns.  Synchronises the plan's stream; *out is
+ * host memory owned by the library until vm_planes_free.  Errors as
+ * vm_fit_planes. */
+vm_status vm_fit_plan_run(vm_fit_plan* plan, const float* xyz, const uint32_t* off, const uint32_t* labels,
+                          uint32_t k, vm_planes* out);
+/* Asynchronous half of a run: enqueues the fit on the plan's stream and
+ * returns; vm_fit_plan_wait synchronises and fills *out (NULL: only waits).
+ * One launch at a time per plan. */
+vm_status vm_fit_plan_launch(vm_fit_plan* plan, const float* xyz, const uint32_t* off, const uint32_t* labels,
+                             uint32_t k);
+vm_status vm_fit_plan_wait(vm_fit_plan* plan, vm_planes* out);
+vm_status vm_fit_plan_set_tuning(vm_fit_plan* plan, const vm_fit_tuning* tuning);
+vm_status vm_fit_plan_get_tuning(const vm_fit_plan* plan, vm_fit_tuning* tuning);
+/* Autotuner (no counterpart in the paper): times the whole fit of this batch
+ * (CUDA events around graph replays, reps timed runs after one warm-up run)
+ * for each candidate tuning -- CTA-per-item tiles of 1024..8192 points and
+ * warp-per-item tiles of 128..1024 points, 2..8 hypotheses per thread,
+ * persistent CTAs per SM up to the occupancy limit -- and keeps the fastest.
+ * *best and *best_ms (either may be NULL) receive it; *n_tried the number of
+ * candidates timed.  Errors as vm_fit_plan_run. */
+vm_status vm_fit_plan_autotune(vm_fit_plan* plan, const float* xyz, const uint32_t* off, const uint32_t* labels,
+                               uint32_t k, uint32_t reps, vm_fit_tuning* best, float* best_ms, uint32_t* n_tried);
+/* Device milliseconds and call counts per stage (names: vm_stage_name) since
+ * the previous call, for a plan created with VM_FIT_STAGE_TIMING; then reset.
+ * ms[cap], calls[cap] host arrays, either may be NULL. */
+vm_status vm_fit_plan_stage_times(vm_fit_plan* plan, double* ms, uint64_t* calls, uint32_t cap, uint32_t* n_stages);
+vm_status vm_fit_plan_destroy(vm_fit_plan* plan);
+
 /* RANSAC without allocation.  The paper has no counterpart: this entry point
  * serves callers that must not allocate device memory while they run -- a
  * robot control loop with a hard deadline (cudaMalloc can stall on

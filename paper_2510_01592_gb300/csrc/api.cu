@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "vm_internal.cuh"
+#include "runtime.cuh"
 
 using namespace vmx;
 
@@ -18,68 +18,13 @@ static thread_local std::string g_err;
 static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long launch_total() { return g_launches.load(); }
+void uncount_launch(unsigned long long n) { g_launches.fetch_sub(n); }
 
 static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "finalize", "moments", "eigen",
                                               "ccl_local", "ccl_cross", "clusters", "ransac_hyp", "ransac_score",
                                               "extract", "refit_hull", "pack"};
 
-// CUDA-event stage timer: begin/end record events on the stream; elapsed times
-// are folded in once the events have completed (at the next sync point).
-struct Timer : StageHook {
-    bool on = false;
-    struct Rec {
-        int st;
-        cudaEvent_t a, b;
-    };
-    std::vector<cudaEvent_t> pool;
-    std::vector<Rec> recs;
-    cudaEvent_t open[kNumStages] = {};
-    double ms[kNumStages] = {};
-    unsigned long long calls[kNumStages] = {};
-    cudaEvent_t get() {
-        if (pool.empty()) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-            return e;
-        }
-        cudaEvent_t e = pool.back();
-        pool.pop_back();
-        return e;
-    }
-    void begin(int st, cudaStream_t s) override {
-        if (!on) return;
-        cudaEvent_t e = get();
-        if (e) cudaEventRecord(e, s);
-        open[st] = e;
-    }
-    void end(int st, cudaStream_t s) override {
-        if (!on || !open[st]) return;
-        cudaEvent_t e = get();
-        if (!e) return;
-        cudaEventRecord(e, s);
-        recs.push_back({st, open[st], e});
-        open[st] = nullptr;
-    }
-    void fold() {
-        for (auto& r : recs) {
-            float t = 0.0f;
-            cudaEventSynchronize(r.b);
-            if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
-                ms[r.st] += t;
-                calls[r.st] += 1;
-            }
-            pool.push_back(r.a);
-            pool.push_back(r.b);
-        }
-        recs.clear();
-    }
-    void release() {
-        fold();
-        for (auto e : pool) cudaEventDestroy(e);
-        pool.clear();
-    }
-    StageHook* hook() { return on ? this : nullptr; }
-};
 
 void set_error(const std::string& msg) { g_err = msg; }
 
@@ -103,39 +48,15 @@ vm_status ensure(DevBuf& b, size_t bytes) {
     return VM_OK;
 }
 
-static void release(DevBuf& b) {
+void release(DevBuf& b) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
 }
 
-// Carves aligned sub-buffers out of one allocation.
-struct Carver {
-    char* base;
-    size_t off = 0;
-    template <typename T>
-    T* take(size_t n) {
-        off = (off + 255) & ~(size_t)255;
-        T* p = reinterpret_cast<T*>(base + off);
-        off += n * sizeof(T);
-        return p;
-    }
-};
 
-// Fit scratch owned by a map or by a calling thread.
-struct FitContext {
-    Timer timer;
-    uint64_t gen = 0;      // bumps whenever the scratch moves
-    DevBuf mem;
-    FitBuffers fb{};
-    size_t kcap = 0, npts = 0, items = 0;
-    int H = 0;
-    DevBuf out;          // device staging of planes / hull arrays
-    void* host = nullptr;  // pinned host staging
-    size_t host_bytes = 0;
-};
 
-static size_t fit_bytes(size_t kcap, size_t npts, size_t items, int H, Carver* c) {
+size_t fit_bytes(size_t kcap, size_t npts, size_t items, int H, Carver* c) {
     Carver dry{nullptr};
     Carver& k = c ? *c : dry;
     FitBuffers fb{};
@@ -162,7 +83,7 @@ static size_t fit_bytes(size_t kcap, size_t npts, size_t items, int H, Carver* c
     return k.off + 256;
 }
 
-static vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile) {
+vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile) {
     const size_t items = npts / (size_t)tile + kcap + 1;
     if (fc.mem.p && kcap <= fc.kcap && npts <= fc.npts && items <= fc.items && H <= fc.H) return VM_OK;
     const size_t k2 = kcap + kcap / 4 + 16, n2 = npts + npts / 4 + 1024, i2 = n2 / (size_t)tile + k2 + 1;
@@ -200,7 +121,7 @@ static vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, in
     return VM_OK;
 }
 
-static void fit_release(FitContext& fc) {
+void fit_release(FitContext& fc) {
     fc.timer.release();
     release(fc.mem);
     release(fc.out);
@@ -211,14 +132,14 @@ static void fit_release(FitContext& fc) {
     fc.H = 0;
 }
 
-static int device_sms() {
+int device_sms() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms > 0 ? sms : 1;
 }
 
-static vm_status check_params(const vm_segment_params* p) {
+vm_status check_params(const vm_segment_params* p) {
     if (!p) {
         set_error("null segment params");
         return VM_ERR_INVALID_ARG;
@@ -298,51 +219,7 @@ static vm_status fit_and_pack(FitContext& fc, const float* pts, const uint32_t* 
     return VM_OK;
 }
 
-}  // namespace vmx
 
-struct vm_map {
-    vm_map_params prm{};
-    Grid g{};
-    uint32_t nb_total = 0;
-    uint32_t capacity = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    // pool
-    int32_t* brick_table = nullptr;
-    int32_t* slot_key = nullptr;
-    unsigned long long* S = nullptr;
-    uint32_t* C = nullptr;
-    MapCounters* ctr = nullptr;
-    uint32_t* err = nullptr;  // segmentation error word
-    DevBuf pool;
-    DevBuf stage;             // host points staged on the device
-    // segmentation
-    DevBuf brick_mem;         // brick-level arrays (fixed size)
-    DevBuf vox_mem;           // rank-dense voxel arrays (grow with the brick count)
-    SegBuffers seg{};
-    size_t seg_nv = 0;
-    SegCounters* hctr = nullptr;  // pinned
-    SegCounters last{};
-    FitContext fit;
-    FitTuning tune = default_tuning();
-    bool segmented = false;
-    // results: mapped pinned host memory written by the kernels
-    void* out_host = nullptr;
-    char* out_dev = nullptr;
-    size_t out_bytes = 0;
-    uint32_t out_kcap = 0, out_hcap = 0;
-    uint32_t kcap = 0;            // kept-cluster capacity of the scratch
-    uint32_t brick_hint = 0, k_hint = 0, hull_hint = 0;
-    uint64_t gen = 0;             // bumps whenever scratch or outputs move
-    // captured segmentation (one CUDA graph, replayed per call)
-    bool use_graph = true;
-    cudaGraphExec_t gexec = nullptr;
-    uint64_t ggen = ~0ull;
-    vm_segment_params gprm{};
-    unsigned long long glaunches = 0;
-};
-
-namespace {
 
 vm_status alloc_vox(vm_map* m, uint32_t n_bricks) {
     const size_t need = (size_t)(n_bricks ? n_bricks : 1) * kBrickVox;
@@ -392,8 +269,6 @@ vm_status alloc_vox(vm_map* m, uint32_t n_bricks) {
     return VM_OK;
 }
 
-// Result block in mapped pinned host memory: the counters, then kcap plane
-// records, then hcap hull vertices (xy int32 pairs, then xyz floats).
 size_t out_planes_off() { return 256; }
 size_t out_xy_off(uint32_t kcap) { return (256 + (size_t)kcap * sizeof(vm_plane) + 255) & ~(size_t)255; }
 size_t out_xyz_off(uint32_t kcap, uint32_t hcap) { return (out_xy_off(kcap) + (size_t)hcap * 8 + 255) & ~(size_t)255; }
@@ -460,18 +335,26 @@ __global__ void k_header(const SegCounters* __restrict__ ctr, const uint32_t* __
 // The whole segmentation as one fixed launch sequence (every count is read on
 // the device): order bricks, means, normals, clustering, clusters, RANSAC,
 // refit, hull, pack into the mapped result block, header.
+cudaError_t enqueue_front(vm_map* m, const vm_segment_params& p, StageHook* hk) {
+    cudaStream_t s = m->stream;
+    const int sms = device_sms();
+    SegBuffers& b = m->seg;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(m->err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(m->fit.fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+    VM_STAGE_BEGIN(hk, kStOrder, s);
+    if ((e = seg_order_bricks(m->brick_table, m->nb_total, b, sms, s)) != cudaSuccess) return e;
+    VM_STAGE_END(hk, kStOrder, s);
+    return seg_run(m->g, m->S, m->C, p, b, m->kcap, m->err, sms, s, hk);
+}
+
 cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk) {
     cudaStream_t s = m->stream;
     const int sms = device_sms();
     SegBuffers& b = m->seg;
     FitBuffers& fb = m->fit.fb;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(m->err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    VM_STAGE_BEGIN(hk, kStOrder, s);
-    if ((e = seg_order_bricks(m->brick_table, m->nb_total, b, sms, s)) != cudaSuccess) return e;
-    VM_STAGE_END(hk, kStOrder, s);
-    if ((e = seg_run(m->g, m->S, m->C, p, b, m->kcap, m->err, sms, s, hk)) != cudaSuccess) return e;
+    if ((e = enqueue_front(m, p, hk)) != cudaSuccess) return e;
     if ((e = launch_fit(b.pts, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, p, fb, m->tune, sms, s, hk)) != cudaSuccess)
         return e;
     char* d = m->out_dev;
@@ -493,7 +376,7 @@ vm_status capture_segment(vm_map* m, const vm_segment_params& p) {
     }
     fit_init_attributes();
     cudaGraph_t graph = nullptr;
-    const unsigned long long l0 = g_launches.load();
+    const unsigned long long l0 = launch_total();
     VM_CUDA(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_segment(m, p, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(m->stream, &graph);
@@ -508,8 +391,8 @@ vm_status capture_segment(vm_map* m, const vm_segment_params& p) {
         m->gexec = nullptr;
         return cuda_status(e, "cudaGraphInstantiate");
     }
-    m->glaunches = g_launches.load() - l0;
-    g_launches.fetch_sub(m->glaunches);  // counted when replayed, not when captured
+    m->glaunches = launch_total() - l0;
+    uncount_launch(m->glaunches);  // counted when replayed, not when captured
     m->ggen = m->gen;
     m->gprm = p;
     return VM_OK;
@@ -523,7 +406,92 @@ vm_status check_map(vm_map* m) {
     return VM_OK;
 }
 
-}  // namespace
+vm_status launch_segment(vm_map* m, const vm_segment_params& p) {
+    cudaStream_t s = m->stream;
+    if (!m->vox_mem.p) {  // first call: size the scratch from the pool's brick count (one read)
+        MapCounters c;
+        VM_CUDA(cudaMemcpyAsync(&c, m->ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaStreamSynchronize(s));
+        m->brick_hint = c.n_bricks < m->capacity ? c.n_bricks : m->capacity;
+    }
+    VM_TRY(plan_capacity(m, p));
+    StageHook* hk = m->fit.timer.hook();
+    if (m->use_graph && !hk && (!m->gexec || m->ggen != m->gen || memcmp(&m->gprm, &p, sizeof(p)) != 0)) {
+        if (capture_segment(m, p) != VM_OK) {  // e.g. a stream that cannot be captured: launch eagerly
+            cudaGetLastError();
+            m->use_graph = false;
+        }
+    }
+    if (m->use_graph && !hk) {
+        VM_CUDA(cudaGraphLaunch(m->gexec, s));
+        count_launch((int)m->glaunches);
+    } else {
+        VM_CUDA(enqueue_segment(m, p, hk));
+    }
+    return VM_OK;
+}
+
+// True when the completed segmentation in the result block ran out of a
+// capacity (scratch or hull output) and must be re-run; updates the hints
+// that size the next attempt.
+static bool take_hints(vm_map* m) {
+    const SegCounters* hdr = static_cast<const SegCounters*>(m->out_host);
+    m->brick_hint = hdr->n_bricks < m->capacity ? hdr->n_bricks : m->capacity;
+    m->k_hint = hdr->k;
+    m->hull_hint = hdr->n_hull;
+    return (hdr->err & kErrScratch) || hdr->n_hull > m->out_hcap;
+}
+
+vm_status finish_segment(vm_map* m, const vm_segment_params& p, vm_planes* out) {
+    for (int attempt = 0;; ++attempt) {
+        VM_CUDA(cudaStreamSynchronize(m->stream));
+        m->fit.timer.fold();
+        if (!take_hints(m)) break;
+        if (attempt == 3) {
+            set_error("segmentation scratch could not be sized for this map");
+            return VM_ERR_OUT_OF_MEMORY;
+        }
+        VM_TRY(launch_segment(m, p));
+    }
+    return read_result(m, out);
+}
+
+vm_status read_result(vm_map* m, vm_planes* out) {
+    const SegCounters* hdr = static_cast<const SegCounters*>(m->out_host);
+    m->last = *hdr;
+    m->segmented = true;
+    const uint32_t K = hdr->k, n_hull = hdr->n_hull;
+    const size_t b_planes = (size_t)K * sizeof(vm_plane);
+    out->planes = static_cast<vm_plane*>(malloc(b_planes ? b_planes : 1));
+    out->hull_xy = static_cast<int32_t*>(malloc(n_hull ? (size_t)n_hull * 8 : 1));
+    out->hull_xyz = static_cast<float*>(malloc(n_hull ? (size_t)n_hull * 12 : 1));
+    if (!out->planes || !out->hull_xy || !out->hull_xyz) {
+        vm_planes_free(out);
+        set_error("host allocation of the result failed");
+        return VM_ERR_OUT_OF_MEMORY;
+    }
+    const char* h = static_cast<const char*>(m->out_host);
+    memcpy(out->planes, h + out_planes_off(), b_planes);
+    memcpy(out->hull_xy, h + out_xy_off(m->out_kcap), (size_t)n_hull * 8);
+    memcpy(out->hull_xyz, h + out_xyz_off(m->out_kcap, m->out_hcap), (size_t)n_hull * 12);
+    out->n_planes = K;
+    out->n_hull = n_hull;
+    if ((hdr->err | hdr->fit_err) & kErrTimeout) {
+        set_error("a bounded device loop reached its iteration cap");
+        return VM_ERR_TIMEOUT;
+    }
+    if (hdr->fit_err & kErrOverflow) {
+        set_error("a cluster spans more than 2^28 hull quanta (4096 m) in its plane; its hull is not exact");
+        return VM_ERR_EXTENT;
+    }
+    if (hdr->map_err & kErrCapacity) {
+        set_error("brick pool full: points in unallocated bricks were dropped");
+        return VM_ERR_CAPACITY;
+    }
+    return VM_OK;
+}
+
+}  // namespace vmx
 
 extern "C" {
 
@@ -690,74 +658,8 @@ vm_status vm_segment(vm_map* m, const vm_segment_params* params, vm_planes* out)
         return VM_ERR_INVALID_ARG;
     }
     memset(out, 0, sizeof(*out));
-    const vm_segment_params& p = *params;
-    cudaStream_t s = m->stream;
-    if (!m->vox_mem.p) {  // first call: size the scratch from the pool's brick count (one read)
-        MapCounters c;
-        VM_CUDA(cudaMemcpyAsync(&c, m->ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
-        VM_CUDA(cudaStreamSynchronize(s));
-        m->brick_hint = c.n_bricks < m->capacity ? c.n_bricks : m->capacity;
-    }
-    const SegCounters* hdr = nullptr;
-    for (int attempt = 0; attempt < 4; ++attempt) {
-        VM_TRY(plan_capacity(m, p));
-        StageHook* hk = m->fit.timer.hook();
-        if (m->use_graph && !hk && (!m->gexec || m->ggen != m->gen || memcmp(&m->gprm, &p, sizeof(p)) != 0)) {
-            if (capture_segment(m, p) != VM_OK) {  // e.g. a stream that cannot be captured: launch eagerly
-                cudaGetLastError();
-                m->use_graph = false;
-            }
-        }
-        if (m->use_graph && !hk) {
-            VM_CUDA(cudaGraphLaunch(m->gexec, s));
-            count_launch((int)m->glaunches);
-        } else {
-            VM_CUDA(enqueue_segment(m, p, hk));
-        }
-        VM_CUDA(cudaStreamSynchronize(s));
-        m->fit.timer.fold();
-        hdr = static_cast<const SegCounters*>(m->out_host);
-        m->brick_hint = hdr->n_bricks < m->capacity ? hdr->n_bricks : m->capacity;
-        m->k_hint = hdr->k;
-        m->hull_hint = hdr->n_hull;
-        const bool retry = (hdr->err & kErrScratch) || hdr->n_hull > m->out_hcap;
-        if (!retry) break;
-        if (attempt == 3) {
-            set_error("segmentation scratch could not be sized for this map");
-            return VM_ERR_OUT_OF_MEMORY;
-        }
-    }
-    m->last = *hdr;
-    m->segmented = true;
-    const uint32_t K = hdr->k, n_hull = hdr->n_hull;
-    const size_t b_planes = (size_t)K * sizeof(vm_plane);
-    out->planes = static_cast<vm_plane*>(malloc(b_planes ? b_planes : 1));
-    out->hull_xy = static_cast<int32_t*>(malloc(n_hull ? (size_t)n_hull * 8 : 1));
-    out->hull_xyz = static_cast<float*>(malloc(n_hull ? (size_t)n_hull * 12 : 1));
-    if (!out->planes || !out->hull_xy || !out->hull_xyz) {
-        vm_planes_free(out);
-        set_error("host allocation of the result failed");
-        return VM_ERR_OUT_OF_MEMORY;
-    }
-    const char* h = static_cast<const char*>(m->out_host);
-    memcpy(out->planes, h + out_planes_off(), b_planes);
-    memcpy(out->hull_xy, h + out_xy_off(m->out_kcap), (size_t)n_hull * 8);
-    memcpy(out->hull_xyz, h + out_xyz_off(m->out_kcap, m->out_hcap), (size_t)n_hull * 12);
-    out->n_planes = K;
-    out->n_hull = n_hull;
-    if ((hdr->err | hdr->fit_err) & kErrTimeout) {
-        set_error("a bounded device loop reached its iteration cap");
-        return VM_ERR_TIMEOUT;
-    }
-    if (hdr->fit_err & kErrOverflow) {
-        set_error("a cluster spans more than 2^28 hull quanta (4096 m) in its plane; its hull is not exact");
-        return VM_ERR_EXTENT;
-    }
-    if (hdr->map_err & kErrCapacity) {
-        set_error("brick pool full: points in unallocated bricks were dropped");
-        return VM_ERR_CAPACITY;
-    }
-    return VM_OK;
+    VM_TRY(launch_segment(m, *params));
+    return finish_segment(m, *params, out);
 }
 
 vm_status vm_planes_free(vm_planes* p) {

@@ -18,7 +18,7 @@
 //            filtering step of the cited convex-hull method), the rest are
 //            appended.
 //  k_refit   per cluster: TLS refit in double from the partial sums.
-//  k_hull    per cluster: a second, 32-direction filter, then a bitonic sort
+//  k_hull    per cluster: a second, 128-direction filter, then a bitonic sort
 //            of the remaining quantised points in shared memory and Andrew's
 //            monotone chain with exact int64 orientation tests; gift wrapping
 //            over global memory when too many remain for shared memory.
@@ -839,6 +839,77 @@ __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restr
     }
 }
 
+// Stage b with one warp per work item (the schedule for many small
+// clusters): each warp pulls its own items from the queue and stages the
+// item's points in its own slice of shared memory; lanes hold R hypotheses
+// each, 32 / ceil(H / R) lanes groups split the points, and the groups' counts
+// are combined with shuffles before the integer atomics.  No CTA barrier.
+template <int R>
+__global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                                                   const uint32_t* __restrict__ item_off,
+                                                   const uint32_t* __restrict__ kp, int H, int T,
+                                                   const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
+                                                   uint32_t* __restrict__ queue, float eps) {
+    const uint32_t k = *kp;
+    extern __shared__ float4 sp[];  // [kT / 32][T]
+    const int lane = threadIdx.x & 31;
+    float4* wp = sp + (size_t)(threadIdx.x >> 5) * T;
+    const int G = (H + R - 1) / R;  // lanes per point group (<= 32, checked by the host)
+    const int P = 32 / G;           // point groups per warp
+    const int g = lane / G, j = lane % G;
+    const bool active = g < P;
+    const uint32_t n_items = item_off[k];
+    for (int guard = 0; guard < kLoopCap; ++guard) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(queue, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        const uint32_t c = find_cluster(item_off, k, it);
+        const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
+        const uint32_t end = min(off[c + 1], start + (uint32_t)T);
+        const int cnt = (int)(end - start);
+        __syncwarp();
+        for (int q = lane; q < cnt; q += 32) {
+            const float* p = pts + 3 * ((size_t)start + q);
+            wp[q] = make_float4(p[0], p[1], p[2], 0.0f);
+        }
+        float4 pl[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int h = j * R + r;
+            pl[r] = (active && h < H) ? hyp[(size_t)c * H + h]
+                                      : make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0x7f800000));
+        }
+        __syncwarp();
+        uint32_t acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0;
+        if (active) {
+            for (int q = g; q < cnt; q += P) {
+                const float4 p = wp[q];
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    acc[r] += plane_dist(pl[r].x, pl[r].y, pl[r].z, pl[r].w, p.x, p.y, p.z) <= eps;
+            }
+        }
+        for (int q = 1; q < P; ++q) {
+            const int src = j + q * G;  // < 32 since P * G <= 32
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint32_t v = __shfl_sync(0xffffffffu, acc[r], src);
+                if (g == 0) acc[r] += v;
+            }
+        }
+        if (g == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int h = j * R + r;
+                if (h < H && acc[r]) atomicAdd(&counts[(size_t)c * H + h], acc[r]);
+            }
+        }
+    }
+}
+
 template <int R>
 cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* kp, int H,
                          int T, const float4* hyp, uint32_t* counts, uint32_t* queue, float eps, int grid,
@@ -850,6 +921,15 @@ cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* 
     return cudaGetLastError();
 }
 
+template <int R>
+cudaError_t launch_score_warp(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* kp,
+                              int H, int T, const float4* hyp, uint32_t* counts, uint32_t* queue, float eps,
+                              int grid, cudaStream_t s) {
+    const size_t smem = (size_t)(kT / 32) * T * sizeof(float4);
+    k_score_warp<R><<<grid, kT, smem, s>>>(pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
+    return cudaGetLastError();
+}
+
 __global__ void k_set_end(uint32_t* __restrict__ arr, const uint32_t* __restrict__ kp, const uint32_t* __restrict__ v) {
     arr[*kp] = *v;
 }
@@ -858,7 +938,51 @@ __global__ void k_set_u32(uint32_t* __restrict__ p, uint32_t v) { *p = v; }
 
 }  // namespace
 
-FitTuning default_tuning() { return FitTuning{2048, 4, 4}; }
+FitTuning default_tuning() { return FitTuning{2048, 4, 4, 0}; }
+
+// The scoring variant launch_fit picks for t and H: hypotheses per thread
+// and whether the warp schedule applies.
+static void score_variant(const FitTuning& t, int H, int& R, bool& warp) {
+    R = t.hyp_per_thread;
+    warp = t.schedule == 1 && H <= 256 && (size_t)(kT / 32) * t.tile * sizeof(float4) <= 200 * 1024;
+    if (warp) {
+        while (R < 8 && (H + R - 1) / R > 32) R <<= 1;
+    } else {
+        while (R < 8 && (H + R - 1) / R > kT) R <<= 1;
+    }
+}
+
+int score_max_ctas_per_sm(const FitTuning& t, int H) {
+    fit_init_attributes();
+    int R;
+    bool warp;
+    score_variant(t, H, R, warp);
+    const int G = (H + R - 1) / R;
+    const size_t smem = warp ? (size_t)(kT / 32) * t.tile * sizeof(float4)
+                             : (size_t)t.tile * sizeof(float4) + (size_t)(kT / G) * G * R * sizeof(uint32_t);
+    int n = 0;
+    cudaError_t e;
+    if (warp) {
+        switch (R) {
+            case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score_warp<1>, kT, smem); break;
+            case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score_warp<2>, kT, smem); break;
+            case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score_warp<4>, kT, smem); break;
+            default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score_warp<8>, kT, smem); break;
+        }
+    } else {
+        switch (R) {
+            case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score<1>, kT, smem); break;
+            case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score<2>, kT, smem); break;
+            case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score<8>, kT, smem); break;
+            default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_score<4>, kT, smem); break;
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
 
 size_t fit_hull_smem() {
     return (size_t)kHullCap * (2 * sizeof(unsigned long long) + 2 * sizeof(uint32_t)) + (size_t)kSurvCap * sizeof(int2);
@@ -872,6 +996,10 @@ void fit_init_attributes() {
     cudaFuncSetAttribute(k_score<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_score<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_score<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_score_warp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_score_warp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_score_warp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_score_warp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     done = true;
 }
 
@@ -902,14 +1030,27 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_END(hk, kStHyp, s);
     count_launch(3);
     const int grid = sms * t.ctas_per_sm;
-    int R = t.hyp_per_thread;
-    while (R < 8 && (H + R - 1) / R > kT) R <<= 1;  // at most one subset row of kT threads
+    // The warp schedule needs ceil(H / R) <= 32 lanes with R <= 8 and its
+    // per-warp tiles within the shared-memory limit; otherwise the CTA one
+    // runs, with at most one subset row of kT threads.
+    int R;
+    bool warp;
+    score_variant(t, H, R, warp);
     VM_STAGE_BEGIN(hk, kStScore, s);
-    switch (R) {
-        case 1: e = launch_score<1>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-        case 2: e = launch_score<2>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-        case 8: e = launch_score<8>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-        default: e = launch_score<4>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+    if (warp) {
+        switch (R) {
+            case 1: e = launch_score_warp<1>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 2: e = launch_score_warp<2>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 4: e = launch_score_warp<4>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            default: e = launch_score_warp<8>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        }
+    } else {
+        switch (R) {
+            case 1: e = launch_score<1>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 2: e = launch_score<2>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 8: e = launch_score<8>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            default: e = launch_score<4>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+        }
     }
     if (e != cudaSuccess) return e;
     VM_STAGE_END(hk, kStScore, s);

@@ -242,8 +242,11 @@ struct FitTuning {
     int tile;               // points per scoring work item
     int hyp_per_thread;     // hypotheses held in registers per thread
     int ctas_per_sm;        // persistent CTAs per SM
+    int schedule;           // 0: a CTA per work item; 1: a warp per work item
 };
 FitTuning default_tuning();
+// Resident scoring CTAs per SM for tuning t and H hypotheses (0 on error).
+int score_max_ctas_per_sm(const FitTuning& t, int H);
 size_t fit_hull_smem();
 
 // Runs RANSAC, selection, extraction, refit and hull for the clusters whose

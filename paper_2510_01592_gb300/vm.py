@@ -68,6 +68,11 @@ class vm_stats(C.Structure):
                 ("clusters", C.c_uint32), ("clustered_points", C.c_uint32), ("device_bytes", C.c_uint64)]
 
 
+class vm_fit_tuning(C.Structure):
+    _fields_ = [("tile", C.c_uint32), ("hyp_per_thread", C.c_uint32), ("ctas_per_sm", C.c_uint32),
+                ("schedule", C.c_uint32)]
+
+
 # name -> (restype, argtypes); every name is declared in include/vm.h
 _SIGS = {
     "vm_create": (C.c_int, [C.POINTER(vm_map_params), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -85,6 +90,18 @@ _SIGS = {
                                    C.c_uint32, C.POINTER(C.c_uint32)]),
     "vm_export_clusters": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32,
                                      C.POINTER(C.c_uint32)]),
+    "vm_fit_plan_create": (C.c_int, [C.c_uint32, C.c_uint32, C.POINTER(vm_segment_params), C.c_void_p, C.c_uint32,
+                                     C.POINTER(C.c_void_p)]),
+    "vm_fit_plan_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32,
+                                  C.POINTER(vm_planes)]),
+    "vm_fit_plan_launch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32]),
+    "vm_fit_plan_wait": (C.c_int, [C.c_void_p, C.POINTER(vm_planes)]),
+    "vm_fit_plan_set_tuning": (C.c_int, [C.c_void_p, C.POINTER(vm_fit_tuning)]),
+    "vm_fit_plan_get_tuning": (C.c_int, [C.c_void_p, C.POINTER(vm_fit_tuning)]),
+    "vm_fit_plan_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32,
+                                       C.POINTER(vm_fit_tuning), C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
+    "vm_fit_plan_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32)]),
+    "vm_fit_plan_destroy": (C.c_int, [C.c_void_p]),
     "vm_stage_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "vm_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32)]),
     "vm_stage_name": (C.c_char_p, [C.c_uint32]),
@@ -276,6 +293,82 @@ def fit_planes(xyz, off, params: vm_segment_params | None = None, labels=None, s
         return _planes_to_numpy(out)
     finally:
         load().vm_planes_free(C.byref(out))
+
+
+VM_FIT_STAGE_TIMING = 1
+VM_FIT_EAGER = 2
+
+
+def _tuning_dict(t: vm_fit_tuning):
+    return {"tile": t.tile, "hyp_per_thread": t.hyp_per_thread, "ctas_per_sm": t.ctas_per_sm,
+            "schedule": "warp" if t.schedule else "cta"}
+
+
+class FitPlan:
+    """A reusable batched fit (vm_fit_plan_*): buffers sized once, the whole fit
+    replayed as one CUDA graph per run.  xyz, off, labels are CUDA tensors."""
+
+    def __init__(self, k_cap, n_cap, params: vm_segment_params | None = None, stream=None, eager=False,
+                 stage_timing=False):
+        self.params = params or segment_params()
+        h = C.c_void_p()
+        flags = (VM_FIT_EAGER if eager else 0) | (VM_FIT_STAGE_TIMING if stage_timing else 0)
+        _check(load().vm_fit_plan_create(int(k_cap), int(n_cap), C.byref(self.params), _stream_handle(stream),
+                                         flags, C.byref(h)))
+        self._h = h
+
+    def stage_times(self):
+        """{stage: (ms, calls)} since the previous call (plans made with stage_timing=True)."""
+        ms = (C.c_double * N_STAGES)()
+        calls = (C.c_uint64 * N_STAGES)()
+        n = C.c_uint32()
+        _check(load().vm_fit_plan_stage_times(self._h, ms, calls, N_STAGES, C.byref(n)))
+        L = load()
+        return {L.vm_stage_name(i).decode(): (ms[i], calls[i]) for i in range(n.value) if calls[i]}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().vm_fit_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, xyz, off, labels=None):
+        k = int(off.numel()) - 1
+        out = vm_planes()
+        _check(load().vm_fit_plan_run(self._h, _ptr(xyz), _ptr(off), _ptr(labels), k, C.byref(out)))
+        try:
+            return _planes_to_numpy(out)
+        finally:
+            load().vm_planes_free(C.byref(out))
+
+    def launch(self, xyz, off, labels=None):
+        _check(load().vm_fit_plan_launch(self._h, _ptr(xyz), _ptr(off), _ptr(labels), int(off.numel()) - 1))
+
+    def wait(self):
+        _check(load().vm_fit_plan_wait(self._h, None))
+
+    @property
+    def tuning(self):
+        t = vm_fit_tuning()
+        _check(load().vm_fit_plan_get_tuning(self._h, C.byref(t)))
+        return _tuning_dict(t)
+
+    def set_tuning(self, tile, hyp_per_thread, ctas_per_sm, schedule="cta"):
+        t = vm_fit_tuning(int(tile), int(hyp_per_thread), int(ctas_per_sm), 1 if schedule == "warp" else 0)
+        _check(load().vm_fit_plan_set_tuning(self._h, C.byref(t)))
+
+    def autotune(self, xyz, off, labels=None, reps=2):
+        """Times every candidate schedule on this batch and keeps the fastest;
+        returns (tuning dict, ms per fit, candidates timed)."""
+        t, ms, n = vm_fit_tuning(), C.c_float(), C.c_uint32()
+        _check(load().vm_fit_plan_autotune(self._h, _ptr(xyz), _ptr(off), _ptr(labels), int(off.numel()) - 1,
+                                           int(reps), C.byref(t), C.byref(ms), C.byref(n)))
+        return _tuning_dict(t), float(ms.value), int(n.value)
 
 
 def stage_times(handle=None):

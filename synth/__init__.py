@@ -18,7 +18,8 @@ Workloads:
   8-step open-tread stair, a desk with a 0.4 m overhang, a 15 deg ramp, floor and
   20 random boxes; frame f uses noise seed f.
 * ``config3_clusters``: caller-formed clusters, sizes log-uniform in
-  [50, 200000], tilts U[0, 35 deg], 5 % outliers, seed 7.
+  [50, 200000], tilts U[0, 35 deg], 5 % outliers, seed 7
+  (``config3_clusters_device``: the same recipe generated on a torch device).
 * ``e5_clusters``: the paper's cluster-parallel ablation (1-16 clusters of M in
   [10k, 30k] points).
 * ``config4_streams``: serving streams with random extents and resolutions.
@@ -31,7 +32,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["MapSpec", "config1", "config2_spec", "config2_scene", "config2_frame", "config2_pose",
-           "config3_clusters", "e5_clusters", "Scene", "Camera", "config4_streams", "identity_pose"]
+           "config3_clusters", "config3_clusters_device", "e5_clusters", "Scene", "Camera", "config4_streams", "identity_pose"]
 
 
 @dataclass
@@ -370,6 +371,55 @@ def config3_clusters(n_clusters: int = 2000, seed: int = 7, size_lo: int = 50, s
         xyz[off[k]:off[k + 1]] = p
         normals[k] = n
     return xyz, off.astype(np.uint32), normals
+
+
+def config3_clusters_device(n_clusters: int = 2000, seed: int = 7, size_lo: int = 50, size_hi: int = 200000,
+                            max_tilt_deg: float = 35.0, outlier_frac: float = 0.05, device="cuda"):
+    """The config-3 recipe generated on a torch device (the 48 M-point batch
+    takes about 30 s in numpy): per-cluster sizes, tilts, azimuths and centres
+    from numpy's PCG64(seed) as in ``config3_clusters``; lattice jitter, normal
+    noise and outliers from a torch generator seeded with ``seed``, each point
+    an outlier with probability ``outlier_frac`` (uniform in its cluster's
+    box padded by 0.05 m).  Returns xyz float32[sum, 3] and off int32[k+1] (the
+    same bits as uint32: every offset is below 2^31) as torch tensors on
+    ``device``, and the true normals float64[k, 3] on the host."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.exp(rng.uniform(math.log(size_lo), math.log(size_hi), n_clusters)).astype(np.int64)
+    sizes = np.clip(sizes, size_lo, size_hi)
+    tilt = np.radians(rng.uniform(0, max_tilt_deg, n_clusters))
+    az = rng.uniform(0, 2 * math.pi, n_clusters)
+    center = rng.uniform(-8, 8, (n_clusters, 3)) * np.array([1, 1, 0.1])
+    n = np.stack([np.sin(tilt) * np.cos(az), np.sin(tilt) * np.sin(az), np.cos(tilt)], 1)
+    a = np.where(np.abs(n[:, :1]) < 0.9, np.array([[1.0, 0, 0]]), np.array([[0, 1.0, 0]]))
+    e1 = np.cross(a, n)
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(n, e1)
+    off = np.zeros(n_clusters + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    f64 = dict(dtype=torch.float64, device=device)
+    cid = torch.repeat_interleave(torch.arange(n_clusters, device=device), torch.as_tensor(sizes, device=device))
+    idx = torch.arange(int(off[-1]), device=device) - torch.as_tensor(off[:-1], device=device)[cid]
+    side = torch.as_tensor(np.ceil(np.sqrt(sizes)), **f64)[cid]
+    jit = 0.003
+    u = (torch.remainder(idx, side) - (side - 1) / 2) * 0.01 + (torch.rand(idx.shape, generator=g, **f64) * 2 - 1) * jit
+    v = (torch.div(idx, side, rounding_mode="floor") - (side - 1) / 2) * 0.01 \
+        + (torch.rand(idx.shape, generator=g, **f64) * 2 - 1) * jit
+    w = torch.randn(idx.shape, generator=g, **f64) * 0.001
+    C_, N_ = torch.as_tensor(center, **f64), torch.as_tensor(n, **f64)
+    E1, E2 = torch.as_tensor(e1, **f64), torch.as_tensor(e2, **f64)
+    p = C_[cid] + u[:, None] * E1[cid] + v[:, None] * E2[cid] + w[:, None] * N_[cid]
+    lo = torch.full((n_clusters, 3), float("inf"), **f64).scatter_reduce(0, cid[:, None].expand(-1, 3), p, "amin")
+    hi = torch.full((n_clusters, 3), float("-inf"), **f64).scatter_reduce(0, cid[:, None].expand(-1, 3), p, "amax")
+    lo, hi = lo - 0.05, hi + 0.05
+    out = torch.rand(idx.shape, generator=g, **f64) < outlier_frac
+    r = torch.rand((int(off[-1]), 3), generator=g, **f64)
+    q = lo[cid] + r * (hi - lo)[cid]
+    p = torch.where(out[:, None], q, p)
+    assert off[-1] < 2**31
+    return (p.to(torch.float32).contiguous(), torch.as_tensor(off.astype(np.int32), device=device), n)
 
 
 def e5_clusters(n_clusters: int, seed: int, m_lo: int = 10000, m_hi: int = 30000):

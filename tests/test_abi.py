@@ -43,8 +43,9 @@ def test_binding_struct_sizes_match_header():
 #include <stddef.h>
 #include "vm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(vm_map_params), sizeof(vm_segment_params), sizeof(vm_plane),
-         sizeof(vm_planes), sizeof(vm_stats), offsetof(vm_plane, hull_offset), offsetof(vm_segment_params, seed));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(vm_map_params), sizeof(vm_segment_params), sizeof(vm_plane),
+         sizeof(vm_planes), sizeof(vm_stats), offsetof(vm_plane, hull_offset), offsetof(vm_segment_params, seed),
+         sizeof(vm_fit_tuning));
   return 0;
 }
 '''
@@ -57,7 +58,7 @@ int main(void) {
     got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(vm.vm_map_params), C.sizeof(vm.vm_segment_params), C.sizeof(vm.vm_plane),
             C.sizeof(vm.vm_planes), C.sizeof(vm.vm_stats), vm.vm_plane.hull_offset.offset,
-            vm.vm_segment_params.seed.offset]
+            vm.vm_segment_params.seed.offset, C.sizeof(vm.vm_fit_tuning)]
     assert got == want
 
 
