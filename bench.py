@@ -62,6 +62,8 @@ def parse():
                     help="profiling driver: integrate frames 1..F, segment --profile-segments times, no timing")
     ap.add_argument("--profile-segments", type=int, default=3)
     ap.add_argument("--no-batching", action="store_true", help="skip the batched-fit and cluster-parallel variants")
+    ap.add_argument("--no-serving", action="store_true", help="skip the 16-stream serving variant")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="Poisson-arrival serving run length")
     ap.add_argument("--profile-fit", type=int, default=0, metavar="K",
                     help="profiling driver: K config-3 clusters (sizes log-uniform in [50, 200000]), "
                          "3 fits with the default schedule, no timing")
@@ -217,6 +219,144 @@ def e5_variant(stream, runs=1000):
     return {"runs": runs, "n_hyp": 100, "by_clusters": out}
 
 
+def serving_variant(dev, seconds, frames_per_stream=32, backlog=24):
+    """Config 4: 16 streams (extents U[2, 6] m x 2 m, resolutions from {0.01,
+    0.02, 0.05} m), 307,200-point frames from the config-2 camera over each
+    stream's own stair/desk/ramp scene, maps resident on the device.
+    saturation: every stream given `backlog` frames at once; frames/s of the
+    batched server, the per-stream-graph server, and the plain per-frame
+    pipeline (one map at a time, one synchronous integrate + segment call per
+    frame).  poisson: arrivals at 30 Hz per stream for `seconds` s, latency =
+    arrival to result on the host (server clock)."""
+    import threading
+
+    import numpy as np
+    import torch
+    from paper_2510_01592_gb300 import serve, vm
+    import synth
+    sts = synth.config4_streams(16)
+    data = []
+    for st in sts:
+        sc = synth.config4_scene(st)
+        fr = [synth.config4_frame(st, sc, f, device=dev) for f in range(frames_per_stream)]
+        nb = 1
+        for d in st.spec.dims:
+            nb *= (d + 7) // 8
+        data.append((st, fr, min(nb, 16384)))
+    torch.cuda.synchronize()
+    params = vm.segment_params(n_hyp=100, seed=0)
+    out = {"streams": len(sts), "resolutions_m": sorted({st.spec.voxel_size for st in sts}),
+           "frames_pregenerated_per_stream": frames_per_stream}
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))] if v else None
+
+    def saturate(mode):
+        srv = serve.Server(params, mode=mode, max_batch=16, max_inflight=2, device=dev.index or 0)
+        ids = [srv.open(st.spec.dims, st.spec.origin, st.spec.voxel_size, cap) for st, _, cap in data]
+        for j in range(2):  # warm-up: maps allocate and graphs are captured
+            for (st, fr, _), sid in zip(data, ids):
+                srv.submit(sid, fr[j][0], fr[j][1])
+        srv.drain()
+        srv.poll(256, with_planes=False)
+        n = 0
+        t0 = srv.now()
+        for j in range(2, 2 + backlog):
+            for (st, fr, _), sid in zip(data, ids):
+                srv.submit(sid, fr[j % len(fr)][0], fr[j % len(fr)][1], t_arrival=t0)
+                n += 1
+        srv.drain()
+        t1 = srv.now()
+        res = []
+        while len(res) < n:
+            res += srv.poll(256, timeout_ms=1000, with_planes=False)
+        assert all(r["status"] == vm.VM_OK for r in res)
+        st = srv.stats()
+        srv.close()
+        return {"frames_per_s": round(n / (t1 - t0), 2), "frames": n,
+                "mean_requests_per_step": round(st["mean_step_requests"], 2), "fallbacks": st["fallbacks"],
+                "hbm_committed_gb": round(st["hbm_committed"] / 1e9, 2),
+                "scheduler_launch_s": round(st["launch_seconds"], 4),
+                "scheduler_complete_s": round(st["complete_seconds"], 4), "wall_s": round(t1 - t0, 4)}
+
+    out["saturation_batched"] = saturate("batched")
+    out["saturation_streams"] = saturate("streams")
+    # the plain per-frame pipeline: one map at a time, a synchronous call per frame
+    maps = [vm.VoxelMap(st.spec.dims, st.spec.origin, st.spec.voxel_size, brick_capacity=cap)
+            for st, _, cap in data]
+    for j in range(2):
+        for m, (st, fr, _) in zip(maps, data):
+            m.integrate(fr[j][0], fr[j][1])
+            m.segment(params)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n = 0
+    for j in range(2, 2 + backlog):
+        for m, (st, fr, _) in zip(maps, data):
+            m.integrate(fr[j % len(fr)][0], fr[j % len(fr)][1])
+            m.segment(params)
+            n += 1
+    plain = n / (time.perf_counter() - t0)
+    for m in maps:
+        m.close()
+    out["saturation_plain_per_frame"] = {"frames_per_s": round(plain, 2), "frames": n}
+    out["served_vs_plain"] = round(out["saturation_batched"]["frames_per_s"] / plain, 3)
+    # Poisson arrivals at 30 Hz per stream
+    srv = serve.Server(params, mode="batched", max_batch=16, max_inflight=2, device=dev.index or 0)
+    ids = [srv.open(st.spec.dims, st.spec.origin, st.spec.voxel_size, cap) for st, _, cap in data]
+    for (st, fr, _), sid in zip(data, ids):
+        srv.submit(sid, fr[0][0], fr[0][1])
+    srv.drain()
+    srv.poll(256, with_planes=False)
+    sched = []
+    for k, (st, fr, _) in enumerate(data):
+        for j, t in enumerate(synth.poisson_arrivals(st.rate_hz, seconds, st.arrival_seed)):
+            sched.append((float(t), k, 1 + j))
+    sched.sort()
+    results = []
+    stop = threading.Event()
+
+    def poller():
+        while not stop.is_set():
+            results.extend(srv.poll(256, timeout_ms=50, with_planes=False))
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = srv.now() + 0.05
+    for t, k, j in sched:
+        ta = t0 + t
+        while True:
+            dt = ta - srv.now()
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 0.002) if dt > 0.0003 else 0)
+        st, fr, _ = data[k]
+        srv.submit(ids[k], fr[j % len(fr)][0], fr[j % len(fr)][1], t_arrival=ta)
+    srv.drain()
+    t_end = srv.now()
+    stop.set()
+    th.join()
+    results.extend(srv.poll(256, with_planes=False))
+    lat = [1e3 * (r["t_done"] - r["t_arrival"]) for r in results]
+    per_stream = {}
+    for r in results:
+        per_stream.setdefault(r["stream"], []).append(1e3 * (r["t_done"] - r["t_arrival"]))
+    st = srv.stats()
+    srv.close()
+    out["poisson_30hz"] = {
+        "seconds": seconds, "frames": len(results), "offered_frames_per_s": round(len(sched) / seconds, 1),
+        "achieved_frames_per_s": round(len(results) / (t_end - t0), 1),
+        "latency_ms": {"p50": round(pct(lat, 0.5), 3), "p99": round(pct(lat, 0.99), 3), "max": round(max(lat), 3)},
+        "worst_stream_p99_ms": round(max(pct(v, 0.99) for v in per_stream.values()), 3),
+        "mean_requests_per_step": round(st["mean_step_requests"], 2),
+        "ok": all(r["status"] == vm.VM_OK for r in results),
+    }
+    del data
+    torch.cuda.empty_cache()
+    return out
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -330,6 +470,8 @@ def run_gpu(args):
     first, sched = frame_schedule(args.steps, args.warmup)
     params = seg_params(vm)
     stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(stream)  # the maps' stream is torch's current one: no cross-stream waits per frame
 
     def fresh_map(timing=False):
         m = vm.VoxelMap(spec.dims, spec.origin, spec.voxel_size, stream=stream, stage_timing=timing)
@@ -465,6 +607,8 @@ def run_gpu(args):
         alu_peak = SM_COUNT * FP32_LANES * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         res["variants"]["batching_config3"] = batching_variant(dev, stream, alu_peak)
         res["variants"]["cluster_parallel_e5"] = e5_variant(stream)
+    if not args.no_serving and rank == 0:
+        res["variants"]["serving_config4"] = serving_variant(dev, args.serve_seconds)
     res["stages_ms_per_step"] = {k: round(v[0] / max(1, args.steps), 4) for k, v in stages.items() if v[1]}
     table = kernel_table(stages, st, load_peaks(), st["clustered_points"])
     res["kernels"] = table

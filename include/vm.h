@@ -274,6 +274,103 @@ vm_status vm_export_labels(vm_map* map, uint32_t* vid, float* normal, uint8_t* s
  * arrays; any may be NULL; *n receives the point count.  Synchronises. */
 vm_status vm_export_clusters(vm_map* map, float* pts, uint32_t* vid, uint8_t* inlier, uint32_t cap, uint32_t* n);
 
+/* ---- Serving ---------------------------------------------------------------
+ * The paper runs one robot's map.  A server runs many sensor streams at once,
+ * each with its own map kept resident on the device (no counterpart in the
+ * paper; every request computes exactly the paper's integrate + segment for
+ * its stream, and its result is the same as that stream's alone).
+ * A request integrates one frame into its stream's map (Sec. III.B) and
+ * segments the map (Sec. III.C).  Requests of one stream run in submission
+ * order; requests of different streams overlap on the GPU.  A scheduler thread
+ * owned by the server forms steps as requests arrive and GPU slots free up
+ * (continuous batching): in VM_SERVE_BATCHED mode each request of a step
+ * integrates and runs the front half of its segmentation (brick order ..
+ * cluster points) on its map's stream, then the clusters of every map in the
+ * step go through one batched fit (one persistent RANSAC launch, refit and
+ * hull over all of them) on the server's stream, and each map's planes are
+ * packed into its own result block; in VM_SERVE_STREAMS mode each request
+ * replays its map's whole segmentation graph on its map's stream.
+ * Admission by device memory: a stream is admitted when its worst-case
+ * footprint (map pool at its brick capacity, segmentation scratch, result
+ * block, input staging) fits in what is left of the budget; until then it
+ * waits, its requests queued, and streams are admitted in the order they were
+ * opened as closing streams free memory. */
+typedef struct vm_server vm_server; /* opaque, library-owned */
+
+#define VM_SERVE_BATCHED 0u
+#define VM_SERVE_STREAMS 1u
+
+typedef struct {
+    uint32_t mode;             /* VM_SERVE_BATCHED or VM_SERVE_STREAMS                       */
+    uint32_t max_batch;        /* requests per step at most, 1..64                           */
+    uint32_t max_inflight;     /* steps on the GPU at once, 1..4 (VM_SERVE_STREAMS: requests
+                                  in flight at once is max_batch * max_inflight)              */
+    uint32_t device;           /* CUDA device ordinal the server runs on                     */
+    uint64_t hbm_budget;       /* bytes the streams may hold; 0: free device memory at
+                                  creation minus hbm_reserve                                  */
+    uint64_t hbm_reserve;      /* bytes kept free when hbm_budget is 0                        */
+    vm_segment_params params;  /* segmentation parameters of every request                   */
+    vm_fit_tuning tuning;      /* batched-fit schedule; tile 0 = the library default          */
+} vm_server_params;
+
+typedef struct {
+    uint64_t ticket;           /* from vm_server_submit                                      */
+    uint32_t stream;           /* stream id                                                  */
+    vm_status status;          /* of this request (its planes are valid when VM_OK)          */
+    vm_planes planes;          /* host memory owned by the caller: release with vm_planes_free */
+    double t_arrival;          /* seconds on the server clock (vm_server_now)                */
+    double t_start;            /* the request's step was launched                            */
+    double t_done;             /* the result was ready on the host                           */
+} vm_server_result;
+
+typedef struct {
+    uint32_t streams_open;     /* opened and not yet closed                                  */
+    uint32_t streams_admitted; /* holding a map on the device                                */
+    uint32_t streams_waiting;  /* opened, waiting for memory                                 */
+    uint32_t reserved;
+    uint64_t requests_submitted, requests_done, steps;
+    uint64_t fallbacks;        /* requests re-run on their own map's path after a capacity miss */
+    uint64_t hbm_budget, hbm_committed;
+    double mean_step_requests; /* requests per step                                          */
+    double launch_seconds;     /* scheduler-thread time spent launching steps                */
+    double complete_seconds;   /* scheduler-thread time spent completing steps (result copies) */
+} vm_server_stats;
+
+/* Creates a server and starts its scheduler thread.  Errors:
+ * VM_ERR_INVALID_ARG, VM_ERR_OUT_OF_MEMORY, VM_ERR_CUDA. */
+vm_status vm_server_create(const vm_server_params* params, vm_server** out);
+/* Opens a stream with its own map (params as vm_create); returns at once with
+ * *stream_id.  The map is created when the stream is admitted.
+ * VM_ERR_OUT_OF_MEMORY when its footprint exceeds the whole budget (it could
+ * never be admitted); VM_ERR_INVALID_ARG / VM_ERR_EXTENT as vm_create. */
+vm_status vm_server_open(vm_server* srv, const vm_map_params* map, uint32_t* stream_id);
+/* Queues a request on a stream: xyz float32[n][3] in the sensor frame (device
+ * memory if xyz_on_device, else host memory), pose3x4 copied.  xyz must stay
+ * valid until the request's result has been polled.  t_arrival: the arrival
+ * time on the server clock, or a negative value for now.  *ticket (may be
+ * NULL) identifies the result.  Errors: VM_ERR_INVALID_ARG (unknown or closed
+ * stream). */
+vm_status vm_server_submit(vm_server* srv, uint32_t stream_id, const float* xyz, uint32_t n, const float pose3x4[12],
+                           int xyz_on_device, double t_arrival, uint64_t* ticket);
+/* Moves up to cap finished results into out[] (oldest first), waiting up to
+ * timeout_ms (0: no wait, negative: until one is there) for the first; *n
+ * receives the count. */
+vm_status vm_server_poll(vm_server* srv, vm_server_result* out, uint32_t cap, uint32_t* n, int timeout_ms);
+/* Waits until every submitted request has a result ready to poll (up to
+ * timeout_ms; negative: no limit).  VM_ERR_TIMEOUT when the time ran out. */
+vm_status vm_server_drain(vm_server* srv, int timeout_ms);
+/* Closes a stream: its queued requests still run; then its map is destroyed
+ * and its memory returns to the budget. */
+vm_status vm_server_close(vm_server* srv, uint32_t stream_id);
+vm_status vm_server_get_stats(vm_server* srv, vm_server_stats* out);
+/* Device bytes vm_server_open would reserve for a map with these parameters. */
+uint64_t vm_server_footprint(const vm_map_params* map, const vm_segment_params* params);
+/* The server clock: seconds since the server was created (monotonic). */
+double vm_server_now(vm_server* srv);
+/* Stops the scheduler after the requests in flight, destroys every map.
+ * Results not polled are released. */
+vm_status vm_server_destroy(vm_server* srv);
+
 /* Diagnostics (no counterpart in the paper).  Stage timing records CUDA
  * events around each pipeline stage on the stream it runs on: integrate,
  * order_bricks, finalize, moments, eigen, ccl_local, ccl_cross, clusters,

@@ -221,6 +221,38 @@ static vm_status fit_and_pack(FitContext& fc, const float* pts, const uint32_t* 
 
 
 
+static size_t vox_tmp_words(size_t nv, uint32_t nb_total) {
+    size_t a = scan_tmp_words(nv + 1), b = sort_tmp_words(nv);
+    size_t c = scan_tmp_words((size_t)nb_total + 1);
+    size_t r = a > b ? a : b;
+    return r > c ? r : c;
+}
+
+// The rank-dense voxel arrays of nv slots, carved in order.
+static void vox_layout(Carver& c, SegBuffers& b, size_t nv, size_t tmp_words) {
+    b.M = c.take<int32_t>(3 * nv);
+    b.nrm = c.take<float>(3 * nv);
+    b.status = c.take<uint8_t>(nv);
+    b.nbr = c.take<uint8_t>(nv);
+    b.rec = c.take<float4>(2 * nv);
+    b.list_idx = c.take<uint32_t>(nv);
+    b.list_A = c.take<float>(6 * nv);
+    b.parent = c.take<uint32_t>(nv);
+    b.count = c.take<uint32_t>(nv);
+    b.cid = c.take<uint32_t>(nv + 1);
+    b.vert_flag = c.take<uint32_t>(nv + 1);
+    b.keys = c.take<uint32_t>(nv);
+    b.vals = c.take<uint32_t>(nv);
+    b.keys_alt = c.take<uint32_t>(nv);
+    b.vals_alt = c.take<uint32_t>(nv);
+    b.cl_size = c.take<uint32_t>(nv + 1);
+    b.cl_off = c.take<uint32_t>(nv + 1);
+    b.cl_label = c.take<uint32_t>(nv + 1);
+    b.pts = c.take<float>(3 * nv);
+    b.pt_vid = c.take<uint32_t>(nv);
+    b.scan_tmp = c.take<uint32_t>(tmp_words);
+}
+
 vm_status alloc_vox(vm_map* m, uint32_t n_bricks) {
     const size_t need = (size_t)(n_bricks ? n_bricks : 1) * kBrickVox;
     if (m->vox_mem.p && need <= m->seg_nv) return VM_OK;
@@ -228,45 +260,35 @@ vm_status alloc_vox(vm_map* m, uint32_t n_bricks) {
     const size_t cap_nv = (size_t)m->capacity * kBrickVox;
     if (nv > cap_nv) nv = cap_nv;
     m->gen++;
-    const size_t tmp_words = [&] {
-        size_t a = scan_tmp_words(nv + 1), b = sort_tmp_words(nv);
-        size_t c = scan_tmp_words((size_t)m->nb_total + 1);
-        size_t r = a > b ? a : b;
-        return r > c ? r : c;
-    }();
-    auto layout = [&](Carver& c, SegBuffers& b) {
-        b.M = c.take<int32_t>(3 * nv);
-        b.nrm = c.take<float>(3 * nv);
-        b.status = c.take<uint8_t>(nv);
-        b.nbr = c.take<uint8_t>(nv);
-        b.rec = c.take<float4>(2 * nv);
-        b.list_idx = c.take<uint32_t>(nv);
-        b.list_A = c.take<float>(6 * nv);
-        b.parent = c.take<uint32_t>(nv);
-        b.count = c.take<uint32_t>(nv);
-        b.cid = c.take<uint32_t>(nv + 1);
-        b.vert_flag = c.take<uint32_t>(nv + 1);
-        b.keys = c.take<uint32_t>(nv);
-        b.vals = c.take<uint32_t>(nv);
-        b.keys_alt = c.take<uint32_t>(nv);
-        b.vals_alt = c.take<uint32_t>(nv);
-        b.cl_size = c.take<uint32_t>(nv + 1);
-        b.cl_off = c.take<uint32_t>(nv + 1);
-        b.cl_label = c.take<uint32_t>(nv + 1);
-        b.pts = c.take<float>(3 * nv);
-        b.pt_vid = c.take<uint32_t>(nv);
-        b.scan_tmp = c.take<uint32_t>(tmp_words);
-    };
+    const size_t tmp_words = vox_tmp_words(nv, m->nb_total);
     Carver dry{nullptr};
     SegBuffers tmp{};
-    layout(dry, tmp);
+    vox_layout(dry, tmp, nv, tmp_words);
     VM_TRY(ensure(m->vox_mem, dry.off + 256));
     Carver c{static_cast<char*>(m->vox_mem.p)};
-    layout(c, m->seg);
+    vox_layout(c, m->seg, nv, tmp_words);
     m->seg.nv = nv;
     m->seg.kcap = nv;
     m->seg_nv = nv;
     return VM_OK;
+}
+
+uint64_t map_footprint(const vm_map_params& p, const vm_segment_params& sp) {
+    uint64_t nb = 1;
+    for (int a = 0; a < 3; ++a) nb *= (uint64_t)((p.dims[a] + kBrick - 1) / kBrick);
+    const uint64_t cap = p.brick_capacity && p.brick_capacity < nb ? p.brick_capacity : nb;
+    const uint64_t pool = nb * 4 + cap * 4 + cap * kBrickVox * (3 * 8 + 4) + 4096;
+    const uint64_t bricks = (nb + 1) * 4 + nb * 4 + cap * 8 + 4096;
+    const size_t nv = (size_t)cap * kBrickVox;
+    Carver dry{nullptr};
+    SegBuffers tmp{};
+    vox_layout(dry, tmp, nv, vox_tmp_words(nv, (uint32_t)nb));
+    const uint32_t mc = sp.min_cluster > 16 ? sp.min_cluster : 16;
+    const uint64_t kcap = nv / mc > 256 ? nv / mc : 256;
+    const uint64_t hcap = 65536 + kcap * 16;
+    const uint64_t out = 256 + kcap * sizeof(vm_plane) + hcap * 20 + 1024;
+    const uint64_t stage = 16ull << 20;  // host-input staging for frames of up to ~1.4 M points
+    return pool + bricks + (uint64_t)dry.off * 5 / 4 + out + stage;
 }
 
 size_t out_planes_off() { return 256; }
@@ -298,7 +320,7 @@ vm_status ensure_out(vm_map* m, uint32_t kcap, uint32_t hcap) {
 
 // Sizes the scratch from the last known counts with headroom; a launch whose
 // counts still do not fit raises kErrScratch and the caller retries.
-vm_status plan_capacity(vm_map* m, const vm_segment_params& p) {
+vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit) {
     const uint32_t want_b = m->brick_hint + m->brick_hint / 4 + 64;
     const uint32_t cap_b = want_b < m->capacity ? want_b : m->capacity;
     if (!m->vox_mem.p || (size_t)cap_b * kBrickVox > m->seg_nv) VM_TRY(alloc_vox(m, cap_b));
@@ -311,9 +333,11 @@ vm_status plan_capacity(vm_map* m, const vm_segment_params& p) {
     if (kcap > nv) kcap = nv;
     if (kcap < m->kcap) kcap = m->kcap;  // never shrink: keeps the captured graph valid
     m->kcap = (uint32_t)kcap;
-    const uint64_t g0 = m->fit.gen;
-    VM_TRY(fit_prepare(m->fit, kcap, nv, (int)p.n_hyp, m->tune.tile));
-    if (m->fit.gen != g0) m->gen++;
+    if (with_fit) {
+        const uint64_t g0 = m->fit.gen;
+        VM_TRY(fit_prepare(m->fit, kcap, nv, (int)p.n_hyp, m->tune.tile));
+        if (m->fit.gen != g0) m->gen++;
+    }
     uint32_t hcap = m->hull_hint + m->hull_hint / 2 + 4096;
     if (hcap < 65536) hcap = 65536;
     if (hcap < m->out_hcap) hcap = m->out_hcap;
@@ -341,7 +365,6 @@ cudaError_t enqueue_front(vm_map* m, const vm_segment_params& p, StageHook* hk) 
     SegBuffers& b = m->seg;
     cudaError_t e;
     if ((e = cudaMemsetAsync(m->err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(m->fit.fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     VM_STAGE_BEGIN(hk, kStOrder, s);
     if ((e = seg_order_bricks(m->brick_table, m->nb_total, b, sms, s)) != cudaSuccess) return e;
     VM_STAGE_END(hk, kStOrder, s);
@@ -354,6 +377,7 @@ cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk
     SegBuffers& b = m->seg;
     FitBuffers& fb = m->fit.fb;
     cudaError_t e;
+    if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     if ((e = enqueue_front(m, p, hk)) != cudaSuccess) return e;
     if ((e = launch_fit(b.pts, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, p, fb, m->tune, sms, s, hk)) != cudaSuccess)
         return e;
@@ -414,7 +438,7 @@ vm_status launch_segment(vm_map* m, const vm_segment_params& p) {
         VM_CUDA(cudaStreamSynchronize(s));
         m->brick_hint = c.n_bricks < m->capacity ? c.n_bricks : m->capacity;
     }
-    VM_TRY(plan_capacity(m, p));
+    VM_TRY(plan_capacity(m, p, true));
     StageHook* hk = m->fit.timer.hook();
     if (m->use_graph && !hk && (!m->gexec || m->ggen != m->gen || memcmp(&m->gprm, &p, sizeof(p)) != 0)) {
         if (capture_segment(m, p) != VM_OK) {  // e.g. a stream that cannot be captured: launch eagerly
@@ -431,10 +455,62 @@ vm_status launch_segment(vm_map* m, const vm_segment_params& p) {
     return VM_OK;
 }
 
+static vm_status capture_front(vm_map* m, const vm_segment_params& p) {
+    if (m->fexec) {
+        cudaGraphExecDestroy(m->fexec);
+        m->fexec = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    const unsigned long long l0 = launch_total();
+    VM_CUDA(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_front(m, p, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(m->stream, &graph);
+    m->flaunches = launch_total() - l0;
+    uncount_launch(m->flaunches);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_status(e, "front capture");
+    }
+    if (e2 != cudaSuccess) return cuda_status(e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&m->fexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        m->fexec = nullptr;
+        return cuda_status(e, "cudaGraphInstantiate");
+    }
+    m->fgen = m->gen;
+    m->fprm = p;
+    return VM_OK;
+}
+
+vm_status launch_front(vm_map* m, const vm_segment_params& p) {
+    cudaStream_t s = m->stream;
+    if (!m->vox_mem.p) {
+        MapCounters c;
+        VM_CUDA(cudaMemcpyAsync(&c, m->ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
+        VM_CUDA(cudaStreamSynchronize(s));
+        m->brick_hint = c.n_bricks < m->capacity ? c.n_bricks : m->capacity;
+    }
+    VM_TRY(plan_capacity(m, p, false));
+    if (m->use_graph && (!m->fexec || m->fgen != m->gen || memcmp(&m->fprm, &p, sizeof(p)) != 0)) {
+        if (capture_front(m, p) != VM_OK) {
+            cudaGetLastError();
+            m->use_graph = false;
+        }
+    }
+    if (m->use_graph) {
+        VM_CUDA(cudaGraphLaunch(m->fexec, s));
+        count_launch((int)m->flaunches);
+    } else {
+        VM_CUDA(enqueue_front(m, p, nullptr));
+    }
+    return VM_OK;
+}
+
 // True when the completed segmentation in the result block ran out of a
 // capacity (scratch or hull output) and must be re-run; updates the hints
 // that size the next attempt.
-static bool take_hints(vm_map* m) {
+bool take_hints(vm_map* m) {
     const SegCounters* hdr = static_cast<const SegCounters*>(m->out_host);
     m->brick_hint = hdr->n_bricks < m->capacity ? hdr->n_bricks : m->capacity;
     m->k_hint = hdr->k;
@@ -621,6 +697,7 @@ vm_status vm_destroy(vm_map* m) {
     release(m->vox_mem);
     fit_release(m->fit);
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
+    if (m->fexec) cudaGraphExecDestroy(m->fexec);
     if (m->out_host) cudaFreeHost(m->out_host);
     if (m->hctr) cudaFreeHost(m->hctr);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);

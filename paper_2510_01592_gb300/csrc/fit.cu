@@ -801,41 +801,9 @@ __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restr
                        int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz, uint32_t hull_cap) {
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
-        const FitCluster f = cl[c];
-        const uint32_t ho = hull_off[c], hn = hull_off[c + 1] - ho;
-        if (threadIdx.x == 0) {
-            vm_plane p;
-            for (int a = 0; a < 3; ++a) {
-                p.normal[a] = f.refit_n[a];
-                p.ransac_normal[a] = f.n[a];
-                p.basis_u[a] = f.u[a];
-                p.basis_v[a] = f.v[a];
-                p.hull_origin[a] = f.o[a];
-            }
-            p.offset = f.refit_d;
-            p.ransac_offset = f.d;
-            p.inlier_count = f.inliers;
-            p.label = labels ? labels[c] : c;
-            p.hull_offset = ho;
-            p.hull_count = hn;
-            p.n_points = off[c + 1] - off[c];
-            p.best_h = f.best_h;
-            p.flags = f.flags;
-            planes[c] = p;
-        }
-        for (uint32_t i = threadIdx.x; i < hn && ho + i < hull_cap; i += blockDim.x) {
-            const int2 q = hull[off[c] + i];
-            hull_xy[2 * (ho + i)] = q.x;
-            hull_xy[2 * (ho + i) + 1] = q.y;
-            const float a = q.x * (1.0f / 65536.0f), b = q.y * (1.0f / 65536.0f);
-            float x = f.o[0] + a * f.u[0] + b * f.v[0];
-            float y = f.o[1] + a * f.u[1] + b * f.v[1];
-            float z = f.o[2] + a * f.u[2] + b * f.v[2];
-            const float e = f.refit_n[0] * x + f.refit_n[1] * y + f.refit_n[2] * z + f.refit_d;
-            hull_xyz[3 * (ho + i)] = x - e * f.refit_n[0];
-            hull_xyz[3 * (ho + i) + 1] = y - e * f.refit_n[1];
-            hull_xyz[3 * (ho + i) + 2] = z - e * f.refit_n[2];
-        }
+        const uint32_t ho = hull_off[c];
+        pack_cluster(cl[c], labels ? labels[c] : c, off[c + 1] - off[c], hull + off[c], ho, hull_off[c + 1] - ho,
+                     planes + c, hull_xy, hull_xyz, hull_cap);
     }
 }
 

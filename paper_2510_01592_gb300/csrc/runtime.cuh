@@ -152,6 +152,11 @@ struct vm_map {
     uint64_t ggen = ~0ull;
     vm_segment_params gprm{};
     unsigned long long glaunches = 0;
+    // captured front half (brick order .. cluster points), for batched serving
+    cudaGraphExec_t fexec = nullptr;
+    uint64_t fgen = ~0ull;
+    vm_segment_params fprm{};
+    unsigned long long flaunches = 0;
 };
 
 namespace vmx {
@@ -159,8 +164,20 @@ namespace vmx {
 vm_status check_map(vm_map* m);
 vm_status alloc_vox(vm_map* m, uint32_t n_bricks);
 vm_status ensure_out(vm_map* m, uint32_t kcap, uint32_t hcap);
-// Sizes the map's scratch and result block for a segmentation with p.
-vm_status plan_capacity(vm_map* m, const vm_segment_params& p);
+// Sizes the map's scratch and result block for a segmentation with p (and
+// its own fit scratch when with_fit).
+vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit);
+// Device bytes a map with these parameters can come to hold at its brick
+// capacity: pool, segmentation scratch, result block and input staging (its
+// own fit scratch, used only when a batched fit falls back, is not counted).
+uint64_t map_footprint(const vm_map_params& p, const vm_segment_params& sp);
+// Launches only the front half of a segmentation (graph replay when enabled):
+// the map's cluster points, offsets, labels and counters are ready once the
+// map's stream reaches this point.
+vm_status launch_front(vm_map* m, const vm_segment_params& p);
+// Updates the sizing hints from the map's result block; true when the last
+// segmentation ran out of a capacity and must be re-run.
+bool take_hints(vm_map* m);
 // Front half of a segmentation (brick order .. cluster points), fit, pack +
 // header into the map's result block; the whole call.
 cudaError_t enqueue_front(vm_map* m, const vm_segment_params& p, StageHook* hk);

@@ -86,6 +86,50 @@ struct FitCluster {
     unsigned long long ext[16]; // filter extremes: (biased value << 32) | point index
 };
 
+// Writes one cluster's output record and its hull vertices (called by a whole
+// block; thread 0 writes the record): the quantised hull (2^-16 m units) and
+// its points lifted onto the refit plane.  ho is the cluster's first vertex in
+// the output arrays, hn its vertex count; vertices at or beyond hull_cap are
+// not written.
+__device__ __forceinline__ void pack_cluster(const FitCluster& f, uint32_t label, uint32_t n_points,
+                                             const int2* __restrict__ hull_src, uint32_t ho, uint32_t hn,
+                                             vm_plane* __restrict__ plane, int32_t* __restrict__ hull_xy,
+                                             float* __restrict__ hull_xyz, uint32_t hull_cap) {
+    if (threadIdx.x == 0) {
+        vm_plane p;
+        for (int a = 0; a < 3; ++a) {
+            p.normal[a] = f.refit_n[a];
+            p.ransac_normal[a] = f.n[a];
+            p.basis_u[a] = f.u[a];
+            p.basis_v[a] = f.v[a];
+            p.hull_origin[a] = f.o[a];
+        }
+        p.offset = f.refit_d;
+        p.ransac_offset = f.d;
+        p.inlier_count = f.inliers;
+        p.label = label;
+        p.hull_offset = ho;
+        p.hull_count = hn;
+        p.n_points = n_points;
+        p.best_h = f.best_h;
+        p.flags = f.flags;
+        *plane = p;
+    }
+    for (uint32_t i = threadIdx.x; i < hn && ho + i < hull_cap; i += blockDim.x) {
+        const int2 q = hull_src[i];
+        hull_xy[2 * (ho + i)] = q.x;
+        hull_xy[2 * (ho + i) + 1] = q.y;
+        const float a = q.x * (1.0f / 65536.0f), b = q.y * (1.0f / 65536.0f);
+        const float x = f.o[0] + a * f.u[0] + b * f.v[0];
+        const float y = f.o[1] + a * f.u[1] + b * f.v[1];
+        const float z = f.o[2] + a * f.u[2] + b * f.v[2];
+        const float e = f.refit_n[0] * x + f.refit_n[1] * y + f.refit_n[2] * z + f.refit_d;
+        hull_xyz[3 * (ho + i)] = x - e * f.refit_n[0];
+        hull_xyz[3 * (ho + i) + 1] = y - e * f.refit_n[1];
+        hull_xyz[3 * (ho + i) + 2] = z - e * f.refit_n[2];
+    }
+}
+
 // ---------------------------------------------------------------- diagnostics
 // Pipeline stages timed by the optional stage timer.
 enum Stage {

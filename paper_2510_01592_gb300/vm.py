@@ -73,6 +73,25 @@ class vm_fit_tuning(C.Structure):
                 ("schedule", C.c_uint32)]
 
 
+class vm_server_params(C.Structure):
+    _fields_ = [("mode", C.c_uint32), ("max_batch", C.c_uint32), ("max_inflight", C.c_uint32),
+                ("device", C.c_uint32), ("hbm_budget", C.c_uint64), ("hbm_reserve", C.c_uint64),
+                ("params", vm_segment_params), ("tuning", vm_fit_tuning)]
+
+
+class vm_server_result(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("stream", C.c_uint32), ("status", C.c_int), ("planes", vm_planes),
+                ("t_arrival", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
+class vm_server_stats(C.Structure):
+    _fields_ = [("streams_open", C.c_uint32), ("streams_admitted", C.c_uint32), ("streams_waiting", C.c_uint32),
+                ("reserved", C.c_uint32), ("requests_submitted", C.c_uint64), ("requests_done", C.c_uint64),
+                ("steps", C.c_uint64), ("fallbacks", C.c_uint64), ("hbm_budget", C.c_uint64),
+                ("hbm_committed", C.c_uint64), ("mean_step_requests", C.c_double), ("launch_seconds", C.c_double),
+                ("complete_seconds", C.c_double)]
+
+
 # name -> (restype, argtypes); every name is declared in include/vm.h
 _SIGS = {
     "vm_create": (C.c_int, [C.POINTER(vm_map_params), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -102,6 +121,18 @@ _SIGS = {
                                        C.POINTER(vm_fit_tuning), C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
     "vm_fit_plan_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32)]),
     "vm_fit_plan_destroy": (C.c_int, [C.c_void_p]),
+    "vm_server_create": (C.c_int, [C.POINTER(vm_server_params), C.POINTER(C.c_void_p)]),
+    "vm_server_open": (C.c_int, [C.c_void_p, C.POINTER(vm_map_params), C.POINTER(C.c_uint32)]),
+    "vm_server_submit": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32, C.POINTER(C.c_float), C.c_int,
+                                   C.c_double, C.POINTER(C.c_uint64)]),
+    "vm_server_poll": (C.c_int, [C.c_void_p, C.POINTER(vm_server_result), C.c_uint32, C.POINTER(C.c_uint32),
+                                 C.c_int]),
+    "vm_server_drain": (C.c_int, [C.c_void_p, C.c_int]),
+    "vm_server_close": (C.c_int, [C.c_void_p, C.c_uint32]),
+    "vm_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(vm_server_stats)]),
+    "vm_server_footprint": (C.c_uint64, [C.POINTER(vm_map_params), C.POINTER(vm_segment_params)]),
+    "vm_server_now": (C.c_double, [C.c_void_p]),
+    "vm_server_destroy": (C.c_int, [C.c_void_p]),
     "vm_stage_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "vm_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32)]),
     "vm_stage_name": (C.c_char_p, [C.c_uint32]),
@@ -181,6 +212,22 @@ def _stream_handle(stream):
     return C.c_void_p(int(stream))
 
 
+def order_after_torch(xyz, stream=None):
+    """Makes work on `stream` (a torch stream the library will use, or None for
+    a stream the library owns) start after the kernels torch has queued to
+    produce the CUDA tensor xyz: a device-side wait when the stream is a torch
+    stream, else the producing stream is synchronised."""
+    if not (hasattr(xyz, "is_cuda") and xyz.is_cuda):
+        return
+    import torch
+    cur = torch.cuda.current_stream(xyz.device)
+    if isinstance(stream, torch.cuda.Stream):
+        if stream != cur:
+            stream.wait_stream(cur)
+    else:
+        cur.synchronize()
+
+
 class VoxelMap:
     """A device-resident voxel map (Sec. III.B) with multi-plane segmentation (Sec. III.C)."""
 
@@ -217,6 +264,7 @@ class VoxelMap:
         else:
             xyz = np.ascontiguousarray(xyz, np.float32)
             n = xyz.size // 3
+        order_after_torch(xyz, self._stream)
         _check(load().vm_integrate(self._h, _ptr(xyz), n, pose.ctypes.data_as(C.POINTER(C.c_float)), on_dev))
 
     def segment(self, params: vm_segment_params | None = None):

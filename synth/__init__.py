@@ -32,7 +32,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 __all__ = ["MapSpec", "config1", "config2_spec", "config2_scene", "config2_frame", "config2_pose",
-           "config3_clusters", "config3_clusters_device", "e5_clusters", "Scene", "Camera", "config4_streams", "identity_pose"]
+           "config3_clusters", "config3_clusters_device", "e5_clusters", "Scene", "Camera", "config4_streams", "config4_scene", "config4_pose", "config4_frame",
+           "poisson_arrivals", "identity_pose"]
 
 
 @dataclass
@@ -461,6 +462,60 @@ def config4_streams(n_streams: int = 16, seed: int = 11, rate_hz: float = 30.0):
         dims = (int(round(ex / res)), int(round(ey / res)), int(round(2.0 / res)))
         out.append(StreamSpec(s, MapSpec(dims, (0.0, 0.0, -0.05), res), 1000 + s, rate_hz, 5000 + s))
     return out
+
+
+def config4_scene(st: StreamSpec) -> Scene:
+    """An independently seeded stair / desk / ramp scene inside a stream's map
+    extent: floor, an open-tread stair (4-8 steps, rise 0.15 m, run 0.30 m,
+    treads 0.03 m thick, 0.8 m wide), a desk (top 0.72 m, 0.03 m thick, legs
+    set back 0.4 m from one edge), a 15 deg ramp and 10 boxes, placed with
+    PCG64(scene_seed)."""
+    rng = np.random.Generator(np.random.PCG64(st.scene_seed))
+    ex = st.spec.dims[0] * st.spec.voxel_size
+    ey = st.spec.dims[1] * st.spec.voxel_size
+    sc = Scene()
+    sc.add(_aabb_planes((-50, -50, -1), (50, 50, 0)))
+    n_steps = int(rng.integers(4, 9))
+    x0 = rng.uniform(0.1, max(0.2, ex - 0.3 * n_steps - 0.1))
+    y0 = rng.uniform(0.1, max(0.2, ey - 0.9))
+    for k in range(1, n_steps + 1):
+        xa = x0 + 0.30 * (k - 1)
+        sc.add(_aabb_planes((xa, y0, 0.15 * k - 0.03), (xa + 0.30, y0 + 0.8, 0.15 * k)))
+    dx, dy = rng.uniform(0.1, max(0.2, ex - 1.3)), rng.uniform(0.1, max(0.2, ey - 0.9))
+    sc.add(_aabb_planes((dx, dy, 0.69), (dx + 1.2, dy + 0.8, 0.72)))
+    for lx in (dx, dx + 0.76):
+        for ly in (dy, dy + 0.76):
+            sc.add(_aabb_planes((lx, ly, 0.0), (lx + 0.04, ly + 0.04, 0.69)))
+    rx, ry = rng.uniform(0.1, max(0.2, ex - 1.5)), rng.uniform(0.1, max(0.2, ey - 0.7))
+    sc.add(_ramp_planes(rx, rx + 1.4, ry, ry + 0.6, 15.0))
+    for _ in range(10):
+        sx, sy = rng.uniform(0.1, 0.5, 2)
+        h = rng.uniform(0.05, 0.4)
+        cx, cy = rng.uniform(0.2, ex - 0.2), rng.uniform(0.2, ey - 0.2)
+        sc.add(_box_planes((cx, cy, h / 2), (sx / 2, sy / 2, h / 2), yaw=rng.uniform(0, math.pi / 2)))
+    return sc
+
+
+def config4_pose(st: StreamSpec, frame: int):
+    """Sensor->map pose of a stream's frame ``frame`` (30 Hz): an ellipse around
+    the extent's centre (radii 0.3 x the extent, one lap in 20 s), 0.45 m above
+    the floor, facing along the path, pitched down 25 deg."""
+    ex = st.spec.dims[0] * st.spec.voxel_size
+    ey = st.spec.dims[1] * st.spec.voxel_size
+    w = 2 * math.pi / 20.0
+    t = frame / 30.0 + (st.scene_seed % 97) * 0.37  # streams start at different phases
+    x = ex / 2 + 0.3 * ex * math.cos(w * t)
+    y = ey / 2 + 0.3 * ey * math.sin(w * t)
+    yaw = math.atan2(0.3 * ey * math.cos(w * t), -0.3 * ex * math.sin(w * t))
+    return camera_pose((x, y, 0.45), yaw, 25.0)
+
+
+def config4_frame(st: StreamSpec, scene: Scene, frame: int, device="cpu"):
+    """(points float32[307200, 3] in the camera frame, pose float32[12]) of a
+    stream's frame; noise seed = scene_seed * 100003 + frame."""
+    pose = config4_pose(st, frame)
+    pts = _depth_frame(scene, Camera(), pose, seed=st.scene_seed * 100003 + frame, device=device)
+    return pts, pose.astype(np.float32).reshape(12)
 
 
 def poisson_arrivals(rate_hz: float, duration_s: float, seed: int):

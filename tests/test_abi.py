@@ -43,9 +43,10 @@ def test_binding_struct_sizes_match_header():
 #include <stddef.h>
 #include "vm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(vm_map_params), sizeof(vm_segment_params), sizeof(vm_plane),
-         sizeof(vm_planes), sizeof(vm_stats), offsetof(vm_plane, hull_offset), offsetof(vm_segment_params, seed),
-         sizeof(vm_fit_tuning));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(vm_map_params), sizeof(vm_segment_params),
+         sizeof(vm_plane), sizeof(vm_planes), sizeof(vm_stats), offsetof(vm_plane, hull_offset),
+         offsetof(vm_segment_params, seed), sizeof(vm_fit_tuning), sizeof(vm_server_params),
+         offsetof(vm_server_params, tuning), sizeof(vm_server_result), sizeof(vm_server_stats));
   return 0;
 }
 '''
@@ -58,7 +59,8 @@ int main(void) {
     got = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(vm.vm_map_params), C.sizeof(vm.vm_segment_params), C.sizeof(vm.vm_plane),
             C.sizeof(vm.vm_planes), C.sizeof(vm.vm_stats), vm.vm_plane.hull_offset.offset,
-            vm.vm_segment_params.seed.offset, C.sizeof(vm.vm_fit_tuning)]
+            vm.vm_segment_params.seed.offset, C.sizeof(vm.vm_fit_tuning), C.sizeof(vm.vm_server_params),
+            vm.vm_server_params.tuning.offset, C.sizeof(vm.vm_server_result), C.sizeof(vm.vm_server_stats)]
     assert got == want
 
 
@@ -85,3 +87,17 @@ def test_invalid_arguments_rejected_before_any_device_work():
     out = vm.vm_planes()
     assert L.vm_fit_planes(None, None, None, 1, C.byref(p), None, C.byref(out)) == vm.VM_ERR_INVALID_ARG
     assert b"n_hyp" in L.vm_last_error()
+
+
+def test_server_footprint_is_host_arithmetic():
+    """vm_server_footprint needs no GPU: it grows with the brick capacity and the
+    resolution, and a capacity above the grid's brick count changes nothing."""
+    from paper_2510_01592_gb300 import serve
+    small = serve.footprint((200, 200, 100), (0, 0, 0), 0.02, brick_capacity=1000)
+    big = serve.footprint((200, 200, 100), (0, 0, 0), 0.02, brick_capacity=4000)
+    fine = serve.footprint((400, 400, 200), (0, 0, 0), 0.01, brick_capacity=4000)
+    assert 0 < small < big < fine
+    n_bricks = 25 * 25 * 13
+    assert serve.footprint((200, 200, 100), (0, 0, 0), 0.02, brick_capacity=0) == \
+        serve.footprint((200, 200, 100), (0, 0, 0), 0.02, brick_capacity=10 * n_bricks)
+    assert big - small > 3000 * 512 * 28  # at least the pool's sums and counts per brick
