@@ -334,6 +334,8 @@ typedef struct {
     double mean_step_requests; /* requests per step                                          */
     double launch_seconds;     /* scheduler-thread time spent launching steps                */
     double complete_seconds;   /* scheduler-thread time spent completing steps (result copies) */
+    uint64_t graph_captures;   /* CUDA graphs captured by the library since the server started */
+    uint64_t allocations;      /* device / pinned allocations by the library since then      */
 } vm_server_stats;
 
 /* Creates a server and starts its scheduler thread.  Errors:

@@ -19,6 +19,11 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void count_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 unsigned long long launch_total() { return g_launches.load(); }
+static std::atomic<unsigned long long> g_captures{0}, g_allocs{0};
+void count_capture() { g_captures.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long capture_total() { return g_captures.load(); }
+void count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long alloc_total() { return g_allocs.load(); }
 void uncount_launch(unsigned long long n) { g_launches.fetch_sub(n); }
 
 static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "finalize", "moments", "eigen",
@@ -39,6 +44,7 @@ vm_status ensure(DevBuf& b, size_t bytes) {
     b.p = nullptr;
     b.bytes = 0;
     size_t want = bytes + bytes / 4 + 256;
+    count_alloc();
     cudaError_t e = cudaMalloc(&b.p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -301,6 +307,7 @@ vm_status ensure_out(vm_map* m, uint32_t kcap, uint32_t hcap) {
     m->out_host = nullptr;
     m->out_dev = nullptr;
     const size_t bytes = out_xyz_off(kcap, hcap) + (size_t)hcap * 12 + 256;
+    count_alloc();
     cudaError_t e = cudaHostAlloc(&m->out_host, bytes, cudaHostAllocMapped);
     if (e != cudaSuccess) {
         m->out_host = nullptr;
@@ -323,7 +330,16 @@ vm_status ensure_out(vm_map* m, uint32_t kcap, uint32_t hcap) {
 vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit) {
     const uint32_t want_b = m->brick_hint + m->brick_hint / 4 + 64;
     const uint32_t cap_b = want_b < m->capacity ? want_b : m->capacity;
-    if (!m->vox_mem.p || (size_t)cap_b * kBrickVox > m->seg_nv) VM_TRY(alloc_vox(m, cap_b));
+    if (!m->vox_mem.p || (size_t)cap_b * kBrickVox > m->seg_nv) {
+        // Geometric growth (at least 1024 bricks, then doubling): a map that
+        // grows every frame re-allocates, and its graph is re-captured, only
+        // a few times.
+        const size_t have_b = m->vox_mem.p ? m->seg_nv / kBrickVox : 0;
+        size_t grow = have_b * 2 > 1024 ? have_b * 2 : 1024;
+        if (grow < cap_b) grow = cap_b;
+        if (grow > m->capacity) grow = m->capacity;
+        VM_TRY(alloc_vox(m, (uint32_t)grow));
+    }
     const size_t nv = m->seg_nv;
     const uint32_t mc = p.min_cluster > 16 ? p.min_cluster : 16;
     size_t kcap = nv / mc;
@@ -401,6 +417,7 @@ vm_status capture_segment(vm_map* m, const vm_segment_params& p) {
     fit_init_attributes();
     cudaGraph_t graph = nullptr;
     const unsigned long long l0 = launch_total();
+    count_capture();
     VM_CUDA(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_segment(m, p, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(m->stream, &graph);
@@ -462,6 +479,7 @@ static vm_status capture_front(vm_map* m, const vm_segment_params& p) {
     }
     cudaGraph_t graph = nullptr;
     const unsigned long long l0 = launch_total();
+    count_capture();
     VM_CUDA(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_front(m, p, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(m->stream, &graph);

@@ -89,6 +89,7 @@ vm_status plan_out(vm_fit_plan* f, uint32_t kcap, uint32_t hcap) {
     f->out_host = nullptr;
     f->out_dev = nullptr;
     const size_t bytes = out_xyz_off(kcap, hcap) + (size_t)hcap * 12 + 256;
+    count_alloc();
     cudaError_t e = cudaHostAlloc(&f->out_host, bytes, cudaHostAllocMapped);
     if (e != cudaSuccess) {
         f->out_host = nullptr;
@@ -150,6 +151,7 @@ vm_status capture_fit(vm_fit_plan* f, const float* x, const uint32_t* off, const
     fit_init_attributes();
     cudaGraph_t graph = nullptr;
     const unsigned long long l0 = launch_total();
+    count_capture();
     VM_CUDA(cudaStreamBeginCapture(f->s, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_fit(f, x, off, lab, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(f->s, &graph);

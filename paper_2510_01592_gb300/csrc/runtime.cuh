@@ -103,6 +103,12 @@ vm_status check_params(const vm_segment_params* p);
 // are taken back and counted again at each replay.
 unsigned long long launch_total();
 void uncount_launch(unsigned long long n);
+// Graph captures and device / pinned allocations made by the library in this
+// process (diagnostics of the serving path).
+void count_capture();
+unsigned long long capture_total();
+void count_alloc();
+unsigned long long alloc_total();
 
 // Result block in mapped pinned host memory: the counters, then kcap plane
 // records, then hcap hull vertices (xy int32 pairs, then xyz floats).

@@ -389,12 +389,30 @@ __global__ void __launch_bounds__(kNormT) k_ccl_local(const uint32_t* __restrict
             lpar[l] = vert ? (uint32_t)l : kNone;
         }
         __syncthreads();
+        // Runs along +x first, without atomics: each 8-voxel row lies in one
+        // warp, whose ballot of +x edges gives every vertex the start (smallest
+        // index) of its run as its parent.
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
+            const bool vert = __float_as_int(sA[l].w) >= want;
+            const int lx = l & 7;
+            bool xe = false;
+            if (vert && lx < 7 && __float_as_int(sA[l + 1].w) >= want) {
+                const float4 a = sA[l], an = sB[l], b = sA[l + 1], bn = sB[l + 1];
+                xe = ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, xe);
+            const uint32_t row = (bal >> ((threadIdx.x & 31) & ~7)) & 0xffu;
+            const uint32_t gap = ~row & ((1u << lx) - 1u);  // missing +x edges below this voxel
+            const int start = gap ? 32 - __clz(gap) : 0;
+            if (vert) lpar[l] = (uint32_t)((l & ~7) + start);
+        }
+        __syncthreads();
         for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
             if (lpar[l] == kNone) continue;
             const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
             const float4 a = sA[l], an = sB[l];
 #pragma unroll
-            for (int k = 0; k < 13; ++k) {
+            for (int k = 0; k < 12; ++k) {  // the +x offset (k = 12) was joined above
                 int dz, dy, dx;
                 fwd_offset(k, dz, dy, dx);
                 const int x = lx + dx, y = ly + dy, z = lz + dz;
@@ -445,8 +463,7 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
                                                        uint32_t* err) {
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ float4 sA[1000];
-    __shared__ float4 sB[1000];
-    __shared__ uint32_t sP[1000];
+    __shared__ float4 sB[1000];  // (normal, parent); parent kNone off the vertex set
     __shared__ unsigned long long set[kPairSlots];
     __shared__ int32_t nb[27];
     for (int q = threadIdx.x; q < kPairSlots; q += kCrossT) set[q] = ~0ull;
@@ -456,16 +473,16 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
         __syncthreads();
         for (int c = threadIdx.x; c < 1000; c += kCrossT) {
             const int32_t idx = halo_index(c, nb);
-            uint32_t pc = kNone;
+            float4 bn = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(kNone));
             if (idx >= 0) {
                 const float4 a = rec[idx];
                 if (__float_as_int(a.w) >= want) {
                     sA[c] = a;
-                    sB[c] = rec[stride + idx];
-                    pc = __ldcg(parent + idx);
+                    bn = rec[stride + idx];
+                    bn.w = __uint_as_float(__ldcg(parent + idx));
                 }
             }
-            sP[c] = pc;
+            sB[c] = bn;
         }
         __syncthreads();
         unsigned long long last = ~0ull;
@@ -473,18 +490,19 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
             const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
             if (!((lx == 0) | (lx == 7) | (ly == 0) | (ly == 7) | (lz == 7))) continue;
             const int c0 = ((lz + 1) * 10 + ly + 1) * 10 + lx + 1;
-            const uint32_t pa = sP[c0];
-            if (pa == kNone) continue;
             const float4 a = sA[c0], an = sB[c0];
+            const uint32_t pa = __float_as_uint(an.w);
+            if (pa == kNone) continue;
             for (int k = 0; k < 13; ++k) {
                 int dz, dy, dx;
                 fwd_offset(k, dz, dy, dx);
                 const int x = lx + dx, y = ly + dy, z = lz + dz;
                 if (x >= 0 && x <= 7 && y >= 0 && y <= 7 && z <= 7) continue;  // inside the brick: done already
                 const int c = c0 + dz * 100 + dy * 10 + dx;
-                const uint32_t pb = sP[c];
+                const float4 bn = sB[c];
+                const uint32_t pb = __float_as_uint(bn.w);
                 if (pb == kNone || pb == pa) continue;
-                const float4 b = sA[c], bn = sB[c];
+                const float4 b = sA[c];
                 if (!ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
                     continue;
                 const uint32_t lo = pa < pb ? pa : pb, hi = pa < pb ? pb : pa;
@@ -706,7 +724,7 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     VM_STAGE_END(hk, kStFinalize, s);
     const uint8_t want = p.classify ? 2 : 1;
     VM_STAGE_BEGIN(hk, kStNormals, s);
-    k_moments<<<clampg(cap_b, sms * 8), kNormT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.M, b.rec,
+    k_moments<<<clampg(cap_b, sms * 16), kNormT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.M, b.rec,
                                                          b.list_idx, b.list_A, b.nbr, stride, b.ctr);
     VM_STAGE_END(hk, kStNormals, s);
     VM_STAGE_BEGIN(hk, kStEigen, s);
@@ -715,11 +733,11 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
                                                                             p.cos_step);
     VM_STAGE_END(hk, kStEigen, s);
     VM_STAGE_BEGIN(hk, kStCclLocal, s);
-    k_ccl_local<<<clampg(cap_b, sms * 8), kNormT, 0, s>>>(nsp, cap_b, b.rec, b.parent, b.count, stride, want, p.d_th2,
+    k_ccl_local<<<clampg(cap_b, sms * 16), kNormT, 0, s>>>(nsp, cap_b, b.rec, b.parent, b.count, stride, want, p.d_th2,
                                                            p.cos_ccl, err);
     VM_STAGE_END(hk, kStCclLocal, s);
     VM_STAGE_BEGIN(hk, kStCcl, s);
-    k_ccl_cross<<<clampg(cap_b, sms * 8), kCrossT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.rec, b.parent,
+    k_ccl_cross<<<clampg(cap_b, sms * 16), kCrossT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.rec, b.parent,
                                                             stride, want, p.d_th2, p.cos_ccl, err);
     VM_STAGE_END(hk, kStCcl, s);
     count_launch(7);

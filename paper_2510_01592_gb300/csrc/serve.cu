@@ -232,6 +232,7 @@ struct vm_server {
     std::deque<vm_server_result> results;
     uint64_t submitted = 0, finished = 0, steps = 0, step_reqs = 0, fallbacks = 0;
     double launch_s = 0.0, complete_s = 0.0;
+    unsigned long long captures0 = 0, allocs0 = 0;
     uint64_t budget = 0, committed = 0;
     bool stop = false;
     std::thread th;
@@ -260,8 +261,8 @@ vm_status bf_size(Server* S, uint32_t K, uint32_t N) {
     BatchFit& b = S->bf;
     if (b.apts && K <= b.kcap && N <= b.ncap) return VM_OK;
     VM_CUDA(cudaStreamSynchronize(S->fit_stream));
-    const uint32_t k2 = (K > b.kcap ? K + K / 4 + 64 : b.kcap);
-    const uint32_t n2 = (N > b.ncap ? N + N / 4 + 65536 : b.ncap);
+    const uint32_t k2 = K > b.kcap ? (K > 2 * b.kcap ? K + K / 4 : 2 * b.kcap) : b.kcap;  // geometric growth
+    const uint32_t n2 = N > b.ncap ? (N > 2 * b.ncap ? N + N / 4 : 2 * b.ncap) : b.ncap;
     VM_TRY(fit_prepare(b.fc, k2, n2, (int)S->prm.params.n_hyp, b.tune.tile));
     Carver dry{nullptr};
     dry.take<float>((size_t)n2 * 3);
@@ -309,6 +310,7 @@ vm_status launch_batch(Server* S, int slot) {
         fit_init_attributes();
         cudaGraph_t graph = nullptr;
         const unsigned long long l0 = launch_total();
+        count_capture();
         VM_CUDA(cudaStreamBeginCapture(S->fit_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t e = enqueue_batch(S, slot);
         cudaError_t e2 = cudaStreamEndCapture(S->fit_stream, &graph);
@@ -718,6 +720,8 @@ vm_status vm_server_create(const vm_server_params* params, vm_server** out) {
     }
     S->prm = *params;
     S->t0 = std::chrono::steady_clock::now();
+    S->captures0 = capture_total();
+    S->allocs0 = alloc_total();
     S->bf.tune = t.tile ? FitTuning{(int)t.tile, (int)t.hyp_per_thread, (int)t.ctas_per_sm, (int)t.schedule}
                         : default_tuning();
     vm_status st = VM_OK;
@@ -897,6 +901,8 @@ vm_status vm_server_get_stats(vm_server* S, vm_server_stats* out) {
     out->mean_step_requests = S->steps ? (double)S->step_reqs / (double)S->steps : 0.0;
     out->launch_seconds = S->launch_s;
     out->complete_seconds = S->complete_s;
+    out->graph_captures = capture_total() - S->captures0;
+    out->allocations = alloc_total() - S->allocs0;
     return VM_OK;
 }
 

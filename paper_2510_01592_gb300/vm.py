@@ -89,7 +89,7 @@ class vm_server_stats(C.Structure):
                 ("reserved", C.c_uint32), ("requests_submitted", C.c_uint64), ("requests_done", C.c_uint64),
                 ("steps", C.c_uint64), ("fallbacks", C.c_uint64), ("hbm_budget", C.c_uint64),
                 ("hbm_committed", C.c_uint64), ("mean_step_requests", C.c_double), ("launch_seconds", C.c_double),
-                ("complete_seconds", C.c_double)]
+                ("complete_seconds", C.c_double), ("graph_captures", C.c_uint64), ("allocations", C.c_uint64)]
 
 
 # name -> (restype, argtypes); every name is declared in include/vm.h
