@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--profile-case", type=int, default=0, metavar="F",
                     help="profiling driver: integrate frames 1..F, segment --profile-segments times, no timing")
     ap.add_argument("--profile-segments", type=int, default=3)
+    ap.add_argument("--profile-tuning", default="auto", metavar="TILE,R,CTAS,cta|warp",
+                    help="fit schedule of the profiling driver: 'auto' runs the autotuner first")
     ap.add_argument("--no-batching", action="store_true", help="skip the batched-fit and cluster-parallel variants")
     ap.add_argument("--no-serving", action="store_true", help="skip the 16-stream serving variant")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="Poisson-arrival serving run length")
@@ -68,10 +70,11 @@ def parse():
     return ap.parse_args()
 
 
-def profile_case(frames, segments):
+def profile_case(frames, segments, tuning="auto"):
     """A small, fixed invocation of the path for profiler captures: frames
-    1..F of the paper-scale trajectory integrated, then `segments` segment
-    calls (the first warms the scratch; capture the later ones)."""
+    1..F of the paper-scale trajectory integrated, one segment call, the fit
+    schedule (the autotuner as the bench runs it, or a given one), then
+    `segments` segment calls."""
     import torch
     from paper_2510_01592_gb300 import vm
     import synth
@@ -81,11 +84,18 @@ def profile_case(frames, segments):
     for f in range(1, frames + 1):
         p, pose = synth.config2_frame(f, scene, device="cuda")
         m.integrate(p, pose)
+    m.segment(seg_params(vm))
+    if tuning == "auto":
+        tuning = m.autotune(seg_params(vm), reps=2)[0]  # the schedule the bench times with
+    else:
+        t, r, c, sched = tuning.split(",")
+        tuning = dict(tile=int(t), hyp_per_thread=int(r), ctas_per_sm=int(c), schedule=sched)
+        m.set_fit_tuning(tuning)
     for _ in range(segments):
         r = m.segment(seg_params(vm))
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": frames, "segments": segments, "planes": int(len(r["planes"])),
-                      "stats": {k: v for k, v in m.stats().items() if isinstance(v, int)}}))
+                      "fit_tuning": tuning, "stats": {k: v for k, v in m.stats().items() if isinstance(v, int)}}))
 
 
 def profile_fit(k):
@@ -487,8 +497,12 @@ def run_gpu(args):
     torch.cuda.synchronize()
     torch.cuda.set_stream(stream)  # the maps' stream is torch's current one: no cross-stream waits per frame
 
+    tuning = None
+
     def fresh_map(timing=False):
         m = vm.VoxelMap(spec.dims, spec.origin, spec.voxel_size, stream=stream, stage_timing=timing)
+        if tuning:
+            m.set_fit_tuning(tuning)
         for f in range(first):
             m.integrate(pts[f], poses[f])
         return m
@@ -501,6 +515,8 @@ def run_gpu(args):
             m.reset()
         m.integrate(pts[f], poses[f])
         m.segment(params)
+    # the fit schedule chosen by the autotuner on the warmed-up map (results do not depend on it)
+    tuning, tune_ms, tune_n = m.autotune(params, reps=3)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -528,6 +544,7 @@ def run_gpu(args):
     m.close()
     # ---------------- plain per-frame launches (kernel by kernel, no graph), same frames
     mp = vm.VoxelMap(spec.dims, spec.origin, spec.voxel_size, stream=stream, eager=True)
+    mp.set_fit_tuning(tuning)
     for f in range(first):
         mp.integrate(pts[f], poses[f])
     for i in range(args.warmup):
@@ -597,6 +614,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "frames_timed": f"{first + args.warmup + 1}..{first + args.warmup + args.steps}"
                    if first + args.warmup + args.steps <= N_FRAMES else "wrapping trajectory",
                    "voxel_m": 0.01, "map_m": [4, 4, 2], "points_per_frame": 307200, "ransac_hypotheses": 100,
+                   "fit_tuning": dict(tuning, autotune_candidates=tune_n, autotune_ms=round(tune_ms, 4)),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2: a distinct 3.7 MB frame per step from a 1.1 GB resident "
                          "trajectory; per-step map state (pool + segmentation arrays) well above the 129 MB L2"},
@@ -737,7 +755,7 @@ def run_reference(args):
 def main():
     args = parse()
     if args.profile_case:
-        profile_case(args.profile_case, args.profile_segments)
+        profile_case(args.profile_case, args.profile_segments, args.profile_tuning)
         return
     if args.profile_fit:
         profile_fit(args.profile_fit)

@@ -172,13 +172,13 @@ vm_status vm_fit_planes(const float* xyz, const uint32_t* off, const uint32_t* l
  * with the same input pointers replays one graph and allocates nothing.
  * A batch larger than any seen so far (more clusters, points or hull
  * vertices) grows the buffers, captures again and re-runs.  Results are
- * identical to vm_fit_planes for every tuning except the refit's double
- * rounding (its partial sums follow the tile split), well inside the refit
- * tolerance; integer results (best_h, inlier counts, hulls) are bit-exact. */
+ * identical to vm_fit_planes bit for bit under every tuning: the refit's
+ * partial sums are formed per 256-point chunk of a cluster whatever the
+ * work-item tile, and a cluster's result never depends on its batch. */
 typedef struct vm_fit_plan vm_fit_plan; /* opaque, library-owned */
 
 typedef struct {
-    uint32_t tile;           /* points per scoring / extraction work item, 64..16384       */
+    uint32_t tile;           /* points per work item, a multiple of 256 in 256..16384       */
     uint32_t hyp_per_thread; /* hypotheses each thread holds in registers: 1, 2, 4 or 8    */
     uint32_t ctas_per_sm;    /* persistent scoring CTAs per SM, 1..16                      */
     uint32_t schedule;       /* 0: a 256-thread CTA per work item; 1: a warp per work item  */
@@ -211,7 +211,7 @@ vm_status vm_fit_plan_get_tuning(const vm_fit_plan* plan, vm_fit_tuning* tuning)
 /* Autotuner (no counterpart in the paper): times the whole fit of this batch
  * (CUDA events around graph replays, reps timed runs after one warm-up run)
  * for each candidate tuning -- CTA-per-item tiles of 1024..8192 points and
- * warp-per-item tiles of 128..1024 points, 2..8 hypotheses per thread,
+ * warp-per-item tiles of 256..1024 points, 2..8 hypotheses per thread,
  * persistent CTAs per SM up to the occupancy limit -- and keeps the fastest.
  * *best and *best_ms (either may be NULL) receive it; *n_tried the number of
  * candidates timed.  Errors as vm_fit_plan_run. */
@@ -273,6 +273,23 @@ vm_status vm_export_labels(vm_map* map, uint32_t* vid, float* normal, uint8_t* s
  * inlier[cap] (1 if an inlier of the cluster's selected hypothesis).  Host
  * arrays; any may be NULL; *n receives the point count.  Synchronises. */
 vm_status vm_export_clusters(vm_map* map, float* pts, uint32_t* vid, uint8_t* inlier, uint32_t cap, uint32_t* n);
+
+/* Fit schedule of a map's segmentations (work-item tile, hypotheses per
+ * thread, persistent scoring CTAs per SM, CTA or warp per item; see
+ * vm_fit_tuning).  Results never depend on it.  tuning NULL: the automatic
+ * choice (the library default, 2048-point CTA items).  Errors:
+ * VM_ERR_INVALID_ARG (out of range). */
+vm_status vm_set_fit_tuning(vm_map* map, const vm_fit_tuning* tuning);
+vm_status vm_get_fit_tuning(vm_map* map, vm_fit_tuning* tuning);
+/* Autotuner for a map's segmentation (no counterpart in the paper): replays
+ * the segmentation of the map as it stands (segmenting does not change the
+ * map) under each candidate schedule -- CTA-per-item tiles of 512..4096
+ * points, warp-per-item tiles of 256..1024 points, 2..8 hypotheses per
+ * thread, 2..8 scoring CTAs per SM within the occupancy limit -- timing reps
+ * runs of each with CUDA events after one warm-up run, and keeps the fastest.
+ * *best, *best_ms, *n_tried may be NULL.  Synchronises the map's stream. */
+vm_status vm_autotune_segment(vm_map* map, const vm_segment_params* params, uint32_t reps, vm_fit_tuning* best,
+                              float* best_ms, uint32_t* n_tried);
 
 /* ---- Serving ---------------------------------------------------------------
  * The paper runs one robot's map.  A server runs many sensor streams at once,

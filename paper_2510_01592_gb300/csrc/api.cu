@@ -62,67 +62,59 @@ void release(DevBuf& b) {
 
 
 
-size_t fit_bytes(size_t kcap, size_t npts, size_t items, int H, Carver* c) {
-    Carver dry{nullptr};
-    Carver& k = c ? *c : dry;
-    FitBuffers fb{};
-    fb.hyp = k.take<float4>(kcap * H);
-    fb.hyp_valid = k.take<uint8_t>(kcap * H);
-    fb.counts = k.take<uint32_t>(kcap * H);
-    fb.cl = k.take<FitCluster>(kcap);
-    fb.item_off = k.take<uint32_t>(kcap + 1);
-    fb.queue = k.take<uint32_t>(4);
-    fb.inlier = k.take<uint8_t>(npts + 1);
-    fb.part = k.take<float>((items + 1) * 10);
-    fb.cen = k.take<double>(kcap * 3);
-    fb.surv = k.take<int2>(npts + 1);
-    fb.hull = k.take<int2>(npts + 1);
-    fb.hull_cnt = k.take<uint32_t>(kcap + 1);
-    size_t sw = scan_tmp_words(kcap + 1);
-    fb.scan_tmp = k.take<uint32_t>(sw);
-    fb.err = k.take<uint32_t>(4);
-    fb.tot = k.take<uint32_t>(4);
-    fb.kdev = k.take<uint32_t>(4);
-    if (c) {
-        c->off = k.off;
-    }
-    return k.off + 256;
-}
-
-vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile) {
-    const size_t items = npts / (size_t)tile + kcap + 1;
-    if (fc.mem.p && kcap <= fc.kcap && npts <= fc.npts && items <= fc.items && H <= fc.H) return VM_OK;
-    const size_t k2 = kcap + kcap / 4 + 16, n2 = npts + npts / 4 + 1024, i2 = n2 / (size_t)tile + k2 + 1;
-    const int H2 = H > fc.H ? H : fc.H;
-    const size_t bytes = fit_bytes(k2, n2, i2, H2, nullptr);
-    VM_TRY(ensure(fc.mem, bytes));
-    Carver c{static_cast<char*>(fc.mem.p)};
-    FitBuffers fb{};
-    fb.hyp = c.take<float4>(k2 * H2);
-    fb.hyp_valid = c.take<uint8_t>(k2 * H2);
-    fb.counts = c.take<uint32_t>(k2 * H2);
-    fb.cl = c.take<FitCluster>(k2);
-    fb.item_off = c.take<uint32_t>(k2 + 1);
+// The fit scratch for kcap clusters, npts points, `chunks` 256-point partial
+// sums and H hypotheses, carved in order.
+static void fit_layout(Carver& c, FitBuffers& fb, size_t kcap, size_t npts, size_t chunks, int H) {
+    fb.hyp = c.take<float4>(kcap * H);
+    fb.hyp_valid = c.take<uint8_t>(kcap * H);
+    fb.counts = c.take<uint32_t>(kcap * H);
+    fb.cl = c.take<FitCluster>(kcap);
+    fb.item_off = c.take<uint32_t>(kcap + 1);
     fb.queue = c.take<uint32_t>(4);
-    fb.inlier = c.take<uint8_t>(n2 + 1);
-    fb.part = c.take<float>((i2 + 1) * 10);
-    fb.cen = c.take<double>(k2 * 3);
-    fb.surv = c.take<int2>(n2 + 1);
-    fb.hull = c.take<int2>(n2 + 1);
-    fb.hull_cnt = c.take<uint32_t>(k2 + 1);
-    fb.scan_tmp = c.take<uint32_t>(scan_tmp_words(k2 + 1));
+    fb.inlier = c.take<uint8_t>(npts + 1);
+    fb.part = c.take<float>((chunks + 1) * 10);
+    fb.cen = c.take<float>(kcap * 6);
+    fb.surv = c.take<int2>(npts + 1);
+    fb.hull = c.take<int2>(npts + 1);
+    fb.hull_cnt = c.take<uint32_t>(kcap + 1);
+    fb.scan_tmp = c.take<uint32_t>(scan_tmp_words(kcap + 1));
     fb.err = c.take<uint32_t>(4);
     fb.tot = c.take<uint32_t>(4);
     fb.kdev = c.take<uint32_t>(4);
+}
+
+size_t fit_bytes(size_t kcap, size_t npts, size_t chunks, int H) {
+    Carver dry{nullptr};
+    FitBuffers fb{};
+    fit_layout(dry, fb, kcap, npts, chunks, H);
+    return dry.off + 256;
+}
+
+// Partial-sum chunks a batch can need with work items of `tile` points (a
+// multiple of 256): every item holds tile / 256 chunk slots.
+static size_t fit_chunks(size_t kcap, size_t npts, int tile) {
+    return (npts / (size_t)tile + kcap + 1) * ((size_t)tile / 256);
+}
+
+vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile) {
+    const size_t chunks = fit_chunks(kcap, npts, tile);
+    if (fc.mem.p && kcap <= fc.kcap && npts <= fc.npts && chunks <= fc.items && H <= fc.H) return VM_OK;
+    const size_t k2 = kcap + kcap / 4 + 16, n2 = npts + npts / 4 + 1024;
+    const size_t c2 = fit_chunks(k2, n2, tile) > fc.items ? fit_chunks(k2, n2, tile) : fc.items;
+    const int H2 = H > fc.H ? H : fc.H;
+    VM_TRY(ensure(fc.mem, fit_bytes(k2, n2, c2, H2)));
+    Carver c{static_cast<char*>(fc.mem.p)};
+    FitBuffers fb{};
+    fit_layout(c, fb, k2, n2, c2, H2);
     fb.kcap = k2;
     fb.npts_cap = n2;
-    fb.items_cap = i2;
+    fb.items_cap = c2;
     fb.H = H2;
     fc.fb = fb;
     fc.gen++;
     fc.kcap = k2;
     fc.npts = n2;
-    fc.items = i2;
+    fc.items = c2;
     fc.H = H2;
     return VM_OK;
 }
@@ -755,6 +747,121 @@ vm_status vm_segment(vm_map* m, const vm_segment_params* params, vm_planes* out)
     memset(out, 0, sizeof(*out));
     VM_TRY(launch_segment(m, *params));
     return finish_segment(m, *params, out);
+}
+
+static bool tuning_ok(const vm_fit_tuning* t) {
+    const bool r_ok = t->hyp_per_thread == 1 || t->hyp_per_thread == 2 || t->hyp_per_thread == 4 ||
+                      t->hyp_per_thread == 8;
+    return t->tile >= 256 && t->tile <= 16384 && t->tile % 256 == 0 && r_ok && t->ctas_per_sm >= 1 &&
+           t->ctas_per_sm <= 16 && t->schedule <= 1;
+}
+
+vm_status vm_set_fit_tuning(vm_map* m, const vm_fit_tuning* t) {
+    VM_TRY(check_map(m));
+    if (t && !tuning_ok(t)) {
+        set_error("tuning out of range (tile a multiple of 256 in 256..16384, hyp_per_thread 1/2/4/8, "
+                  "ctas_per_sm 1..16, schedule 0/1)");
+        return VM_ERR_INVALID_ARG;
+    }
+    m->tune = t ? FitTuning{(int)t->tile, (int)t->hyp_per_thread, (int)t->ctas_per_sm, (int)t->schedule}
+                : default_tuning();
+    m->gen++;  // the captured graph holds the old schedule
+    return VM_OK;
+}
+
+vm_status vm_get_fit_tuning(vm_map* m, vm_fit_tuning* t) {
+    VM_TRY(check_map(m));
+    if (!t) {
+        set_error("null output");
+        return VM_ERR_INVALID_ARG;
+    }
+    t->tile = (uint32_t)m->tune.tile;
+    t->hyp_per_thread = (uint32_t)m->tune.hyp_per_thread;
+    t->ctas_per_sm = (uint32_t)m->tune.ctas_per_sm;
+    t->schedule = (uint32_t)m->tune.schedule;
+    return VM_OK;
+}
+
+vm_status vm_autotune_segment(vm_map* m, const vm_segment_params* params, uint32_t reps, vm_fit_tuning* best,
+                              float* best_ms, uint32_t* n_tried) {
+    VM_TRY(check_map(m));
+    VM_TRY(check_params(params));
+    if (reps < 1) reps = 1;
+    const vm_segment_params& p = *params;
+    const int H = (int)p.n_hyp;
+    std::vector<FitTuning> cand;
+    const int tiles_cta[] = {512, 1024, 2048, 4096};
+    const int tiles_warp[] = {256, 512, 1024};
+    const int rs[] = {2, 4, 8};
+    const int ctas[] = {2, 4, 8};
+    for (int sched = 0; sched < 2; ++sched) {
+        const int* tiles = sched ? tiles_warp : tiles_cta;
+        const int nt = sched ? 3 : 4;
+        for (int ti = 0; ti < nt; ++ti)
+            for (int r : rs) {
+                if ((sched == 1 && (H + r - 1) / r > 32) || (sched == 0 && (H + r - 1) / r > 256)) continue;
+                const FitTuning base{tiles[ti], r, 1, sched};
+                const int occ = score_max_ctas_per_sm(base, H);
+                for (int c : ctas) {
+                    if (c > occ) break;
+                    FitTuning t = base;
+                    t.ctas_per_sm = c;
+                    cand.push_back(t);
+                }
+            }
+    }
+    const FitTuning keep = m->tune;
+    const bool timing = m->fit.timer.on;
+    m->fit.timer.on = false;  // time graph replays
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    VM_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        m->fit.timer.on = timing;
+        return cuda_status(cudaErrorUnknown, "cudaEventCreate");
+    }
+    vm_status st = VM_OK;
+    float best_t = -1.0f;
+    FitTuning best_c = keep;
+    uint32_t tried = 0;
+    for (size_t i = 0; st == VM_OK && i < cand.size(); ++i) {
+        m->tune = cand[i];
+        m->gen++;
+        st = launch_segment(m, p);  // warm-up: sizes and captures
+        vm_planes tmp{};
+        if (st == VM_OK) st = finish_segment(m, p, &tmp);
+        vm_planes_free(&tmp);
+        if (st != VM_OK) break;
+        cudaEventRecord(e0, m->stream);
+        for (uint32_t r = 0; r < reps && st == VM_OK; ++r) st = launch_segment(m, p);
+        cudaEventRecord(e1, m->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = cuda_status(cudaGetLastError(), "autotune timing");
+        if (st != VM_OK) break;
+        if (take_hints(m)) continue;  // ran out of a capacity: not a valid timing
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        ++tried;
+        if (best_t < 0.0f || ms < best_t) {
+            best_t = ms;
+            best_c = cand[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    m->fit.timer.on = timing;
+    m->tune = st == VM_OK ? best_c : keep;
+    m->gen++;
+    if (st != VM_OK) return st;
+    if (best) {
+        best->tile = (uint32_t)best_c.tile;
+        best->hyp_per_thread = (uint32_t)best_c.hyp_per_thread;
+        best->ctas_per_sm = (uint32_t)best_c.ctas_per_sm;
+        best->schedule = (uint32_t)best_c.schedule;
+    }
+    if (best_ms) *best_ms = best_t;
+    if (n_tried) *n_tried = tried;
+    return VM_OK;
 }
 
 vm_status vm_planes_free(vm_planes* p) {

@@ -17,7 +17,8 @@
 //            extreme points cannot be hull vertices and are dropped (the GPU
 //            filtering step of the cited convex-hull method), the rest are
 //            appended.
-//  k_refit   per cluster: TLS refit in double from the partial sums.
+//  k_refit   per cluster: TLS refit from the partial sums (double-float sums,
+//            adjugate power iteration).
 //  k_hull    per cluster: a second, 128-direction filter, then a bitonic sort
 //            of the remaining quantised points in shared memory and Andrew's
 //            monotone chain with exact int64 orientation tests; gift wrapping
@@ -269,6 +270,45 @@ __device__ __forceinline__ Tv block_sum(Tv v, Tv* sh) {
     return t;  // valid in thread 0
 }
 
+// Partial sums of the refit are formed per 256-point chunk of a cluster (one
+// point per thread, a fixed reduction tree), whatever the work-item tile: the
+// refit is then the same for every scoring schedule, and a cluster's result
+// does not depend on the batch it is fitted in.
+constexpr uint32_t kChunk = kT;
+
+// Per-chunk sums in a fixed order without a barrier per chunk: each warp
+// reduces its 32 values with a shuffle tree and parks the result in shared
+// memory (wp[chunk][warp][value]); after the item's last chunk one barrier,
+// then thread j adds chunk j's eight warp results in warp order.
+constexpr int kMaxChunksPerItem = 16384 / (int)kChunk;
+
+template <int NV>
+__device__ __forceinline__ void warp_park(float (&v)[NV], float* wp, uint32_t j) {
+#pragma unroll
+    for (int e = 0; e < NV; ++e)
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], s);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int e = 0; e < NV; ++e) wp[(j * (kT / 32) + (threadIdx.x >> 5)) * NV + e] = v[e];
+}
+
+template <int NV>
+__device__ __forceinline__ void chunks_out(const float* wp, uint32_t n_chunks, float* dst /* [chunk][10] */, int first) {
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < n_chunks; j += kT) {
+        float t[NV];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) t[e] = 0.0f;
+        for (int w = 0; w < kT / 32; ++w)
+#pragma unroll
+            for (int e = 0; e < NV; ++e) t[e] += wp[(j * (kT / 32) + w) * NV + e];
+#pragma unroll
+        for (int e = 0; e < NV; ++e) dst[(size_t)j * 10 + first + e] = t[e];
+    }
+    __syncthreads();
+}
+
 // Inliers, centroid partials (relative to the origin) and the extreme inliers
 // along the 16 filter directions (reduced per warp, then atomicMax).
 __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
@@ -276,46 +316,45 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
                                                 FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
                                                 float* __restrict__ part, float eps, uint32_t* __restrict__ err) {
     const uint32_t k = *kp;
-    __shared__ float shf[kT / 32];
-    __shared__ uint32_t shu[kT / 32];
+    __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 4];
     const uint32_t n_items = item_off[k];
+    const uint32_t cpt = (uint32_t)T / kChunk;  // chunks per work item
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         const uint32_t c = find_cluster(item_off, k, it);
         const FitCluster f = cl[c];
         const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
         const uint32_t end = min(off[c + 1], start + (uint32_t)T);
-        float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-        uint32_t cnt = 0;
         unsigned long long ext[kFiltDirs];
 #pragma unroll
         for (int d = 0; d < kFiltDirs; ++d) ext[d] = 0;
         bool big = false;
-        for (uint32_t q = start + threadIdx.x; q < end; q += kT) {
-            const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
-            const bool in = f.best_h >= 0 && plane_dist(f.n[0], f.n[1], f.n[2], f.d, px, py, pz) <= eps;
-            inlier[q] = in;
-            if (!in) continue;
-            ++cnt;
-            sx += __fsub_rn(px, f.o[0]);
-            sy += __fsub_rn(py, f.o[1]);
-            sz += __fsub_rn(pz, f.o[2]);
-            const int2 xy = quantise(f, px, py, pz);
-            big |= (abs(xy.x) >= (1 << 28)) | (abs(xy.y) >= (1 << 28));
-            const uint32_t idx = q - off[c];
+        uint32_t j = 0;  // chunk within the item; its slot is it * cpt + j (item_off[c] * cpt + its chunk in the cluster)
+        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {
+            const uint32_t q = q0 + threadIdx.x;
+            float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // count, sum (p - o)
+            if (q < end) {
+                const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
+                const bool in = f.best_h >= 0 && plane_dist(f.n[0], f.n[1], f.n[2], f.d, px, py, pz) <= eps;
+                inlier[q] = in;
+                if (in) {
+                    v[0] = 1.0f;
+                    v[1] = __fsub_rn(px, f.o[0]);
+                    v[2] = __fsub_rn(py, f.o[1]);
+                    v[3] = __fsub_rn(pz, f.o[2]);
+                    const int2 xy = quantise(f, px, py, pz);
+                    big |= (abs(xy.x) >= (1 << 28)) | (abs(xy.y) >= (1 << 28));
+                    const uint32_t idx = q - off[c];
 #pragma unroll
-            for (int d = 0; d < kFiltDirs; ++d) {
-                const unsigned long long key = ext_key(dir_value(d, xy), idx);
-                ext[d] = key > ext[d] ? key : ext[d];
+                    for (int d = 0; d < kFiltDirs; ++d) {
+                        const unsigned long long key = ext_key(dir_value(d, xy), idx);
+                        ext[d] = key > ext[d] ? key : ext[d];
+                    }
+                }
             }
+            warp_park<4>(v, wp, j);
         }
+        chunks_out<4>(wp, j, part + (size_t)it * cpt * 10, 0);  // slot 0 holds the count (at most 256: exact)
         if (big) atomicOr(err, kErrOverflow);
-        const float tx = block_sum(sx, shf), ty = block_sum(sy, shf), tz = block_sum(sz, shf);
-        const uint32_t tc = block_sum(cnt, shu);
-        if (threadIdx.x == 0) {
-            float* pp = part + (size_t)it * 10;
-            pp[0] = __uint_as_float(tc);
-            pp[1] = tx; pp[2] = ty; pp[3] = tz;
-        }
 #pragma unroll
         for (int d = 0; d < kFiltDirs; ++d) {
             unsigned long long m = ext[d];
@@ -330,36 +369,91 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
     }
 }
 
-// Per cluster (one warp each): inlier count and centroid, the per-item
-// partial sums added in double in a fixed order (lane-strided, then a shuffle
-// tree), so the result does not depend on scheduling.
-__global__ void k_centroid(const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, const float* __restrict__ part,
-                           FitCluster* __restrict__ cl, double* __restrict__ cen) {
+// Double-float arithmetic: a value is hi + lo with |lo| at most half an ulp of
+// hi, about 46 significant bits, on the FP32 pipes (FP64 is a slow path on
+// this part).  Built from the error-free transformations TwoSum (Knuth) and
+// TwoProduct (Dekker; exact here with an fma).
+struct df2 {
+    float hi, lo;
+};
+__device__ __forceinline__ df2 df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ df2 df_fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df2 df_add(df2 x, df2 y) {
+    df2 s = df_two_sum(x.hi, y.hi);
+    const df2 t = df_two_sum(x.lo, y.lo);
+    s = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ df2 df_neg(df2 x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ df2 df_sub(df2 x, df2 y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ df2 df_mul(df2 x, df2 y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df2 df_mulf(df2 x, float y) { return df_mul(x, df2{y, 0.0f}); }
+// x / n for a count n < 2^24 (exact in FP32): one quotient, its exact
+// residual, one correction.
+__device__ __forceinline__ df2 df_div_count(df2 x, uint32_t n) {
+    const float fn = (float)n;
+    const float q1 = __fdiv_rn(x.hi, fn);
+    const df2 r = df_sub(x, df2{__fmul_rn(q1, fn), __fmaf_rn(q1, fn, -__fmul_rn(q1, fn))});
+    return df_fast_two_sum(q1, __fdiv_rn(r.hi, fn));
+}
+__device__ __forceinline__ df2 df_shfl_xor(df2 x, int o) {
+    return {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+
+// Per cluster (one warp each): inlier count and centroid, the per-chunk
+// partial sums added in double-float in a fixed order (lane-strided, then a
+// shuffle tree), so the result does not depend on scheduling.  The centroid
+// is kept as (hi, lo) per axis.
+__global__ void k_centroid(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
+                           const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
+                           FitCluster* __restrict__ cl, float* __restrict__ cen /* [k][3][2] */) {
     const uint32_t k = *kp;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kT / 32);
+    const uint32_t cpt = (uint32_t)T / kChunk;
     for (uint32_t c = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); c < k; c += warps) {
-        double sx = 0, sy = 0, sz = 0;
+        df2 sx{0.0f, 0.0f}, sy{0.0f, 0.0f}, sz{0.0f, 0.0f};
         uint32_t n = 0;
-        for (uint32_t it = item_off[c] + lane; it < item_off[c + 1]; it += 32) {
-            const float* pp = part + (size_t)it * 10;
-            n += __float_as_uint(pp[0]);
-            sx += pp[1]; sy += pp[2]; sz += pp[3];
+        const uint32_t base = item_off[c] * cpt, nch = (off[c + 1] - off[c] + kChunk - 1) / kChunk;
+        for (uint32_t j = lane; j < nch; j += 32) {
+            const float* pp = part + (size_t)(base + j) * 10;
+            n += (uint32_t)pp[0];
+            sx = df_add(sx, df2{pp[1], 0.0f});
+            sy = df_add(sy, df2{pp[2], 0.0f});
+            sz = df_add(sz, df2{pp[3], 0.0f});
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             n += __shfl_xor_sync(0xffffffffu, n, o);
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+            sx = df_add(sx, df_shfl_xor(sx, o));
+            sy = df_add(sy, df_shfl_xor(sy, o));
+            sz = df_add(sz, df_shfl_xor(sz, o));
         }
         if (lane == 0) {
             FitCluster& f = cl[c];
             f.inliers = n;
-            double cx = f.o[0], cy = f.o[1], cz = f.o[2];
-            if (n) { cx += sx / n; cy += sy / n; cz += sz / n; }
-            cen[3 * c] = cx; cen[3 * c + 1] = cy; cen[3 * c + 2] = cz;
-            f.c[0] = (float)cx; f.c[1] = (float)cy; f.c[2] = (float)cz;
+            df2 cx{f.o[0], 0.0f}, cy{f.o[1], 0.0f}, cz{f.o[2], 0.0f};
+            if (n) {
+                cx = df_add(cx, df_div_count(sx, n));
+                cy = df_add(cy, df_div_count(sy, n));
+                cz = df_add(cz, df_div_count(sz, n));
+            }
+            float* ce = cen + 6 * (size_t)c;
+            ce[0] = cx.hi; ce[1] = cx.lo; ce[2] = cy.hi; ce[3] = cy.lo; ce[4] = cz.hi; ce[5] = cz.lo;
+            f.c[0] = cx.hi; f.c[1] = cy.hi; f.c[2] = cz.hi;
         }
     }
 }
@@ -374,14 +468,15 @@ __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b) {
 __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                                const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int T,
                                                FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
-                                               const double* __restrict__ cen, float* __restrict__ part,
+                                               const float* __restrict__ cen, float* __restrict__ part,
                                                int2* __restrict__ surv) {
     const uint32_t k = *kp;
-    __shared__ float shf[kT / 32];
+    __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 6];
     __shared__ int2 poly[kFiltDirs + 1];
     __shared__ int npoly;
     const uint32_t n_items = item_off[k];
     const int lane = threadIdx.x & 31;
+    const uint32_t cpt = (uint32_t)T / kChunk;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
         const uint32_t c = find_cluster(item_off, k, it);
         const FitCluster f = cl[c];
@@ -411,17 +506,18 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
         }
         __syncthreads();
         const int m = npoly;
-        const float cx = (float)cen[3 * c], cy = (float)cen[3 * c + 1], cz = (float)cen[3 * c + 2];
-        float a00 = 0, a11 = 0, a22 = 0, a01 = 0, a02 = 0, a12 = 0;
-        for (uint32_t q0 = start; q0 < end; q0 += kT) {
+        const float cx = cen[6 * c], cy = cen[6 * c + 2], cz = cen[6 * c + 4];  // nearest floats of the centroid
+        uint32_t j = 0;
+        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {
             const uint32_t q = q0 + threadIdx.x;
             bool keep = false;
             int2 xy = make_int2(0, 0);
+            float v[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // centred second moments
             if (q < end && inlier[q]) {
                 const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
                 const float rx = __fsub_rn(px, cx), ry = __fsub_rn(py, cy), rz = __fsub_rn(pz, cz);
-                a00 = __fmaf_rn(rx, rx, a00); a11 = __fmaf_rn(ry, ry, a11); a22 = __fmaf_rn(rz, rz, a22);
-                a01 = __fmaf_rn(rx, ry, a01); a02 = __fmaf_rn(rx, rz, a02); a12 = __fmaf_rn(ry, rz, a12);
+                v[0] = __fmul_rn(rx, rx); v[1] = __fmul_rn(ry, ry); v[2] = __fmul_rn(rz, rz);
+                v[3] = __fmul_rn(rx, ry); v[4] = __fmul_rn(rx, rz); v[5] = __fmul_rn(ry, rz);
                 xy = quantise(f, px, py, pz);
                 keep = true;
                 for (int i = 0; i < m; ++i) {  // strictly inside every edge -> not a hull vertex
@@ -434,82 +530,99 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
             if (lane == 0 && b) pos = atomicAdd(&cl[c].n_surv, (uint32_t)__popc(b));
             pos = __shfl_sync(0xffffffffu, pos, 0);
             if (keep) surv[base + pos + __popc(b & ((1u << lane) - 1u))] = xy;
+            warp_park<6>(v, wp, j);
         }
-        const float s0 = block_sum(a00, shf), s1 = block_sum(a11, shf), s2 = block_sum(a22, shf);
-        const float s3 = block_sum(a01, shf), s4 = block_sum(a02, shf), s5 = block_sum(a12, shf);
-        if (threadIdx.x == 0) {
-            float* pp = part + (size_t)it * 10 + 4;
-            pp[0] = s0; pp[1] = s1; pp[2] = s2; pp[3] = s3; pp[4] = s4; pp[5] = s5;
-        }
+        chunks_out<6>(wp, j, part + (size_t)it * cpt * 10, 4);
     }
 }
 
-// 1/sqrt(x) in double from an FP32 estimate and two Newton steps (double
-// division and square root are slow on this part).
-__device__ __forceinline__ double rsqrt_d(double x) {
-    double y = (double)rsqrtf((float)x);
-    y = y * (1.5 - 0.5 * x * y * y);
-    return y * (1.5 - 0.5 * x * y * y);
-}
-
 // Refit (one warp per cluster): total least squares on the inliers.  The
-// covariance A about the centroid is summed in double over the per-item
-// partials.  Its smallest eigenvector is the dominant eigenvector of the
-// adjugate adj(A) (eigenvalues lambda_j lambda_k), so power iteration on adj(A)
-// from the selected RANSAC normal converges by lambda_min / lambda_mid per
-// step; six steps in double, multiplies and adds only.  n_z >= 0,
-// d = -n . centroid; lambda_mid < 10 lambda_min (from the trace, the Rayleigh
-// quotient and x^T adj(A) x = lambda_1 lambda_2) flags the plane ill-conditioned.
-__global__ void k_refit(const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, const float* __restrict__ part,
-                        const double* __restrict__ cen, FitCluster* __restrict__ cl) {
+// covariance A about the centroid is summed in double-float over the
+// per-chunk partials and scaled by its trace.  Its smallest eigenvector is the
+// dominant eigenvector of the adjugate adj(A) (eigenvalues lambda_j lambda_k);
+// the adjugate's cofactors, where the cancellation is, are formed in
+// double-float and rounded, then six steps of power iteration in FP32 from
+// the selected RANSAC normal converge by lambda_min / lambda_mid per step.
+// n_z >= 0, d = -n . centroid (double-float); lambda_mid < 10 lambda_min
+// (from the trace, the Rayleigh quotient in double-float and
+// x^T adj(A) x = lambda_1 lambda_2) flags the plane ill-conditioned.
+__global__ void k_refit(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
+                        const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
+                        const float* __restrict__ cen, FitCluster* __restrict__ cl) {
     const uint32_t k = *kp;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kT / 32);
+    const uint32_t cpt = (uint32_t)T / kChunk;
     for (uint32_t c = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); c < k; c += warps) {
-        double A[6] = {0, 0, 0, 0, 0, 0};
-        for (uint32_t it = item_off[c] + lane; it < item_off[c + 1]; it += 32)
-            for (int e = 0; e < 6; ++e) A[e] += part[(size_t)it * 10 + 4 + e];
+        df2 A[6];
+#pragma unroll
+        for (int e = 0; e < 6; ++e) A[e] = df2{0.0f, 0.0f};
+        const uint32_t base = item_off[c] * cpt, nch = (off[c + 1] - off[c] + kChunk - 1) / kChunk;
+        for (uint32_t j = lane; j < nch; j += 32)
+#pragma unroll
+            for (int e = 0; e < 6; ++e) A[e] = df_add(A[e], df2{part[(size_t)(base + j) * 10 + 4 + e], 0.0f});
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int e = 0; e < 6; ++e) A[e] += __shfl_xor_sync(0xffffffffu, A[e], o);
+            for (int e = 0; e < 6; ++e) A[e] = df_add(A[e], df_shfl_xor(A[e], o));
         if (lane) continue;
         FitCluster& f = cl[c];
         uint32_t flags = 0;
         float rn[3] = {0.0f, 0.0f, 0.0f}, rd = 0.0f;
-        if (f.best_h >= 0 && f.inliers > 0) {
-            const double a = A[0], b = A[1], cc = A[2], d = A[3], e = A[4], g = A[5];
+        const float tr = __fadd_rn(__fadd_rn(A[0].hi, A[1].hi), A[2].hi);
+        if (f.best_h >= 0 && f.inliers > 0 && tr > 0.0f) {
+            // A / tr: entries of magnitude at most 1 (the diagonal is non-negative)
+            const float itr = __fdiv_rn(1.0f, tr);
+            df2 S[6];
+#pragma unroll
+            for (int e = 0; e < 6; ++e) S[e] = df_mulf(A[e], itr);
+            const df2 a = S[0], b = S[1], cc = S[2], d = S[3], e = S[4], g = S[5];
             // symmetric adjugate (cofactors) of [[a d e] [d b g] [e g cc]]
-            const double m00 = b * cc - g * g, m11 = a * cc - e * e, m22 = a * b - d * d;
-            const double m01 = e * g - d * cc, m02 = d * g - e * b, m12 = d * e - a * g;
-            double x = f.n[0], y = f.n[1], z = f.n[2];
+            const float m00 = df_sub(df_mul(b, cc), df_mul(g, g)).hi, m11 = df_sub(df_mul(a, cc), df_mul(e, e)).hi;
+            const float m22 = df_sub(df_mul(a, b), df_mul(d, d)).hi, m01 = df_sub(df_mul(e, g), df_mul(d, cc)).hi;
+            const float m02 = df_sub(df_mul(d, g), df_mul(e, b)).hi, m12 = df_sub(df_mul(d, e), df_mul(a, g)).hi;
+            float x = f.n[0], y = f.n[1], z = f.n[2];
             bool ok = true;
             for (int it = 0; it < 6; ++it) {
-                const double nx = m00 * x + m01 * y + m02 * z;
-                const double ny = m01 * x + m11 * y + m12 * z;
-                const double nz = m02 * x + m12 * y + m22 * z;
-                const double q = nx * nx + ny * ny + nz * nz;
-                if (!(q > 0.0) || !(q < 1e300)) { ok = false; break; }  // rank <= 1: keep the RANSAC normal
-                const double s = rsqrt_d(q);
-                x = nx * s; y = ny * s; z = nz * s;
+                const float nx = __fmaf_rn(m02, z, __fmaf_rn(m01, y, __fmul_rn(m00, x)));
+                const float ny = __fmaf_rn(m12, z, __fmaf_rn(m11, y, __fmul_rn(m01, x)));
+                const float nz = __fmaf_rn(m22, z, __fmaf_rn(m12, y, __fmul_rn(m02, x)));
+                const float q = __fmaf_rn(nz, nz, __fmaf_rn(ny, ny, __fmul_rn(nx, nx)));
+                if (!(q > 1e-30f) || !(q < 1e30f)) { ok = false; break; }  // rank <= 1: keep the RANSAC normal
+                const float sc = rsqrtf(q);
+                x = __fmul_rn(nx, sc); y = __fmul_rn(ny, sc); z = __fmul_rn(nz, sc);
             }
             if (!ok) {
-                const double s = rsqrt_d((double)f.n[0] * f.n[0] + (double)f.n[1] * f.n[1] + (double)f.n[2] * f.n[2]);
-                x = f.n[0] * s; y = f.n[1] * s; z = f.n[2] * s;
+                x = f.n[0]; y = f.n[1]; z = f.n[2];
                 flags |= 1u;
             }
-            if (z < 0.0 || (z == 0.0 && (y < 0.0 || (y == 0.0 && x < 0.0)))) { x = -x; y = -y; z = -z; }
-            // eigenvalues for the conditioning flag
-            const double lmin = x * (a * x + d * y + e * z) + y * (d * x + b * y + g * z) + z * (e * x + g * y + cc * z);
-            const double p12 = x * (m00 * x + m01 * y + m02 * z) + y * (m01 * x + m11 * y + m12 * z) +
-                               z * (m02 * x + m12 * y + m22 * z);
-            const float S = (float)(a + b + cc - lmin);
-            const float disc = fmaxf(S * S - 4.0f * (float)p12, 0.0f);
-            const float lmax = 0.5f * (S + sqrtf(disc));
-            const float lmid = lmax > 0.0f ? (float)p12 / lmax : 0.0f;  // no cancellation
-            if (!(lmid >= 10.0f * (float)lmin)) flags |= 1u;
-            rn[0] = (float)x; rn[1] = (float)y; rn[2] = (float)z;
-            rd = (float)(-(x * cen[3 * c] + y * cen[3 * c + 1] + z * cen[3 * c + 2]));
+            // unit length to FP32 accuracy
+            const float inv = __fdiv_rn(1.0f, __fsqrt_rn(__fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x)))));
+            x = __fmul_rn(x, inv); y = __fmul_rn(y, inv); z = __fmul_rn(z, inv);
+            if (z < 0.0f || (z == 0.0f && (y < 0.0f || (y == 0.0f && x < 0.0f)))) { x = -x; y = -y; z = -z; }
+            // eigenvalues (scaled by 1 / tr) for the conditioning flag
+            const df2 ax = df_add(df_add(df_mulf(a, x), df_mulf(d, y)), df_mulf(e, z));
+            const df2 ay = df_add(df_add(df_mulf(d, x), df_mulf(b, y)), df_mulf(g, z));
+            const df2 az = df_add(df_add(df_mulf(e, x), df_mulf(g, y)), df_mulf(cc, z));
+            const float lmin = df_add(df_add(df_mulf(ax, x), df_mulf(ay, y)), df_mulf(az, z)).hi;
+            const float p12 = x * (m00 * x + m01 * y + m02 * z) + y * (m01 * x + m11 * y + m12 * z) +
+                              z * (m02 * x + m12 * y + m22 * z);
+            const float Sx = 1.0f - lmin;
+            const float disc = fmaxf(Sx * Sx - 4.0f * p12, 0.0f);
+            const float lmax = 0.5f * (Sx + sqrtf(disc));
+            const float lmid = lmax > 0.0f ? p12 / lmax : 0.0f;  // no cancellation
+            if (!(lmid >= 10.0f * lmin)) flags |= 1u;
+            rn[0] = x; rn[1] = y; rn[2] = z;
+            const float* ce = cen + 6 * (size_t)c;
+            const df2 dot = df_add(df_add(df_mulf(df2{ce[0], ce[1]}, x), df_mulf(df2{ce[2], ce[3]}, y)),
+                                   df_mulf(df2{ce[4], ce[5]}, z));
+            rd = -dot.hi;
+        } else if (f.best_h >= 0 && f.inliers > 0) {
+            flags |= 1u;  // zero spread: no plane to fit; the RANSAC normal through the centroid
+            rn[0] = f.n[0]; rn[1] = f.n[1]; rn[2] = f.n[2];
+            const float* ce = cen + 6 * (size_t)c;
+            rd = -df_add(df_add(df_mulf(df2{ce[0], ce[1]}, rn[0]), df_mulf(df2{ce[2], ce[3]}, rn[1])),
+                         df_mulf(df2{ce[4], ce[5]}, rn[2])).hi;
         }
         f.refit_n[0] = rn[0]; f.refit_n[1] = rn[1]; f.refit_n[2] = rn[2];
         f.refit_d = rd;
@@ -983,7 +1096,7 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     if (kcap == 0) return cudaSuccess;
     fit_init_attributes();
     const int H = (int)p.n_hyp;
-    const int T = t.tile;
+    const int T = (t.tile + (int)kChunk - 1) / (int)kChunk * (int)kChunk;  // callers validate; never below a chunk
     cudaError_t e;
     VM_STAGE_BEGIN(hk, kStHyp, s);
     const unsigned kgrid = (kcap + kT - 1) / kT < (uint32_t)sms * 8 ? (kcap + kT - 1) / kT : (uint32_t)sms * 8;
@@ -1030,12 +1143,12 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     k_extract<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
     const unsigned wgrid0 = (kcap + kT / 32 - 1) / (kT / 32);
     const unsigned wgrid = wgrid0 < (uint32_t)sms * 8 ? wgrid0 : (uint32_t)sms * 8;
-    k_centroid<<<wgrid, kT, 0, s>>>(fb.item_off, kp, fb.part, fb.cl, fb.cen);
+    k_centroid<<<wgrid, kT, 0, s>>>(off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
     k_filter<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
     VM_STAGE_END(hk, kStExtract, s);
     count_launch(4);
     VM_STAGE_BEGIN(hk, kStHull, s);
-    k_refit<<<wgrid, kT, 0, s>>>(fb.item_off, kp, fb.part, fb.cen, fb.cl);
+    k_refit<<<wgrid, kT, 0, s>>>(off, fb.item_off, kp, T, fb.part, fb.cen, fb.cl);
     k_hull<<<cgrid, kT, fit_hull_smem(), s>>>(off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
     e = exclusive_scan_dev(fb.hull_cnt, fb.hull_cnt, fb.tot + 1, kp, kcap, fb.scan_tmp, s);
     if (e != cudaSuccess) return e;

@@ -273,9 +273,10 @@ vm_status check_tuning(const vm_fit_tuning* t) {
     }
     const bool r_ok = t->hyp_per_thread == 1 || t->hyp_per_thread == 2 || t->hyp_per_thread == 4 ||
                       t->hyp_per_thread == 8;
-    if (t->tile < 64 || t->tile > 16384 || !r_ok || t->ctas_per_sm < 1 || t->ctas_per_sm > 16 ||
+    if (t->tile < 256 || t->tile > 16384 || t->tile % 256 || !r_ok || t->ctas_per_sm < 1 || t->ctas_per_sm > 16 ||
         t->schedule > 1) {
-        set_error("tuning out of range (tile 64..16384, hyp_per_thread 1/2/4/8, ctas_per_sm 1..16, schedule 0/1)");
+        set_error("tuning out of range (tile a multiple of 256 in 256..16384, hyp_per_thread 1/2/4/8, "
+                  "ctas_per_sm 1..16, schedule 0/1)");
         return VM_ERR_INVALID_ARG;
     }
     return VM_OK;
@@ -431,7 +432,7 @@ vm_status vm_fit_plan_autotune(vm_fit_plan* f, const float* xyz, const uint32_t*
     const int H = (int)f->prm.n_hyp;
     std::vector<FitTuning> cand;
     const int tiles_cta[] = {1024, 2048, 4096, 8192};
-    const int tiles_warp[] = {128, 256, 512, 1024};
+    const int tiles_warp[] = {256, 512, 768, 1024};
     const int rs[] = {2, 4, 8};
     const int ctas[] = {1, 2, 4, 8};
     for (int sched = 0; sched < 2; ++sched) {

@@ -94,7 +94,7 @@ struct FitContext {
 };
 
 void release(DevBuf& b);
-size_t fit_bytes(size_t kcap, size_t npts, size_t items, int H, Carver* c);
+size_t fit_bytes(size_t kcap, size_t npts, size_t chunks, int H);
 vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile);
 void fit_release(FitContext& fc);
 int device_sms();

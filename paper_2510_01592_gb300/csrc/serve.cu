@@ -703,7 +703,7 @@ vm_status vm_server_create(const vm_server_params* params, vm_server** out) {
         return VM_ERR_INVALID_ARG;
     }
     const vm_fit_tuning& t = params->tuning;
-    if (t.tile && (t.tile < 64 || t.tile > 16384 || !(t.hyp_per_thread == 1 || t.hyp_per_thread == 2 ||
+    if (t.tile && (t.tile < 256 || t.tile > 16384 || t.tile % 256 || !(t.hyp_per_thread == 1 || t.hyp_per_thread == 2 ||
                                                       t.hyp_per_thread == 4 || t.hyp_per_thread == 8) ||
                    t.ctas_per_sm < 1 || t.ctas_per_sm > 16 || t.schedule > 1)) {
         set_error("tuning out of range");

@@ -270,7 +270,7 @@ struct FitBuffers {
     uint32_t* queue;        // [4] work-queue heads
     uint8_t* inlier;        // [npts]
     float* part;            // [items][10] per-item partial sums
-    double* cen;            // [kcap][3] inlier centroids
+    float* cen;             // [kcap][3][2] inlier centroids, double-float (hi, lo)
     int2* surv;             // [npts] hull candidates (per-cluster segments at cluster offsets)
     int2* hull;             // [npts] hull vertices (per-cluster segments at cluster offsets)
     uint32_t* hull_cnt;     // [kcap + 1] -> hull offsets (scan)
@@ -278,12 +278,12 @@ struct FitBuffers {
     uint32_t* err;          // device error word
     uint32_t* tot;          // [4] scan totals
     uint32_t* kdev;         // cluster count when the caller supplies it
-    size_t kcap, npts_cap, items_cap;
+    size_t kcap, npts_cap, items_cap;  // items_cap: 256-point partial-sum chunks
     int H;
 };
 
 struct FitTuning {
-    int tile;               // points per scoring work item
+    int tile;               // points per work item, a multiple of 256 (the partial-sum chunk)
     int hyp_per_thread;     // hypotheses held in registers per thread
     int ctas_per_sm;        // persistent CTAs per SM
     int schedule;           // 0: a CTA per work item; 1: a warp per work item

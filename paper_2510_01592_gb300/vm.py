@@ -133,6 +133,10 @@ _SIGS = {
     "vm_server_footprint": (C.c_uint64, [C.POINTER(vm_map_params), C.POINTER(vm_segment_params)]),
     "vm_server_now": (C.c_double, [C.c_void_p]),
     "vm_server_destroy": (C.c_int, [C.c_void_p]),
+    "vm_set_fit_tuning": (C.c_int, [C.c_void_p, C.POINTER(vm_fit_tuning)]),
+    "vm_get_fit_tuning": (C.c_int, [C.c_void_p, C.POINTER(vm_fit_tuning)]),
+    "vm_autotune_segment": (C.c_int, [C.c_void_p, C.POINTER(vm_segment_params), C.c_uint32,
+                                      C.POINTER(vm_fit_tuning), C.POINTER(C.c_float), C.POINTER(C.c_uint32)]),
     "vm_stage_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "vm_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32)]),
     "vm_stage_name": (C.c_char_p, [C.c_uint32]),
@@ -279,6 +283,30 @@ class VoxelMap:
         finally:
             load().vm_planes_free(C.byref(out))
         return res
+
+    @property
+    def fit_tuning(self):
+        t = vm_fit_tuning()
+        _check(load().vm_get_fit_tuning(self._h, C.byref(t)))
+        return _tuning_dict(t)
+
+    def set_fit_tuning(self, tuning: dict | None):
+        """Fit schedule of this map's segmentations (results do not depend on it); None: the default."""
+        if tuning is None:
+            _check(load().vm_set_fit_tuning(self._h, None))
+            return
+        t = vm_fit_tuning(int(tuning["tile"]), int(tuning["hyp_per_thread"]), int(tuning["ctas_per_sm"]),
+                          1 if tuning.get("schedule") == "warp" else 0)
+        _check(load().vm_set_fit_tuning(self._h, C.byref(t)))
+
+    def autotune(self, params: vm_segment_params | None = None, reps: int = 3):
+        """Times the segmentation of the map as it stands under each candidate
+        schedule and keeps the fastest; returns (tuning dict, ms, candidates)."""
+        params = params or segment_params()
+        t, ms, n = vm_fit_tuning(), C.c_float(), C.c_uint32()
+        _check(load().vm_autotune_segment(self._h, C.byref(params), int(reps), C.byref(t), C.byref(ms),
+                                          C.byref(n)))
+        return _tuning_dict(t), float(ms.value), int(n.value)
 
     def reset(self):
         _check(load().vm_reset(self._h))
