@@ -96,7 +96,7 @@ static size_t fit_chunks(size_t kcap, size_t npts, int tile) {
     return (npts / (size_t)tile + kcap + 1) * ((size_t)tile / 256);
 }
 
-vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile) {
+vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile, cudaStream_t s) {
     const size_t chunks = fit_chunks(kcap, npts, tile);
     if (fc.mem.p && kcap <= fc.kcap && npts <= fc.npts && chunks <= fc.items && H <= fc.H) return VM_OK;
     const size_t k2 = kcap + kcap / 4 + 16, n2 = npts + npts / 4 + 1024;
@@ -106,6 +106,7 @@ vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile)
     Carver c{static_cast<char*>(fc.mem.p)};
     FitBuffers fb{};
     fit_layout(c, fb, k2, n2, c2, H2);
+    VM_CUDA(cudaMemsetAsync(fb.scan_tmp, 0, scan_tmp_words(k2 + 1) * sizeof(uint32_t), s));  // scan state
     fb.kcap = k2;
     fb.npts_cap = n2;
     fb.items_cap = c2;
@@ -159,7 +160,7 @@ static vm_status fit_and_pack(FitContext& fc, const float* pts, const uint32_t* 
                               cudaStream_t s, vm_planes* out) {
     memset(out, 0, sizeof(*out));
     if (k == 0) return VM_OK;
-    VM_TRY(fit_prepare(fc, k, npts, (int)p.n_hyp, tune.tile));
+    VM_TRY(fit_prepare(fc, k, npts, (int)p.n_hyp, tune.tile, s));
     FitBuffers& fb = fc.fb;
     VM_CUDA(cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s));
     StageHook* hk = fc.timer.hook();
@@ -219,11 +220,10 @@ static vm_status fit_and_pack(FitContext& fc, const float* pts, const uint32_t* 
 
 
 
+// Scan state for every scan of a segmentation (at most max(nv, bricks) + 1
+// elements); the radix sort has its own region (histograms and their scan).
 static size_t vox_tmp_words(size_t nv, uint32_t nb_total) {
-    size_t a = scan_tmp_words(nv + 1), b = sort_tmp_words(nv);
-    size_t c = scan_tmp_words((size_t)nb_total + 1);
-    size_t r = a > b ? a : b;
-    return r > c ? r : c;
+    return scan_tmp_words((nv > (size_t)nb_total ? nv : (size_t)nb_total) + 1);
 }
 
 // The rank-dense voxel arrays of nv slots, carved in order.
@@ -249,6 +249,7 @@ static void vox_layout(Carver& c, SegBuffers& b, size_t nv, size_t tmp_words) {
     b.pts = c.take<float>(3 * nv);
     b.pt_vid = c.take<uint32_t>(nv);
     b.scan_tmp = c.take<uint32_t>(tmp_words);
+    b.sort_tmp = c.take<uint32_t>(sort_tmp_words(nv));
 }
 
 vm_status alloc_vox(vm_map* m, uint32_t n_bricks) {
@@ -265,6 +266,8 @@ vm_status alloc_vox(vm_map* m, uint32_t n_bricks) {
     VM_TRY(ensure(m->vox_mem, dry.off + 256));
     Carver c{static_cast<char*>(m->vox_mem.p)};
     vox_layout(c, m->seg, nv, tmp_words);
+    VM_CUDA(cudaMemsetAsync(m->seg.scan_tmp, 0, tmp_words * sizeof(uint32_t), m->stream));  // scan states
+    VM_CUDA(cudaMemsetAsync(m->seg.sort_tmp, 0, sort_tmp_words(nv) * sizeof(uint32_t), m->stream));
     m->seg.nv = nv;
     m->seg.kcap = nv;
     m->seg_nv = nv;
@@ -343,7 +346,7 @@ vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit) {
     m->kcap = (uint32_t)kcap;
     if (with_fit) {
         const uint64_t g0 = m->fit.gen;
-        VM_TRY(fit_prepare(m->fit, kcap, nv, (int)p.n_hyp, m->tune.tile));
+        VM_TRY(fit_prepare(m->fit, kcap, nv, (int)p.n_hyp, m->tune.tile, m->stream));
         if (m->fit.gen != g0) m->gen++;
     }
     uint32_t hcap = m->hull_hint + m->hull_hint / 2 + 4096;

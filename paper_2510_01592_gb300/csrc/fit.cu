@@ -1101,7 +1101,7 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_BEGIN(hk, kStHyp, s);
     const unsigned kgrid = (kcap + kT - 1) / kT < (uint32_t)sms * 8 ? (kcap + kT - 1) / kT : (uint32_t)sms * 8;
     k_items<<<kgrid, kT, 0, s>>>(off, kp, T, fb.item_off);
-    e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s);
+    e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s, fb.err);
     if (e != cudaSuccess) return e;
     k_set_end<<<1, 1, 0, s>>>(fb.item_off, kp, fb.tot);
     if ((e = cudaMemsetAsync(fb.queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
@@ -1150,7 +1150,7 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_BEGIN(hk, kStHull, s);
     k_refit<<<wgrid, kT, 0, s>>>(off, fb.item_off, kp, T, fb.part, fb.cen, fb.cl);
     k_hull<<<cgrid, kT, fit_hull_smem(), s>>>(off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
-    e = exclusive_scan_dev(fb.hull_cnt, fb.hull_cnt, fb.tot + 1, kp, kcap, fb.scan_tmp, s);
+    e = exclusive_scan_dev(fb.hull_cnt, fb.hull_cnt, fb.tot + 1, kp, kcap, fb.scan_tmp, s, fb.err);
     if (e != cudaSuccess) return e;
     k_set_end<<<1, 1, 0, s>>>(fb.hull_cnt, kp, fb.tot + 1);
     VM_STAGE_END(hk, kStHull, s);
@@ -1284,7 +1284,7 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
         return cuda_status(e, "cudaMemsetAsync");
     k_set_u32<<<1, 1, 0, s>>>(kdev, k);
     k_items<<<(k + kT - 1) / kT, kT, 0, s>>>(off, kdev, t.tile, item_off);
-    if ((e = exclusive_scan_dev(item_off, item_off, total, kdev, k, scan_tmp, s)) != cudaSuccess)
+    if ((e = exclusive_scan_dev(item_off, item_off, total, kdev, k, scan_tmp, s, nullptr)) != cudaSuccess)
         return cuda_status(e, "scan");
     k_set_end<<<1, 1, 0, s>>>(item_off, kdev, total);
     const size_t kh = (size_t)k * H;

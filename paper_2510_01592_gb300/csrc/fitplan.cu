@@ -111,7 +111,7 @@ vm_status plan_size(vm_fit_plan* f, uint32_t k, uint32_t n, uint32_t hull) {
     const uint64_t g0 = f->fc.gen;
     const size_t kk = k > f->fc.kcap ? k : f->fc.kcap;
     const size_t nn = n > f->fc.npts ? n : f->fc.npts;
-    VM_TRY(fit_prepare(f->fc, kk ? kk : 1, nn ? nn : 1, (int)f->prm.n_hyp, f->tune.tile));
+    VM_TRY(fit_prepare(f->fc, kk ? kk : 1, nn ? nn : 1, (int)f->prm.n_hyp, f->tune.tile, f->s));
     if (f->fc.gen != g0) f->gen++;
     uint32_t hcap = hull + hull / 2 + 4096;
     const uint32_t floor_h = (uint32_t)(f->fc.kcap * 64 < 65536 ? 65536 : f->fc.kcap * 64);

@@ -95,7 +95,8 @@ struct FitContext {
 
 void release(DevBuf& b);
 size_t fit_bytes(size_t kcap, size_t npts, size_t chunks, int H);
-vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile);
+// Sizes fit scratch (zeroing its scan state on s when it is re-allocated).
+vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile, cudaStream_t s);
 void fit_release(FitContext& fc);
 int device_sms();
 vm_status check_params(const vm_segment_params* p);

@@ -120,6 +120,111 @@ __global__ void k_tile_scan(const uint32_t* in, uint32_t* out, size_t n_cap, con
     }
 }
 
+// Single-pass scan with decoupled look-back (Merrill and Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", 2016).  Each CTA takes the
+// next tile from a ticket counter (so every earlier tile belongs to a CTA that
+// has started), publishes its tile sum, then walks back over earlier tiles'
+// published words until it meets an inclusive prefix, and publishes its own.
+// A status word is (epoch << 34 | flag << 32 | value), a 30-bit epoch: words
+// of an earlier
+// launch (another epoch) read as not yet published, so no clearing pass is
+// needed; the last CTA to finish resets the ticket and advances the epoch.
+// The state (ticket, done, epoch, then one 64-bit word per tile) must start
+// zeroed once, when its memory is allocated.  Every wait is bounded: a wait
+// that runs out sets kErrTimeout in *err and counts the missing prefix as 0.
+constexpr unsigned long long kFlagAgg = 1ull, kFlagInc = 2ull;
+constexpr int kLookbackCap = 1 << 20;
+
+constexpr uint32_t kEpochMask = (1u << 30) - 1u;
+__device__ __forceinline__ unsigned long long lb_word(uint32_t epoch, unsigned long long flag, uint32_t v) {
+    return ((unsigned long long)(epoch & kEpochMask) << 34) | (flag << 32) | (unsigned long long)v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_lookback(const uint32_t* in, uint32_t* out, size_t n_cap,
+                                                                const uint32_t* __restrict__ n_dev,
+                                                                uint32_t* __restrict__ total,
+                                                                uint32_t* __restrict__ state, uint32_t* err) {
+    __shared__ uint32_t buf[kScanTile];
+    __shared__ uint32_t ws[kScanThreads / 32];
+    __shared__ uint32_t tot, s_tile, s_prefix;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(state + 4);
+    const size_t n = dev_count(n_cap, n_dev);
+    const uint32_t nt_used = (uint32_t)((n + kScanTile - 1) / kScanTile);
+    const uint32_t epoch = *(volatile uint32_t*)(state + 2);
+    if (threadIdx.x == 0) s_tile = atomicAdd(state, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile < nt_used) {
+        const size_t base = (size_t)tile * kScanTile;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int t = i * kScanThreads + threadIdx.x;
+            const size_t j = base + t;
+            buf[t] = (j < n) ? in[j] : 0u;
+        }
+        __syncthreads();
+        uint32_t v[kScanItems];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            v[i] = buf[threadIdx.x * kScanItems + i];
+            sum += v[i];
+        }
+        const uint32_t ex_local = block_excl_scan(sum, ws, &tot);
+        if (threadIdx.x == 0) {
+            const uint32_t agg = tot;
+            uint32_t prefix = 0;
+            if (tile == 0) {
+                atomicExch(status, lb_word(epoch, kFlagInc, agg));
+            } else {
+                atomicExch(status + tile, lb_word(epoch, kFlagAgg, agg));
+                for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
+                    unsigned long long w = 0;
+                    int it = 0;
+                    for (; it < kLookbackCap; ++it) {
+                        w = *(volatile unsigned long long*)(status + p);
+                        if ((uint32_t)(w >> 34) == (epoch & kEpochMask) && ((w >> 32) & 3ull)) break;
+                    }
+                    if (it == kLookbackCap) {  // the predecessor never published: report, count it as 0
+                        if (err) atomicOr(err, kErrTimeout);
+                        break;
+                    }
+                    prefix += (uint32_t)(w & 0xffffffffull);
+                    if (((w >> 32) & 3ull) == kFlagInc) break;
+                }
+                atomicExch(status + tile, lb_word(epoch, kFlagInc, prefix + agg));
+            }
+            s_prefix = prefix;
+            if (tile == nt_used - 1 && total) *total = prefix + agg;
+        }
+        __syncthreads();
+        uint32_t ex = ex_local + s_prefix;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            buf[threadIdx.x * kScanItems + i] = ex;
+            ex += v[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int t = i * kScanThreads + threadIdx.x;
+            const size_t j = base + t;
+            if (j < n) out[j] = buf[t];
+        }
+    } else if (tile == 0 && threadIdx.x == 0 && total) {
+        *total = 0;  // nothing to scan
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(state + 1, 1u) == gridDim.x - 1) {  // the last CTA: reset for the next launch
+            state[0] = 0;
+            state[1] = 0;
+            state[2] = epoch + 1;
+            __threadfence();
+        }
+    }
+}
+
 // ------------------------------------------------------------------ radix sort
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -236,10 +341,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const uint32_t* in
 
 }  // namespace
 
-size_t scan_tmp_words(size_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+// Look-back state: ticket, done, epoch, pad, then one 64-bit word per tile.
+size_t scan_tmp_words(size_t n) { return 4 + 2 * ((n + kScanTile - 1) / kScanTile) + 2; }
 
 cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
-                               uint32_t* tmp, cudaStream_t s) {
+                               uint32_t* tmp, cudaStream_t s, uint32_t* err) {
     if (n_cap == 0) {
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
         return cudaSuccess;
@@ -250,16 +356,14 @@ cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* tota
         return cudaGetLastError();
     }
     const size_t nt = (n_cap + kScanTile - 1) / kScanTile;
-    k_tile_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n_cap, n_dev, tmp);
-    k_scan_sums<<<1, kScanThreads, 0, s>>>(tmp, nt, total);
-    k_tile_scan<<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, n_cap, n_dev, tmp);
-    count_launch(3);
+    k_scan_lookback<<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, n_cap, n_dev, total, tmp, err);
+    count_launch(1);
     return cudaGetLastError();
 }
 
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total, size_t n, uint32_t* tmp,
-                               cudaStream_t s) {
-    return exclusive_scan_dev(in, out, total, nullptr, n, tmp, s);
+                               cudaStream_t s, uint32_t* err) {
+    return exclusive_scan_dev(in, out, total, nullptr, n, tmp, s, err);
 }
 
 size_t sort_tmp_words(size_t n) {
@@ -268,7 +372,8 @@ size_t sort_tmp_words(size_t n) {
 }
 
 cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                                  const uint32_t* n_dev, size_t n_cap, int bits, uint32_t* tmp, cudaStream_t s) {
+                                  const uint32_t* n_dev, size_t n_cap, int bits, uint32_t* tmp, cudaStream_t s,
+                                  uint32_t* err) {
     if (n_cap == 0 || bits <= 0) return cudaSuccess;
     const size_t nt = (n_cap + kSortTile - 1) / kSortTile;
     uint32_t* ghist = tmp;
@@ -278,7 +383,7 @@ cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys
     for (int p = 0; p < passes; ++p) {
         const int shift = 8 * p;
         k_rs_hist<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, ghist, nt);
-        cudaError_t e = exclusive_scan_dev(ghist, ghist, nullptr, nullptr, 256 * nt, stmp, s);
+        cudaError_t e = exclusive_scan_dev(ghist, ghist, nullptr, nullptr, 256 * nt, stmp, s, err);
         if (e != cudaSuccess) return e;
         k_rs_scatter<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, ghist, nt);
         count_launch(2);
@@ -294,8 +399,8 @@ cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys
 }
 
 cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
-                                  int bits, uint32_t* tmp, cudaStream_t s) {
-    return stable_sort_pairs_dev(keys, vals, keys_alt, vals_alt, nullptr, n, bits, tmp, s);
+                                  int bits, uint32_t* tmp, cudaStream_t s, uint32_t* err) {
+    return stable_sort_pairs_dev(keys, vals, keys_alt, vals_alt, nullptr, n, bits, tmp, s, err);
 }
 
 }  // namespace vmx

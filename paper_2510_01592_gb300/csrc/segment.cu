@@ -688,7 +688,7 @@ cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegB
     cudaError_t e = cudaMemsetAsync(b.ctr, 0, sizeof(SegCounters), s);
     if (e != cudaSuccess) return e;
     k_brick_flags<<<grid_for(nb_total, sms), kT, 0, s>>>(brick_table, nb_total, b.flags);
-    e = exclusive_scan_u32(b.flags, b.flags, &b.ctr->n_sorted, nb_total, b.scan_tmp, s);
+    e = exclusive_scan_u32(b.flags, b.flags, &b.ctr->n_sorted, nb_total, b.scan_tmp, s, &b.ctr->err);
     if (e != cudaSuccess) return e;
     k_brick_compact<<<grid_for(nb_total, sms), kT, 0, s>>>(brick_table, nb_total, b.flags, b.rank_table,
                                                              b.sorted_slot, b.sorted_key);
@@ -749,9 +749,9 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     uint32_t* nroot = b.vert_flag;  // vert_flag for kept roots
     const unsigned bgrid = clampg(cap_b, sms * 4);
     k_brick_tally<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot);
-    cudaError_t e = exclusive_scan_dev(nroot, nroot, &b.ctr->k, nsp, cap_b, b.scan_tmp, s);
+    cudaError_t e = exclusive_scan_dev(nroot, nroot, &b.ctr->k, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
-    e = exclusive_scan_dev(nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp, s);
+    e = exclusive_scan_dev(nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
     k_brick_roots<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nroot, b.sorted_key, b.cid,
                                                b.cl_size, b.cl_label, kcap);
@@ -759,9 +759,9 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     k_brick_verts<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nvert, b.cid, b.keys, b.vals);
     int bits = 1;
     while ((1ull << bits) < kcap && bits < 32) ++bits;
-    e = stable_sort_pairs_dev(b.keys, b.vals, b.keys_alt, b.vals_alt, &b.ctr->n_kept, b.nv, bits, b.scan_tmp, s);
+    e = stable_sort_pairs_dev(b.keys, b.vals, b.keys_alt, b.vals_alt, &b.ctr->n_kept, b.nv, bits, b.sort_tmp, s, err);
     if (e != cudaSuccess) return e;
-    e = exclusive_scan_dev(b.cl_size, b.cl_off, &b.ctr->tot, &b.ctr->k, kcap, b.scan_tmp, s);
+    e = exclusive_scan_dev(b.cl_size, b.cl_off, &b.ctr->tot, &b.ctr->k, kcap, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
     k_set_end_u32<<<1, 1, 0, s>>>(b.cl_off, &b.ctr->k, &b.ctr->tot);
     k_gather<<<grid_for(b.nv, sms), kT, 0, s>>>(&b.ctr->n_kept, b.vals, b.M, b.nv, b.sorted_key, g, b.pts, b.pt_vid);

@@ -263,7 +263,7 @@ vm_status bf_size(Server* S, uint32_t K, uint32_t N) {
     VM_CUDA(cudaStreamSynchronize(S->fit_stream));
     const uint32_t k2 = K > b.kcap ? (K > 2 * b.kcap ? K + K / 4 : 2 * b.kcap) : b.kcap;  // geometric growth
     const uint32_t n2 = N > b.ncap ? (N > 2 * b.ncap ? N + N / 4 : 2 * b.ncap) : b.ncap;
-    VM_TRY(fit_prepare(b.fc, k2, n2, (int)S->prm.params.n_hyp, b.tune.tile));
+    VM_TRY(fit_prepare(b.fc, k2, n2, (int)S->prm.params.n_hyp, b.tune.tile, S->fit_stream));
     Carver dry{nullptr};
     dry.take<float>((size_t)n2 * 3);
     dry.take<uint32_t>((size_t)k2 + 1);

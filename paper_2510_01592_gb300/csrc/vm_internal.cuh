@@ -192,21 +192,26 @@ vm_status ensure(DevBuf& b, size_t bytes);
 // ---------------------------------------------------------------- scan.cu
 // Exclusive prefix sum of n uint32 values: out[i] = sum(in[0..i-1]); *total
 // (device) receives the sum.  in and out may alias.  tmp must hold
-// scan_tmp_words(n) words.
+// scan_tmp_words(n) words and be zeroed once when it is allocated (it keeps
+// the single-pass scan's look-back state, which every launch leaves ready
+// for the next).  err (device, may be null): kErrTimeout when a bounded
+// look-back wait ran out.
 size_t scan_tmp_words(size_t n);
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total, size_t n, uint32_t* tmp,
-                               cudaStream_t s);
+                               cudaStream_t s, uint32_t* err);
 // Stable sort of (key, value) pairs by key, key < 2^bits (bits <= 32), LSD
-// 8-bit digits.  keys/vals are sorted in place using the alt buffers.
+// 8-bit digits.  keys/vals are sorted in place using the alt buffers; tmp
+// (sort_tmp_words) zeroed once when allocated.
 // Variants whose element count is read on the device from n_dev (clamped to
 // the host bound n_cap, which sizes the grids): usable inside a CUDA graph.
 cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
-                               uint32_t* tmp, cudaStream_t s);
+                               uint32_t* tmp, cudaStream_t s, uint32_t* err);
 cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                                  const uint32_t* n_dev, size_t n_cap, int bits, uint32_t* tmp, cudaStream_t s);
+                                  const uint32_t* n_dev, size_t n_cap, int bits, uint32_t* tmp, cudaStream_t s,
+                                  uint32_t* err);
 size_t sort_tmp_words(size_t n);
 cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
-                                  int bits, uint32_t* tmp, cudaStream_t s);
+                                  int bits, uint32_t* tmp, cudaStream_t s, uint32_t* err);
 
 // ---------------------------------------------------------------- integrate.cu
 cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, int32_t* brick_table,
@@ -243,7 +248,8 @@ struct SegBuffers {
     uint32_t* cl_label;     // [kcap]
     float* pts;             // [nv][3]  cluster points in cluster order
     uint32_t* pt_vid;       // [nv]
-    uint32_t* scan_tmp;
+    uint32_t* scan_tmp;     // look-back state of the segmentation's scans
+    uint32_t* sort_tmp;     // the radix sort's histograms and their scan state
     SegCounters* ctr;       // device
     size_t nv, kcap;
 };
