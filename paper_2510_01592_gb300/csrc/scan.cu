@@ -231,10 +231,24 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortIters = 8;                               // 32-item rounds per warp
 constexpr int kSortTile = kSortThreads * kSortIters;        // 2048
 
-__global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t n_cap, const uint32_t* __restrict__ n_dev, int shift,
-                          uint32_t* __restrict__ ghist, size_t nt) {
+// Pass `pass` of the sort runs only when some key reaches its digit: with a
+// device bound kb on the keys (every key < kb), pass p > 0 runs iff
+// kb > 2^(8p).  Tiles past the device count do nothing; the histograms are
+// laid out digit-major over the used tiles only, and *cnt receives their
+// count (the scan's length).
+__device__ __forceinline__ bool rs_pass_active(const uint32_t* kb, int pass) {
+    return pass == 0 || !kb || (unsigned long long)*kb > (1ull << (8 * pass));
+}
+
+__global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t n_cap, const uint32_t* __restrict__ n_dev, int pass,
+                          const uint32_t* __restrict__ kb, uint32_t* __restrict__ ghist, uint32_t* __restrict__ cnt) {
     __shared__ uint32_t h[256];
-    const size_t n = dev_count(n_cap, n_dev);
+    const bool active = rs_pass_active(kb, pass);
+    const size_t n = active ? dev_count(n_cap, n_dev) : 0;
+    const size_t ntu = (n + kSortTile - 1) / kSortTile;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *cnt = (uint32_t)(256 * ntu);
+    if (blockIdx.x >= ntu) return;
+    const int shift = 8 * pass;
     h[threadIdx.x] = 0;
     __syncthreads();
     const size_t base = (size_t)blockIdx.x * kSortTile;
@@ -243,17 +257,20 @@ __global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t n_cap, const
         if (j < n) atomicAdd(&h[(keys[j] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    ghist[(size_t)threadIdx.x * nt + blockIdx.x] = h[threadIdx.x];
+    ghist[(size_t)threadIdx.x * ntu + blockIdx.x] = h[threadIdx.x];
 }
 
 // Stable scatter: warp w owns items [w*256, w*256+256) of the tile, in order.
 __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t n_cap,
-                             const uint32_t* __restrict__ n_dev, int shift, const uint32_t* __restrict__ goff,
-                             size_t nt) {
+                             const uint32_t* __restrict__ n_dev, int pass, const uint32_t* __restrict__ kb,
+                             const uint32_t* __restrict__ goff) {
     __shared__ uint32_t wc[kSortWarps][256];
+    if (!rs_pass_active(kb, pass)) return;
     const size_t n = dev_count(n_cap, n_dev);
     if ((size_t)blockIdx.x * kSortTile >= n) return;
+    const size_t nt = (n + kSortTile - 1) / kSortTile;  // used tiles: the histogram stride
+    const int shift = 8 * pass;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wc[0][0])[d] = 0;
     __syncthreads();
@@ -368,30 +385,30 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* tota
 
 size_t sort_tmp_words(size_t n) {
     const size_t nt = (n + kSortTile - 1) / kSortTile;
-    return 256 * nt + scan_tmp_words(256 * nt) + 1;
+    return 256 * nt + 64 + scan_tmp_words(256 * nt);
 }
 
 cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                   const uint32_t* n_dev, size_t n_cap, int bits, uint32_t* tmp, cudaStream_t s,
-                                  uint32_t* err) {
+                                  uint32_t* err, const uint32_t* key_bound) {
     if (n_cap == 0 || bits <= 0) return cudaSuccess;
     const size_t nt = (n_cap + kSortTile - 1) / kSortTile;
     uint32_t* ghist = tmp;
-    uint32_t* stmp = tmp + 256 * nt;
+    uint32_t* cnt = tmp + 256 * nt;          // the histogram scan's length (device)
+    uint32_t* stmp = tmp + 256 * nt + 64;    // its look-back state
     uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
     const int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        k_rs_hist<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, ghist, nt);
-        cudaError_t e = exclusive_scan_dev(ghist, ghist, nullptr, nullptr, 256 * nt, stmp, s, err);
+        k_rs_hist<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, n_cap, n_dev, p, key_bound, ghist, cnt);
+        cudaError_t e = exclusive_scan_dev(ghist, ghist, nullptr, cnt, 256 * nt, stmp, s, err);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, ghist, nt);
+        k_rs_scatter<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_cap, n_dev, p, key_bound, ghist);
         count_launch(2);
         uint32_t* t;
         t = ki; ki = ko; ko = t;
         t = vi; vi = vo; vo = t;
     }
-    if (ki != keys) {  // odd number of passes: copy back (n_cap elements; the tail is scratch)
+    if (!key_bound && ki != keys) {  // odd number of passes: copy back (n_cap elements; the tail is scratch)
         cudaMemcpyAsync(keys, ki, n_cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(vals, vi, n_cap * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
     }
@@ -400,7 +417,7 @@ cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys
 
 cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
                                   int bits, uint32_t* tmp, cudaStream_t s, uint32_t* err) {
-    return stable_sort_pairs_dev(keys, vals, keys_alt, vals_alt, nullptr, n, bits, tmp, s, err);
+    return stable_sort_pairs_dev(keys, vals, keys_alt, vals_alt, nullptr, n, bits, tmp, s, err, nullptr);
 }
 
 }  // namespace vmx

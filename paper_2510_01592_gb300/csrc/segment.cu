@@ -543,24 +543,25 @@ __device__ __forceinline__ uint32_t uf_root(const uint32_t* P, uint32_t x, uint3
     return x;
 }
 
-// Pointer jumping to the root: afterwards parent[i] is the component's
-// smallest index (its label) for every vertex.
-__global__ void k_ccl_compress(const uint32_t* __restrict__ nsp, uint32_t cap_b, uint32_t* parent, uint32_t* err) {
-    const size_t nv = (size_t)min(*nsp, cap_b) * kBrickVox;
-    for (size_t i = (size_t)blockIdx.x * kT + threadIdx.x; i < nv; i += (size_t)gridDim.x * kT) {
-        if (parent[i] != kNone) parent[i] = uf_root(parent, (uint32_t)i, err);
-    }
-}
 
-// Component sizes: warps aggregate equal roots before the atomic.
-__global__ void k_count(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent, uint32_t* __restrict__ count,
-                        SegCounters* __restrict__ ctr) {
+
+// Pointer jumping to the root and component sizes in one pass: each vertex
+// walks to its root read-only, writes only its own entry (a walk through it
+// then reads either its old parent or the root, both ancestors), and warps
+// aggregate equal roots before the size atomics.  Afterwards parent[i] is the
+// component's smallest index (its label) for every vertex.
+__global__ void k_compress_count(const uint32_t* __restrict__ nsp, uint32_t cap_b, uint32_t* parent,
+                                 uint32_t* __restrict__ count, SegCounters* __restrict__ ctr, uint32_t* err) {
     const size_t nv = (size_t)min(*nsp, cap_b) * kBrickVox;
     uint32_t nvert = 0;
     for (size_t base = ((size_t)blockIdx.x * kT + threadIdx.x) & ~(size_t)31; base < nv;
          base += (size_t)gridDim.x * kT) {
         const size_t i = base + (threadIdx.x & 31);
-        const uint32_t root = (i < nv) ? parent[i] : kNone;
+        uint32_t root = kNone;
+        if (i < nv && __ldcg(parent + i) != kNone) {
+            root = uf_root(parent, (uint32_t)i, err);
+            parent[i] = root;
+        }
         const uint32_t m = __match_any_sync(0xffffffffu, root);
         if (root != kNone) {
             ++nvert;
@@ -596,55 +597,52 @@ __device__ __forceinline__ uint32_t brick_rank(bool f, uint32_t* wcnt, uint32_t*
     return pre + __popc(bal & ((1u << lane) - 1u));
 }
 
-// (1) per-brick counts of kept vertices and of kept roots;
+// (1) per-brick counts of kept vertices and of kept roots, and the mask of the
+// brick's kept roots;
 __global__ void __launch_bounds__(kBrickVox) k_brick_tally(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent,
                                                            const uint32_t* __restrict__ count, uint32_t min_cluster,
-                                                           uint32_t* __restrict__ nvert, uint32_t* __restrict__ nroot) {
+                                                           uint32_t* __restrict__ nvert, uint32_t* __restrict__ nroot,
+                                                           uint32_t* __restrict__ rmask) {
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ uint32_t wc[kBrickVox / 32];
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
         const size_t i = (size_t)r * kBrickVox + threadIdx.x;
         const uint32_t p = parent[i];
         const bool kept = p != kNone && count[p] >= min_cluster;
+        const bool root = kept && p == (uint32_t)i;
+        const uint32_t bal = __ballot_sync(0xffffffffu, root);  // this brick's kept roots, 32 voxels a word
+        if ((threadIdx.x & 31) == 0) rmask[(size_t)r * (kBrickVox / 32) + (threadIdx.x >> 5)] = bal;
         uint32_t tv, tr;
         brick_rank(kept, wc, &tv);
-        brick_rank(kept && p == (uint32_t)i, wc, &tr);
+        brick_rank(root, wc, &tr);
         if (threadIdx.x == 0) { nvert[r] = tv; nroot[r] = tr; }
     }
 }
 
-// (2) kept roots numbered in index order (= label order): cluster sizes and labels;
-__global__ void __launch_bounds__(kBrickVox) k_brick_roots(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent,
-                                                           const uint32_t* __restrict__ count, uint32_t min_cluster,
-                                                           const uint32_t* __restrict__ rbase,
-                                                           const int32_t* __restrict__ sorted_key,
-                                                           uint32_t* __restrict__ cid, uint32_t* __restrict__ cl_size,
-                                                           uint32_t* __restrict__ cl_label, uint32_t kcap) {
-    const uint32_t n_sorted = min(*nsp, cap_b);
-    __shared__ uint32_t wc[kBrickVox / 32];
-    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
-        const size_t i = (size_t)r * kBrickVox + threadIdx.x;
-        const uint32_t p = parent[i];
-        const bool root = p == (uint32_t)i && count[p] >= min_cluster;
-        uint32_t t;
-        const uint32_t rank = brick_rank(root, wc, &t);
-        if (root) {
-            const uint32_t c = rbase[r] + rank;
-            cid[i] = c;
-            if (c < kcap) {
-                cl_size[c] = count[i];
-                cl_label[c] = vid_of(i, sorted_key);
-            }
-        }
-    }
+// Cluster number of a kept root p: kept roots before its brick (rbase) plus
+// kept roots before it in its brick (popcount of the brick's root mask).
+__device__ __forceinline__ uint32_t cluster_of(uint32_t p, const uint32_t* __restrict__ rbase,
+                                               const uint32_t* __restrict__ rmask) {
+    const uint32_t r = p / kBrickVox, l = p % kBrickVox;
+    const uint32_t* m = rmask + (size_t)r * (kBrickVox / 32);
+    uint32_t c = rbase[r];
+    for (uint32_t w = 0; w < (l >> 5); ++w) c += __popc(__ldg(m + w));
+    return c + __popc(__ldg(m + (l >> 5)) & ((1u << (l & 31)) - 1u));
 }
 
-// (3) kept vertices compacted in index order as (cluster, index) pairs.
-__global__ void __launch_bounds__(kBrickVox) k_brick_verts(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent,
-                                                           const uint32_t* __restrict__ count, uint32_t min_cluster,
-                                                           const uint32_t* __restrict__ vbase,
-                                                           const uint32_t* __restrict__ cid,
-                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+// (2) in one pass per brick: kept roots numbered in index order (= label
+// order) with their sizes and labels, and kept vertices compacted in index
+// order as (cluster, index) pairs.
+__global__ void __launch_bounds__(kBrickVox) k_brick_clusters(const uint32_t* __restrict__ nsp, uint32_t cap_b,
+                                                              const uint32_t* __restrict__ parent,
+                                                              const uint32_t* __restrict__ count, uint32_t min_cluster,
+                                                              const uint32_t* __restrict__ rbase,
+                                                              const uint32_t* __restrict__ vbase,
+                                                              const uint32_t* __restrict__ rmask,
+                                                              const int32_t* __restrict__ sorted_key,
+                                                              uint32_t* __restrict__ cl_size,
+                                                              uint32_t* __restrict__ cl_label, uint32_t kcap,
+                                                              uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ uint32_t wc[kBrickVox / 32];
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
@@ -652,20 +650,33 @@ __global__ void __launch_bounds__(kBrickVox) k_brick_verts(const uint32_t* __res
         const uint32_t p = parent[i];
         const bool kept = p != kNone && count[p] >= min_cluster;
         uint32_t t;
-        const uint32_t rank = brick_rank(kept, wc, &t);
+        const uint32_t vrank = brick_rank(kept, wc, &t);
+        const uint32_t rrank = brick_rank(kept && p == (uint32_t)i, wc, &t);
         if (kept) {
-            const uint32_t pos = vbase[r] + rank;
-            keys[pos] = cid[p];
+            if (p == (uint32_t)i) {
+                const uint32_t c = rbase[r] + rrank;
+                if (c < kcap) {
+                    cl_size[c] = count[i];
+                    cl_label[c] = vid_of(i, sorted_key);
+                }
+            }
+            const uint32_t pos = vbase[r] + vrank;
+            keys[pos] = cluster_of(p, rbase, rmask);
             vals[pos] = (uint32_t)i;
         }
     }
 }
 
+
+
 // Cluster points in cluster order: mean positions and voxel ids.
-__global__ void k_gather(const uint32_t* __restrict__ np, const uint32_t* __restrict__ vals, const int32_t* __restrict__ M, size_t stride,
+__global__ void k_gather(const uint32_t* __restrict__ np, const uint32_t* __restrict__ vals_main,
+                         const uint32_t* __restrict__ vals_alt, const uint32_t* __restrict__ kp, int bits,
+                         const int32_t* __restrict__ M, size_t stride,
                          const int32_t* __restrict__ sorted_key, Grid g, float* __restrict__ pts,
                          uint32_t* __restrict__ pt_vid) {
     const uint32_t n = *np;
+    const uint32_t* __restrict__ vals = sort_result_alt(*kp, bits) ? vals_alt : vals_main;  // where the sort ended
     for (uint32_t p = blockIdx.x * kT + threadIdx.x; p < n; p += gridDim.x * kT) {
         const uint32_t i = vals[p];
         pts[3 * (size_t)p + 0] = __fadd_rn(g.ox, __fmul_rn(__int2float_rn(M[i]), kInvQ));
@@ -701,15 +712,14 @@ cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegB
 __global__ void k_seg_guard(SegCounters* __restrict__ ctr, uint32_t cap_b) {
     if (ctr->n_sorted > cap_b) ctr->err |= kErrScratch;
 }
-__global__ void k_seg_guard_k(SegCounters* __restrict__ ctr, uint32_t kcap) {
+// Clusters beyond the scratch flag a re-run (the count is clamped for the
+// kernels that follow); cl_off[k] = the number of clustered points.
+__global__ void k_clusters_end(SegCounters* __restrict__ ctr, uint32_t kcap, uint32_t* __restrict__ cl_off) {
     if (ctr->k > kcap) {
         ctr->err |= kErrScratch;
         ctr->k = kcap;
     }
-}
-__global__ void k_set_end_u32(uint32_t* __restrict__ arr, const uint32_t* __restrict__ kp,
-                              const uint32_t* __restrict__ v) {
-    arr[*kp] = *v;
+    cl_off[ctr->k] = ctr->tot;
 }
 
 cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* C, const vm_segment_params& p,
@@ -740,33 +750,33 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     k_ccl_cross<<<clampg(cap_b, sms * 16), kCrossT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.rec, b.parent,
                                                             stride, want, p.d_th2, p.cos_ccl, err);
     VM_STAGE_END(hk, kStCcl, s);
-    count_launch(7);
+    count_launch(6);
     VM_STAGE_BEGIN(hk, kStClusters, s);
-    k_ccl_compress<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, err);
-    k_count<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, b.count, b.ctr);
+    k_compress_count<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, b.count, b.ctr, err);
     const uint32_t min_cl = p.min_cluster ? p.min_cluster : 1u;
     uint32_t* nvert = b.flags;      // per-brick tallies: flags reused for kept vertices,
-    uint32_t* nroot = b.vert_flag;  // vert_flag for kept roots
+    uint32_t* nroot = b.vert_flag;  // vert_flag for kept roots,
+    uint32_t* rmask = b.cid;        // cid for the kept-root masks (16 words a brick)
     const unsigned bgrid = clampg(cap_b, sms * 4);
-    k_brick_tally<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot);
+    k_brick_tally<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot, rmask);
     cudaError_t e = exclusive_scan_dev(nroot, nroot, &b.ctr->k, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
     e = exclusive_scan_dev(nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
-    k_brick_roots<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nroot, b.sorted_key, b.cid,
-                                               b.cl_size, b.cl_label, kcap);
-    k_seg_guard_k<<<1, 1, 0, s>>>(b.ctr, kcap);
-    k_brick_verts<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nvert, b.cid, b.keys, b.vals);
+    k_brick_clusters<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nroot, nvert, rmask,
+                                                  b.sorted_key, b.cl_size, b.cl_label, kcap, b.keys, b.vals);
     int bits = 1;
     while ((1ull << bits) < kcap && bits < 32) ++bits;
-    e = stable_sort_pairs_dev(b.keys, b.vals, b.keys_alt, b.vals_alt, &b.ctr->n_kept, b.nv, bits, b.sort_tmp, s, err);
+    e = stable_sort_pairs_dev(b.keys, b.vals, b.keys_alt, b.vals_alt, &b.ctr->n_kept, b.nv, bits, b.sort_tmp, s, err,
+                              &b.ctr->k);
     if (e != cudaSuccess) return e;
     e = exclusive_scan_dev(b.cl_size, b.cl_off, &b.ctr->tot, &b.ctr->k, kcap, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
-    k_set_end_u32<<<1, 1, 0, s>>>(b.cl_off, &b.ctr->k, &b.ctr->tot);
-    k_gather<<<grid_for(b.nv, sms), kT, 0, s>>>(&b.ctr->n_kept, b.vals, b.M, b.nv, b.sorted_key, g, b.pts, b.pt_vid);
+    k_clusters_end<<<1, 1, 0, s>>>(b.ctr, kcap, b.cl_off);
+    k_gather<<<grid_for(b.nv, sms), kT, 0, s>>>(&b.ctr->n_kept, b.vals, b.vals_alt, &b.ctr->k, bits, b.M, b.nv,
+                                                 b.sorted_key, g, b.pts, b.pt_vid);
     VM_STAGE_END(hk, kStClusters, s);
-    count_launch(9);
+    count_launch(5);
     return cudaGetLastError();
 }
 

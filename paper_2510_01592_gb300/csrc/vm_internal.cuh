@@ -206,9 +206,19 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* tota
 // the host bound n_cap, which sizes the grids): usable inside a CUDA graph.
 cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
                                uint32_t* tmp, cudaStream_t s, uint32_t* err);
+// key_bound (device, may be null): every key is below *key_bound; passes whose
+// digit no key reaches are skipped on the device, and the result then lies in
+// (keys, vals) after an even number of executed passes and in the alt buffers
+// after an odd number (sort_result_alt tells which, on the device).  Without
+// a bound the result is always in (keys, vals).
 cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                                   const uint32_t* n_dev, size_t n_cap, int bits, uint32_t* tmp, cudaStream_t s,
-                                  uint32_t* err);
+                                  uint32_t* err, const uint32_t* key_bound);
+__device__ __forceinline__ bool sort_result_alt(uint32_t key_bound, int bits) {
+    int executed = 1;
+    for (int p = 1; p < (bits + 7) / 8; ++p) executed += (unsigned long long)key_bound > (1ull << (8 * p));
+    return executed & 1;
+}
 size_t sort_tmp_words(size_t n);
 cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
                                   int bits, uint32_t* tmp, cudaStream_t s, uint32_t* err);
