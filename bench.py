@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-batching", action="store_true", help="skip the batched-fit and cluster-parallel variants")
     ap.add_argument("--no-serving", action="store_true", help="skip the 16-stream serving variant")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="Poisson-arrival serving run length")
+    ap.add_argument("--no-stress", action="store_true", help="skip the LiDAR stress variant")
+    ap.add_argument("--stress-seconds", type=float, default=10.0, help="stress variant arrival run length")
     ap.add_argument("--profile-fit", type=int, default=0, metavar="K",
                     help="profiling driver: K config-3 clusters (sizes log-uniform in [50, 200000]), "
                          "3 fits with the default schedule, no timing")
@@ -384,6 +386,113 @@ def serving_variant(dev, seconds, frames_per_stream=32, backlog=96):
     return out
 
 
+def stress_variant(dev, seconds, lidar_frames=40, cam_frames=32):
+    """Config 5: one 8 x 8 x 3 m map at 0.01 m fed by a 128-beam spinning LiDAR
+    (1,300,480 rays a frame, 20 Hz) over multi-level floors and 500 boxes and
+    slabs, served alongside 8 paper-scale camera streams (4 x 4 x 2 m at 0.01 m,
+    30 Hz, the trajectory's frames at different phases) by one batched server.
+    saturation: 200 LiDAR frames and 8 x 300 camera frames queued at once;
+    arrivals: LiDAR every 50 ms and Poisson camera arrivals at 30 Hz for
+    `seconds` s, latency = arrival to result on the host.  The first
+    `lidar_frames` / `cam_frames` frames are generated and cycled."""
+    import threading
+
+    import numpy as np
+    import torch
+    from paper_2510_01592_gb300 import serve, vm
+    import synth
+    spec5, spec2 = synth.config5_spec(), synth.config2_spec()
+    sc5, sc2 = synth.config5_scene(), synth.config2_scene()
+    lid = [synth.config5_frame(f, sc5, device=dev) for f in range(lidar_frames)]
+    cam = [synth.config2_frame(f, sc2, device=dev) for f in range(1, cam_frames + 1)]
+    torch.cuda.synchronize()
+    params = vm.segment_params(n_hyp=100, seed=0)
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))] if v else None
+
+    def setup():
+        srv = serve.Server(params, mode="batched", max_batch=16, max_inflight=2, device=dev.index or 0)
+        s5 = srv.open(spec5.dims, spec5.origin, spec5.voxel_size, 131072)
+        s2 = [srv.open(spec2.dims, spec2.origin, spec2.voxel_size, 4096) for _ in range(8)]
+        for f in range(2):  # warm-up
+            srv.submit(s5, lid[f][0], lid[f][1])
+            for j, sid in enumerate(s2):
+                srv.submit(sid, cam[(f + 4 * j) % cam_frames][0], cam[(f + 4 * j) % cam_frames][1])
+        srv.drain()
+        srv.poll(256, with_planes=False)
+        return srv, s5, s2
+
+    out = {"lidar_rays_per_frame": int(lid[0][0].shape[0]),
+           "lidar_returns_per_frame": int(torch.isfinite(lid[0][0]).all(1).sum()),
+           "camera_streams": 8}
+    srv, s5, s2 = setup()
+    t0 = srv.now()
+    n5 = n2 = 0
+    for f in range(2, 202):
+        srv.submit(s5, lid[f % lidar_frames][0], lid[f % lidar_frames][1], t_arrival=t0)
+        n5 += 1
+    for f in range(2, 302):
+        for j, sid in enumerate(s2):
+            k = (f + 4 * j) % cam_frames
+            srv.submit(sid, cam[k][0], cam[k][1], t_arrival=t0)
+            n2 += 1
+    srv.drain()
+    t1 = srv.now()
+    res = []
+    while len(res) < n5 + n2:
+        res += srv.poll(512, timeout_ms=1000, with_planes=False)
+    lid_done = max(r["t_done"] for r in res if r["stream"] == s5)
+    out["saturation"] = {"frames": n5 + n2, "seconds": round(t1 - t0, 3),
+                         "frames_per_s": round((n5 + n2) / (t1 - t0), 1),
+                         "lidar_frames_per_s": round(n5 / (lid_done - t0), 2),
+                         "ok": all(r["status"] == vm.VM_OK for r in res)}
+    st = srv.stats()
+    out["map_bricks_committed_gb"] = round(st["hbm_committed"] / 1e9, 2)
+    srv.close()
+    srv, s5, s2 = setup()
+    sched = [(k * 0.05, -1, 2 + k) for k in range(int(seconds * 20))]
+    for j in range(8):
+        sched += [(float(t), j, 2 + i) for i, t in enumerate(synth.poisson_arrivals(30.0, seconds, 9000 + j))]
+    sched.sort()
+    results, stop = [], threading.Event()
+
+    def poller():
+        while not stop.is_set():
+            results.extend(srv.poll(256, timeout_ms=50, with_planes=False))
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = srv.now() + 0.05
+    for t, j, f in sched:
+        ta = t0 + t
+        while True:
+            dt = ta - srv.now()
+            if dt <= 0:
+                break
+            time.sleep(min(dt, 0.002) if dt > 0.0003 else 0)
+        if j < 0:
+            srv.submit(s5, lid[f % lidar_frames][0], lid[f % lidar_frames][1], t_arrival=ta)
+        else:
+            k = (f + 4 * j) % cam_frames
+            srv.submit(s2[j], cam[k][0], cam[k][1], t_arrival=ta)
+    srv.drain()
+    stop.set()
+    th.join()
+    results.extend(srv.poll(512, with_planes=False))
+    srv.close()
+    l5 = [1e3 * (r["t_done"] - r["t_arrival"]) for r in results if r["stream"] == s5]
+    l2 = [1e3 * (r["t_done"] - r["t_arrival"]) for r in results if r["stream"] != s5]
+    out["arrivals"] = {"seconds": seconds, "lidar_frames": len(l5), "camera_frames": len(l2),
+                       "lidar_latency_ms": {"p50": round(pct(l5, 0.5), 3), "p99": round(pct(l5, 0.99), 3)},
+                       "camera_latency_ms": {"p50": round(pct(l2, 0.5), 3), "p99": round(pct(l2, 0.99), 3)},
+                       "ok": all(r["status"] == vm.VM_OK for r in results)}
+    del lid, cam
+    torch.cuda.empty_cache()
+    return out
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -644,6 +753,8 @@ def run_gpu(args):
         res["variants"]["cluster_parallel_e5"] = e5_variant(stream)
     if not args.no_serving and rank == 0:
         res["variants"]["serving_config4"] = serving_variant(dev, args.serve_seconds)
+    if not args.no_stress and rank == 0:
+        res["variants"]["stress_config5"] = stress_variant(dev, args.stress_seconds)
     res["stages_ms_per_step"] = {k: round(v[0] / max(1, args.steps), 4) for k, v in stages.items() if v[1]}
     table = kernel_table(stages, st, load_peaks(), st["clustered_points"])
     res["kernels"] = table

@@ -23,6 +23,8 @@ Workloads:
 * ``e5_clusters``: the paper's cluster-parallel ablation (1-16 clusters of M in
   [10k, 30k] points).
 * ``config4_streams``: serving streams with random extents and resolutions.
+* ``config5_*``: the stress workload, a 128-beam spinning LiDAR (1.3 M rays a
+  frame) over multi-level floors and 500 boxes and slabs in an 8 x 8 x 3 m map.
 """
 from __future__ import annotations
 
@@ -33,7 +35,8 @@ import numpy as np
 
 __all__ = ["MapSpec", "config1", "config2_spec", "config2_scene", "config2_frame", "config2_pose",
            "config3_clusters", "config3_clusters_device", "e5_clusters", "Scene", "Camera", "config4_streams", "config4_scene", "config4_pose", "config4_frame",
-           "poisson_arrivals", "identity_pose"]
+           "poisson_arrivals", "identity_pose", "config5_spec", "config5_scene", "config5_pose",
+           "config5_frame", "Lidar"]
 
 
 @dataclass
@@ -515,6 +518,96 @@ def config4_frame(st: StreamSpec, scene: Scene, frame: int, device="cpu"):
     stream's frame; noise seed = scene_seed * 100003 + frame."""
     pose = config4_pose(st, frame)
     pts = _depth_frame(scene, Camera(), pose, seed=st.scene_seed * 100003 + frame, device=device)
+    return pts, pose.astype(np.float32).reshape(12)
+
+
+# --------------------------------------------------------------------------
+# Config 5: the stress workload (spinning LiDAR over a cluttered multi-level
+# scene).
+# --------------------------------------------------------------------------
+
+def config5_spec():
+    """8 x 8 x 3 m map at 0.01 m (800 x 800 x 300 voxels)."""
+    return MapSpec((800, 800, 300), (0.0, 0.0, -0.05), 0.01)
+
+
+@dataclass
+class Lidar:
+    """A 128-beam spinning LiDAR: beams evenly spaced over a vertical field of
+    view of +-22.5 deg (the builder's choice where the workload gives none),
+    10,160 azimuth steps per revolution (1,300,480 rays a frame), range
+    0.5-20 m, sigma 5 mm along the ray, 20 Hz."""
+    beams: int = 128
+    steps: int = 10160
+    vfov_deg: float = 22.5
+    r_min: float = 0.5
+    r_max: float = 20.0
+    sigma: float = 0.005
+
+    def rays(self):
+        """Unit ray directions in the sensor frame (z up), beam-major."""
+        el = np.radians(np.linspace(-self.vfov_deg, self.vfov_deg, self.beams))
+        az = np.arange(self.steps) * (2 * math.pi / self.steps)
+        E, A = np.meshgrid(el, az, indexing="ij")
+        return np.stack([np.cos(E) * np.cos(A), np.cos(E) * np.sin(A), np.sin(E)], axis=-1).reshape(-1, 3)
+
+
+def config5_scene(seed: int = 5, n_objects: int = 500) -> Scene:
+    """Multi-level floors with overhangs and 500 boxes and slabs: a ground floor,
+    a mezzanine slab at 1.2 m over y in [5, 8] m and a gallery slab at 2.2 m
+    over x in [0, 2.5] m (both 0.05 m thick, open underneath), and 500 objects
+    with sizes log-uniform in [0.1, 2] m, tilts up to 30 deg and random yaw;
+    a third of them are slabs (0.02-0.08 m thick); objects rest on the level
+    under them.  PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sc = Scene()
+    sc.add(_aabb_planes((-50, -50, -1), (50, 50, 0)))
+    sc.add(_aabb_planes((0.0, 5.0, 1.15), (8.0, 8.0, 1.2)))
+    sc.add(_aabb_planes((0.0, 0.0, 2.15), (2.5, 8.0, 2.2)))
+    for i in range(n_objects):
+        sx, sy = np.exp(rng.uniform(math.log(0.1), math.log(2.0), 2))
+        slab = i % 3 == 0
+        sz = rng.uniform(0.02, 0.08) if slab else float(np.exp(rng.uniform(math.log(0.1), math.log(1.0))))
+        cx, cy = rng.uniform(0.2, 7.8, 2)
+        base = 0.0
+        if cy >= 5.0 and rng.uniform() < 0.5:
+            base = 1.2
+        elif cx <= 2.5 and rng.uniform() < 0.3:
+            base = 2.2
+        tilt = math.radians(rng.uniform(0, 30))
+        sc.add(_box_planes((cx, cy, base + sz / 2), (sx / 2, sy / 2, sz / 2), yaw=rng.uniform(0, math.pi),
+                           tilt=tilt, tilt_az=rng.uniform(0, 2 * math.pi)))
+    return sc
+
+
+def config5_pose(frame: int):
+    """Sensor->map pose of frame ``frame`` (20 Hz): a circle of radius 2.5 m
+    about the room's centre at 0.5 m/s, 0.6 m above the ground floor, the
+    sensor level (z up)."""
+    t = frame / 20.0
+    w = 0.5 / 2.5
+    x, y = 4.0 + 2.5 * math.cos(w * t), 4.0 + 2.5 * math.sin(w * t)
+    R = _rot_z(w * t + math.pi / 2)
+    return np.concatenate([R, np.array([[x], [y], [0.6]])], axis=1)
+
+
+def config5_frame(frame: int, scene: Scene, device="cpu", lidar: Lidar | None = None):
+    """(points float32[1,300,480, 3] in the sensor frame, NaN without a return
+    in range; pose float32[12]).  Noise seed = 500,000 + frame."""
+    import torch
+    lidar = lidar or Lidar()
+    pose = config5_pose(frame)
+    dirs = lidar.rays()
+    R, t = pose[:, :3], pose[:, 3]
+    rng = np.random.Generator(np.random.PCG64(500000 + frame))
+    noise = rng.standard_normal(dirs.shape[0]).astype(np.float32)
+    r = raycast(scene, t, dirs @ R.T, device=device)
+    nz = torch.as_tensor(noise, device=device)
+    valid = (r >= lidar.r_min) & (r <= lidar.r_max)
+    rn = r + nz * lidar.sigma
+    d = torch.as_tensor(dirs, dtype=torch.float32, device=device)
+    pts = d * rn[:, None]
+    pts = torch.where(valid[:, None], pts, torch.full_like(pts, float("nan")))
     return pts, pose.astype(np.float32).reshape(12)
 
 
