@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared", "-fPIC",
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu11", "-pthread", "-shared", "-fPIC",
                "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
@@ -99,12 +99,24 @@ def lib():
             L.orc_map_n_vox.restype = C.c_uint32
             L.orc_map_voxels.argtypes = [vp]
             L.orc_map_voxels.restype = C.POINTER(Voxel)
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_get_threads.restype = C.c_int
             L.orc_voxel_size.restype = C.c_uint32
             L.orc_plane_size.restype = C.c_uint32
             assert L.orc_voxel_size() == C.sizeof(Voxel), "oracle voxel layout mismatch"
             assert L.orc_plane_size() == C.sizeof(Plane), "oracle plane layout mismatch"
             _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Host threads for the stages whose items are independent (integration,
+    normals, per-cluster fits); results do not depend on it."""
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def _fp(a):

@@ -18,11 +18,55 @@
  * Parity pins (tests/test_oracle_*.py): every function below is pinned against
  * brute force, closed forms, numpy/scipy routines or invariants.  Nothing here
  * is "parity unpinned".
+ *
+ * orc_set_threads(n) (default 1) splits the stages whose items are
+ * independent -- points of one integration (integer atomics), voxels of the
+ * normal computation, clusters of the plane fit -- over n POSIX threads, for
+ * the all-cores timing of the CPU baseline; results are identical to one
+ * thread.  With one thread every loop below runs exactly as written.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : (n > 256 ? 256 : n); }
+int orc_get_threads(void) { return g_threads; }
+
+/* Runs fn(ctx, lo, hi) over contiguous ranges of [0, n) on g_threads threads
+ * (the calling thread takes the first range). */
+typedef void (*range_fn)(void *ctx, uint64_t lo, uint64_t hi);
+typedef struct { range_fn fn; void *ctx; uint64_t lo, hi; } range_job;
+static void *range_thread(void *p)
+{
+    range_job *j = (range_job *)p;
+    j->fn(j->ctx, j->lo, j->hi);
+    return NULL;
+}
+static void par_for(uint64_t n, range_fn fn, void *ctx)
+{
+    int t = g_threads;
+    if (t <= 1 || n < 2) { fn(ctx, 0, n); return; }
+    if ((uint64_t)t > n) t = (int)n;
+    range_job jobs[256];
+    pthread_t th[256];
+    int started[256];
+    for (int i = 0; i < t; ++i) {
+        jobs[i].fn = fn; jobs[i].ctx = ctx;
+        jobs[i].lo = n * (uint64_t)i / (uint64_t)t;
+        jobs[i].hi = n * (uint64_t)(i + 1) / (uint64_t)t;
+        started[i] = 0;
+    }
+    for (int i = 1; i < t; ++i) started[i] = pthread_create(&th[i], NULL, range_thread, &jobs[i]) == 0;
+    for (int i = 1; i < t; ++i)
+        if (!started[i]) range_thread(&jobs[i]);  /* no thread: run it here */
+    range_thread(&jobs[0]);
+    for (int i = 1; i < t; ++i)
+        if (started[i]) pthread_join(th[i], NULL);
+}
 
 #define ORC_OK 0
 #define ORC_ERR_INVALID_ARG 1
@@ -159,12 +203,15 @@ void orc_map_destroy(void *h)
  * dropped and counted.  Eq. 1's running mean is kept as exact integer sums of
  * rint(d * 2^20) (2^-20 m ~ 0.95 um units) plus a count: the mean it defines
  * is recovered in orc_segment up to that quantum, independent of point order. */
-int orc_integrate(void *h, const float *xyz, uint64_t n, const float pose[12])
+typedef struct { orc_map *m; const float *xyz; const float *pose; } integ_ctx;
+static void integrate_range(void *vc, uint64_t lo, uint64_t hi)
 {
-    orc_map *m = (orc_map *)h;
-    if (!m || (!xyz && n)) return ORC_ERR_INVALID_ARG;
+    integ_ctx *cx = (integ_ctx *)vc;
+    orc_map *m = cx->m;
+    const float *xyz = cx->xyz, *pose = cx->pose;
+    const int atomic = g_threads > 1;  /* integer sums: the same in any order */
     const float q = 1048576.0f; /* 2^20 */
-    for (uint64_t p = 0; p < n; ++p) {
+    for (uint64_t p = lo; p < hi; ++p) {
         float x = xyz[3 * p + 0], y = xyz[3 * p + 1], z = xyz[3 * p + 2];
         float wx = fmaf(pose[2], z, fmaf(pose[1], y, fmaf(pose[0], x, pose[3])));
         float wy = fmaf(pose[6], z, fmaf(pose[5], y, fmaf(pose[4], x, pose[7])));
@@ -173,14 +220,31 @@ int orc_integrate(void *h, const float *xyz, uint64_t n, const float pose[12])
         float fx = floorf(dx * m->inv_res), fy = floorf(dy * m->inv_res), fz = floorf(dz * m->inv_res);
         int ok = (fx >= 0.0f) && (fx < (float)m->nx) && (fy >= 0.0f) && (fy < (float)m->ny) &&
                  (fz >= 0.0f) && (fz < (float)m->nz);
-        if (!ok) { m->n_dropped++; continue; }
-        uint64_t v = vid_of(m, (int)fx, (int)fy, (int)fz);
-        m->S[3 * v + 0] += (int64_t)rintf(dx * q);
-        m->S[3 * v + 1] += (int64_t)rintf(dy * q);
-        m->S[3 * v + 2] += (int64_t)rintf(dz * q);
-        m->C[v] += 1u;
-        m->n_in++;
+        uint64_t v = ok ? vid_of(m, (int)fx, (int)fy, (int)fz) : 0;
+        if (!atomic) {
+            if (!ok) { m->n_dropped++; continue; }
+            m->S[3 * v + 0] += (int64_t)rintf(dx * q);
+            m->S[3 * v + 1] += (int64_t)rintf(dy * q);
+            m->S[3 * v + 2] += (int64_t)rintf(dz * q);
+            m->C[v] += 1u;
+            m->n_in++;
+        } else {
+            if (!ok) { __atomic_fetch_add(&m->n_dropped, 1, __ATOMIC_RELAXED); continue; }
+            __atomic_fetch_add(&m->S[3 * v + 0], (int64_t)rintf(dx * q), __ATOMIC_RELAXED);
+            __atomic_fetch_add(&m->S[3 * v + 1], (int64_t)rintf(dy * q), __ATOMIC_RELAXED);
+            __atomic_fetch_add(&m->S[3 * v + 2], (int64_t)rintf(dz * q), __ATOMIC_RELAXED);
+            __atomic_fetch_add(&m->C[v], 1u, __ATOMIC_RELAXED);
+            __atomic_fetch_add(&m->n_in, 1, __ATOMIC_RELAXED);
+        }
     }
+}
+
+int orc_integrate(void *h, const float *xyz, uint64_t n, const float pose[12])
+{
+    orc_map *m = (orc_map *)h;
+    if (!m || (!xyz && n)) return ORC_ERR_INVALID_ARG;
+    integ_ctx cx = {m, xyz, pose};
+    par_for(n, integrate_range, &cx);
     return ORC_OK;
 }
 
@@ -563,6 +627,52 @@ static int fit_cluster(const float *pts, uint32_t n, uint32_t label, const orc_p
     return st;
 }
 
+/* The fit of clusters c = 0..k-1 (points pts + 3 off[c], n = off[c+1] -
+ * off[c], Philox label lab[c]) into r->planes[0..k) with their hulls appended
+ * to r in cluster order.  With several threads each range of clusters keeps
+ * its hulls apart and they are appended in cluster order afterwards. */
+typedef struct {
+    orc_result *r; const uint32_t *off; const uint32_t *lab; const orc_params *prm;
+    int nt; orc_result part[256]; int st[256]; uint64_t lo[256];
+} fit_ctx;
+static void fit_range(void *vc, uint64_t lo, uint64_t hi)
+{
+    fit_ctx *cx = (fit_ctx *)vc;
+    int t = 0;  /* this range's index: par_for splits [0, k) exactly as fit_all does */
+    while (t + 1 < cx->nt && cx->lo[t] != lo) ++t;
+    orc_result *hr = g_threads > 1 ? &cx->part[t] : cx->r;
+    for (uint64_t c = lo; c < hi && cx->st[t] == ORC_OK; ++c) {
+        orc_plane *pl = &cx->r->planes[c];
+        const uint32_t o = cx->off[c];
+        cx->st[t] = fit_cluster(cx->r->pts + 3 * (size_t)o, cx->off[c + 1] - o, cx->lab ? cx->lab[c] : (uint32_t)c,
+                                cx->prm, pl, cx->r->inlier + o, hr);
+        pl->point_off = o;
+    }
+}
+static int fit_all(orc_result *r, const uint32_t *off, const uint32_t *lab, uint32_t k, const orc_params *prm)
+{
+    fit_ctx *cx = (fit_ctx *)calloc(1, sizeof(fit_ctx));
+    if (!cx) return ORC_ERR_OUT_OF_MEMORY;
+    cx->r = r; cx->off = off; cx->lab = lab; cx->prm = prm;
+    int t = g_threads < (int)(k ? k : 1) ? g_threads : (int)(k ? k : 1);
+    cx->nt = t;
+    for (int i = 0; i < t; ++i) cx->lo[i] = (uint64_t)k * (uint64_t)i / (uint64_t)t;
+    par_for(k, fit_range, cx);
+    int st = ORC_OK;
+    for (int i = 0; i < 256; ++i) if (cx->st[i] != ORC_OK) st = cx->st[i];
+    if (g_threads > 1 && st == ORC_OK) {  /* hulls in cluster order: shift each range's offsets */
+        for (int i = 0; i < t && st == ORC_OK; ++i) {
+            const uint64_t end = i + 1 < t ? cx->lo[i + 1] : k;
+            for (uint64_t c = cx->lo[i]; c < end; ++c) r->planes[c].hull_off += r->n_hull;
+            st = push_hull(r, cx->part[i].hull_xy, cx->part[i].n_hull);
+        }
+    }
+    for (int i = 0; i < 256; ++i) free(cx->part[i].hull_xy);
+    free(cx);
+    r->n_planes = k;
+    return st;
+}
+
 void orc_result_free(void *h)
 {
     orc_result *r = (orc_result *)h;
@@ -583,15 +693,9 @@ void *orc_fit_planes(const float *xyz, const uint32_t *off, const uint32_t *labe
     if (!r->planes || !r->pts || !r->inlier) { orc_result_free(r); return NULL; }
     memcpy(r->pts, xyz, (size_t)npts * 3 * sizeof(float));
     r->n_pts = npts;
-    for (uint32_t c = 0; c < k; ++c) {
-        uint32_t n = off[c + 1] - off[c];
-        orc_plane *pl = &r->planes[r->n_planes];
-        if (fit_cluster(r->pts + 3 * (size_t)off[c], n, label ? label[c] : c, prm, pl, r->inlier + off[c], r)) {
-            orc_result_free(r);
-            return NULL;
-        }
-        pl->point_off = off[c];
-        r->n_planes++;
+    if (fit_all(r, off, label, k, prm) != ORC_OK) {
+        orc_result_free(r);
+        return NULL;
     }
     return r;
 }
@@ -614,6 +718,49 @@ static int ccl_edge(const orc_voxel *a, const orc_voxel *b, const orc_params *pr
     float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
     float c = fmaf(a->n[2], b->n[2], fmaf(a->n[1], b->n[1], a->n[0] * b->n[0]));
     return (d2 < prm->d_th2) && (fabsf(c) > prm->cos_ccl);
+}
+
+/* Eq. 3 / Eq. 4 for the occupied voxels lo..hi-1 (each reads the window's
+ * means and writes only its own normal, N and status). */
+typedef struct { orc_map *m; const int32_t *occ_index; const orc_params *prm; } normals_ctx;
+static void normals_range(void *vc, uint64_t lo, uint64_t hi)
+{
+    normals_ctx *cx = (normals_ctx *)vc;
+    orc_map *m = cx->m;
+    const int32_t *occ_index = cx->occ_index;
+    const orc_params *prm = cx->prm;
+    for (uint64_t i = lo; i < hi; ++i) {
+        orc_voxel *x = &m->vox[i];
+        int64_t s1[3] = {0, 0, 0}, s2[6] = {0, 0, 0, 0, 0, 0};
+        int64_t cnt = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t j = idx_lookup(m, occ_index, x->ijk[0] + dx, x->ijk[1] + dy, x->ijk[2] + dz);
+                    if (j < 0) continue;
+                    const orc_voxel *y = &m->vox[j];
+                    int64_t a = (int64_t)y->M[0] - x->M[0], b = (int64_t)y->M[1] - x->M[1],
+                            c = (int64_t)y->M[2] - x->M[2];
+                    s1[0] += a; s1[1] += b; s1[2] += c;
+                    s2[0] += a * a; s2[1] += b * b; s2[2] += c * c;
+                    s2[3] += a * b; s2[4] += a * c; s2[5] += b * c;
+                    ++cnt;
+                }
+        x->nbr = (uint32_t)(cnt - 1);
+        int64_t A[6];
+        A[0] = cnt * s2[0] - s1[0] * s1[0];
+        A[1] = cnt * s2[1] - s1[1] * s1[1];
+        A[2] = cnt * s2[2] - s1[2] * s1[2];
+        A[3] = cnt * s2[3] - s1[0] * s1[1];
+        A[4] = cnt * s2[4] - s1[0] * s1[2];
+        A[5] = cnt * s2[5] - s1[1] * s1[2];
+        float Af[6];
+        for (int a = 0; a < 6; ++a) Af[a] = (float)A[a];
+        float V[3][3], D[3];
+        jacobi3_f32(Af, 6, V, D);
+        pick_normal_f32(V, D, x->n);
+        x->status = (x->nbr >= prm->n_th && fabsf(x->n[2]) >= prm->cos_step) ? 2u : 1u;
+    }
 }
 
 void *orc_segment(void *h, const orc_params *prm)
@@ -652,38 +799,8 @@ void *orc_segment(void *h, const orc_params *prm)
     /* Eq. 3 / Eq. 4: covariance of the mean positions in the 3x3x3 window
      * (self included), normal = eigenvector of the smallest eigenvalue by FP32
      * Jacobi; steppable iff N >= N_th and |n_z| >= cos(theta_th). */
-    for (uint32_t i = 0; i < nocc; ++i) {
-        orc_voxel *x = &m->vox[i];
-        int64_t s1[3] = {0, 0, 0}, s2[6] = {0, 0, 0, 0, 0, 0};
-        int64_t cnt = 0;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int64_t j = idx_lookup(m, occ_index, x->ijk[0] + dx, x->ijk[1] + dy, x->ijk[2] + dz);
-                    if (j < 0) continue;
-                    const orc_voxel *y = &m->vox[j];
-                    int64_t a = (int64_t)y->M[0] - x->M[0], b = (int64_t)y->M[1] - x->M[1],
-                            c = (int64_t)y->M[2] - x->M[2];
-                    s1[0] += a; s1[1] += b; s1[2] += c;
-                    s2[0] += a * a; s2[1] += b * b; s2[2] += c * c;
-                    s2[3] += a * b; s2[4] += a * c; s2[5] += b * c;
-                    ++cnt;
-                }
-        x->nbr = (uint32_t)(cnt - 1);
-        int64_t A[6];
-        A[0] = cnt * s2[0] - s1[0] * s1[0];
-        A[1] = cnt * s2[1] - s1[1] * s1[1];
-        A[2] = cnt * s2[2] - s1[2] * s1[2];
-        A[3] = cnt * s2[3] - s1[0] * s1[1];
-        A[4] = cnt * s2[4] - s1[0] * s1[2];
-        A[5] = cnt * s2[5] - s1[1] * s1[2];
-        float Af[6];
-        for (int a = 0; a < 6; ++a) Af[a] = (float)A[a];
-        float V[3][3], D[3];
-        jacobi3_f32(Af, 6, V, D);
-        pick_normal_f32(V, D, x->n);
-        x->status = (x->nbr >= prm->n_th && fabsf(x->n[2]) >= prm->cos_step) ? 2u : 1u;
-    }
+    normals_ctx ncx = {m, occ_index, prm};
+    par_for(nocc, normals_range, &ncx);
     /* Algorithm 1: connected components of the steppable voxels under the
      * distance / normal-angle adjacency over the 26-neighbourhood.  The fixed
      * point of the min-label propagation labels every component by its
@@ -788,13 +905,7 @@ void *orc_segment(void *h, const orc_params *prm)
             r->pt_vid[pos] = m->vox[i].vid;
         }
         /* Sec. III.C: multi-plane estimation and boundary polygon per cluster */
-        int st = ORC_OK;
-        for (uint32_t c = 0; c < n_lab && st == ORC_OK; ++c) {
-            orc_plane *pl = &r->planes[r->n_planes];
-            st = fit_cluster(r->pts + 3 * (size_t)off[c], lab_cnt[c], lab_list[c], prm, pl, r->inlier + off[c], r);
-            pl->point_off = off[c];
-            r->n_planes++;
-        }
+        int st = fit_all(r, off, lab_list, n_lab, prm);
         free(off); free(fill); free(cnt_by_idx); free(root_idx); free(lab_list); free(lab_cnt); free(cl_of_root);
         if (st != ORC_OK) { orc_result_free(r); return NULL; }
         return r;
