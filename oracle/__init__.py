@@ -99,6 +99,8 @@ def lib():
             L.orc_map_n_vox.restype = C.c_uint32
             L.orc_map_voxels.argtypes = [vp]
             L.orc_map_voxels.restype = C.POINTER(Voxel)
+            L.orc_clear_rays.argtypes = [vp, C.POINTER(C.c_float), C.c_uint64, C.POINTER(C.c_float),
+                                         C.POINTER(C.c_uint64)]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             L.orc_voxel_size.restype = C.c_uint32
@@ -204,6 +206,18 @@ class OracleMap:
         st = lib().orc_integrate(self._h, _fp(xyz), xyz.shape[0], _fp(pose))
         if st:
             raise RuntimeError(f"orc_integrate failed: {st}")
+
+    def clear_rays(self, xyz, pose):
+        """Eq. 2: clears every occupied voxel that a ray from the sensor (the
+        pose's translation) to a point passes through before the point's own
+        voxel; returns the number of voxels cleared."""
+        xyz = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+        pose = np.ascontiguousarray(pose, np.float32).reshape(12)
+        k = C.c_uint64()
+        st = lib().orc_clear_rays(self._h, _fp(xyz), xyz.shape[0], _fp(pose), C.byref(k))
+        if st:
+            raise RuntimeError(f"orc_clear_rays failed: {st}")
+        return int(k.value)
 
     def counts(self):
         out = (C.c_uint64 * 2)()

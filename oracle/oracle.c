@@ -248,6 +248,112 @@ int orc_integrate(void *h, const float *xyz, uint64_t n, const float pose[12])
     return ORC_OK;
 }
 
+/* Section III.B, Eq. 2 (voxel information clearing): the voxels that the ray
+ * from the sensor to a point passes through are free space; a voxel that at
+ * least one ray of the frame passes through (n_i > 0) is cleared.  Reading:
+ * the traversal is a monotone 6-connected walk in voxel units from the
+ * sensor's voxel to the point's voxel (Amanatides and Woo's grid traversal,
+ * 1987): s = (t - origin) * inv_res and e = (p' - origin) * inv_res in FP32
+ * (p' is the point in the map frame, keyed exactly as orc_integrate keys it),
+ * d = e - s; per axis the parameter of the next voxel boundary
+ * tmax = (boundary - s) / d and its increment tdelta = 1 / |d|; each step
+ * advances the axis with the smallest tmax (ties to x, then y, then z) among
+ * the axes not yet at the end voxel's coordinate, so the walk reaches the
+ * end voxel in exactly |ve - v0| (L1) steps.  Every voxel walked before the
+ * end voxel is marked if it lies in the grid; the end voxel (the point's own)
+ * is not.  The walk stops early once it is outside the grid on an axis it is
+ * not moving back along.  Points that are not finite cast no ray.  All marks
+ * of the frame are collected first, then the marked voxels are cleared (sums
+ * and count to zero); integrating the frame's points follows. */
+typedef struct { orc_map *m; const float *xyz; const float *pose; uint8_t *mark; } clear_ctx;
+static void clear_range(void *vc, uint64_t lo, uint64_t hi)
+{
+    clear_ctx *cx = (clear_ctx *)vc;
+    orc_map *m = cx->m;
+    const float *xyz = cx->xyz, *pose = cx->pose;
+    const int dims[3] = {m->nx, m->ny, m->nz};
+    const float org[3] = {m->ox, m->oy, m->oz};
+    const float tr[3] = {pose[3], pose[7], pose[11]};
+    float s[3];
+    for (int a = 0; a < 3; ++a) s[a] = (tr[a] - org[a]) * m->inv_res;
+    for (uint64_t p = lo; p < hi; ++p) {
+        float x = xyz[3 * p + 0], y = xyz[3 * p + 1], z = xyz[3 * p + 2];
+        float w[3];
+        w[0] = fmaf(pose[2], z, fmaf(pose[1], y, fmaf(pose[0], x, pose[3])));
+        w[1] = fmaf(pose[6], z, fmaf(pose[5], y, fmaf(pose[4], x, pose[7])));
+        w[2] = fmaf(pose[10], z, fmaf(pose[9], y, fmaf(pose[8], x, pose[11])));
+        float e[3];
+        int fin = 1;
+        for (int a = 0; a < 3; ++a) {
+            e[a] = (w[a] - org[a]) * m->inv_res;
+            fin &= isfinite(e[a]) && isfinite(s[a]);
+        }
+        if (!fin) continue;
+        int64_t v[3], ve[3];
+        int step[3];
+        float tmax[3], tdel[3];
+        int64_t left = 0;
+        for (int a = 0; a < 3; ++a) {
+            v[a] = (int64_t)floorf(s[a]);
+            ve[a] = (int64_t)floorf(e[a]);
+            const float d = e[a] - s[a];
+            if (d > 0.0f) {
+                step[a] = 1;
+                tmax[a] = ((float)(v[a] + 1) - s[a]) / d;
+                tdel[a] = 1.0f / d;
+            } else if (d < 0.0f) {
+                step[a] = -1;
+                tmax[a] = ((float)v[a] - s[a]) / d;
+                tdel[a] = -1.0f / d;
+            } else {
+                step[a] = 0;
+                tmax[a] = INFINITY;
+                tdel[a] = INFINITY;
+            }
+            left += ve[a] > v[a] ? ve[a] - v[a] : v[a] - ve[a];
+        }
+        for (; left > 0; --left) {
+            int inside = 1, gone = 0;
+            for (int a = 0; a < 3; ++a) {
+                inside &= v[a] >= 0 && v[a] < dims[a];
+                gone |= (v[a] < 0 && step[a] <= 0) || (v[a] >= dims[a] && step[a] >= 0);
+            }
+            if (gone) break;
+            if (inside) {
+                const uint64_t vid = vid_of(m, (int)v[0], (int)v[1], (int)v[2]);
+                if (m->C[vid]) __atomic_store_n(&cx->mark[vid], (uint8_t)1, __ATOMIC_RELAXED);
+            }
+            int best = -1;
+            for (int a = 0; a < 3; ++a) {
+                if (v[a] == ve[a]) continue;
+                if (best < 0 || tmax[a] < tmax[best]) best = a;
+            }
+            v[best] += step[best];
+            tmax[best] += tdel[best];
+        }
+    }
+}
+
+int orc_clear_rays(void *h, const float *xyz, uint64_t n, const float pose[12], uint64_t *cleared)
+{
+    orc_map *m = (orc_map *)h;
+    if (!m || (!xyz && n)) return ORC_ERR_INVALID_ARG;
+    uint8_t *mark = (uint8_t *)calloc(m->nv ? m->nv : 1, 1);
+    if (!mark) return ORC_ERR_OUT_OF_MEMORY;
+    clear_ctx cx = {m, xyz, pose, mark};
+    par_for(n, clear_range, &cx);
+    uint64_t k = 0;
+    for (uint64_t v = 0; v < m->nv; ++v) {
+        if (!mark[v]) continue;
+        m->S[3 * v + 0] = m->S[3 * v + 1] = m->S[3 * v + 2] = 0;
+        m->C[v] = 0;
+        ++k;
+    }
+    free(mark);
+    if (cleared) *cleared = k;
+    return ORC_OK;
+}
+
 void orc_map_counts(void *h, uint64_t out[2])
 {
     orc_map *m = (orc_map *)h;
