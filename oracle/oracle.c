@@ -261,10 +261,12 @@ int orc_integrate(void *h, const float *xyz, uint64_t n, const float pose[12])
  * the axes not yet at the end voxel's coordinate, so the walk reaches the
  * end voxel in exactly |ve - v0| (L1) steps.  Every voxel walked before the
  * end voxel is marked if it lies in the grid; the end voxel (the point's own)
- * is not.  The walk stops early once it is outside the grid on an axis it is
- * not moving back along.  Points that are not finite cast no ray.  All marks
- * of the frame are collected first, then the marked voxels are cleared (sums
- * and count to zero); integrating the frame's points follows. */
+ * is not.  The walk stops once it leaves the grid (a monotone walk does not
+ * come back).  A sensor outside the grid casts no rays (a robot-centric map
+ * holds its sensor); points that are not finite, or more than 2^30 voxels
+ * away, cast no ray.  All marks of the frame are collected first, then the
+ * marked voxels are cleared (sums and count to zero); integrating the
+ * frame's points follows. */
 typedef struct { orc_map *m; const float *xyz; const float *pose; uint8_t *mark; } clear_ctx;
 static void clear_range(void *vc, uint64_t lo, uint64_t hi)
 {
@@ -286,7 +288,7 @@ static void clear_range(void *vc, uint64_t lo, uint64_t hi)
         int fin = 1;
         for (int a = 0; a < 3; ++a) {
             e[a] = (w[a] - org[a]) * m->inv_res;
-            fin &= isfinite(e[a]) && isfinite(s[a]);
+            fin &= isfinite(e[a]) && fabsf(e[a]) < 1073741824.0f;
         }
         if (!fin) continue;
         int64_t v[3], ve[3];
@@ -341,7 +343,11 @@ int orc_clear_rays(void *h, const float *xyz, uint64_t n, const float pose[12], 
     uint8_t *mark = (uint8_t *)calloc(m->nv ? m->nv : 1, 1);
     if (!mark) return ORC_ERR_OUT_OF_MEMORY;
     clear_ctx cx = {m, xyz, pose, mark};
-    par_for(n, clear_range, &cx);
+    const float sv[3] = {(pose[3] - m->ox) * m->inv_res, (pose[7] - m->oy) * m->inv_res,
+                         (pose[11] - m->oz) * m->inv_res};
+    const int sensor_in = sv[0] >= 0.0f && sv[0] < (float)m->nx && sv[1] >= 0.0f && sv[1] < (float)m->ny &&
+                          sv[2] >= 0.0f && sv[2] < (float)m->nz;
+    if (sensor_in) par_for(n, clear_range, &cx);
     uint64_t k = 0;
     for (uint64_t v = 0; v < m->nv; ++v) {
         if (!mark[v]) continue;

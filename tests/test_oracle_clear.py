@@ -172,3 +172,10 @@ def test_clearing_is_the_same_on_all_threads(orc):
     assert res[0][0] == res[1][0]
     for x, y in zip(res[0][1], res[1][1]):
         assert np.array_equal(x, y)
+
+
+def test_a_sensor_outside_the_grid_casts_no_ray(orc):
+    m, _ = _full_map(orc)
+    t = np.float32([-0.5, 0.55, 0.55])  # 0.5 m outside the x = 0 face
+    e, gone, k = _ray(m, t, [0.95, 0.55, 0.55])
+    assert k == 0 and not gone
