@@ -109,6 +109,7 @@ typedef struct {
     uint32_t clusters;           /* kept clusters at the last segmentation        */
     uint32_t clustered_points;   /* points in kept clusters at the last segmentation */
     uint64_t device_bytes;       /* device memory held by the map                 */
+    uint64_t voxels_cleared;     /* voxels cleared by ray casting since creation / reset */
 } vm_stats;
 
 /* Create a map.  params: see vm_map_params.  cuda_stream: a cudaStream_t the
@@ -129,6 +130,21 @@ vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out
  * VM_ERR_CUDA; a full brick pool is reported by the next vm_segment /
  * vm_get_stats as VM_ERR_CAPACITY. */
 vm_status vm_integrate(vm_map* map, const float* xyz, uint32_t n, const float pose3x4[12], int xyz_on_device);
+
+/* Voxel information clearing (Sec. III.B, Eq. 2) before the update.
+ * flags: VM_INTEGRATE_CLEAR first clears every occupied voxel that the ray
+ * from the sensor (the pose's translation) to one of the frame's points
+ * passes through, the point's own voxel excepted, then integrates the frame
+ * as vm_integrate does.  The ray is walked voxel by voxel from the sensor's
+ * voxel to the point's (a monotone 6-connected grid traversal: each step on
+ * the axis whose next voxel boundary comes first, ties to x, then y, then z,
+ * among the axes not yet at the point's voxel coordinate; FP32, explicit
+ * rounding), and stops where it leaves the grid.  A sensor outside the grid
+ * casts no rays; points that are not finite cast none.  Other arguments and
+ * errors as vm_integrate; cleared voxels are counted in vm_stats. */
+#define VM_INTEGRATE_CLEAR 1u
+vm_status vm_integrate_ex(vm_map* map, const float* xyz, uint32_t n, const float pose3x4[12], int xyz_on_device,
+                          uint32_t flags);
 
 /* Multi-plane segmentation of the accumulated map (Sec. III.C): mean
  * positions, normals and steppable classification (Eq. 3, Eq. 4), clustering
@@ -393,8 +409,8 @@ vm_status vm_server_destroy(vm_server* srv);
 /* Diagnostics (no counterpart in the paper).  Stage timing records CUDA
  * events around each pipeline stage on the stream it runs on: integrate,
  * order_bricks, finalize, moments, eigen, ccl_local, ccl_cross, clusters,
- * ransac_hyp, ransac_score, extract, refit_hull, pack (vm_stage_name gives the
- * names).
+ * ransac_hyp, ransac_score, extract, refit_hull, pack, clear (vm_stage_name
+ * gives the names).
  * vm_stage_timing: enable (1) or disable (0) for a map, or for this thread's
  * vm_fit_planes calls when map is NULL.  vm_stage_times: device milliseconds
  * and call counts per stage accumulated since the previous call (then reset);

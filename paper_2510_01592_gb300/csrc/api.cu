@@ -28,7 +28,7 @@ void uncount_launch(unsigned long long n) { g_launches.fetch_sub(n); }
 
 static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "finalize", "moments", "eigen",
                                               "ccl_local", "ccl_cross", "clusters", "ransac_hyp", "ransac_score",
-                                              "extract", "refit_hull", "pack"};
+                                              "extract", "refit_hull", "pack", "clear"};
 
 
 void set_error(const std::string& msg) { g_err = msg; }
@@ -278,7 +278,7 @@ uint64_t map_footprint(const vm_map_params& p, const vm_segment_params& sp) {
     uint64_t nb = 1;
     for (int a = 0; a < 3; ++a) nb *= (uint64_t)((p.dims[a] + kBrick - 1) / kBrick);
     const uint64_t cap = p.brick_capacity && p.brick_capacity < nb ? p.brick_capacity : nb;
-    const uint64_t pool = nb * 4 + cap * 4 + cap * kBrickVox * (3 * 8 + 4) + 4096;
+    const uint64_t pool = nb * 4 + cap * 4 + cap * kBrickVox * (3 * 8 + 4) + cap * (kBrickVox / 8) + 4096;
     const uint64_t bricks = (nb + 1) * 4 + nb * 4 + cap * 8 + 4096;
     const size_t nv = (size_t)cap * kBrickVox;
     Carver dry{nullptr};
@@ -646,6 +646,7 @@ vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out
     dry.take<unsigned long long>((size_t)m->capacity * 3 * kBrickVox);
     dry.take<uint32_t>((size_t)m->capacity * kBrickVox);
     dry.take<MapCounters>(1);
+    dry.take<uint32_t>((size_t)m->capacity * (kBrickVox / 32));
     dry.take<uint32_t>(4);
     vm_status st = ensure(m->pool, dry.off + 256);
     if (st != VM_OK) {
@@ -658,6 +659,7 @@ vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out
     m->S = c.take<unsigned long long>((size_t)m->capacity * 3 * kBrickVox);
     m->C = c.take<uint32_t>((size_t)m->capacity * kBrickVox);
     m->ctr = c.take<MapCounters>(1);
+    m->mark = c.take<uint32_t>((size_t)m->capacity * (kBrickVox / 32));
     m->err = c.take<uint32_t>(4);
     // brick-level segmentation arrays
     Carver bd{nullptr};
@@ -697,6 +699,7 @@ vm_status vm_reset(vm_map* m) {
     VM_CUDA(cudaMemsetAsync(m->S, 0, (size_t)m->capacity * 3 * kBrickVox * sizeof(unsigned long long), m->stream));
     VM_CUDA(cudaMemsetAsync(m->C, 0, (size_t)m->capacity * kBrickVox * sizeof(uint32_t), m->stream));
     VM_CUDA(cudaMemsetAsync(m->ctr, 0, sizeof(MapCounters), m->stream));
+    VM_CUDA(cudaMemsetAsync(m->mark, 0, (size_t)m->capacity * (kBrickVox / 32) * sizeof(uint32_t), m->stream));
     m->segmented = false;
     return VM_OK;
 }
@@ -719,6 +722,11 @@ vm_status vm_destroy(vm_map* m) {
 }
 
 vm_status vm_integrate(vm_map* m, const float* xyz, uint32_t n, const float pose3x4[12], int xyz_on_device) {
+    return vm_integrate_ex(m, xyz, n, pose3x4, xyz_on_device, 0);
+}
+
+vm_status vm_integrate_ex(vm_map* m, const float* xyz, uint32_t n, const float pose3x4[12], int xyz_on_device,
+                          uint32_t flags) {
     VM_TRY(check_map(m));
     if ((!xyz && n) || !pose3x4) {
         set_error("null points or pose");
@@ -734,6 +742,11 @@ vm_status vm_integrate(vm_map* m, const float* xyz, uint32_t n, const float pose
     Pose P;
     memcpy(P.r, pose3x4, sizeof(P.r));
     StageHook* hk = m->fit.timer.hook();
+    if (flags & VM_INTEGRATE_CLEAR) {
+        VM_STAGE_BEGIN(hk, kStClear, m->stream);
+        VM_CUDA(launch_clear(d, n, P, m->g, m->brick_table, m->S, m->C, m->mark, m->ctr, m->capacity, m->stream));
+        VM_STAGE_END(hk, kStClear, m->stream);
+    }
     VM_STAGE_BEGIN(hk, kStIntegrate, m->stream);
     VM_CUDA(launch_integrate(d, n, P, m->g, m->brick_table, m->slot_key, m->S, m->C, m->ctr, m->capacity, m->stream));
     VM_STAGE_END(hk, kStIntegrate, m->stream);
@@ -895,6 +908,7 @@ vm_status vm_get_stats(vm_map* m, vm_stats* out) {
     out->steppable_voxels = m->last.n_vert;
     out->clusters = m->last.k;
     out->clustered_points = m->last.n_kept;
+    out->voxels_cleared = c.cleared;
     out->device_bytes = m->pool.bytes + m->stage.bytes + m->brick_mem.bytes + m->vox_mem.bytes + m->fit.mem.bytes +
                         m->fit.out.bytes;
     (void)0;

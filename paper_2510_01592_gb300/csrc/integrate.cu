@@ -141,7 +141,145 @@ __global__ void __launch_bounds__(kThreads) k_accum(const float* __restrict__ xy
     }
 }
 
+// Eq. 2: one thread per point walks the point's ray from the sensor's voxel
+// to the point's voxel (excluded): a monotone 6-connected walk, each step on
+// the axis whose next voxel boundary comes first along the ray (ties to x,
+// then y, then z) among the axes not yet at the end voxel's coordinate, all in
+// FP32 with explicit round-to-nearest operations.  The walk stops when it
+// leaves the grid (a monotone walk does not come back); the caller has
+// checked that the sensor is inside the grid.  An occupied voxel on the walk
+// gets its bit in the mark bitmap (a plain read skips the atomic when the bit
+// is already set).
+__global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict__ xyz, uint32_t n, Pose P, Grid g,
+                                                        const int32_t* __restrict__ table,
+                                                        const uint32_t* __restrict__ C, uint32_t* mark,
+                                                        MapCounters* __restrict__ ctr) {
+    const float s[3] = {__fmul_rn(__fsub_rn(P.r[3], g.ox), g.inv_res), __fmul_rn(__fsub_rn(P.r[7], g.oy), g.inv_res),
+                        __fmul_rn(__fsub_rn(P.r[11], g.oz), g.inv_res)};
+    const int dims[3] = {g.nx, g.ny, g.nz};
+    const long long cap = (long long)g.nx + g.ny + g.nz + 3;  // a walk inside the grid is never longer
+    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
+        const float x = xyz[3 * (size_t)i + 0], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
+        float e[3];
+        e[0] = __fmul_rn(__fsub_rn(__fmaf_rn(P.r[2], z, __fmaf_rn(P.r[1], y, __fmaf_rn(P.r[0], x, P.r[3]))), g.ox),
+                         g.inv_res);
+        e[1] = __fmul_rn(__fsub_rn(__fmaf_rn(P.r[6], z, __fmaf_rn(P.r[5], y, __fmaf_rn(P.r[4], x, P.r[7]))), g.oy),
+                         g.inv_res);
+        e[2] = __fmul_rn(__fsub_rn(__fmaf_rn(P.r[10], z, __fmaf_rn(P.r[9], y, __fmaf_rn(P.r[8], x, P.r[11]))), g.oz),
+                         g.inv_res);
+        bool fin = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fin &= isfinite(e[a]) && fabsf(e[a]) < 1073741824.0f;
+        if (!fin) continue;
+        long long v[3], ve[3], left = 0;
+        int step[3];
+        float tmax[3], tdel[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            v[a] = (long long)floorf(s[a]);
+            ve[a] = (long long)floorf(e[a]);
+            const float d = __fsub_rn(e[a], s[a]);
+            if (d > 0.0f) {
+                step[a] = 1;
+                tmax[a] = __fdiv_rn(__fsub_rn(__ll2float_rn(v[a] + 1), s[a]), d);
+                tdel[a] = __fdiv_rn(1.0f, d);
+            } else if (d < 0.0f) {
+                step[a] = -1;
+                tmax[a] = __fdiv_rn(__fsub_rn(__ll2float_rn(v[a]), s[a]), d);
+                tdel[a] = __fdiv_rn(-1.0f, d);
+            } else {
+                step[a] = 0;
+                tmax[a] = __int_as_float(0x7f800000);
+                tdel[a] = __int_as_float(0x7f800000);
+            }
+            left += ve[a] > v[a] ? ve[a] - v[a] : v[a] - ve[a];
+        }
+        if (left > cap) left = cap;  // the walk leaves the grid first
+        for (; left > 0; --left) {
+            bool inside = true, gone = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                inside &= v[a] >= 0 && v[a] < dims[a];
+                gone |= (v[a] < 0 && step[a] <= 0) || (v[a] >= dims[a] && step[a] >= 0);
+            }
+            if (gone) break;
+            if (inside) {
+                const int ix = (int)v[0], iy = (int)v[1], iz = (int)v[2];
+                const uint32_t brick =
+                    ((uint32_t)(iz >> 3) * (uint32_t)g.nby + (uint32_t)(iy >> 3)) * (uint32_t)g.nbx + (uint32_t)(ix >> 3);
+                const int32_t slot = table[brick];
+                if (slot >= 0) {
+                    const uint32_t idx = (uint32_t)slot * kBrickVox + (uint32_t)((((iz & 7) << 3) | (iy & 7)) << 3 | (ix & 7));
+                    const uint32_t bit = 1u << (idx & 31);
+                    if (C[idx] && !(__ldcg(mark + (idx >> 5)) & bit)) atomicOr(mark + (idx >> 5), bit);
+                }
+            }
+            int best = -1;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (v[a] == ve[a]) continue;
+                if (best < 0 || tmax[a] < tmax[best]) best = a;
+            }
+            v[best] += step[best];
+            tmax[best] = __fadd_rn(tmax[best], tdel[best]);
+        }
+    }
+}
+
+// Clears the marked voxels of the allocated slots (sums and count to zero)
+// and their marks; counts the cleared voxels.
+__global__ void __launch_bounds__(kThreads) k_clear_apply(unsigned long long* __restrict__ S, uint32_t* __restrict__ C,
+                                                         uint32_t* __restrict__ mark, MapCounters* __restrict__ ctr,
+                                                         uint32_t capacity) {
+    const uint32_t nb = min(ctr->n_bricks, capacity);
+    const size_t words = (size_t)nb * (kBrickVox / 32);
+    uint32_t cleared = 0;
+    for (size_t w = (size_t)blockIdx.x * kThreads + threadIdx.x; w < words; w += (size_t)gridDim.x * kThreads) {
+        uint32_t m = mark[w];
+        if (!m) continue;
+        mark[w] = 0;
+        const uint32_t slot = (uint32_t)(w / (kBrickVox / 32));
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t l = (uint32_t)((w % (kBrickVox / 32)) * 32 + b);
+            unsigned long long* sp = S + (size_t)slot * 3 * kBrickVox + l;
+            sp[0] = 0;
+            sp[kBrickVox] = 0;
+            sp[2 * kBrickVox] = 0;
+            C[(size_t)slot * kBrickVox + l] = 0;
+            ++cleared;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cleared += __shfl_xor_sync(0xffffffffu, cleared, o);
+    if ((threadIdx.x & 31) == 0 && cleared) atomicAdd(&ctr->cleared, (unsigned long long)cleared);
+}
+
 }  // namespace
+
+cudaError_t launch_clear(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, const int32_t* brick_table,
+                         unsigned long long* S, uint32_t* C, uint32_t* mark, MapCounters* ctr, uint32_t capacity,
+                         cudaStream_t s) {
+    // A sensor outside the grid casts no rays (host check, same arithmetic as the walk's start).
+    const float sx = (pose.r[3] - g.ox) * g.inv_res, sy = (pose.r[7] - g.oy) * g.inv_res,
+                sz = (pose.r[11] - g.oz) * g.inv_res;
+    if (!(sx >= 0.0f && sx < (float)g.nx && sy >= 0.0f && sy < (float)g.ny && sz >= 0.0f && sz < (float)g.nz) ||
+        n == 0)
+        return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t want = (n + kThreads - 1) / kThreads;
+    const uint32_t grid = want < (uint32_t)(sms * 8) ? want : (uint32_t)(sms * 8);
+    k_clear_mark<<<grid, kThreads, 0, s>>>(xyz, n, pose, g, brick_table, C, mark, ctr);
+    const size_t words = (size_t)capacity * (kBrickVox / 32);
+    const size_t wgrid = (words + kThreads - 1) / kThreads;
+    k_clear_apply<<<(unsigned)(wgrid < (size_t)sms * 8 ? wgrid : (size_t)sms * 8), kThreads, 0, s>>>(S, C, mark, ctr,
+                                                                                                      capacity);
+    count_launch(2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, int32_t* brick_table,
                              int32_t* slot_key, unsigned long long* S, uint32_t* C, MapCounters* ctr,

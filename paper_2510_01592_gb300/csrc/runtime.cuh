@@ -133,6 +133,7 @@ struct vm_map {
     uint32_t* C = nullptr;
     vmx::MapCounters* ctr = nullptr;
     uint32_t* err = nullptr;  // segmentation error word
+    uint32_t* mark = nullptr; // ray-cast clearing marks, one bit per voxel slot
     vmx::DevBuf pool;
     vmx::DevBuf stage;             // host points staged on the device
     // segmentation

@@ -49,6 +49,7 @@ struct MapCounters {
     unsigned long long no_capacity;
     uint32_t n_bricks;   // bricks allocated (may exceed capacity on overflow)
     uint32_t err;        // error bits
+    unsigned long long cleared;  // voxels cleared by ray casting (Eq. 2)
 };
 
 // Counters produced by one segmentation, read back by the host.
@@ -133,7 +134,7 @@ __device__ __forceinline__ void pack_cluster(const FitCluster& f, uint32_t label
 // ---------------------------------------------------------------- diagnostics
 // Pipeline stages timed by the optional stage timer.
 enum Stage {
-    kStIntegrate = 0,  // claim + accumulate
+    kStIntegrate = 0,  // claim + accumulate (and ray-cast clearing when asked)
     kStOrder,          // bricks in key order
     kStFinalize,       // integer means
     kStNormals,        // Eq. 3 window moments (k_moments)
@@ -146,6 +147,7 @@ enum Stage {
     kStExtract,        // stage c, inliers, centroid, filter
     kStHull,           // refit + hull
     kStPack,           // output records
+    kStClear,          // Eq. 2 ray-cast clearing (before the frame's integration)
     kNumStages
 };
 
@@ -227,6 +229,13 @@ cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys
 cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, int32_t* brick_table,
                              int32_t* slot_key, unsigned long long* S, uint32_t* C, MapCounters* ctr,
                              uint32_t capacity, cudaStream_t s);
+// Voxel information clearing (Sec. III.B, Eq. 2): marks every occupied voxel
+// that a point's ray from the sensor passes through before the point's own
+// voxel (mark: one bit per voxel slot, capacity * 16 words, zero between
+// calls), then clears the marked voxels and the marks.
+cudaError_t launch_clear(const float* xyz, uint32_t n, const Pose& pose, const Grid& g,
+                         const int32_t* brick_table, unsigned long long* S, uint32_t* C, uint32_t* mark,
+                         MapCounters* ctr, uint32_t capacity, cudaStream_t s);
 
 // ---------------------------------------------------------------- segment.cu
 struct SegBuffers {

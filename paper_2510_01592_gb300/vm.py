@@ -65,7 +65,8 @@ class vm_stats(C.Structure):
     _fields_ = [("points_integrated", C.c_uint64), ("points_dropped", C.c_uint64),
                 ("points_no_capacity", C.c_uint64), ("bricks_allocated", C.c_uint32),
                 ("brick_capacity", C.c_uint32), ("occupied_voxels", C.c_uint32), ("steppable_voxels", C.c_uint32),
-                ("clusters", C.c_uint32), ("clustered_points", C.c_uint32), ("device_bytes", C.c_uint64)]
+                ("clusters", C.c_uint32), ("clustered_points", C.c_uint32), ("device_bytes", C.c_uint64),
+                ("voxels_cleared", C.c_uint64)]
 
 
 class vm_fit_tuning(C.Structure):
@@ -96,6 +97,7 @@ class vm_server_stats(C.Structure):
 _SIGS = {
     "vm_create": (C.c_int, [C.POINTER(vm_map_params), C.c_void_p, C.POINTER(C.c_void_p)]),
     "vm_integrate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_float), C.c_int]),
+    "vm_integrate_ex": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_float), C.c_int, C.c_uint32]),
     "vm_segment": (C.c_int, [C.c_void_p, C.POINTER(vm_segment_params), C.POINTER(vm_planes)]),
     "vm_planes_free": (C.c_int, [C.POINTER(vm_planes)]),
     "vm_reset": (C.c_int, [C.c_void_p]),
@@ -258,8 +260,9 @@ class VoxelMap:
         except Exception:
             pass
 
-    def integrate(self, xyz, pose):
-        """xyz: float32 [n, 3] torch tensor (CUDA or CPU) or numpy array; pose: 12 floats, sensor->map."""
+    def integrate(self, xyz, pose, clear=False):
+        """xyz: float32 [n, 3] torch tensor (CUDA or CPU) or numpy array; pose: 12 floats, sensor->map.
+        clear: first clear the voxels the points' rays pass through (Eq. 2)."""
         pose = np.ascontiguousarray(pose, np.float32).reshape(12)
         on_dev = 1 if (hasattr(xyz, "is_cuda") and xyz.is_cuda) else 0
         if hasattr(xyz, "is_contiguous"):
@@ -269,7 +272,8 @@ class VoxelMap:
             xyz = np.ascontiguousarray(xyz, np.float32)
             n = xyz.size // 3
         order_after_torch(xyz, self._stream)
-        _check(load().vm_integrate(self._h, _ptr(xyz), n, pose.ctypes.data_as(C.POINTER(C.c_float)), on_dev))
+        _check(load().vm_integrate_ex(self._h, _ptr(xyz), n, pose.ctypes.data_as(C.POINTER(C.c_float)), on_dev,
+                                      VM_INTEGRATE_CLEAR if clear else 0))
 
     def segment(self, params: vm_segment_params | None = None):
         params = params or segment_params()
@@ -371,6 +375,7 @@ def fit_planes(xyz, off, params: vm_segment_params | None = None, labels=None, s
         load().vm_planes_free(C.byref(out))
 
 
+VM_INTEGRATE_CLEAR = 1
 VM_FIT_STAGE_TIMING = 1
 VM_FIT_EAGER = 2
 
