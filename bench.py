@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the 16-stream serving variant")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="Poisson-arrival serving run length")
     ap.add_argument("--no-stress", action="store_true", help="skip the LiDAR stress variant")
+    ap.add_argument("--no-eval", action="store_true", help="skip the time sweeps and the plane IoU")
     ap.add_argument("--stress-seconds", type=float, default=10.0, help="stress variant arrival run length")
     ap.add_argument("--profile-fit", type=int, default=0, metavar="K",
                     help="profiling driver: K config-3 clusters (sizes log-uniform in [50, 200000]), "
@@ -493,6 +494,126 @@ def stress_variant(dev, seconds, lidar_frames=40, cam_frames=32):
     return out
 
 
+def polygon_area(P):
+    """Signed area of a polygon (shoelace), positive counter-clockwise."""
+    import numpy as np
+    P = np.asarray(P, float)
+    x, y = P[:, 0], P[:, 1]
+    return 0.5 * float(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1)))
+
+
+def convex_iou(A, B):
+    """Intersection over union of two convex polygons (Sutherland-Hodgman
+    clipping of A by each edge of B, both counter-clockwise)."""
+    import numpy as np
+    A = [tuple(p) for p in np.asarray(A, float)]
+    B = [tuple(p) for p in np.asarray(B, float)]
+    if polygon_area(A) < 0:
+        A = A[::-1]
+    if polygon_area(B) < 0:
+        B = B[::-1]
+    out = A
+    for i in range(len(B)):
+        if not out:
+            break
+        c0, c1 = B[i], B[(i + 1) % len(B)]
+
+        def side(p):
+            return (c1[0] - c0[0]) * (p[1] - c0[1]) - (c1[1] - c0[1]) * (p[0] - c0[0])
+
+        inp, out = out, []
+        for j in range(len(inp)):
+            p, q = inp[j], inp[(j + 1) % len(inp)]
+            sp, sq = side(p), side(q)
+            if sp >= 0:
+                out.append(p)
+            if (sp >= 0) != (sq >= 0):
+                t = sp / (sp - sq)
+                out.append((p[0] + t * (q[0] - p[0]), p[1] + t * (q[1] - p[1])))
+    inter = polygon_area(out) if len(out) >= 3 else 0.0
+    union = polygon_area(A) + polygon_area(B) - inter
+    return inter / union if union > 0 else 0.0
+
+
+def evaluation_variant(dev, stream):
+    """The paper's evaluation shapes on synthetic scenes.  Mapping time against
+    points per frame (a LiDAR frame's first n rays into the 8 x 8 x 3 m map);
+    segmentation time against accumulated occupied voxels along the
+    paper-scale trajectory; the stage top's plane IoU against its exact
+    region after a 48-frame orbit of the single-stage scene."""
+    import numpy as np
+    import torch
+    from paper_2510_01592_gb300 import vm
+    import synth
+    out = {}
+    params = vm.segment_params(n_hyp=100, seed=0)
+
+    def ev_ms(fn, reps):
+        """Median device time of reps calls (after one untimed call)."""
+        fn()
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+        ev[0].record(stream)
+        for i in range(reps):
+            fn()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(ev[i].elapsed_time(ev[i + 1]) for i in range(reps))
+
+    # mapping time against points per frame
+    spec5, sc5 = synth.config5_spec(), synth.config5_scene()
+    lp, lpose = synth.config5_frame(0, sc5, device=dev)
+    m5 = vm.VoxelMap(spec5.dims, spec5.origin, spec5.voxel_size, brick_capacity=131072, stream=stream)
+    m5.integrate(lp, lpose)
+    sweep = []
+    for n in (19200, 76800, 307200, 650240, 1300480):
+        sub = lp[:n].contiguous()
+        ms = ev_ms(lambda: m5.integrate(sub, lpose), 10)
+        msc = ev_ms(lambda: m5.integrate(sub, lpose, clear=True), 5)
+        sweep.append({"points": n, "integrate_ms": round(ms, 4), "clear_and_integrate_ms": round(msc, 4)})
+    m5.close()
+    out["mapping_vs_points"] = sweep
+    # segmentation time against accumulated occupied voxels
+    spec2, sc2 = synth.config2_spec(), synth.config2_scene()
+    m2 = vm.VoxelMap(spec2.dims, spec2.origin, spec2.voxel_size, stream=stream)
+    marks = {10, 30, 60, 100, 150, 200, 250, 300}
+    curve = []
+    for f in range(1, N_FRAMES + 1):
+        p, pose = synth.config2_frame(f, sc2, device=dev)
+        m2.integrate(p, pose)
+        if f in marks:
+            ms = ev_ms(lambda: m2.segment(params), 15)
+            st = m2.stats()
+            curve.append({"frame": f, "occupied_voxels": st["occupied_voxels"], "clusters": st["clusters"],
+                          "segment_ms": round(ms, 4)})
+    m2.close()
+    out["segmentation_vs_voxels"] = curve
+    # plane IoU of the stage top
+    spec = synth.config2_spec()
+    sc = synth.stage_scene()
+    ms_ = vm.VoxelMap(spec.dims, spec.origin, spec.voxel_size, stream=stream)
+    for k in range(48):
+        p, pose = synth.stage_orbit_frame(k, 48, sc, device=dev)
+        ms_.integrate(p, pose)
+    r = ms_.segment(params)
+    ms_.close()
+    (x0, y0), (x1, y1), h = synth.STAGE
+    gt = [(x0, y0), (x1, y0), (x1, y1), (x0, y1)]
+    best = None
+    for i, pl in enumerate(r["planes"]):
+        if pl["best_h"] < 0 or abs(float(pl["normal"][2])) < 0.99 or abs(-float(pl["offset"]) - h) > 0.02:
+            continue
+        o, c = int(pl["hull_offset"]), int(pl["hull_count"])
+        poly = r["hull_xyz"][o:o + c, :2]
+        iou = convex_iou(poly, gt)
+        if best is None or iou > best["iou"]:
+            best = {"iou": round(iou, 4), "inliers": int(pl["inlier_count"]), "hull_vertices": c,
+                    "height_m": round(-float(pl["offset"]), 5)}
+    out["stage_top_iou"] = best
+    out["planes_found"] = int(len(r["planes"]))
+    return out
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -794,6 +915,8 @@ def run_gpu(args):
         res["variants"]["serving_config4"] = serving_variant(dev, args.serve_seconds)
     if not args.no_stress and rank == 0:
         res["variants"]["stress_config5"] = stress_variant(dev, args.stress_seconds)
+    if not args.no_eval and rank == 0:
+        res["variants"]["evaluation"] = evaluation_variant(dev, stream)
     res["stages_ms_per_step"] = {k: round(v[0] / max(1, args.steps), 4) for k, v in stages.items() if v[1]}
     table = kernel_table(stages, st, load_peaks(), st["clustered_points"])
     res["kernels"] = table

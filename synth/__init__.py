@@ -36,7 +36,7 @@ import numpy as np
 __all__ = ["MapSpec", "config1", "config2_spec", "config2_scene", "config2_frame", "config2_pose",
            "config3_clusters", "config3_clusters_device", "e5_clusters", "Scene", "Camera", "config4_streams", "config4_scene", "config4_pose", "config4_frame",
            "poisson_arrivals", "identity_pose", "config5_spec", "config5_scene", "config5_pose",
-           "config5_frame", "Lidar"]
+           "config5_frame", "Lidar", "STAGE", "stage_scene", "stage_orbit_frame"]
 
 
 @dataclass
@@ -608,6 +608,33 @@ def config5_frame(frame: int, scene: Scene, device="cpu", lidar: Lidar | None = 
     d = torch.as_tensor(dirs, dtype=torch.float32, device=device)
     pts = d * rn[:, None]
     pts = torch.where(valid[:, None], pts, torch.full_like(pts, float("nan")))
+    return pts, pose.astype(np.float32).reshape(12)
+
+
+# --------------------------------------------------------------------------
+# The single-stage scene for the plane IoU evaluation.
+# --------------------------------------------------------------------------
+
+STAGE = ((1.2, 1.4), (2.8, 2.6), 0.25)  # (x0, y0), (x1, y1), height: the stage top's ground truth
+
+
+def stage_scene() -> Scene:
+    """Floor and one stage (a 1.6 x 1.2 m box, 0.25 m high, centred at (2, 2)):
+    its top is a plane whose region is known exactly."""
+    sc = Scene()
+    sc.add(_aabb_planes((-50, -50, -1), (50, 50, 0)))
+    (x0, y0), (x1, y1), h = STAGE
+    sc.add(_aabb_planes((x0, y0, 0.0), (x1, y1, h)))
+    return sc
+
+
+def stage_orbit_frame(k: int, n: int, scene: Scene, device="cpu"):
+    """Frame k of n from the config-2 camera on a 1.9 m circle about the stage,
+    1.1 m up, facing its centre, pitched down 35 deg; noise seed 700,000 + k."""
+    a = 2 * math.pi * k / n
+    pos = (2.0 + 1.9 * math.cos(a), 2.0 + 1.9 * math.sin(a), 1.1)
+    pose = camera_pose(pos, a + math.pi, 35.0)
+    pts = _depth_frame(scene, Camera(), pose, seed=700000 + k, device=device)
     return pts, pose.astype(np.float32).reshape(12)
 
 
