@@ -52,13 +52,13 @@ class Plane(C.Structure):
                 ("best_h", C.c_int32), ("ill_conditioned", C.c_int32), ("ransac_n", C.c_float * 3),
                 ("ransac_d", C.c_float), ("refit_n", C.c_double * 3), ("refit_d", C.c_double),
                 ("basis_u", C.c_float * 3), ("basis_v", C.c_float * 3), ("origin", C.c_float * 3),
-                ("hull_off", C.c_uint32), ("hull_n", C.c_uint32), ("point_off", C.c_uint32)]
+                ("hull_off", C.c_uint32), ("hull_n", C.c_uint32), ("point_off", C.c_uint32), ("round", C.c_uint32)]
 
 
 class Params(C.Structure):
     _fields_ = [("n_th", C.c_uint32), ("cos_step", C.c_float), ("d_th2", C.c_float), ("cos_ccl", C.c_float),
                 ("min_cluster", C.c_uint32), ("n_hyp", C.c_uint32), ("eps", C.c_float), ("seed", C.c_uint64),
-                ("classify", C.c_uint32)]
+                ("classify", C.c_uint32), ("planes_per_cluster", C.c_uint32)]
 
 
 def lib():
@@ -130,19 +130,19 @@ def _u32p(a):
 
 
 def make_params(n_th=3, theta_step_deg=15.0, d_th=0.05, theta_ccl_deg=15.0, min_cluster=50, n_hyp=100,
-                eps=0.01, seed=0, classify=1) -> Params:
+                eps=0.01, seed=0, classify=1, planes_per_cluster=1) -> Params:
     """Segmentation parameters (paper defaults: N_th=3, theta_th=15 deg, d_th=0.05 m,
     I=100, eps=0.01 m).  Cosines and d_th^2 are formed in double, then rounded to FP32."""
     import math
     return Params(n_th, np.float32(math.cos(math.radians(theta_step_deg))), np.float32(d_th * d_th),
                   np.float32(math.cos(math.radians(theta_ccl_deg))), min_cluster, n_hyp, np.float32(eps), seed,
-                  classify)
+                  classify, planes_per_cluster)
 
 
 def _planes_to_dict(planes, n):
     out = {k: [] for k in ("label", "n_points", "inlier_count", "best_h", "ill_conditioned", "ransac_n",
                            "ransac_d", "refit_n", "refit_d", "basis_u", "basis_v", "origin", "hull_off",
-                           "hull_n", "point_off")}
+                           "hull_n", "point_off", "round")}
     for i in range(n):
         p = planes[i]
         for k in out:
@@ -151,7 +151,7 @@ def _planes_to_dict(planes, n):
     dt = {"label": np.uint32, "n_points": np.uint32, "inlier_count": np.uint32, "best_h": np.int32,
           "ill_conditioned": np.int32, "ransac_n": np.float32, "ransac_d": np.float32, "refit_n": np.float64,
           "refit_d": np.float64, "basis_u": np.float32, "basis_v": np.float32, "origin": np.float32,
-          "hull_off": np.uint32, "hull_n": np.uint32, "point_off": np.uint32}
+          "hull_off": np.uint32, "hull_n": np.uint32, "point_off": np.uint32, "round": np.uint32}
     res = {}
     for k, v in out.items():
         a = np.array(v, dtype=dt[k])

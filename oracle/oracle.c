@@ -108,6 +108,7 @@ typedef struct {
     uint32_t hull_off;
     uint32_t hull_n;
     uint32_t point_off;      /* offset of this cluster in the point arrays    */
+    uint32_t round;          /* extraction round of this plane in its cluster */
 } orc_plane;
 
 typedef struct {
@@ -134,6 +135,7 @@ typedef struct {
     float eps;           /* RANSAC inlier threshold epsilon             */
     uint64_t seed;
     uint32_t classify;   /* 1: cluster steppable voxels only (paper); 0: all occupied */
+    uint32_t planes_per_cluster; /* extraction rounds per cluster; 0 or 1: one plane (paper) */
 } orc_params;
 
 /* Planes / hulls / per-point results of the last fit, owned by a result set. */
@@ -533,10 +535,10 @@ void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4
  * Philox4x64-10 with counter (label, h, 0, 0) and key (seed, 0); index
  * k = floor(r * n / 2^64).  Returns 0 for a degenerate sample (repeated index
  * or zero cross product). */
-static int ransac_hypothesis(const float *pts, uint32_t n, uint32_t label, uint32_t h, uint64_t seed,
-                             float nrm[3], float *dd)
+static int ransac_hypothesis(const float *pts, uint32_t n, uint32_t label, uint32_t h, uint32_t round,
+                             uint64_t seed, float nrm[3], float *dd)
 {
-    uint64_t ctr[4] = {label, h, 0, 0}, key[2] = {seed, 0}, r[4];
+    uint64_t ctr[4] = {label, h, round, 0}, key[2] = {seed, 0}, r[4];
     orc_philox4x64(ctr, key, r);
     uint64_t k[3], lo;
     for (int i = 0; i < 3; ++i) mulhilo64(r[i], (uint64_t)n, &k[i], &lo);
@@ -573,7 +575,7 @@ int32_t orc_ransac_counts(const float *pts, uint32_t n, uint32_t label, uint32_t
         float nrm[3], d;
         counts[h] = -1;
         planes4[4 * h] = planes4[4 * h + 1] = planes4[4 * h + 2] = planes4[4 * h + 3] = 0.0f;
-        if (!ransac_hypothesis(pts, n, label, h, seed, nrm, &d)) continue;
+        if (!ransac_hypothesis(pts, n, label, h, 0, seed, nrm, &d)) continue;
         int64_t cnt = 0;
         for (uint32_t k = 0; k < n; ++k) cnt += (plane_dist(nrm, d, pts + 3 * k) <= eps);
         counts[h] = cnt;
@@ -643,20 +645,21 @@ static int push_hull(orc_result *r, const int32_t *h, uint32_t k)
 /* One cluster: RANSAC (Sec. III.C stages a-c), refit, boundary polygon
  * (Sec. III.C, boundary polygon generation).  pts are the cluster's points in
  * cluster order; inl receives the inlier flags. */
-static int fit_cluster(const float *pts, uint32_t n, uint32_t label, const orc_params *prm, orc_plane *pl,
-                       uint8_t *inl, orc_result *res)
+static int fit_cluster(const float *pts, uint32_t n, uint32_t label, uint32_t round, const orc_params *prm,
+                       orc_plane *pl, uint8_t *inl, orc_result *res)
 {
     memset(pl, 0, sizeof(*pl));
     pl->label = label;
     pl->n_points = n;
     pl->best_h = -1;
+    pl->round = round;
     memset(inl, 0, n);
     /* a) hypotheses, b) inlier counting, c) selection: max count, lowest h on ties */
     int64_t best = -1;
     float bn[3] = {0, 0, 0}, bd = 0.0f;
     for (uint32_t h = 0; h < prm->n_hyp; ++h) {
         float nrm[3], d;
-        if (!ransac_hypothesis(pts, n, label, h, prm->seed, nrm, &d)) continue;
+        if (!ransac_hypothesis(pts, n, label, h, round, prm->seed, nrm, &d)) continue;
         int64_t cnt = 0;
         for (uint32_t k = 0; k < n; ++k) cnt += (plane_dist(nrm, d, pts + 3 * k) <= prm->eps);
         if (cnt > best) { best = cnt; pl->best_h = (int32_t)h; bn[0] = nrm[0]; bn[1] = nrm[1]; bn[2] = nrm[2]; bd = d; }
@@ -740,11 +743,19 @@ static int fit_cluster(const float *pts, uint32_t n, uint32_t label, const orc_p
 }
 
 /* The fit of clusters c = 0..k-1 (points pts + 3 off[c], n = off[c+1] -
- * off[c], Philox label lab[c]) into r->planes[0..k) with their hulls appended
- * to r in cluster order.  With several threads each range of clusters keeps
- * its hulls apart and they are appended in cluster order afterwards. */
+ * off[c], Philox label lab[c]) into r->planes, in cluster order and, within a
+ * cluster, in extraction round order, with their hulls appended to r in the
+ * same order.  Round 0 is the paper's single plane (always recorded).  With
+ * planes_per_cluster P > 1, round q + 1 runs on the points of round q that
+ * are not its inliers (in their order) when round q found a plane with at
+ * least min_cluster inliers and at least min_cluster points remain; its
+ * Philox counter is (label, h, q + 1, 0); it is recorded when it finds a
+ * plane.  With several threads each range of clusters keeps its planes and
+ * hulls apart and they are appended in order afterwards. */
 typedef struct {
-    orc_result *r; const uint32_t *off; const uint32_t *lab; const orc_params *prm;
+    orc_result *r; const uint32_t *off; const uint32_t *lab; const orc_params *prm; uint32_t P;
+    orc_plane *slots;  /* [k][P] */
+    uint32_t *n_rec;   /* [k] records per cluster */
     int nt; orc_result part[256]; int st[256]; uint64_t lo[256];
 } fit_ctx;
 static void fit_range(void *vc, uint64_t lo, uint64_t hi)
@@ -753,35 +764,82 @@ static void fit_range(void *vc, uint64_t lo, uint64_t hi)
     int t = 0;  /* this range's index: par_for splits [0, k) exactly as fit_all does */
     while (t + 1 < cx->nt && cx->lo[t] != lo) ++t;
     orc_result *hr = g_threads > 1 ? &cx->part[t] : cx->r;
+    const uint32_t minc = cx->prm->min_cluster;
     for (uint64_t c = lo; c < hi && cx->st[t] == ORC_OK; ++c) {
-        orc_plane *pl = &cx->r->planes[c];
-        const uint32_t o = cx->off[c];
-        cx->st[t] = fit_cluster(cx->r->pts + 3 * (size_t)o, cx->off[c + 1] - o, cx->lab ? cx->lab[c] : (uint32_t)c,
-                                cx->prm, pl, cx->r->inlier + o, hr);
+        const uint32_t o = cx->off[c], n = cx->off[c + 1] - o;
+        const uint32_t label = cx->lab ? cx->lab[c] : (uint32_t)c;
+        orc_plane *pl = &cx->slots[c * cx->P];
+        cx->st[t] = fit_cluster(cx->r->pts + 3 * (size_t)o, n, label, 0, cx->prm, pl, cx->r->inlier + o, hr);
         pl->point_off = o;
+        cx->n_rec[c] = 1;
+        if (cx->P <= 1 || cx->st[t] != ORC_OK) continue;
+        /* further rounds on the points that are not inliers of the previous round */
+        float *cur = (float *)malloc(((size_t)n + 1) * 3 * sizeof(float));
+        float *nxt = (float *)malloc(((size_t)n + 1) * 3 * sizeof(float));
+        uint8_t *inl = (uint8_t *)malloc((size_t)n + 1);
+        if (!cur || !nxt || !inl) { free(cur); free(nxt); free(inl); cx->st[t] = ORC_ERR_OUT_OF_MEMORY; break; }
+        memcpy(cur, cx->r->pts + 3 * (size_t)o, (size_t)n * 3 * sizeof(float));
+        memcpy(inl, cx->r->inlier + o, n);
+        uint32_t cn = n;
+        orc_plane *prev = pl;
+        for (uint32_t q = 1; q < cx->P; ++q) {
+            if (prev->best_h < 0 || prev->inlier_count < minc) break;
+            uint32_t m = 0;
+            for (uint32_t i = 0; i < cn; ++i)
+                if (!inl[i]) {
+                    nxt[3 * m] = cur[3 * i]; nxt[3 * m + 1] = cur[3 * i + 1]; nxt[3 * m + 2] = cur[3 * i + 2];
+                    ++m;
+                }
+            if (m < minc || m == 0) break;
+            orc_plane *pq = &cx->slots[c * cx->P + q];
+            cx->st[t] = fit_cluster(nxt, m, label, q, cx->prm, pq, inl, hr);
+            if (cx->st[t] != ORC_OK) break;
+            if (pq->best_h < 0) break;
+            pq->point_off = o;
+            cx->n_rec[c] = q + 1;
+            float *sw = cur; cur = nxt; nxt = sw;
+            cn = m;
+            prev = pq;
+        }
+        free(cur); free(nxt); free(inl);
     }
 }
 static int fit_all(orc_result *r, const uint32_t *off, const uint32_t *lab, uint32_t k, const orc_params *prm)
 {
     fit_ctx *cx = (fit_ctx *)calloc(1, sizeof(fit_ctx));
     if (!cx) return ORC_ERR_OUT_OF_MEMORY;
-    cx->r = r; cx->off = off; cx->lab = lab; cx->prm = prm;
+    const uint32_t P = prm->planes_per_cluster > 1 ? prm->planes_per_cluster : 1;
+    cx->r = r; cx->off = off; cx->lab = lab; cx->prm = prm; cx->P = P;
+    cx->slots = (orc_plane *)calloc((size_t)(k ? k : 1) * P, sizeof(orc_plane));
+    cx->n_rec = (uint32_t *)calloc(k ? k : 1, sizeof(uint32_t));
+    if (!cx->slots || !cx->n_rec) { free(cx->slots); free(cx->n_rec); free(cx); return ORC_ERR_OUT_OF_MEMORY; }
     int t = g_threads < (int)(k ? k : 1) ? g_threads : (int)(k ? k : 1);
     cx->nt = t;
     for (int i = 0; i < t; ++i) cx->lo[i] = (uint64_t)k * (uint64_t)i / (uint64_t)t;
     par_for(k, fit_range, cx);
     int st = ORC_OK;
     for (int i = 0; i < 256; ++i) if (cx->st[i] != ORC_OK) st = cx->st[i];
-    if (g_threads > 1 && st == ORC_OK) {  /* hulls in cluster order: shift each range's offsets */
+    if (g_threads > 1 && st == ORC_OK) {  /* hulls in order: shift each range's offsets */
         for (int i = 0; i < t && st == ORC_OK; ++i) {
             const uint64_t end = i + 1 < t ? cx->lo[i + 1] : k;
-            for (uint64_t c = cx->lo[i]; c < end; ++c) r->planes[c].hull_off += r->n_hull;
+            for (uint64_t c = cx->lo[i]; c < end; ++c)
+                for (uint32_t q = 0; q < cx->n_rec[c]; ++q) cx->slots[c * P + q].hull_off += r->n_hull;
             st = push_hull(r, cx->part[i].hull_xy, cx->part[i].n_hull);
         }
     }
+    uint32_t np = 0;
+    for (uint32_t c = 0; c < k; ++c) np += cx->n_rec[c];
+    if (np > k) {
+        orc_plane *grown = (orc_plane *)realloc(r->planes, (size_t)np * sizeof(orc_plane));
+        if (!grown) st = ORC_ERR_OUT_OF_MEMORY; else r->planes = grown;
+    }
+    uint32_t j = 0;
+    if (st == ORC_OK)
+        for (uint32_t c = 0; c < k; ++c)
+            for (uint32_t q = 0; q < cx->n_rec[c]; ++q) r->planes[j++] = cx->slots[c * P + q];
     for (int i = 0; i < 256; ++i) free(cx->part[i].hull_xy);
-    free(cx);
-    r->n_planes = k;
+    free(cx->slots); free(cx->n_rec); free(cx);
+    r->n_planes = j;
     return st;
 }
 
