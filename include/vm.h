@@ -67,10 +67,15 @@ typedef struct {
     float eps;                 /* RANSAC inlier threshold: |n.p + d| <= eps               */
     uint64_t seed;             /* Philox4x64-10 key word 0                                */
     uint32_t classify;         /* 1: cluster steppable voxels only (paper); 0: all occupied */
-    uint32_t reserved;
+    uint32_t planes_per_cluster; /* extraction rounds per cluster, 0 or 1: one plane (paper); up to 8.
+                                  Round q + 1 fits the points of round q that are not its inliers
+                                  (in order), Philox counter (label, h, q + 1, 0), when round q found
+                                  a plane with >= min_cluster inliers and >= min_cluster points
+                                  remain; it is output when it finds a plane.  vm_segment only.  */
 } vm_segment_params;
 
-/* One output plane: one per cluster, clusters in ascending label order. */
+/* One output plane: one per cluster (per extraction round when
+ * planes_per_cluster > 1), in ascending label order, then round order. */
 typedef struct {
     float normal[3];           /* refit normal (total least squares on the inliers), n_z >= 0 */
     float offset;              /* refit plane: normal . x + offset = 0                       */
@@ -85,7 +90,8 @@ typedef struct {
     uint32_t hull_count;       /* vertices, counter-clockwise from the lexicographic minimum */
     uint32_t n_points;         /* points in the cluster                                      */
     int32_t best_h;            /* selected hypothesis index; -1: no valid hypothesis, no plane */
-    uint32_t flags;            /* bit 0: refit ill-conditioned (lambda_mid < 10 lambda_min)  */
+    uint32_t flags;            /* bit 0: refit ill-conditioned (lambda_mid < 10 lambda_min);
+                                  bits 8-15: extraction round of the plane in its cluster     */
 } vm_plane;
 
 /* Result of vm_segment / vm_fit_planes; host memory owned by the library
@@ -409,8 +415,9 @@ vm_status vm_server_destroy(vm_server* srv);
 /* Diagnostics (no counterpart in the paper).  Stage timing records CUDA
  * events around each pipeline stage on the stream it runs on: integrate,
  * order_bricks, finalize, moments, eigen, ccl_local, ccl_cross, clusters,
- * ransac_hyp, ransac_score, extract, refit_hull, pack, clear (vm_stage_name
- * gives the names).
+ * ransac_hyp, ransac_score, extract, refit_hull, pack, clear, rounds
+ * (vm_stage_name gives the names; the RANSAC stages of every extraction round
+ * add up under their own names, the work between rounds under rounds).
  * vm_stage_timing: enable (1) or disable (0) for a map, or for this thread's
  * vm_fit_planes calls when map is NULL.  vm_stage_times: device milliseconds
  * and call counts per stage accumulated since the previous call (then reset);

@@ -28,7 +28,7 @@ void uncount_launch(unsigned long long n) { g_launches.fetch_sub(n); }
 
 static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "finalize", "moments", "eigen",
                                               "ccl_local", "ccl_cross", "clusters", "ransac_hyp", "ransac_score",
-                                              "extract", "refit_hull", "pack", "clear"};
+                                              "extract", "refit_hull", "pack", "clear", "rounds"};
 
 
 void set_error(const std::string& msg) { g_err = msg; }
@@ -149,6 +149,19 @@ vm_status check_params(const vm_segment_params* p) {
     }
     if (!(p->eps >= 0.0f) || !(p->d_th2 >= 0.0f)) {
         set_error("eps and d_th2 must be non-negative");
+        return VM_ERR_INVALID_ARG;
+    }
+    if (p->planes_per_cluster > kMaxRounds) {
+        set_error("planes_per_cluster must be at most 8");
+        return VM_ERR_INVALID_ARG;
+    }
+    return VM_OK;
+}
+
+vm_status check_single_round(const vm_segment_params* p) {
+    VM_TRY(check_params(p));
+    if (p->planes_per_cluster > 1) {
+        set_error("planes_per_cluster > 1 is supported by vm_segment only");
         return VM_ERR_INVALID_ARG;
     }
     return VM_OK;
@@ -320,6 +333,17 @@ vm_status ensure_out(vm_map* m, uint32_t kcap, uint32_t hcap) {
     return VM_OK;
 }
 
+// Scratch of the further extraction rounds: remaining points of nv voxels,
+// kcap clusters, hcap staged hull vertices (the result block's hull capacity).
+static vm_status ensure_rounds(vm_map* m, size_t nv, size_t kcap, size_t hcap) {
+    RoundBuffers& rb = m->rounds;
+    if (m->round_mem.p && rb.nv >= nv && rb.kcap >= kcap && rb.hcap >= hcap) return VM_OK;
+    VM_TRY(ensure(m->round_mem, rounds_bytes(nv, kcap, hcap)));
+    rounds_layout(static_cast<char*>(m->round_mem.p), rb, nv, kcap, hcap);
+    m->gen++;
+    return VM_OK;
+}
+
 // Sizes the scratch from the last known counts with headroom; a launch whose
 // counts still do not fit raises kErrScratch and the caller retries.
 vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit) {
@@ -352,14 +376,27 @@ vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit) {
     uint32_t hcap = m->hull_hint + m->hull_hint / 2 + 4096;
     if (hcap < 65536) hcap = 65536;
     if (hcap < m->out_hcap) hcap = m->out_hcap;
-    return ensure_out(m, (uint32_t)kcap, hcap);
+    const uint32_t P = p.planes_per_cluster > 1 ? p.planes_per_cluster : 1;
+    size_t rcap = kcap;  // output records: one per cluster, more with several rounds
+    if (P > 1) {
+        const size_t rh = (size_t)m->rec_hint + m->rec_hint / 4 + 64;
+        if (rcap < rh) rcap = rh;
+        if (rcap > kcap * P) rcap = kcap * P;
+    }
+    VM_TRY(ensure_out(m, (uint32_t)rcap, hcap));
+    if (with_fit && P > 1) VM_TRY(ensure_rounds(m, nv, kcap, m->out_hcap));
+    return VM_OK;
 }
 
+// The result header; rounds (null for one plane per cluster): the record and
+// hull-vertex totals of the extraction rounds.
 __global__ void k_header(const SegCounters* __restrict__ ctr, const uint32_t* __restrict__ hull_off,
-                         const uint32_t* __restrict__ fit_err, const MapCounters* __restrict__ mc,
-                         const uint32_t* __restrict__ seg_err, SegCounters* __restrict__ out) {
+                         const uint32_t* __restrict__ rounds, const uint32_t* __restrict__ fit_err,
+                         const MapCounters* __restrict__ mc, const uint32_t* __restrict__ seg_err,
+                         SegCounters* __restrict__ out) {
     SegCounters h = *ctr;
-    h.n_hull = hull_off[h.k];
+    h.n_hull = rounds ? rounds[kWordHullTot] : hull_off[h.k];
+    h.n_planes = rounds ? rounds[kWordRec] : h.k;
     h.fit_err = *fit_err;
     h.n_bricks = mc->n_bricks;
     h.map_err = mc->err;
@@ -390,15 +427,26 @@ cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk
     cudaError_t e;
     if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     if ((e = enqueue_front(m, p, hk)) != cudaSuccess) return e;
-    if ((e = launch_fit(b.pts, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, p, fb, m->tune, sms, s, hk)) != cudaSuccess)
-        return e;
     char* d = m->out_dev;
-    VM_STAGE_BEGIN(hk, kStPack, s);
-    e = launch_pack(fb, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, reinterpret_cast<vm_plane*>(d + out_planes_off()),
-                    reinterpret_cast<int32_t*>(d + out_xy_off(m->out_kcap)),
-                    reinterpret_cast<float*>(d + out_xyz_off(m->out_kcap, m->out_hcap)), m->out_hcap, s);
-    if (e != cudaSuccess) return e;
-    k_header<<<1, 1, 0, s>>>(b.ctr, fb.hull_cnt, fb.err, m->ctr, m->err, reinterpret_cast<SegCounters*>(d));
+    vm_plane* planes = reinterpret_cast<vm_plane*>(d + out_planes_off());
+    int32_t* hull_xy = reinterpret_cast<int32_t*>(d + out_xy_off(m->out_kcap));
+    float* hull_xyz = reinterpret_cast<float*>(d + out_xyz_off(m->out_kcap, m->out_hcap));
+    const uint32_t* rounds = nullptr;
+    if (p.planes_per_cluster > 1) {
+        e = launch_rounds(b, m->kcap, p, fb, m->rounds, m->tune, sms, b.scan_tmp, planes, m->out_kcap, hull_xy,
+                          hull_xyz, m->out_hcap, s, hk);
+        if (e != cudaSuccess) return e;
+        rounds = m->rounds.word;
+        VM_STAGE_BEGIN(hk, kStPack, s);
+    } else {
+        if ((e = launch_fit(b.pts, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, p, fb, m->tune, sms, s, hk)) !=
+            cudaSuccess)
+            return e;
+        VM_STAGE_BEGIN(hk, kStPack, s);
+        e = launch_pack(fb, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, planes, hull_xy, hull_xyz, m->out_hcap, s);
+        if (e != cudaSuccess) return e;
+    }
+    k_header<<<1, 1, 0, s>>>(b.ctr, fb.hull_cnt, rounds, fb.err, m->ctr, m->err, reinterpret_cast<SegCounters*>(d));
     count_launch(1);
     VM_STAGE_END(hk, kStPack, s);
     return cudaGetLastError();
@@ -451,6 +499,7 @@ vm_status launch_segment(vm_map* m, const vm_segment_params& p) {
         m->brick_hint = c.n_bricks < m->capacity ? c.n_bricks : m->capacity;
     }
     VM_TRY(plan_capacity(m, p, true));
+    m->seg_rounds = p.planes_per_cluster > 1 ? p.planes_per_cluster : 1;
     StageHook* hk = m->fit.timer.hook();
     if (m->use_graph && !hk && (!m->gexec || m->ggen != m->gen || memcmp(&m->gprm, &p, sizeof(p)) != 0)) {
         if (capture_segment(m, p) != VM_OK) {  // e.g. a stream that cannot be captured: launch eagerly
@@ -528,7 +577,8 @@ bool take_hints(vm_map* m) {
     m->brick_hint = hdr->n_bricks < m->capacity ? hdr->n_bricks : m->capacity;
     m->k_hint = hdr->k;
     m->hull_hint = hdr->n_hull;
-    return (hdr->err & kErrScratch) || hdr->n_hull > m->out_hcap;
+    m->rec_hint = hdr->n_planes;
+    return (hdr->err & kErrScratch) || hdr->n_hull > m->out_hcap || hdr->n_planes > m->out_kcap;
 }
 
 vm_status finish_segment(vm_map* m, const vm_segment_params& p, vm_planes* out) {
@@ -549,7 +599,7 @@ vm_status read_result(vm_map* m, vm_planes* out) {
     const SegCounters* hdr = static_cast<const SegCounters*>(m->out_host);
     m->last = *hdr;
     m->segmented = true;
-    const uint32_t K = hdr->k, n_hull = hdr->n_hull;
+    const uint32_t K = hdr->n_planes, n_hull = hdr->n_hull;
     const size_t b_planes = (size_t)K * sizeof(vm_plane);
     out->planes = static_cast<vm_plane*>(malloc(b_planes ? b_planes : 1));
     out->hull_xy = static_cast<int32_t*>(malloc(n_hull ? (size_t)n_hull * 8 : 1));
@@ -711,6 +761,7 @@ vm_status vm_destroy(vm_map* m) {
     release(m->stage);
     release(m->brick_mem);
     release(m->vox_mem);
+    release(m->round_mem);
     fit_release(m->fit);
     if (m->gexec) cudaGraphExecDestroy(m->gexec);
     if (m->fexec) cudaGraphExecDestroy(m->fexec);
@@ -1021,8 +1072,9 @@ vm_status vm_export_clusters(vm_map* m, float* pts, uint32_t* vid, uint8_t* inli
     if (w) {
         if (pts) VM_CUDA(cudaMemcpyAsync(pts, m->seg.pts, (size_t)w * 3 * sizeof(float), cudaMemcpyDeviceToHost, s));
         if (vid) VM_CUDA(cudaMemcpyAsync(vid, m->seg.pt_vid, (size_t)w * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-        if (inlier && m->last.k)
-            VM_CUDA(cudaMemcpyAsync(inlier, m->fit.fb.inlier, (size_t)w, cudaMemcpyDeviceToHost, s));
+        if (inlier && m->last.k)  // the first round's inliers (the paper's plane) when there were several
+            VM_CUDA(cudaMemcpyAsync(inlier, m->seg_rounds > 1 ? m->rounds.inl0 : m->fit.fb.inlier, (size_t)w,
+                                    cudaMemcpyDeviceToHost, s));
     }
     VM_CUDA(cudaStreamSynchronize(s));
     *n = np;
@@ -1058,7 +1110,7 @@ uint64_t vm_launch_count(void) { return g_launches.load(); }
 
 vm_status vm_fit_planes(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
                         const vm_segment_params* params, void* stream, vm_planes* out) {
-    VM_TRY(check_params(params));
+    VM_TRY(check_single_round(params));
     if (!out || (k && (!xyz || !off))) {
         set_error("null argument");
         return VM_ERR_INVALID_ARG;

@@ -74,14 +74,15 @@ __device__ __forceinline__ uint32_t find_cluster(const uint32_t* __restrict__ it
 // ---------------------------------------------------------------- stage a
 __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                       const uint32_t* __restrict__ labels, const uint32_t* __restrict__ kp, int H, unsigned long long seed,
-                      float4* __restrict__ hyp, uint8_t* __restrict__ valid, uint32_t* __restrict__ counts) {
+                      uint32_t round, float4* __restrict__ hyp, uint8_t* __restrict__ valid,
+                      uint32_t* __restrict__ counts) {
     const uint32_t k = *kp;
     const size_t total = (size_t)k * H;
     for (size_t t = (size_t)blockIdx.x * kT + threadIdx.x; t < total; t += (size_t)gridDim.x * kT) {
         const uint32_t c = (uint32_t)(t / H), h = (uint32_t)(t % H);
         const uint32_t base = off[c], n = off[c + 1] - base;
         const uint32_t label = labels ? labels[c] : c;
-        const unsigned long long ctr[4] = {label, h, 0ull, 0ull}, key[2] = {seed, 0ull};
+        const unsigned long long ctr[4] = {label, h, round, 0ull}, key[2] = {seed, 0ull};
         unsigned long long r[4];
         philox4x64_10(ctr, key, r);
         const uint32_t i0 = (uint32_t)__umul64hi(r[0], n), i1 = (uint32_t)__umul64hi(r[1], n),
@@ -1092,7 +1093,7 @@ cudaError_t fit_set_count(uint32_t* kdev, uint32_t k, cudaStream_t s) {
 
 cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
                        uint32_t kcap, const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int sms,
-                       cudaStream_t s, StageHook* hk) {
+                       cudaStream_t s, StageHook* hk, uint32_t round) {
     if (kcap == 0) return cudaSuccess;
     fit_init_attributes();
     const int H = (int)p.n_hyp;
@@ -1107,7 +1108,7 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     if ((e = cudaMemsetAsync(fb.queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
     const size_t kh = (size_t)kcap * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    k_hyp<<<hgrid, kT, 0, s>>>(pts, off, labels, kp, H, p.seed, fb.hyp, fb.hyp_valid, fb.counts);
+    k_hyp<<<hgrid, kT, 0, s>>>(pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid, fb.counts);
     VM_STAGE_END(hk, kStHyp, s);
     count_launch(3);
     const int grid = sms * t.ctas_per_sm;
@@ -1234,8 +1235,8 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
         set_error("vm_ransac_static: null argument");
         return VM_ERR_INVALID_ARG;
     }
-    if (params->n_hyp < 1 || params->n_hyp > 1024 || !(params->eps >= 0.0f)) {
-        set_error("vm_ransac_static: n_hyp must be in [1, 1024] and eps >= 0");
+    if (params->n_hyp < 1 || params->n_hyp > 1024 || !(params->eps >= 0.0f) || params->planes_per_cluster > 1) {
+        set_error("vm_ransac_static: n_hyp must be in [1, 1024], eps >= 0 and planes_per_cluster <= 1");
         return VM_ERR_INVALID_ARG;
     }
     if (k == 0) return VM_OK;
@@ -1289,7 +1290,7 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     k_set_end<<<1, 1, 0, s>>>(item_off, kdev, total);
     const size_t kh = (size_t)k * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    k_hyp<<<hgrid, kT, 0, s>>>(xyz, off, labels, kdev, H, params->seed, hyp, valid, counts);
+    k_hyp<<<hgrid, kT, 0, s>>>(xyz, off, labels, kdev, H, params->seed, 0u, hyp, valid, counts);
     int R = t.hyp_per_thread;
     while (R < 8 && (H + R - 1) / R > kT) R <<= 1;
     const int grid = sms * t.ctas_per_sm;

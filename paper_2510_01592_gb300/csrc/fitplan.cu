@@ -295,7 +295,7 @@ extern "C" {
 
 vm_status vm_fit_plan_create(uint32_t k_cap, uint32_t n_cap, const vm_segment_params* params, void* stream,
                              uint32_t flags, vm_fit_plan** out) {
-    VM_TRY(check_params(params));
+    VM_TRY(check_single_round(params));
     if (!out) {
         set_error("null output");
         return VM_ERR_INVALID_ARG;

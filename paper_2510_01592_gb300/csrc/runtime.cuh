@@ -100,6 +100,9 @@ vm_status fit_prepare(FitContext& fc, size_t kcap, size_t npts, int H, int tile,
 void fit_release(FitContext& fc);
 int device_sms();
 vm_status check_params(const vm_segment_params* p);
+// check_params, and one plane per cluster (the batched fits and vm_fit_planes
+// run a single extraction round).
+vm_status check_single_round(const vm_segment_params* p);
 // Launch bookkeeping around graph capture: launches recorded while capturing
 // are taken back and counted again at each replay.
 unsigned long long launch_total();
@@ -146,6 +149,11 @@ struct vm_map {
     vmx::FitContext fit;
     vmx::FitTuning tune = vmx::default_tuning();
     bool segmented = false;
+    // further extraction rounds (planes_per_cluster > 1)
+    vmx::DevBuf round_mem;
+    vmx::RoundBuffers rounds{};
+    uint32_t seg_rounds = 1;      // rounds of the last segmentation launched
+    uint32_t rec_hint = 0;        // output records of the last segmentation
     // results: mapped pinned host memory written by the kernels
     void* out_host = nullptr;
     char* out_dev = nullptr;

@@ -153,6 +153,7 @@ __global__ void k_batch_header(const BatchTable* __restrict__ t, const uint32_t*
         const BatchEntry& E = t->e[m];
         SegCounters h = *E.ctr;
         h.n_hull = t->err ? 0u : hull_off[E.base_k + E.k] - hull_off[E.base_k];
+        h.n_planes = t->err ? 0u : h.k;
         h.fit_err = *fit_err;
         h.n_bricks = E.mc->n_bricks;
         h.map_err = E.mc->err;
@@ -696,7 +697,7 @@ vm_status vm_server_create(const vm_server_params* params, vm_server** out) {
         return VM_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    VM_TRY(check_params(&params->params));
+    VM_TRY(check_single_round(&params->params));
     if (params->max_batch < 1 || params->max_batch > (uint32_t)kMaxBatch || params->max_inflight < 1 ||
         params->max_inflight > (uint32_t)kMaxSlots || params->mode > VM_SERVE_STREAMS) {
         set_error("max_batch must be 1..64, max_inflight 1..4, mode VM_SERVE_BATCHED or VM_SERVE_STREAMS");

@@ -66,7 +66,8 @@ struct SegCounters {
     uint32_t map_err;    // map error bits (copied at the end)
     uint32_t fit_err;    // fit error bits (copied at the end)
     uint32_t n_list;     // occupied voxels listed for the eigen-solve
-    uint32_t pad[4];
+    uint32_t n_planes;   // output plane records (k, or more with several extraction rounds)
+    uint32_t pad[3];
 };
 
 // Per-cluster fit state on the device.
@@ -87,48 +88,57 @@ struct FitCluster {
     unsigned long long ext[16]; // filter extremes: (biased value << 32) | point index
 };
 
+// One cluster's output record: the refit plane, the selected hypothesis, the
+// hull basis and origin; ho / hn: its first hull vertex and vertex count.
+__device__ __forceinline__ vm_plane make_plane(const FitCluster& f, uint32_t label, uint32_t n_points, uint32_t ho,
+                                               uint32_t hn) {
+    vm_plane p;
+    for (int a = 0; a < 3; ++a) {
+        p.normal[a] = f.refit_n[a];
+        p.ransac_normal[a] = f.n[a];
+        p.basis_u[a] = f.u[a];
+        p.basis_v[a] = f.v[a];
+        p.hull_origin[a] = f.o[a];
+    }
+    p.offset = f.refit_d;
+    p.ransac_offset = f.d;
+    p.inlier_count = f.inliers;
+    p.label = label;
+    p.hull_offset = ho;
+    p.hull_count = hn;
+    p.n_points = n_points;
+    p.best_h = f.best_h;
+    p.flags = f.flags;
+    return p;
+}
+
+// Writes hull vertex q (2^-16 m units in p's basis) at index at of the output
+// arrays: the quantised pair and the point lifted onto p's refit plane.
+__device__ __forceinline__ void write_vertex(const vm_plane& p, int2 q, uint32_t at, int32_t* __restrict__ hull_xy,
+                                             float* __restrict__ hull_xyz) {
+    hull_xy[2 * at] = q.x;
+    hull_xy[2 * at + 1] = q.y;
+    const float a = q.x * (1.0f / 65536.0f), b = q.y * (1.0f / 65536.0f);
+    const float x = p.hull_origin[0] + a * p.basis_u[0] + b * p.basis_v[0];
+    const float y = p.hull_origin[1] + a * p.basis_u[1] + b * p.basis_v[1];
+    const float z = p.hull_origin[2] + a * p.basis_u[2] + b * p.basis_v[2];
+    const float e = p.normal[0] * x + p.normal[1] * y + p.normal[2] * z + p.offset;
+    hull_xyz[3 * at] = x - e * p.normal[0];
+    hull_xyz[3 * at + 1] = y - e * p.normal[1];
+    hull_xyz[3 * at + 2] = z - e * p.normal[2];
+}
+
 // Writes one cluster's output record and its hull vertices (called by a whole
-// block; thread 0 writes the record): the quantised hull (2^-16 m units) and
-// its points lifted onto the refit plane.  ho is the cluster's first vertex in
+// block; thread 0 writes the record).  ho is the cluster's first vertex in
 // the output arrays, hn its vertex count; vertices at or beyond hull_cap are
 // not written.
 __device__ __forceinline__ void pack_cluster(const FitCluster& f, uint32_t label, uint32_t n_points,
                                              const int2* __restrict__ hull_src, uint32_t ho, uint32_t hn,
                                              vm_plane* __restrict__ plane, int32_t* __restrict__ hull_xy,
                                              float* __restrict__ hull_xyz, uint32_t hull_cap) {
-    if (threadIdx.x == 0) {
-        vm_plane p;
-        for (int a = 0; a < 3; ++a) {
-            p.normal[a] = f.refit_n[a];
-            p.ransac_normal[a] = f.n[a];
-            p.basis_u[a] = f.u[a];
-            p.basis_v[a] = f.v[a];
-            p.hull_origin[a] = f.o[a];
-        }
-        p.offset = f.refit_d;
-        p.ransac_offset = f.d;
-        p.inlier_count = f.inliers;
-        p.label = label;
-        p.hull_offset = ho;
-        p.hull_count = hn;
-        p.n_points = n_points;
-        p.best_h = f.best_h;
-        p.flags = f.flags;
-        *plane = p;
-    }
-    for (uint32_t i = threadIdx.x; i < hn && ho + i < hull_cap; i += blockDim.x) {
-        const int2 q = hull_src[i];
-        hull_xy[2 * (ho + i)] = q.x;
-        hull_xy[2 * (ho + i) + 1] = q.y;
-        const float a = q.x * (1.0f / 65536.0f), b = q.y * (1.0f / 65536.0f);
-        const float x = f.o[0] + a * f.u[0] + b * f.v[0];
-        const float y = f.o[1] + a * f.u[1] + b * f.v[1];
-        const float z = f.o[2] + a * f.u[2] + b * f.v[2];
-        const float e = f.refit_n[0] * x + f.refit_n[1] * y + f.refit_n[2] * z + f.refit_d;
-        hull_xyz[3 * (ho + i)] = x - e * f.refit_n[0];
-        hull_xyz[3 * (ho + i) + 1] = y - e * f.refit_n[1];
-        hull_xyz[3 * (ho + i) + 2] = z - e * f.refit_n[2];
-    }
+    const vm_plane p = make_plane(f, label, n_points, ho, hn);
+    if (threadIdx.x == 0) *plane = p;
+    for (uint32_t i = threadIdx.x; i < hn && ho + i < hull_cap; i += blockDim.x) write_vertex(p, hull_src[i], ho + i, hull_xy, hull_xyz);
 }
 
 // ---------------------------------------------------------------- diagnostics
@@ -148,6 +158,7 @@ enum Stage {
     kStHull,           // refit + hull
     kStPack,           // output records
     kStClear,          // Eq. 2 ray-cast clearing (before the frame's integration)
+    kStRounds,         // further extraction rounds: staging, remaining points, final order
     kNumStages
 };
 
@@ -326,14 +337,60 @@ size_t fit_hull_smem();
 // in fb.hull at each cluster's point offset and their offsets in fb.hull_cnt.
 void fit_init_attributes();
 cudaError_t fit_set_count(uint32_t* kdev, uint32_t k, cudaStream_t s);
+// round: the extraction round (Philox counter word 2; 0 for the paper's
+// single plane per cluster).
 cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
                        uint32_t kcap, const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int num_sms,
-                       cudaStream_t s, StageHook* hk);
+                       cudaStream_t s, StageHook* hk, uint32_t round = 0);
 
 // Packs vm_plane records and hull arrays (at most hull_cap vertices) for the
 // *kp clusters; the destinations may be mapped host memory.
 cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
                         uint32_t kcap, vm_plane* planes, int32_t* hull_xy, float* hull_xyz, uint32_t hull_cap,
                         cudaStream_t s);
+
+// ---------------------------------------------------------------- rounds.cu
+// Sequential multi-plane extraction (planes_per_cluster P > 1): round r + 1
+// fits the points of round r that are not its inliers, for the clusters whose
+// round r found a plane with >= min_cluster inliers and that keep >=
+// min_cluster points.  Scratch for the remaining points of two rounds
+// (ping-pong), the records of every round staged per cluster, and their hull
+// vertices.
+constexpr uint32_t kMaxRounds = 8;
+struct RoundBuffers {
+    float* pts[2];          // [nv][3]   remaining points, in cluster order
+    uint32_t* off[2];       // [kcap + 1]
+    uint32_t* lab[2];       // [kcap]    Philox labels
+    uint32_t* orig[2];      // [kcap]    round-0 cluster index
+    uint32_t* keep;         // [nv]      1: the point goes on to the next round
+    uint32_t* kpos;         // [nv]      its position there (scan)
+    uint32_t* act;          // [kcap]    1: the cluster goes on to the next round
+    uint32_t* apos;         // [kcap]    its index there (scan)
+    uint32_t* cnt;          // [kcap]    records per round-0 cluster
+    uint32_t* cpos;         // [kcap]    first record (scan)
+    uint32_t* hcnt;         // [kcap]    hull vertices per round-0 cluster
+    uint32_t* hpos;         // [kcap]    first hull vertex (scan)
+    uint32_t* word;         // [64] counts: k per round, staged hull bases, totals
+    uint8_t* inl0;          // [nv]      round-0 inlier flags
+    vm_plane* slot;         // [kcap][kMaxRounds] staged records
+    int2* hull;             // [hcap]    staged hull vertices
+    size_t nv, kcap, hcap;
+};
+// Word indices in RoundBuffers::word.
+constexpr int kWordK = 0;                        // [kMaxRounds] clusters in round r (r >= 1)
+constexpr int kWordHull = 8;                     // [kMaxRounds + 1] staged hull base of round r
+constexpr int kWordNpts = 20, kWordKeep = 21;    // round points, kept points
+constexpr int kWordRec = 22, kWordHullTot = 23;  // output records, output hull vertices
+size_t rounds_bytes(size_t nv, size_t kcap, size_t hcap);
+void rounds_layout(char* base, RoundBuffers& rb, size_t nv, size_t kcap, size_t hcap);
+// Runs every round on the clusters of b (count b.ctr->k) and writes the
+// records in (cluster, round) order to planes (at most rec_cap) with their
+// hull vertices (at most hull_cap); the totals land in rb.word[kWordRec] and
+// rb.word[kWordHullTot].  scan_tmp: look-back state for scans of up to
+// rb.nv + 1 elements.
+cudaError_t launch_rounds(const SegBuffers& b, uint32_t kcap, const vm_segment_params& p, FitBuffers& fb,
+                          RoundBuffers& rb, const FitTuning& t, int sms, uint32_t* scan_tmp, vm_plane* planes,
+                          uint32_t rec_cap, int32_t* hull_xy, float* hull_xyz, uint32_t hull_cap, cudaStream_t s,
+                          StageHook* hk);
 
 }  // namespace vmx

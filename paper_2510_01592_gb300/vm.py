@@ -45,7 +45,7 @@ class vm_map_params(C.Structure):
 class vm_segment_params(C.Structure):
     _fields_ = [("n_th", C.c_uint32), ("cos_step", C.c_float), ("d_th2", C.c_float), ("cos_ccl", C.c_float),
                 ("min_cluster", C.c_uint32), ("n_hyp", C.c_uint32), ("eps", C.c_float), ("seed", C.c_uint64),
-                ("classify", C.c_uint32), ("reserved", C.c_uint32)]
+                ("classify", C.c_uint32), ("planes_per_cluster", C.c_uint32)]
 
 
 class vm_plane(C.Structure):
@@ -175,11 +175,11 @@ def _check(st):
 
 
 def segment_params(n_th=3, theta_step_deg=15.0, d_th=0.05, theta_ccl_deg=15.0, min_cluster=50, n_hyp=100, eps=0.01,
-                   seed=0, classify=1) -> vm_segment_params:
+                   seed=0, classify=1, planes_per_cluster=1) -> vm_segment_params:
     """Paper defaults (Sec. III.C, Sec. IV-A); cosines and d_th^2 in double, then FP32."""
     return vm_segment_params(n_th, np.float32(math.cos(math.radians(theta_step_deg))), np.float32(d_th * d_th),
                              np.float32(math.cos(math.radians(theta_ccl_deg))), min_cluster, n_hyp,
-                             np.float32(eps), seed, classify, 0)
+                             np.float32(eps), seed, classify, planes_per_cluster)
 
 
 def _planes_to_numpy(out: vm_planes):

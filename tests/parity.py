@@ -62,6 +62,8 @@ def compare_planes(gres, ores, gclusters=None, check_refit=True):
     assert_same(gp["label"], op["label"], "labels")
     assert_same(gp["n_points"], op["n_points"], "cluster sizes")
     assert_same(gp["best_h"], op["best_h"], "selected hypotheses")
+    if "round" in op:
+        assert_same((gp["flags"] >> 8) & 0xFF, op["round"].astype(np.uint32), "extraction rounds")
     if gclusters is not None:
         assert_same(gclusters["pts"], ores["pts"], "cluster points")
         if ores["pt_vid"] is not None:
