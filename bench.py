@@ -868,6 +868,40 @@ def run_gpu(args):
     clear_stage = mct.stage_times().get("clear", (0.0, 0))
     mct.close()
 
+    # ---------------- sequential multi-plane extraction: the same steps with up to 3 planes per cluster
+    def steps_pass(prm):
+        mm = fresh_map()
+        for i in range(args.warmup):
+            f = sched[i]
+            mm.integrate(pts[f], poses[f])
+            mm.segment(prm)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        planes, extra = [], []
+        a.record(stream)
+        for i in range(args.steps):
+            f = sched[args.warmup + i]
+            if f == 0 and (args.warmup + i):
+                mm.reset()
+            mm.integrate(pts[f], poses[f])
+            p = mm.segment(prm)["planes"]
+            planes.append(len(p))
+            extra.append(int((((p["flags"] >> 8) & 0xFF) > 0).sum()))
+        b.record(stream)
+        torch.cuda.synchronize()
+        mm.close()
+        return {"frames_per_s": round(args.steps / (a.elapsed_time(b) / 1e3), 2),
+                "planes_per_frame": round(float(np.mean(planes)), 2),
+                "later_round_planes_per_frame": round(float(np.mean(extra)), 2)}
+
+    multiplane = {"steppable_p3": steps_pass(vm.segment_params(n_hyp=100, seed=0, planes_per_cluster=3)),
+                  "all_occupied_p1": steps_pass(vm.segment_params(n_hyp=100, seed=0, classify=0)),
+                  "all_occupied_p3": steps_pass(vm.segment_params(n_hyp=100, seed=0, classify=0,
+                                                                  planes_per_cluster=3)),
+                  "note": "the same timed steps with up to 3 planes per cluster (round r + 1 on round r's "
+                          "non-inliers); steppable: the paper's clustering, all_occupied: every occupied voxel "
+                          "clustered, where clusters join walls and ledges; graph replay"}
+
     if ws > 1:
         t = torch.tensor([total_ms, e2e_s], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -896,6 +930,7 @@ def run_gpu(args):
                                   "voxels_cleared_per_frame": round(cleared / args.steps, 1),
                                   "note": "the same timed steps with ray-cast clearing (Eq. 2) of every frame's "
                                           "rays before its update; graph replay"},
+                     "multiplane": multiplane,
                      "graph_frames_per_s": round(value, 2),
                      "plain_eager_frames_per_s": round(args.steps / (eager_ms / 1e3), 2),
                      "note": "graph: each segment call replays one captured CUDA graph of the whole device-driven "

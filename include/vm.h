@@ -427,8 +427,14 @@ vm_status vm_stage_timing(vm_map* map, int enable);
 vm_status vm_stage_times(vm_map* map, double* ms, uint64_t* calls, uint32_t cap, uint32_t* n_stages);
 const char* vm_stage_name(uint32_t stage);
 
-/* Number of CUDA kernel launches the library has issued in this process. */
+/* Number of CUDA kernel launches the library has issued in this process
+ * (kernels of a replayed graph count at each replay, not at capture). */
 uint64_t vm_launch_count(void);
+/* Number of CUDA graphs the library has captured, and of device or pinned
+ * host allocations it has made, in this process (a map whose scratch grows
+ * re-allocates and re-captures; both should stay flat in a steady state). */
+uint64_t vm_capture_count(void);
+uint64_t vm_allocation_count(void);
 
 /* Thread-local message describing the last error of this thread. */
 const char* vm_last_error(void);

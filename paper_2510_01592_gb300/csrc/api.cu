@@ -350,20 +350,22 @@ vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit) {
     const uint32_t want_b = m->brick_hint + m->brick_hint / 4 + 64;
     const uint32_t cap_b = want_b < m->capacity ? want_b : m->capacity;
     if (!m->vox_mem.p || (size_t)cap_b * kBrickVox > m->seg_nv) {
-        // Geometric growth (at least 1024 bricks, then doubling): a map that
+        // Geometric growth (at least 1024 bricks and 1.5x the hint, then
+        // doubling): a map that
         // grows every frame re-allocates, and its graph is re-captured, only
         // a few times.
         const size_t have_b = m->vox_mem.p ? m->seg_nv / kBrickVox : 0;
         size_t grow = have_b * 2 > 1024 ? have_b * 2 : 1024;
-        if (grow < cap_b) grow = cap_b;
+        if (grow < (size_t)cap_b + cap_b / 2) grow = (size_t)cap_b + cap_b / 2;
         if (grow > m->capacity) grow = m->capacity;
         VM_TRY(alloc_vox(m, (uint32_t)grow));
     }
     const size_t nv = m->seg_nv;
-    const uint32_t mc = p.min_cluster > 16 ? p.min_cluster : 16;
-    size_t kcap = nv / mc;
-    const size_t kh = (size_t)m->k_hint + m->k_hint / 4 + 64;
-    if (kcap < kh) kcap = kh;
+    // Cluster capacity from the last count with headroom (a segmentation with
+    // more clusters flags itself and is re-run with the count it needed): the
+    // fit's grids, the sort's digit passes and the fit scratch all scale with
+    // it, so it tracks the map rather than the worst case nv / min_cluster.
+    size_t kcap = (size_t)m->k_hint + m->k_hint / 4 + 64;
     if (kcap < 256) kcap = 256;
     if (kcap > nv) kcap = nv;
     if (kcap < m->kcap) kcap = m->kcap;  // never shrink: keeps the captured graph valid
@@ -575,7 +577,7 @@ vm_status launch_front(vm_map* m, const vm_segment_params& p) {
 bool take_hints(vm_map* m) {
     const SegCounters* hdr = static_cast<const SegCounters*>(m->out_host);
     m->brick_hint = hdr->n_bricks < m->capacity ? hdr->n_bricks : m->capacity;
-    m->k_hint = hdr->k;
+    m->k_hint = hdr->k_need > hdr->k ? hdr->k_need : hdr->k;
     m->hull_hint = hdr->n_hull;
     m->rec_hint = hdr->n_planes;
     return (hdr->err & kErrScratch) || hdr->n_hull > m->out_hcap || hdr->n_planes > m->out_kcap;
@@ -920,6 +922,13 @@ vm_status vm_autotune_segment(vm_map* m, const vm_segment_params* params, uint32
     m->tune = st == VM_OK ? best_c : keep;
     m->gen++;
     if (st != VM_OK) return st;
+    {  // leave the map ready: scratch sized and the graph captured for the chosen schedule
+        vm_planes tmp{};
+        st = launch_segment(m, p);
+        if (st == VM_OK) st = finish_segment(m, p, &tmp);
+        vm_planes_free(&tmp);
+        if (st != VM_OK) return st;
+    }
     if (best) {
         best->tile = (uint32_t)best_c.tile;
         best->hyp_per_thread = (uint32_t)best_c.hyp_per_thread;
@@ -1107,6 +1116,8 @@ vm_status vm_stage_times(vm_map* map, double* ms, uint64_t* calls, uint32_t cap,
 const char* vm_stage_name(uint32_t stage) { return stage < (uint32_t)kNumStages ? kStageNames[stage] : ""; }
 
 uint64_t vm_launch_count(void) { return g_launches.load(); }
+uint64_t vm_capture_count(void) { return capture_total(); }
+uint64_t vm_allocation_count(void) { return alloc_total(); }
 
 vm_status vm_fit_planes(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
                         const vm_segment_params* params, void* stream, vm_planes* out) {

@@ -715,6 +715,7 @@ __global__ void k_seg_guard(SegCounters* __restrict__ ctr, uint32_t cap_b) {
 // Clusters beyond the scratch flag a re-run (the count is clamped for the
 // kernels that follow); cl_off[k] = the number of clustered points.
 __global__ void k_clusters_end(SegCounters* __restrict__ ctr, uint32_t kcap, uint32_t* __restrict__ cl_off) {
+    ctr->k_need = ctr->k;
     if (ctr->k > kcap) {
         ctr->err |= kErrScratch;
         ctr->k = kcap;

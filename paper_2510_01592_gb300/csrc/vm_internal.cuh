@@ -67,7 +67,8 @@ struct SegCounters {
     uint32_t fit_err;    // fit error bits (copied at the end)
     uint32_t n_list;     // occupied voxels listed for the eigen-solve
     uint32_t n_planes;   // output plane records (k, or more with several extraction rounds)
-    uint32_t pad[3];
+    uint32_t k_need;     // kept clusters before clamping to the scratch (sizes a re-run)
+    uint32_t pad[2];
 };
 
 // Per-cluster fit state on the device.

@@ -143,6 +143,8 @@ _SIGS = {
     "vm_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32)]),
     "vm_stage_name": (C.c_char_p, [C.c_uint32]),
     "vm_launch_count": (C.c_uint64, []),
+    "vm_capture_count": (C.c_uint64, []),
+    "vm_allocation_count": (C.c_uint64, []),
     "vm_last_error": (C.c_char_p, []),
     "vm_version": (C.c_char_p, []),
 }
@@ -468,6 +470,14 @@ def set_fit_stage_timing(enable: bool):
 
 def launch_count() -> int:
     return int(load().vm_launch_count())
+
+
+def capture_count() -> int:
+    return int(load().vm_capture_count())
+
+
+def allocation_count() -> int:
+    return int(load().vm_allocation_count())
 
 
 # C-ABI names re-exported for callers who want the raw entry points.
