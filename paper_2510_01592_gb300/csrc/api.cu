@@ -33,6 +33,14 @@ static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "fina
 
 void set_error(const std::string& msg) { g_err = msg; }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* v = getenv("VOXMPS_PDL");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 vm_status cuda_status(cudaError_t e, const char* what) {
     g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return e == cudaErrorMemoryAllocation ? VM_ERR_OUT_OF_MEMORY : VM_ERR_CUDA;
@@ -351,9 +359,8 @@ vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit) {
     const uint32_t cap_b = want_b < m->capacity ? want_b : m->capacity;
     if (!m->vox_mem.p || (size_t)cap_b * kBrickVox > m->seg_nv) {
         // Geometric growth (at least 1024 bricks and 1.5x the hint, then
-        // doubling): a map that
-        // grows every frame re-allocates, and its graph is re-captured, only
-        // a few times.
+        // doubling): a map that grows every frame re-allocates, and its graph
+        // is re-captured, only a few times.
         const size_t have_b = m->vox_mem.p ? m->seg_nv / kBrickVox : 0;
         size_t grow = have_b * 2 > 1024 ? have_b * 2 : 1024;
         if (grow < (size_t)cap_b + cap_b / 2) grow = (size_t)cap_b + cap_b / 2;
@@ -396,6 +403,7 @@ __global__ void k_header(const SegCounters* __restrict__ ctr, const uint32_t* __
                          const uint32_t* __restrict__ rounds, const uint32_t* __restrict__ fit_err,
                          const MapCounters* __restrict__ mc, const uint32_t* __restrict__ seg_err,
                          SegCounters* __restrict__ out) {
+    pdl_gate();
     SegCounters h = *ctr;
     h.n_hull = rounds ? rounds[kWordHullTot] : hull_off[h.k];
     h.n_planes = rounds ? rounds[kWordRec] : h.k;
@@ -448,7 +456,7 @@ cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk
         e = launch_pack(fb, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, planes, hull_xy, hull_xyz, m->out_hcap, s);
         if (e != cudaSuccess) return e;
     }
-    k_header<<<1, 1, 0, s>>>(b.ctr, fb.hull_cnt, rounds, fb.err, m->ctr, m->err, reinterpret_cast<SegCounters*>(d));
+    launch_k(k_header, dim3(1), dim3(1), 0, s, b.ctr, fb.hull_cnt, rounds, fb.err, m->ctr, m->err, reinterpret_cast<SegCounters*>(d));
     count_launch(1);
     VM_STAGE_END(hk, kStPack, s);
     return cudaGetLastError();

@@ -76,6 +76,7 @@ __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict_
                       const uint32_t* __restrict__ labels, const uint32_t* __restrict__ kp, int H, unsigned long long seed,
                       uint32_t round, float4* __restrict__ hyp, uint8_t* __restrict__ valid,
                       uint32_t* __restrict__ counts) {
+    pdl_gate();
     const uint32_t k = *kp;
     const size_t total = (size_t)k * H;
     for (size_t t = (size_t)blockIdx.x * kT + threadIdx.x; t < total; t += (size_t)gridDim.x * kT) {
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
                                               const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int H, int T,
                                               const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
                                               uint32_t* __restrict__ queue, float eps) {
+    pdl_gate();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];                // T staged points
     uint32_t* red = reinterpret_cast<uint32_t*>(sp + T);  // [P][G*R]
@@ -177,6 +179,7 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
 __global__ void k_select(const float* __restrict__ pts, const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int H,
                          const float4* __restrict__ hyp, const uint8_t* __restrict__ valid,
                          const uint32_t* __restrict__ counts, FitCluster* __restrict__ cl) {
+    pdl_gate();
     const uint32_t k = *kp;
     __shared__ unsigned long long wbest[kT / 32];
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
@@ -316,6 +319,7 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
                                                 const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int T,
                                                 FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
                                                 float* __restrict__ part, float eps, uint32_t* __restrict__ err) {
+    pdl_gate();
     const uint32_t k = *kp;
     __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 4];
     const uint32_t n_items = item_off[k];
@@ -421,6 +425,7 @@ __device__ __forceinline__ df2 df_shfl_xor(df2 x, int o) {
 __global__ void k_centroid(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
                            const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
                            FitCluster* __restrict__ cl, float* __restrict__ cen /* [k][3][2] */) {
+    pdl_gate();
     const uint32_t k = *kp;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kT / 32);
@@ -471,6 +476,7 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
                                                FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
                                                const float* __restrict__ cen, float* __restrict__ part,
                                                int2* __restrict__ surv) {
+    pdl_gate();
     const uint32_t k = *kp;
     __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 6];
     __shared__ int2 poly[kFiltDirs + 1];
@@ -550,6 +556,7 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
 __global__ void k_refit(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
                         const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
                         const float* __restrict__ cen, FitCluster* __restrict__ cl) {
+    pdl_gate();
     const uint32_t k = *kp;
     const int lane = threadIdx.x & 31;
     const uint32_t warps = gridDim.x * (kT / 32);
@@ -690,6 +697,7 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
                                              const FitCluster* __restrict__ cl, const int2* __restrict__ surv,
                                              int2* __restrict__ hull, uint32_t* __restrict__ hull_cnt,
                                              uint32_t* __restrict__ err) {
+    pdl_gate();
     const uint32_t k = *kp;
     extern __shared__ unsigned long long sk[];              // kHullCap keys, then kHullCap unique
     unsigned long long* uq = sk + kHullCap;
@@ -904,6 +912,7 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
 }
 
 __global__ void k_items(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int T, uint32_t* __restrict__ item_cnt) {
+    pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT)
         item_cnt[c] = (off[c + 1] - off[c] + (uint32_t)T - 1) / (uint32_t)T;
@@ -913,6 +922,7 @@ __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restr
                        const FitCluster* __restrict__ cl, const int2* __restrict__ hull,
                        const uint32_t* __restrict__ hull_off, vm_plane* __restrict__ planes,
                        int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz, uint32_t hull_cap) {
+    pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
         const uint32_t ho = hull_off[c];
@@ -932,6 +942,7 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
                                                    const uint32_t* __restrict__ kp, int H, int T,
                                                    const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
                                                    uint32_t* __restrict__ queue, float eps) {
+    pdl_gate();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];  // [kT / 32][T]
     const int lane = threadIdx.x & 31;
@@ -999,7 +1010,7 @@ cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* 
     const int G = (H + R - 1) / R;
     const int P = kT / G;
     const size_t smem = (size_t)T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
-    k_score<R><<<grid, kT, smem, s>>>(pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
+    launch_k(k_score<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
     return cudaGetLastError();
 }
 
@@ -1008,15 +1019,16 @@ cudaError_t launch_score_warp(const float* pts, const uint32_t* off, const uint3
                               int H, int T, const float4* hyp, uint32_t* counts, uint32_t* queue, float eps,
                               int grid, cudaStream_t s) {
     const size_t smem = (size_t)(kT / 32) * T * sizeof(float4);
-    k_score_warp<R><<<grid, kT, smem, s>>>(pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
+    launch_k(k_score_warp<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
     return cudaGetLastError();
 }
 
 __global__ void k_set_end(uint32_t* __restrict__ arr, const uint32_t* __restrict__ kp, const uint32_t* __restrict__ v) {
+    pdl_gate();
     arr[*kp] = *v;
 }
 
-__global__ void k_set_u32(uint32_t* __restrict__ p, uint32_t v) { *p = v; }
+__global__ void k_set_u32(uint32_t* __restrict__ p, uint32_t v) { pdl_gate(); *p = v; }
 
 }  // namespace
 
@@ -1086,7 +1098,7 @@ void fit_init_attributes() {
 }
 
 cudaError_t fit_set_count(uint32_t* kdev, uint32_t k, cudaStream_t s) {
-    k_set_u32<<<1, 1, 0, s>>>(kdev, k);
+    launch_k(k_set_u32, dim3(1), dim3(1), 0, s, kdev, k);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -1101,14 +1113,14 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     cudaError_t e;
     VM_STAGE_BEGIN(hk, kStHyp, s);
     const unsigned kgrid = (kcap + kT - 1) / kT < (uint32_t)sms * 8 ? (kcap + kT - 1) / kT : (uint32_t)sms * 8;
-    k_items<<<kgrid, kT, 0, s>>>(off, kp, T, fb.item_off);
+    launch_k(k_items, dim3(kgrid), dim3(kT), 0, s, off, kp, T, fb.item_off);
     e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s, fb.err);
     if (e != cudaSuccess) return e;
-    k_set_end<<<1, 1, 0, s>>>(fb.item_off, kp, fb.tot);
+    launch_k(k_set_end, dim3(1), dim3(1), 0, s, fb.item_off, kp, fb.tot);
     if ((e = cudaMemsetAsync(fb.queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
     const size_t kh = (size_t)kcap * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    k_hyp<<<hgrid, kT, 0, s>>>(pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid, fb.counts);
+    launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid, fb.counts);
     VM_STAGE_END(hk, kStHyp, s);
     count_launch(3);
     const int grid = sms * t.ctas_per_sm;
@@ -1139,21 +1151,21 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     count_launch(1);
     const unsigned cgrid = kcap < (uint32_t)sms * 8 ? kcap : (uint32_t)sms * 8;
     VM_STAGE_BEGIN(hk, kStExtract, s);
-    k_select<<<cgrid, kT, 0, s>>>(pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
+    launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
     const unsigned igrid = (unsigned)sms * 8;
-    k_extract<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
+    launch_k(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
     const unsigned wgrid0 = (kcap + kT / 32 - 1) / (kT / 32);
     const unsigned wgrid = wgrid0 < (uint32_t)sms * 8 ? wgrid0 : (uint32_t)sms * 8;
-    k_centroid<<<wgrid, kT, 0, s>>>(off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
-    k_filter<<<igrid, kT, 0, s>>>(pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
+    launch_k(k_centroid, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
+    launch_k(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
     VM_STAGE_END(hk, kStExtract, s);
     count_launch(4);
     VM_STAGE_BEGIN(hk, kStHull, s);
-    k_refit<<<wgrid, kT, 0, s>>>(off, fb.item_off, kp, T, fb.part, fb.cen, fb.cl);
-    k_hull<<<cgrid, kT, fit_hull_smem(), s>>>(off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
+    launch_k(k_refit, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cen, fb.cl);
+    launch_k(k_hull, dim3(cgrid), dim3(kT), fit_hull_smem(), s, off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
     e = exclusive_scan_dev(fb.hull_cnt, fb.hull_cnt, fb.tot + 1, kp, kcap, fb.scan_tmp, s, fb.err);
     if (e != cudaSuccess) return e;
-    k_set_end<<<1, 1, 0, s>>>(fb.hull_cnt, kp, fb.tot + 1);
+    launch_k(k_set_end, dim3(1), dim3(1), 0, s, fb.hull_cnt, kp, fb.tot + 1);
     VM_STAGE_END(hk, kStHull, s);
     count_launch(3);
     return cudaGetLastError();
@@ -1163,7 +1175,7 @@ cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_
                         uint32_t kcap, vm_plane* planes, int32_t* hull_xy, float* hull_xyz, uint32_t hull_cap,
                         cudaStream_t s) {
     if (kcap == 0) return cudaSuccess;
-    k_pack<<<kcap < 4096 ? kcap : 4096, 128, 0, s>>>(off, labels, kp, fb.cl, fb.hull, fb.hull_cnt, planes, hull_xy,
+    launch_k(k_pack, dim3(kcap < 4096 ? kcap : 4096), dim3(128), 0, s, off, labels, kp, fb.cl, fb.hull, fb.hull_cnt, planes, hull_xy,
                                                     hull_xyz, hull_cap);
     count_launch(1);
     return cudaGetLastError();
@@ -1202,6 +1214,7 @@ constexpr size_t kStaticBytes = kOffScan + align256(kScanWords * sizeof(uint32_t
 // to the caller's arrays.
 __global__ void k_static_out(const FitCluster* __restrict__ cl, const uint32_t* __restrict__ kp, float* __restrict__ planes,
                              int32_t* __restrict__ best_h, uint32_t* __restrict__ inliers) {
+    pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT) {
         const FitCluster f = cl[c];
@@ -1283,14 +1296,14 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     // the work queue starts at zero every call; counts are zeroed by k_hyp
     if ((e = cudaMemsetAsync(queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess)
         return cuda_status(e, "cudaMemsetAsync");
-    k_set_u32<<<1, 1, 0, s>>>(kdev, k);
-    k_items<<<(k + kT - 1) / kT, kT, 0, s>>>(off, kdev, t.tile, item_off);
+    launch_k(k_set_u32, dim3(1), dim3(1), 0, s, kdev, k);
+    launch_k(k_items, dim3((k + kT - 1) / kT), dim3(kT), 0, s, off, kdev, t.tile, item_off);
     if ((e = exclusive_scan_dev(item_off, item_off, total, kdev, k, scan_tmp, s, nullptr)) != cudaSuccess)
         return cuda_status(e, "scan");
-    k_set_end<<<1, 1, 0, s>>>(item_off, kdev, total);
+    launch_k(k_set_end, dim3(1), dim3(1), 0, s, item_off, kdev, total);
     const size_t kh = (size_t)k * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    k_hyp<<<hgrid, kT, 0, s>>>(xyz, off, labels, kdev, H, params->seed, 0u, hyp, valid, counts);
+    launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, xyz, off, labels, kdev, H, params->seed, 0u, hyp, valid, counts);
     int R = t.hyp_per_thread;
     while (R < 8 && (H + R - 1) / R > kT) R <<= 1;
     const int grid = sms * t.ctas_per_sm;
@@ -1300,8 +1313,8 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     }
     if (e != cudaSuccess) return cuda_status(e, "k_score");
     const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;
-    k_select<<<cgrid, kT, 0, s>>>(xyz, off, kdev, H, hyp, valid, counts, cl);
-    k_static_out<<<(k + kT - 1) / kT, kT, 0, s>>>(cl, kdev, planes_out, best_h_out, inliers_out);
+    launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, xyz, off, kdev, H, hyp, valid, counts, cl);
+    launch_k(k_static_out, dim3((k + kT - 1) / kT), dim3(kT), 0, s, cl, kdev, planes_out, best_h_out, inliers_out);
     count_launch(7);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "vm_ransac_static launch");

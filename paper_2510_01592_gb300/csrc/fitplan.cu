@@ -27,6 +27,7 @@ struct FitHeader {
 // then sees zero clusters, and the host grows the scratch and runs again.
 __global__ void k_fit_guard(const uint32_t* __restrict__ off, uint32_t* __restrict__ kdev, uint32_t ncap,
                             uint32_t* __restrict__ err, uint32_t* __restrict__ n_out) {
+    pdl_gate();
     const uint32_t k = *kdev;
     const uint32_t n = off[k];
     *n_out = n;
@@ -39,6 +40,7 @@ __global__ void k_fit_guard(const uint32_t* __restrict__ off, uint32_t* __restri
 __global__ void k_fit_header(const uint32_t* __restrict__ kdev, const uint32_t* __restrict__ n_pts,
                              const uint32_t* __restrict__ hull_off, const uint32_t* __restrict__ err,
                              FitHeader* __restrict__ out) {
+    pdl_gate();
     FitHeader h;
     h.k = *kdev;
     h.n_points = *n_pts;
@@ -128,7 +130,7 @@ cudaError_t enqueue_fit(vm_fit_plan* f, const float* x, const uint32_t* off, con
     if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(fb.kdev, f->k_host, sizeof(uint32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;
-    k_fit_guard<<<1, 1, 0, s>>>(off, fb.kdev, (uint32_t)f->fc.npts, fb.err, fb.tot + 2);
+    launch_k(k_fit_guard, dim3(1), dim3(1), 0, s, off, fb.kdev, (uint32_t)f->fc.npts, fb.err, fb.tot + 2);
     if ((e = launch_fit(x, off, lab, fb.kdev, kcap, f->prm, fb, f->tune, device_sms(), s, hk)) != cudaSuccess)
         return e;
     char* d = f->out_dev;
@@ -137,7 +139,7 @@ cudaError_t enqueue_fit(vm_fit_plan* f, const float* x, const uint32_t* off, con
                     reinterpret_cast<int32_t*>(d + out_xy_off(f->out_kcap)),
                     reinterpret_cast<float*>(d + out_xyz_off(f->out_kcap, f->out_hcap)), f->out_hcap, s);
     if (e != cudaSuccess) return e;
-    k_fit_header<<<1, 1, 0, s>>>(fb.kdev, fb.tot + 2, fb.hull_cnt, fb.err, reinterpret_cast<FitHeader*>(d));
+    launch_k(k_fit_header, dim3(1), dim3(1), 0, s, fb.kdev, fb.tot + 2, fb.hull_cnt, fb.err, reinterpret_cast<FitHeader*>(d));
     VM_STAGE_END(hk, kStPack, s);
     count_launch(2);
     return cudaGetLastError();

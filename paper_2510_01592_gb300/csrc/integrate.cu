@@ -62,6 +62,7 @@ __device__ __forceinline__ Keyed key_point(const float* __restrict__ xyz, uint32
 __global__ void __launch_bounds__(kThreads) k_claim(const float* __restrict__ xyz, uint32_t n, Pose P, Grid g,
                                                    int32_t* __restrict__ table, int32_t* __restrict__ slot_key,
                                                    MapCounters* __restrict__ ctr, uint32_t capacity) {
+    pdl_gate();
     for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         Keyed k = key_point(xyz, i, P, g);
         if (!k.ok) continue;
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_accum(const float* __restrict__ xy
                                                    const int32_t* __restrict__ table,
                                                    unsigned long long* __restrict__ S, uint32_t* __restrict__ C,
                                                    MapCounters* __restrict__ ctr) {
+    pdl_gate();
     const int lane = threadIdx.x & 31;
     const uint32_t warp_global = (blockIdx.x * kThreads + threadIdx.x) >> 5;
     const uint32_t n_warps = (gridDim.x * kThreads) >> 5;
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
                                                         const int32_t* __restrict__ table,
                                                         const uint32_t* __restrict__ C, uint32_t* mark,
                                                         MapCounters* __restrict__ ctr) {
+    pdl_gate();
     const float s[3] = {__fmul_rn(__fsub_rn(P.r[3], g.ox), g.inv_res), __fmul_rn(__fsub_rn(P.r[7], g.oy), g.inv_res),
                         __fmul_rn(__fsub_rn(P.r[11], g.oz), g.inv_res)};
     const int dims[3] = {g.nx, g.ny, g.nz};
@@ -231,6 +234,7 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
 __global__ void __launch_bounds__(kThreads) k_clear_apply(unsigned long long* __restrict__ S, uint32_t* __restrict__ C,
                                                          uint32_t* __restrict__ mark, MapCounters* __restrict__ ctr,
                                                          uint32_t capacity) {
+    pdl_gate();
     const uint32_t nb = min(ctr->n_bricks, capacity);
     const size_t words = (size_t)nb * (kBrickVox / 32);
     uint32_t cleared = 0;
@@ -272,10 +276,10 @@ cudaError_t launch_clear(const float* xyz, uint32_t n, const Pose& pose, const G
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint32_t want = (n + kThreads - 1) / kThreads;
     const uint32_t grid = want < (uint32_t)(sms * 8) ? want : (uint32_t)(sms * 8);
-    k_clear_mark<<<grid, kThreads, 0, s>>>(xyz, n, pose, g, brick_table, C, mark, ctr);
+    launch_k(k_clear_mark, dim3(grid), dim3(kThreads), 0, s, xyz, n, pose, g, brick_table, C, mark, ctr);
     const size_t words = (size_t)capacity * (kBrickVox / 32);
     const size_t wgrid = (words + kThreads - 1) / kThreads;
-    k_clear_apply<<<(unsigned)(wgrid < (size_t)sms * 8 ? wgrid : (size_t)sms * 8), kThreads, 0, s>>>(S, C, mark, ctr,
+    launch_k(k_clear_apply, dim3((unsigned)(wgrid < (size_t)sms * 8 ? wgrid : (size_t)sms * 8)), dim3(kThreads), 0, s, S, C, mark, ctr,
                                                                                                       capacity);
     count_launch(2);
     return cudaGetLastError();
@@ -290,8 +294,8 @@ cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, con
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint32_t want = (n + kThreads - 1) / kThreads;
     const uint32_t grid = want < (uint32_t)(sms * 8) ? want : (uint32_t)(sms * 8);
-    k_claim<<<grid, kThreads, 0, s>>>(xyz, n, pose, g, brick_table, slot_key, ctr, capacity);
-    k_accum<<<grid, kThreads, 0, s>>>(xyz, n, pose, g, brick_table, S, C, ctr);
+    launch_k(k_claim, dim3(grid), dim3(kThreads), 0, s, xyz, n, pose, g, brick_table, slot_key, ctr, capacity);
+    launch_k(k_accum, dim3(grid), dim3(kThreads), 0, s, xyz, n, pose, g, brick_table, S, C, ctr);
     count_launch(2);
     return cudaGetLastError();
 }

@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(kRT) k_round_stage(const uint32_t* __restrict_
                                                      uint32_t* __restrict__ hbase, vm_plane* __restrict__ slot,
                                                      uint32_t* __restrict__ cnt, int2* __restrict__ shull,
                                                      uint32_t hcap) {
+    pdl_gate();
     const uint32_t k = *kp;
     const uint32_t base = r ? hbase[r] : 0u;
     if (blockIdx.x == 0 && threadIdx.x == 0) hbase[r + 1] = base + hull_off[k];
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(kRT) k_round_stage(const uint32_t* __restrict_
 __global__ void k_round_active(const uint32_t* __restrict__ kp, const uint32_t* __restrict__ off,
                                const FitCluster* __restrict__ cl, uint32_t minc, uint32_t* __restrict__ act,
                                uint32_t* __restrict__ npts) {
+    pdl_gate();
     const uint32_t k = *kp;
     const uint32_t tid = blockIdx.x * kRT + threadIdx.x;
     if (tid == 0) *npts = off[k];
@@ -77,6 +79,7 @@ __global__ void k_round_active(const uint32_t* __restrict__ kp, const uint32_t* 
 __global__ void __launch_bounds__(kRT) k_round_keep(const uint32_t* __restrict__ kp, const uint32_t* __restrict__ off,
                                                     const uint32_t* __restrict__ act, const uint8_t* __restrict__ inl,
                                                     uint32_t* __restrict__ keep, uint8_t* __restrict__ inl0) {
+    pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
         const uint32_t a = act[c], o1 = off[c + 1];
@@ -96,6 +99,7 @@ __global__ void k_round_scatter(const uint32_t* __restrict__ kp, const uint32_t*
                                 const uint32_t* __restrict__ knext, const uint32_t* __restrict__ keep_tot,
                                 float* __restrict__ pts_n, uint32_t* __restrict__ off_n, uint32_t* __restrict__ lab_n,
                                 uint32_t* __restrict__ orig_n) {
+    pdl_gate();
     const uint32_t k = *kp, n = *npts;
     const uint32_t tid = blockIdx.x * kRT + threadIdx.x, stride = gridDim.x * kRT;
     for (uint32_t i = tid; i < n; i += stride) {
@@ -118,6 +122,7 @@ __global__ void k_round_scatter(const uint32_t* __restrict__ kp, const uint32_t*
 // Hull vertices per round-0 cluster, over its records.
 __global__ void k_round_totals(const uint32_t* __restrict__ kp, const uint32_t* __restrict__ cnt,
                                const vm_plane* __restrict__ slot, uint32_t* __restrict__ hcnt) {
+    pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x * kRT + threadIdx.x; c < k; c += gridDim.x * kRT) {
         uint32_t h = 0;
@@ -134,6 +139,7 @@ __global__ void __launch_bounds__(kRT) k_round_pack(const uint32_t* __restrict__
                                                     uint32_t hcap, vm_plane* __restrict__ planes, uint32_t rec_cap,
                                                     int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz,
                                                     uint32_t hull_cap) {
+    pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
         uint32_t ho = hpos[c];
@@ -214,20 +220,20 @@ cudaError_t launch_rounds(const SegBuffers& b, uint32_t kcap, const vm_segment_p
     for (uint32_t r = 0; r < P; ++r) {
         if ((e = launch_fit(pts, off, lab, kp, kcap, p, fb, t, sms, s, hk, r)) != cudaSuccess) return e;
         VM_STAGE_BEGIN(hk, kStRounds, s);
-        k_round_stage<<<gc, kRT, 0, s>>>(kp, off, lab, orig, fb.cl, fb.hull, fb.hull_cnt, r, rb.word + kWordHull,
+        launch_k(k_round_stage, dim3(gc), dim3(kRT), 0, s, kp, off, lab, orig, fb.cl, fb.hull, fb.hull_cnt, r, rb.word + kWordHull,
                                          rb.slot, rb.cnt, rb.hull, (uint32_t)rb.hcap);
         count_launch(1);
         if (r + 1 < P) {
             const int nx = (r + 1) & 1;
             uint32_t* knext = rb.word + kWordK + r + 1;
-            k_round_active<<<gk, kRT, 0, s>>>(kp, off, fb.cl, minc, rb.act, rb.word + kWordNpts);
+            launch_k(k_round_active, dim3(gk), dim3(kRT), 0, s, kp, off, fb.cl, minc, rb.act, rb.word + kWordNpts);
             e = exclusive_scan_dev(rb.act, rb.apos, knext, kp, kcap, scan_tmp, s, fb.err);
             if (e != cudaSuccess) return e;
-            k_round_keep<<<gc, kRT, 0, s>>>(kp, off, rb.act, fb.inlier, rb.keep, r == 0 ? rb.inl0 : nullptr);
+            launch_k(k_round_keep, dim3(gc), dim3(kRT), 0, s, kp, off, rb.act, fb.inlier, rb.keep, r == 0 ? rb.inl0 : nullptr);
             e = exclusive_scan_dev(rb.keep, rb.kpos, rb.word + kWordKeep, rb.word + kWordNpts, nv, scan_tmp, s,
                                    fb.err);
             if (e != cudaSuccess) return e;
-            k_round_scatter<<<gp, kRT, 0, s>>>(kp, off, lab, orig, rb.act, rb.apos, rb.keep, rb.kpos, pts,
+            launch_k(k_round_scatter, dim3(gp), dim3(kRT), 0, s, kp, off, lab, orig, rb.act, rb.apos, rb.keep, rb.kpos, pts,
                                                rb.word + kWordNpts, knext, rb.word + kWordKeep, rb.pts[nx],
                                                rb.off[nx], rb.lab[nx], rb.orig[nx]);
             count_launch(3);
@@ -240,14 +246,14 @@ cudaError_t launch_rounds(const SegBuffers& b, uint32_t kcap, const vm_segment_p
         VM_STAGE_END(hk, kStRounds, s);
     }
     VM_STAGE_BEGIN(hk, kStPack, s);
-    k_round_totals<<<gk, kRT, 0, s>>>(k0, rb.cnt, rb.slot, rb.hcnt);
+    launch_k(k_round_totals, dim3(gk), dim3(kRT), 0, s, k0, rb.cnt, rb.slot, rb.hcnt);
     count_launch(1);
     if ((e = exclusive_scan_dev(rb.cnt, rb.cpos, rb.word + kWordRec, k0, kcap, scan_tmp, s, fb.err)) != cudaSuccess)
         return e;
     if ((e = exclusive_scan_dev(rb.hcnt, rb.hpos, rb.word + kWordHullTot, k0, kcap, scan_tmp, s, fb.err)) !=
         cudaSuccess)
         return e;
-    k_round_pack<<<clampg(kcap, sms, 8), kRT, 0, s>>>(k0, rb.cnt, rb.cpos, rb.hpos, rb.slot, rb.hull,
+    launch_k(k_round_pack, dim3(clampg(kcap, sms, 8)), dim3(kRT), 0, s, k0, rb.cnt, rb.cpos, rb.hpos, rb.slot, rb.hull,
                                                       (uint32_t)rb.hcap, planes, rec_cap, hull_xy, hull_xyz, hull_cap);
     count_launch(1);
     VM_STAGE_END(hk, kStPack, s);

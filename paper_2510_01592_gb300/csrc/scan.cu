@@ -44,91 +44,15 @@ __device__ __forceinline__ size_t dev_count(size_t n, const uint32_t* n_dev) {
     return d < n ? d : n;
 }
 
-__global__ void k_tile_reduce(const uint32_t* __restrict__ in, size_t n_cap, const uint32_t* __restrict__ n_dev,
-                              uint32_t* __restrict__ tile_sum) {
-    __shared__ uint32_t ws[kScanThreads / 32];
-    const size_t n = dev_count(n_cap, n_dev);
-    const size_t base = (size_t)blockIdx.x * kScanTile;
-    uint32_t s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        size_t j = base + (size_t)i * kScanThreads + threadIdx.x;
-        if (j < n) s += in[j];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) t += ws[w];
-        tile_sum[blockIdx.x] = t;
-    }
-}
-
-// One block scans the tile sums in place (exclusive), carrying across chunks.
-__global__ void k_scan_sums(uint32_t* __restrict__ sums, size_t nt, uint32_t* __restrict__ total) {
-    __shared__ uint32_t ws[kScanThreads / 32];
-    __shared__ uint32_t chunk_total;
-    uint32_t carry = 0;
-    for (size_t base = 0; base < nt; base += kScanThreads) {
-        size_t j = base + threadIdx.x;
-        uint32_t v = (j < nt) ? sums[j] : 0u;
-        uint32_t ex = block_excl_scan(v, ws, &chunk_total);
-        if (j < nt) sums[j] = ex + carry;
-        __syncthreads();
-        carry += chunk_total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && total) *total = carry;
-}
-
-__global__ void k_tile_scan(const uint32_t* in, uint32_t* out, size_t n_cap, const uint32_t* __restrict__ n_dev,
-                            const uint32_t* __restrict__ tile_off) {
-    __shared__ uint32_t buf[kScanTile];
-    __shared__ uint32_t ws[kScanThreads / 32];
-    __shared__ uint32_t tot;
-    const size_t n = dev_count(n_cap, n_dev);
-    const size_t base = (size_t)blockIdx.x * kScanTile;
-    if (base >= n) return;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        int t = i * kScanThreads + threadIdx.x;
-        size_t j = base + t;
-        buf[t] = (j < n) ? in[j] : 0u;
-    }
-    __syncthreads();
-    uint32_t v[kScanItems];
-    uint32_t s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        v[i] = buf[threadIdx.x * kScanItems + i];
-        s += v[i];
-    }
-    uint32_t ex = block_excl_scan(s, ws, &tot) + tile_off[blockIdx.x];
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        buf[threadIdx.x * kScanItems + i] = ex;
-        ex += v[i];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        int t = i * kScanThreads + threadIdx.x;
-        size_t j = base + t;
-        if (j < n) out[j] = buf[t];
-    }
-}
-
 // Single-pass scan with decoupled look-back (Merrill and Garland, "Single-pass
 // parallel prefix scan with decoupled look-back", 2016).  Each CTA takes the
 // next tile from a ticket counter (so every earlier tile belongs to a CTA that
 // has started), publishes its tile sum, then walks back over earlier tiles'
 // published words until it meets an inclusive prefix, and publishes its own.
 // A status word is (epoch << 34 | flag << 32 | value), a 30-bit epoch: words
-// of an earlier
-// launch (another epoch) read as not yet published, so no clearing pass is
-// needed; the last CTA to finish resets the ticket and advances the epoch.
+// of an earlier launch (another epoch) read as not yet published, so no
+// clearing pass is needed; the last CTA to finish resets the ticket and
+// advances the epoch.
 // The state (ticket, done, epoch, then one 64-bit word per tile) must start
 // zeroed once, when its memory is allocated.  Every wait is bounded: a wait
 // that runs out sets kErrTimeout in *err and counts the missing prefix as 0.
@@ -144,6 +68,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(const uint32_t* 
                                                                 const uint32_t* __restrict__ n_dev,
                                                                 uint32_t* __restrict__ total,
                                                                 uint32_t* __restrict__ state, uint32_t* err) {
+    pdl_gate();
     __shared__ uint32_t buf[kScanTile];
     __shared__ uint32_t ws[kScanThreads / 32];
     __shared__ uint32_t tot, s_tile, s_prefix;
@@ -242,6 +167,7 @@ __device__ __forceinline__ bool rs_pass_active(const uint32_t* kb, int pass) {
 
 __global__ void k_rs_hist(const uint32_t* __restrict__ keys, size_t n_cap, const uint32_t* __restrict__ n_dev, int pass,
                           const uint32_t* __restrict__ kb, uint32_t* __restrict__ ghist, uint32_t* __restrict__ cnt) {
+    pdl_gate();
     __shared__ uint32_t h[256];
     const bool active = rs_pass_active(kb, pass);
     const size_t n = active ? dev_count(n_cap, n_dev) : 0;
@@ -265,6 +191,7 @@ __global__ void k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* _
                              uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, size_t n_cap,
                              const uint32_t* __restrict__ n_dev, int pass, const uint32_t* __restrict__ kb,
                              const uint32_t* __restrict__ goff) {
+    pdl_gate();
     __shared__ uint32_t wc[kSortWarps][256];
     if (!rs_pass_active(kb, pass)) return;
     const size_t n = dev_count(n_cap, n_dev);
@@ -321,6 +248,7 @@ constexpr size_t kSmallMax = 16384;
 
 __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const uint32_t* in, uint32_t* out, size_t n_cap,
                                                               const uint32_t* __restrict__ n_dev, uint32_t* total) {
+    pdl_gate();
     __shared__ uint32_t ws[kSmallThreads / 32];
     __shared__ uint32_t round_total;
     const size_t n = dev_count(n_cap, n_dev);
@@ -368,12 +296,12 @@ cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* tota
         return cudaSuccess;
     }
     if (n_cap <= kSmallMax) {
-        k_scan_small<<<1, kSmallThreads, 0, s>>>(in, out, n_cap, n_dev, total);
+        launch_k(k_scan_small, dim3(1), dim3(kSmallThreads), 0, s, in, out, n_cap, n_dev, total);
         count_launch(1);
         return cudaGetLastError();
     }
     const size_t nt = (n_cap + kScanTile - 1) / kScanTile;
-    k_scan_lookback<<<(unsigned)nt, kScanThreads, 0, s>>>(in, out, n_cap, n_dev, total, tmp, err);
+    launch_k(k_scan_lookback, dim3((unsigned)nt), dim3(kScanThreads), 0, s, in, out, n_cap, n_dev, total, tmp, err);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -399,10 +327,10 @@ cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys
     uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
     const int passes = (bits + 7) / 8;
     for (int p = 0; p < passes; ++p) {
-        k_rs_hist<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, n_cap, n_dev, p, key_bound, ghist, cnt);
+        launch_k(k_rs_hist, dim3((unsigned)nt), dim3(kSortThreads), 0, s, ki, n_cap, n_dev, p, key_bound, ghist, cnt);
         cudaError_t e = exclusive_scan_dev(ghist, ghist, nullptr, cnt, 256 * nt, stmp, s, err);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<<<(unsigned)nt, kSortThreads, 0, s>>>(ki, vi, ko, vo, n_cap, n_dev, p, key_bound, ghist);
+        launch_k(k_rs_scatter, dim3((unsigned)nt), dim3(kSortThreads), 0, s, ki, vi, ko, vo, n_cap, n_dev, p, key_bound, ghist);
         count_launch(2);
         uint32_t* t;
         t = ki; ki = ko; ko = t;

@@ -30,12 +30,14 @@ __device__ __forceinline__ void brick_coords(int32_t key, const Grid& g, int& bx
 }
 
 __global__ void k_brick_flags(const int32_t* __restrict__ table, uint32_t nb, uint32_t* __restrict__ flags) {
+    pdl_gate();
     for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < nb; i += gridDim.x * kT) flags[i] = table[i] >= 0;
 }
 
 __global__ void k_brick_compact(const int32_t* __restrict__ table, uint32_t nb, const uint32_t* __restrict__ flags,
                                 int32_t* __restrict__ rank_table, int32_t* __restrict__ sorted_slot,
                                 int32_t* __restrict__ sorted_key) {
+    pdl_gate();
     for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < nb; i += gridDim.x * kT) {
         const int32_t t = table[i];
         if (t >= 0) {
@@ -56,6 +58,7 @@ __global__ void __launch_bounds__(kT) k_finalize(const uint32_t* __restrict__ ns
                                                  const uint32_t* __restrict__ C, int32_t* __restrict__ M,
                                                  uint8_t* __restrict__ status, size_t stride,
                                                  SegCounters* __restrict__ ctr) {
+    pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     uint32_t occ = 0;
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
@@ -266,6 +269,7 @@ __global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__
                                                     uint32_t* __restrict__ list_idx, float* __restrict__ list_A,
                                                     uint8_t* __restrict__ nbr, size_t stride,
                                                     SegCounters* __restrict__ ctr) {
+    pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ int32_t sM[3][1000];
     __shared__ uint16_t list[512];
@@ -348,6 +352,7 @@ __global__ void __launch_bounds__(256) k_eigen(const SegCounters* __restrict__ c
                                                float* __restrict__ nrm, uint8_t* __restrict__ status,
                                                float4* __restrict__ rec, size_t stride, uint32_t n_th,
                                                float cos_step) {
+    pdl_gate();
     const uint32_t n = ctr->n_list;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         float v[3][3], d[3], nv[3];
@@ -374,6 +379,7 @@ __global__ void __launch_bounds__(kNormT) k_ccl_local(const uint32_t* __restrict
                                                       const float4* __restrict__ rec, uint32_t* __restrict__ parent,
                                                       uint32_t* __restrict__ count, size_t stride, uint8_t want,
                                                       float d_th2, float cos_ccl, uint32_t* err) {
+    pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ float4 sA[512];
     __shared__ float4 sB[512];
@@ -461,6 +467,7 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
                                                        const float4* __restrict__ rec, uint32_t* parent,
                                                        size_t stride, uint8_t want, float d_th2, float cos_ccl,
                                                        uint32_t* err) {
+    pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ float4 sA[1000];
     __shared__ float4 sB[1000];  // (normal, parent); parent kNone off the vertex set
@@ -552,6 +559,7 @@ __device__ __forceinline__ uint32_t uf_root(const uint32_t* P, uint32_t x, uint3
 // component's smallest index (its label) for every vertex.
 __global__ void k_compress_count(const uint32_t* __restrict__ nsp, uint32_t cap_b, uint32_t* parent,
                                  uint32_t* __restrict__ count, SegCounters* __restrict__ ctr, uint32_t* err) {
+    pdl_gate();
     const size_t nv = (size_t)min(*nsp, cap_b) * kBrickVox;
     uint32_t nvert = 0;
     for (size_t base = ((size_t)blockIdx.x * kT + threadIdx.x) & ~(size_t)31; base < nv;
@@ -603,6 +611,7 @@ __global__ void __launch_bounds__(kBrickVox) k_brick_tally(const uint32_t* __res
                                                            const uint32_t* __restrict__ count, uint32_t min_cluster,
                                                            uint32_t* __restrict__ nvert, uint32_t* __restrict__ nroot,
                                                            uint32_t* __restrict__ rmask) {
+    pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ uint32_t wc[kBrickVox / 32];
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
@@ -643,6 +652,7 @@ __global__ void __launch_bounds__(kBrickVox) k_brick_clusters(const uint32_t* __
                                                               uint32_t* __restrict__ cl_size,
                                                               uint32_t* __restrict__ cl_label, uint32_t kcap,
                                                               uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ uint32_t wc[kBrickVox / 32];
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
@@ -675,6 +685,7 @@ __global__ void k_gather(const uint32_t* __restrict__ np, const uint32_t* __rest
                          const int32_t* __restrict__ M, size_t stride,
                          const int32_t* __restrict__ sorted_key, Grid g, float* __restrict__ pts,
                          uint32_t* __restrict__ pt_vid) {
+    pdl_gate();
     const uint32_t n = *np;
     const uint32_t* __restrict__ vals = sort_result_alt(*kp, bits) ? vals_alt : vals_main;  // where the sort ended
     for (uint32_t p = blockIdx.x * kT + threadIdx.x; p < n; p += gridDim.x * kT) {
@@ -698,10 +709,10 @@ inline unsigned grid_for(size_t n, int sms, int per_sm = 8) {
 cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(b.ctr, 0, sizeof(SegCounters), s);
     if (e != cudaSuccess) return e;
-    k_brick_flags<<<grid_for(nb_total, sms), kT, 0, s>>>(brick_table, nb_total, b.flags);
+    launch_k(k_brick_flags, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags);
     e = exclusive_scan_u32(b.flags, b.flags, &b.ctr->n_sorted, nb_total, b.scan_tmp, s, &b.ctr->err);
     if (e != cudaSuccess) return e;
-    k_brick_compact<<<grid_for(nb_total, sms), kT, 0, s>>>(brick_table, nb_total, b.flags, b.rank_table,
+    launch_k(k_brick_compact, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags, b.rank_table,
                                                              b.sorted_slot, b.sorted_key);
     count_launch(2);
     return cudaGetLastError();
@@ -710,11 +721,13 @@ cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegB
 // Flags a segmentation whose brick or cluster count exceeds the scratch it was
 // launched with; the kernels clamp to the scratch, the host regrows and reruns.
 __global__ void k_seg_guard(SegCounters* __restrict__ ctr, uint32_t cap_b) {
+    pdl_gate();
     if (ctr->n_sorted > cap_b) ctr->err |= kErrScratch;
 }
 // Clusters beyond the scratch flag a re-run (the count is clamped for the
 // kernels that follow); cl_off[k] = the number of clustered points.
 __global__ void k_clusters_end(SegCounters* __restrict__ ctr, uint32_t kcap, uint32_t* __restrict__ cl_off) {
+    pdl_gate();
     ctr->k_need = ctr->k;
     if (ctr->k > kcap) {
         ctr->err |= kErrScratch;
@@ -729,42 +742,42 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     const size_t stride = b.nv;
     const uint32_t* nsp = &b.ctr->n_sorted;
     const auto clampg = [&](uint32_t want, uint32_t mx) { return want < mx ? (want ? want : 1u) : mx; };
-    k_seg_guard<<<1, 1, 0, s>>>(b.ctr, cap_b);
+    launch_k(k_seg_guard, dim3(1), dim3(1), 0, s, b.ctr, cap_b);
     VM_STAGE_BEGIN(hk, kStFinalize, s);
-    k_finalize<<<clampg(cap_b, sms * 4), kT, 0, s>>>(nsp, cap_b, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
+    launch_k(k_finalize, dim3(clampg(cap_b, sms * 4)), dim3(kT), 0, s, nsp, cap_b, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
     VM_STAGE_END(hk, kStFinalize, s);
     const uint8_t want = p.classify ? 2 : 1;
     VM_STAGE_BEGIN(hk, kStNormals, s);
-    k_moments<<<clampg(cap_b, sms * 16), kNormT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.M, b.rec,
+    launch_k(k_moments, dim3(clampg(cap_b, sms * 16)), dim3(kNormT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table, b.M, b.rec,
                                                          b.list_idx, b.list_A, b.nbr, stride, b.ctr);
     VM_STAGE_END(hk, kStNormals, s);
     VM_STAGE_BEGIN(hk, kStEigen, s);
-    k_eigen<<<clampg((uint32_t)((b.nv + 255) / 256), sms * 16), 256, 0, s>>>(b.ctr, b.list_idx, b.list_A, b.nbr, b.nrm,
+    launch_k(k_eigen, dim3(clampg((uint32_t)((b.nv + 255) / 256), sms * 16)), dim3(256), 0, s, b.ctr, b.list_idx, b.list_A, b.nbr, b.nrm,
                                                                             b.status, b.rec, stride, p.n_th,
                                                                             p.cos_step);
     VM_STAGE_END(hk, kStEigen, s);
     VM_STAGE_BEGIN(hk, kStCclLocal, s);
-    k_ccl_local<<<clampg(cap_b, sms * 16), kNormT, 0, s>>>(nsp, cap_b, b.rec, b.parent, b.count, stride, want, p.d_th2,
+    launch_k(k_ccl_local, dim3(clampg(cap_b, sms * 16)), dim3(kNormT), 0, s, nsp, cap_b, b.rec, b.parent, b.count, stride, want, p.d_th2,
                                                            p.cos_ccl, err);
     VM_STAGE_END(hk, kStCclLocal, s);
     VM_STAGE_BEGIN(hk, kStCcl, s);
-    k_ccl_cross<<<clampg(cap_b, sms * 16), kCrossT, 0, s>>>(nsp, cap_b, g, b.sorted_key, b.rank_table, b.rec, b.parent,
+    launch_k(k_ccl_cross, dim3(clampg(cap_b, sms * 16)), dim3(kCrossT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table, b.rec, b.parent,
                                                             stride, want, p.d_th2, p.cos_ccl, err);
     VM_STAGE_END(hk, kStCcl, s);
     count_launch(6);
     VM_STAGE_BEGIN(hk, kStClusters, s);
-    k_compress_count<<<grid_for(b.nv, sms), kT, 0, s>>>(nsp, cap_b, b.parent, b.count, b.ctr, err);
+    launch_k(k_compress_count, dim3(grid_for(b.nv, sms)), dim3(kT), 0, s, nsp, cap_b, b.parent, b.count, b.ctr, err);
     const uint32_t min_cl = p.min_cluster ? p.min_cluster : 1u;
     uint32_t* nvert = b.flags;      // per-brick tallies: flags reused for kept vertices,
     uint32_t* nroot = b.vert_flag;  // vert_flag for kept roots,
     uint32_t* rmask = b.cid;        // cid for the kept-root masks (16 words a brick)
     const unsigned bgrid = clampg(cap_b, sms * 4);
-    k_brick_tally<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot, rmask);
+    launch_k(k_brick_tally, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot, rmask);
     cudaError_t e = exclusive_scan_dev(nroot, nroot, &b.ctr->k, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
     e = exclusive_scan_dev(nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
-    k_brick_clusters<<<bgrid, kBrickVox, 0, s>>>(nsp, cap_b, b.parent, b.count, min_cl, nroot, nvert, rmask,
+    launch_k(k_brick_clusters, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nroot, nvert, rmask,
                                                   b.sorted_key, b.cl_size, b.cl_label, kcap, b.keys, b.vals);
     int bits = 1;
     while ((1ull << bits) < kcap && bits < 32) ++bits;
@@ -773,8 +786,8 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     if (e != cudaSuccess) return e;
     e = exclusive_scan_dev(b.cl_size, b.cl_off, &b.ctr->tot, &b.ctr->k, kcap, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
-    k_clusters_end<<<1, 1, 0, s>>>(b.ctr, kcap, b.cl_off);
-    k_gather<<<grid_for(b.nv, sms), kT, 0, s>>>(&b.ctr->n_kept, b.vals, b.vals_alt, &b.ctr->k, bits, b.M, b.nv,
+    launch_k(k_clusters_end, dim3(1), dim3(1), 0, s, b.ctr, kcap, b.cl_off);
+    launch_k(k_gather, dim3(grid_for(b.nv, sms)), dim3(kT), 0, s, &b.ctr->n_kept, b.vals, b.vals_alt, &b.ctr->k, bits, b.M, b.nv,
                                                  b.sorted_key, g, b.pts, b.pt_vid);
     VM_STAGE_END(hk, kStClusters, s);
     count_launch(5);

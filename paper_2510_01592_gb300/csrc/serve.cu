@@ -62,6 +62,7 @@ struct BatchStatus {
 // contributes nothing (the host re-runs it alone).  A batch larger than the
 // arena contributes nothing either and is re-run after the arena grows.
 __global__ void k_batch_prefix(BatchTable* __restrict__ t, uint32_t kcap, uint32_t ncap, uint32_t* __restrict__ kdev) {
+    pdl_gate();
     uint32_t K = 0, N = 0;
     for (uint32_t m = 0; m < t->n_maps; ++m) {
         BatchEntry& e = t->e[m];
@@ -99,6 +100,7 @@ __device__ __forceinline__ uint32_t member_of(const uint32_t* base, uint32_t nm,
 // Concatenates the members' cluster points, offsets and labels into the arena.
 __global__ void __launch_bounds__(kGatherT) k_batch_gather(const BatchTable* __restrict__ t, float* __restrict__ apts,
                                                            uint32_t* __restrict__ aoff, uint32_t* __restrict__ alab) {
+    pdl_gate();
     __shared__ uint32_t sbn[kMaxBatch], sbk[kMaxBatch];
     const uint32_t nm = t->n_maps, N = t->N, K = t->K;
     for (uint32_t m = threadIdx.x; m < nm; m += blockDim.x) {
@@ -130,6 +132,7 @@ __global__ void k_pack_batch(const BatchTable* __restrict__ t, const uint32_t* _
                              const uint32_t* __restrict__ aoff, const uint32_t* __restrict__ alab,
                              const FitCluster* __restrict__ cl, const int2* __restrict__ hull,
                              const uint32_t* __restrict__ hull_off) {
+    pdl_gate();
     __shared__ uint32_t sbk[kMaxBatch];
     const uint32_t nm = t->n_maps, K = *kdev;
     for (uint32_t m = threadIdx.x; m < nm; m += blockDim.x) sbk[m] = t->e[m].base_k;
@@ -148,6 +151,7 @@ __global__ void k_pack_batch(const BatchTable* __restrict__ t, const uint32_t* _
 // writes) and the batch status for the host.
 __global__ void k_batch_header(const BatchTable* __restrict__ t, const uint32_t* __restrict__ hull_off,
                                const uint32_t* __restrict__ fit_err, BatchStatus* __restrict__ st) {
+    pdl_gate();
     const uint32_t m = threadIdx.x;
     if (m < t->n_maps) {
         const BatchEntry& E = t->e[m];
@@ -289,16 +293,16 @@ cudaError_t enqueue_batch(Server* S, int slot) {
     if ((e = cudaMemcpyAsync(b.dtab, b.htab[slot], sizeof(BatchTable), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    k_batch_prefix<<<1, 1, 0, s>>>(b.dtab, b.kcap, b.ncap, fb.kdev);
+    launch_k(k_batch_prefix, dim3(1), dim3(1), 0, s, b.dtab, b.kcap, b.ncap, fb.kdev);
     const unsigned g = (unsigned)(sms * 8);
-    k_batch_gather<<<g, kGatherT, 0, s>>>(b.dtab, b.apts, b.aoff, b.alab);
+    launch_k(k_batch_gather, dim3(g), dim3(kGatherT), 0, s, b.dtab, b.apts, b.aoff, b.alab);
     count_launch(2);
     if ((e = launch_fit(b.apts, b.aoff, b.alab, fb.kdev, b.kcap, S->prm.params, fb, b.tune, sms, s, nullptr)) !=
         cudaSuccess)
         return e;
-    k_pack_batch<<<b.kcap < 4096 ? b.kcap : 4096, 128, 0, s>>>(b.dtab, fb.kdev, b.aoff, b.alab, fb.cl, fb.hull,
+    launch_k(k_pack_batch, dim3(b.kcap < 4096 ? b.kcap : 4096), dim3(128), 0, s, b.dtab, fb.kdev, b.aoff, b.alab, fb.cl, fb.hull,
                                                                   fb.hull_cnt);
-    k_batch_header<<<1, kMaxBatch, 0, s>>>(b.dtab, fb.hull_cnt, fb.err, b.dstat[slot]);
+    launch_k(k_batch_header, dim3(1), dim3(kMaxBatch), 0, s, b.dtab, fb.hull_cnt, fb.err, b.dstat[slot]);
     count_launch(2);
     return cudaGetLastError();
 }

@@ -12,10 +12,44 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 
 #include "../../include/vm.h"
 
 namespace vmx {
+
+// Programmatic dependent launch (sm_90 and later).  Every kernel of the
+// library opens with pdl_gate(): griddepcontrol.wait blocks until the kernel
+// launched before it on the stream has completed and its memory is visible (a
+// no-op for a launch that was not programmatic), then
+// griddepcontrol.launch_dependents lets the next kernel on the stream start
+// launching.  So each launch, and the rasterisation of its CTAs, overlaps the
+// kernel before it instead of following it: in a chain of small kernels (a
+// segmentation is ~40) that gap, not the work, is most of the time.  A kernel
+// touches no global memory before the gate, so ordering is that of plain
+// stream launches.
+__device__ __forceinline__ void pdl_gate() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Whether launch_k marks launches programmatic (on unless the environment
+// variable VOXMPS_PDL is "0"; read once).
+bool pdl_enabled();
+// kernel<<<grid, block, smem, s>>>(args...) as a programmatic launch.
+template <typename... K, typename... A>
+cudaError_t launch_k(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
 
 constexpr int kBrick = 8;
 constexpr int kBrickVox = 512;
