@@ -75,6 +75,10 @@ def lib():
             L.orc_count_occupied.argtypes = [vp]
             L.orc_count_occupied.restype = C.c_uint32
             L.orc_export_sums.argtypes = [vp, C.POINTER(C.c_uint32), C.POINTER(C.c_int64), C.POINTER(C.c_uint32)]
+            L.orc_map_scroll.argtypes = [vp, C.POINTER(C.c_int32)]
+            L.orc_scroll_target.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
+            L.orc_map_window.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_float),
+                                         C.POINTER(C.c_uint64)]
             L.orc_jacobi3_f32.argtypes = [C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_float),
                                           C.POINTER(C.c_float), C.POINTER(C.c_float)]
             L.orc_philox4x64.argtypes = [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
@@ -223,6 +227,38 @@ class OracleMap:
         out = (C.c_uint64 * 2)()
         lib().orc_map_counts(self._h, out)
         return int(out[0]), int(out[1])
+
+    def scroll(self, shift):
+        """Moves the window by whole bricks (shift: 3 ints); voxels whose brick
+        leaves it are evicted."""
+        sh = np.ascontiguousarray(shift, np.int32).reshape(3)
+        st = lib().orc_map_scroll(self._h, sh.ctypes.data_as(C.POINTER(C.c_int32)))
+        if st:
+            raise RuntimeError(f"orc_map_scroll failed: {st}")
+
+    def scroll_target(self, center):
+        """The brick shift that centres the window on center (map frame)."""
+        c = np.ascontiguousarray(center, np.float32).reshape(3)
+        sh = np.zeros(3, np.int32)
+        lib().orc_scroll_target(self._h, _fp(c), sh.ctypes.data_as(C.POINTER(C.c_int32)))
+        return sh
+
+    def scroll_to(self, center):
+        sh = self.scroll_target(center)
+        if sh.any():
+            self.scroll(sh)
+        return sh
+
+    def window(self):
+        """Window offset w (voxels), sum anchor A (2^-20 m units), position
+        origin (map frame) and the occupied voxels evicted so far."""
+        w = np.zeros(3, np.int32)
+        A = np.zeros(3, np.int64)
+        po = np.zeros(3, np.float32)
+        ev = C.c_uint64()
+        lib().orc_map_window(self._h, w.ctypes.data_as(C.POINTER(C.c_int32)), A.ctypes.data_as(C.POINTER(C.c_int64)),
+                             _fp(po), C.byref(ev))
+        return {"offset": w, "anchor": A, "position_origin": po, "voxels_evicted": int(ev.value)}
 
     def export_sums(self):
         n = lib().orc_count_occupied(self._h)

@@ -114,12 +114,15 @@ typedef struct {
 typedef struct {
     int32_t nx, ny, nz;
     int32_t nbx, nby, nbz;
-    float ox, oy, oz;
+    float ox, oy, oz;    /* base origin: a point's key is floor((p - origin) * inv_res) */
     float inv_res;
+    int32_t w[3];        /* window: the grid holds keys w .. w + dims - 1 (w a multiple of 8) */
+    int64_t A[3];        /* sums are rint((p - origin) * 2^20) - A, A = anchor(w)          */
+    float po[3];         /* origin of the mean positions: origin + A * 2^-20, rounded        */
     uint64_t nv;
     int64_t *S;      /* [nv][3] */
     uint32_t *C;     /* [nv]    */
-    uint64_t n_in, n_dropped;
+    uint64_t n_in, n_dropped, n_evicted;
     /* last segmentation */
     orc_voxel *vox;  /* occupied voxels in vid order */
     uint32_t n_vox;
@@ -183,6 +186,7 @@ void *orc_map_create(const int32_t dims[3], const float origin[3], float inv_res
     m->nbz = (m->nz + BRICK - 1) / BRICK;
     m->ox = origin[0]; m->oy = origin[1]; m->oz = origin[2];
     m->inv_res = inv_res;
+    m->po[0] = origin[0]; m->po[1] = origin[1]; m->po[2] = origin[2];  /* w = 0: A = 0 */
     m->nv = (uint64_t)m->nbx * (uint64_t)m->nby * (uint64_t)m->nbz * BRICK_VOX;
     if (m->nv > 0xFFFFFFFFull) { free(m); return NULL; }
     m->S = (int64_t *)calloc(m->nv * 3, sizeof(int64_t));
@@ -200,11 +204,13 @@ void orc_map_destroy(void *h)
 
 /* Section III.B, Eq. 1 and the thread-per-point update it describes.
  * Reading: the pose is sensor->map, row-major [R|t]; the transform is the
- * fma chain below; the voxel index is floor(d * inv_res) of the offset d from
- * the map origin; points whose index falls outside the grid (NaN included) are
- * dropped and counted.  Eq. 1's running mean is kept as exact integer sums of
- * rint(d * 2^20) (2^-20 m ~ 0.95 um units) plus a count: the mean it defines
- * is recovered in orc_segment up to that quantum, independent of point order. */
+ * fma chain below; the voxel key is floor(d * inv_res) of the offset d from
+ * the map's base origin, and the grid index is the key minus the window
+ * offset w (0 until the map scrolls); points whose index falls outside the
+ * grid (NaN included) are dropped and counted.  Eq. 1's running mean is kept
+ * as exact integer sums of rint(d * 2^20) - A (2^-20 m ~ 0.95 um units, A
+ * the window's anchor) plus a count: the mean it defines is recovered in
+ * orc_segment up to that quantum, independent of point order. */
 typedef struct { orc_map *m; const float *xyz; const float *pose; } integ_ctx;
 static void integrate_range(void *vc, uint64_t lo, uint64_t hi)
 {
@@ -220,21 +226,28 @@ static void integrate_range(void *vc, uint64_t lo, uint64_t hi)
         float wz = fmaf(pose[10], z, fmaf(pose[9], y, fmaf(pose[8], x, pose[11])));
         float dx = wx - m->ox, dy = wy - m->oy, dz = wz - m->oz;
         float fx = floorf(dx * m->inv_res), fy = floorf(dy * m->inv_res), fz = floorf(dz * m->inv_res);
-        int ok = (fx >= 0.0f) && (fx < (float)m->nx) && (fy >= 0.0f) && (fy < (float)m->ny) &&
-                 (fz >= 0.0f) && (fz < (float)m->nz);
-        uint64_t v = ok ? vid_of(m, (int)fx, (int)fy, (int)fz) : 0;
+        /* the window bounds are integers below 2^24: exact as floats */
+        int ok = (fx >= (float)m->w[0]) && (fx < (float)(m->w[0] + m->nx)) && (fy >= (float)m->w[1]) &&
+                 (fy < (float)(m->w[1] + m->ny)) && (fz >= (float)m->w[2]) && (fz < (float)(m->w[2] + m->nz));
+        uint64_t v = ok ? vid_of(m, (int)fx - m->w[0], (int)fy - m->w[1], (int)fz - m->w[2]) : 0;
+        int64_t F[3] = {0, 0, 0};
+        if (ok) {
+            F[0] = (int64_t)rintf(dx * q) - m->A[0];
+            F[1] = (int64_t)rintf(dy * q) - m->A[1];
+            F[2] = (int64_t)rintf(dz * q) - m->A[2];
+        }
         if (!atomic) {
             if (!ok) { m->n_dropped++; continue; }
-            m->S[3 * v + 0] += (int64_t)rintf(dx * q);
-            m->S[3 * v + 1] += (int64_t)rintf(dy * q);
-            m->S[3 * v + 2] += (int64_t)rintf(dz * q);
+            m->S[3 * v + 0] += F[0];
+            m->S[3 * v + 1] += F[1];
+            m->S[3 * v + 2] += F[2];
             m->C[v] += 1u;
             m->n_in++;
         } else {
             if (!ok) { __atomic_fetch_add(&m->n_dropped, 1, __ATOMIC_RELAXED); continue; }
-            __atomic_fetch_add(&m->S[3 * v + 0], (int64_t)rintf(dx * q), __ATOMIC_RELAXED);
-            __atomic_fetch_add(&m->S[3 * v + 1], (int64_t)rintf(dy * q), __ATOMIC_RELAXED);
-            __atomic_fetch_add(&m->S[3 * v + 2], (int64_t)rintf(dz * q), __ATOMIC_RELAXED);
+            __atomic_fetch_add(&m->S[3 * v + 0], F[0], __ATOMIC_RELAXED);
+            __atomic_fetch_add(&m->S[3 * v + 1], F[1], __ATOMIC_RELAXED);
+            __atomic_fetch_add(&m->S[3 * v + 2], F[2], __ATOMIC_RELAXED);
             __atomic_fetch_add(&m->C[v], 1u, __ATOMIC_RELAXED);
             __atomic_fetch_add(&m->n_in, 1, __ATOMIC_RELAXED);
         }
@@ -262,11 +275,11 @@ int orc_integrate(void *h, const float *xyz, uint64_t n, const float pose[12])
  * advances the axis with the smallest tmax (ties to x, then y, then z) among
  * the axes not yet at the end voxel's coordinate, so the walk reaches the
  * end voxel in exactly |ve - v0| (L1) steps.  Every voxel walked before the
- * end voxel is marked if it lies in the grid; the end voxel (the point's own)
- * is not.  The walk stops once it leaves the grid (a monotone walk does not
- * come back).  A sensor outside the grid casts no rays (a robot-centric map
- * holds its sensor); points that are not finite, or more than 2^30 voxels
- * away, cast no ray.  All marks of the frame are collected first, then the
+ * end voxel is marked if it lies in the grid (its key minus the window
+ * offset w in range); the end voxel (the point's own) is not.  The walk stops
+ * once it leaves the grid (a monotone walk does not come back).  A sensor
+ * outside the grid casts no rays (a robot-centric map holds its sensor);
+ * points that are not finite, or more than 2^30 voxels away, cast no ray.  All marks of the frame are collected first, then the
  * marked voxels are cleared (sums and count to zero); integrating the
  * frame's points follows. */
 typedef struct { orc_map *m; const float *xyz; const float *pose; uint8_t *mark; } clear_ctx;
@@ -319,12 +332,13 @@ static void clear_range(void *vc, uint64_t lo, uint64_t hi)
         for (; left > 0; --left) {
             int inside = 1, gone = 0;
             for (int a = 0; a < 3; ++a) {
-                inside &= v[a] >= 0 && v[a] < dims[a];
-                gone |= (v[a] < 0 && step[a] <= 0) || (v[a] >= dims[a] && step[a] >= 0);
+                const int64_t g = v[a] - m->w[a];
+                inside &= g >= 0 && g < dims[a];
+                gone |= (g < 0 && step[a] <= 0) || (g >= dims[a] && step[a] >= 0);
             }
             if (gone) break;
             if (inside) {
-                const uint64_t vid = vid_of(m, (int)v[0], (int)v[1], (int)v[2]);
+                const uint64_t vid = vid_of(m, (int)(v[0] - m->w[0]), (int)(v[1] - m->w[1]), (int)(v[2] - m->w[2]));
                 if (m->C[vid]) __atomic_store_n(&cx->mark[vid], (uint8_t)1, __ATOMIC_RELAXED);
             }
             int best = -1;
@@ -347,8 +361,9 @@ int orc_clear_rays(void *h, const float *xyz, uint64_t n, const float pose[12], 
     clear_ctx cx = {m, xyz, pose, mark};
     const float sv[3] = {(pose[3] - m->ox) * m->inv_res, (pose[7] - m->oy) * m->inv_res,
                          (pose[11] - m->oz) * m->inv_res};
-    const int sensor_in = sv[0] >= 0.0f && sv[0] < (float)m->nx && sv[1] >= 0.0f && sv[1] < (float)m->ny &&
-                          sv[2] >= 0.0f && sv[2] < (float)m->nz;
+    const int sensor_in = sv[0] >= (float)m->w[0] && sv[0] < (float)(m->w[0] + m->nx) &&
+                          sv[1] >= (float)m->w[1] && sv[1] < (float)(m->w[1] + m->ny) &&
+                          sv[2] >= (float)m->w[2] && sv[2] < (float)(m->w[2] + m->nz);
     if (sensor_in) par_for(n, clear_range, &cx);
     uint64_t k = 0;
     for (uint64_t v = 0; v < m->nv; ++v) {
@@ -367,6 +382,92 @@ void orc_map_counts(void *h, uint64_t out[2])
     orc_map *m = (orc_map *)h;
     out[0] = m->n_in;
     out[1] = m->n_dropped;
+}
+
+/* Robot-centric map (Sec. III.B: the map's centre follows the robot).
+ * Reading: the grid is a window over keys anchored at the base origin, moved
+ * in whole bricks so that every kept voxel keeps its key, its points and its
+ * exact sums; a voxel whose brick leaves the window is dropped (evicted) and
+ * the bricks that enter are empty.  The sums are re-expressed against the
+ * new window's anchor, an integer change: S -= C * (A' - A).  The anchor is
+ * A = floor(w * 2^20 / inv_res) in double (at or below the window's corner
+ * in 2^-20 m units, so sums stay small), and mean positions are
+ * po + M * 2^-20 with po = (float)(origin + A * 2^-20) in double. */
+static int64_t anchor_of(int32_t w, float inv_res)
+{
+    return (int64_t)floor((double)w * 1048576.0 / (double)inv_res);
+}
+
+int orc_map_scroll(void *h, const int32_t shift[3])
+{
+    orc_map *m = (orc_map *)h;
+    if (!m || !shift) return ORC_ERR_INVALID_ARG;
+    int32_t w2[3];
+    for (int a = 0; a < 3; ++a) {
+        const int64_t t = (int64_t)m->w[a] + 8 * (int64_t)shift[a];
+        if (t < -(1 << 23) || t > (1 << 23)) return ORC_ERR_INVALID_ARG;  /* keys stay exact in FP32 */
+        w2[a] = (int32_t)t;
+    }
+    int64_t A2[3], dA[3];
+    for (int a = 0; a < 3; ++a) {
+        A2[a] = anchor_of(w2[a], m->inv_res);
+        dA[a] = A2[a] - m->A[a];
+    }
+    int64_t *S2 = (int64_t *)calloc(m->nv * 3, sizeof(int64_t));
+    uint32_t *C2 = (uint32_t *)calloc(m->nv, sizeof(uint32_t));
+    if (!S2 || !C2) { free(S2); free(C2); return ORC_ERR_OUT_OF_MEMORY; }
+    /* every voxel of the old window: keep it if its key is in the new window */
+    for (uint64_t v = 0; v < m->nv; ++v) {
+        if (!m->C[v]) continue;
+        int32_t ijk[3];
+        ijk_of(m, v, ijk);
+        int keep = 1;
+        int32_t g[3];
+        for (int a = 0; a < 3; ++a) {
+            g[a] = ijk[a] + m->w[a] - w2[a];
+            keep &= g[a] >= 0 && g[a] < (a == 0 ? m->nx : a == 1 ? m->ny : m->nz);
+        }
+        if (!keep) { m->n_evicted++; continue; }
+        const uint64_t u = vid_of(m, g[0], g[1], g[2]);
+        for (int a = 0; a < 3; ++a) S2[3 * u + a] = m->S[3 * v + a] - (int64_t)m->C[v] * dA[a];
+        C2[u] = m->C[v];
+    }
+    free(m->S); free(m->C);
+    m->S = S2; m->C = C2;
+    const float o[3] = {m->ox, m->oy, m->oz};
+    for (int a = 0; a < 3; ++a) {
+        m->w[a] = w2[a];
+        m->A[a] = A2[a];
+        m->po[a] = (float)((double)o[a] + (double)A2[a] / 1048576.0);
+    }
+    return ORC_OK;
+}
+
+/* The brick shift that centres the window on c (map frame): the key of c,
+ * floor((c - origin) * inv_res) in FP32 as a point is keyed, minus half the
+ * grid, rounded down to a whole brick, is the new window offset. */
+void orc_scroll_target(void *h, const float c[3], int32_t shift[3])
+{
+    orc_map *m = (orc_map *)h;
+    const float o[3] = {m->ox, m->oy, m->oz};
+    const int32_t n[3] = {m->nx, m->ny, m->nz};
+    for (int a = 0; a < 3; ++a) {
+        const int64_t key = (int64_t)floorf((c[a] - o[a]) * m->inv_res);
+        int64_t t = key - n[a] / 2;
+        t = (t >= 0 ? t / 8 : -((-t + 7) / 8));  /* floor(t / 8) */
+        shift[a] = (int32_t)(t - m->w[a] / 8);
+    }
+}
+
+void orc_map_window(void *h, int32_t w[3], int64_t A[3], float po[3], uint64_t *evicted)
+{
+    orc_map *m = (orc_map *)h;
+    for (int a = 0; a < 3; ++a) {
+        if (w) w[a] = m->w[a];
+        if (A) A[a] = m->A[a];
+        if (po) po[a] = m->po[a];
+    }
+    if (evicted) *evicted = m->n_evicted;
 }
 
 /* Occupied voxels in vid order with their sums and counts. */
@@ -946,7 +1047,7 @@ void *orc_segment(void *h, const orc_params *prm)
     int32_t *occ_index = (int32_t *)malloc(m->nv * sizeof(int32_t));
     if (!m->vox || !occ_index) { free(occ_index); return NULL; }
     const float iq = 9.5367431640625e-07f; /* 2^-20 */
-    const float o[3] = {m->ox, m->oy, m->oz};
+    const float o[3] = {m->po[0], m->po[1], m->po[2]};  /* the window's position origin */
     uint32_t k = 0;
     for (uint64_t v = 0; v < m->nv; ++v) {
         occ_index[v] = -1;
