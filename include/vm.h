@@ -116,6 +116,7 @@ typedef struct {
     uint32_t clustered_points;   /* points in kept clusters at the last segmentation */
     uint64_t device_bytes;       /* device memory held by the map                 */
     uint64_t voxels_cleared;     /* voxels cleared by ray casting since creation / reset */
+    uint64_t voxels_evicted;     /* occupied voxels evicted by vm_scroll since creation / reset */
 } vm_stats;
 
 /* Create a map.  params: see vm_map_params.  cuda_stream: a cudaStream_t the
@@ -165,8 +166,35 @@ vm_status vm_segment(vm_map* map, const vm_segment_params* params, vm_planes* ou
 /* Free the host arrays of a vm_planes and zero it.  NULL members are fine. */
 vm_status vm_planes_free(vm_planes* planes);
 
-/* Clear the map (every voxel free) without releasing memory. */
+/* Clear the map (every voxel free) without releasing memory; the window
+ * (below) stays where it is. */
 vm_status vm_reset(vm_map* map);
+
+/* Robot-centric map (Sec. III.B: the map's centre follows the robot).  A
+ * point's key is floor((p - origin) * inv_res) from the map's fixed base
+ * origin (vm_map_params.origin); the grid of dims voxels is a window over
+ * keys offset..offset + dims - 1, offset a multiple of 8 per axis (whole
+ * bricks), 0 at creation.  vm_scroll moves the window by shift_bricks[3]
+ * bricks: voxels whose brick leaves it are evicted (counted in vm_stats),
+ * the bricks that enter are empty, and every kept voxel keeps its key, its
+ * points and its exact sums.  Voxel ids (labels, exports) are window
+ * coordinates, so they change with the window; planes and hulls stay in the
+ * map frame.  The offset must stay within +-2^23 voxels (keys exact in
+ * FP32): VM_ERR_INVALID_ARG otherwise, the window unchanged.  Sums exported
+ * by vm_export_voxels are relative to the window's anchor, 2^-20 m units:
+ * the mean position is position_origin + (sums / count) * 2^-20.  Precision
+ * of keys and sums is that of FP32 offsets from the base origin (about 1 um
+ * at 16 m, 8 um at 128 m).  Asynchronous on the map's stream; no graph is
+ * re-captured.
+ * vm_scroll_target: the shift that centres the window on center[3] (map
+ * frame): the new offset is the centre's key minus dims / 2, rounded down to
+ * a multiple of 8.  vm_scroll_to: vm_scroll_target then vm_scroll (shift may
+ * be NULL).  vm_get_window: the offset (voxels) and position origin (map
+ * frame); either may be NULL. */
+vm_status vm_scroll(vm_map* map, const int32_t shift_bricks[3]);
+vm_status vm_scroll_target(vm_map* map, const float center[3], int32_t shift_bricks[3]);
+vm_status vm_scroll_to(vm_map* map, const float center[3], int32_t shift_bricks[3]);
+vm_status vm_get_window(vm_map* map, int32_t offset_voxels[3], float position_origin[3]);
 
 /* Destroy a map and release its device memory; waits for its stream. */
 vm_status vm_destroy(vm_map* map);

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of libvoxmps.so (include/vm.h): map lifecycle, device
 // scratch management and the host-side ordering of the kernels of one call.
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -299,7 +300,8 @@ uint64_t map_footprint(const vm_map_params& p, const vm_segment_params& sp) {
     uint64_t nb = 1;
     for (int a = 0; a < 3; ++a) nb *= (uint64_t)((p.dims[a] + kBrick - 1) / kBrick);
     const uint64_t cap = p.brick_capacity && p.brick_capacity < nb ? p.brick_capacity : nb;
-    const uint64_t pool = nb * 4 + cap * 4 + cap * kBrickVox * (3 * 8 + 4) + cap * (kBrickVox / 8) + 4096;
+    const uint64_t pool = nb * 4 + cap * 4 + cap * kBrickVox * (3 * 8 + 4) + cap * (kBrickVox / 8) +
+                          scroll_tmp_words((uint32_t)cap) * 4 + 4096;
     const uint64_t bricks = (nb + 1) * 4 + nb * 4 + cap * 8 + 4096;
     const size_t nv = (size_t)cap * kBrickVox;
     Carver dry{nullptr};
@@ -680,6 +682,8 @@ vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out
     g.nbz = (g.nz + kBrick - 1) / kBrick;
     g.ox = p.origin[0]; g.oy = p.origin[1]; g.oz = p.origin[2];
     g.inv_res = (float)(1.0 / (double)p.voxel_size);
+    g.wx = g.wy = g.wz = 0;  // the window starts at the base origin (anchor 0)
+    g.ax = g.ay = g.az = 0;
     const unsigned long long nb = (unsigned long long)g.nbx * g.nby * g.nbz;
     if (nb * kBrickVox > 0xFFFFFFFFull) {
         delete m;
@@ -708,6 +712,8 @@ vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out
     dry.take<MapCounters>(1);
     dry.take<uint32_t>((size_t)m->capacity * (kBrickVox / 32));
     dry.take<uint32_t>(4);
+    dry.take<uint32_t>(scroll_tmp_words(m->capacity));
+    dry.take<float>(4);
     vm_status st = ensure(m->pool, dry.off + 256);
     if (st != VM_OK) {
         vm_destroy(m);
@@ -721,6 +727,9 @@ vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out
     m->ctr = c.take<MapCounters>(1);
     m->mark = c.take<uint32_t>((size_t)m->capacity * (kBrickVox / 32));
     m->err = c.take<uint32_t>(4);
+    m->scroll_tmp = c.take<uint32_t>(scroll_tmp_words(m->capacity));
+    m->po_dev = c.take<float>(4);
+    g.po = m->po_dev;
     // brick-level segmentation arrays
     Carver bd{nullptr};
     bd.take<uint32_t>((size_t)m->nb_total + 1);
@@ -745,6 +754,13 @@ vm_status vm_create(const vm_map_params* params, void* cuda_stream, vm_map** out
         return cuda_status(e, "cudaMallocHost");
     }
     st = vm_reset(m);
+    if (st == VM_OK) {
+        const float po[4] = {g.ox, g.oy, g.oz, 0.0f};
+        e = cudaMemsetAsync(m->scroll_tmp, 0, scroll_tmp_words(m->capacity) * sizeof(uint32_t), m->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(m->po_dev, po, sizeof(po), cudaMemcpyHostToDevice, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) st = cuda_status(e, "map initialisation");
+    }
     if (st != VM_OK) {
         vm_destroy(m);
         return st;
@@ -761,6 +777,83 @@ vm_status vm_reset(vm_map* m) {
     VM_CUDA(cudaMemsetAsync(m->ctr, 0, sizeof(MapCounters), m->stream));
     VM_CUDA(cudaMemsetAsync(m->mark, 0, (size_t)m->capacity * (kBrickVox / 32) * sizeof(uint32_t), m->stream));
     m->segmented = false;
+    return VM_OK;
+}
+
+// The window's anchor in 2^-20 m units: at or below its corner, so the sums
+// of the voxels inside stay small and non-negative.
+static long long window_anchor(int w, float inv_res) {
+    return (long long)floor((double)w * 1048576.0 / (double)inv_res);
+}
+
+vm_status vm_scroll(vm_map* m, const int32_t shift[3]) {
+    VM_TRY(check_map(m));
+    if (!shift) {
+        set_error("null shift");
+        return VM_ERR_INVALID_ARG;
+    }
+    if (!shift[0] && !shift[1] && !shift[2]) return VM_OK;
+    Grid g2 = m->g;
+    const int w[3] = {m->g.wx, m->g.wy, m->g.wz};
+    int w2[3];
+    for (int a = 0; a < 3; ++a) {
+        const long long t = (long long)w[a] + 8ll * (long long)shift[a];
+        if (t < -(1ll << 23) || t > (1ll << 23)) {
+            set_error("window offset beyond 2^23 voxels (keys must stay exact in FP32)");
+            return VM_ERR_INVALID_ARG;
+        }
+        w2[a] = (int)t;
+    }
+    g2.wx = w2[0]; g2.wy = w2[1]; g2.wz = w2[2];
+    g2.ax = window_anchor(w2[0], g2.inv_res);
+    g2.ay = window_anchor(w2[1], g2.inv_res);
+    g2.az = window_anchor(w2[2], g2.inv_res);
+    const float po2[3] = {(float)((double)g2.ox + (double)g2.ax / 1048576.0),
+                          (float)((double)g2.oy + (double)g2.ay / 1048576.0),
+                          (float)((double)g2.oz + (double)g2.az / 1048576.0)};
+    VM_CUDA(launch_scroll(m->g, g2, shift, po2, m->brick_table, m->nb_total, m->slot_key, m->S, m->C, m->ctr,
+                          m->capacity, m->scroll_tmp, m->stream));
+    m->g = g2;
+    return VM_OK;
+}
+
+vm_status vm_scroll_target(vm_map* m, const float center[3], int32_t shift[3]) {
+    VM_TRY(check_map(m));
+    if (!center || !shift) {
+        set_error("null argument");
+        return VM_ERR_INVALID_ARG;
+    }
+    const float o[3] = {m->g.ox, m->g.oy, m->g.oz};
+    const int n[3] = {m->g.nx, m->g.ny, m->g.nz}, w[3] = {m->g.wx, m->g.wy, m->g.wz};
+    for (int a = 0; a < 3; ++a) {
+        const float f = floorf((center[a] - o[a]) * m->g.inv_res);  // the centre's key, keyed as a point is
+        if (!(fabsf(f) < 8388608.0f)) {
+            set_error("window centre not finite or beyond 2^23 voxels");
+            return VM_ERR_INVALID_ARG;
+        }
+        long long t = (long long)f - n[a] / 2;
+        t = t >= 0 ? t / 8 : -((-t + 7) / 8);  // floor(t / 8): the new offset in bricks
+        shift[a] = (int32_t)(t - w[a] / 8);
+    }
+    return VM_OK;
+}
+
+vm_status vm_scroll_to(vm_map* m, const float center[3], int32_t shift[3]) {
+    int32_t sh[3];
+    VM_TRY(vm_scroll_target(m, center, sh));
+    if (shift) memcpy(shift, sh, sizeof(sh));
+    return vm_scroll(m, sh);
+}
+
+vm_status vm_get_window(vm_map* m, int32_t offset[3], float position_origin[3]) {
+    VM_TRY(check_map(m));
+    const int w[3] = {m->g.wx, m->g.wy, m->g.wz};
+    const long long A[3] = {m->g.ax, m->g.ay, m->g.az};
+    const float o[3] = {m->g.ox, m->g.oy, m->g.oz};
+    for (int a = 0; a < 3; ++a) {
+        if (offset) offset[a] = w[a];
+        if (position_origin) position_origin[a] = (float)((double)o[a] + (double)A[a] / 1048576.0);
+    }
     return VM_OK;
 }
 
@@ -977,6 +1070,7 @@ vm_status vm_get_stats(vm_map* m, vm_stats* out) {
     out->clusters = m->last.k;
     out->clustered_points = m->last.n_kept;
     out->voxels_cleared = c.cleared;
+    out->voxels_evicted = c.evicted;
     out->device_bytes = m->pool.bytes + m->stage.bytes + m->brick_mem.bytes + m->vox_mem.bytes + m->fit.mem.bytes +
                         m->fit.out.bytes;
     (void)0;

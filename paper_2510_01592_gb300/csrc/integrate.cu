@@ -4,9 +4,14 @@
 // Storage: a direct-indexed brick table (one int32 per 8^3-voxel brick of the
 // grid) maps a brick to a slot of a pool allocated on first touch.  A slot
 // holds, per voxel, the exact fixed-point coordinate sums S (int64, 2^-20 m
-// units relative to the map origin) and the point count C.  Eq. 1's running
-// mean is the ratio S / C, independent of the order the points arrive in, so
-// concurrent updates need only integer atomics.
+// units relative to the window's anchor) and the point count C.  Eq. 1's
+// running mean is the ratio S / C, independent of the order the points arrive
+// in, so concurrent updates need only integer atomics.
+//
+// The grid is a window over voxel keys floor((p - origin) * inv_res) taken
+// from the map's fixed base origin (Sec. III.B: the map's centre follows the
+// robot): the window moves in whole bricks (launch_scroll), so a voxel keeps
+// its key, its points and its exact sums for as long as it stays inside.
 //
 // Two launches per frame, both reading the frame's points (the second read is
 // served from L2):
@@ -42,15 +47,16 @@ __device__ __forceinline__ Keyed key_point(const float* __restrict__ xyz, uint32
     const float fx = floorf(__fmul_rn(dx, g.inv_res));
     const float fy = floorf(__fmul_rn(dy, g.inv_res));
     const float fz = floorf(__fmul_rn(dz, g.inv_res));
-    k.ok = (fx >= 0.0f) & (fx < (float)g.nx) & (fy >= 0.0f) & (fy < (float)g.ny) & (fz >= 0.0f) &
-           (fz < (float)g.nz);
+    // window bounds: integers below 2^24, exact as floats
+    k.ok = (fx >= (float)g.wx) & (fx < (float)(g.wx + g.nx)) & (fy >= (float)g.wy) & (fy < (float)(g.wy + g.ny)) &
+           (fz >= (float)g.wz) & (fz < (float)(g.wz + g.nz));
     if (k.ok) {
-        const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
+        const int ix = (int)fx - g.wx, iy = (int)fy - g.wy, iz = (int)fz - g.wz;
         k.brick = ((uint32_t)(iz >> 3) * (uint32_t)g.nby + (uint32_t)(iy >> 3)) * (uint32_t)g.nbx + (uint32_t)(ix >> 3);
         k.local = (uint32_t)((((iz & 7) << 3) | (iy & 7)) << 3 | (ix & 7));
-        k.F[0] = (int32_t)__float2ll_rn(__fmul_rn(dx, 1048576.0f));
-        k.F[1] = (int32_t)__float2ll_rn(__fmul_rn(dy, 1048576.0f));
-        k.F[2] = (int32_t)__float2ll_rn(__fmul_rn(dz, 1048576.0f));
+        k.F[0] = (int32_t)(__float2ll_rn(__fmul_rn(dx, 1048576.0f)) - g.ax);
+        k.F[1] = (int32_t)(__float2ll_rn(__fmul_rn(dy, 1048576.0f)) - g.ay);
+        k.F[2] = (int32_t)(__float2ll_rn(__fmul_rn(dz, 1048576.0f)) - g.az);
     } else {
         k.brick = kNone;
         k.local = 0;
@@ -160,6 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
     const float s[3] = {__fmul_rn(__fsub_rn(P.r[3], g.ox), g.inv_res), __fmul_rn(__fsub_rn(P.r[7], g.oy), g.inv_res),
                         __fmul_rn(__fsub_rn(P.r[11], g.oz), g.inv_res)};
     const int dims[3] = {g.nx, g.ny, g.nz};
+    const long long w[3] = {g.wx, g.wy, g.wz};
     const long long cap = (long long)g.nx + g.ny + g.nz + 3;  // a walk inside the grid is never longer
     for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         const float x = xyz[3 * (size_t)i + 0], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
@@ -202,12 +209,13 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
             bool inside = true, gone = false;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                inside &= v[a] >= 0 && v[a] < dims[a];
-                gone |= (v[a] < 0 && step[a] <= 0) || (v[a] >= dims[a] && step[a] >= 0);
+                const long long q = v[a] - w[a];  // window coordinate
+                inside &= q >= 0 && q < dims[a];
+                gone |= (q < 0 && step[a] <= 0) || (q >= dims[a] && step[a] >= 0);
             }
             if (gone) break;
             if (inside) {
-                const int ix = (int)v[0], iy = (int)v[1], iz = (int)v[2];
+                const int ix = (int)(v[0] - w[0]), iy = (int)(v[1] - w[1]), iz = (int)(v[2] - w[2]);
                 const uint32_t brick =
                     ((uint32_t)(iz >> 3) * (uint32_t)g.nby + (uint32_t)(iy >> 3)) * (uint32_t)g.nbx + (uint32_t)(ix >> 3);
                 const int32_t slot = table[brick];
@@ -260,7 +268,151 @@ __global__ void __launch_bounds__(kThreads) k_clear_apply(unsigned long long* __
     if ((threadIdx.x & 31) == 0 && cleared) atomicAdd(&ctr->cleared, (unsigned long long)cleared);
 }
 
+// ---------------------------------------------------------------- scrolling
+// keep[s] = 1 when allocated slot s's brick lies in the window moved by
+// (sx, sy, sz) bricks.
+__global__ void k_scroll_keep(const int32_t* __restrict__ slot_key, const MapCounters* __restrict__ ctr,
+                              uint32_t capacity, int sx, int sy, int sz, int nbx, int nby, int nbz,
+                              uint32_t* __restrict__ keep) {
+    pdl_gate();
+    const uint32_t nb = min(ctr->n_bricks, capacity);
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < nb; s += gridDim.x * kThreads) {
+        const int b = slot_key[s];
+        const int bx = b % nbx - sx, by = (b / nbx) % nby - sy, bz = b / (nbx * nby) - sz;
+        keep[s] = (bx >= 0 && bx < nbx && by >= 0 && by < nby && bz >= 0 && bz < nbz) ? 1u : 0u;
+    }
+}
+
+// hole[r] = the r-th slot below the kept count that is not kept.
+__global__ void k_scroll_holes(const MapCounters* __restrict__ ctr, uint32_t capacity,
+                               const uint32_t* __restrict__ keep, const uint32_t* __restrict__ kpos,
+                               const uint32_t* __restrict__ n_keep, uint32_t* __restrict__ hole) {
+    pdl_gate();
+    const uint32_t nk = *n_keep;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < nk; s += gridDim.x * kThreads)
+        if (!keep[s]) hole[s - kpos[s]] = s;
+}
+
+// Occupied voxels of the evicted slots (one CTA per slot; before the move
+// overwrites them).
+__global__ void __launch_bounds__(kThreads) k_scroll_count(const uint32_t* __restrict__ keep, uint32_t capacity,
+                                                          const uint32_t* __restrict__ C,
+                                                          MapCounters* __restrict__ ctr) {
+    pdl_gate();
+    const uint32_t nb = min(ctr->n_bricks, capacity);
+    uint32_t occ = 0;
+    for (uint32_t s = blockIdx.x; s < nb; s += gridDim.x) {
+        if (keep[s]) continue;
+        for (int l = threadIdx.x; l < kBrickVox; l += kThreads) occ += C[(size_t)s * kBrickVox + l] != 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) occ += __shfl_xor_sync(0xffffffffu, occ, o);
+    if ((threadIdx.x & 31) == 0 && occ) atomicAdd(&ctr->evicted, (unsigned long long)occ);
+}
+
+// One CTA per slot: a kept slot below the kept count stays and a kept slot
+// above it moves into the hole of the same rank (holes are evicted slots, read
+// by nothing here); either way its sums are re-anchored (S - C da) and its key
+// shifted into the new window.
+__global__ void __launch_bounds__(kThreads) k_scroll_move(const MapCounters* __restrict__ ctr, uint32_t capacity,
+                                                         const uint32_t* __restrict__ keep,
+                                                         const uint32_t* __restrict__ kpos,
+                                                         const uint32_t* __restrict__ n_keep,
+                                                         const uint32_t* __restrict__ hole, int32_t* slot_key,
+                                                         int shift_key, long long dax, long long day, long long daz,
+                                                         unsigned long long* S, uint32_t* C) {
+    pdl_gate();
+    const uint32_t nb = min(ctr->n_bricks, capacity), nk = *n_keep;
+    const uint32_t below = nk < nb ? kpos[nk] : nk;  // kept slots below the kept count
+    for (uint32_t s = blockIdx.x; s < nb; s += gridDim.x) {
+        if (!keep[s]) continue;
+        const uint32_t* cs = C + (size_t)s * kBrickVox;
+        const uint32_t d = s < nk ? s : hole[kpos[s] - below];
+        const unsigned long long* ss = S + (size_t)s * 3 * kBrickVox;
+        unsigned long long* sd = S + (size_t)d * 3 * kBrickVox;
+        uint32_t* cd = C + (size_t)d * kBrickVox;
+        for (int l = threadIdx.x; l < kBrickVox; l += kThreads) {
+            const uint32_t c = cs[l];
+            const long long cc = (long long)c;
+            sd[l] = (unsigned long long)((long long)ss[l] - cc * dax);
+            sd[kBrickVox + l] = (unsigned long long)((long long)ss[kBrickVox + l] - cc * day);
+            sd[2 * kBrickVox + l] = (unsigned long long)((long long)ss[2 * kBrickVox + l] - cc * daz);
+            cd[l] = c;
+        }
+        if (threadIdx.x == 0) slot_key[d] = slot_key[s] - shift_key;
+    }
+}
+
+// Zeroes the slots from the kept count to the old count (their bricks moved
+// or were evicted) so they can be claimed again.
+__global__ void k_scroll_zero(const uint32_t* __restrict__ n_keep, const MapCounters* __restrict__ ctr,
+                              uint32_t capacity, unsigned long long* S, uint32_t* C) {
+    pdl_gate();
+    const size_t lo = (size_t)*n_keep * kBrickVox, hi = (size_t)min(ctr->n_bricks, capacity) * kBrickVox;
+    for (size_t i = lo + (size_t)blockIdx.x * kThreads + threadIdx.x; i < hi; i += (size_t)gridDim.x * kThreads) {
+        const size_t slot = i / kBrickVox, l = i % kBrickVox;
+        S[slot * 3 * kBrickVox + l] = 0;
+        S[slot * 3 * kBrickVox + kBrickVox + l] = 0;
+        S[slot * 3 * kBrickVox + 2 * kBrickVox + l] = 0;
+        C[i] = 0;
+    }
+}
+
+// The brick table of the new window (cleared before), the new brick count
+// and the new position origin.
+__global__ void k_scroll_table(const uint32_t* __restrict__ n_keep, const int32_t* __restrict__ slot_key,
+                               int32_t* __restrict__ table, MapCounters* __restrict__ ctr, float* __restrict__ po,
+                               float px, float py, float pz) {
+    pdl_gate();
+    const uint32_t nk = *n_keep;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < nk; s += gridDim.x * kThreads) table[slot_key[s]] = (int32_t)s;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->n_bricks = nk;
+        po[0] = px;
+        po[1] = py;
+        po[2] = pz;
+    }
+}
+
 }  // namespace
+
+size_t scroll_tmp_words(uint32_t capacity) {
+    return 3 * (size_t)capacity + 64 + scan_tmp_words((size_t)capacity + 1);
+}
+
+cudaError_t launch_scroll(const Grid& g, const Grid& g2, const int32_t shift[3], const float po2[3],
+                          int32_t* brick_table, uint32_t nb_total, int32_t* slot_key, unsigned long long* S,
+                          uint32_t* C, MapCounters* ctr, uint32_t capacity, uint32_t* tmp, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint32_t* keep = tmp;
+    uint32_t* kpos = keep + capacity;
+    uint32_t* hole = kpos + capacity;
+    uint32_t* word = hole + capacity;  // [0] kept count, [1] the old count
+    uint32_t* scan_state = word + 64;
+    const unsigned gs = (unsigned)((capacity + kThreads - 1) / kThreads < (uint32_t)sms * 8
+                                       ? (capacity + kThreads - 1) / kThreads
+                                       : (uint32_t)sms * 8);
+    const int shift_key = (shift[2] * g.nby + shift[1]) * g.nbx + shift[0];
+    launch_k(k_scroll_keep, dim3(gs), dim3(kThreads), 0, s, slot_key, ctr, capacity, shift[0], shift[1], shift[2],
+             g.nbx, g.nby, g.nbz, keep);
+    cudaError_t e = exclusive_scan_dev(keep, kpos, word, &ctr->n_bricks, capacity, scan_state, s, nullptr);
+    if (e != cudaSuccess) return e;
+    launch_k(k_scroll_holes, dim3(gs), dim3(kThreads), 0, s, ctr, capacity, keep, kpos, word, hole);
+    const unsigned gm = capacity < (uint32_t)sms * 8 ? capacity : (uint32_t)sms * 8;
+    launch_k(k_scroll_count, dim3(gm), dim3(kThreads), 0, s, keep, capacity, C, ctr);
+    launch_k(k_scroll_move, dim3(gm), dim3(kThreads), 0, s, ctr, capacity, keep, kpos, word, hole, slot_key, shift_key,
+             g2.ax - g.ax, g2.ay - g.ay, g2.az - g.az, S, C);
+    const size_t zw = ((size_t)capacity * kBrickVox + kThreads - 1) / kThreads;
+    launch_k(k_scroll_zero, dim3((unsigned)(zw < (size_t)sms * 8 ? zw : (size_t)sms * 8)), dim3(kThreads), 0, s, word,
+             ctr, capacity, S, C);
+    if ((e = cudaMemsetAsync(brick_table, 0xFF, (size_t)nb_total * sizeof(int32_t), s)) != cudaSuccess) return e;
+    launch_k(k_scroll_table, dim3(gs), dim3(kThreads), 0, s, word, slot_key, brick_table, ctr,
+             const_cast<float*>(g2.po), po2[0], po2[1], po2[2]);
+    count_launch(6);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_clear(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, const int32_t* brick_table,
                          unsigned long long* S, uint32_t* C, uint32_t* mark, MapCounters* ctr, uint32_t capacity,
@@ -268,7 +420,8 @@ cudaError_t launch_clear(const float* xyz, uint32_t n, const Pose& pose, const G
     // A sensor outside the grid casts no rays (host check, same arithmetic as the walk's start).
     const float sx = (pose.r[3] - g.ox) * g.inv_res, sy = (pose.r[7] - g.oy) * g.inv_res,
                 sz = (pose.r[11] - g.oz) * g.inv_res;
-    if (!(sx >= 0.0f && sx < (float)g.nx && sy >= 0.0f && sy < (float)g.ny && sz >= 0.0f && sz < (float)g.nz) ||
+    if (!(sx >= (float)g.wx && sx < (float)(g.wx + g.nx) && sy >= (float)g.wy && sy < (float)(g.wy + g.ny) &&
+          sz >= (float)g.wz && sz < (float)(g.wz + g.nz)) ||
         n == 0)
         return cudaSuccess;
     int dev = 0, sms = 0;

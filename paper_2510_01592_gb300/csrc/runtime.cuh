@@ -137,6 +137,8 @@ struct vm_map {
     vmx::MapCounters* ctr = nullptr;
     uint32_t* err = nullptr;  // segmentation error word
     uint32_t* mark = nullptr; // ray-cast clearing marks, one bit per voxel slot
+    uint32_t* scroll_tmp = nullptr;  // window-scroll scratch (flags, positions, holes, scan state)
+    float* po_dev = nullptr;         // position origin of the window, read by the segmentation
     vmx::DevBuf pool;
     vmx::DevBuf stage;             // host points staged on the device
     // segmentation

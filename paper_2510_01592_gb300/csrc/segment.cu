@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__
                                                     SegCounters* __restrict__ ctr) {
     pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
+    const float pox = g.po[0], poy = g.po[1], poz = g.po[2];
     __shared__ int32_t sM[3][1000];
     __shared__ uint16_t list[512];
     __shared__ int32_t nb[27];
@@ -297,7 +298,7 @@ __global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__
             const size_t o = (size_t)r * kBrickVox + l;
             if (sM[0][c0] != INT_MIN) {
                 list[atomicAdd(&n_list, 1)] = (uint16_t)l;
-                rec[o] = make_float4(mean_pos(g.ox, sM[0][c0]), mean_pos(g.oy, sM[1][c0]), mean_pos(g.oz, sM[2][c0]),
+                rec[o] = make_float4(mean_pos(pox, sM[0][c0]), mean_pos(poy, sM[1][c0]), mean_pos(poz, sM[2][c0]),
                                      __int_as_float(0));
             } else {
                 rec[o] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
@@ -688,11 +689,12 @@ __global__ void k_gather(const uint32_t* __restrict__ np, const uint32_t* __rest
     pdl_gate();
     const uint32_t n = *np;
     const uint32_t* __restrict__ vals = sort_result_alt(*kp, bits) ? vals_alt : vals_main;  // where the sort ended
+    const float pox = g.po[0], poy = g.po[1], poz = g.po[2];
     for (uint32_t p = blockIdx.x * kT + threadIdx.x; p < n; p += gridDim.x * kT) {
         const uint32_t i = vals[p];
-        pts[3 * (size_t)p + 0] = __fadd_rn(g.ox, __fmul_rn(__int2float_rn(M[i]), kInvQ));
-        pts[3 * (size_t)p + 1] = __fadd_rn(g.oy, __fmul_rn(__int2float_rn(M[stride + i]), kInvQ));
-        pts[3 * (size_t)p + 2] = __fadd_rn(g.oz, __fmul_rn(__int2float_rn(M[2 * stride + i]), kInvQ));
+        pts[3 * (size_t)p + 0] = __fadd_rn(pox, __fmul_rn(__int2float_rn(M[i]), kInvQ));
+        pts[3 * (size_t)p + 1] = __fadd_rn(poy, __fmul_rn(__int2float_rn(M[stride + i]), kInvQ));
+        pts[3 * (size_t)p + 2] = __fadd_rn(poz, __fmul_rn(__int2float_rn(M[2 * stride + i]), kInvQ));
         pt_vid[p] = vid_of(i, sorted_key);
     }
 }

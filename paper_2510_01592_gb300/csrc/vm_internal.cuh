@@ -72,8 +72,11 @@ struct Pose {
 struct Grid {
     int nx, ny, nz;
     int nbx, nby, nbz;
-    float ox, oy, oz;
+    float ox, oy, oz;       // base origin: a point's key is floor((p - origin) * inv_res)
     float inv_res;
+    int wx, wy, wz;         // window: the grid holds keys w .. w + n - 1 (multiples of 8)
+    long long ax, ay, az;   // sums are rint((p - origin) * 2^20) - a, a = the window's anchor
+    const float* po;        // device float[3]: origin of the mean positions (origin + a * 2^-20)
 };
 
 // Counters kept in device memory per map.
@@ -84,6 +87,7 @@ struct MapCounters {
     uint32_t n_bricks;   // bricks allocated (may exceed capacity on overflow)
     uint32_t err;        // error bits
     unsigned long long cleared;  // voxels cleared by ray casting (Eq. 2)
+    unsigned long long evicted;  // occupied voxels evicted by scrolling the window
 };
 
 // Counters produced by one segmentation, read back by the host.
@@ -272,6 +276,17 @@ cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys
                                   int bits, uint32_t* tmp, cudaStream_t s, uint32_t* err);
 
 // ---------------------------------------------------------------- integrate.cu
+// Robot-centric window (Sec. III.B): moves the window of g by shift whole
+// bricks (g holds the old window; g2 the new one and its anchor; po2 its
+// position origin).  Bricks that leave are evicted and their occupied voxels
+// counted; the pool is compacted (kept bricks past the new count move into
+// the holes), the kept sums are re-anchored (S -= C (a2 - a)), the table is
+// rebuilt and po2 written to the device copy g2.po.  tmp: scratch of
+// scroll_tmp_words(capacity) words, zeroed once when allocated.
+size_t scroll_tmp_words(uint32_t capacity);
+cudaError_t launch_scroll(const Grid& g, const Grid& g2, const int32_t shift[3], const float po2[3],
+                          int32_t* brick_table, uint32_t nb_total, int32_t* slot_key, unsigned long long* S,
+                          uint32_t* C, MapCounters* ctr, uint32_t capacity, uint32_t* tmp, cudaStream_t s);
 cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, int32_t* brick_table,
                              int32_t* slot_key, unsigned long long* S, uint32_t* C, MapCounters* ctr,
                              uint32_t capacity, cudaStream_t s);

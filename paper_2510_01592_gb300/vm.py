@@ -66,7 +66,7 @@ class vm_stats(C.Structure):
                 ("points_no_capacity", C.c_uint64), ("bricks_allocated", C.c_uint32),
                 ("brick_capacity", C.c_uint32), ("occupied_voxels", C.c_uint32), ("steppable_voxels", C.c_uint32),
                 ("clusters", C.c_uint32), ("clustered_points", C.c_uint32), ("device_bytes", C.c_uint64),
-                ("voxels_cleared", C.c_uint64)]
+                ("voxels_cleared", C.c_uint64), ("voxels_evicted", C.c_uint64)]
 
 
 class vm_fit_tuning(C.Structure):
@@ -101,6 +101,10 @@ _SIGS = {
     "vm_segment": (C.c_int, [C.c_void_p, C.POINTER(vm_segment_params), C.POINTER(vm_planes)]),
     "vm_planes_free": (C.c_int, [C.POINTER(vm_planes)]),
     "vm_reset": (C.c_int, [C.c_void_p]),
+    "vm_scroll": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "vm_scroll_target": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
+    "vm_scroll_to": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int32)]),
+    "vm_get_window": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
     "vm_destroy": (C.c_int, [C.c_void_p]),
     "vm_get_stats": (C.c_int, [C.c_void_p, C.POINTER(vm_stats)]),
     "vm_fit_planes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(vm_segment_params),
@@ -316,6 +320,33 @@ class VoxelMap:
 
     def reset(self):
         _check(load().vm_reset(self._h))
+
+    def scroll(self, shift):
+        """Moves the window by whole bricks (3 ints); voxels whose brick leaves
+        it are evicted."""
+        sh = (C.c_int32 * 3)(*[int(v) for v in np.asarray(shift).reshape(3)])
+        _check(load().vm_scroll(self._h, sh))
+
+    def scroll_target(self, center):
+        """The brick shift that centres the window on center (map frame)."""
+        c = (C.c_float * 3)(*[float(v) for v in np.asarray(center, np.float32).reshape(3)])
+        sh = (C.c_int32 * 3)()
+        _check(load().vm_scroll_target(self._h, c, sh))
+        return np.array(sh[:], np.int32)
+
+    def scroll_to(self, center):
+        """Centres the window on center (map frame); returns the brick shift."""
+        c = (C.c_float * 3)(*[float(v) for v in np.asarray(center, np.float32).reshape(3)])
+        sh = (C.c_int32 * 3)()
+        _check(load().vm_scroll_to(self._h, c, sh))
+        return np.array(sh[:], np.int32)
+
+    def window(self):
+        """Window offset (voxels) and position origin (map frame)."""
+        w = (C.c_int32 * 3)()
+        po = (C.c_float * 3)()
+        _check(load().vm_get_window(self._h, w, po))
+        return {"offset": np.array(w[:], np.int32), "position_origin": np.array(po[:], np.float32)}
 
     def stats(self):
         s = vm_stats()
