@@ -376,8 +376,12 @@ __global__ void k_scroll_table(const uint32_t* __restrict__ n_keep, const int32_
 
 }  // namespace
 
+// Each array of the scratch starts on a 256-byte boundary (the scan's state
+// holds 64-bit words).
+static size_t scroll_stride(uint32_t capacity) { return ((size_t)capacity + 63) & ~(size_t)63; }
+
 size_t scroll_tmp_words(uint32_t capacity) {
-    return 3 * (size_t)capacity + 64 + scan_tmp_words((size_t)capacity + 1);
+    return 3 * scroll_stride(capacity) + 64 + scan_tmp_words((size_t)capacity + 1);
 }
 
 cudaError_t launch_scroll(const Grid& g, const Grid& g2, const int32_t shift[3], const float po2[3],
@@ -386,10 +390,11 @@ cudaError_t launch_scroll(const Grid& g, const Grid& g2, const int32_t shift[3],
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t stride = scroll_stride(capacity);
     uint32_t* keep = tmp;
-    uint32_t* kpos = keep + capacity;
-    uint32_t* hole = kpos + capacity;
-    uint32_t* word = hole + capacity;  // [0] kept count, [1] the old count
+    uint32_t* kpos = keep + stride;
+    uint32_t* hole = kpos + stride;
+    uint32_t* word = hole + stride;  // [0] the kept count
     uint32_t* scan_state = word + 64;
     const unsigned gs = (unsigned)((capacity + kThreads - 1) / kThreads < (uint32_t)sms * 8
                                        ? (capacity + kThreads - 1) / kThreads

@@ -300,6 +300,7 @@ cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* tota
         count_launch(1);
         return cudaGetLastError();
     }
+    if (reinterpret_cast<uintptr_t>(tmp) & 7) return cudaErrorInvalidValue;  // 64-bit status words
     const size_t nt = (n_cap + kScanTile - 1) / kScanTile;
     launch_k(k_scan_lookback, dim3((unsigned)nt), dim3(kScanThreads), 0, s, in, out, n_cap, n_dev, total, tmp, err);
     count_launch(1);

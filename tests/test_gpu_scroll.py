@@ -140,3 +140,22 @@ def test_far_scroll_empties_the_map_and_bad_shifts_are_refused(vmmod):
     assert np.array_equal(m.window()["offset"], w)
     with pytest.raises(vmmod.VmError):
         m.scroll_to((float("nan"), 0.0, 0.0))
+
+
+def test_odd_pool_capacity_above_the_small_scan(orc, vmmod):
+    """An odd brick capacity (16,385: the scroll's scan takes the multi-CTA
+    look-back path, whose state holds 64-bit words) against the oracle."""
+    dims, origin, res = (264, 264, 128), (-6.6, -6.6, -3.2), 0.05
+    gm = vmmod.VoxelMap(dims, origin, res, brick_capacity=16385)
+    om = orc.OracleMap(dims, origin, res)
+    rng = np.random.default_rng(4)
+    eye = np.eye(3, 4, dtype=np.float32).reshape(12)
+    for sh in [None, (10, 0, 0), (-12, 3, 2)]:
+        if sh is not None:
+            gm.scroll(sh)
+            om.scroll(sh)
+        p = (rng.uniform(-1, 1, (200000, 3)) * [3.0, 3.0, 1.5]).astype(np.float32)
+        gm.integrate(p, eye)
+        om.integrate(p)
+        compare_sums(gm, om)
+    assert gm.stats()["voxels_evicted"] == om.window()["voxels_evicted"] > 0
