@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
                                               const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int H, int T,
                                               const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
                                               uint32_t* __restrict__ queue, float eps) {
-    pdl_gate();
+    pdl_wait();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];                // T staged points
     uint32_t* red = reinterpret_cast<uint32_t*>(sp + T);  // [P][G*R]
@@ -942,7 +942,7 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
                                                    const uint32_t* __restrict__ kp, int H, int T,
                                                    const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
                                                    uint32_t* __restrict__ queue, float eps) {
-    pdl_gate();
+    pdl_wait();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];  // [kT / 32][T]
     const int lane = threadIdx.x & 31;
@@ -1010,7 +1010,7 @@ cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* 
     const int G = (H + R - 1) / R;
     const int P = kT / G;
     const size_t smem = (size_t)T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
-    launch_k(k_score<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
+    launch_full(k_score<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
     return cudaGetLastError();
 }
 
@@ -1019,7 +1019,7 @@ cudaError_t launch_score_warp(const float* pts, const uint32_t* off, const uint3
                               int H, int T, const float4* hyp, uint32_t* counts, uint32_t* queue, float eps,
                               int grid, cudaStream_t s) {
     const size_t smem = (size_t)(kT / 32) * T * sizeof(float4);
-    launch_k(k_score_warp<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
+    launch_full(k_score_warp<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
     return cudaGetLastError();
 }
 
@@ -1153,11 +1153,11 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_BEGIN(hk, kStExtract, s);
     launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
     const unsigned igrid = (unsigned)sms * 8;
-    launch_k(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
+    launch_full(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
     const unsigned wgrid0 = (kcap + kT / 32 - 1) / (kT / 32);
     const unsigned wgrid = wgrid0 < (uint32_t)sms * 8 ? wgrid0 : (uint32_t)sms * 8;
     launch_k(k_centroid, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
-    launch_k(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
+    launch_full(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
     VM_STAGE_END(hk, kStExtract, s);
     count_launch(4);
     VM_STAGE_BEGIN(hk, kStHull, s);

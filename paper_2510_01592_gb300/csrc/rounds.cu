@@ -75,19 +75,24 @@ __global__ void k_round_active(const uint32_t* __restrict__ kp, const uint32_t* 
 }
 
 // keep[i] = 1 for the points of active clusters that are not inliers; inl0
-// (round 0 only, else null) keeps the round's inlier flags for export.
+// (round 0 only, else null) keeps the round's inlier flags for export.  One
+// thread per point; its cluster by binary search over the offsets (a few
+// cached steps), so a large cluster does not serialise on one CTA.
 __global__ void __launch_bounds__(kRT) k_round_keep(const uint32_t* __restrict__ kp, const uint32_t* __restrict__ off,
                                                     const uint32_t* __restrict__ act, const uint8_t* __restrict__ inl,
-                                                    uint32_t* __restrict__ keep, uint8_t* __restrict__ inl0) {
+                                                    const uint32_t* __restrict__ npts, uint32_t* __restrict__ keep,
+                                                    uint8_t* __restrict__ inl0) {
     pdl_gate();
-    const uint32_t k = *kp;
-    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
-        const uint32_t a = act[c], o1 = off[c + 1];
-        for (uint32_t i = off[c] + threadIdx.x; i < o1; i += kRT) {
-            const uint8_t v = inl[i];
-            keep[i] = (a && !v) ? 1u : 0u;
-            if (inl0) inl0[i] = v;
+    const uint32_t k = *kp, n = *npts;
+    for (uint32_t i = blockIdx.x * kRT + threadIdx.x; i < n; i += gridDim.x * kRT) {
+        uint32_t lo = 0, hi = k;  // the cluster c with off[c] <= i < off[c + 1]
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (off[mid] <= i) lo = mid; else hi = mid;
         }
+        const uint8_t v = inl[i];
+        keep[i] = (act[lo] && !v) ? 1u : 0u;
+        if (inl0) inl0[i] = v;
     }
 }
 
@@ -229,7 +234,8 @@ cudaError_t launch_rounds(const SegBuffers& b, uint32_t kcap, const vm_segment_p
             launch_k(k_round_active, dim3(gk), dim3(kRT), 0, s, kp, off, fb.cl, minc, rb.act, rb.word + kWordNpts);
             e = exclusive_scan_dev(rb.act, rb.apos, knext, kp, kcap, scan_tmp, s, fb.err);
             if (e != cudaSuccess) return e;
-            launch_k(k_round_keep, dim3(gc), dim3(kRT), 0, s, kp, off, rb.act, fb.inlier, rb.keep, r == 0 ? rb.inl0 : nullptr);
+            launch_k(k_round_keep, dim3(gp), dim3(kRT), 0, s, kp, off, rb.act, fb.inlier, rb.word + kWordNpts, rb.keep,
+                     r == 0 ? rb.inl0 : nullptr);
             e = exclusive_scan_dev(rb.keep, rb.kpos, rb.word + kWordKeep, rb.word + kWordNpts, nv, scan_tmp, s,
                                    fb.err);
             if (e != cudaSuccess) return e;

@@ -27,17 +27,21 @@ namespace vmx {
 // kernel before it instead of following it: in a chain of small kernels (a
 // segmentation is ~40) that gap, not the work, is most of the time.  A kernel
 // touches no global memory before the gate, so ordering is that of plain
-// stream launches.
+// stream launches.  A long, issue-bound kernel that leaves room on its SMs
+// (the persistent RANSAC scoring) waits without the early trigger
+// (pdl_wait): its dependents then launch as it finishes instead of sitting
+// resident beside it for its whole run.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_gate() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    pdl_wait();
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 // Whether launch_k marks launches programmatic (on unless the environment
 // variable VOXMPS_PDL is "0"; read once).
 bool pdl_enabled();
-// kernel<<<grid, block, smem, s>>>(args...) as a programmatic launch.
 template <typename... K, typename... A>
-cudaError_t launch_k(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+cudaError_t launch_as(bool programmatic, void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                      A&&... args) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = grid;
     cfg.blockDim = block;
@@ -47,8 +51,21 @@ cudaError_t launch_k(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, c
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cfg.numAttrs = programmatic && pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
+}
+// kernel<<<grid, block, smem, s>>>(args...) as a programmatic launch.
+template <typename... K, typename... A>
+cudaError_t launch_k(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    return launch_as(true, kernel, grid, block, smem, s, std::forward<A>(args)...);
+}
+// A plain launch, for a kernel whose grid is sized to fill the GPU and whose
+// work is balanced by that placement (the persistent scoring, the chunked
+// extraction passes): launched early beside the kernel before it, its CTAs
+// would land unevenly on the SMs that kernel frees first.
+template <typename... K, typename... A>
+cudaError_t launch_full(void (*kernel)(K...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A&&... args) {
+    return launch_as(false, kernel, grid, block, smem, s, std::forward<A>(args)...);
 }
 
 constexpr int kBrick = 8;

@@ -491,7 +491,7 @@ def stage_times(handle=None):
     calls = (C.c_uint64 * N_STAGES)()
     n = C.c_uint32()
     _check(L.vm_stage_times(handle, ms, calls, N_STAGES, C.byref(n)))
-    return {L.vm_stage_name(i).decode(): (ms[i], int(calls[i])) for i in range(n.value)}
+    return {L.vm_stage_name(i).decode(): (ms[i], int(calls[i])) for i in range(min(n.value, N_STAGES))}
 
 
 def set_fit_stage_timing(enable: bool):
