@@ -902,6 +902,31 @@ def run_gpu(args):
                           "non-inliers); steppable: the paper's clustering, all_occupied: every occupied voxel "
                           "clustered, where clusters join walls and ledges; graph replay"}
 
+    # ---------------- config 1: the single frame (20,000 points, 50 x 50 x 25 map at 0.02 m, 64 hypotheses)
+    spec1, pts1_np, _ = synth.config1()
+    pts1 = torch.from_numpy(pts1_np).to(dev)
+    eye = np.eye(3, 4, dtype=np.float32).reshape(12)
+    p1 = vm.segment_params(n_hyp=64, seed=0)
+    m1 = vm.VoxelMap(spec1.dims, spec1.origin, spec1.voxel_size, stream=stream)
+    for _ in range(5):
+        m1.reset()
+        m1.integrate(pts1, eye)
+        m1.segment(p1)
+    torch.cuda.synchronize()
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(51)]
+    ev1[0].record(stream)
+    for i in range(50):
+        m1.reset()
+        m1.integrate(pts1, eye)
+        n1 = len(m1.segment(p1)["planes"])
+        ev1[i + 1].record(stream)
+    torch.cuda.synchronize()
+    c1 = sorted(ev1[i].elapsed_time(ev1[i + 1]) for i in range(50))
+    config1 = {"frames_per_s": round(50 / (ev1[0].elapsed_time(ev1[-1]) / 1e3), 2), "p50_ms": round(c1[25], 4),
+               "p99_ms": round(c1[49], 4), "planes": n1,
+               "note": "reset + integrate the 20,000-point frame + segment (64 hypotheses) per step, graph replay"}
+    m1.close()
+
     # ---------------- robot-centric map: a 5 m cube at 0.01 m (the paper's mapping volume) centred on the
     # camera before every frame, the same timed steps
     def cam_of(f):
@@ -969,6 +994,7 @@ def run_gpu(args):
                                   "voxels_cleared_per_frame": round(cleared / args.steps, 1),
                                   "note": "the same timed steps with ray-cast clearing (Eq. 2) of every frame's "
                                           "rays before its update; graph replay"},
+                     "config1_single_frame": config1,
                      "multiplane": multiplane,
                      "robot_centric": robot_centric,
                      "graph_frames_per_s": round(value, 2),
@@ -1106,6 +1132,62 @@ def cpu_baseline(budget_s, all_cores=True):
     return out
 
 
+def cpu_baseline_configs(config3_sample_every=20):
+    """The oracle on the other configurations' single units, on the host:
+    config 1 (one frame of 20,000 points into the 50 x 50 x 25 map at 0.02 m,
+    integrate + segment with 64 hypotheses), 1 core and all cores; config 3
+    (the 2,000-cluster batch, H = 256), all cores on the whole batch and 1 core
+    on every config3_sample_every-th cluster, scaled by point-hypothesis tests
+    to the whole batch."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    out = {}
+    spec, pts, _ = synth.config1()
+    prm1 = oracle.make_params(n_hyp=64, seed=0)
+    n = os.cpu_count() or 1
+    for th in (1, n):
+        oracle.set_threads(th)
+        try:
+            ts = []
+            for _ in range(5):
+                om = oracle.OracleMap(spec.dims, spec.origin, spec.voxel_size)
+                t0 = time.perf_counter()
+                om.integrate(pts)
+                om.segment(prm1)
+                ts.append(time.perf_counter() - t0)
+                om.close()
+        finally:
+            oracle.set_threads(1)
+        out.setdefault("config1", {})["ms_1core" if th == 1 else "ms_all_cores"] = round(1e3 * min(ts), 3)
+    out["config1"]["cores"] = n
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    xyz, off, _ = synth.config3_clusters_device(device=dev)
+    xyz, off = xyz.cpu().numpy(), off.cpu().numpy().astype(np.uint32)
+    prm3 = oracle.make_params(n_hyp=256, seed=7)
+    oracle.set_threads(n)
+    try:
+        t0 = time.perf_counter()
+        oracle.fit_planes(xyz, off, prm3)
+        t_all = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    sel = np.arange(0, off.shape[0] - 1, config3_sample_every)
+    sizes = (off[1:] - off[:-1]).astype(np.int64)
+    sub_off = np.concatenate([[0], np.cumsum(sizes[sel])]).astype(np.uint32)
+    sub = np.concatenate([xyz[off[c]:off[c + 1]] for c in sel])
+    t0 = time.perf_counter()
+    oracle.fit_planes(sub, sub_off, prm3, labels=sel.astype(np.uint32))
+    t_one = time.perf_counter() - t0
+    out["config3"] = {"ms_all_cores": round(1e3 * t_all, 1), "cores": n,
+                      "ms_1core_scaled": round(1e3 * t_one * float(sizes.sum()) / float(sizes[sel].sum()), 1),
+                      "sample_1core": f"every {config3_sample_every}th cluster ({len(sel)} clusters, "
+                                      f"{int(sizes[sel].sum())} points) timed on 1 core, scaled by points"}
+    return out
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -1138,6 +1220,7 @@ def main():
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(args.cpu_budget_s)
+            res["cpu_baseline"]["other_configs"] = cpu_baseline_configs()
         if args.stages:
             print(json.dumps(res["stages_ms_per_step"], indent=1), file=sys.stderr)
         print(json.dumps(res))

@@ -205,6 +205,8 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
             left += ve[a] > v[a] ? ve[a] - v[a] : v[a] - ve[a];
         }
         if (left > cap) left = cap;  // the walk leaves the grid first
+        uint32_t cur_brick = kNone;  // the brick of the last step and its slot: one table read per brick crossed
+        int32_t cur_slot = -1;
         for (; left > 0; --left) {
             bool inside = true, gone = false;
 #pragma unroll
@@ -218,7 +220,11 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
                 const int ix = (int)(v[0] - w[0]), iy = (int)(v[1] - w[1]), iz = (int)(v[2] - w[2]);
                 const uint32_t brick =
                     ((uint32_t)(iz >> 3) * (uint32_t)g.nby + (uint32_t)(iy >> 3)) * (uint32_t)g.nbx + (uint32_t)(ix >> 3);
-                const int32_t slot = table[brick];
+                if (brick != cur_brick) {
+                    cur_brick = brick;
+                    cur_slot = table[brick];
+                }
+                const int32_t slot = cur_slot;
                 if (slot >= 0) {
                     const uint32_t idx = (uint32_t)slot * kBrickVox + (uint32_t)((((iz & 7) << 3) | (iy & 7)) << 3 | (ix & 7));
                     const uint32_t bit = 1u << (idx & 31);

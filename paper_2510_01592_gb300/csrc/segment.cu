@@ -479,18 +479,46 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
         __syncthreads();
         load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
         __syncthreads();
-        for (int c = threadIdx.x; c < 1000; c += kCrossT) {
-            const int32_t idx = halo_index(c, nb);
-            float4 bn = make_float4(0.0f, 0.0f, 0.0f, __uint_as_float(kNone));
-            if (idx >= 0) {
-                const float4 a = rec[idx];
-                if (__float_as_int(a.w) >= want) {
-                    sA[c] = a;
-                    bn = rec[stride + idx];
-                    bn.w = __uint_as_float(__ldcg(parent + idx));
+        // Load only the cells a cross-brick edge can touch: the brick's own
+        // cells on the faces forward edges leave through (lx 0 or 7, ly 0 or
+        // 7, lz 7) and the halo cells outside the brick at lz 0..8 (648 of the
+        // 1000); the others are staged as non-vertices.  A thread issues its
+        // record loads four at a time before using them.
+        constexpr int kIt = (1000 + kCrossT - 1) / kCrossT;  // cells per thread
+        constexpr int kGroup = 4;                              // loads in flight per thread
+#pragma unroll 1
+        for (int j0 = 0; j0 < kIt; j0 += kGroup) {
+            int32_t idx[kGroup];
+            float4 a[kGroup];
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                const int c = threadIdx.x + (j0 + j) * kCrossT;
+                idx[j] = -1;
+                if (c < 1000) {
+                    const int gx = c % 10 - 1, gy = (c / 10) % 10 - 1, gz = c / 100 - 1;
+                    const bool inside = gx >= 0 && gx <= 7 && gy >= 0 && gy <= 7 && gz >= 0 && gz <= 7;
+                    const bool source = inside && (gx == 0 || gx == 7 || gy == 0 || gy == 7 || gz == 7);
+                    const bool target = !inside && gz >= 0;
+                    if (source || target) idx[j] = halo_index(c, nb);
+                }
+                a[j] = idx[j] >= 0 ? rec[idx[j]] : make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
+            }
+            float4 bn[kGroup];
+            uint32_t par[kGroup];
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                const bool v = idx[j] >= 0 && __float_as_int(a[j].w) >= want;
+                bn[j] = v ? rec[stride + idx[j]] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                par[j] = v ? __ldcg(parent + idx[j]) : kNone;
+            }
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                const int c = threadIdx.x + (j0 + j) * kCrossT;
+                if (c < 1000) {
+                    sA[c] = a[j];
+                    sB[c] = make_float4(bn[j].x, bn[j].y, bn[j].z, __uint_as_float(par[j]));
                 }
             }
-            sB[c] = bn;
         }
         __syncthreads();
         unsigned long long last = ~0ull;
