@@ -102,6 +102,33 @@ def test_config2_frames(orc, vmmod):
             _check_segment(orc, vmmod, gm, om, op, gp)
 
 
+def test_config2_full_trajectory_checkpoints(orc, vmmod):
+    """The whole 300-frame trajectory at full size, in the bench's launch
+    configuration (graph replays, the autotuned fit schedule, 100 hypotheses),
+    segmented at frames 1, 50, 100, 150, 200, 250 and 300 against the oracle
+    (its independent stages on every host core; their results do not depend
+    on the thread count)."""
+    import os
+    spec = synth.config2_spec()
+    scene = synth.config2_scene()
+    gm = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size)
+    om = orc.OracleMap(spec.dims, spec.origin, spec.voxel_size)
+    op, gp = _params_pair(orc, vmmod, n_hyp=100, seed=0)
+    orc.set_threads(os.cpu_count() or 1)
+    try:
+        for f in range(1, 301):
+            pts, pose = synth.config2_frame(f, scene, device="cuda")
+            gm.integrate(pts, pose)
+            om.integrate(pts.cpu().numpy(), pose)
+            if f == 50:
+                gm.autotune(gp, reps=1)
+            if f in (1, 50, 100, 150, 200, 250, 300):
+                _check_segment(orc, vmmod, gm, om, op, gp)
+    finally:
+        orc.set_threads(1)
+    assert gm.stats()["bricks_allocated"] > 2000
+
+
 def test_host_and_device_inputs_agree(vmmod):
     spec, pts, pose = synth.config1()
     import torch
