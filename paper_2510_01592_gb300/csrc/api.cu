@@ -419,14 +419,13 @@ __global__ void k_header(const SegCounters* __restrict__ ctr, const uint32_t* __
 // The whole segmentation as one fixed launch sequence (every count is read on
 // the device): order bricks, means, normals, clustering, clusters, RANSAC,
 // refit, hull, pack into the mapped result block, header.
-cudaError_t enqueue_front(vm_map* m, const vm_segment_params& p, StageHook* hk) {
+cudaError_t enqueue_front(vm_map* m, const vm_segment_params& p, StageHook* hk, uint32_t* also_zero) {
     cudaStream_t s = m->stream;
     const int sms = device_sms();
     SegBuffers& b = m->seg;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(m->err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     VM_STAGE_BEGIN(hk, kStOrder, s);
-    if ((e = seg_order_bricks(m->brick_table, m->nb_total, b, sms, s)) != cudaSuccess) return e;
+    if ((e = seg_order_bricks(m->brick_table, m->nb_total, b, sms, s, m->err, also_zero)) != cudaSuccess) return e;
     VM_STAGE_END(hk, kStOrder, s);
     return seg_run(m->g, m->S, m->C, p, b, m->kcap, m->err, sms, s, hk);
 }
@@ -437,8 +436,7 @@ cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk
     SegBuffers& b = m->seg;
     FitBuffers& fb = m->fit.fb;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    if ((e = enqueue_front(m, p, hk)) != cudaSuccess) return e;
+    if ((e = enqueue_front(m, p, hk, fb.err)) != cudaSuccess) return e;
     char* d = m->out_dev;
     vm_plane* planes = reinterpret_cast<vm_plane*>(d + out_planes_off());
     int32_t* hull_xy = reinterpret_cast<int32_t*>(d + out_xy_off(m->out_kcap));

@@ -1030,6 +1030,15 @@ __global__ void k_set_end(uint32_t* __restrict__ arr, const uint32_t* __restrict
 
 __global__ void k_set_u32(uint32_t* __restrict__ p, uint32_t v) { pdl_gate(); *p = v; }
 
+// arr[*kp] = *v (the end of the work-item offsets) and the work queue's heads
+// cleared for the scoring that follows.
+__global__ void k_items_end(uint32_t* __restrict__ arr, const uint32_t* __restrict__ kp, const uint32_t* __restrict__ v,
+                            uint32_t* __restrict__ queue) {
+    pdl_gate();
+    if (threadIdx.x == 0) arr[*kp] = *v;
+    if (threadIdx.x < 4) queue[threadIdx.x] = 0;
+}
+
 }  // namespace
 
 FitTuning default_tuning() { return FitTuning{2048, 4, 4, 0}; }
@@ -1116,8 +1125,7 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     launch_k(k_items, dim3(kgrid), dim3(kT), 0, s, off, kp, T, fb.item_off);
     e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s, fb.err);
     if (e != cudaSuccess) return e;
-    launch_k(k_set_end, dim3(1), dim3(1), 0, s, fb.item_off, kp, fb.tot);
-    if ((e = cudaMemsetAsync(fb.queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    launch_k(k_items_end, dim3(1), dim3(32), 0, s, fb.item_off, kp, fb.tot, fb.queue);
     const size_t kh = (size_t)kcap * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
     launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid, fb.counts);
@@ -1293,14 +1301,12 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
     fit_init_attributes();
-    // the work queue starts at zero every call; counts are zeroed by k_hyp
-    if ((e = cudaMemsetAsync(queue, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess)
-        return cuda_status(e, "cudaMemsetAsync");
+    // the work queue starts at zero every call (k_items_end); counts are zeroed by k_hyp
     launch_k(k_set_u32, dim3(1), dim3(1), 0, s, kdev, k);
     launch_k(k_items, dim3((k + kT - 1) / kT), dim3(kT), 0, s, off, kdev, t.tile, item_off);
     if ((e = exclusive_scan_dev(item_off, item_off, total, kdev, k, scan_tmp, s, nullptr)) != cudaSuccess)
         return cuda_status(e, "scan");
-    launch_k(k_set_end, dim3(1), dim3(1), 0, s, item_off, kdev, total);
+    launch_k(k_items_end, dim3(1), dim3(32), 0, s, item_off, kdev, total, queue);
     const size_t kh = (size_t)k * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
     launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, xyz, off, labels, kdev, H, params->seed, 0u, hyp, valid, counts);

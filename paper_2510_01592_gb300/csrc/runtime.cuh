@@ -198,7 +198,7 @@ vm_status launch_front(vm_map* m, const vm_segment_params& p);
 bool take_hints(vm_map* m);
 // Front half of a segmentation (brick order .. cluster points), fit, pack +
 // header into the map's result block; the whole call.
-cudaError_t enqueue_front(vm_map* m, const vm_segment_params& p, StageHook* hk);
+cudaError_t enqueue_front(vm_map* m, const vm_segment_params& p, StageHook* hk, uint32_t* also_zero = nullptr);
 cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk);
 // Launches the map's segmentation on its stream (graph replay when enabled)
 // without waiting; finish_segment waits, re-runs with grown scratch when a

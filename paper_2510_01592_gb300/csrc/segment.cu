@@ -29,8 +29,21 @@ __device__ __forceinline__ void brick_coords(int32_t key, const Grid& g, int& bx
     bz = key / (g.nbx * g.nby);
 }
 
-__global__ void k_brick_flags(const int32_t* __restrict__ table, uint32_t nb, uint32_t* __restrict__ flags) {
+// Also clears the segmentation's counters and error words (block 0): the
+// first kernel of a segmentation does it instead of separate memsets, so the
+// launches that follow chain programmatically from the start.
+__global__ void k_brick_flags(const int32_t* __restrict__ table, uint32_t nb, uint32_t* __restrict__ flags,
+                              SegCounters* __restrict__ ctr, uint32_t* __restrict__ zero0,
+                              uint32_t* __restrict__ zero1) {
     pdl_gate();
+    if (blockIdx.x == 0) {
+        uint32_t* w = reinterpret_cast<uint32_t*>(ctr);
+        for (int i = threadIdx.x; i < (int)(sizeof(SegCounters) / 4); i += kT) w[i] = 0;
+        if (threadIdx.x == 0) {
+            if (zero0) *zero0 = 0;
+            if (zero1) *zero1 = 0;
+        }
+    }
     for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < nb; i += gridDim.x * kT) flags[i] = table[i] >= 0;
 }
 
@@ -736,11 +749,11 @@ inline unsigned grid_for(size_t n, int sms, int per_sm = 8) {
 
 }  // namespace
 
-cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(b.ctr, 0, sizeof(SegCounters), s);
-    if (e != cudaSuccess) return e;
-    launch_k(k_brick_flags, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags);
-    e = exclusive_scan_u32(b.flags, b.flags, &b.ctr->n_sorted, nb_total, b.scan_tmp, s, &b.ctr->err);
+cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s,
+                             uint32_t* zero0, uint32_t* zero1) {
+    launch_k(k_brick_flags, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags, b.ctr, zero0,
+             zero1);
+    cudaError_t e = exclusive_scan_u32(b.flags, b.flags, &b.ctr->n_sorted, nb_total, b.scan_tmp, s, &b.ctr->err);
     if (e != cudaSuccess) return e;
     launch_k(k_brick_compact, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags, b.rank_table,
                                                              b.sorted_slot, b.sorted_key);

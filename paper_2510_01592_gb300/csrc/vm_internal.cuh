@@ -352,8 +352,10 @@ struct SegBuffers {
 };
 
 // Orders the allocated bricks by key (rank table, sorted slots/keys); the
-// brick count lands in b.ctr->n_sorted.
-cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s);
+// brick count lands in b.ctr->n_sorted.  Clears b.ctr first, and the device
+// words zero0 / zero1 (either may be null).
+cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s,
+                             uint32_t* zero0 = nullptr, uint32_t* zero1 = nullptr);
 // Means, normals, classification, clustering, cluster numbering, the cluster
 // point lists in cluster order and their offsets, for the bricks ordered by
 // seg_order_bricks.  Every count is read on the device (clamped to the
