@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
         for (int d = 0; d < kFiltDirs; ++d) ext[d] = 0;
         bool big = false;
         uint32_t j = 0;  // chunk within the item; its slot is it * cpt + j (item_off[c] * cpt + its chunk in the cluster)
-        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {
+#pragma unroll 4
+        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {  // unrolled: later chunks' loads go out early
             const uint32_t q = q0 + threadIdx.x;
             float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // count, sum (p - o)
             if (q < end) {
@@ -434,7 +435,8 @@ __global__ void k_centroid(const uint32_t* __restrict__ off, const uint32_t* __r
         df2 sx{0.0f, 0.0f}, sy{0.0f, 0.0f}, sz{0.0f, 0.0f};
         uint32_t n = 0;
         const uint32_t base = item_off[c] * cpt, nch = (off[c + 1] - off[c] + kChunk - 1) / kChunk;
-        for (uint32_t j = lane; j < nch; j += 32) {
+#pragma unroll 4
+        for (uint32_t j = lane; j < nch; j += 32) {  // unrolled: the next chunks' loads overlap this one's adds
             const float* pp = part + (size_t)(base + j) * 10;
             n += (uint32_t)pp[0];
             sx = df_add(sx, df2{pp[1], 0.0f});
@@ -470,7 +472,10 @@ __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b) {
 
 // Covariance partials about the centroid, and the 16-gon filter: inliers
 // strictly inside the polygon through the 16 extreme inliers cannot be hull
-// vertices; the others are appended to the cluster's survivor list.
+// vertices; the others are appended to the cluster's survivor list.  Each
+// warp gathers its survivors in shared memory and reserves room in the list
+// with one atomic per kSurvBuf survivors (usually one per work item) instead
+// of one returned atomic per chunk on the loop's critical path.
 __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                                const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int T,
                                                FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
@@ -478,9 +483,12 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
                                                int2* __restrict__ surv) {
     pdl_gate();
     const uint32_t k = *kp;
+    constexpr int kSurvBuf = 128;
     __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 6];
     __shared__ int2 poly[kFiltDirs + 1];
     __shared__ int npoly;
+    __shared__ int2 sbuf[kT / 32][kSurvBuf];
+    int2* sb = sbuf[threadIdx.x >> 5];
     const uint32_t n_items = item_off[k];
     const int lane = threadIdx.x & 31;
     const uint32_t cpt = (uint32_t)T / kChunk;
@@ -514,8 +522,18 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
         __syncthreads();
         const int m = npoly;
         const float cx = cen[6 * c], cy = cen[6 * c + 2], cz = cen[6 * c + 4];  // nearest floats of the centroid
+        int cnt = 0;  // survivors in this warp's buffer (warp-uniform)
+        auto flush = [&]() {
+            uint32_t pos = 0;
+            if (lane == 0) pos = atomicAdd(&cl[c].n_surv, (uint32_t)cnt);
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            for (int i = lane; i < cnt; i += 32) surv[base + pos + i] = sb[i];
+            __syncwarp();
+            cnt = 0;
+        };
         uint32_t j = 0;
-        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {
+#pragma unroll 4
+        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {  // unrolled: later chunks' loads go out early
             const uint32_t q = q0 + threadIdx.x;
             bool keep = false;
             int2 xy = make_int2(0, 0);
@@ -533,12 +551,13 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
                 }
             }
             const uint32_t b = __ballot_sync(0xffffffffu, keep);
-            uint32_t pos = 0;
-            if (lane == 0 && b) pos = atomicAdd(&cl[c].n_surv, (uint32_t)__popc(b));
-            pos = __shfl_sync(0xffffffffu, pos, 0);
-            if (keep) surv[base + pos + __popc(b & ((1u << lane) - 1u))] = xy;
+            if (cnt + __popc(b) > kSurvBuf) flush();
+            if (keep) sb[cnt + __popc(b & ((1u << lane) - 1u))] = xy;
+            cnt += __popc(b);
+            __syncwarp();
             warp_park<6>(v, wp, j);
         }
+        if (cnt) flush();
         chunks_out<6>(wp, j, part + (size_t)it * cpt * 10, 4);
     }
 }
@@ -566,6 +585,7 @@ __global__ void k_refit(const uint32_t* __restrict__ off, const uint32_t* __rest
 #pragma unroll
         for (int e = 0; e < 6; ++e) A[e] = df2{0.0f, 0.0f};
         const uint32_t base = item_off[c] * cpt, nch = (off[c + 1] - off[c] + kChunk - 1) / kChunk;
+#pragma unroll 4
         for (uint32_t j = lane; j < nch; j += 32)
 #pragma unroll
             for (int e = 0; e < 6; ++e) A[e] = df_add(A[e], df2{part[(size_t)(base + j) * 10 + 4 + e], 0.0f});

@@ -23,18 +23,17 @@ struct FitHeader {
     uint32_t err;        // kErr* bits
 };
 
-// Rejects a batch whose point count exceeds the scratch: every later kernel
-// then sees zero clusters, and the host grows the scratch and runs again.
+// Starts the fit's error word and rejects a batch whose point count exceeds
+// the scratch: every later kernel then sees zero clusters, and the host grows
+// the scratch and runs again.
 __global__ void k_fit_guard(const uint32_t* __restrict__ off, uint32_t* __restrict__ kdev, uint32_t ncap,
                             uint32_t* __restrict__ err, uint32_t* __restrict__ n_out) {
     pdl_gate();
     const uint32_t k = *kdev;
     const uint32_t n = off[k];
     *n_out = n;
-    if (n > ncap) {
-        atomicOr(err, kErrScratch);
-        *kdev = 0;
-    }
+    *err = n > ncap ? kErrScratch : 0u;
+    if (n > ncap) *kdev = 0;
 }
 
 __global__ void k_fit_header(const uint32_t* __restrict__ kdev, const uint32_t* __restrict__ n_pts,
@@ -127,7 +126,6 @@ cudaError_t enqueue_fit(vm_fit_plan* f, const float* x, const uint32_t* off, con
     FitBuffers& fb = f->fc.fb;
     const uint32_t kcap = (uint32_t)f->fc.kcap;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(fb.kdev, f->k_host, sizeof(uint32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;
     launch_k(k_fit_guard, dim3(1), dim3(1), 0, s, off, fb.kdev, (uint32_t)f->fc.npts, fb.err, fb.tot + 2);

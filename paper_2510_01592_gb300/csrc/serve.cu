@@ -61,8 +61,10 @@ struct BatchStatus {
 // Batch offsets of every member; a member whose front half ran out of scratch
 // contributes nothing (the host re-runs it alone).  A batch larger than the
 // arena contributes nothing either and is re-run after the arena grows.
-__global__ void k_batch_prefix(BatchTable* __restrict__ t, uint32_t kcap, uint32_t ncap, uint32_t* __restrict__ kdev) {
+__global__ void k_batch_prefix(BatchTable* __restrict__ t, uint32_t kcap, uint32_t ncap, uint32_t* __restrict__ kdev,
+                               uint32_t* __restrict__ fit_err) {
     pdl_gate();
+    *fit_err = 0;  // the batch fit's error word starts clear
     uint32_t K = 0, N = 0;
     for (uint32_t m = 0; m < t->n_maps; ++m) {
         BatchEntry& e = t->e[m];
@@ -292,8 +294,7 @@ cudaError_t enqueue_batch(Server* S, int slot) {
     const int sms = device_sms();
     if ((e = cudaMemcpyAsync(b.dtab, b.htab[slot], sizeof(BatchTable), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;
-    if ((e = cudaMemsetAsync(fb.err, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-    launch_k(k_batch_prefix, dim3(1), dim3(1), 0, s, b.dtab, b.kcap, b.ncap, fb.kdev);
+    launch_k(k_batch_prefix, dim3(1), dim3(1), 0, s, b.dtab, b.kcap, b.ncap, fb.kdev, fb.err);
     const unsigned g = (unsigned)(sms * 8);
     launch_k(k_batch_gather, dim3(g), dim3(kGatherT), 0, s, b.dtab, b.apts, b.aoff, b.alab);
     count_launch(2);
