@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
     const float s[3] = {__fmul_rn(__fsub_rn(P.r[3], g.ox), g.inv_res), __fmul_rn(__fsub_rn(P.r[7], g.oy), g.inv_res),
                         __fmul_rn(__fsub_rn(P.r[11], g.oz), g.inv_res)};
     const int dims[3] = {g.nx, g.ny, g.nz};
-    const long long w[3] = {g.wx, g.wy, g.wz};
+    const int w0 = g.wx, w1 = g.wy, w2 = g.wz;
     const long long cap = (long long)g.nx + g.ny + g.nz + 3;  // a walk inside the grid is never longer
     for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         const float x = xyz[3 * (size_t)i + 0], y = xyz[3 * (size_t)i + 1], z = xyz[3 * (size_t)i + 2];
@@ -181,64 +181,71 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
 #pragma unroll
         for (int a = 0; a < 3; ++a) fin &= isfinite(e[a]) && fabsf(e[a]) < 1073741824.0f;
         if (!fin) continue;
-        long long v[3], ve[3], left = 0;
-        int step[3];
-        float tmax[3], tdel[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            v[a] = (long long)floorf(s[a]);
-            ve[a] = (long long)floorf(e[a]);
-            const float d = __fsub_rn(e[a], s[a]);
+        // Per-axis state in scalars (an array indexed by the chosen axis would
+        // live in local memory).  Keys fit in int32: the sensor is inside the
+        // grid and |e| < 2^30.
+        int v0, v1, v2, e0i, e1i, e2i, st0, st1, st2;
+        float t0, t1, t2, dl0, dl1, dl2;
+        auto axis = [](float sa, float ea, int& va, int& vea, int& sta, float& ta, float& dla) {
+            va = (int)floorf(sa);
+            vea = (int)floorf(ea);
+            const float d = __fsub_rn(ea, sa);
             if (d > 0.0f) {
-                step[a] = 1;
-                tmax[a] = __fdiv_rn(__fsub_rn(__ll2float_rn(v[a] + 1), s[a]), d);
-                tdel[a] = __fdiv_rn(1.0f, d);
+                sta = 1;
+                ta = __fdiv_rn(__fsub_rn(__int2float_rn(va + 1), sa), d);
+                dla = __fdiv_rn(1.0f, d);
             } else if (d < 0.0f) {
-                step[a] = -1;
-                tmax[a] = __fdiv_rn(__fsub_rn(__ll2float_rn(v[a]), s[a]), d);
-                tdel[a] = __fdiv_rn(-1.0f, d);
+                sta = -1;
+                ta = __fdiv_rn(__fsub_rn(__int2float_rn(va), sa), d);
+                dla = __fdiv_rn(-1.0f, d);
             } else {
-                step[a] = 0;
-                tmax[a] = __int_as_float(0x7f800000);
-                tdel[a] = __int_as_float(0x7f800000);
+                sta = 0;
+                ta = __int_as_float(0x7f800000);
+                dla = __int_as_float(0x7f800000);
             }
-            left += ve[a] > v[a] ? ve[a] - v[a] : v[a] - ve[a];
-        }
-        if (left > cap) left = cap;  // the walk leaves the grid first
+        };
+        axis(s[0], e[0], v0, e0i, st0, t0, dl0);
+        axis(s[1], e[1], v1, e1i, st1, t1, dl1);
+        axis(s[2], e[2], v2, e2i, st2, t2, dl2);
+        const long long l64 = llabs((long long)e0i - v0) + llabs((long long)e1i - v1) + llabs((long long)e2i - v2);
+        int left = (int)(l64 < cap ? l64 : cap);  // the walk leaves the grid first
         uint32_t cur_brick = kNone;  // the brick of the last step and its slot: one table read per brick crossed
         int32_t cur_slot = -1;
         for (; left > 0; --left) {
-            bool inside = true, gone = false;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const long long q = v[a] - w[a];  // window coordinate
-                inside &= q >= 0 && q < dims[a];
-                gone |= (q < 0 && step[a] <= 0) || (q >= dims[a] && step[a] >= 0);
-            }
+            const int q0 = v0 - w0, q1 = v1 - w1, q2 = v2 - w2;  // window coordinates
+            const bool gone = (q0 < 0 && st0 <= 0) || (q0 >= dims[0] && st0 >= 0) || (q1 < 0 && st1 <= 0) ||
+                              (q1 >= dims[1] && st1 >= 0) || (q2 < 0 && st2 <= 0) || (q2 >= dims[2] && st2 >= 0);
             if (gone) break;
-            if (inside) {
-                const int ix = (int)(v[0] - w[0]), iy = (int)(v[1] - w[1]), iz = (int)(v[2] - w[2]);
+            if (q0 >= 0 && q0 < dims[0] && q1 >= 0 && q1 < dims[1] && q2 >= 0 && q2 < dims[2]) {
                 const uint32_t brick =
-                    ((uint32_t)(iz >> 3) * (uint32_t)g.nby + (uint32_t)(iy >> 3)) * (uint32_t)g.nbx + (uint32_t)(ix >> 3);
+                    ((uint32_t)(q2 >> 3) * (uint32_t)g.nby + (uint32_t)(q1 >> 3)) * (uint32_t)g.nbx + (uint32_t)(q0 >> 3);
                 if (brick != cur_brick) {
                     cur_brick = brick;
                     cur_slot = table[brick];
                 }
-                const int32_t slot = cur_slot;
-                if (slot >= 0) {
-                    const uint32_t idx = (uint32_t)slot * kBrickVox + (uint32_t)((((iz & 7) << 3) | (iy & 7)) << 3 | (ix & 7));
+                if (cur_slot >= 0) {
+                    const uint32_t idx =
+                        (uint32_t)cur_slot * kBrickVox + (uint32_t)((((q2 & 7) << 3) | (q1 & 7)) << 3 | (q0 & 7));
                     const uint32_t bit = 1u << (idx & 31);
                     if (C[idx] && !(__ldcg(mark + (idx >> 5)) & bit)) atomicOr(mark + (idx >> 5), bit);
                 }
             }
+            // the axis whose next boundary comes first, ties to x, then y, then z, among those not at the end
             int best = -1;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                if (v[a] == ve[a]) continue;
-                if (best < 0 || tmax[a] < tmax[best]) best = a;
+            float bt = 0.0f;
+            if (v0 != e0i) { best = 0; bt = t0; }
+            if (v1 != e1i && (best < 0 || t1 < bt)) { best = 1; bt = t1; }
+            if (v2 != e2i && (best < 0 || t2 < bt)) best = 2;
+            if (best == 0) {
+                v0 += st0;
+                t0 = __fadd_rn(t0, dl0);
+            } else if (best == 1) {
+                v1 += st1;
+                t1 = __fadd_rn(t1, dl1);
+            } else {
+                v2 += st2;
+                t2 = __fadd_rn(t2, dl2);
             }
-            v[best] += step[best];
-            tmax[best] = __fadd_rn(tmax[best], tdel[best]);
         }
     }
 }
