@@ -483,8 +483,12 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
                                                        uint32_t* err) {
     pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
-    __shared__ float4 sA[1000];
-    __shared__ float4 sB[1000];  // (normal, parent); parent kNone off the vertex set
+    // The halo at z 0..8 only (forward edges never reach z -1): 10 x 10 x 9
+    // cells, cell c = halo cell c + 100.  Means without the status word (a
+    // vertex is a cell whose parent is not kNone): 27 KB a CTA, 8 CTAs an SM.
+    constexpr int kCells = 900;
+    __shared__ float3 sA[kCells];
+    __shared__ float4 sB[kCells];  // (normal, parent); parent kNone off the vertex set
     __shared__ unsigned long long set[kPairSlots];
     __shared__ int32_t nb[27];
     for (int q = threadIdx.x; q < kPairSlots; q += kCrossT) set[q] = ~0ull;
@@ -495,10 +499,10 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
         // Load only the cells a cross-brick edge can touch: the brick's own
         // cells on the faces forward edges leave through (lx 0 or 7, ly 0 or
         // 7, lz 7) and the halo cells outside the brick at lz 0..8 (648 of the
-        // 1000); the others are staged as non-vertices.  A thread issues its
+        // 900); the others are staged as non-vertices.  A thread issues its
         // record loads four at a time before using them.
-        constexpr int kIt = (1000 + kCrossT - 1) / kCrossT;  // cells per thread
-        constexpr int kGroup = 4;                              // loads in flight per thread
+        constexpr int kIt = (kCells + kCrossT - 1) / kCrossT;  // cells per thread
+        constexpr int kGroup = 4;                               // loads in flight per thread
 #pragma unroll 1
         for (int j0 = 0; j0 < kIt; j0 += kGroup) {
             int32_t idx[kGroup];
@@ -507,12 +511,12 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
             for (int j = 0; j < kGroup; ++j) {
                 const int c = threadIdx.x + (j0 + j) * kCrossT;
                 idx[j] = -1;
-                if (c < 1000) {
-                    const int gx = c % 10 - 1, gy = (c / 10) % 10 - 1, gz = c / 100 - 1;
-                    const bool inside = gx >= 0 && gx <= 7 && gy >= 0 && gy <= 7 && gz >= 0 && gz <= 7;
+                if (c < kCells) {
+                    const int h = c + 100;  // the 10 x 10 x 10 halo index
+                    const int gx = h % 10 - 1, gy = (h / 10) % 10 - 1, gz = h / 100 - 1;
+                    const bool inside = gx >= 0 && gx <= 7 && gy >= 0 && gy <= 7 && gz <= 7;
                     const bool source = inside && (gx == 0 || gx == 7 || gy == 0 || gy == 7 || gz == 7);
-                    const bool target = !inside && gz >= 0;
-                    if (source || target) idx[j] = halo_index(c, nb);
+                    if (source || !inside) idx[j] = halo_index(h, nb);
                 }
                 a[j] = idx[j] >= 0 ? rec[idx[j]] : make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
             }
@@ -527,8 +531,8 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
 #pragma unroll
             for (int j = 0; j < kGroup; ++j) {
                 const int c = threadIdx.x + (j0 + j) * kCrossT;
-                if (c < 1000) {
-                    sA[c] = a[j];
+                if (c < kCells) {
+                    sA[c] = make_float3(a[j].x, a[j].y, a[j].z);
                     sB[c] = make_float4(bn[j].x, bn[j].y, bn[j].z, __uint_as_float(par[j]));
                 }
             }
@@ -538,8 +542,9 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
         for (int l = threadIdx.x; l < kBrickVox; l += kCrossT) {
             const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
             if (!((lx == 0) | (lx == 7) | (ly == 0) | (ly == 7) | (lz == 7))) continue;
-            const int c0 = ((lz + 1) * 10 + ly + 1) * 10 + lx + 1;
-            const float4 a = sA[c0], an = sB[c0];
+            const int c0 = (lz * 10 + ly + 1) * 10 + lx + 1;
+            const float3 a = sA[c0];
+            const float4 an = sB[c0];
             const uint32_t pa = __float_as_uint(an.w);
             if (pa == kNone) continue;
             for (int k = 0; k < 13; ++k) {
@@ -551,7 +556,7 @@ __global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restric
                 const float4 bn = sB[c];
                 const uint32_t pb = __float_as_uint(bn.w);
                 if (pb == kNone || pb == pa) continue;
-                const float4 b = sA[c];
+                const float3 b = sA[c];
                 if (!ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
                     continue;
                 const uint32_t lo = pa < pb ? pa : pb, hi = pa < pb ? pb : pa;
@@ -781,6 +786,12 @@ __global__ void k_clusters_end(SegCounters* __restrict__ ctr, uint32_t kcap, uin
 
 cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* C, const vm_segment_params& p,
                     SegBuffers& b, uint32_t kcap, uint32_t* err, int sms, cudaStream_t s, StageHook* hk) {
+    static bool attributes_set = false;
+    if (!attributes_set) {  // the cross-brick pass fits 8 CTAs an SM only with the largest shared-memory split
+        cudaFuncSetAttribute(k_ccl_cross, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+        attributes_set = true;
+    }
     const uint32_t cap_b = (uint32_t)(b.nv / kBrickVox);
     const size_t stride = b.nv;
     const uint32_t* nsp = &b.ctr->n_sorted;
