@@ -295,14 +295,32 @@ __global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__
         if (threadIdx.x == 0) n_list = 0;
         load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
         __syncthreads();
-        for (int c = threadIdx.x; c < 1000; c += kNormT) {
-            const int32_t idx = halo_index(c, nb);
-            if (idx >= 0) {
-                sM[0][c] = M[idx];
-                sM[1][c] = M[stride + idx];
-                sM[2][c] = M[2 * stride + idx];
-            } else {
-                sM[0][c] = INT_MIN;
+        // the 10^3 halo of means, each thread's loads issued four cells at a time
+        constexpr int kIt = (1000 + kNormT - 1) / kNormT, kGroup = 4;
+#pragma unroll 1
+        for (int j0 = 0; j0 < kIt; j0 += kGroup) {
+            int32_t idx[kGroup], m[kGroup][3];
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                const int c = threadIdx.x + (j0 + j) * kNormT;
+                idx[j] = c < 1000 ? halo_index(c, nb) : -1;
+                if (idx[j] >= 0) {
+                    m[j][0] = M[idx[j]];
+                    m[j][1] = M[stride + idx[j]];
+                    m[j][2] = M[2 * stride + idx[j]];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                const int c = threadIdx.x + (j0 + j) * kNormT;
+                if (c >= 1000) continue;
+                if (idx[j] >= 0) {
+                    sM[0][c] = m[j][0];
+                    sM[1][c] = m[j][1];
+                    sM[2][c] = m[j][2];
+                } else {
+                    sM[0][c] = INT_MIN;
+                }
             }
         }
         __syncthreads();
@@ -389,7 +407,7 @@ __global__ void __launch_bounds__(256) k_eigen(const SegCounters* __restrict__ c
 // inside the brick with a union-find in shared memory; the global parent of
 // each vertex is set to its local root (the smallest index of its in-brick
 // component).  Edges that leave the brick follow in k_ccl_cross.
-__global__ void __launch_bounds__(kNormT) k_ccl_local(const uint32_t* __restrict__ nsp, uint32_t cap_b,
+__global__ void __launch_bounds__(kNormT, 8) k_ccl_local(const uint32_t* __restrict__ nsp, uint32_t cap_b,
                                                       const float4* __restrict__ rec, uint32_t* __restrict__ parent,
                                                       uint32_t* __restrict__ count, size_t stride, uint8_t want,
                                                       float d_th2, float cos_ccl, uint32_t* err) {
@@ -400,13 +418,22 @@ __global__ void __launch_bounds__(kNormT) k_ccl_local(const uint32_t* __restrict
     __shared__ uint32_t lpar[512];
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
         __syncthreads();
-        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
-            const size_t o = (size_t)r * kBrickVox + l;
-            const float4 a = rec[o];
-            sA[l] = a;
-            const bool vert = __float_as_int(a.w) >= want;
-            if (vert) sB[l] = rec[stride + o];
-            lpar[l] = vert ? (uint32_t)l : kNone;
+        {  // the brick's records, all of a thread's loads in flight together
+            constexpr int kIt = kBrickVox / kNormT;
+            float4 a[kIt], bn[kIt];
+#pragma unroll
+            for (int j = 0; j < kIt; ++j) a[j] = rec[(size_t)r * kBrickVox + threadIdx.x + j * kNormT];
+#pragma unroll
+            for (int j = 0; j < kIt; ++j)
+                if (__float_as_int(a[j].w) >= want) bn[j] = rec[stride + (size_t)r * kBrickVox + threadIdx.x + j * kNormT];
+#pragma unroll
+            for (int j = 0; j < kIt; ++j) {
+                const int l = threadIdx.x + j * kNormT;
+                const bool vert = __float_as_int(a[j].w) >= want;
+                sA[l] = a[j];
+                if (vert) sB[l] = bn[j];
+                lpar[l] = vert ? (uint32_t)l : kNone;
+            }
         }
         __syncthreads();
         // Runs along +x first, without atomics: each 8-voxel row lies in one
