@@ -76,16 +76,24 @@ __global__ void __launch_bounds__(kT) k_finalize(const uint32_t* __restrict__ ns
     uint32_t occ = 0;
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
         const int32_t slot = sorted_slot[r];
-        for (int l = threadIdx.x; l < kBrickVox; l += kT) {
-            const uint32_t c = C[(size_t)slot * kBrickVox + l];
-            const size_t o = (size_t)r * kBrickVox + l;
-            if (c) {
-                const long long c2 = 2ll * (long long)c;
+        constexpr int kIt = kBrickVox / kT;
+        uint32_t c[kIt];
+        long long sv[kIt][3];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const long long s = (long long)S[((size_t)slot * 3 + a) * kBrickVox + l];
-                    M[a * stride + o] = (int32_t)((2ll * s + (long long)c) / c2);
-                }
+        for (int j = 0; j < kIt; ++j) c[j] = C[(size_t)slot * kBrickVox + threadIdx.x + j * kT];
+#pragma unroll
+        for (int j = 0; j < kIt; ++j)  // a thread's sums loaded together
+            if (c[j])
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    sv[j][a] = (long long)S[((size_t)slot * 3 + a) * kBrickVox + threadIdx.x + j * kT];
+#pragma unroll
+        for (int j = 0; j < kIt; ++j) {
+            const size_t o = (size_t)r * kBrickVox + threadIdx.x + j * kT;
+            if (c[j]) {
+                const long long c2 = 2ll * (long long)c[j];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) M[a * stride + o] = (int32_t)((2ll * sv[j][a] + (long long)c[j]) / c2);
                 status[o] = 1;
                 ++occ;
             } else {
@@ -825,7 +833,7 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     const auto clampg = [&](uint32_t want, uint32_t mx) { return want < mx ? (want ? want : 1u) : mx; };
     launch_k(k_seg_guard, dim3(1), dim3(1), 0, s, b.ctr, cap_b);
     VM_STAGE_BEGIN(hk, kStFinalize, s);
-    launch_k(k_finalize, dim3(clampg(cap_b, sms * 4)), dim3(kT), 0, s, nsp, cap_b, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
+    launch_k(k_finalize, dim3(clampg(cap_b, sms * 16)), dim3(kT), 0, s, nsp, cap_b, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
     VM_STAGE_END(hk, kStFinalize, s);
     const uint8_t want = p.classify ? 2 : 1;
     VM_STAGE_BEGIN(hk, kStNormals, s);
