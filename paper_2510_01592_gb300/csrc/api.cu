@@ -79,6 +79,7 @@ static void fit_layout(Carver& c, FitBuffers& fb, size_t kcap, size_t npts, size
     fb.counts = c.take<uint32_t>(kcap * H);
     fb.cl = c.take<FitCluster>(kcap);
     fb.item_off = c.take<uint32_t>(kcap + 1);
+    fb.item_cl = c.take<uint32_t>(chunks + 1);  // items never outnumber the chunk slots
     fb.queue = c.take<uint32_t>(4);
     fb.inlier = c.take<uint8_t>(npts + 1);
     fb.part = c.take<float>((chunks + 1) * 10);

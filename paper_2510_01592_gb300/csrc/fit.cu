@@ -62,7 +62,11 @@ __device__ __forceinline__ float plane_dist(float nx, float ny, float nz, float 
     return fabsf(__fmaf_rn(nz, pz, __fmaf_rn(ny, py, __fmaf_rn(nx, px, d))));
 }
 
-__device__ __forceinline__ uint32_t find_cluster(const uint32_t* __restrict__ item_off, uint32_t k, uint32_t it) {
+// The cluster of work item it: one load from the item -> cluster table k_hyp
+// writes (item_cl), else a binary search over the item offsets.
+__device__ __forceinline__ uint32_t find_cluster(const uint32_t* __restrict__ item_cl,
+                                                 const uint32_t* __restrict__ item_off, uint32_t k, uint32_t it) {
+    if (item_cl) return item_cl[it];
     uint32_t lo = 0, hi = k;  // largest c with item_off[c] <= it
     while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
@@ -72,15 +76,20 @@ __device__ __forceinline__ uint32_t find_cluster(const uint32_t* __restrict__ it
 }
 
 // ---------------------------------------------------------------- stage a
+// Also writes the item -> cluster table (item_cl, when not null): the thread
+// of hypothesis 0 of each cluster fills its cluster's items.
 __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                       const uint32_t* __restrict__ labels, const uint32_t* __restrict__ kp, int H, unsigned long long seed,
                       uint32_t round, float4* __restrict__ hyp, uint8_t* __restrict__ valid,
-                      uint32_t* __restrict__ counts) {
+                      uint32_t* __restrict__ counts, const uint32_t* __restrict__ item_off,
+                      uint32_t* __restrict__ item_cl) {
     pdl_gate();
     const uint32_t k = *kp;
     const size_t total = (size_t)k * H;
     for (size_t t = (size_t)blockIdx.x * kT + threadIdx.x; t < total; t += (size_t)gridDim.x * kT) {
         const uint32_t c = (uint32_t)(t / H), h = (uint32_t)(t % H);
+        if (h == 0 && item_cl)
+            for (uint32_t it = item_off[c], e = item_off[c + 1]; it < e; ++it) item_cl[it] = c;
         const uint32_t base = off[c], n = off[c + 1] - base;
         const uint32_t label = labels ? labels[c] : c;
         const unsigned long long ctr[4] = {label, h, round, 0ull}, key[2] = {seed, 0ull};
@@ -118,7 +127,8 @@ __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict_
 // ---------------------------------------------------------------- stage b
 template <int R>
 __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                              const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int H, int T,
+                                              const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ item_cl,
+                                              const uint32_t* __restrict__ kp, int H, int T,
                                               const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
                                               uint32_t* __restrict__ queue, float eps) {
     pdl_wait();
@@ -137,7 +147,7 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
         __syncthreads();
         const uint32_t it = s_item;
         if (it >= n_items) break;
-        const uint32_t c = find_cluster(item_off, k, it);
+        const uint32_t c = find_cluster(item_cl, item_off, k, it);
         const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
         const uint32_t end = min(off[c + 1], start + (uint32_t)T);
         const int cnt = (int)(end - start);
@@ -316,7 +326,8 @@ __device__ __forceinline__ void chunks_out(const float* wp, uint32_t n_chunks, f
 // Inliers, centroid partials (relative to the origin) and the extreme inliers
 // along the 16 filter directions (reduced per warp, then atomicMax).
 __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                                const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int T,
+                                                const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ item_cl,
+                                                const uint32_t* __restrict__ kp, int T,
                                                 FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
                                                 float* __restrict__ part, float eps, uint32_t* __restrict__ err) {
     pdl_gate();
@@ -325,7 +336,7 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
     const uint32_t n_items = item_off[k];
     const uint32_t cpt = (uint32_t)T / kChunk;  // chunks per work item
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const uint32_t c = find_cluster(item_off, k, it);
+        const uint32_t c = find_cluster(item_cl, item_off, k, it);
         const FitCluster f = cl[c];
         const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
         const uint32_t end = min(off[c + 1], start + (uint32_t)T);
@@ -477,7 +488,8 @@ __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b) {
 // with one atomic per kSurvBuf survivors (usually one per work item) instead
 // of one returned atomic per chunk on the loop's critical path.
 __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                               const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp, int T,
+                                               const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ item_cl,
+                                               const uint32_t* __restrict__ kp, int T,
                                                FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
                                                const float* __restrict__ cen, float* __restrict__ part,
                                                int2* __restrict__ surv) {
@@ -493,7 +505,7 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
     const int lane = threadIdx.x & 31;
     const uint32_t cpt = (uint32_t)T / kChunk;
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const uint32_t c = find_cluster(item_off, k, it);
+        const uint32_t c = find_cluster(item_cl, item_off, k, it);
         const FitCluster f = cl[c];
         const uint32_t base = off[c];
         const uint32_t start = base + (it - item_off[c]) * (uint32_t)T;
@@ -959,6 +971,7 @@ __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restr
 template <int R>
 __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                                    const uint32_t* __restrict__ item_off,
+                                                   const uint32_t* __restrict__ item_cl,
                                                    const uint32_t* __restrict__ kp, int H, int T,
                                                    const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
                                                    uint32_t* __restrict__ queue, float eps) {
@@ -977,7 +990,7 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
         if (lane == 0) it = atomicAdd(queue, 1u);
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
-        const uint32_t c = find_cluster(item_off, k, it);
+        const uint32_t c = find_cluster(item_cl, item_off, k, it);
         const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
         const uint32_t end = min(off[c + 1], start + (uint32_t)T);
         const int cnt = (int)(end - start);
@@ -1024,22 +1037,24 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
 }
 
 template <int R>
-cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* kp, int H,
-                         int T, const float4* hyp, uint32_t* counts, uint32_t* queue, float eps, int grid,
-                         cudaStream_t s) {
+cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* item_cl,
+                         const uint32_t* kp, int H, int T, const float4* hyp, uint32_t* counts, uint32_t* queue,
+                         float eps, int grid, cudaStream_t s) {
     const int G = (H + R - 1) / R;
     const int P = kT / G;
     const size_t smem = (size_t)T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
-    launch_full(k_score<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
+    launch_full(k_score<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, item_cl, kp, H, T, hyp, counts, queue,
+                eps);
     return cudaGetLastError();
 }
 
 template <int R>
-cudaError_t launch_score_warp(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* kp,
-                              int H, int T, const float4* hyp, uint32_t* counts, uint32_t* queue, float eps,
-                              int grid, cudaStream_t s) {
+cudaError_t launch_score_warp(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* item_cl,
+                              const uint32_t* kp, int H, int T, const float4* hyp, uint32_t* counts, uint32_t* queue,
+                              float eps, int grid, cudaStream_t s) {
     const size_t smem = (size_t)(kT / 32) * T * sizeof(float4);
-    launch_full(k_score_warp<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, kp, H, T, hyp, counts, queue, eps);
+    launch_full(k_score_warp<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, item_cl, kp, H, T, hyp, counts,
+                queue, eps);
     return cudaGetLastError();
 }
 
@@ -1148,7 +1163,8 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     launch_k(k_items_end, dim3(1), dim3(32), 0, s, fb.item_off, kp, fb.tot, fb.queue);
     const size_t kh = (size_t)kcap * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid, fb.counts);
+    launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid, fb.counts,
+             fb.item_off, fb.item_cl);
     VM_STAGE_END(hk, kStHyp, s);
     count_launch(3);
     const int grid = sms * t.ctas_per_sm;
@@ -1161,17 +1177,17 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_BEGIN(hk, kStScore, s);
     if (warp) {
         switch (R) {
-            case 1: e = launch_score_warp<1>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            case 2: e = launch_score_warp<2>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            case 4: e = launch_score_warp<4>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            default: e = launch_score_warp<8>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 1: e = launch_score_warp<1>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 2: e = launch_score_warp<2>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 4: e = launch_score_warp<4>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            default: e = launch_score_warp<8>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
         }
     } else {
         switch (R) {
-            case 1: e = launch_score<1>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            case 2: e = launch_score<2>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            case 8: e = launch_score<8>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            default: e = launch_score<4>(pts, off, fb.item_off, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 1: e = launch_score<1>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 2: e = launch_score<2>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 8: e = launch_score<8>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            default: e = launch_score<4>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
         }
     }
     if (e != cudaSuccess) return e;
@@ -1181,11 +1197,11 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_BEGIN(hk, kStExtract, s);
     launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
     const unsigned igrid = (unsigned)sms * 8;
-    launch_full(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
+    launch_full(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
     const unsigned wgrid0 = (kcap + kT / 32 - 1) / (kT / 32);
     const unsigned wgrid = wgrid0 < (uint32_t)sms * 8 ? wgrid0 : (uint32_t)sms * 8;
     launch_k(k_centroid, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
-    launch_full(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
+    launch_full(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
     VM_STAGE_END(hk, kStExtract, s);
     count_launch(4);
     VM_STAGE_BEGIN(hk, kStHull, s);
@@ -1329,13 +1345,19 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     launch_k(k_items_end, dim3(1), dim3(32), 0, s, item_off, kdev, total, queue);
     const size_t kh = (size_t)k * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, xyz, off, labels, kdev, H, params->seed, 0u, hyp, valid, counts);
+    launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, xyz, off, labels, kdev, H, params->seed, 0u, hyp, valid, counts,
+             item_off, static_cast<uint32_t*>(nullptr));
     int R = t.hyp_per_thread;
     while (R < 8 && (H + R - 1) / R > kT) R <<= 1;
     const int grid = sms * t.ctas_per_sm;
+    const uint32_t* no_table = nullptr;  // clusters of work items by binary search
     switch (R) {
-        case 8: e = launch_score<8>(xyz, off, item_off, kdev, H, t.tile, hyp, counts, queue, params->eps, grid, s); break;
-        default: e = launch_score<4>(xyz, off, item_off, kdev, H, t.tile, hyp, counts, queue, params->eps, grid, s); break;
+        case 8:
+            e = launch_score<8>(xyz, off, item_off, no_table, kdev, H, t.tile, hyp, counts, queue, params->eps, grid, s);
+            break;
+        default:
+            e = launch_score<4>(xyz, off, item_off, no_table, kdev, H, t.tile, hyp, counts, queue, params->eps, grid, s);
+            break;
     }
     if (e != cudaSuccess) return cuda_status(e, "k_score");
     const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;

@@ -372,6 +372,7 @@ struct FitBuffers {
     uint32_t* counts;       // [kcap * H]
     FitCluster* cl;         // [kcap]
     uint32_t* item_off;     // [kcap + 1] work-item offsets (scan)
+    uint32_t* item_cl;      // [items] the cluster of each work item
     uint32_t* queue;        // [4] work-queue heads
     uint8_t* inlier;        // [npts]
     float* part;            // [items][10] per-item partial sums
