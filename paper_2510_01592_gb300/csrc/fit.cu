@@ -717,30 +717,6 @@ __device__ __forceinline__ bool jarvis_better(int2 cur, int2 a, bool a_ok, int2 
 // it lies in the convex hull of the polygon's vertices and is not an extreme
 // point); the directions only decide how much it removes.
 constexpr int kHullDirs = 128;
-constexpr int kCoarseDirs = 32;      // the coarse first filter of a cluster with many survivors
-constexpr int kCoarseMin = 512;      // survivors above which it runs
-constexpr int kGone = INT_MIN;       // a survivor the coarse filter dropped (no quantised point is INT_MIN)
-
-// Closes the polygon through the extreme points poly[0..n) (in direction
-// order): missing entries (INT_MIN) and consecutive duplicates removed; its
-// vertex count, or 0 when fewer than 3 remain or its area is not positive
-// (such a polygon filters nothing).  One thread.
-__device__ int close_polygon(int2* poly, int n) {
-    int m = 0;
-    for (int j = 0; j < n; ++j) {
-        const int2 p = poly[j];
-        if (p.x == INT_MIN && p.y == INT_MIN) continue;
-        if (m && poly[m - 1].x == p.x && poly[m - 1].y == p.y) continue;
-        poly[m++] = p;
-    }
-    if (m > 1 && poly[m - 1].x == poly[0].x && poly[m - 1].y == poly[0].y) --m;
-    long long area2 = 0;
-    for (int i = 0; i < m; ++i) {
-        const int2 a = poly[i], b = poly[(i + 1) % m];
-        area2 += (long long)a.x * b.y - (long long)a.y * b.x;
-    }
-    return (m >= 3 && area2 > 0) ? m : 0;
-}
 
 // Per cluster hull of the first filter's survivors: (1) extreme survivors along
 // kHullDirs directions; (2) survivors strictly inside the polygon they span
@@ -750,7 +726,7 @@ __device__ int close_polygon(int2* poly, int n) {
 // and upper halves built concurrently by two threads.  If more than
 // kHullCap points remain, gift wrapping runs over the survivors instead.
 __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp,
-                                             const FitCluster* __restrict__ cl, int2* __restrict__ surv,
+                                             const FitCluster* __restrict__ cl, const int2* __restrict__ surv,
                                              int2* __restrict__ hull, uint32_t* __restrict__ hull_cnt,
                                              uint32_t* __restrict__ err) {
     pdl_gate();
@@ -779,54 +755,10 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
         int2* out = hull + base;
         if (threadIdx.x == 0) s_cnt = 0;
         // stage the survivors (when they fit) so the scans below read shared memory
-        int2* sv = surv + base;
+        const int2* sv = surv + base;
         if (s <= kSurvCap) {
             for (int i = threadIdx.x; i < s; i += kT) ssv[i] = sv[i];
             sv = ssv;
-            __syncthreads();
-        }
-        // (0) many survivors: a coarser filter first.  Extremes along every
-        // fourth direction (32); survivors strictly inside the polygon through
-        // them are marked dropped (kGone), so the 128-direction scans below
-        // skip them.  Dropped points are strictly inside a polygon through
-        // input points: not hull vertices.
-        if (s > kCoarseMin) {
-            constexpr int kPer0 = kCoarseDirs / (kT / 32);
-            long long bv[kPer0];
-            int bi[kPer0];
-#pragma unroll
-            for (int q = 0; q < kPer0; ++q) { bv[q] = LLONG_MIN; bi[q] = -1; }
-            for (int i = lane; i < s; i += 32) {
-                const int2 p = sv[i];
-#pragma unroll
-                for (int q = 0; q < kPer0; ++q) {
-                    const int2 dv = sdir[(kPer0 * w + q) * (kHullDirs / kCoarseDirs)];
-                    const long long v = (long long)dv.x * p.x + (long long)dv.y * p.y;
-                    if (v > bv[q]) { bv[q] = v; bi[q] = i; }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < kPer0; ++q) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const long long ov = __shfl_xor_sync(0xffffffffu, bv[q], o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
-                    if (ov > bv[q] || (ov == bv[q] && oi < bi[q])) { bv[q] = ov; bi[q] = oi; }
-                }
-                if (lane == 0) poly[kPer0 * w + q] = (bi[q] >= 0) ? sv[bi[q]] : make_int2(INT_MIN, INT_MIN);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) s_m = close_polygon(poly, kCoarseDirs);
-            __syncthreads();
-            const int m0 = s_m;
-            if (m0) {
-                for (int i = threadIdx.x; i < s; i += kT) {
-                    const int2 p = sv[i];
-                    bool inside = true;
-                    for (int e = 0; e < m0 && inside; ++e) inside = cross3(poly[e], poly[e + 1 < m0 ? e + 1 : 0], p) > 0;
-                    if (inside) sv[i] = make_int2(kGone, kGone);
-                }
-            }
             __syncthreads();
         }
         // (1) extreme points along kHullDirs directions: warp w takes 16 of them
@@ -838,7 +770,6 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
             for (int q = 0; q < kPer; ++q) { bv[q] = LLONG_MIN; bi[q] = -1; }
             for (int i = lane; i < s; i += 32) {
                 const int2 p = sv[i];
-                if (p.x == kGone) continue;
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) {
                     const int2 dv = sdir[kPer * w + q];
@@ -858,7 +789,22 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_m = close_polygon(poly, kHullDirs);
+        if (threadIdx.x == 0) {  // polygon through the extremes, consecutive duplicates removed
+            int m = 0;
+            for (int j = 0; j < kHullDirs; ++j) {
+                const int2 p = poly[j];
+                if (p.x == INT_MIN && p.y == INT_MIN) continue;
+                if (m && poly[m - 1].x == p.x && poly[m - 1].y == p.y) continue;
+                poly[m++] = p;
+            }
+            if (m > 1 && poly[m - 1].x == poly[0].x && poly[m - 1].y == poly[0].y) --m;
+            long long area2 = 0;
+            for (int i = 0; i < m; ++i) {
+                const int2 a = poly[i], b = poly[(i + 1) % m];
+                area2 += (long long)a.x * b.y - (long long)a.y * b.x;
+            }
+            s_m = (m >= 3 && area2 > 0) ? m : 0;
+        }
         __syncthreads();
         const int m = s_m;
         // (2) drop survivors strictly inside the polygon
@@ -866,7 +812,7 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
             const int i = i0 + threadIdx.x;
             bool keep = false;
             int2 p = make_int2(0, 0);
-            if (i < s && sv[i].x != kGone) {
+            if (i < s) {
                 p = sv[i];
                 keep = (m == 0);
                 for (int e = 0; e < m; ++e) {
@@ -939,7 +885,6 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
             // gift wrapping over all survivors in global memory
             unsigned long long bk = ~0ull;
             for (int i = threadIdx.x; i < s; i += kT) {
-                if (sv[i].x == kGone) continue;
                 const unsigned long long key = xy_key(sv[i]);
                 bk = key < bk ? key : bk;
             }
@@ -965,7 +910,7 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
                 bool ok = false;
                 for (int i = threadIdx.x; i < s; i += kT) {
                     const int2 p = sv[i];
-                    const bool pok = p.x != kGone && !(p.x == cur.x && p.y == cur.y);
+                    const bool pok = !(p.x == cur.x && p.y == cur.y);
                     if (jarvis_better(cur, cand, ok, p, pok)) { cand = p; ok = true; }
                 }
                 jcand[threadIdx.x] = cand;
