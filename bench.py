@@ -38,10 +38,10 @@ N_FRAMES = 300
 # launch stages a fixed halo per brick, so traffic is scaled to the timed map by
 # its brick count.  Remove a kernel's entry when the kernel changes.
 TRAFFIC_PER_BRICK = {
-    "moments": (9290240.0 + 256.0) / 1498,
-    "eigen": (4146176.0 + 72192.0) / 1498,
-    "ccl_local": 14559232.0 / 1498,
-    "ccl_cross": (15071232.0 + 256.0) / 1498,
+    "moments": (9291776.0 + 0.0) / 1498,
+    "eigen": (4150016.0 + 77568.0) / 1498,
+    "ccl_local": 14557952.0 / 1498,
+    "ccl_cross": (15073792.0 + 1536.0) / 1498,
 }
 METRIC = "0.01 m integrate+segment: frames/s, p50/p99 ms, batched/served vs plain GPU"
 WORKLOAD = ("paper-scale trajectory: 4x4x2 m map at 0.01 m (sparse 8^3 bricks), 640x480 depth camera "
