@@ -1031,8 +1031,8 @@ SM_COUNT, FP32_LANES = 152, 128
 
 def kernel_table(stages, st, peaks, n_points_segment):
     """Per-stage average launch time and, for single-kernel stages, the achieved
-    rate against the measured peak.  Algorithmic bytes / ops per unit:
-    slots = allocated bricks x 512 voxels, occ = occupied voxels."""
+    rate against the measured peak.  Algorithmic bytes / ops per unit of each
+    kernel's model: slots = allocated bricks x 512 voxels, occ = occupied voxels."""
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     clk = (peaks or {}).get("sm_max_mhz", 2070.0) * 1e6
     alu_peak = SM_COUNT * FP32_LANES * clk / 1e12  # T instructions/s
