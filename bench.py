@@ -621,6 +621,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, device):
+    """The elementwise maximum of values over every rank (the slowest rank's
+    times); needs the process group when WORLD_SIZE > 1."""
+    ws, _, _ = dist_env()
+    if ws <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(steps, ws, slowest_ms):
+    """Frames of every rank (replicas of the same steps) over the slowest rank's time."""
+    return steps * ws / (slowest_ms / 1e3)
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -769,6 +787,8 @@ def run_gpu(args):
         n_planes.append(len(r["planes"]))
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
     launches = vm.launch_count() - launches0
     clocks = sampler.stop()
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
@@ -966,12 +986,9 @@ def run_gpu(args):
                              "then integrate + segment; graph replay"}
     mr.close()
 
-    if ws > 1:
-        t = torch.tensor([total_ms, e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_s = float(t[0]), float(t[1])
+    total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev)
     frames = args.steps * ws
-    value = frames / (total_ms / 1e3)
+    value = whole_job_rate(args.steps, ws, total_ms)
     res = {
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
