@@ -430,50 +430,73 @@ __device__ __forceinline__ df2 df_shfl_xor(df2 x, int o) {
     return {__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
 }
 
-// Per cluster (one warp each): inlier count and centroid, the per-chunk
-// partial sums added in double-float in a fixed order (lane-strided, then a
-// shuffle tree), so the result does not depend on scheduling.  The centroid
+// Sums NV double-float values over a CTA in a fixed order: a shuffle tree in
+// each warp, then the warps' results in warp order.  The total is valid in
+// thread 0.  sh: NV * (kT / 32) entries of shared memory.
+template <int NV>
+__device__ __forceinline__ void block_df_sum(df2 (&v)[NV], df2* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int e = 0; e < NV; ++e) v[e] = df_add(v[e], df_shfl_xor(v[e], o));
+    if (lane == 0)
+#pragma unroll
+        for (int e = 0; e < NV; ++e) sh[e * (kT / 32) + w] = v[e];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            df2 t = sh[e * (kT / 32)];
+            for (int q = 1; q < kT / 32; ++q) t = df_add(t, sh[e * (kT / 32) + q]);
+            v[e] = t;
+        }
+}
+
+// Per cluster (one CTA each): inlier count and centroid, the per-chunk
+// partial sums added in double-float in a fixed order (thread-strided, then
+// block_df_sum), so the result does not depend on scheduling.  The centroid
 // is kept as (hi, lo) per axis.
-__global__ void k_centroid(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
-                           const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
-                           FitCluster* __restrict__ cl, float* __restrict__ cen /* [k][3][2] */) {
+__global__ void __launch_bounds__(kT) k_centroid(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
+                                                 const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
+                                                 FitCluster* __restrict__ cl, float* __restrict__ cen /* [k][3][2] */) {
     pdl_gate();
     const uint32_t k = *kp;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (kT / 32);
     const uint32_t cpt = (uint32_t)T / kChunk;
-    for (uint32_t c = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); c < k; c += warps) {
-        df2 sx{0.0f, 0.0f}, sy{0.0f, 0.0f}, sz{0.0f, 0.0f};
+    __shared__ df2 sh[3 * (kT / 32)];
+    __shared__ uint32_t shn[kT / 32];
+    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
+        df2 v[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
         uint32_t n = 0;
         const uint32_t base = item_off[c] * cpt, nch = (off[c + 1] - off[c] + kChunk - 1) / kChunk;
-#pragma unroll 4
-        for (uint32_t j = lane; j < nch; j += 32) {  // unrolled: the next chunks' loads overlap this one's adds
+#pragma unroll 2
+        for (uint32_t j = threadIdx.x; j < nch; j += kT) {
             const float* pp = part + (size_t)(base + j) * 10;
             n += (uint32_t)pp[0];
-            sx = df_add(sx, df2{pp[1], 0.0f});
-            sy = df_add(sy, df2{pp[2], 0.0f});
-            sz = df_add(sz, df2{pp[3], 0.0f});
+            v[0] = df_add(v[0], df2{pp[1], 0.0f});
+            v[1] = df_add(v[1], df2{pp[2], 0.0f});
+            v[2] = df_add(v[2], df2{pp[3], 0.0f});
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            n += __shfl_xor_sync(0xffffffffu, n, o);
-            sx = df_add(sx, df_shfl_xor(sx, o));
-            sy = df_add(sy, df_shfl_xor(sy, o));
-            sz = df_add(sz, df_shfl_xor(sz, o));
-        }
-        if (lane == 0) {
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+        if ((threadIdx.x & 31) == 0) shn[threadIdx.x >> 5] = n;
+        block_df_sum<3>(v, sh);
+        if (threadIdx.x == 0) {
+            n = 0;
+            for (int q = 0; q < kT / 32; ++q) n += shn[q];
             FitCluster& f = cl[c];
             f.inliers = n;
             df2 cx{f.o[0], 0.0f}, cy{f.o[1], 0.0f}, cz{f.o[2], 0.0f};
             if (n) {
-                cx = df_add(cx, df_div_count(sx, n));
-                cy = df_add(cy, df_div_count(sy, n));
-                cz = df_add(cz, df_div_count(sz, n));
+                cx = df_add(cx, df_div_count(v[0], n));
+                cy = df_add(cy, df_div_count(v[1], n));
+                cz = df_add(cz, df_div_count(v[2], n));
             }
             float* ce = cen + 6 * (size_t)c;
             ce[0] = cx.hi; ce[1] = cx.lo; ce[2] = cy.hi; ce[3] = cy.lo; ce[4] = cz.hi; ce[5] = cz.lo;
             f.c[0] = cx.hi; f.c[1] = cy.hi; f.c[2] = cz.hi;
         }
+        __syncthreads();  // shared partials reused by the next cluster
     }
 }
 
@@ -584,28 +607,25 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
 // n_z >= 0, d = -n . centroid (double-float); lambda_mid < 10 lambda_min
 // (from the trace, the Rayleigh quotient in double-float and
 // x^T adj(A) x = lambda_1 lambda_2) flags the plane ill-conditioned.
-__global__ void k_refit(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
-                        const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
-                        const float* __restrict__ cen, FitCluster* __restrict__ cl) {
+__global__ void __launch_bounds__(kT) k_refit(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
+                                              const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
+                                              const float* __restrict__ cen, FitCluster* __restrict__ cl) {
     pdl_gate();
     const uint32_t k = *kp;
-    const int lane = threadIdx.x & 31;
-    const uint32_t warps = gridDim.x * (kT / 32);
     const uint32_t cpt = (uint32_t)T / kChunk;
-    for (uint32_t c = blockIdx.x * (kT / 32) + (threadIdx.x >> 5); c < k; c += warps) {
+    __shared__ df2 sh[6 * (kT / 32)];
+    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
         df2 A[6];
 #pragma unroll
         for (int e = 0; e < 6; ++e) A[e] = df2{0.0f, 0.0f};
         const uint32_t base = item_off[c] * cpt, nch = (off[c + 1] - off[c] + kChunk - 1) / kChunk;
-#pragma unroll 4
-        for (uint32_t j = lane; j < nch; j += 32)
+#pragma unroll 2
+        for (uint32_t j = threadIdx.x; j < nch; j += kT)
 #pragma unroll
             for (int e = 0; e < 6; ++e) A[e] = df_add(A[e], df2{part[(size_t)(base + j) * 10 + 4 + e], 0.0f});
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int e = 0; e < 6; ++e) A[e] = df_add(A[e], df_shfl_xor(A[e], o));
-        if (lane) continue;
+        block_df_sum<6>(A, sh);
+        __syncthreads();  // thread 0 holds the sums; the shared partials are free for the next cluster
+        if (threadIdx.x) continue;
         FitCluster& f = cl[c];
         uint32_t flags = 0;
         float rn[3] = {0.0f, 0.0f, 0.0f}, rd = 0.0f;
@@ -1198,8 +1218,7 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
     const unsigned igrid = (unsigned)sms * 8;
     launch_full(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
-    const unsigned wgrid0 = (kcap + kT / 32 - 1) / (kT / 32);
-    const unsigned wgrid = wgrid0 < (uint32_t)sms * 8 ? wgrid0 : (uint32_t)sms * 8;
+    const unsigned wgrid = kcap < (uint32_t)sms * 8 ? kcap : (uint32_t)sms * 8;  // a CTA per cluster
     launch_k(k_centroid, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
     launch_full(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
     VM_STAGE_END(hk, kStExtract, s);
