@@ -279,9 +279,9 @@ int orc_integrate(void *h, const float *xyz, uint64_t n, const float pose[12])
  * offset w in range); the end voxel (the point's own) is not.  The walk stops
  * once it leaves the grid (a monotone walk does not come back).  A sensor
  * outside the grid casts no rays (a robot-centric map holds its sensor);
- * points that are not finite, or more than 2^30 voxels away, cast no ray.  All marks of the frame are collected first, then the
- * marked voxels are cleared (sums and count to zero); integrating the
- * frame's points follows. */
+ * points that are not finite, or more than 2^30 voxels away, cast no ray.
+ * All marks of the frame are collected first, then the marked voxels are
+ * cleared (sums and count to zero); integrating the frame's points follows. */
 typedef struct { orc_map *m; const float *xyz; const float *pose; uint8_t *mark; } clear_ctx;
 static void clear_range(void *vc, uint64_t lo, uint64_t hi)
 {

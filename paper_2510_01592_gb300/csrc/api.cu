@@ -457,7 +457,8 @@ cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk
         e = launch_pack(fb, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, planes, hull_xy, hull_xyz, m->out_hcap, s);
         if (e != cudaSuccess) return e;
     }
-    launch_k(k_header, dim3(1), dim3(1), 0, s, b.ctr, fb.hull_cnt, rounds, fb.err, m->ctr, m->err, reinterpret_cast<SegCounters*>(d));
+    launch_k(k_header, dim3(1), dim3(1), 0, s, b.ctr, fb.hull_cnt, rounds, fb.err, m->ctr, m->err,
+             reinterpret_cast<SegCounters*>(d));
     count_launch(1);
     VM_STAGE_END(hk, kStPack, s);
     return cudaGetLastError();

@@ -79,8 +79,8 @@ __device__ __forceinline__ uint32_t find_cluster(const uint32_t* __restrict__ it
 // Also writes the item -> cluster table (item_cl, when not null): the thread
 // of hypothesis 0 of each cluster fills its cluster's items.
 __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                      const uint32_t* __restrict__ labels, const uint32_t* __restrict__ kp, int H, unsigned long long seed,
-                      uint32_t round, float4* __restrict__ hyp, uint8_t* __restrict__ valid,
+                      const uint32_t* __restrict__ labels, const uint32_t* __restrict__ kp, int H,
+                      unsigned long long seed, uint32_t round, float4* __restrict__ hyp, uint8_t* __restrict__ valid,
                       uint32_t* __restrict__ counts, const uint32_t* __restrict__ item_off,
                       uint32_t* __restrict__ item_cl) {
     pdl_gate();
@@ -127,10 +127,10 @@ __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict_
 // ---------------------------------------------------------------- stage b
 template <int R>
 __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                              const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ item_cl,
-                                              const uint32_t* __restrict__ kp, int H, int T,
-                                              const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
-                                              uint32_t* __restrict__ queue, float eps) {
+                                              const uint32_t* __restrict__ item_off,
+                                              const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
+                                              int H, int T, const float4* __restrict__ hyp,
+                                              uint32_t* __restrict__ counts, uint32_t* __restrict__ queue, float eps) {
     pdl_wait();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];                // T staged points
@@ -186,9 +186,10 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
 }
 
 // ---------------------------------------------------------------- stage c
-__global__ void k_select(const float* __restrict__ pts, const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int H,
-                         const float4* __restrict__ hyp, const uint8_t* __restrict__ valid,
-                         const uint32_t* __restrict__ counts, FitCluster* __restrict__ cl) {
+__global__ void k_select(const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                         const uint32_t* __restrict__ kp, int H, const float4* __restrict__ hyp,
+                         const uint8_t* __restrict__ valid, const uint32_t* __restrict__ counts,
+                         FitCluster* __restrict__ cl) {
     pdl_gate();
     const uint32_t k = *kp;
     __shared__ unsigned long long wbest[kT / 32];
@@ -308,7 +309,8 @@ __device__ __forceinline__ void warp_park(float (&v)[NV], float* wp, uint32_t j)
 }
 
 template <int NV>
-__device__ __forceinline__ void chunks_out(const float* wp, uint32_t n_chunks, float* dst /* [chunk][10] */, int first) {
+__device__ __forceinline__ void chunks_out(const float* wp, uint32_t n_chunks, float* dst /* [chunk][10] */,
+                                           int first) {
     __syncthreads();
     for (uint32_t j = threadIdx.x; j < n_chunks; j += kT) {
         float t[NV];
@@ -326,9 +328,9 @@ __device__ __forceinline__ void chunks_out(const float* wp, uint32_t n_chunks, f
 // Inliers, centroid partials (relative to the origin) and the extreme inliers
 // along the 16 filter directions (reduced per warp, then atomicMax).
 __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                                const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ item_cl,
-                                                const uint32_t* __restrict__ kp, int T,
-                                                FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
+                                                const uint32_t* __restrict__ item_off,
+                                                const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
+                                                int T, FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
                                                 float* __restrict__ part, float eps, uint32_t* __restrict__ err) {
     pdl_gate();
     const uint32_t k = *kp;
@@ -344,7 +346,8 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
 #pragma unroll
         for (int d = 0; d < kFiltDirs; ++d) ext[d] = 0;
         bool big = false;
-        uint32_t j = 0;  // chunk within the item; its slot is it * cpt + j (item_off[c] * cpt + its chunk in the cluster)
+        // chunk within the item; its slot is it * cpt + j (item_off[c] * cpt + its chunk in the cluster)
+        uint32_t j = 0;
 #pragma unroll 4
         for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {  // unrolled: later chunks' loads go out early
             const uint32_t q = q0 + threadIdx.x;
@@ -457,9 +460,10 @@ __device__ __forceinline__ void block_df_sum(df2 (&v)[NV], df2* sh) {
 // partial sums added in double-float in a fixed order (thread-strided, then
 // block_df_sum), so the result does not depend on scheduling.  The centroid
 // is kept as (hi, lo) per axis.
-__global__ void __launch_bounds__(kT) k_centroid(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
-                                                 const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
-                                                 FitCluster* __restrict__ cl, float* __restrict__ cen /* [k][3][2] */) {
+__global__ void __launch_bounds__(kT) k_centroid(const uint32_t* __restrict__ off,
+                                                 const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp,
+                                                 int T, const float* __restrict__ part, FitCluster* __restrict__ cl,
+                                                 float* __restrict__ cen /* [k][3][2] */) {
     pdl_gate();
     const uint32_t k = *kp;
     const uint32_t cpt = (uint32_t)T / kChunk;
@@ -511,9 +515,9 @@ __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b) {
 // with one atomic per kSurvBuf survivors (usually one per work item) instead
 // of one returned atomic per chunk on the loop's critical path.
 __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                               const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ item_cl,
-                                               const uint32_t* __restrict__ kp, int T,
-                                               FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
+                                               const uint32_t* __restrict__ item_off,
+                                               const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
+                                               int T, FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
                                                const float* __restrict__ cen, float* __restrict__ part,
                                                int2* __restrict__ surv) {
     pdl_gate();
@@ -963,17 +967,19 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
     }
 }
 
-__global__ void k_items(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int T, uint32_t* __restrict__ item_cnt) {
+__global__ void k_items(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int T,
+                        uint32_t* __restrict__ item_cnt) {
     pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT)
         item_cnt[c] = (off[c + 1] - off[c] + (uint32_t)T - 1) / (uint32_t)T;
 }
 
-__global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restrict__ labels, const uint32_t* __restrict__ kp,
-                       const FitCluster* __restrict__ cl, const int2* __restrict__ hull,
-                       const uint32_t* __restrict__ hull_off, vm_plane* __restrict__ planes,
-                       int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz, uint32_t hull_cap) {
+__global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restrict__ labels,
+                       const uint32_t* __restrict__ kp, const FitCluster* __restrict__ cl,
+                       const int2* __restrict__ hull, const uint32_t* __restrict__ hull_off,
+                       vm_plane* __restrict__ planes, int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz,
+                       uint32_t hull_cap) {
     pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
@@ -1056,25 +1062,36 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
     }
 }
 
+// The scoring launch's arguments (stage b).
+struct ScoreArgs {
+    const float* pts;
+    const uint32_t* off;
+    const uint32_t* item_off;
+    const uint32_t* item_cl;  // item -> cluster table, or null for a binary search
+    const uint32_t* kp;
+    int H, T;
+    const float4* hyp;
+    uint32_t* counts;
+    uint32_t* queue;
+    float eps;
+    int grid;
+};
+
 template <int R>
-cudaError_t launch_score(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* item_cl,
-                         const uint32_t* kp, int H, int T, const float4* hyp, uint32_t* counts, uint32_t* queue,
-                         float eps, int grid, cudaStream_t s) {
-    const int G = (H + R - 1) / R;
+cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s) {
+    const int G = (a.H + R - 1) / R;
     const int P = kT / G;
-    const size_t smem = (size_t)T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
-    launch_full(k_score<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, item_cl, kp, H, T, hyp, counts, queue,
-                eps);
+    const size_t smem = (size_t)a.T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
+    launch_full(k_score<R>, dim3(a.grid), dim3(kT), smem, s, a.pts, a.off, a.item_off, a.item_cl, a.kp, a.H, a.T,
+                a.hyp, a.counts, a.queue, a.eps);
     return cudaGetLastError();
 }
 
 template <int R>
-cudaError_t launch_score_warp(const float* pts, const uint32_t* off, const uint32_t* item_off, const uint32_t* item_cl,
-                              const uint32_t* kp, int H, int T, const float4* hyp, uint32_t* counts, uint32_t* queue,
-                              float eps, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)(kT / 32) * T * sizeof(float4);
-    launch_full(k_score_warp<R>, dim3(grid), dim3(kT), smem, s, pts, off, item_off, item_cl, kp, H, T, hyp, counts,
-                queue, eps);
+cudaError_t launch_score_warp(const ScoreArgs& a, cudaStream_t s) {
+    const size_t smem = (size_t)(kT / 32) * a.T * sizeof(float4);
+    launch_full(k_score_warp<R>, dim3(a.grid), dim3(kT), smem, s, a.pts, a.off, a.item_off, a.item_cl, a.kp, a.H,
+                a.T, a.hyp, a.counts, a.queue, a.eps);
     return cudaGetLastError();
 }
 
@@ -1183,8 +1200,8 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     launch_k(k_items_end, dim3(1), dim3(32), 0, s, fb.item_off, kp, fb.tot, fb.queue);
     const size_t kh = (size_t)kcap * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
-    launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid, fb.counts,
-             fb.item_off, fb.item_cl);
+    launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid,
+             fb.counts, fb.item_off, fb.item_cl);
     VM_STAGE_END(hk, kStHyp, s);
     count_launch(3);
     const int grid = sms * t.ctas_per_sm;
@@ -1195,19 +1212,20 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     bool warp;
     score_variant(t, H, R, warp);
     VM_STAGE_BEGIN(hk, kStScore, s);
+    const ScoreArgs sa{pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid};
     if (warp) {
         switch (R) {
-            case 1: e = launch_score_warp<1>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            case 2: e = launch_score_warp<2>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            case 4: e = launch_score_warp<4>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            default: e = launch_score_warp<8>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 1: e = launch_score_warp<1>(sa, s); break;
+            case 2: e = launch_score_warp<2>(sa, s); break;
+            case 4: e = launch_score_warp<4>(sa, s); break;
+            default: e = launch_score_warp<8>(sa, s); break;
         }
     } else {
         switch (R) {
-            case 1: e = launch_score<1>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            case 2: e = launch_score<2>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            case 8: e = launch_score<8>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
-            default: e = launch_score<4>(pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid, s); break;
+            case 1: e = launch_score<1>(sa, s); break;
+            case 2: e = launch_score<2>(sa, s); break;
+            case 8: e = launch_score<8>(sa, s); break;
+            default: e = launch_score<4>(sa, s); break;
         }
     }
     if (e != cudaSuccess) return e;
@@ -1217,10 +1235,12 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_BEGIN(hk, kStExtract, s);
     launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
     const unsigned igrid = (unsigned)sms * 8;
-    launch_full(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err);
+    launch_full(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier,
+                fb.part, p.eps, fb.err);
     const unsigned wgrid = kcap < (uint32_t)sms * 8 ? kcap : (uint32_t)sms * 8;  // a CTA per cluster
     launch_k(k_centroid, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
-    launch_full(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv);
+    launch_full(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier,
+                fb.cen, fb.part, fb.surv);
     VM_STAGE_END(hk, kStExtract, s);
     count_launch(4);
     VM_STAGE_BEGIN(hk, kStHull, s);
@@ -1238,8 +1258,8 @@ cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_
                         uint32_t kcap, vm_plane* planes, int32_t* hull_xy, float* hull_xyz, uint32_t hull_cap,
                         cudaStream_t s) {
     if (kcap == 0) return cudaSuccess;
-    launch_k(k_pack, dim3(kcap < 4096 ? kcap : 4096), dim3(128), 0, s, off, labels, kp, fb.cl, fb.hull, fb.hull_cnt, planes, hull_xy,
-                                                    hull_xyz, hull_cap);
+    launch_k(k_pack, dim3(kcap < 4096 ? kcap : 4096), dim3(128), 0, s, off, labels, kp, fb.cl, fb.hull, fb.hull_cnt,
+             planes, hull_xy, hull_xyz, hull_cap);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -1275,8 +1295,8 @@ constexpr size_t kStaticBytes = kOffScan + align256(kScanWords * sizeof(uint32_t
 
 // Copies the selected plane, hypothesis index and inlier count of each cluster
 // to the caller's arrays.
-__global__ void k_static_out(const FitCluster* __restrict__ cl, const uint32_t* __restrict__ kp, float* __restrict__ planes,
-                             int32_t* __restrict__ best_h, uint32_t* __restrict__ inliers) {
+__global__ void k_static_out(const FitCluster* __restrict__ cl, const uint32_t* __restrict__ kp,
+                             float* __restrict__ planes, int32_t* __restrict__ best_h, uint32_t* __restrict__ inliers) {
     pdl_gate();
     const uint32_t k = *kp;
     for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT) {
@@ -1369,15 +1389,9 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     int R = t.hyp_per_thread;
     while (R < 8 && (H + R - 1) / R > kT) R <<= 1;
     const int grid = sms * t.ctas_per_sm;
-    const uint32_t* no_table = nullptr;  // clusters of work items by binary search
-    switch (R) {
-        case 8:
-            e = launch_score<8>(xyz, off, item_off, no_table, kdev, H, t.tile, hyp, counts, queue, params->eps, grid, s);
-            break;
-        default:
-            e = launch_score<4>(xyz, off, item_off, no_table, kdev, H, t.tile, hyp, counts, queue, params->eps, grid, s);
-            break;
-    }
+    // no item -> cluster table here: the clusters of work items by binary search
+    const ScoreArgs sa{xyz, off, item_off, nullptr, kdev, H, t.tile, hyp, counts, queue, params->eps, grid};
+    e = R == 8 ? launch_score<8>(sa, s) : launch_score<4>(sa, s);
     if (e != cudaSuccess) return cuda_status(e, "k_score");
     const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;
     launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, xyz, off, kdev, H, hyp, valid, counts, cl);

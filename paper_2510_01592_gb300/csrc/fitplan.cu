@@ -137,7 +137,8 @@ cudaError_t enqueue_fit(vm_fit_plan* f, const float* x, const uint32_t* off, con
                     reinterpret_cast<int32_t*>(d + out_xy_off(f->out_kcap)),
                     reinterpret_cast<float*>(d + out_xyz_off(f->out_kcap, f->out_hcap)), f->out_hcap, s);
     if (e != cudaSuccess) return e;
-    launch_k(k_fit_header, dim3(1), dim3(1), 0, s, fb.kdev, fb.tot + 2, fb.hull_cnt, fb.err, reinterpret_cast<FitHeader*>(d));
+    launch_k(k_fit_header, dim3(1), dim3(1), 0, s, fb.kdev, fb.tot + 2, fb.hull_cnt, fb.err,
+             reinterpret_cast<FitHeader*>(d));
     VM_STAGE_END(hk, kStPack, s);
     count_launch(2);
     return cudaGetLastError();

@@ -218,7 +218,8 @@ __global__ void __launch_bounds__(kThreads) k_clear_mark(const float* __restrict
             if (gone) break;
             if (q0 >= 0 && q0 < dims[0] && q1 >= 0 && q1 < dims[1] && q2 >= 0 && q2 < dims[2]) {
                 const uint32_t brick =
-                    ((uint32_t)(q2 >> 3) * (uint32_t)g.nby + (uint32_t)(q1 >> 3)) * (uint32_t)g.nbx + (uint32_t)(q0 >> 3);
+                    ((uint32_t)(q2 >> 3) * (uint32_t)g.nby + (uint32_t)(q1 >> 3)) * (uint32_t)g.nbx +
+                    (uint32_t)(q0 >> 3);
                 if (brick != cur_brick) {
                     cur_brick = brick;
                     cur_slot = table[brick];
@@ -378,7 +379,8 @@ __global__ void k_scroll_table(const uint32_t* __restrict__ n_keep, const int32_
                                float px, float py, float pz) {
     pdl_gate();
     const uint32_t nk = *n_keep;
-    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < nk; s += gridDim.x * kThreads) table[slot_key[s]] = (int32_t)s;
+    for (uint32_t s = blockIdx.x * kThreads + threadIdx.x; s < nk; s += gridDim.x * kThreads)
+        table[slot_key[s]] = (int32_t)s;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->n_bricks = nk;
         po[0] = px;
@@ -450,8 +452,8 @@ cudaError_t launch_clear(const float* xyz, uint32_t n, const Pose& pose, const G
     launch_k(k_clear_mark, dim3(grid), dim3(kThreads), 0, s, xyz, n, pose, g, brick_table, C, mark, ctr);
     const size_t words = (size_t)capacity * (kBrickVox / 32);
     const size_t wgrid = (words + kThreads - 1) / kThreads;
-    launch_k(k_clear_apply, dim3((unsigned)(wgrid < (size_t)sms * 8 ? wgrid : (size_t)sms * 8)), dim3(kThreads), 0, s, S, C, mark, ctr,
-                                                                                                      capacity);
+    launch_k(k_clear_apply, dim3((unsigned)(wgrid < (size_t)sms * 8 ? wgrid : (size_t)sms * 8)), dim3(kThreads), 0, s,
+             S, C, mark, ctr, capacity);
     count_launch(2);
     return cudaGetLastError();
 }

@@ -30,7 +30,8 @@ namespace {
 constexpr int kRT = 256;
 
 __global__ void __launch_bounds__(kRT) k_round_stage(const uint32_t* __restrict__ kp, const uint32_t* __restrict__ off,
-                                                     const uint32_t* __restrict__ lab, const uint32_t* __restrict__ orig,
+                                                     const uint32_t* __restrict__ lab,
+                                                     const uint32_t* __restrict__ orig,
                                                      const FitCluster* __restrict__ cl, const int2* __restrict__ hull,
                                                      const uint32_t* __restrict__ hull_off, uint32_t r,
                                                      uint32_t* __restrict__ hbase, vm_plane* __restrict__ slot,
@@ -139,7 +140,8 @@ __global__ void k_round_totals(const uint32_t* __restrict__ kp, const uint32_t* 
 // The records of round-0 cluster c at cpos[c] + round, their hull vertices
 // from hpos[c] on, in round order.
 __global__ void __launch_bounds__(kRT) k_round_pack(const uint32_t* __restrict__ kp, const uint32_t* __restrict__ cnt,
-                                                    const uint32_t* __restrict__ cpos, const uint32_t* __restrict__ hpos,
+                                                    const uint32_t* __restrict__ cpos,
+                                                    const uint32_t* __restrict__ hpos,
                                                     const vm_plane* __restrict__ slot, const int2* __restrict__ shull,
                                                     uint32_t hcap, vm_plane* __restrict__ planes, uint32_t rec_cap,
                                                     int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz,
@@ -225,8 +227,8 @@ cudaError_t launch_rounds(const SegBuffers& b, uint32_t kcap, const vm_segment_p
     for (uint32_t r = 0; r < P; ++r) {
         if ((e = launch_fit(pts, off, lab, kp, kcap, p, fb, t, sms, s, hk, r)) != cudaSuccess) return e;
         VM_STAGE_BEGIN(hk, kStRounds, s);
-        launch_k(k_round_stage, dim3(gc), dim3(kRT), 0, s, kp, off, lab, orig, fb.cl, fb.hull, fb.hull_cnt, r, rb.word + kWordHull,
-                                         rb.slot, rb.cnt, rb.hull, (uint32_t)rb.hcap);
+        launch_k(k_round_stage, dim3(gc), dim3(kRT), 0, s, kp, off, lab, orig, fb.cl, fb.hull, fb.hull_cnt, r,
+                 rb.word + kWordHull, rb.slot, rb.cnt, rb.hull, (uint32_t)rb.hcap);
         count_launch(1);
         if (r + 1 < P) {
             const int nx = (r + 1) & 1;
@@ -239,9 +241,9 @@ cudaError_t launch_rounds(const SegBuffers& b, uint32_t kcap, const vm_segment_p
             e = exclusive_scan_dev(rb.keep, rb.kpos, rb.word + kWordKeep, rb.word + kWordNpts, nv, scan_tmp, s,
                                    fb.err);
             if (e != cudaSuccess) return e;
-            launch_k(k_round_scatter, dim3(gp), dim3(kRT), 0, s, kp, off, lab, orig, rb.act, rb.apos, rb.keep, rb.kpos, pts,
-                                               rb.word + kWordNpts, knext, rb.word + kWordKeep, rb.pts[nx],
-                                               rb.off[nx], rb.lab[nx], rb.orig[nx]);
+            launch_k(k_round_scatter, dim3(gp), dim3(kRT), 0, s, kp, off, lab, orig, rb.act, rb.apos, rb.keep, rb.kpos,
+                     pts, rb.word + kWordNpts, knext, rb.word + kWordKeep, rb.pts[nx], rb.off[nx], rb.lab[nx],
+                     rb.orig[nx]);
             count_launch(3);
             pts = rb.pts[nx];
             off = rb.off[nx];

@@ -331,7 +331,8 @@ cudaError_t stable_sort_pairs_dev(uint32_t* keys, uint32_t* vals, uint32_t* keys
         launch_k(k_rs_hist, dim3((unsigned)nt), dim3(kSortThreads), 0, s, ki, n_cap, n_dev, p, key_bound, ghist, cnt);
         cudaError_t e = exclusive_scan_dev(ghist, ghist, nullptr, cnt, 256 * nt, stmp, s, err);
         if (e != cudaSuccess) return e;
-        launch_k(k_rs_scatter, dim3((unsigned)nt), dim3(kSortThreads), 0, s, ki, vi, ko, vo, n_cap, n_dev, p, key_bound, ghist);
+        launch_k(k_rs_scatter, dim3((unsigned)nt), dim3(kSortThreads), 0, s, ki, vi, ko, vo, n_cap, n_dev, p, key_bound,
+                 ghist);
         count_launch(2);
         uint32_t* t;
         t = ki; ki = ko; ko = t;

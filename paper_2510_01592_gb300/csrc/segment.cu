@@ -66,7 +66,8 @@ __global__ void k_brick_compact(const int32_t* __restrict__ table, uint32_t nb, 
 
 // Mean of each voxel: M = floor((2 S + c) / (2 c)), the exact integer mean in
 // 2^-20 m units rounded half up (Eq. 1's mu up to that quantum).
-__global__ void __launch_bounds__(kT) k_finalize(const uint32_t* __restrict__ nsp, uint32_t cap_b, const int32_t* __restrict__ sorted_slot,
+__global__ void __launch_bounds__(kT) k_finalize(const uint32_t* __restrict__ nsp, uint32_t cap_b,
+                                                 const int32_t* __restrict__ sorted_slot,
                                                  const unsigned long long* __restrict__ S,
                                                  const uint32_t* __restrict__ C, int32_t* __restrict__ M,
                                                  uint8_t* __restrict__ status, size_t stride,
@@ -387,11 +388,11 @@ __global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__
 // k_eigen, one thread per occupied voxel: normal = eigenvector of the smallest
 // eigenvalue by FP32 Jacobi (6 sweeps); steppable iff N >= n_th and
 // |n_z| >= cos_step (status 2, else 1).
-__global__ void __launch_bounds__(256) k_eigen(const SegCounters* __restrict__ ctr, const uint32_t* __restrict__ list_idx,
-                                               const float* __restrict__ list_A, const uint8_t* __restrict__ nbr,
-                                               float* __restrict__ nrm, uint8_t* __restrict__ status,
-                                               float4* __restrict__ rec, size_t stride, uint32_t n_th,
-                                               float cos_step) {
+__global__ void __launch_bounds__(256) k_eigen(const SegCounters* __restrict__ ctr,
+                                               const uint32_t* __restrict__ list_idx, const float* __restrict__ list_A,
+                                               const uint8_t* __restrict__ nbr, float* __restrict__ nrm,
+                                               uint8_t* __restrict__ status, float4* __restrict__ rec, size_t stride,
+                                               uint32_t n_th, float cos_step) {
     pdl_gate();
     const uint32_t n = ctr->n_list;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -433,7 +434,8 @@ __global__ void __launch_bounds__(kNormT, 8) k_ccl_local(const uint32_t* __restr
             for (int j = 0; j < kIt; ++j) a[j] = rec[(size_t)r * kBrickVox + threadIdx.x + j * kNormT];
 #pragma unroll
             for (int j = 0; j < kIt; ++j)
-                if (__float_as_int(a[j].w) >= want) bn[j] = rec[stride + (size_t)r * kBrickVox + threadIdx.x + j * kNormT];
+                if (__float_as_int(a[j].w) >= want)
+                    bn[j] = rec[stride + (size_t)r * kBrickVox + threadIdx.x + j * kNormT];
 #pragma unroll
             for (int j = 0; j < kIt; ++j) {
                 const int l = threadIdx.x + j * kNormT;
@@ -511,11 +513,11 @@ __global__ void __launch_bounds__(kNormT, 8) k_ccl_local(const uint32_t* __restr
 // few pairs.
 constexpr int kCrossT = 128;
 constexpr int kPairSlots = 256;
-__global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restrict__ nsp, uint32_t cap_b, Grid g, const int32_t* __restrict__ sorted_key,
+__global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restrict__ nsp, uint32_t cap_b, Grid g,
+                                                       const int32_t* __restrict__ sorted_key,
                                                        const int32_t* __restrict__ rank_table,
-                                                       const float4* __restrict__ rec, uint32_t* parent,
-                                                       size_t stride, uint8_t want, float d_th2, float cos_ccl,
-                                                       uint32_t* err) {
+                                                       const float4* __restrict__ rec, uint32_t* parent, size_t stride,
+                                                       uint8_t want, float d_th2, float cos_ccl, uint32_t* err) {
     pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     // The halo at z 0..8 only (forward edges never reach z -1): 10 x 10 x 9
@@ -689,7 +691,8 @@ __device__ __forceinline__ uint32_t brick_rank(bool f, uint32_t* wcnt, uint32_t*
 
 // (1) per-brick counts of kept vertices and of kept roots, and the mask of the
 // brick's kept roots;
-__global__ void __launch_bounds__(kBrickVox) k_brick_tally(const uint32_t* __restrict__ nsp, uint32_t cap_b, const uint32_t* __restrict__ parent,
+__global__ void __launch_bounds__(kBrickVox) k_brick_tally(const uint32_t* __restrict__ nsp, uint32_t cap_b,
+                                                           const uint32_t* __restrict__ parent,
                                                            const uint32_t* __restrict__ count, uint32_t min_cluster,
                                                            uint32_t* __restrict__ nvert, uint32_t* __restrict__ nroot,
                                                            uint32_t* __restrict__ rmask) {
@@ -733,7 +736,8 @@ __global__ void __launch_bounds__(kBrickVox) k_brick_clusters(const uint32_t* __
                                                               const int32_t* __restrict__ sorted_key,
                                                               uint32_t* __restrict__ cl_size,
                                                               uint32_t* __restrict__ cl_label, uint32_t kcap,
-                                                              uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                                              uint32_t* __restrict__ keys,
+                                                              uint32_t* __restrict__ vals) {
     pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ uint32_t wc[kBrickVox / 32];
@@ -795,8 +799,8 @@ cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegB
              zero1);
     cudaError_t e = exclusive_scan_u32(b.flags, b.flags, &b.ctr->n_sorted, nb_total, b.scan_tmp, s, &b.ctr->err);
     if (e != cudaSuccess) return e;
-    launch_k(k_brick_compact, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags, b.rank_table,
-                                                             b.sorted_slot, b.sorted_key);
+    launch_k(k_brick_compact, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags,
+             b.rank_table, b.sorted_slot, b.sorted_key);
     count_launch(2);
     return cudaGetLastError();
 }
@@ -833,25 +837,25 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     const auto clampg = [&](uint32_t want, uint32_t mx) { return want < mx ? (want ? want : 1u) : mx; };
     launch_k(k_seg_guard, dim3(1), dim3(1), 0, s, b.ctr, cap_b);
     VM_STAGE_BEGIN(hk, kStFinalize, s);
-    launch_k(k_finalize, dim3(clampg(cap_b, sms * 16)), dim3(kT), 0, s, nsp, cap_b, b.sorted_slot, S, C, b.M, b.status, stride, b.ctr);
+    launch_k(k_finalize, dim3(clampg(cap_b, sms * 16)), dim3(kT), 0, s, nsp, cap_b, b.sorted_slot, S, C, b.M, b.status,
+             stride, b.ctr);
     VM_STAGE_END(hk, kStFinalize, s);
     const uint8_t want = p.classify ? 2 : 1;
     VM_STAGE_BEGIN(hk, kStNormals, s);
-    launch_k(k_moments, dim3(clampg(cap_b, sms * 16)), dim3(kNormT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table, b.M, b.rec,
-                                                         b.list_idx, b.list_A, b.nbr, stride, b.ctr);
+    launch_k(k_moments, dim3(clampg(cap_b, sms * 16)), dim3(kNormT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table,
+             b.M, b.rec, b.list_idx, b.list_A, b.nbr, stride, b.ctr);
     VM_STAGE_END(hk, kStNormals, s);
     VM_STAGE_BEGIN(hk, kStEigen, s);
-    launch_k(k_eigen, dim3(clampg((uint32_t)((b.nv + 255) / 256), sms * 16)), dim3(256), 0, s, b.ctr, b.list_idx, b.list_A, b.nbr, b.nrm,
-                                                                            b.status, b.rec, stride, p.n_th,
-                                                                            p.cos_step);
+    launch_k(k_eigen, dim3(clampg((uint32_t)((b.nv + 255) / 256), sms * 16)), dim3(256), 0, s, b.ctr, b.list_idx,
+             b.list_A, b.nbr, b.nrm, b.status, b.rec, stride, p.n_th, p.cos_step);
     VM_STAGE_END(hk, kStEigen, s);
     VM_STAGE_BEGIN(hk, kStCclLocal, s);
-    launch_k(k_ccl_local, dim3(clampg(cap_b, sms * 16)), dim3(kNormT), 0, s, nsp, cap_b, b.rec, b.parent, b.count, stride, want, p.d_th2,
-                                                           p.cos_ccl, err);
+    launch_k(k_ccl_local, dim3(clampg(cap_b, sms * 16)), dim3(kNormT), 0, s, nsp, cap_b, b.rec, b.parent, b.count,
+             stride, want, p.d_th2, p.cos_ccl, err);
     VM_STAGE_END(hk, kStCclLocal, s);
     VM_STAGE_BEGIN(hk, kStCcl, s);
-    launch_k(k_ccl_cross, dim3(clampg(cap_b, sms * 16)), dim3(kCrossT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table, b.rec, b.parent,
-                                                            stride, want, p.d_th2, p.cos_ccl, err);
+    launch_k(k_ccl_cross, dim3(clampg(cap_b, sms * 16)), dim3(kCrossT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table,
+             b.rec, b.parent, stride, want, p.d_th2, p.cos_ccl, err);
     VM_STAGE_END(hk, kStCcl, s);
     count_launch(6);
     VM_STAGE_BEGIN(hk, kStClusters, s);
@@ -861,13 +865,14 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     uint32_t* nroot = b.vert_flag;  // vert_flag for kept roots,
     uint32_t* rmask = b.cid;        // cid for the kept-root masks (16 words a brick)
     const unsigned bgrid = clampg(cap_b, sms * 4);
-    launch_k(k_brick_tally, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot, rmask);
+    launch_k(k_brick_tally, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot,
+             rmask);
     cudaError_t e = exclusive_scan_dev(nroot, nroot, &b.ctr->k, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
     e = exclusive_scan_dev(nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
-    launch_k(k_brick_clusters, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nroot, nvert, rmask,
-                                                  b.sorted_key, b.cl_size, b.cl_label, kcap, b.keys, b.vals);
+    launch_k(k_brick_clusters, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nroot, nvert,
+             rmask, b.sorted_key, b.cl_size, b.cl_label, kcap, b.keys, b.vals);
     int bits = 1;
     while ((1ull << bits) < kcap && bits < 32) ++bits;
     e = stable_sort_pairs_dev(b.keys, b.vals, b.keys_alt, b.vals_alt, &b.ctr->n_kept, b.nv, bits, b.sort_tmp, s, err,
@@ -876,8 +881,8 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     e = exclusive_scan_dev(b.cl_size, b.cl_off, &b.ctr->tot, &b.ctr->k, kcap, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
     launch_k(k_clusters_end, dim3(1), dim3(1), 0, s, b.ctr, kcap, b.cl_off);
-    launch_k(k_gather, dim3(grid_for(b.nv, sms)), dim3(kT), 0, s, &b.ctr->n_kept, b.vals, b.vals_alt, &b.ctr->k, bits, b.M, b.nv,
-                                                 b.sorted_key, g, b.pts, b.pt_vid);
+    launch_k(k_gather, dim3(grid_for(b.nv, sms)), dim3(kT), 0, s, &b.ctr->n_kept, b.vals, b.vals_alt, &b.ctr->k, bits,
+             b.M, b.nv, b.sorted_key, g, b.pts, b.pt_vid);
     VM_STAGE_END(hk, kStClusters, s);
     count_launch(5);
     return cudaGetLastError();

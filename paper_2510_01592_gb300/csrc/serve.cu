@@ -301,8 +301,8 @@ cudaError_t enqueue_batch(Server* S, int slot) {
     if ((e = launch_fit(b.apts, b.aoff, b.alab, fb.kdev, b.kcap, S->prm.params, fb, b.tune, sms, s, nullptr)) !=
         cudaSuccess)
         return e;
-    launch_k(k_pack_batch, dim3(b.kcap < 4096 ? b.kcap : 4096), dim3(128), 0, s, b.dtab, fb.kdev, b.aoff, b.alab, fb.cl, fb.hull,
-                                                                  fb.hull_cnt);
+    launch_k(k_pack_batch, dim3(b.kcap < 4096 ? b.kcap : 4096), dim3(128), 0, s, b.dtab, fb.kdev, b.aoff, b.alab, fb.cl,
+             fb.hull, fb.hull_cnt);
     launch_k(k_batch_header, dim3(1), dim3(kMaxBatch), 0, s, b.dtab, fb.hull_cnt, fb.err, b.dstat[slot]);
     count_launch(2);
     return cudaGetLastError();
@@ -394,7 +394,8 @@ void launch_step(Server* S, Server::Step& st) {
         vm_status s = vm_integrate(m, r.xyz, r.n, r.pose, r.on_dev);
         if (s == VM_OK) s = batched ? launch_front(m, S->prm.params) : launch_segment(m, S->prm.params);
         if (s == VM_OK && !sp->ev) sp->ev = get_event(S);
-        if (s == VM_OK && cudaEventRecord(sp->ev, m->stream) != cudaSuccess) s = cuda_status(cudaGetLastError(), "event");
+        if (s == VM_OK && cudaEventRecord(sp->ev, m->stream) != cudaSuccess)
+            s = cuda_status(cudaGetLastError(), "event");
         if (s != VM_OK) {
             vm_planes none{};
             push_result(S, r, s, none, st.t_start);
@@ -428,7 +429,8 @@ void launch_step(Server* S, Server::Step& st) {
     if (s == VM_OK) s = launch_batch(S, st.slot);
     if (s == VM_OK) {
         st.done = get_event(S);
-        if (!st.done || cudaEventRecord(st.done, S->fit_stream) != cudaSuccess) s = cuda_status(cudaGetLastError(), "event");
+        if (!st.done || cudaEventRecord(st.done, S->fit_stream) != cudaSuccess)
+            s = cuda_status(cudaGetLastError(), "event");
     }
     if (s != VM_OK) {  // the batch could not be launched: every member runs alone
         cudaStreamSynchronize(S->fit_stream);

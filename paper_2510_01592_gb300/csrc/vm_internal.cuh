@@ -194,7 +194,8 @@ __device__ __forceinline__ void pack_cluster(const FitCluster& f, uint32_t label
                                              float* __restrict__ hull_xyz, uint32_t hull_cap) {
     const vm_plane p = make_plane(f, label, n_points, ho, hn);
     if (threadIdx.x == 0) *plane = p;
-    for (uint32_t i = threadIdx.x; i < hn && ho + i < hull_cap; i += blockDim.x) write_vertex(p, hull_src[i], ho + i, hull_xy, hull_xyz);
+    for (uint32_t i = threadIdx.x; i < hn && ho + i < hull_cap; i += blockDim.x)
+        write_vertex(p, hull_src[i], ho + i, hull_xy, hull_xyz);
 }
 
 // ---------------------------------------------------------------- diagnostics
