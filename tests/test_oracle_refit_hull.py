@@ -128,7 +128,7 @@ def test_hull_against_qhull(orc, seed):
 
 
 def test_plane_hulls_on_config1(orc):
-    """Invariants on the config-1 planes: orthonormal in-plane basis, strictly
+    """Invariants on the config-1 planes: orthonormal right-handed in-plane basis, strictly
     convex CCW hull, every quantised inlier inside or on it, hull vertices are
     quantised inliers, and the projection agrees with float64 to one unit."""
     import synth
@@ -143,6 +143,10 @@ def test_plane_hulls_on_config1(orc):
         u, v = P["basis_u"][k].astype(np.float64), P["basis_v"][k].astype(np.float64)
         assert abs(u @ n) < 1e-6 and abs(v @ n) < 1e-6 and abs(u @ v) < 1e-6
         assert abs(np.linalg.norm(u) - 1) < 1e-6 and abs(np.linalg.norm(v) - 1) < 1e-6
+        # right-handed (u, v, n): counter-clockwise in (X, Y) is counter-clockwise seen from +n
+        assert np.linalg.det(np.stack([u, v, n])) > 1 - 1e-6
+        # u is e_x x n (no x component) unless n is within 26 deg of e_x, then e_y x n
+        assert P["basis_u"][k][0 if abs(n[0]) < 0.9 else 1] == 0.0
         o, cnt = P["point_off"][k], P["n_points"][k]
         cp = res["pts"][o:o + cnt]
         assert np.array_equal(P["origin"][k], cp[0])
