@@ -967,10 +967,13 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
     }
 }
 
+// Work items per cluster (scanned into the item offsets next), and the work
+// queue's heads cleared for the scoring that follows.
 __global__ void k_items(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int T,
-                        uint32_t* __restrict__ item_cnt) {
+                        uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ queue) {
     pdl_gate();
     const uint32_t k = *kp;
+    if (blockIdx.x == 0 && threadIdx.x < 4) queue[threadIdx.x] = 0;
     for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT)
         item_cnt[c] = (off[c + 1] - off[c] + (uint32_t)T - 1) / (uint32_t)T;
 }
@@ -1095,21 +1098,7 @@ cudaError_t launch_score_warp(const ScoreArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-__global__ void k_set_end(uint32_t* __restrict__ arr, const uint32_t* __restrict__ kp, const uint32_t* __restrict__ v) {
-    pdl_gate();
-    arr[*kp] = *v;
-}
-
 __global__ void k_set_u32(uint32_t* __restrict__ p, uint32_t v) { pdl_gate(); *p = v; }
-
-// arr[*kp] = *v (the end of the work-item offsets) and the work queue's heads
-// cleared for the scoring that follows.
-__global__ void k_items_end(uint32_t* __restrict__ arr, const uint32_t* __restrict__ kp, const uint32_t* __restrict__ v,
-                            uint32_t* __restrict__ queue) {
-    pdl_gate();
-    if (threadIdx.x == 0) arr[*kp] = *v;
-    if (threadIdx.x < 4) queue[threadIdx.x] = 0;
-}
 
 }  // namespace
 
@@ -1194,16 +1183,15 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     cudaError_t e;
     VM_STAGE_BEGIN(hk, kStHyp, s);
     const unsigned kgrid = (kcap + kT - 1) / kT < (uint32_t)sms * 8 ? (kcap + kT - 1) / kT : (uint32_t)sms * 8;
-    launch_k(k_items, dim3(kgrid), dim3(kT), 0, s, off, kp, T, fb.item_off);
-    e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s, fb.err);
+    launch_k(k_items, dim3(kgrid), dim3(kT), 0, s, off, kp, T, fb.item_off, fb.queue);
+    e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s, fb.err, true);
     if (e != cudaSuccess) return e;
-    launch_k(k_items_end, dim3(1), dim3(32), 0, s, fb.item_off, kp, fb.tot, fb.queue);
     const size_t kh = (size_t)kcap * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
     launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid,
              fb.counts, fb.item_off, fb.item_cl);
     VM_STAGE_END(hk, kStHyp, s);
-    count_launch(3);
+    count_launch(2);
     const int grid = sms * t.ctas_per_sm;
     // The warp schedule needs ceil(H / R) <= 32 lanes with R <= 8 and its
     // per-warp tiles within the shared-memory limit; otherwise the CTA one
@@ -1246,11 +1234,10 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     VM_STAGE_BEGIN(hk, kStHull, s);
     launch_k(k_refit, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cen, fb.cl);
     launch_k(k_hull, dim3(cgrid), dim3(kT), fit_hull_smem(), s, off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
-    e = exclusive_scan_dev(fb.hull_cnt, fb.hull_cnt, fb.tot + 1, kp, kcap, fb.scan_tmp, s, fb.err);
+    e = exclusive_scan_dev(fb.hull_cnt, fb.hull_cnt, fb.tot + 1, kp, kcap, fb.scan_tmp, s, fb.err, true);
     if (e != cudaSuccess) return e;
-    launch_k(k_set_end, dim3(1), dim3(1), 0, s, fb.hull_cnt, kp, fb.tot + 1);
     VM_STAGE_END(hk, kStHull, s);
-    count_launch(3);
+    count_launch(2);
     return cudaGetLastError();
 }
 
@@ -1376,12 +1363,11 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
     fit_init_attributes();
-    // the work queue starts at zero every call (k_items_end); counts are zeroed by k_hyp
+    // the work queue starts at zero every call (k_items); counts are zeroed by k_hyp
     launch_k(k_set_u32, dim3(1), dim3(1), 0, s, kdev, k);
-    launch_k(k_items, dim3((k + kT - 1) / kT), dim3(kT), 0, s, off, kdev, t.tile, item_off);
-    if ((e = exclusive_scan_dev(item_off, item_off, total, kdev, k, scan_tmp, s, nullptr)) != cudaSuccess)
+    launch_k(k_items, dim3((k + kT - 1) / kT), dim3(kT), 0, s, off, kdev, t.tile, item_off, queue);
+    if ((e = exclusive_scan_dev(item_off, item_off, total, kdev, k, scan_tmp, s, nullptr, true)) != cudaSuccess)
         return cuda_status(e, "scan");
-    launch_k(k_items_end, dim3(1), dim3(32), 0, s, item_off, kdev, total, queue);
     const size_t kh = (size_t)k * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
     launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, xyz, off, labels, kdev, H, params->seed, 0u, hyp, valid, counts,
@@ -1396,7 +1382,7 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;
     launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, xyz, off, kdev, H, hyp, valid, counts, cl);
     launch_k(k_static_out, dim3((k + kT - 1) / kT), dim3(kT), 0, s, cl, kdev, planes_out, best_h_out, inliers_out);
-    count_launch(7);
+    count_launch(6);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "vm_ransac_static launch");
     return VM_OK;

@@ -67,7 +67,7 @@ __device__ __forceinline__ unsigned long long lb_word(uint32_t epoch, unsigned l
 __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(const uint32_t* in, uint32_t* out, size_t n_cap,
                                                                 const uint32_t* __restrict__ n_dev,
                                                                 uint32_t* __restrict__ total,
-                                                                uint32_t* __restrict__ state, uint32_t* err) {
+                                                                uint32_t* __restrict__ state, uint32_t* err, int end) {
     pdl_gate();
     __shared__ uint32_t buf[kScanTile];
     __shared__ uint32_t ws[kScanThreads / 32];
@@ -120,7 +120,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(const uint32_t* 
                 atomicExch(status + tile, lb_word(epoch, kFlagInc, prefix + agg));
             }
             s_prefix = prefix;
-            if (tile == nt_used - 1 && total) *total = prefix + agg;
+            if (tile == nt_used - 1) {
+                if (total) *total = prefix + agg;
+                if (end) out[n] = prefix + agg;  // no tile reads in[n]
+            }
         }
         __syncthreads();
         uint32_t ex = ex_local + s_prefix;
@@ -136,8 +139,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(const uint32_t* 
             const size_t j = base + t;
             if (j < n) out[j] = buf[t];
         }
-    } else if (tile == 0 && threadIdx.x == 0 && total) {
-        *total = 0;  // nothing to scan
+    } else if (tile == 0 && threadIdx.x == 0) {  // nothing to scan
+        if (total) *total = 0;
+        if (end) out[0] = 0;
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -247,7 +251,8 @@ constexpr int kSmallItems = 4;
 constexpr size_t kSmallMax = 16384;
 
 __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const uint32_t* in, uint32_t* out, size_t n_cap,
-                                                              const uint32_t* __restrict__ n_dev, uint32_t* total) {
+                                                              const uint32_t* __restrict__ n_dev, uint32_t* total,
+                                                              int end) {
     pdl_gate();
     __shared__ uint32_t ws[kSmallThreads / 32];
     __shared__ uint32_t round_total;
@@ -281,7 +286,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const uint32_t* in
         carry += round_total;
         __syncthreads();
     }
-    if (threadIdx.x == 0 && total) *total = carry;
+    if (threadIdx.x == 0) {
+        if (total) *total = carry;
+        if (end) out[n] = carry;  // read by no thread: every load is below n
+    }
 }
 
 }  // namespace
@@ -290,19 +298,22 @@ __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const uint32_t* in
 size_t scan_tmp_words(size_t n) { return 4 + 2 * ((n + kScanTile - 1) / kScanTile) + 2; }
 
 cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
-                               uint32_t* tmp, cudaStream_t s, uint32_t* err) {
+                               uint32_t* tmp, cudaStream_t s, uint32_t* err, bool end) {
     if (n_cap == 0) {
-        if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
-        return cudaSuccess;
+        cudaError_t e = cudaSuccess;
+        if (total) e = cudaMemsetAsync(total, 0, sizeof(uint32_t), s);
+        if (end && e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
+        return e;
     }
     if (n_cap <= kSmallMax) {
-        launch_k(k_scan_small, dim3(1), dim3(kSmallThreads), 0, s, in, out, n_cap, n_dev, total);
+        launch_k(k_scan_small, dim3(1), dim3(kSmallThreads), 0, s, in, out, n_cap, n_dev, total, (int)end);
         count_launch(1);
         return cudaGetLastError();
     }
     if (reinterpret_cast<uintptr_t>(tmp) & 7) return cudaErrorInvalidValue;  // 64-bit status words
     const size_t nt = (n_cap + kScanTile - 1) / kScanTile;
-    launch_k(k_scan_lookback, dim3((unsigned)nt), dim3(kScanThreads), 0, s, in, out, n_cap, n_dev, total, tmp, err);
+    launch_k(k_scan_lookback, dim3((unsigned)nt), dim3(kScanThreads), 0, s, in, out, n_cap, n_dev, total, tmp, err,
+             (int)end);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -73,6 +73,9 @@ __global__ void __launch_bounds__(kT) k_finalize(const uint32_t* __restrict__ ns
                                                  uint8_t* __restrict__ status, size_t stride,
                                                  SegCounters* __restrict__ ctr) {
     pdl_gate();
+    // more bricks than the scratch was sized for: the kernels clamp to it, the
+    // host regrows and reruns
+    if (blockIdx.x == 0 && threadIdx.x == 0 && *nsp > cap_b) atomicOr(&ctr->err, kErrScratch);
     const uint32_t n_sorted = min(*nsp, cap_b);
     uint32_t occ = 0;
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
@@ -805,12 +808,6 @@ cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegB
     return cudaGetLastError();
 }
 
-// Flags a segmentation whose brick or cluster count exceeds the scratch it was
-// launched with; the kernels clamp to the scratch, the host regrows and reruns.
-__global__ void k_seg_guard(SegCounters* __restrict__ ctr, uint32_t cap_b) {
-    pdl_gate();
-    if (ctr->n_sorted > cap_b) ctr->err |= kErrScratch;
-}
 // Clusters beyond the scratch flag a re-run (the count is clamped for the
 // kernels that follow); cl_off[k] = the number of clustered points.
 __global__ void k_clusters_end(SegCounters* __restrict__ ctr, uint32_t kcap, uint32_t* __restrict__ cl_off) {
@@ -835,7 +832,6 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     const size_t stride = b.nv;
     const uint32_t* nsp = &b.ctr->n_sorted;
     const auto clampg = [&](uint32_t want, uint32_t mx) { return want < mx ? (want ? want : 1u) : mx; };
-    launch_k(k_seg_guard, dim3(1), dim3(1), 0, s, b.ctr, cap_b);
     VM_STAGE_BEGIN(hk, kStFinalize, s);
     launch_k(k_finalize, dim3(clampg(cap_b, sms * 16)), dim3(kT), 0, s, nsp, cap_b, b.sorted_slot, S, C, b.M, b.status,
              stride, b.ctr);
@@ -857,7 +853,7 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     launch_k(k_ccl_cross, dim3(clampg(cap_b, sms * 16)), dim3(kCrossT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table,
              b.rec, b.parent, stride, want, p.d_th2, p.cos_ccl, err);
     VM_STAGE_END(hk, kStCcl, s);
-    count_launch(6);
+    count_launch(5);
     VM_STAGE_BEGIN(hk, kStClusters, s);
     launch_k(k_compress_count, dim3(grid_for(b.nv, sms)), dim3(kT), 0, s, nsp, cap_b, b.parent, b.count, b.ctr, err);
     const uint32_t min_cl = p.min_cluster ? p.min_cluster : 1u;

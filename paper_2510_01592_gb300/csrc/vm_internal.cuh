@@ -274,8 +274,10 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* tota
 // (sort_tmp_words) zeroed once when allocated.
 // Variants whose element count is read on the device from n_dev (clamped to
 // the host bound n_cap, which sizes the grids): usable inside a CUDA graph.
+// end: also write the sum at out[n] (n the device count clamped to n_cap; out
+// then holds n_cap + 1 words), the closing offset of an offsets array.
 cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
-                               uint32_t* tmp, cudaStream_t s, uint32_t* err);
+                               uint32_t* tmp, cudaStream_t s, uint32_t* err, bool end = false);
 // key_bound (device, may be null): every key is below *key_bound; passes whose
 // digit no key reaches are skipped on the device, and the result then lies in
 // (keys, vals) after an even number of executed passes and in the alt buffers
