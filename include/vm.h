@@ -196,7 +196,8 @@ vm_status vm_scroll_target(vm_map* map, const float center[3], int32_t shift_bri
 vm_status vm_scroll_to(vm_map* map, const float center[3], int32_t shift_bricks[3]);
 vm_status vm_get_window(vm_map* map, int32_t offset_voxels[3], float position_origin[3]);
 
-/* Destroy a map and release its device memory; waits for its stream. */
+/* Destroy a map and release its device memory; waits for its stream.  A NULL
+ * map is accepted and does nothing (VM_OK). */
 vm_status vm_destroy(vm_map* map);
 
 /* Counters of the map; synchronises its stream. */

@@ -101,3 +101,28 @@ def test_server_footprint_is_host_arithmetic():
     assert serve.footprint((200, 200, 100), (0, 0, 0), 0.02, brick_capacity=0) == \
         serve.footprint((200, 200, 100), (0, 0, 0), 0.02, brick_capacity=10 * n_bricks)
     assert big - small > 3000 * 512 * 28  # at least the pool's sums and counts per brick
+
+
+def test_parameter_and_handle_checks_need_no_gpu():
+    """Segment parameters are validated on the host by every entry point that
+    takes them (n_hyp range, non-negative eps, at most 8 planes a cluster, one
+    round outside vm_segment), and a null map is refused by the window calls."""
+    from paper_2510_01592_gb300 import vm
+    L = vm.load()
+    out = vm.vm_planes()
+    h = C.c_void_p()
+    cases = [(dict(n_hyp=2000), b"n_hyp"), (dict(eps=float("nan")), b"eps"), (dict(eps=-0.01), b"eps"),
+             (dict(planes_per_cluster=9), b"at most 8"), (dict(planes_per_cluster=2), b"vm_segment only")]
+    for kw, msg in cases:
+        p = vm.segment_params(**kw)
+        assert L.vm_fit_planes(None, None, None, 1, C.byref(p), None, C.byref(out)) == vm.VM_ERR_INVALID_ARG
+        assert msg in L.vm_last_error()
+        assert L.vm_fit_plan_create(10, 100, C.byref(p), None, 0, C.byref(h)) == vm.VM_ERR_INVALID_ARG
+        assert msg in L.vm_last_error()
+    sh, ctr = (C.c_int32 * 3)(1, 0, 0), (C.c_float * 3)(0, 0, 0)
+    assert L.vm_scroll(None, sh) == vm.VM_ERR_INVALID_ARG
+    assert L.vm_scroll_to(None, ctr, sh) == vm.VM_ERR_INVALID_ARG
+    assert L.vm_scroll_target(None, ctr, sh) == vm.VM_ERR_INVALID_ARG
+    assert L.vm_get_window(None, sh, ctr) == vm.VM_ERR_INVALID_ARG
+    assert L.vm_integrate(None, None, 0, None, 0) == vm.VM_ERR_INVALID_ARG
+    assert L.vm_destroy(None) == vm.VM_OK  # like free(NULL)
