@@ -14,6 +14,7 @@
 // voxel) with the brick and a one-voxel halo from its 26 neighbours staged in
 // shared memory.
 #include <climits>
+#include <mutex>
 
 #include "vm_internal.cuh"
 
@@ -822,12 +823,12 @@ __global__ void k_clusters_end(SegCounters* __restrict__ ctr, uint32_t kcap, uin
 
 cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* C, const vm_segment_params& p,
                     SegBuffers& b, uint32_t kcap, uint32_t* err, int sms, cudaStream_t s, StageHook* hk) {
-    static bool attributes_set = false;
-    if (!attributes_set) {  // the cross-brick pass fits 8 CTAs an SM only with the largest shared-memory split
+    // the cross-brick pass fits 8 CTAs an SM only with the largest shared-memory split
+    static std::once_flag once;
+    std::call_once(once, [] {
         cudaFuncSetAttribute(k_ccl_cross, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
-        attributes_set = true;
-    }
+    });
     const uint32_t cap_b = (uint32_t)(b.nv / kBrickVox);
     const size_t stride = b.nv;
     const uint32_t* nsp = &b.ctr->n_sorted;
