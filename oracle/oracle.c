@@ -1,11 +1,11 @@
 /*
- * oracle.c -- plain, slow, single-threaded CPU oracle for voxel integration and
+ * oracle.c -- plain, slow CPU oracle for voxel integration and
  * multi-plane segmentation ("Real-time Multi-Plane Segmentation Based on GPU
  * Accelerated High-Resolution 3D Voxel Mapping for Legged Robot Locomotion",
  * arXiv 2510.01592).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
- * baseline leg of the benchmark may load this library.  It shares no code,
+ * baseline and reference legs of the benchmark may load this library.  It shares no code,
  * header, table or constant generator with the CUDA library; the CUDA path
  * never calls it.
  *
