@@ -4,10 +4,10 @@
  * Accelerated High-Resolution 3D Voxel Mapping for Legged Robot Locomotion",
  * arXiv 2510.01592).
  *
- * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
- * baseline and reference legs of the benchmark may load this library.  It shares no code,
- * header, table or constant generator with the CUDA library; the CUDA path
- * never calls it.
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline and reference legs of the benchmark may load this library.  It
+ * shares no code, header, table or constant generator with the CUDA library;
+ * the CUDA path never calls it.
  *
  * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC.  Contraction
  * must stay off: every fused multiply-add below is an explicit fmaf()/fma().
