@@ -126,3 +126,22 @@ def test_parameter_and_handle_checks_need_no_gpu():
     assert L.vm_get_window(None, sh, ctr) == vm.VM_ERR_INVALID_ARG
     assert L.vm_integrate(None, None, 0, None, 0) == vm.VM_ERR_INVALID_ARG
     assert L.vm_destroy(None) == vm.VM_OK  # like free(NULL)
+
+
+def test_binding_constants_match_header():
+    """Every status code and flag the header defines has the same value in the
+    Python binding (status names included)."""
+    from paper_2510_01592_gb300 import vm
+    src = open(os.path.join(ROOT, "include", "vm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {n: int(v) for n, v in re.findall(r"\b(VM_[A-Z_]+)\s*=\s*(\d+)", src)}
+    consts.update({n: int(v) for n, v in re.findall(r"#define\s+(VM_[A-Z_]+)\s+(\d+)u?", src)})
+    assert {"VM_OK", "VM_ERR_EXTENT", "VM_MAP_EAGER", "VM_INTEGRATE_CLEAR", "VM_FIT_EAGER"} <= set(consts)
+    for name, value in consts.items():
+        if name.startswith("VM_SERVE_"):
+            from paper_2510_01592_gb300 import serve
+            assert getattr(serve, name[len("VM_SERVE_"):]) == value, name  # serve.BATCHED, serve.STREAMS
+            continue
+        assert getattr(vm, name) == value, name
+        if name.startswith("VM_ERR_") or name == "VM_OK":
+            assert vm.STATUS_NAMES[value] == name
