@@ -129,9 +129,11 @@ __global__ void __launch_bounds__(kThreads) k_accum(const float* __restrict__ xy
         if (tail && key != kNone) {
             const uint32_t slot = key / kBrickVox, l = key % kBrickVox;
             unsigned long long* s = S + (size_t)slot * 3 * kBrickVox + l;
-            atomicAdd(s, (unsigned long long)(uint32_t)v0);
-            atomicAdd(s + kBrickVox, (unsigned long long)(uint32_t)v1);
-            atomicAdd(s + 2 * kBrickVox, (unsigned long long)(uint32_t)v2);
+            // sign-extended: a run sum is negative when its points lie a
+            // quantum below the window's anchor (reading of the scrolled sums)
+            atomicAdd(s, (unsigned long long)(long long)v0);
+            atomicAdd(s + kBrickVox, (unsigned long long)(long long)v1);
+            atomicAdd(s + 2 * kBrickVox, (unsigned long long)(long long)v2);
             atomicAdd(C + key, (uint32_t)(lane - start + 1));
         }
     }

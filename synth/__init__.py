@@ -36,7 +36,8 @@ import numpy as np
 __all__ = ["MapSpec", "config1", "config2_spec", "config2_scene", "config2_frame", "config2_pose",
            "config3_clusters", "config3_clusters_device", "e5_clusters", "Scene", "Camera", "config4_streams", "config4_scene", "config4_pose", "config4_frame",
            "poisson_arrivals", "identity_pose", "config5_spec", "config5_scene", "config5_pose",
-           "config5_frame", "Lidar", "STAGE", "stage_scene", "stage_orbit_frame"]
+           "config5_frame", "Lidar", "STAGE", "stage_scene", "stage_orbit_frame", "face_values",
+           "far_window_points"]
 
 
 @dataclass
@@ -646,3 +647,59 @@ def poisson_arrivals(rate_hz: float, duration_s: float, seed: int):
         if t >= duration_s:
             return np.array(out)
         out.append(t)
+
+
+def face_values(corner: float, n_ulps: int = 8):
+    """The FP32 values within n_ulps units in the last place of fl32(corner),
+    on both sides of it, ascending (2 n_ulps + 1 values)."""
+    c = np.float32(corner)
+    vals, up, dn = [c], c, c
+    for _ in range(n_ulps):
+        up = np.nextafter(up, np.float32(np.inf))
+        dn = np.nextafter(dn, np.float32(-np.inf))
+        vals += [up, dn]
+    return np.sort(np.array(vals, np.float32))
+
+
+def far_window_points(w, dims, voxel_size, per_cell: int = 12, n_ulps: int = 8, seed: int = 0):
+    """Points around the low faces of a map window far from the base origin.
+
+    The map's base origin is (0, 0, 0) and its window covers voxels
+    w .. w + dims - 1 per axis, so its low face on axis a lies at
+    w[a] * voxel_size.  For each axis a:
+    * a plane over the lower half of the window in the two other axes:
+      per voxel column of that half, per_cell points jittered by up to 0.4
+      voxel about the column's centre, all with the same coordinate a, taken
+      in turn from face_values(w[a] * voxel_size, n_ulps) (the FP32 values
+      just below and above the face);
+    * single points, one per voxel: coordinate a again from those face values
+      (each value twice), the other two at voxel centres of the window's upper
+      half in both of them, so no other point shares their voxels.
+    Identity pose; float32 [n, 3]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = np.asarray(w, np.int64)
+    dims = np.asarray(dims, np.int64)
+    res = float(voxel_size)
+    out = []
+    for a in range(3):
+        fv = face_values(float(w[a]) * res, n_ulps)
+        b, c = (a + 1) % 3, (a + 2) % 3
+        hb, hc = dims[b] // 2, dims[c] // 2
+        ib, ic = np.meshgrid(np.arange(hb), np.arange(hc), indexing="ij")
+        col = np.repeat(np.arange(hb * hc), per_cell)
+        p = np.zeros((len(col), 3), np.float64)
+        p[:, a] = fv[col % len(fv)]
+        p[:, b] = (w[b] + ib.reshape(-1)[col] + 0.5 + rng.uniform(-0.4, 0.4, len(col))) * res
+        p[:, c] = (w[c] + ic.reshape(-1)[col] + 0.5 + rng.uniform(-0.4, 0.4, len(col))) * res
+        out.append(p.astype(np.float32))
+        # singles: voxel centres of the upper half in b and c, one point each
+        cells = [(i, j) for i in range(hb, dims[b]) for j in range(hc, dims[c])]
+        n_single = min(2 * len(fv), len(cells))
+        q = np.zeros((n_single, 3), np.float64)
+        q[:, a] = np.concatenate([fv, fv])[:n_single]
+        for k in range(n_single):
+            i, j = cells[(k * 7) % len(cells)]
+            q[k, b] = (w[b] + i + 0.5) * res
+            q[k, c] = (w[c] + j + 0.5) * res
+        out.append(q.astype(np.float32))
+    return np.concatenate(out)

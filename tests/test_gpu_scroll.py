@@ -159,3 +159,37 @@ def test_odd_pool_capacity_above_the_small_scan(orc, vmmod):
         om.integrate(p)
         compare_sums(gm, om)
     assert gm.stats()["voxels_evicted"] == om.window()["voxels_evicted"] > 0
+
+
+@pytest.mark.parametrize("res,w", [(0.01, (2104, -2072, 2104)), (0.05, (544, -528, -528)),
+                                   (0.02, (-1040, 1056, -1040))])
+def test_far_window_negative_sums_match_the_oracle(orc, vmmod, res, w):
+    """A window far from the base origin (about 21 m at 0.01 m voxels, 26 m
+    at 0.05 m, either sign): points keyed into its first voxel row can
+    quantise one 2^-20 m unit below the window's anchor, so voxel sums are
+    negative (tests/test_oracle_scroll.py checks that these inputs reach that
+    case on every axis, in single-point and many-point voxels).  Sums and
+    counts, means, normals, labels and planes match the oracle bit for bit."""
+    dims = (32, 32, 32)
+    gm = vmmod.VoxelMap(dims, (0.0, 0.0, 0.0), res)
+    om = orc.OracleMap(dims, (0.0, 0.0, 0.0), res)
+    sh = np.asarray(w, np.int32) // 8
+    gm.scroll(sh)
+    om.scroll(sh)
+    assert np.array_equal(gm.window()["offset"], w)
+    p = synth.far_window_points(w, dims, res)
+    eye = np.eye(3, 4, dtype=np.float32).reshape(12)
+    for half in (p[0::2], p[1::2]):  # two frames
+        gm.integrate(half, eye)
+        om.integrate(half)
+    compare_sums(gm, om)
+    _, S, c = om.export_sums()
+    assert ((S < 0) & (c[:, None] == 1)).any() and ((S < 0) & (c[:, None] > 1)).any()
+    d_th = max(0.05, 2 * res)  # at 0.05 m voxels the paper's 0.05 m would cut most neighbour pairs
+    gp = vmmod.segment_params(n_hyp=64, classify=0, d_th=d_th)
+    op = orc.make_params(n_hyp=64, classify=0, d_th=d_th)
+    ores = om.segment(op)
+    gres = gm.segment(gp)
+    compare_labels(gm.export_labels(), ores["voxels"])
+    compare_planes(gres, ores, gm.export_clusters())
+    assert len(gres["planes"]) >= 3

@@ -166,3 +166,40 @@ def test_segmentation_positions_follow_the_window_origin(orc):
     M = ((2 * S + C[:, None]) // (2 * C[:, None].astype(np.int64))).astype(np.int32)
     assert np.array_equal(vb["mu"], (po + M.astype(np.float32) * np.float32(2.0 ** -20)).astype(np.float32))
     assert len(ra["planes"]["label"]) == len(rb["planes"]["label"])
+
+
+# Windows whose low face lies far from the base origin (0.01, 0.02 and 0.05 m
+# voxels, both signs of the offset): there, FP32 points keyed into the window's
+# first voxel row can quantise one 2^-20 m unit below the window's anchor, so
+# their sums are negative.
+FAR_WINDOWS = [(0.01, (2104, -2072, 2104)), (0.05, (544, -528, -528)), (0.02, (-1040, 1056, -1040))]
+FAR_DIMS = (32, 32, 32)
+
+
+@pytest.mark.parametrize("res,w", FAR_WINDOWS)
+def test_far_window_inputs_reach_negative_sums(orc, res, w):
+    """The far-window inputs of the GPU test really contain points keyed into
+    the window whose quantised offset from the anchor is -1, on every axis,
+    in voxels holding many points and in single-point voxels.  Checked two
+    ways: the oracle's exported sums, and a direct numpy evaluation of the
+    keying and quantisation (FP32 floor of d * inv_res; rint of d * 2^20 less
+    the anchor floor(w * 2^20 / inv_res) in double)."""
+    m = orc.OracleMap(FAR_DIMS, (0.0, 0.0, 0.0), res)
+    m.scroll(np.asarray(w, np.int32) // 8)
+    assert np.array_equal(m.window()["offset"], w)
+    p = synth.far_window_points(w, FAR_DIMS, res)
+    m.integrate(p)
+    vid, S, c = m.export_sums()
+    inv = np.float32(1.0 / res)
+    for a in range(3):
+        assert (S[:, a] < 0).any(), f"axis {a}: no negative sum"
+        assert ((S[:, a] == -1) & (c == 1)).any(), f"axis {a}: no single-point voxel at -1"
+        assert ((S[:, a] < 0) & (c > 1)).any(), f"axis {a}: no negative sum over several points"
+        key = np.floor((p[:, a] * inv).astype(np.float32)).astype(np.int64)
+        anchor = int(np.floor(w[a] * 1048576.0 / float(inv)))
+        F = np.rint((p[:, a] * np.float32(1048576.0)).astype(np.float32)).astype(np.int64) - anchor
+        inside = np.ones(len(p), bool)
+        for b in range(3):
+            kb = np.floor((p[:, b] * inv).astype(np.float32)).astype(np.int64)
+            inside &= (kb >= w[b]) & (kb < w[b] + FAR_DIMS[b])
+        assert ((key == w[a]) & (F == -1) & inside).any()
