@@ -52,7 +52,8 @@ class Plane(C.Structure):
                 ("best_h", C.c_int32), ("ill_conditioned", C.c_int32), ("ransac_n", C.c_float * 3),
                 ("ransac_d", C.c_float), ("refit_n", C.c_double * 3), ("refit_d", C.c_double),
                 ("basis_u", C.c_float * 3), ("basis_v", C.c_float * 3), ("origin", C.c_float * 3),
-                ("hull_off", C.c_uint32), ("hull_n", C.c_uint32), ("point_off", C.c_uint32), ("round", C.c_uint32)]
+                ("hull_off", C.c_uint32), ("hull_n", C.c_uint32), ("point_off", C.c_uint32), ("round", C.c_uint32),
+                ("cond", C.c_double)]
 
 
 class Params(C.Structure):
@@ -146,7 +147,7 @@ def make_params(n_th=3, theta_step_deg=15.0, d_th=0.05, theta_ccl_deg=15.0, min_
 def _planes_to_dict(planes, n):
     out = {k: [] for k in ("label", "n_points", "inlier_count", "best_h", "ill_conditioned", "ransac_n",
                            "ransac_d", "refit_n", "refit_d", "basis_u", "basis_v", "origin", "hull_off",
-                           "hull_n", "point_off", "round")}
+                           "hull_n", "point_off", "round", "cond")}
     for i in range(n):
         p = planes[i]
         for k in out:
@@ -155,7 +156,8 @@ def _planes_to_dict(planes, n):
     dt = {"label": np.uint32, "n_points": np.uint32, "inlier_count": np.uint32, "best_h": np.int32,
           "ill_conditioned": np.int32, "ransac_n": np.float32, "ransac_d": np.float32, "refit_n": np.float64,
           "refit_d": np.float64, "basis_u": np.float32, "basis_v": np.float32, "origin": np.float32,
-          "hull_off": np.uint32, "hull_n": np.uint32, "point_off": np.uint32, "round": np.uint32}
+          "hull_off": np.uint32, "hull_n": np.uint32, "point_off": np.uint32, "round": np.uint32,
+          "cond": np.float64}
     res = {}
     for k, v in out.items():
         a = np.array(v, dtype=dt[k])

@@ -109,6 +109,7 @@ typedef struct {
     uint32_t hull_n;
     uint32_t point_off;      /* offset of this cluster in the point arrays    */
     uint32_t round;          /* extraction round of this plane in its cluster */
+    double cond;             /* refit: lambda_mid / lambda_min (inf when only lambda_min is 0, NaN when both are) */
 } orc_plane;
 
 typedef struct {
@@ -807,6 +808,7 @@ static int fit_cluster(const float *pts, uint32_t n, uint32_t label, uint32_t ro
         lo = e[0];
     }
     pl->ill_conditioned = !(mid >= 10.0 * lo);
+    pl->cond = lo > 0.0 ? mid / lo : (mid > 0.0 ? INFINITY : NAN);
     /* hull: in-plane basis from the RANSAC normal, origin = the cluster's first
      * point, coordinates quantised to 2^-16 m, exact integer monotone chain */
     float nx = bn[0], ny = bn[1], nz = bn[2];

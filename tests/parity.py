@@ -3,7 +3,9 @@
 Bit-exact: voxel ids, sums and counts; normals, N and status; CCL labels;
 cluster point lists; RANSAC hypothesis index, plane, inlier sets; in-plane
 basis, origin and quantised hulls.  Tolerance (the refit): normal within
-1e-4 rad and offset within 1e-5 m, planes flagged ill-conditioned excluded."""
+1e-4 rad and offset within 1e-5 m, planes the oracle flags ill-conditioned
+excluded; the GPU's ill-conditioned flag equals the oracle's wherever the
+oracle's lambda_mid / lambda_min lies outside [9, 11]."""
 import math
 
 import numpy as np
@@ -55,8 +57,23 @@ def compare_labels(glab, ovox):
     assert_same(glab["label"], ovox["label"], "CCL labels")
 
 
+class RefitReport(tuple):
+    """(worst angle, worst offset, planes excluded from the refit tolerance,
+    planes with a valid hypothesis); unpacks as (worst angle, worst offset)
+    for callers that want only those."""
+
+    def __new__(cls, worst_angle, worst_offset, excluded, checked):
+        r = super().__new__(cls, (worst_angle, worst_offset))
+        r.excluded, r.valid = excluded, checked
+        return r
+
+
 def compare_planes(gres, ores, gclusters=None, check_refit=True):
-    """gres: VoxelMap.segment / fit_planes output; ores: oracle result dict."""
+    """gres: VoxelMap.segment / fit_planes output; ores: oracle result dict.
+
+    Returns a RefitReport.  A plane is excluded from the refit tolerance only
+    by the oracle (ill-conditioned in double, or fewer than 3 inliers), never
+    by a flag the GPU sets."""
     gp, op = gres["planes"], ores["planes"]
     assert len(gp) == len(op["label"]), f"plane count {len(gp)} vs {len(op['label'])}"
     assert_same(gp["label"], op["label"], "labels")
@@ -82,9 +99,25 @@ def compare_planes(gres, ores, gclusters=None, check_refit=True):
         o = ores["hull"][op["hull_off"][i]:op["hull_off"][i] + op["hull_n"][i]]
         assert np.array_equal(g, o), f"hull of plane {i} (label {gp['label'][i]}): {g[:6]} vs {o[:6]}"
     worst_a = worst_d = 0.0
+    excluded = 0
     if check_refit:
         for i in np.nonzero(valid)[0]:
-            if op["ill_conditioned"][i] or (gp["flags"][i] & 1) or op["inlier_count"][i] < 3:
+            if op["inlier_count"][i] < 3:
+                excluded += 1
+                continue
+            # The ill-conditioned flag is checked against the oracle's own
+            # lambda_mid / lambda_min wherever that ratio is clear of the
+            # threshold 10 (outside [9, 11]); near it, the GPU's FP32 /
+            # double-float eigenvalues and the oracle's double Jacobi may
+            # round to different sides, and the flag is not compared.
+            cond = float(op["cond"][i]) if "cond" in op else float("nan")
+            if not (9.0 <= cond <= 11.0) and not math.isnan(cond):
+                assert bool(gp["flags"][i] & 1) == bool(op["ill_conditioned"][i]), \
+                    f"ill-conditioned flag of plane {i}: GPU {gp['flags'][i] & 1}, oracle " \
+                    f"{op['ill_conditioned'][i]} (lambda_mid / lambda_min = {cond:.4g})"
+            # Only the oracle's flag excludes a plane from the tolerance.
+            if op["ill_conditioned"][i]:
+                excluded += 1
                 continue
             gn = gp["normal"][i].astype(np.float64)
             on = op["refit_n"][i]
@@ -95,4 +128,4 @@ def compare_planes(gres, ores, gclusters=None, check_refit=True):
             worst_a, worst_d = max(worst_a, ang), max(worst_d, dd)
             assert ang <= REFIT_ANGLE_TOL, f"refit normal of plane {i}: {ang:.3g} rad"
             assert dd <= REFIT_OFFSET_TOL, f"refit offset of plane {i}: {dd:.3g} m"
-    return worst_a, worst_d
+    return RefitReport(worst_a, worst_d, excluded, int(valid.sum()))

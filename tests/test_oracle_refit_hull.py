@@ -53,6 +53,11 @@ def test_refit_matches_svd(orc, seed):
     n = Vt[-1] * np.sign(Vt[-1][2])
     assert abs(float(n @ P["refit_n"][0])) > 1 - 1e-12
     assert abs(P["refit_d"][0] + float(n @ c)) < 1e-9
+    # the conditioning the ill-conditioned flag reads: lambda_mid / lambda_min
+    # of the centred inlier scatter, from the squared singular values
+    sv = np.linalg.svd(X - c, compute_uv=False) ** 2
+    assert abs(P["cond"][0] / (sv[1] / sv[2]) - 1) < 1e-8
+    assert P["ill_conditioned"][0] == (sv[1] / sv[2] < 10)
 
 
 def test_refit_flags_ill_conditioned_strip(orc):
@@ -61,6 +66,10 @@ def test_refit_flags_ill_conditioned_strip(orc):
     pts = np.c_[x, rng.uniform(0, 0.001, 2000), rng.normal(0, 0.0005, 2000)].astype(np.float32)
     res = orc.fit_planes(pts, [0, 2000], orc.make_params(n_hyp=64, eps=0.01))
     assert res["planes"]["ill_conditioned"][0] == 1
+    X = pts[res["inlier"].astype(bool)].astype(np.float64)
+    sv = np.linalg.svd(X - X.mean(axis=0), compute_uv=False) ** 2
+    assert res["planes"]["cond"][0] < 10
+    assert abs(res["planes"]["cond"][0] / (sv[1] / sv[2]) - 1) < 1e-8
 
 
 def _brute_hull(P):
