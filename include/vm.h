@@ -279,11 +279,19 @@ vm_status vm_fit_plan_destroy(vm_fit_plan* plan);
  * robot control loop with a hard deadline (cudaMalloc can stall on
  * device-wide synchronisation for an unbounded time) or a host program whose
  * device memory is owned up front by another allocator.  It runs the same
- * hypothesis, scoring and selection kernels as vm_fit_planes (Sec. III.C
- * stages a-c) on caller-formed clusters, with all scratch in one array
- * compiled into the library (about 11 MiB per GPU that loads it, held until
- * the process exits); it calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * hypothesis, scoring and selection kernels as vm_fit_planes on
+ * caller-formed clusters, with all scratch in one array compiled into the
+ * library (about 11 MiB); it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ * Set-up: the array is placed on a GPU when the library's device code is
+ * loaded there, which with lazy module loading (the CUDA default) happens at
+ * the first call made on that device; that call also looks up the array's
+ * device address (with the device current) and caches it.  Make that first
+ * call during set-up, before any stream capture: a call with k == 0 does the
+ * set-up and launches nothing.  From then on the array stays on that device
+ * until the process exits.  The cached address does not survive
+ * cudaDeviceReset (or any other teardown of the device's primary context):
+ * do not call this entry point after one.
  * Limits: k <= 4096 clusters and k * n_hyp <= 524288; larger requests return
  * VM_ERR_CAPACITY with a message and launch nothing.
  * Inputs (device): xyz float32[off[k]][3]; off uint32[k+1]; labels uint32[k]
@@ -296,9 +304,7 @@ vm_status vm_fit_plan_destroy(vm_fit_plan* plan);
  * Every call on a device shares the one scratch array, which keeps the last
  * call's contents (the work queue and counters are cleared at the start of
  * each call): calls whose work overlaps on the GPU race, so serialise them
- * (one stream, or events).  The first call on a device looks up the array's
- * device address with that device current; make that first call before any
- * stream capture. */
+ * (one stream, or events). */
 vm_status vm_ransac_static(const float* xyz, const uint32_t* off, const uint32_t* labels, uint32_t k,
                            const vm_segment_params* params, void* stream, float* planes_out, int32_t* best_h_out,
                            uint32_t* inliers_out);

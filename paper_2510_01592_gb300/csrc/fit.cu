@@ -1277,7 +1277,8 @@ constexpr size_t kOffCl = kOffValid + align256((size_t)kStaticMaxSlots);
 constexpr size_t kOffItems = kOffCl + align256((size_t)kStaticMaxClusters * sizeof(FitCluster));
 constexpr size_t kOffQueue = kOffItems + align256((size_t)(kStaticMaxClusters + 1) * sizeof(uint32_t));
 constexpr size_t kOffScan = kOffQueue + 256;  // the queue area also holds the count and a scan total
-constexpr size_t kScanWords = 64;  // >= scan_tmp_words(kStaticMaxClusters + 1)
+constexpr size_t kScanWords = 64;
+static_assert(kScanWords >= scan_tmp_words(kStaticMaxClusters + 1), "static scan scratch too small");
 constexpr size_t kStaticBytes = kOffScan + align256(kScanWords * sizeof(uint32_t));
 
 // Copies the selected plane, hypothesis index and inlier count of each cluster
@@ -1322,13 +1323,14 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
         set_error("vm_ransac_static: n_hyp must be in [1, 1024], eps >= 0 and planes_per_cluster <= 1");
         return VM_ERR_INVALID_ARG;
     }
-    if (k == 0) return VM_OK;
     if (k > kStaticMaxClusters || (uint64_t)k * params->n_hyp > kStaticMaxSlots) {
         set_error("vm_ransac_static: " + std::to_string(k) + " clusters x " + std::to_string(params->n_hyp) +
                   " hypotheses exceed the static scratch (at most " + std::to_string(kStaticMaxClusters) +
                   " clusters and " + std::to_string(kStaticMaxSlots) + " cluster-hypothesis pairs)");
         return VM_ERR_CAPACITY;
     }
+    // The address lookup comes before the k == 0 return, so an empty call
+    // serves as the set-up call that loads the array on this device.
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
@@ -1347,6 +1349,7 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
         }
         base = static_cast<char*>(g_static_addr[dev]);
     }
+    if (k == 0) return VM_OK;
     const int H = (int)params->n_hyp;
     const FitTuning t = default_tuning();
     float4* hyp = reinterpret_cast<float4*>(base + kOffHyp);
@@ -1372,12 +1375,22 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
     launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, xyz, off, labels, kdev, H, params->seed, 0u, hyp, valid, counts,
              item_off, static_cast<uint32_t*>(nullptr));
-    int R = t.hyp_per_thread;
-    while (R < 8 && (H + R - 1) / R > kT) R <<= 1;
+    // The CTA-per-item schedule whatever the tuning asks for: with no
+    // item -> cluster table here, the clusters of work items come from a
+    // binary search, which only that schedule does.
+    FitTuning tc = t;
+    tc.schedule = 0;
+    int R;
+    bool warp;
+    score_variant(tc, H, R, warp);
     const int grid = sms * t.ctas_per_sm;
-    // no item -> cluster table here: the clusters of work items by binary search
     const ScoreArgs sa{xyz, off, item_off, nullptr, kdev, H, t.tile, hyp, counts, queue, params->eps, grid};
-    e = R == 8 ? launch_score<8>(sa, s) : launch_score<4>(sa, s);
+    switch (R) {
+        case 1: e = launch_score<1>(sa, s); break;
+        case 2: e = launch_score<2>(sa, s); break;
+        case 8: e = launch_score<8>(sa, s); break;
+        default: e = launch_score<4>(sa, s); break;
+    }
     if (e != cudaSuccess) return cuda_status(e, "k_score");
     const unsigned cgrid = k < (uint32_t)sms * 8 ? k : (uint32_t)sms * 8;
     launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, xyz, off, kdev, H, hyp, valid, counts, cl);

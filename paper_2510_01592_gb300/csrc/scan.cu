@@ -294,8 +294,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const uint32_t* in
 
 }  // namespace
 
-// Look-back state: ticket, done, epoch, pad, then one 64-bit word per tile.
-size_t scan_tmp_words(size_t n) { return 4 + 2 * ((n + kScanTile - 1) / kScanTile) + 2; }
+static_assert((size_t)kScanTile == kScanTileElems, "scan_tmp_words assumes the scan's tile size");
 
 cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
                                uint32_t* tmp, cudaStream_t s, uint32_t* err, bool end) {

@@ -266,7 +266,10 @@ vm_status ensure(DevBuf& b, size_t bytes);
 // the single-pass scan's look-back state, which every launch leaves ready
 // for the next).  err (device, may be null): kErrTimeout when a bounded
 // look-back wait ran out.
-size_t scan_tmp_words(size_t n);
+// Elements per tile of the single-pass scan; its look-back state is a
+// ticket, a done count, an epoch, a pad word and one 64-bit word per tile.
+constexpr size_t kScanTileElems = 2048;
+constexpr size_t scan_tmp_words(size_t n) { return 4 + 2 * ((n + kScanTileElems - 1) / kScanTileElems) + 2; }
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* total, size_t n, uint32_t* tmp,
                                cudaStream_t s, uint32_t* err);
 // Stable sort of (key, value) pairs by key, key < 2^bits (bits <= 32), LSD

@@ -4,9 +4,10 @@ Some callers cannot allocate device memory while running (a control loop with
 a deadline, or a program whose device memory is owned by another allocator);
 vm_ransac_static serves them from scratch compiled into the library.  This
 test calls it through the C ABI, twice in a row on different batches, and
-checks each result against vm_fit_planes on the same clusters: selected
-hypothesis, plane and inlier count must be equal bit for bit (the tolerance
-the parity tests use for RANSAC).  The file sorts last so a stop-at-first-
+checks each result against vm_fit_planes and against the CPU oracle on the
+same clusters: selected hypothesis, plane and inlier count must be equal bit
+for bit (the tolerance the parity tests use for RANSAC).  A first call with
+no clusters does the per-device set-up.  The file sorts last so a stop-at-first-
 failure run has run every other test before it."""
 import ctypes as C
 
@@ -39,10 +40,13 @@ def lib():
     return vm, vm.load()
 
 
-def test_static_ransac_matches_fit_planes_twice(lib):
+def test_static_ransac_matches_fit_planes_twice(lib, orc):
     import torch
     vm, L = lib
     fn = _static_fn(L)
+    # the set-up call: k == 0 loads the array and looks up its address
+    prm0 = vm.segment_params(n_hyp=16)
+    assert fn(None, None, None, 0, C.addressof(prm0), None, None, None, None) == vm.VM_OK
     for call, (seed, k, hi, H, key) in enumerate([(21, 300, 30000, 256, 7), (22, 57, 5000, 100, 99)]):
         xyz, off = _batch(seed, k, hi)
         labels = (np.arange(k, dtype=np.uint32) * 3 + call).astype(np.uint32)
@@ -65,6 +69,12 @@ def test_static_ransac_matches_fit_planes_twice(lib):
         assert np.array_equal(planes[ok, :3].view(np.uint32), ref["ransac_normal"][ok].view(np.uint32))
         assert np.array_equal(planes[ok, 3].view(np.uint32), ref["ransac_offset"][ok].view(np.uint32))
         assert np.array_equal(inl[ok], ref["inlier_count"][ok])
+        # and directly against the oracle's stages a-c on the same clusters
+        o = orc.fit_planes(xyz, off, orc.make_params(n_hyp=H, seed=key), labels=labels)["planes"]
+        assert np.array_equal(best, o["best_h"])
+        assert np.array_equal(planes[ok, :3].view(np.uint32), o["ransac_n"][ok].view(np.uint32))
+        assert np.array_equal(planes[ok, 3].view(np.uint32), o["ransac_d"][ok].view(np.uint32))
+        assert np.array_equal(inl[ok], o["inlier_count"][ok])
 
 
 def test_static_ransac_rejects_oversize_requests(lib):
