@@ -32,17 +32,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N_FRAMES = 300
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per allocated
-# brick, from one ncu capture of each kernel as it stands on the 60-frame case
-# of the trajectory (1,498 bricks; profiles/segment_kernels_60frames.md).  A
-# launch stages a fixed halo per brick, so traffic is scaled to the timed map by
-# its brick count.  Remove a kernel's entry when the kernel changes.
-TRAFFIC_PER_BRICK = {
-    "moments": (9291776.0 + 0.0) / 1498,
-    "eigen": (4150016.0 + 77568.0) / 1498,
-    "ccl_local": 14557952.0 / 1498,
-    "ccl_cross": (15073792.0 + 1536.0) / 1498,
-}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# kernel, from one ncu capture of the kernel as it stands, divided by the
+# stat its work scales with: {stage: (bytes per unit, stat)}.  Remove a
+# kernel's entry when the kernel changes.
+TRAFFIC_PER_UNIT = {}
 METRIC = "0.01 m integrate+segment: frames/s, p50/p99 ms, batched/served vs plain GPU"
 WORKLOAD = ("paper-scale trajectory: 4x4x2 m map at 0.01 m (sparse 8^3 bricks), 640x480 depth camera "
             "(87x58 deg, 0.3-4 m, sigma 1 mm + 0.2% range) over an 8-step open-tread stair, overhanging desk, "
@@ -727,6 +721,19 @@ def seg_params(vm):
     return vm.segment_params(n_hyp=100, seed=0)
 
 
+def bench_config(steps, warmup, ws=1):
+    """The workload description both arms print (the GPU arm and the oracle's
+    reference arm time the same frames of the same trajectory)."""
+    first, _ = frame_schedule(steps, warmup)
+    return {"workload": WORKLOAD,
+            "frames_timed": f"{first + warmup + 1}..{first + warmup + steps}"
+            if first + warmup + steps <= N_FRAMES else "wrapping trajectory",
+            "voxel_m": 0.01, "map_m": [4, 4, 2], "points_per_frame": 307200, "ransac_hypotheses": 100,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "l2": "inputs larger than L2: a distinct 3.7 MB frame per step from a 1.1 GB resident "
+                  "trajectory; per-step map state (pool + segmentation arrays) well above the 129 MB L2"}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -993,13 +1000,8 @@ def run_gpu(args):
         "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic (ray-cast scenes)",
-        "config": {"workload": WORKLOAD, "frames_timed": f"{first + args.warmup + 1}..{first + args.warmup + args.steps}"
-                   if first + args.warmup + args.steps <= N_FRAMES else "wrapping trajectory",
-                   "voxel_m": 0.01, "map_m": [4, 4, 2], "points_per_frame": 307200, "ransac_hypotheses": 100,
-                   "fit_tuning": dict(tuning, autotune_candidates=tune_n, autotune_ms=round(tune_ms, 4)),
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2: a distinct 3.7 MB frame per step from a 1.1 GB resident "
-                         "trajectory; per-step map state (pool + segmentation arrays) well above the 129 MB L2"},
+        "config": bench_config(args.steps, args.warmup, ws),
+        "fit_tuning": dict(tuning, autotune_candidates=tune_n, autotune_ms=round(tune_ms, 4)),
         "p50_ms": round(statistics.median(per_step), 4),
         "p99_ms": round(sorted(per_step)[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)], 4),
         "gpu_launches": int(launches),
@@ -1036,9 +1038,12 @@ def run_gpu(args):
     if not args.no_eval and rank == 0:
         res["variants"]["evaluation"] = evaluation_variant(dev, stream)
     res["stages_ms_per_step"] = {k: round(v[0] / max(1, args.steps), 4) for k, v in stages.items() if v[1]}
-    table = kernel_table(stages, st, load_peaks(), st["clustered_points"])
+    timed = [sched[args.warmup + i] for i in range(args.steps)]
+    fv = sum(frame_voxels(pts[f], poses[f], spec) for f in timed) / max(1, len(timed))
+    table = kernel_table(stages, st, load_peaks(), st["clustered_points"], frame_points=640 * 480,
+                         frame_voxels=fv)
     res["kernels"] = table
-    res["roofline"] = roofline(table, {k: v * st["bricks_allocated"] for k, v in TRAFFIC_PER_BRICK.items()})
+    res["roofline"] = roofline(table, {k: v * st[unit] for k, (v, unit) in TRAFFIC_PER_UNIT.items()})
     return res, rank
 
 
@@ -1046,22 +1051,37 @@ def run_gpu(args):
 SM_COUNT, FP32_LANES = 152, 128
 
 
-def kernel_table(stages, st, peaks, n_points_segment):
-    """Per-stage average launch time and, for single-kernel stages, the achieved
-    rate against the measured peak.  Algorithmic bytes / ops per unit of each
-    kernel's model: slots = allocated bricks x 512 voxels, occ = occupied voxels."""
+def kernel_table(stages, st, peaks, n_points_segment, frame_points=0, frame_voxels=0, n_hyp=100):
+    """Per-stage average launch time and, for the stages the method's own
+    units price, the achieved rate against the measured peak: algorithmic
+    bytes (or instructions) of one launch / its average CUDA-event time.
+
+    Algorithmic units (what the method must move, whatever the kernel
+    stages): integrate 12 B read per frame point + 4 B brick-table probe per
+    point + 28 B read-modify-write per distinct voxel the frame touches;
+    finalize 28 B sums and count read + 12 B mean written + 4 B id per
+    occupied voxel; moments 12 B mean read + 1 B neighbour count written per
+    occupied voxel; eigen ~520 FP32 instructions per occupied voxel; CCL 24 B
+    (mean, normal) + 4 B label x (1 + 1 pass) per vertex (steppable voxel);
+    RANSAC scoring 5 instructions per point-hypothesis test.  staged_bytes:
+    what the kernel as written reads and writes for the same launch, where
+    it differs (per-slot staging of allocated bricks: slots = bricks x 512).
+    kernels: launches in the stage; only single-kernel stages are roofline
+    candidates."""
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     clk = (peaks or {}).get("sm_max_mhz", 2070.0) * 1e6
     alu_peak = SM_COUNT * FP32_LANES * clk / 1e12  # T instructions/s
     occ = st["occupied_voxels"]
+    vert = st["steppable_voxels"]
     slots = st["bricks_allocated"] * 512
-    model = {
-        "finalize": ("hbm", slots * (4 + 1 + 12) + occ * 24),
-        "moments": ("hbm", slots * (12 + 16) + occ * (4 + 24 + 1)),
-        "eigen": ("alu", occ * 520),
-        "ccl_local": ("hbm", slots * (16 + 8) + occ * 16),
-        "ccl_cross": ("hbm", slots * (16 + 4) + occ * 16),
-        "ransac_score": ("alu", n_points_segment * 100 * 5),
+    model = {  # name: (bound, algorithmic amount, staged bytes or None, kernels in the stage)
+        "integrate": ("hbm", frame_points * (12 + 4) + frame_voxels * 28,
+                      frame_points * (12 * 2 + 4) + frame_voxels * 28, 2),
+        "finalize": ("hbm", occ * (28 + 12 + 4), slots * (4 + 1 + 12) + occ * 24, 1),
+        "moments": ("hbm", occ * (12 + 1), slots * (12 + 16 + 8) + occ * (4 + 24 + 1), 1),
+        "eigen": ("alu", occ * 520, None, 1),
+        "ccl": ("hbm", vert * (24 + 4 * 2), None, 1),
+        "ransac_score": ("alu", n_points_segment * n_hyp * 5, None, 1),
     }
     out = {}
     for name, (ms_tot, calls) in stages.items():
@@ -1070,7 +1090,7 @@ def kernel_table(stages, st, peaks, n_points_segment):
         ms = ms_tot / calls
         row = {"avg_launch_ms": round(ms, 4)}
         if name in model:
-            bound, amount = model[name]
+            bound, amount, staged, nk = model[name]
             if bound == "hbm":
                 ach = amount / (ms / 1e3) / 1e9
                 row.update(bound="hbm", achieved=round(ach, 1), peak=hbm, unit="GB/s", frac=round(ach / hbm, 4),
@@ -1079,13 +1099,18 @@ def kernel_table(stages, st, peaks, n_points_segment):
                 ach = amount / (ms / 1e3) / 1e12
                 row.update(bound="alu", achieved=round(ach, 3), peak=round(alu_peak, 1), unit="T instr/s",
                            frac=round(ach / alu_peak, 4), algorithmic=int(amount))
+            if staged is not None:
+                row["staged_bytes"] = int(staged)
+            row["kernels"] = nk
         out[name] = row
     return out
 
 
 def roofline(table, traffic=None):
-    """The dominant single-kernel stage's row (a stage of one kernel)."""
-    single = {k: v for k, v in table.items() if "bound" in v}
+    """The dominant single-kernel stage's row; traffic: DRAM bytes per launch
+    from an ncu capture of that kernel, and its ratio to the algorithmic
+    bytes."""
+    single = {k: v for k, v in table.items() if "bound" in v and v.get("kernels", 1) == 1}
     if not single:
         return None
     dom = max(single, key=lambda k: single[k]["avg_launch_ms"])
@@ -1093,17 +1118,55 @@ def roofline(table, traffic=None):
     r["kernel"] = dom
     t = (traffic or {}).get(dom)
     r["traffic"] = None if t is None else int(t)
+    if t is not None and r["bound"] == "hbm" and r["algorithmic"]:
+        r["traffic_ratio"] = round(t / r["algorithmic"], 3)
     r["peak_source"] = "MEASURED_PEAKS.json" if load_peaks() else "fallback"
     return r
 
 
-def cpu_baseline(budget_s, all_cores=True):
+def frame_voxels(pts, pose, spec):
+    """Distinct voxels a frame's points fall in (the integrate stage's
+    algorithmic unit), counted with torch on the frame's device."""
+    import torch
+    R = torch.tensor(pose, dtype=torch.float32, device=pts.device).reshape(3, 4)
+    w = pts @ R[:, :3].T + R[:, 3]
+    o = torch.tensor(spec.origin, dtype=torch.float32, device=pts.device)
+    k = torch.floor((w - o) * (1.0 / spec.voxel_size)).to(torch.int64)
+    d = torch.tensor(spec.dims, dtype=torch.int64, device=pts.device)
+    ok = ((k >= 0) & (k < d)).all(dim=1)
+    k = k[ok]
+    return int(torch.unique((k[:, 2] * d[1] + k[:, 1]) * d[0] + k[:, 0]).numel())
+
+
+def headline(res):
+    """The batched / served figures against the plain per-frame pipeline,
+    gathered from the variants into flat keys."""
+    v = res.get("variants", {})
+    h = {"graph_frames_per_s": v.get("graph_frames_per_s"),
+         "plain_eager_frames_per_s": v.get("plain_eager_frames_per_s")}
+    sv = v.get("serving_config4")
+    if sv:
+        h.update(served_fps=sv["saturation_batched"]["frames_per_s"],
+                 served_streams_fps=sv["saturation_streams"]["frames_per_s"],
+                 plain_fps=sv["saturation_plain_per_frame"]["frames_per_s"],
+                 served_p50_ms=sv["poisson_30hz"]["latency_ms"]["p50"],
+                 served_p99_ms=sv["poisson_30hz"]["latency_ms"]["p99"],
+                 served_worst_stream_p99_ms=sv["poisson_30hz"]["worst_stream_p99_ms"],
+                 served_streams=sv["streams"], served_rate_hz=30)
+    bt = v.get("batching_config3")
+    if bt:
+        h.update(batch_ms=bt["batched_ms"], plain_batch_ms=bt["plain_ms"], batch_speedup=bt["speedup"])
+    return {k: x for k, x in h.items() if x is not None}
+
+
+def cpu_baseline(budget_s, all_cores=True, steps=30, warmup=0):
     """The oracle as it stands, single-threaded on the host, over a bounded
-    sample: frames integrated untimed up to the timed window, then
-    integrate + segment per frame until the budget is spent.  all_cores adds
-    the same sample with the oracle's independent stages (integration over
-    point ranges, normals over voxels, fits over clusters) on every host core;
-    its results are identical."""
+    sample of the frames the GPU arm times: the frames before them
+    integrated untimed (the warm-up frames integrated and segmented), then
+    integrate + segment per frame until the frames or the budget run out.
+    all_cores adds the same sample with the oracle's independent stages
+    (integration over point ranges, normals over voxels, fits over clusters)
+    on every host core; its results are identical."""
     import torch
 
     import oracle
@@ -1112,7 +1175,8 @@ def cpu_baseline(budget_s, all_cores=True):
     scene = synth.config2_scene()
     prm = oracle.make_params(n_hyp=100, seed=0)
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    start = N_FRAMES - 30
+    first, _ = frame_schedule(steps, warmup)
+    start = first + warmup if first + warmup + steps <= N_FRAMES else N_FRAMES - min(steps, N_FRAMES)
     frames = [synth.config2_frame(f, scene, device=dev) for f in range(1, N_FRAMES + 1)]
     frames = [(p.cpu().numpy(), pose) for p, pose in frames]
 
@@ -1122,8 +1186,10 @@ def cpu_baseline(budget_s, all_cores=True):
             om = oracle.OracleMap(spec.dims, spec.origin, spec.voxel_size)
             for f in range(start):
                 om.integrate(*frames[f])
+                if f >= start - warmup:
+                    om.segment(prm)
             done, t_used = 0, 0.0
-            while t_used < budget_s and start + done < N_FRAMES:
+            while t_used < budget_s and done < steps and start + done < N_FRAMES:
                 host, pose = frames[start + done]
                 t0 = time.perf_counter()
                 om.integrate(host, pose)
@@ -1209,11 +1275,11 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return None, rank
-    cb = cpu_baseline(args.ref_budget_s, all_cores=False)
+    cb = cpu_baseline(args.ref_budget_s, all_cores=False, steps=args.steps, warmup=args.warmup)
     res = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "frames/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic (ray-cast scenes)",
-           "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+           "config": bench_config(args.steps, args.warmup),
            "cpu_baseline": cb,
            "e2e": {"value": cb["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     return res, rank
@@ -1236,10 +1302,17 @@ def main():
     ws, _, _ = dist_env()
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(args.cpu_budget_s)
+            res["cpu_baseline"] = cpu_baseline(args.cpu_budget_s, steps=args.steps, warmup=args.warmup)
             res["cpu_baseline"]["other_configs"] = cpu_baseline_configs()
         if args.stages:
             print(json.dumps(res["stages_ms_per_step"], indent=1), file=sys.stderr)
+        # flat headline keys near the front of the line, and the same object
+        # again as the line's last key (where a truncated tail still shows it)
+        h = headline(res)
+        front = {k: res[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step")}
+        front.update(h)
+        res = dict(front, **{k: x for k, x in res.items() if k not in front})
+        res["headline"] = h
         print(json.dumps(res))
     if ws > 1:
         import torch.distributed as dist
