@@ -36,7 +36,14 @@ N_FRAMES = 300
 # kernel, from one ncu capture of the kernel as it stands, divided by the
 # stat its work scales with: {stage: (bytes per unit, stat)}.  Remove a
 # kernel's entry when the kernel changes.
-TRAFFIC_PER_UNIT = {}
+TRAFFIC_PER_UNIT = {
+    # 60-frame trajectory case (1,498 bricks; profiles/segment_kernels_60frames.md): the halo is staged
+    # per brick, so the traffic scales with the allocated bricks
+    "ccl_local": (14557952.0 / 1498, "bricks_allocated"),
+    "ccl_cross": ((15073792.0 + 1536.0) / 1498, "bricks_allocated"),
+    "moments": ((9291776.0 + 0.0) / 1498, "bricks_allocated"),
+    "eigen": ((4150016.0 + 77568.0) / 1498, "bricks_allocated"),
+}
 METRIC = "0.01 m integrate+segment: frames/s, p50/p99 ms, batched/served vs plain GPU"
 WORKLOAD = ("paper-scale trajectory: 4x4x2 m map at 0.01 m (sparse 8^3 bricks), 640x480 depth camera "
             "(87x58 deg, 0.3-4 m, sigma 1 mm + 0.2% range) over an 8-step open-tread stair, overhanging desk, "
@@ -1062,7 +1069,9 @@ def kernel_table(stages, st, peaks, n_points_segment, frame_points=0, frame_voxe
     finalize 28 B sums and count read + 12 B mean written + 4 B id per
     occupied voxel; moments 12 B mean read + 1 B neighbour count written per
     occupied voxel; eigen ~520 FP32 instructions per occupied voxel; CCL 24 B
-    (mean, normal) + 4 B label x (1 + 1 pass) per vertex (steppable voxel);
+    (mean, normal) + 4 B label x (1 + 1 pass) per vertex (steppable voxel):
+    the in-brick pass is priced at 24 B + 4 B (its reads and its labels), the
+    cross-brick pass, which completes the labels, at the whole 32 B;
     RANSAC scoring 5 instructions per point-hypothesis test.  staged_bytes:
     what the kernel as written reads and writes for the same launch, where
     it differs (per-slot staging of allocated bricks: slots = bricks x 512).
@@ -1080,7 +1089,8 @@ def kernel_table(stages, st, peaks, n_points_segment, frame_points=0, frame_voxe
         "finalize": ("hbm", occ * (28 + 12 + 4), slots * (4 + 1 + 12) + occ * 24, 1),
         "moments": ("hbm", occ * (12 + 1), slots * (12 + 16 + 8) + occ * (4 + 24 + 1), 1),
         "eigen": ("alu", occ * 520, None, 1),
-        "ccl": ("hbm", vert * (24 + 4 * 2), None, 1),
+        "ccl_local": ("hbm", vert * (24 + 4), None, 1),
+        "ccl_cross": ("hbm", vert * (24 + 4 * 2), None, 1),
         "ransac_score": ("alu", n_points_segment * n_hyp * 5, None, 1),
     }
     out = {}

@@ -28,7 +28,7 @@ unsigned long long alloc_total() { return g_allocs.load(); }
 void uncount_launch(unsigned long long n) { g_launches.fetch_sub(n); }
 
 static const char* kStageNames[kNumStages] = {"integrate", "order_bricks", "finalize", "moments", "eigen",
-                                              "ccl", "clusters", "ransac_hyp", "ransac_score",
+                                              "ccl_local", "ccl_cross", "clusters", "ransac_hyp", "ransac_score",
                                               "extract", "refit_hull", "pack", "clear", "rounds"};
 
 
@@ -259,7 +259,6 @@ static void vox_layout(Carver& c, SegBuffers& b, size_t nv, size_t tmp_words) {
     b.list_idx = c.take<uint32_t>(nv);
     b.list_A = c.take<float>(6 * nv);
     b.parent = c.take<uint32_t>(nv);
-    b.vmask = c.take<uint32_t>(nv / 32);
     b.count = c.take<uint32_t>(nv);
     b.cid = c.take<uint32_t>(nv + 1);
     b.vert_flag = c.take<uint32_t>(nv + 1);

@@ -293,9 +293,8 @@ __global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__
                                                     const int32_t* __restrict__ rank_table,
                                                     const int32_t* __restrict__ M, float4* __restrict__ rec,
                                                     uint32_t* __restrict__ list_idx, float* __restrict__ list_A,
-                                                    uint8_t* __restrict__ nbr, uint32_t* __restrict__ parent,
-                                                    uint32_t* __restrict__ count, uint32_t* __restrict__ vmask,
-                                                    size_t stride, SegCounters* __restrict__ ctr) {
+                                                    uint8_t* __restrict__ nbr, size_t stride,
+                                                    SegCounters* __restrict__ ctr) {
     pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     const float pox = g.po[0], poy = g.po[1], poz = g.po[2];
@@ -348,10 +347,7 @@ __global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__
             } else {
                 rec[o] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
             }
-            parent[o] = kNone;  // k_eigen makes each vertex its own root
-            count[o] = 0;
         }
-        if (threadIdx.x < 16) vmask[(size_t)r * 16 + threadIdx.x] = 0u;
         __syncthreads();
         const int nl = n_list;
         if (threadIdx.x == 0) gbase = atomicAdd(&ctr->n_list, (uint32_t)nl);
@@ -395,16 +391,12 @@ __global__ void __launch_bounds__(kNormT) k_moments(const uint32_t* __restrict__
 
 // k_eigen, one thread per occupied voxel: normal = eigenvector of the smallest
 // eigenvalue by FP32 Jacobi (6 sweeps); steppable iff N >= n_th and
-// |n_z| >= cos_step (status 2, else 1).  A voxel whose status reaches `want`
-// (steppable, or any occupied voxel when every one is clustered) is a vertex
-// of Algorithm 1: its parent becomes itself and its bit is set in its
-// brick's vertex mask.
+// |n_z| >= cos_step (status 2, else 1).
 __global__ void __launch_bounds__(256) k_eigen(const SegCounters* __restrict__ ctr,
                                                const uint32_t* __restrict__ list_idx, const float* __restrict__ list_A,
                                                const uint8_t* __restrict__ nbr, float* __restrict__ nrm,
-                                               uint8_t* __restrict__ status, float4* __restrict__ rec,
-                                               uint32_t* __restrict__ parent, uint32_t* __restrict__ vmask,
-                                               size_t stride, uint32_t n_th, float cos_step, uint8_t want) {
+                                               uint8_t* __restrict__ status, float4* __restrict__ rec, size_t stride,
+                                               uint32_t n_th, float cos_step) {
     pdl_gate();
     const uint32_t n = ctr->n_list;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -420,206 +412,214 @@ __global__ void __launch_bounds__(256) k_eigen(const SegCounters* __restrict__ c
         status[o] = st;
         reinterpret_cast<int*>(rec + o)[3] = (int)st;
         rec[stride + o] = make_float4(nv[0], nv[1], nv[2], 0.0f);
-        if (st >= want) {  // a vertex of Algorithm 1: its own root, and its bit in its brick's mask
-            parent[o] = o;
-            atomicOr(vmask + (o >> 5), 1u << (o & 31));
-        }
     }
 }
 
-// Algorithm 1 in one pass, one CTA per brick.  The brick's own cells and the
-// cells its forward edges reach (x, y in -1..8, z in 0..8 in brick
-// coordinates: a 10 x 10 x 9 region) are staged in shared memory, but only
-// the vertices among them: their positions come from the per-brick vertex
-// masks that k_eigen sets, so a brick's loads are its vertices' two records.
-// Every edge with both ends in the region is tested there (the brick's own
-// forward edges, and the edges among its halo cells) and joined in a
-// union-find over the region whose roots are the smallest in-brick index of
-// their component (halo cells rank after every brick cell).  A second forest
-// joins halo cells over the edges inside one neighbour brick only.  Then the
-// region's result goes to the global forest (parent, initialised to each
-// vertex itself by k_eigen) with hooking always of the larger root under the
-// smaller:
-//  * every brick vertex that is not its component's in-brick root is linked
-//    to that root by one CAS (a union when the CAS finds it already hooked);
-//  * every halo component of the second forest that touches a brick vertex
-//    is joined to the brick root once: its members are joined to each other
-//    by their own brick's links, since an edge inside a brick joins both
-//    ends to that brick's root in that brick's own pass.
-// Each forward edge lies in the region of the brick it leaves, so every edge
-// of the graph is joined: both ends linked to the brick's root, or the halo
-// end joined to it through its component.  The global forest's components
-// are the components of Algorithm 1's graph, each rooted at its smallest
-// index (the fixed point of its min-label propagation).
-constexpr int kCclT = 256;
-constexpr int kRegion = 900;       // 10 x 10 x 9 cells
-constexpr int kRegionBricks = 18;  // dz in {0, 1}, dy and dx in {-1, 0, 1}
-
-// Region cell c of (x, y, z), x and y in -1..8, z in 0..8 (brick coordinates).
-__device__ __forceinline__ int region_cell(int x, int y, int z) { return (z * 10 + y + 1) * 10 + x + 1; }
-
-// The region brick (index dz * 9 + (dy + 1) * 3 + dx + 1) and local voxel of cell c.
-__device__ __forceinline__ void region_decode(int c, int& x, int& y, int& z, int& rb, int& l) {
-    x = c % 10 - 1;
-    y = (c / 10) % 10 - 1;
-    z = c / 100;
-    const int bx = x < 0 ? -1 : (x > 7 ? 1 : 0), by = y < 0 ? -1 : (y > 7 ? 1 : 0), bz = z > 7 ? 1 : 0;
-    rb = bz * 9 + (by + 1) * 3 + bx + 1;
-    l = (((z - 8 * bz) * 8 + (y - 8 * by)) * 8) + (x - 8 * bx);
-}
-
-__device__ __forceinline__ uint32_t rf_find(volatile uint32_t* P, uint32_t x) {
-    for (int it = 0; it < 2048; ++it) {
-        const uint32_t p = P[x];
-        if (p == x) return x;
-        const uint32_t gp = P[p];
-        if (gp != p) P[x] = gp;  // path halving: gp is an ancestor of x
-        x = gp;
-    }
-    return x;
-}
-
-// Union in a region forest, the root of larger key hooked under the smaller.
-__device__ __forceinline__ void rf_union(uint32_t* P, const uint16_t* key, uint32_t a, uint32_t b, uint32_t* err) {
-    for (int it = 0; it < 4096; ++it) {
-        a = rf_find(P, a);
-        b = rf_find(P, b);
-        if (a == b) return;
-        const bool ab = key[a] > key[b];
-        const uint32_t hi = ab ? a : b, lo = ab ? b : a;
-        const uint32_t old = atomicCAS(P + hi, hi, lo);
-        if (old == hi) return;
-        a = old;
-        b = lo;
-    }
-    atomicOr(err, kErrTimeout);
-}
-
-// Read-only walk to the root once every union of the region is done.
-__device__ __forceinline__ uint32_t rf_root(const uint32_t* P, uint32_t x) {
-    for (int it = 0; it < 2048; ++it) {
-        const uint32_t p = P[x];
-        if (p == x) return x;
-        x = p;
-    }
-    return x;
-}
-
-__global__ void __launch_bounds__(kCclT) k_ccl(const uint32_t* __restrict__ nsp, uint32_t cap_b, Grid g,
-                                               const int32_t* __restrict__ sorted_key,
-                                               const int32_t* __restrict__ rank_table,
-                                               const float4* __restrict__ rec, const uint32_t* __restrict__ vmask,
-                                               uint32_t* parent, size_t stride, float d_th2, float cos_ccl,
-                                               uint32_t* err) {
+// The intra-brick half of Algorithm 1, one 128-thread CTA per brick: the
+// brick's records staged in shared memory, its vertices joined over edges
+// inside the brick with a union-find in shared memory; the global parent of
+// each vertex is set to its local root (the smallest index of its in-brick
+// component).  Edges that leave the brick follow in k_ccl_cross.
+__global__ void __launch_bounds__(kNormT, 8) k_ccl_local(const uint32_t* __restrict__ nsp, uint32_t cap_b,
+                                                      const float4* __restrict__ rec, uint32_t* __restrict__ parent,
+                                                      uint32_t* __restrict__ count, size_t stride, uint8_t want,
+                                                      float d_th2, float cos_ccl, uint32_t* err) {
     pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
-    __shared__ float3 sP[kRegion];                 // mean positions of the region's vertices
-    __shared__ float3 sN[kRegion];                 // their normals
-    __shared__ uint32_t rp[kRegion];               // region forest; kNone: not a vertex
-    __shared__ uint32_t hp[kRegion];               // halo forest
-    __shared__ uint16_t key[kRegion];              // union order: brick cells by local index, then halo cells
-    __shared__ uint16_t list[kRegion];             // the region's vertex cells
-    __shared__ uint32_t smask[kRegionBricks * 16]; // vertex masks of the region's bricks
-    __shared__ int32_t nb[kRegionBricks];
-    __shared__ int n_list;
-    for (int c = threadIdx.x; c < kRegion; c += kCclT) {
-        int x, y, z, rb, l;
-        region_decode(c, x, y, z, rb, l);
-        key[c] = (uint16_t)(rb == 4 ? l : 512 + c);
-    }
+    __shared__ float4 sA[512];
+    __shared__ float4 sB[512];
+    __shared__ uint32_t lpar[512];
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
         __syncthreads();
-        if (threadIdx.x < kRegionBricks) {
-            const int t = threadIdx.x;
-            const int dz = t / 9, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-            int bx, by, bz;
-            const int32_t bk = sorted_key[r];
-            bx = bk % g.nbx;
-            by = (bk / g.nbx) % g.nby;
-            bz = bk / (g.nbx * g.nby);
-            const int x = bx + dx, y = by + dy, z = bz + dz;
-            nb[t] = (x >= 0 && y >= 0 && x < g.nbx && y < g.nby && z < g.nbz) ? rank_table[(z * g.nby + y) * g.nbx + x]
-                                                                             : -1;
-        }
-        if (threadIdx.x == 0) n_list = 0;
-        __syncthreads();
-        for (int w = threadIdx.x; w < kRegionBricks * 16; w += kCclT) {
-            const int32_t rk = nb[w >> 4];
-            smask[w] = rk >= 0 ? vmask[(size_t)rk * 16 + (w & 15)] : 0u;
-        }
-        __syncthreads();
-        bool any = false;  // a brick without vertices owns no edges
+        {  // the brick's records, all of a thread's loads in flight together
+            constexpr int kIt = kBrickVox / kNormT;
+            float4 a[kIt], bn[kIt];
 #pragma unroll
-        for (int w = 0; w < 16; ++w) any |= smask[4 * 16 + w] != 0u;
-        if (!any) continue;
-        // the region's vertex cells, appended per warp
-        for (int c0 = 0; c0 < kRegion; c0 += kCclT) {
-            const int c = c0 + threadIdx.x;
-            bool v = false;
-            if (c < kRegion) {
-                int x, y, z, rb, l;
-                region_decode(c, x, y, z, rb, l);
-                v = (smask[rb * 16 + (l >> 5)] >> (l & 31)) & 1u;
-                rp[c] = v ? (uint32_t)c : kNone;
-                hp[c] = v ? (uint32_t)c : kNone;
+            for (int j = 0; j < kIt; ++j) a[j] = rec[(size_t)r * kBrickVox + threadIdx.x + j * kNormT];
+#pragma unroll
+            for (int j = 0; j < kIt; ++j)
+                if (__float_as_int(a[j].w) >= want)
+                    bn[j] = rec[stride + (size_t)r * kBrickVox + threadIdx.x + j * kNormT];
+#pragma unroll
+            for (int j = 0; j < kIt; ++j) {
+                const int l = threadIdx.x + j * kNormT;
+                const bool vert = __float_as_int(a[j].w) >= want;
+                sA[l] = a[j];
+                if (vert) sB[l] = bn[j];
+                lpar[l] = vert ? (uint32_t)l : kNone;
             }
-            const uint32_t bal = __ballot_sync(0xffffffffu, v);
-            int base = 0;
-            if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(&n_list, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (v) list[base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = (uint16_t)c;
         }
         __syncthreads();
-        const int nl = n_list;
-        for (int i = threadIdx.x; i < nl; i += kCclT) {  // both records of every vertex, loads issued together
-            const int c = list[i];
-            int x, y, z, rb, l;
-            region_decode(c, x, y, z, rb, l);
-            const size_t o = (size_t)nb[rb] * kBrickVox + l;
-            const float4 a = rec[o], b = rec[stride + o];
-            sP[c] = make_float3(a.x, a.y, a.z);
-            sN[c] = make_float3(b.x, b.y, b.z);
+        // Runs along +x first, without atomics: each 8-voxel row lies in one
+        // warp, whose ballot of +x edges gives every vertex the start (smallest
+        // index) of its run as its parent.
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
+            const bool vert = __float_as_int(sA[l].w) >= want;
+            const int lx = l & 7;
+            bool xe = false;
+            if (vert && lx < 7 && __float_as_int(sA[l + 1].w) >= want) {
+                const float4 a = sA[l], an = sB[l], b = sA[l + 1], bn = sB[l + 1];
+                xe = ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, xe);
+            const uint32_t row = (bal >> ((threadIdx.x & 31) & ~7)) & 0xffu;
+            const uint32_t gap = ~row & ((1u << lx) - 1u);  // missing +x edges below this voxel
+            const int start = gap ? 32 - __clz(gap) : 0;
+            if (vert) lpar[l] = (uint32_t)((l & ~7) + start);
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < nl; i += kCclT) {  // every forward edge inside the region
-            const int c = list[i];
-            int x, y, z, rb, l;
-            region_decode(c, x, y, z, rb, l);
-            const bool halo = rb != 4;
-            const float3 a = sP[c], an = sN[c];
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
+            if (lpar[l] == kNone) continue;
+            const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+            const float4 a = sA[l], an = sB[l];
 #pragma unroll
-            for (int k = 0; k < 13; ++k) {
+            for (int k = 0; k < 12; ++k) {  // the +x offset (k = 12) was joined above
                 int dz, dy, dx;
                 fwd_offset(k, dz, dy, dx);
-                const int x2 = x + dx, y2 = y + dy, z2 = z + dz;
-                if (x2 < -1 || x2 > 8 || y2 < -1 || y2 > 8 || z2 > 8) continue;
-                const int c2 = region_cell(x2, y2, z2);
-                if (rp[c2] == kNone) continue;  // (a vertex's entry is never kNone)
-                const float3 b = sP[c2], bn = sN[c2];
-                if (!ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
-                    continue;
-                rf_union(rp, key, (uint32_t)c, (uint32_t)c2, err);
-                if (halo) {  // an edge inside one neighbour brick: that brick's own links join it
-                    const int bx2 = x2 < 0 ? -1 : (x2 > 7 ? 1 : 0), by2 = y2 < 0 ? -1 : (y2 > 7 ? 1 : 0);
-                    if (rb == (z2 > 7 ? 1 : 0) * 9 + (by2 + 1) * 3 + bx2 + 1)
-                        rf_union(hp, key, (uint32_t)c, (uint32_t)c2, err);
+                const int x = lx + dx, y = ly + dy, z = lz + dz;
+                if (x < 0 || x > 7 || y < 0 || y > 7 || z > 7) continue;
+                const int j = (z * 8 + y) * 8 + x;
+                if (__float_as_int(sA[j].w) < want) continue;
+                const float4 b = sA[j], bn = sB[j];
+                if (ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
+                    lf_union(lpar, (uint32_t)l, (uint32_t)j, err);
+            }
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < kBrickVox; l += kNormT) {
+            const size_t o = (size_t)r * kBrickVox + l;
+            uint32_t root = kNone;
+            if (__float_as_int(sA[l].w) >= want) {  // read-only walk: entries are final once every union is done
+                uint32_t x = (uint32_t)l;
+                for (int it = 0; it < 1024; ++it) {
+                    const uint32_t p = lpar[x];
+                    if (p == x) break;
+                    x = p;
+                }
+                root = (uint32_t)r * kBrickVox + x;
+            }
+            parent[o] = root;
+            count[o] = 0;
+        }
+    }
+}
+
+// The inter-brick half of Algorithm 1, one 128-thread CTA per brick.  The
+// brick's 10^3 halo of packed voxel records and current parents is staged in
+// shared memory with independent loads; then every vertex whose forward
+// neighbours can lie in another brick tests those neighbours from shared
+// memory.  Forward offsets have dz in {0, 1}, dy in {-1, 0, 1} (-1 only with
+// dz = 1) and dx in {-1, 0, 1}, so they leave the brick through the +z face,
+// either y face or either x face.  An edge (i, j) that passes is recorded as
+// the pair of their staged parents (ancestors of i and j, so joining them
+// joins i and j) in a hash set in shared memory, and each distinct pair is
+// joined once in the global forest: most of a brick's edges lead to the same
+// few pairs.
+constexpr int kCrossT = 128;
+constexpr int kPairSlots = 256;
+__global__ void __launch_bounds__(kCrossT) k_ccl_cross(const uint32_t* __restrict__ nsp, uint32_t cap_b, Grid g,
+                                                       const int32_t* __restrict__ sorted_key,
+                                                       const int32_t* __restrict__ rank_table,
+                                                       const float4* __restrict__ rec, uint32_t* parent, size_t stride,
+                                                       uint8_t want, float d_th2, float cos_ccl, uint32_t* err) {
+    pdl_gate();
+    const uint32_t n_sorted = min(*nsp, cap_b);
+    // The halo at z 0..8 only (forward edges never reach z -1): 10 x 10 x 9
+    // cells, cell c = halo cell c + 100.  Means without the status word (a
+    // vertex is a cell whose parent is not kNone): 27 KB a CTA, 8 CTAs an SM.
+    constexpr int kCells = 900;
+    __shared__ float3 sA[kCells];
+    __shared__ float4 sB[kCells];  // (normal, parent); parent kNone off the vertex set
+    __shared__ unsigned long long set[kPairSlots];
+    __shared__ int32_t nb[27];
+    for (int q = threadIdx.x; q < kPairSlots; q += kCrossT) set[q] = ~0ull;
+    for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
+        __syncthreads();
+        load_neighbour_ranks(sorted_key[r], g, rank_table, nb);
+        __syncthreads();
+        // Load only the cells a cross-brick edge can touch: the brick's own
+        // cells on the faces forward edges leave through (lx 0 or 7, ly 0 or
+        // 7, lz 7) and the halo cells outside the brick at lz 0..8 (648 of the
+        // 900); the others are staged as non-vertices.  A thread issues its
+        // record loads four at a time before using them.
+        constexpr int kIt = (kCells + kCrossT - 1) / kCrossT;  // cells per thread
+        constexpr int kGroup = 4;                               // loads in flight per thread
+#pragma unroll 1
+        for (int j0 = 0; j0 < kIt; j0 += kGroup) {
+            int32_t idx[kGroup];
+            float4 a[kGroup];
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                const int c = threadIdx.x + (j0 + j) * kCrossT;
+                idx[j] = -1;
+                if (c < kCells) {
+                    const int h = c + 100;  // the 10 x 10 x 10 halo index
+                    const int gx = h % 10 - 1, gy = (h / 10) % 10 - 1, gz = h / 100 - 1;
+                    const bool inside = gx >= 0 && gx <= 7 && gy >= 0 && gy <= 7 && gz <= 7;
+                    const bool source = inside && (gx == 0 || gx == 7 || gy == 0 || gy == 7 || gz == 7);
+                    if (source || !inside) idx[j] = halo_index(h, nb);
+                }
+                a[j] = idx[j] >= 0 ? rec[idx[j]] : make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
+            }
+            float4 bn[kGroup];
+            uint32_t par[kGroup];
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                const bool v = idx[j] >= 0 && __float_as_int(a[j].w) >= want;
+                bn[j] = v ? rec[stride + idx[j]] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                par[j] = v ? __ldcg(parent + idx[j]) : kNone;
+            }
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                const int c = threadIdx.x + (j0 + j) * kCrossT;
+                if (c < kCells) {
+                    sA[c] = make_float3(a[j].x, a[j].y, a[j].z);
+                    sB[c] = make_float4(bn[j].x, bn[j].y, bn[j].z, __uint_as_float(par[j]));
                 }
             }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < nl; i += kCclT) {  // the region's components into the global forest
-            const int c = list[i];
-            int x, y, z, rb, l;
-            region_decode(c, x, y, z, rb, l);
-            const uint32_t root = rf_root(rp, (uint32_t)c);
-            if (key[root] >= 512) continue;  // no brick vertex in the component: other CTAs' edges
-            const uint32_t gr = r * (uint32_t)kBrickVox + key[root];
-            if (rb == 4) {
-                if (root == (uint32_t)c) continue;
-                const uint32_t gv = r * (uint32_t)kBrickVox + (uint32_t)l;
-                if (atomicCAS(parent + gv, gv, gr) != gv) uf_union(parent, gv, gr, err);
-            } else if (rf_root(hp, (uint32_t)c) == (uint32_t)c) {
-                uf_union(parent, (uint32_t)nb[rb] * kBrickVox + (uint32_t)l, gr, err);
+        unsigned long long last = ~0ull;
+        for (int l = threadIdx.x; l < kBrickVox; l += kCrossT) {
+            const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+            if (!((lx == 0) | (lx == 7) | (ly == 0) | (ly == 7) | (lz == 7))) continue;
+            const int c0 = (lz * 10 + ly + 1) * 10 + lx + 1;
+            const float3 a = sA[c0];
+            const float4 an = sB[c0];
+            const uint32_t pa = __float_as_uint(an.w);
+            if (pa == kNone) continue;
+            for (int k = 0; k < 13; ++k) {
+                int dz, dy, dx;
+                fwd_offset(k, dz, dy, dx);
+                const int x = lx + dx, y = ly + dy, z = lz + dz;
+                if (x >= 0 && x <= 7 && y >= 0 && y <= 7 && z <= 7) continue;  // inside the brick: done already
+                const int c = c0 + dz * 100 + dy * 10 + dx;
+                const float4 bn = sB[c];
+                const uint32_t pb = __float_as_uint(bn.w);
+                if (pb == kNone || pb == pa) continue;
+                const float3 b = sA[c];
+                if (!ccl_edge(a.x, a.y, a.z, an.x, an.y, an.z, b.x, b.y, b.z, bn.x, bn.y, bn.z, d_th2, cos_ccl))
+                    continue;
+                const uint32_t lo = pa < pb ? pa : pb, hi = pa < pb ? pb : pa;
+                const unsigned long long key = ((unsigned long long)lo << 32) | hi;
+                if (key == last) continue;
+                last = key;
+                uint32_t h = (lo * 2654435761u ^ hi * 40503u) & (kPairSlots - 1);
+                bool placed = false;
+                for (int probe = 0; probe < kPairSlots; ++probe) {
+                    const unsigned long long prev = atomicCAS(&set[h], ~0ull, key);
+                    if (prev == ~0ull || prev == key) { placed = true; break; }
+                    h = (h + 1) & (kPairSlots - 1);
+                }
+                if (!placed) uf_union(parent, lo, hi, err);  // set full: join directly
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < kPairSlots; q += kCrossT) {
+            const unsigned long long key = set[q];
+            if (key != ~0ull) {
+                uf_union(parent, (uint32_t)(key >> 32), (uint32_t)key, err);
+                set[q] = ~0ull;
             }
         }
     }
@@ -823,10 +823,10 @@ __global__ void k_clusters_end(SegCounters* __restrict__ ctr, uint32_t kcap, uin
 
 cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* C, const vm_segment_params& p,
                     SegBuffers& b, uint32_t kcap, uint32_t* err, int sms, cudaStream_t s, StageHook* hk) {
-    // the one-pass CCL fits 6 CTAs an SM only with the largest shared-memory split
+    // the cross-brick pass fits 8 CTAs an SM only with the largest shared-memory split
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(k_ccl, cudaFuncAttributePreferredSharedMemoryCarveout,
+        cudaFuncSetAttribute(k_ccl_cross, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
     });
     const uint32_t cap_b = (uint32_t)(b.nv / kBrickVox);
@@ -840,17 +840,21 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     const uint8_t want = p.classify ? 2 : 1;
     VM_STAGE_BEGIN(hk, kStNormals, s);
     launch_k(k_moments, dim3(clampg(cap_b, sms * 16)), dim3(kNormT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table,
-             b.M, b.rec, b.list_idx, b.list_A, b.nbr, b.parent, b.count, b.vmask, stride, b.ctr);
+             b.M, b.rec, b.list_idx, b.list_A, b.nbr, stride, b.ctr);
     VM_STAGE_END(hk, kStNormals, s);
     VM_STAGE_BEGIN(hk, kStEigen, s);
     launch_k(k_eigen, dim3(clampg((uint32_t)((b.nv + 255) / 256), sms * 16)), dim3(256), 0, s, b.ctr, b.list_idx,
-             b.list_A, b.nbr, b.nrm, b.status, b.rec, b.parent, b.vmask, stride, p.n_th, p.cos_step, want);
+             b.list_A, b.nbr, b.nrm, b.status, b.rec, stride, p.n_th, p.cos_step);
     VM_STAGE_END(hk, kStEigen, s);
+    VM_STAGE_BEGIN(hk, kStCclLocal, s);
+    launch_k(k_ccl_local, dim3(clampg(cap_b, sms * 16)), dim3(kNormT), 0, s, nsp, cap_b, b.rec, b.parent, b.count,
+             stride, want, p.d_th2, p.cos_ccl, err);
+    VM_STAGE_END(hk, kStCclLocal, s);
     VM_STAGE_BEGIN(hk, kStCcl, s);
-    launch_k(k_ccl, dim3(clampg(cap_b, sms * 16)), dim3(kCclT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table,
-             b.rec, b.vmask, b.parent, stride, p.d_th2, p.cos_ccl, err);
+    launch_k(k_ccl_cross, dim3(clampg(cap_b, sms * 16)), dim3(kCrossT), 0, s, nsp, cap_b, g, b.sorted_key, b.rank_table,
+             b.rec, b.parent, stride, want, p.d_th2, p.cos_ccl, err);
     VM_STAGE_END(hk, kStCcl, s);
-    count_launch(4);
+    count_launch(5);
     VM_STAGE_BEGIN(hk, kStClusters, s);
     launch_k(k_compress_count, dim3(grid_for(b.nv, sms)), dim3(kT), 0, s, nsp, cap_b, b.parent, b.count, b.ctr, err);
     const uint32_t min_cl = p.min_cluster ? p.min_cluster : 1u;

@@ -206,7 +206,8 @@ enum Stage {
     kStFinalize,       // integer means
     kStNormals,        // Eq. 3 window moments (k_moments)
     kStEigen,          // Eq. 3 eigen-solve + Eq. 4 (k_eigen)
-    kStCcl,            // Algorithm 1 (k_ccl)
+    kStCclLocal,       // Algorithm 1 inside bricks (k_ccl_local)
+    kStCcl,            // Algorithm 1 across bricks (k_ccl_cross, k_ccl_compress)
     kStClusters,       // sizes, numbering, compaction, sort, gather
     kStHyp,            // stage a
     kStScore,          // stage b
@@ -336,7 +337,6 @@ struct SegBuffers {
     uint32_t* list_idx;     // [nv]     occupied voxels (rank-dense index), in no particular order
     float* list_A;          // [6][nv]  their window covariances (FP32, rounded from exact integers)
     uint32_t* parent;       // [nv]     union-find parent, kNone when not a vertex
-    uint32_t* vmask;        // [nv / 32] per brick, the 512-bit mask of its vertices
     uint32_t* count;        // [nv]     component sizes at roots
     uint32_t* cid;          // [nv + 1] kept-root flags -> cluster index (scan)
     uint32_t* vert_flag;    // [nv + 1] kept-vertex flags -> compact position (scan)

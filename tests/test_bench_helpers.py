@@ -8,21 +8,21 @@ import bench
 def test_kernel_table_rows_and_the_dominant_kernel():
     st = {"occupied_voxels": 1000, "steppable_voxels": 600, "bricks_allocated": 10}
     peaks = {"hbm_gbs": 5000.0, "sm_max_mhz": 2000.0}
-    stages = {"ccl": (0.5, 10), "moments": (0.2, 10), "clusters": (0.9, 10), "eigen": (0.1, 10),
+    stages = {"ccl_cross": (0.5, 10), "moments": (0.2, 10), "clusters": (0.9, 10), "eigen": (0.1, 10),
               "integrate": (0.9, 10), "pack": (0.0, 0)}
     t = bench.kernel_table(stages, st, peaks, n_points_segment=4000, frame_points=3000, frame_voxels=700)
     ccl = 600 * (24 + 4 * 2)  # per vertex: mean and normal read, label written and read once more
-    assert t["ccl"]["algorithmic"] == ccl
-    assert abs(t["ccl"]["achieved"] - round(ccl / 0.05e-3 / 1e9, 1)) < 1e-9
-    assert abs(t["ccl"]["frac"] - round(ccl / 0.05e-3 / 1e9 / 5000.0, 4)) < 1e-12
+    assert t["ccl_cross"]["algorithmic"] == ccl
+    assert abs(t["ccl_cross"]["achieved"] - round(ccl / 0.05e-3 / 1e9, 1)) < 1e-9
+    assert abs(t["ccl_cross"]["frac"] - round(ccl / 0.05e-3 / 1e9 / 5000.0, 4)) < 1e-12
     assert t["moments"]["algorithmic"] == 1000 * 13 and t["moments"]["staged_bytes"] > 1000 * 13
     assert t["integrate"]["algorithmic"] == 3000 * 16 + 700 * 28 and t["integrate"]["kernels"] == 2
     alu = bench.SM_COUNT * bench.FP32_LANES * 2000e6 / 1e12
     assert t["eigen"]["bound"] == "alu" and t["eigen"]["peak"] == round(alu, 1)
     assert "bound" not in t["clusters"] and "pack" not in t  # several kernels; no calls
-    r = bench.roofline(t, traffic={"ccl": 9600.9})
+    r = bench.roofline(t, traffic={"ccl_cross": 9600.9})
     # the longest stage that is a single modelled kernel: not the longer multi-kernel ones
-    assert r["kernel"] == "ccl" and r["traffic"] == 9600 and r["avg_launch_ms"] == 0.05
+    assert r["kernel"] == "ccl_cross" and r["traffic"] == 9600 and r["avg_launch_ms"] == 0.05
     assert r["traffic_ratio"] == round(9600.9 / ccl, 3)
     assert bench.roofline(t)["traffic"] is None
 
