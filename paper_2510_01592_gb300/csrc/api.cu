@@ -91,6 +91,7 @@ static void fit_layout(Carver& c, FitBuffers& fb, size_t kcap, size_t npts, size
     fb.err = c.take<uint32_t>(4);
     fb.tot = c.take<uint32_t>(4);
     fb.kdev = c.take<uint32_t>(4);
+    fb.done = c.take<uint32_t>(kcap * 3);
 }
 
 size_t fit_bytes(size_t kcap, size_t npts, size_t chunks, int H) {

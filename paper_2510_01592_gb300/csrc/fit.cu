@@ -124,18 +124,122 @@ __global__ void k_hyp(const float* __restrict__ pts, const uint32_t* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- stage c
+// The record of cluster c from its best (count << 32 | ~h) key (0: no valid
+// hypothesis): the selected plane, the in-plane basis and the hull origin.
+__device__ __forceinline__ void select_record(uint32_t c, unsigned long long best, const float* __restrict__ pts,
+                                              const uint32_t* __restrict__ off, int H,
+                                              const float4* __restrict__ hyp, FitCluster* __restrict__ cl) {
+    FitCluster f;
+    memset(&f, 0, sizeof(f));
+    const uint32_t n = off[c + 1] - off[c];
+    if (best != 0) {
+        const int h = (int)(~(uint32_t)(best & 0xffffffffu));
+        const float4 pl = hyp[(size_t)c * H + h];
+        f.best_h = h;
+        f.n[0] = pl.x; f.n[1] = pl.y; f.n[2] = pl.z; f.d = pl.w;
+        f.inliers = (uint32_t)(best >> 32);
+        const float nx = pl.x, ny = pl.y, nz = pl.z;
+        float ux, uy, uz;
+        if (fabsf(nx) < 0.9f) { ux = 0.0f; uy = -nz; uz = ny; }  // e_x cross n
+        else { ux = nz; uy = 0.0f; uz = -nx; }                   // e_y cross n
+        const float ul = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
+        const float ui = __fdiv_rn(1.0f, __fsqrt_rn(ul));
+        ux = __fmul_rn(ux, ui); uy = __fmul_rn(uy, ui); uz = __fmul_rn(uz, ui);
+        f.u[0] = ux; f.u[1] = uy; f.u[2] = uz;
+        f.v[0] = __fmaf_rn(ny, uz, -__fmul_rn(nz, uy));
+        f.v[1] = __fmaf_rn(nz, ux, -__fmul_rn(nx, uz));
+        f.v[2] = __fmaf_rn(nx, uy, -__fmul_rn(ny, ux));
+    } else {
+        f.best_h = -1;
+    }
+    if (n) {
+        const float* p = pts + 3 * (size_t)off[c];
+        f.o[0] = p[0]; f.o[1] = p[1]; f.o[2] = p[2];
+    }
+    cl[c] = f;
+}
+
+// This thread's best (count << 32 | ~h) key over hypotheses h = i, i + step,
+// ... of cluster c (counts read from L2: other CTAs added them).
+__device__ __forceinline__ unsigned long long best_key(uint32_t c, int i, int step, int H,
+                                                       const uint8_t* __restrict__ valid,
+                                                       const uint32_t* __restrict__ counts) {
+    unsigned long long best = 0;  // 0 = none
+    for (int h = i; h < H; h += step) {
+        const size_t t = (size_t)c * H + h;
+        if (valid[t]) {
+            const unsigned long long key = ((unsigned long long)__ldcg(counts + t) << 32) | (uint32_t)(~(uint32_t)h);
+            best = key > best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, s);
+        best = o > best ? o : best;
+    }
+    return best;
+}
+
+// Stage c for cluster c by a whole CTA of kT threads (wbest: kT / 32 words
+// of shared memory): maximum count, lowest hypothesis index on ties.
+__device__ __forceinline__ void select_cta(uint32_t c, const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                                           int H, const float4* __restrict__ hyp, const uint8_t* __restrict__ valid,
+                                           const uint32_t* __restrict__ counts, FitCluster* __restrict__ cl,
+                                           unsigned long long* wbest) {
+    unsigned long long best = best_key(c, threadIdx.x, kT, H, valid, counts);
+    if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kT / 32; ++w) best = wbest[w] > best ? wbest[w] : best;
+        select_record(c, best, pts, off, H, hyp, cl);
+    }
+    __syncthreads();
+}
+
+__global__ void k_select(const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                         const uint32_t* __restrict__ kp, int H, const float4* __restrict__ hyp,
+                         const uint8_t* __restrict__ valid, const uint32_t* __restrict__ counts,
+                         FitCluster* __restrict__ cl) {
+    pdl_gate();
+    const uint32_t k = *kp;
+    __shared__ unsigned long long wbest[kT / 32];
+    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) select_cta(c, pts, off, H, hyp, valid, counts, cl, wbest);
+}
+
+// Per-cluster completion: every work item of a cluster, after its results
+// are visible device-wide, counts itself done; the CTA (or warp) that
+// completes the cluster's last item runs the cluster's next serial step
+// (stage c after scoring, the centroid after extraction, the refit after the
+// filter) in place of a kernel of its own.  done: three counters a cluster,
+// cleared before the fit.
+__device__ __forceinline__ bool cta_last_item(uint32_t* done, uint32_t n_items, uint32_t* flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = atomicAdd(done, 1u) + 1u == n_items;
+    __syncthreads();
+    const bool last = *flag != 0u;
+    if (last) __threadfence();
+    return last;
+}
+
 // ---------------------------------------------------------------- stage b
+// done (may be null): per-cluster completion counters; the CTA that scores a
+// cluster's last item then runs stage c for it.
 template <int R>
 __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                               const uint32_t* __restrict__ item_off,
                                               const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
                                               int H, int T, const float4* __restrict__ hyp,
-                                              uint32_t* __restrict__ counts, uint32_t* __restrict__ queue, float eps) {
+                                              uint32_t* __restrict__ counts, uint32_t* __restrict__ queue, float eps,
+                                              const uint8_t* __restrict__ valid, FitCluster* __restrict__ cl,
+                                              uint32_t* __restrict__ done) {
     pdl_wait();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];                // T staged points
     uint32_t* red = reinterpret_cast<uint32_t*>(sp + T);  // [P][G*R]
-    __shared__ uint32_t s_item;
+    __shared__ uint32_t s_item, s_last;
+    __shared__ unsigned long long wbest[kT / 32];
     const int G = (H + R - 1) / R;                // threads per point subset
     const int P = kT / G;                         // point subsets
     const int g = threadIdx.x / G, j = threadIdx.x % G;
@@ -182,65 +286,8 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
             for (int q = 0; q < P; ++q) s += red[q * (G * R) + h];
             if (s) atomicAdd(&counts[(size_t)c * H + h], s);
         }
-    }
-}
-
-// ---------------------------------------------------------------- stage c
-__global__ void k_select(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                         const uint32_t* __restrict__ kp, int H, const float4* __restrict__ hyp,
-                         const uint8_t* __restrict__ valid, const uint32_t* __restrict__ counts,
-                         FitCluster* __restrict__ cl) {
-    pdl_gate();
-    const uint32_t k = *kp;
-    __shared__ unsigned long long wbest[kT / 32];
-    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
-        unsigned long long best = 0;  // (count << 32) | ~h ; 0 = none
-        for (int h = threadIdx.x; h < H; h += kT) {
-            const size_t t = (size_t)c * H + h;
-            if (valid[t]) {
-                const unsigned long long key = ((unsigned long long)counts[t] << 32) | (uint32_t)(~(uint32_t)h);
-                best = key > best ? key : best;
-            }
-        }
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, s);
-            best = o > best ? o : best;
-        }
-        if ((threadIdx.x & 31) == 0) wbest[threadIdx.x >> 5] = best;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int w = 1; w < kT / 32; ++w) best = wbest[w] > best ? wbest[w] : best;
-            FitCluster f;
-            memset(&f, 0, sizeof(f));
-            const uint32_t n = off[c + 1] - off[c];
-            if (best != 0) {
-                const int h = (int)(~(uint32_t)(best & 0xffffffffu));
-                const float4 pl = hyp[(size_t)c * H + h];
-                f.best_h = h;
-                f.n[0] = pl.x; f.n[1] = pl.y; f.n[2] = pl.z; f.d = pl.w;
-                f.inliers = (uint32_t)(best >> 32);
-                const float nx = pl.x, ny = pl.y, nz = pl.z;
-                float ux, uy, uz;
-                if (fabsf(nx) < 0.9f) { ux = 0.0f; uy = -nz; uz = ny; }  // e_x cross n
-                else { ux = nz; uy = 0.0f; uz = -nx; }                   // e_y cross n
-                const float ul = __fmaf_rn(uz, uz, __fmaf_rn(uy, uy, __fmul_rn(ux, ux)));
-                const float ui = __fdiv_rn(1.0f, __fsqrt_rn(ul));
-                ux = __fmul_rn(ux, ui); uy = __fmul_rn(uy, ui); uz = __fmul_rn(uz, ui);
-                f.u[0] = ux; f.u[1] = uy; f.u[2] = uz;
-                f.v[0] = __fmaf_rn(ny, uz, -__fmul_rn(nz, uy));
-                f.v[1] = __fmaf_rn(nz, ux, -__fmul_rn(nx, uz));
-                f.v[2] = __fmaf_rn(nx, uy, -__fmul_rn(ny, ux));
-            } else {
-                f.best_h = -1;
-            }
-            if (n) {
-                const float* p = pts + 3 * (size_t)off[c];
-                f.o[0] = p[0]; f.o[1] = p[1]; f.o[2] = p[2];
-            }
-            cl[c] = f;
-        }
-        __syncthreads();
+        if (done && cta_last_item(done + 3 * (size_t)c, item_off[c + 1] - item_off[c], &s_last))
+            select_cta(c, pts, off, H, hyp, valid, counts, cl, wbest);
     }
 }
 
@@ -325,70 +372,6 @@ __device__ __forceinline__ void chunks_out(const float* wp, uint32_t n_chunks, f
     __syncthreads();
 }
 
-// Inliers, centroid partials (relative to the origin) and the extreme inliers
-// along the 16 filter directions (reduced per warp, then atomicMax).
-__global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
-                                                const uint32_t* __restrict__ item_off,
-                                                const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
-                                                int T, FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
-                                                float* __restrict__ part, float eps, uint32_t* __restrict__ err) {
-    pdl_gate();
-    const uint32_t k = *kp;
-    __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 4];
-    const uint32_t n_items = item_off[k];
-    const uint32_t cpt = (uint32_t)T / kChunk;  // chunks per work item
-    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const uint32_t c = find_cluster(item_cl, item_off, k, it);
-        const FitCluster f = cl[c];
-        const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
-        const uint32_t end = min(off[c + 1], start + (uint32_t)T);
-        unsigned long long ext[kFiltDirs];
-#pragma unroll
-        for (int d = 0; d < kFiltDirs; ++d) ext[d] = 0;
-        bool big = false;
-        // chunk within the item; its slot is it * cpt + j (item_off[c] * cpt + its chunk in the cluster)
-        uint32_t j = 0;
-#pragma unroll 4
-        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {  // unrolled: later chunks' loads go out early
-            const uint32_t q = q0 + threadIdx.x;
-            float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // count, sum (p - o)
-            if (q < end) {
-                const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
-                const bool in = f.best_h >= 0 && plane_dist(f.n[0], f.n[1], f.n[2], f.d, px, py, pz) <= eps;
-                inlier[q] = in;
-                if (in) {
-                    v[0] = 1.0f;
-                    v[1] = __fsub_rn(px, f.o[0]);
-                    v[2] = __fsub_rn(py, f.o[1]);
-                    v[3] = __fsub_rn(pz, f.o[2]);
-                    const int2 xy = quantise(f, px, py, pz);
-                    big |= (abs(xy.x) >= (1 << 28)) | (abs(xy.y) >= (1 << 28));
-                    const uint32_t idx = q - off[c];
-#pragma unroll
-                    for (int d = 0; d < kFiltDirs; ++d) {
-                        const unsigned long long key = ext_key(dir_value(d, xy), idx);
-                        ext[d] = key > ext[d] ? key : ext[d];
-                    }
-                }
-            }
-            warp_park<4>(v, wp, j);
-        }
-        chunks_out<4>(wp, j, part + (size_t)it * cpt * 10, 0);  // slot 0 holds the count (at most 256: exact)
-        if (big) atomicOr(err, kErrOverflow);
-#pragma unroll
-        for (int d = 0; d < kFiltDirs; ++d) {
-            unsigned long long m = ext[d];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
-                m = t > m ? t : m;
-            }
-            if ((threadIdx.x & 31) == 0 && m) atomicMax(&cl[c].ext[d], m);
-        }
-        __syncthreads();
-    }
-}
-
 // Double-float arithmetic: a value is hi + lo with |lo| at most half an ulp of
 // hi, about 46 significant bits, on the FP32 pipes (FP64 is a slow path on
 // this part).  Built from the error-free transformations TwoSum (Knuth) and
@@ -456,57 +439,124 @@ __device__ __forceinline__ void block_df_sum(df2 (&v)[NV], df2* sh) {
         }
 }
 
-// Per cluster (one CTA each): inlier count and centroid, the per-chunk
-// partial sums added in double-float in a fixed order (thread-strided, then
-// block_df_sum), so the result does not depend on scheduling.  The centroid
-// is kept as (hi, lo) per axis.
-__global__ void __launch_bounds__(kT) k_centroid(const uint32_t* __restrict__ off,
-                                                 const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp,
-                                                 int T, const float* __restrict__ part, FitCluster* __restrict__ cl,
-                                                 float* __restrict__ cen /* [k][3][2] */) {
+// Inlier count and centroid of cluster c by a whole CTA: the per-chunk
+// partial sums (read from L2: other CTAs wrote them) added in double-float in
+// a fixed order (thread-strided, then block_df_sum), so the result does not
+// depend on scheduling.  The centroid is kept as (hi, lo) per axis.
+__device__ __forceinline__ void centroid_cta(uint32_t c, const uint32_t* __restrict__ off,
+                                             const uint32_t* __restrict__ item_off, int T,
+                                             const float* __restrict__ part, FitCluster* __restrict__ cl,
+                                             float* __restrict__ cen, df2* sh, uint32_t* shn) {
+    const uint32_t cpt = (uint32_t)T / kChunk;
+    df2 v[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    uint32_t n = 0;
+    const uint32_t base = item_off[c] * cpt, nch = (off[c + 1] - off[c] + kChunk - 1) / kChunk;
+#pragma unroll 2
+    for (uint32_t j = threadIdx.x; j < nch; j += kT) {
+        const float* pp = part + (size_t)(base + j) * 10;
+        n += (uint32_t)__ldcg(pp);
+        v[0] = df_add(v[0], df2{__ldcg(pp + 1), 0.0f});
+        v[1] = df_add(v[1], df2{__ldcg(pp + 2), 0.0f});
+        v[2] = df_add(v[2], df2{__ldcg(pp + 3), 0.0f});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if ((threadIdx.x & 31) == 0) shn[threadIdx.x >> 5] = n;
+    block_df_sum<3>(v, sh);
+    if (threadIdx.x == 0) {
+        n = 0;
+        for (int q = 0; q < kT / 32; ++q) n += shn[q];
+        FitCluster& f = cl[c];
+        f.inliers = n;
+        df2 cx{f.o[0], 0.0f}, cy{f.o[1], 0.0f}, cz{f.o[2], 0.0f};
+        if (n) {
+            cx = df_add(cx, df_div_count(v[0], n));
+            cy = df_add(cy, df_div_count(v[1], n));
+            cz = df_add(cz, df_div_count(v[2], n));
+        }
+        float* ce = cen + 6 * (size_t)c;
+        ce[0] = cx.hi; ce[1] = cx.lo; ce[2] = cy.hi; ce[3] = cy.lo; ce[4] = cz.hi; ce[5] = cz.lo;
+        f.c[0] = cx.hi; f.c[1] = cy.hi; f.c[2] = cz.hi;
+    }
+    __syncthreads();  // shared partials reused next
+}
+
+// Inliers, centroid partials (relative to the origin) and the extreme inliers
+// along the 16 filter directions (reduced per warp, then atomicMax).
+__global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
+                                                const uint32_t* __restrict__ item_off,
+                                                const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
+                                                int T, FitCluster* __restrict__ cl, uint8_t* __restrict__ inlier,
+                                                float* __restrict__ part, float eps, uint32_t* __restrict__ err,
+                                                uint32_t* __restrict__ done, float* __restrict__ cen) {
     pdl_gate();
     const uint32_t k = *kp;
-    const uint32_t cpt = (uint32_t)T / kChunk;
+    __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 4];
     __shared__ df2 sh[3 * (kT / 32)];
-    __shared__ uint32_t shn[kT / 32];
-    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
-        df2 v[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
-        uint32_t n = 0;
-        const uint32_t base = item_off[c] * cpt, nch = (off[c + 1] - off[c] + kChunk - 1) / kChunk;
-#pragma unroll 2
-        for (uint32_t j = threadIdx.x; j < nch; j += kT) {
-            const float* pp = part + (size_t)(base + j) * 10;
-            n += (uint32_t)pp[0];
-            v[0] = df_add(v[0], df2{pp[1], 0.0f});
-            v[1] = df_add(v[1], df2{pp[2], 0.0f});
-            v[2] = df_add(v[2], df2{pp[3], 0.0f});
-        }
+    __shared__ uint32_t shn[kT / 32], s_last;
+    const uint32_t n_items = item_off[k];
+    const uint32_t cpt = (uint32_t)T / kChunk;  // chunks per work item
+    for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const uint32_t c = find_cluster(item_cl, item_off, k, it);
+        const FitCluster f = cl[c];
+        const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
+        const uint32_t end = min(off[c + 1], start + (uint32_t)T);
+        unsigned long long ext[kFiltDirs];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-        if ((threadIdx.x & 31) == 0) shn[threadIdx.x >> 5] = n;
-        block_df_sum<3>(v, sh);
-        if (threadIdx.x == 0) {
-            n = 0;
-            for (int q = 0; q < kT / 32; ++q) n += shn[q];
-            FitCluster& f = cl[c];
-            f.inliers = n;
-            df2 cx{f.o[0], 0.0f}, cy{f.o[1], 0.0f}, cz{f.o[2], 0.0f};
-            if (n) {
-                cx = df_add(cx, df_div_count(v[0], n));
-                cy = df_add(cy, df_div_count(v[1], n));
-                cz = df_add(cz, df_div_count(v[2], n));
+        for (int d = 0; d < kFiltDirs; ++d) ext[d] = 0;
+        bool big = false;
+        // chunk within the item; its slot is it * cpt + j (item_off[c] * cpt + its chunk in the cluster)
+        uint32_t j = 0;
+#pragma unroll 4
+        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {  // unrolled: later chunks' loads go out early
+            const uint32_t q = q0 + threadIdx.x;
+            float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};  // count, sum (p - o)
+            if (q < end) {
+                const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
+                const bool in = f.best_h >= 0 && plane_dist(f.n[0], f.n[1], f.n[2], f.d, px, py, pz) <= eps;
+                inlier[q] = in;
+                if (in) {
+                    v[0] = 1.0f;
+                    v[1] = __fsub_rn(px, f.o[0]);
+                    v[2] = __fsub_rn(py, f.o[1]);
+                    v[3] = __fsub_rn(pz, f.o[2]);
+                    const int2 xy = quantise(f, px, py, pz);
+                    big |= (abs(xy.x) >= (1 << 28)) | (abs(xy.y) >= (1 << 28));
+                    const uint32_t idx = q - off[c];
+#pragma unroll
+                    for (int d = 0; d < kFiltDirs; ++d) {
+                        const unsigned long long key = ext_key(dir_value(d, xy), idx);
+                        ext[d] = key > ext[d] ? key : ext[d];
+                    }
+                }
             }
-            float* ce = cen + 6 * (size_t)c;
-            ce[0] = cx.hi; ce[1] = cx.lo; ce[2] = cy.hi; ce[3] = cy.lo; ce[4] = cz.hi; ce[5] = cz.lo;
-            f.c[0] = cx.hi; f.c[1] = cy.hi; f.c[2] = cz.hi;
+            warp_park<4>(v, wp, j);
         }
-        __syncthreads();  // shared partials reused by the next cluster
+        chunks_out<4>(wp, j, part + (size_t)it * cpt * 10, 0);  // slot 0 holds the count (at most 256: exact)
+        if (big) atomicOr(err, kErrOverflow);
+#pragma unroll
+        for (int d = 0; d < kFiltDirs; ++d) {
+            unsigned long long m = ext[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+                m = t > m ? t : m;
+            }
+            if ((threadIdx.x & 31) == 0 && m) atomicMax(&cl[c].ext[d], m);
+        }
+        __syncthreads();
+        if (cta_last_item(done + 3 * (size_t)c + 1, item_off[c + 1] - item_off[c], &s_last))
+            centroid_cta(c, off, item_off, T, part, cl, cen, sh, shn);
     }
 }
 
 __device__ __forceinline__ long long cross3(int2 o, int2 a, int2 b) {
     return (long long)(a.x - o.x) * (long long)(b.y - o.y) - (long long)(a.y - o.y) * (long long)(b.x - o.x);
 }
+
+__device__ __forceinline__ void refit_cta(uint32_t c, const uint32_t* __restrict__ off,
+                                          const uint32_t* __restrict__ item_off, int T, const float* __restrict__ part,
+                                          const float* __restrict__ cen, FitCluster* __restrict__ cl, df2* sh);
 
 // Covariance partials about the centroid, and the 16-gon filter: inliers
 // strictly inside the polygon through the 16 extreme inliers cannot be hull
@@ -519,10 +569,12 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
                                                const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
                                                int T, FitCluster* __restrict__ cl, const uint8_t* __restrict__ inlier,
                                                const float* __restrict__ cen, float* __restrict__ part,
-                                               int2* __restrict__ surv) {
+                                               int2* __restrict__ surv, uint32_t* __restrict__ done) {
     pdl_gate();
     const uint32_t k = *kp;
     constexpr int kSurvBuf = 128;
+    __shared__ df2 sh[6 * (kT / 32)];
+    __shared__ uint32_t s_last;
     __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 6];
     __shared__ int2 poly[kFiltDirs + 1];
     __shared__ int npoly;
@@ -598,10 +650,12 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
         }
         if (cnt) flush();
         chunks_out<6>(wp, j, part + (size_t)it * cpt * 10, 4);
+        if (cta_last_item(done + 3 * (size_t)c + 2, item_off[c + 1] - item_off[c], &s_last))
+            refit_cta(c, off, item_off, T, part, cen, cl, sh);
     }
 }
 
-// Refit (one warp per cluster): total least squares on the inliers.  The
+// Refit of cluster c by a whole CTA: total least squares on the inliers.  The
 // covariance A about the centroid is summed in double-float over the
 // per-chunk partials and scaled by its trace.  Its smallest eigenvector is the
 // dominant eigenvector of the adjugate adj(A) (eigenvalues lambda_j lambda_k);
@@ -611,14 +665,11 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
 // n_z >= 0, d = -n . centroid (double-float); lambda_mid < 10 lambda_min
 // (from the trace, the Rayleigh quotient in double-float and
 // x^T adj(A) x = lambda_1 lambda_2) flags the plane ill-conditioned.
-__global__ void __launch_bounds__(kT) k_refit(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
-                                              const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
-                                              const float* __restrict__ cen, FitCluster* __restrict__ cl) {
-    pdl_gate();
-    const uint32_t k = *kp;
+__device__ __forceinline__ void refit_cta(uint32_t c, const uint32_t* __restrict__ off,
+                                          const uint32_t* __restrict__ item_off, int T, const float* __restrict__ part,
+                                          const float* __restrict__ cen, FitCluster* __restrict__ cl, df2* sh) {
     const uint32_t cpt = (uint32_t)T / kChunk;
-    __shared__ df2 sh[6 * (kT / 32)];
-    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
+    {
         df2 A[6];
 #pragma unroll
         for (int e = 0; e < 6; ++e) A[e] = df2{0.0f, 0.0f};
@@ -626,72 +677,73 @@ __global__ void __launch_bounds__(kT) k_refit(const uint32_t* __restrict__ off, 
 #pragma unroll 2
         for (uint32_t j = threadIdx.x; j < nch; j += kT)
 #pragma unroll
-            for (int e = 0; e < 6; ++e) A[e] = df_add(A[e], df2{part[(size_t)(base + j) * 10 + 4 + e], 0.0f});
+            for (int e = 0; e < 6; ++e) A[e] = df_add(A[e], df2{__ldcg(part + (size_t)(base + j) * 10 + 4 + e), 0.0f});
         block_df_sum<6>(A, sh);
-        __syncthreads();  // thread 0 holds the sums; the shared partials are free for the next cluster
-        if (threadIdx.x) continue;
-        FitCluster& f = cl[c];
-        uint32_t flags = 0;
-        float rn[3] = {0.0f, 0.0f, 0.0f}, rd = 0.0f;
-        const float tr = __fadd_rn(__fadd_rn(A[0].hi, A[1].hi), A[2].hi);
-        if (f.best_h >= 0 && f.inliers > 0 && tr > 0.0f) {
-            // A / tr: entries of magnitude at most 1 (the diagonal is non-negative)
-            const float itr = __fdiv_rn(1.0f, tr);
-            df2 S[6];
-#pragma unroll
-            for (int e = 0; e < 6; ++e) S[e] = df_mulf(A[e], itr);
-            const df2 a = S[0], b = S[1], cc = S[2], d = S[3], e = S[4], g = S[5];
-            // symmetric adjugate (cofactors) of [[a d e] [d b g] [e g cc]]
-            const float m00 = df_sub(df_mul(b, cc), df_mul(g, g)).hi, m11 = df_sub(df_mul(a, cc), df_mul(e, e)).hi;
-            const float m22 = df_sub(df_mul(a, b), df_mul(d, d)).hi, m01 = df_sub(df_mul(e, g), df_mul(d, cc)).hi;
-            const float m02 = df_sub(df_mul(d, g), df_mul(e, b)).hi, m12 = df_sub(df_mul(d, e), df_mul(a, g)).hi;
-            float x = f.n[0], y = f.n[1], z = f.n[2];
-            bool ok = true;
-            for (int it = 0; it < 6; ++it) {
-                const float nx = __fmaf_rn(m02, z, __fmaf_rn(m01, y, __fmul_rn(m00, x)));
-                const float ny = __fmaf_rn(m12, z, __fmaf_rn(m11, y, __fmul_rn(m01, x)));
-                const float nz = __fmaf_rn(m22, z, __fmaf_rn(m12, y, __fmul_rn(m02, x)));
-                const float q = __fmaf_rn(nz, nz, __fmaf_rn(ny, ny, __fmul_rn(nx, nx)));
-                if (!(q > 1e-30f) || !(q < 1e30f)) { ok = false; break; }  // rank <= 1: keep the RANSAC normal
-                const float sc = rsqrtf(q);
-                x = __fmul_rn(nx, sc); y = __fmul_rn(ny, sc); z = __fmul_rn(nz, sc);
-            }
-            if (!ok) {
-                x = f.n[0]; y = f.n[1]; z = f.n[2];
-                flags |= 1u;
-            }
-            // unit length to FP32 accuracy
-            const float inv = __fdiv_rn(1.0f, __fsqrt_rn(__fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x)))));
-            x = __fmul_rn(x, inv); y = __fmul_rn(y, inv); z = __fmul_rn(z, inv);
-            if (z < 0.0f || (z == 0.0f && (y < 0.0f || (y == 0.0f && x < 0.0f)))) { x = -x; y = -y; z = -z; }
-            // eigenvalues (scaled by 1 / tr) for the conditioning flag
-            const df2 ax = df_add(df_add(df_mulf(a, x), df_mulf(d, y)), df_mulf(e, z));
-            const df2 ay = df_add(df_add(df_mulf(d, x), df_mulf(b, y)), df_mulf(g, z));
-            const df2 az = df_add(df_add(df_mulf(e, x), df_mulf(g, y)), df_mulf(cc, z));
-            const float lmin = df_add(df_add(df_mulf(ax, x), df_mulf(ay, y)), df_mulf(az, z)).hi;
-            const float p12 = x * (m00 * x + m01 * y + m02 * z) + y * (m01 * x + m11 * y + m12 * z) +
-                              z * (m02 * x + m12 * y + m22 * z);
-            const float Sx = 1.0f - lmin;
-            const float disc = fmaxf(Sx * Sx - 4.0f * p12, 0.0f);
-            const float lmax = 0.5f * (Sx + sqrtf(disc));
-            const float lmid = lmax > 0.0f ? p12 / lmax : 0.0f;  // no cancellation
-            if (!(lmid >= 10.0f * lmin)) flags |= 1u;
-            rn[0] = x; rn[1] = y; rn[2] = z;
-            const float* ce = cen + 6 * (size_t)c;
-            const df2 dot = df_add(df_add(df_mulf(df2{ce[0], ce[1]}, x), df_mulf(df2{ce[2], ce[3]}, y)),
-                                   df_mulf(df2{ce[4], ce[5]}, z));
-            rd = -dot.hi;
-        } else if (f.best_h >= 0 && f.inliers > 0) {
-            flags |= 1u;  // zero spread: no plane to fit; the RANSAC normal through the centroid
-            rn[0] = f.n[0]; rn[1] = f.n[1]; rn[2] = f.n[2];
-            const float* ce = cen + 6 * (size_t)c;
-            rd = -df_add(df_add(df_mulf(df2{ce[0], ce[1]}, rn[0]), df_mulf(df2{ce[2], ce[3]}, rn[1])),
-                         df_mulf(df2{ce[4], ce[5]}, rn[2])).hi;
+        if (threadIdx.x == 0) {
+            FitCluster& f = cl[c];
+            uint32_t flags = 0;
+            float rn[3] = {0.0f, 0.0f, 0.0f}, rd = 0.0f;
+            const float tr = __fadd_rn(__fadd_rn(A[0].hi, A[1].hi), A[2].hi);
+            if (f.best_h >= 0 && f.inliers > 0 && tr > 0.0f) {
+                // A / tr: entries of magnitude at most 1 (the diagonal is non-negative)
+                const float itr = __fdiv_rn(1.0f, tr);
+                df2 S[6];
+    #pragma unroll
+                for (int e = 0; e < 6; ++e) S[e] = df_mulf(A[e], itr);
+                const df2 a = S[0], b = S[1], cc = S[2], d = S[3], e = S[4], g = S[5];
+                // symmetric adjugate (cofactors) of [[a d e] [d b g] [e g cc]]
+                const float m00 = df_sub(df_mul(b, cc), df_mul(g, g)).hi, m11 = df_sub(df_mul(a, cc), df_mul(e, e)).hi;
+                const float m22 = df_sub(df_mul(a, b), df_mul(d, d)).hi, m01 = df_sub(df_mul(e, g), df_mul(d, cc)).hi;
+                const float m02 = df_sub(df_mul(d, g), df_mul(e, b)).hi, m12 = df_sub(df_mul(d, e), df_mul(a, g)).hi;
+                float x = f.n[0], y = f.n[1], z = f.n[2];
+                bool ok = true;
+                for (int it = 0; it < 6; ++it) {
+                    const float nx = __fmaf_rn(m02, z, __fmaf_rn(m01, y, __fmul_rn(m00, x)));
+                    const float ny = __fmaf_rn(m12, z, __fmaf_rn(m11, y, __fmul_rn(m01, x)));
+                    const float nz = __fmaf_rn(m22, z, __fmaf_rn(m12, y, __fmul_rn(m02, x)));
+                    const float q = __fmaf_rn(nz, nz, __fmaf_rn(ny, ny, __fmul_rn(nx, nx)));
+                    if (!(q > 1e-30f) || !(q < 1e30f)) { ok = false; break; }  // rank <= 1: keep the RANSAC normal
+                    const float sc = rsqrtf(q);
+                    x = __fmul_rn(nx, sc); y = __fmul_rn(ny, sc); z = __fmul_rn(nz, sc);
+                }
+                if (!ok) {
+                    x = f.n[0]; y = f.n[1]; z = f.n[2];
+                    flags |= 1u;
+                }
+                // unit length to FP32 accuracy
+                const float inv = __fdiv_rn(1.0f, __fsqrt_rn(__fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x)))));
+                x = __fmul_rn(x, inv); y = __fmul_rn(y, inv); z = __fmul_rn(z, inv);
+                if (z < 0.0f || (z == 0.0f && (y < 0.0f || (y == 0.0f && x < 0.0f)))) { x = -x; y = -y; z = -z; }
+                // eigenvalues (scaled by 1 / tr) for the conditioning flag
+                const df2 ax = df_add(df_add(df_mulf(a, x), df_mulf(d, y)), df_mulf(e, z));
+                const df2 ay = df_add(df_add(df_mulf(d, x), df_mulf(b, y)), df_mulf(g, z));
+                const df2 az = df_add(df_add(df_mulf(e, x), df_mulf(g, y)), df_mulf(cc, z));
+                const float lmin = df_add(df_add(df_mulf(ax, x), df_mulf(ay, y)), df_mulf(az, z)).hi;
+                const float p12 = x * (m00 * x + m01 * y + m02 * z) + y * (m01 * x + m11 * y + m12 * z) +
+                                  z * (m02 * x + m12 * y + m22 * z);
+                const float Sx = 1.0f - lmin;
+                const float disc = fmaxf(Sx * Sx - 4.0f * p12, 0.0f);
+                const float lmax = 0.5f * (Sx + sqrtf(disc));
+                const float lmid = lmax > 0.0f ? p12 / lmax : 0.0f;  // no cancellation
+                if (!(lmid >= 10.0f * lmin)) flags |= 1u;
+                rn[0] = x; rn[1] = y; rn[2] = z;
+                const float* ce = cen + 6 * (size_t)c;
+                const df2 dot = df_add(df_add(df_mulf(df2{ce[0], ce[1]}, x), df_mulf(df2{ce[2], ce[3]}, y)),
+                                       df_mulf(df2{ce[4], ce[5]}, z));
+                rd = -dot.hi;
+            } else if (f.best_h >= 0 && f.inliers > 0) {
+                flags |= 1u;  // zero spread: no plane to fit; the RANSAC normal through the centroid
+                rn[0] = f.n[0]; rn[1] = f.n[1]; rn[2] = f.n[2];
+                const float* ce = cen + 6 * (size_t)c;
+                rd = -df_add(df_add(df_mulf(df2{ce[0], ce[1]}, rn[0]), df_mulf(df2{ce[2], ce[3]}, rn[1])),
+                             df_mulf(df2{ce[4], ce[5]}, rn[2])).hi;
         }
         f.refit_n[0] = rn[0]; f.refit_n[1] = rn[1]; f.refit_n[2] = rn[2];
         f.refit_d = rd;
         f.flags = flags;
+        }
     }
+    __syncthreads();  // shared partials reused next
 }
 
 __device__ __forceinline__ unsigned long long xy_key(int2 p) {
@@ -749,10 +801,13 @@ constexpr int kHullDirs = 128;
 // (3) bitonic sort by (X, Y), duplicates removed; (4) monotone chain, lower
 // and upper halves built concurrently by two threads.  If more than
 // kHullCap points remain, gift wrapping runs over the survivors instead.
+// hull_ctr: a word that is zero at launch; the last CTA to finish turns
+// hull_cnt into the hulls' offsets (exclusive scan, the total at [k]) and
+// zeroes the word again.
 __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp,
                                              const FitCluster* __restrict__ cl, const int2* __restrict__ surv,
                                              int2* __restrict__ hull, uint32_t* __restrict__ hull_cnt,
-                                             uint32_t* __restrict__ err) {
+                                             uint32_t* __restrict__ err, uint32_t* __restrict__ hull_ctr) {
     pdl_gate();
     const uint32_t k = *kp;
     extern __shared__ unsigned long long sk[];              // kHullCap keys, then kHullCap unique
@@ -965,17 +1020,54 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
             if (threadIdx.x == 0) hull_cnt[c] = (uint32_t)h;
         }
     }
+    // hull offsets, by the last CTA to finish
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_cnt = atomicAdd(hull_ctr, 1u) + 1u == gridDim.x;
+    __syncthreads();
+    if (!s_cnt) return;
+    __threadfence();
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < k; c0 += kT) {
+        const uint32_t c = c0 + threadIdx.x;
+        const uint32_t v = c < k ? __ldcg(hull_cnt + c) : 0u;
+        uint32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        uint32_t wpre = 0, tot = 0;
+        for (int q = 0; q < kT / 32; ++q) {
+            if (q < w) wpre += wsum[q];
+            tot += wsum[q];
+        }
+        if (c < k) hull_cnt[c] = carry + wpre + inc - v;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        hull_cnt[k] = carry;
+        *hull_ctr = 0;
+    }
 }
 
-// Work items per cluster (scanned into the item offsets next), and the work
-// queue's heads cleared for the scoring that follows.
+// Work items per cluster (scanned into the item offsets next) -- at least one,
+// so that an empty cluster's per-cluster steps still run -- the work queue's
+// heads and the per-cluster completion counters (done, may be null) cleared
+// for the fit that follows.
 __global__ void k_items(const uint32_t* __restrict__ off, const uint32_t* __restrict__ kp, int T,
-                        uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ queue) {
+                        uint32_t* __restrict__ item_cnt, uint32_t* __restrict__ queue, uint32_t* __restrict__ done) {
     pdl_gate();
     const uint32_t k = *kp;
     if (blockIdx.x == 0 && threadIdx.x < 4) queue[threadIdx.x] = 0;
-    for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT)
-        item_cnt[c] = (off[c + 1] - off[c] + (uint32_t)T - 1) / (uint32_t)T;
+    for (uint32_t c = blockIdx.x * kT + threadIdx.x; c < k; c += gridDim.x * kT) {
+        const uint32_t n = off[c + 1] - off[c];
+        item_cnt[c] = n ? (n + (uint32_t)T - 1) / (uint32_t)T : 1u;
+        if (done) done[3 * (size_t)c] = done[3 * (size_t)c + 1] = done[3 * (size_t)c + 2] = 0u;
+    }
 }
 
 __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restrict__ labels,
@@ -1003,7 +1095,9 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
                                                    const uint32_t* __restrict__ item_cl,
                                                    const uint32_t* __restrict__ kp, int H, int T,
                                                    const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
-                                                   uint32_t* __restrict__ queue, float eps) {
+                                                   uint32_t* __restrict__ queue, float eps,
+                                                   const uint8_t* __restrict__ valid, FitCluster* __restrict__ cl,
+                                                   uint32_t* __restrict__ done) {
     pdl_wait();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];  // [kT / 32][T]
@@ -1062,6 +1156,17 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
                 if (h < H && acc[r]) atomicAdd(&counts[(size_t)c * H + h], acc[r]);
             }
         }
+        if (done) {  // the warp that scores a cluster's last item runs stage c for it
+            __threadfence();
+            __syncwarp();
+            uint32_t last = 0;
+            if (lane == 0) last = atomicAdd(done + 3 * (size_t)c, 1u) + 1u == item_off[c + 1] - item_off[c];
+            if (__shfl_sync(0xffffffffu, last, 0)) {
+                __threadfence();
+                const unsigned long long best = best_key(c, lane, 32, H, valid, counts);
+                if (lane == 0) select_record(c, best, pts, off, H, hyp, cl);
+            }
+        }
     }
 }
 
@@ -1078,6 +1183,9 @@ struct ScoreArgs {
     uint32_t* queue;
     float eps;
     int grid;
+    const uint8_t* valid;     // stage c after the last item of each cluster: with done non-null
+    FitCluster* cl;
+    uint32_t* done;
 };
 
 template <int R>
@@ -1086,7 +1194,7 @@ cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s) {
     const int P = kT / G;
     const size_t smem = (size_t)a.T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
     launch_full(k_score<R>, dim3(a.grid), dim3(kT), smem, s, a.pts, a.off, a.item_off, a.item_cl, a.kp, a.H, a.T,
-                a.hyp, a.counts, a.queue, a.eps);
+                a.hyp, a.counts, a.queue, a.eps, a.valid, a.cl, a.done);
     return cudaGetLastError();
 }
 
@@ -1094,7 +1202,7 @@ template <int R>
 cudaError_t launch_score_warp(const ScoreArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)(kT / 32) * a.T * sizeof(float4);
     launch_full(k_score_warp<R>, dim3(a.grid), dim3(kT), smem, s, a.pts, a.off, a.item_off, a.item_cl, a.kp, a.H,
-                a.T, a.hyp, a.counts, a.queue, a.eps);
+                a.T, a.hyp, a.counts, a.queue, a.eps, a.valid, a.cl, a.done);
     return cudaGetLastError();
 }
 
@@ -1183,7 +1291,7 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     cudaError_t e;
     VM_STAGE_BEGIN(hk, kStHyp, s);
     const unsigned kgrid = (kcap + kT - 1) / kT < (uint32_t)sms * 8 ? (kcap + kT - 1) / kT : (uint32_t)sms * 8;
-    launch_k(k_items, dim3(kgrid), dim3(kT), 0, s, off, kp, T, fb.item_off, fb.queue);
+    launch_k(k_items, dim3(kgrid), dim3(kT), 0, s, off, kp, T, fb.item_off, fb.queue, fb.done);
     e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s, fb.err, true);
     if (e != cudaSuccess) return e;
     const size_t kh = (size_t)kcap * H;
@@ -1200,7 +1308,8 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     bool warp;
     score_variant(t, H, R, warp);
     VM_STAGE_BEGIN(hk, kStScore, s);
-    const ScoreArgs sa{pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid};
+    const ScoreArgs sa{pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid,
+                       fb.hyp_valid, fb.cl, fb.done};
     if (warp) {
         switch (R) {
             case 1: e = launch_score_warp<1>(sa, s); break;
@@ -1219,25 +1328,22 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     if (e != cudaSuccess) return e;
     VM_STAGE_END(hk, kStScore, s);
     count_launch(1);
+    // stage c ran in the scoring kernel (the last item of each cluster), the
+    // centroid runs in the extraction kernel, the refit in the filter kernel
     const unsigned cgrid = kcap < (uint32_t)sms * 8 ? kcap : (uint32_t)sms * 8;
     VM_STAGE_BEGIN(hk, kStExtract, s);
-    launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
     const unsigned igrid = (unsigned)sms * 8;
     launch_full(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier,
-                fb.part, p.eps, fb.err);
-    const unsigned wgrid = kcap < (uint32_t)sms * 8 ? kcap : (uint32_t)sms * 8;  // a CTA per cluster
-    launch_k(k_centroid, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
+                fb.part, p.eps, fb.err, fb.done, fb.cen);
     launch_full(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier,
-                fb.cen, fb.part, fb.surv);
+                fb.cen, fb.part, fb.surv, fb.done);
     VM_STAGE_END(hk, kStExtract, s);
-    count_launch(4);
-    VM_STAGE_BEGIN(hk, kStHull, s);
-    launch_k(k_refit, dim3(wgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cen, fb.cl);
-    launch_k(k_hull, dim3(cgrid), dim3(kT), fit_hull_smem(), s, off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err);
-    e = exclusive_scan_dev(fb.hull_cnt, fb.hull_cnt, fb.tot + 1, kp, kcap, fb.scan_tmp, s, fb.err, true);
-    if (e != cudaSuccess) return e;
-    VM_STAGE_END(hk, kStHull, s);
     count_launch(2);
+    VM_STAGE_BEGIN(hk, kStHull, s);
+    launch_k(k_hull, dim3(cgrid), dim3(kT), fit_hull_smem(), s, off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err,
+             fb.queue + 3);
+    VM_STAGE_END(hk, kStHull, s);
+    count_launch(1);
     return cudaGetLastError();
 }
 
@@ -1368,7 +1474,8 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     fit_init_attributes();
     // the work queue starts at zero every call (k_items); counts are zeroed by k_hyp
     launch_k(k_set_u32, dim3(1), dim3(1), 0, s, kdev, k);
-    launch_k(k_items, dim3((k + kT - 1) / kT), dim3(kT), 0, s, off, kdev, t.tile, item_off, queue);
+    launch_k(k_items, dim3((k + kT - 1) / kT), dim3(kT), 0, s, off, kdev, t.tile, item_off, queue,
+             static_cast<uint32_t*>(nullptr));
     if ((e = exclusive_scan_dev(item_off, item_off, total, kdev, k, scan_tmp, s, nullptr, true)) != cudaSuccess)
         return cuda_status(e, "scan");
     const size_t kh = (size_t)k * H;
@@ -1384,7 +1491,8 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     bool warp;
     score_variant(tc, H, R, warp);
     const int grid = sms * t.ctas_per_sm;
-    const ScoreArgs sa{xyz, off, item_off, nullptr, kdev, H, t.tile, hyp, counts, queue, params->eps, grid};
+    const ScoreArgs sa{xyz, off, item_off, nullptr, kdev, H, t.tile, hyp, counts, queue, params->eps, grid,
+                       valid, cl, nullptr};
     switch (R) {
         case 1: e = launch_score<1>(sa, s); break;
         case 2: e = launch_score<2>(sa, s); break;

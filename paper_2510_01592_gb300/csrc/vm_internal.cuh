@@ -390,6 +390,7 @@ struct FitBuffers {
     uint32_t* err;          // device error word
     uint32_t* tot;          // [4] scan totals
     uint32_t* kdev;         // cluster count when the caller supplies it
+    uint32_t* done;         // [kcap][3] per-cluster completion counters (scoring, extraction, filter)
     size_t kcap, npts_cap, items_cap;  // items_cap: 256-point partial-sum chunks
     int H;
 };
