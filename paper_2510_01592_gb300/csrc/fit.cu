@@ -1070,6 +1070,51 @@ __global__ void k_items(const uint32_t* __restrict__ off, const uint32_t* __rest
     }
 }
 
+// The work items of up to kItemsScanMax clusters and their offsets in one
+// CTA: counts as in k_items, an exclusive scan with a carry across rounds,
+// the total at item_off[k].
+constexpr int kItemsScanT = 1024;
+constexpr uint32_t kItemsScanMax = 16384;
+__global__ void __launch_bounds__(kItemsScanT) k_items_scan(const uint32_t* __restrict__ off,
+                                                             const uint32_t* __restrict__ kp, int T,
+                                                             uint32_t* __restrict__ item_off,
+                                                             uint32_t* __restrict__ queue,
+                                                             uint32_t* __restrict__ done) {
+    pdl_gate();
+    __shared__ uint32_t ws[kItemsScanT / 32];
+    const uint32_t k = *kp;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < 4) queue[threadIdx.x] = 0;
+    uint32_t carry = 0;
+    for (uint32_t c0 = 0; c0 < k; c0 += kItemsScanT) {
+        const uint32_t c = c0 + threadIdx.x;
+        uint32_t v = 0;
+        if (c < k) {
+            const uint32_t n = off[c + 1] - off[c];
+            v = n ? (n + (uint32_t)T - 1) / (uint32_t)T : 1u;
+            if (done) done[3 * (size_t)c] = done[3 * (size_t)c + 1] = done[3 * (size_t)c + 2] = 0u;
+        }
+        uint32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) ws[w] = inc;
+        __syncthreads();
+        uint32_t wpre = 0, tot = 0;
+        for (int q = 0; q < kItemsScanT / 32; ++q) {
+            const uint32_t t = ws[q];
+            wpre += q < w ? t : 0u;
+            tot += t;
+        }
+        if (c < k) item_off[c] = carry + wpre + inc - v;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) item_off[k] = carry;
+}
+
 __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restrict__ labels,
                        const uint32_t* __restrict__ kp, const FitCluster* __restrict__ cl,
                        const int2* __restrict__ hull, const uint32_t* __restrict__ hull_off,
@@ -1290,16 +1335,22 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     const int T = (t.tile + (int)kChunk - 1) / (int)kChunk * (int)kChunk;  // callers validate; never below a chunk
     cudaError_t e;
     VM_STAGE_BEGIN(hk, kStHyp, s);
-    const unsigned kgrid = (kcap + kT - 1) / kT < (uint32_t)sms * 8 ? (kcap + kT - 1) / kT : (uint32_t)sms * 8;
-    launch_k(k_items, dim3(kgrid), dim3(kT), 0, s, off, kp, T, fb.item_off, fb.queue, fb.done);
-    e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s, fb.err, true);
-    if (e != cudaSuccess) return e;
+    if (kcap <= kItemsScanMax) {
+        launch_k(k_items_scan, dim3(1), dim3(kItemsScanT), 0, s, off, kp, T, fb.item_off, fb.queue, fb.done);
+        count_launch(1);
+    } else {
+        const unsigned kgrid = (kcap + kT - 1) / kT < (uint32_t)sms * 8 ? (kcap + kT - 1) / kT : (uint32_t)sms * 8;
+        launch_k(k_items, dim3(kgrid), dim3(kT), 0, s, off, kp, T, fb.item_off, fb.queue, fb.done);
+        e = exclusive_scan_dev(fb.item_off, fb.item_off, fb.tot, kp, kcap, fb.scan_tmp, s, fb.err, true);
+        if (e != cudaSuccess) return e;
+        count_launch(1);
+    }
     const size_t kh = (size_t)kcap * H;
     const unsigned hgrid = (unsigned)((kh + kT - 1) / kT < (size_t)sms * 16 ? (kh + kT - 1) / kT : (size_t)sms * 16);
     launch_k(k_hyp, dim3(hgrid), dim3(kT), 0, s, pts, off, labels, kp, H, p.seed, round, fb.hyp, fb.hyp_valid,
              fb.counts, fb.item_off, fb.item_cl);
     VM_STAGE_END(hk, kStHyp, s);
-    count_launch(2);
+    count_launch(1);
     const int grid = sms * t.ctas_per_sm;
     // The warp schedule needs ceil(H / R) <= 32 lanes with R <= 8 and its
     // per-warp tiles within the shared-memory limit; otherwise the CTA one

@@ -154,6 +154,110 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(const uint32_t* 
     }
 }
 
+// The allocated bricks in key order in one pass (a stream compaction with the
+// look-back scan above): tile t of the brick table flags its allocated
+// entries (slot >= 0), ranks them within the tile, looks back for the count
+// of allocated bricks before the tile, then writes every entry's rank (or -1)
+// and, per allocated brick, its slot and key at its rank.  The last tile
+// writes the count.  Block 0 also clears the words clear[1 .. n_clear) (a
+// counter block whose word 0 is the count) and zero0 / zero1 (may be null).
+__global__ void __launch_bounds__(kScanThreads) k_order_bricks(const int32_t* __restrict__ table, uint32_t nb,
+                                                               int32_t* __restrict__ rank_table,
+                                                               int32_t* __restrict__ sorted_slot,
+                                                               int32_t* __restrict__ sorted_key,
+                                                               uint32_t* __restrict__ clear, int n_clear,
+                                                               uint32_t* __restrict__ zero0,
+                                                               uint32_t* __restrict__ zero1,
+                                                               uint32_t* __restrict__ state, uint32_t* err) {
+    pdl_gate();
+    __shared__ int32_t buf[kScanTile];
+    __shared__ uint32_t ws[kScanThreads / 32];
+    __shared__ uint32_t tot, s_tile, s_prefix;
+    unsigned long long* status = reinterpret_cast<unsigned long long*>(state + 4);
+    if (blockIdx.x == 0) {
+        for (int i = 1 + threadIdx.x; i < n_clear; i += kScanThreads) clear[i] = 0u;
+        if (threadIdx.x == 0) {
+            if (zero0) *zero0 = 0u;
+            if (zero1) *zero1 = 0u;
+        }
+    }
+    const uint32_t nt_used = (nb + kScanTile - 1) / kScanTile;
+    const uint32_t epoch = *(volatile uint32_t*)(state + 2);
+    if (threadIdx.x == 0) s_tile = atomicAdd(state, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile < nt_used) {
+        const uint32_t base = tile * kScanTile;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const uint32_t j = base + i * kScanThreads + threadIdx.x;
+            buf[i * kScanThreads + threadIdx.x] = j < nb ? table[j] : -1;
+        }
+        __syncthreads();
+        int32_t v[kScanItems];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            v[i] = buf[threadIdx.x * kScanItems + i];
+            sum += v[i] >= 0;
+        }
+        const uint32_t ex_local = block_excl_scan(sum, ws, &tot);
+        if (threadIdx.x == 0) {
+            const uint32_t agg = tot;
+            uint32_t prefix = 0;
+            if (tile == 0) {
+                atomicExch(status, lb_word(epoch, kFlagInc, agg));
+            } else {
+                atomicExch(status + tile, lb_word(epoch, kFlagAgg, agg));
+                for (int64_t p = (int64_t)tile - 1; p >= 0; --p) {
+                    unsigned long long w = 0;
+                    int it = 0;
+                    for (; it < kLookbackCap; ++it) {
+                        w = *(volatile unsigned long long*)(status + p);
+                        if ((uint32_t)(w >> 34) == (epoch & kEpochMask) && ((w >> 32) & 3ull)) break;
+                    }
+                    if (it == kLookbackCap) {  // the predecessor never published: report, count it as 0
+                        if (err) atomicOr(err, kErrTimeout);
+                        break;
+                    }
+                    prefix += (uint32_t)(w & 0xffffffffull);
+                    if (((w >> 32) & 3ull) == kFlagInc) break;
+                }
+                atomicExch(status + tile, lb_word(epoch, kFlagInc, prefix + agg));
+            }
+            s_prefix = prefix;
+            if (tile == nt_used - 1) clear[0] = prefix + agg;
+        }
+        __syncthreads();
+        uint32_t rank = ex_local + s_prefix;
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const uint32_t j = base + threadIdx.x * kScanItems + i;
+            if (j < nb) {
+                if (v[i] >= 0) {
+                    sorted_slot[rank] = v[i];
+                    sorted_key[rank] = (int32_t)j;
+                    rank_table[j] = (int32_t)rank;
+                    ++rank;
+                } else {
+                    rank_table[j] = -1;
+                }
+            }
+        }
+    } else if (tile == 0 && threadIdx.x == 0) {  // an empty table
+        clear[0] = 0u;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(state + 1, 1u) == gridDim.x - 1) {  // the last CTA: reset for the next launch
+            state[0] = 0;
+            state[1] = 0;
+            state[2] = epoch + 1;
+            __threadfence();
+        }
+    }
+}
+
 // ------------------------------------------------------------------ radix sort
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
@@ -313,6 +417,17 @@ cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* tota
     const size_t nt = (n_cap + kScanTile - 1) / kScanTile;
     launch_k(k_scan_lookback, dim3((unsigned)nt), dim3(kScanThreads), 0, s, in, out, n_cap, n_dev, total, tmp, err,
              (int)end);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t order_bricks_dev(const int32_t* table, uint32_t nb, int32_t* rank_table, int32_t* sorted_slot,
+                             int32_t* sorted_key, uint32_t* clear, int n_clear, uint32_t* zero0, uint32_t* zero1,
+                             uint32_t* tmp, cudaStream_t s, uint32_t* err) {
+    if (reinterpret_cast<uintptr_t>(tmp) & 7) return cudaErrorInvalidValue;  // 64-bit status words
+    const size_t nt = ((size_t)nb + kScanTile - 1) / kScanTile;
+    launch_k(k_order_bricks, dim3((unsigned)(nt ? nt : 1)), dim3(kScanThreads), 0, s, table, nb, rank_table,
+             sorted_slot, sorted_key, clear, n_clear, zero0, zero1, tmp, err);
     count_launch(1);
     return cudaGetLastError();
 }

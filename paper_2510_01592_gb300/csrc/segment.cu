@@ -14,6 +14,7 @@
 // voxel) with the brick and a one-voxel halo from its 26 neighbours staged in
 // shared memory.
 #include <climits>
+#include <cstddef>
 #include <mutex>
 
 #include "vm_internal.cuh"
@@ -28,41 +29,6 @@ __device__ __forceinline__ void brick_coords(int32_t key, const Grid& g, int& bx
     bx = key % g.nbx;
     by = (key / g.nbx) % g.nby;
     bz = key / (g.nbx * g.nby);
-}
-
-// Also clears the segmentation's counters and error words (block 0): the
-// first kernel of a segmentation does it instead of separate memsets, so the
-// launches that follow chain programmatically from the start.
-__global__ void k_brick_flags(const int32_t* __restrict__ table, uint32_t nb, uint32_t* __restrict__ flags,
-                              SegCounters* __restrict__ ctr, uint32_t* __restrict__ zero0,
-                              uint32_t* __restrict__ zero1) {
-    pdl_gate();
-    if (blockIdx.x == 0) {
-        uint32_t* w = reinterpret_cast<uint32_t*>(ctr);
-        for (int i = threadIdx.x; i < (int)(sizeof(SegCounters) / 4); i += kT) w[i] = 0;
-        if (threadIdx.x == 0) {
-            if (zero0) *zero0 = 0;
-            if (zero1) *zero1 = 0;
-        }
-    }
-    for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < nb; i += gridDim.x * kT) flags[i] = table[i] >= 0;
-}
-
-__global__ void k_brick_compact(const int32_t* __restrict__ table, uint32_t nb, const uint32_t* __restrict__ flags,
-                                int32_t* __restrict__ rank_table, int32_t* __restrict__ sorted_slot,
-                                int32_t* __restrict__ sorted_key) {
-    pdl_gate();
-    for (uint32_t i = blockIdx.x * kT + threadIdx.x; i < nb; i += gridDim.x * kT) {
-        const int32_t t = table[i];
-        if (t >= 0) {
-            const uint32_t r = flags[i];
-            sorted_slot[r] = t;
-            sorted_key[r] = (int32_t)i;
-            rank_table[i] = (int32_t)r;
-        } else {
-            rank_table[i] = -1;
-        }
-    }
 }
 
 // Mean of each voxel: M = floor((2 S + c) / (2 c)), the exact integer mean in
@@ -741,10 +707,21 @@ __global__ void __launch_bounds__(kBrickVox) k_brick_clusters(const uint32_t* __
                                                               uint32_t* __restrict__ cl_size,
                                                               uint32_t* __restrict__ cl_label, uint32_t kcap,
                                                               uint32_t* __restrict__ keys,
-                                                              uint32_t* __restrict__ vals) {
+                                                              uint32_t* __restrict__ vals,
+                                                              SegCounters* __restrict__ ctr) {
     pdl_gate();
     const uint32_t n_sorted = min(*nsp, cap_b);
     __shared__ uint32_t wc[kBrickVox / 32];
+    // Clusters beyond the scratch flag a re-run, and the count is clamped for
+    // the kernels after this one (nothing here reads it).
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint32_t k = ctr->k;
+        ctr->k_need = k;
+        if (k > kcap) {
+            atomicOr(&ctr->err, kErrScratch);
+            ctr->k = kcap;
+        }
+    }
     for (uint32_t r = blockIdx.x; r < n_sorted; r += gridDim.x) {
         const size_t i = (size_t)r * kBrickVox + threadIdx.x;
         const uint32_t p = parent[i];
@@ -799,26 +776,12 @@ inline unsigned grid_for(size_t n, int sms, int per_sm = 8) {
 
 cudaError_t seg_order_bricks(const int32_t* brick_table, uint32_t nb_total, SegBuffers& b, int sms, cudaStream_t s,
                              uint32_t* zero0, uint32_t* zero1) {
-    launch_k(k_brick_flags, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags, b.ctr, zero0,
-             zero1);
-    cudaError_t e = exclusive_scan_u32(b.flags, b.flags, &b.ctr->n_sorted, nb_total, b.scan_tmp, s, &b.ctr->err);
-    if (e != cudaSuccess) return e;
-    launch_k(k_brick_compact, dim3(grid_for(nb_total, sms)), dim3(kT), 0, s, brick_table, nb_total, b.flags,
-             b.rank_table, b.sorted_slot, b.sorted_key);
-    count_launch(2);
-    return cudaGetLastError();
-}
-
-// Clusters beyond the scratch flag a re-run (the count is clamped for the
-// kernels that follow); cl_off[k] = the number of clustered points.
-__global__ void k_clusters_end(SegCounters* __restrict__ ctr, uint32_t kcap, uint32_t* __restrict__ cl_off) {
-    pdl_gate();
-    ctr->k_need = ctr->k;
-    if (ctr->k > kcap) {
-        ctr->err |= kErrScratch;
-        ctr->k = kcap;
-    }
-    cl_off[ctr->k] = ctr->tot;
+    (void)sms;
+    // n_sorted is the counter block's word 0: the pass writes it and clears the others
+    static_assert(offsetof(SegCounters, n_sorted) == 0, "the brick count leads the segmentation counters");
+    return order_bricks_dev(brick_table, nb_total, b.rank_table, b.sorted_slot, b.sorted_key,
+                            reinterpret_cast<uint32_t*>(b.ctr), (int)(sizeof(SegCounters) / 4), zero0, zero1,
+                            b.scan_tmp, s, &b.ctr->err);
 }
 
 cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* C, const vm_segment_params& p,
@@ -869,19 +832,19 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     e = exclusive_scan_dev(nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp, s, err);
     if (e != cudaSuccess) return e;
     launch_k(k_brick_clusters, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nroot, nvert,
-             rmask, b.sorted_key, b.cl_size, b.cl_label, kcap, b.keys, b.vals);
+             rmask, b.sorted_key, b.cl_size, b.cl_label, kcap, b.keys, b.vals, b.ctr);
     int bits = 1;
     while ((1ull << bits) < kcap && bits < 32) ++bits;
     e = stable_sort_pairs_dev(b.keys, b.vals, b.keys_alt, b.vals_alt, &b.ctr->n_kept, b.nv, bits, b.sort_tmp, s, err,
                               &b.ctr->k);
     if (e != cudaSuccess) return e;
-    e = exclusive_scan_dev(b.cl_size, b.cl_off, &b.ctr->tot, &b.ctr->k, kcap, b.scan_tmp, s, err);
+    // cluster offsets, closed by the number of clustered points at cl_off[k]
+    e = exclusive_scan_dev(b.cl_size, b.cl_off, &b.ctr->tot, &b.ctr->k, kcap, b.scan_tmp, s, err, true);
     if (e != cudaSuccess) return e;
-    launch_k(k_clusters_end, dim3(1), dim3(1), 0, s, b.ctr, kcap, b.cl_off);
     launch_k(k_gather, dim3(grid_for(b.nv, sms)), dim3(kT), 0, s, &b.ctr->n_kept, b.vals, b.vals_alt, &b.ctr->k, bits,
              b.M, b.nv, b.sorted_key, g, b.pts, b.pt_vid);
     VM_STAGE_END(hk, kStClusters, s);
-    count_launch(5);
+    count_launch(4);
     return cudaGetLastError();
 }
 

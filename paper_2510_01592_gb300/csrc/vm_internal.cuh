@@ -295,6 +295,14 @@ __device__ __forceinline__ bool sort_result_alt(uint32_t key_bound, int bits) {
     return executed & 1;
 }
 size_t sort_tmp_words(size_t n);
+// The allocated bricks of a brick table of nb entries in key order, in one
+// kernel: rank_table[j] = the rank of brick key j (-1: unallocated),
+// sorted_slot / sorted_key by rank; the count lands in clear[0] and the words
+// clear[1 .. n_clear) and zero0 / zero1 (may be null) are cleared.  tmp: the
+// look-back state of a scan of nb elements (scan_tmp_words(nb)), zeroed once.
+cudaError_t order_bricks_dev(const int32_t* table, uint32_t nb, int32_t* rank_table, int32_t* sorted_slot,
+                             int32_t* sorted_key, uint32_t* clear, int n_clear, uint32_t* zero0, uint32_t* zero1,
+                             uint32_t* tmp, cudaStream_t s, uint32_t* err);
 cudaError_t stable_sort_pairs_u32(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt, size_t n,
                                   int bits, uint32_t* tmp, cudaStream_t s, uint32_t* err);
 
