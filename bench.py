@@ -782,12 +782,16 @@ def run_gpu(args):
         m.segment(params)
     # the fit schedule chosen by the autotuner on the warmed-up map (results do not depend on it)
     tuning, tune_ms, tune_n = m.autotune(params, reps=3)
+    # one more segmentation of the same map (it does not change the map): the
+    # scratch the chosen schedule needs is sized, and its graph captured, here
+    m.segment(params)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     sampler = ClockSampler(local)
     sampler.start()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]  # where each step's GPU work begins
     launches0 = vm.launch_count()
     torch.cuda.synchronize()
     ev[0].record(stream)
@@ -796,6 +800,7 @@ def run_gpu(args):
         f = sched[args.warmup + i]
         if f == 0 and (args.warmup + i):
             m.reset()
+        evs[i].record(stream)
         m.integrate(pts[f], poses[f])
         r = m.segment(params)
         n_planes.append(len(r["planes"]))
@@ -806,6 +811,9 @@ def run_gpu(args):
     launches = vm.launch_count() - launches0
     clocks = sampler.stop()
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    # the GPU's idle time between steps: the host reads a step's result and
+    # enqueues the next step (a synchronous segment call per frame)
+    host_gap_ms = statistics.median(ev[i].elapsed_time(evs[i]) for i in range(1, args.steps)) if args.steps > 1 else 0.0
     total_ms = ev[0].elapsed_time(ev[-1])
     st = m.stats()
     m.close()
@@ -1009,6 +1017,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic (ray-cast scenes)",
         "config": bench_config(args.steps, args.warmup, ws),
         "fit_tuning": dict(tuning, autotune_candidates=tune_n, autotune_ms=round(tune_ms, 4)),
+        "host_gap_ms": round(host_gap_ms, 4),
         "p50_ms": round(statistics.median(per_step), 4),
         "p99_ms": round(sorted(per_step)[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)], 4),
         "gpu_launches": int(launches),

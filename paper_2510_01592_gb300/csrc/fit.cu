@@ -35,6 +35,7 @@ namespace {
 constexpr int kT = 256;
 constexpr int kHullCap = 2048;   // hull candidates sorted in shared memory
 constexpr int kSurvCap = 12288;  // first-filter survivors staged in shared memory
+constexpr size_t kFusedFitPoints = size_t(4) << 20;  // fits of at most this many points: per-cluster tails fused
 
 // ---------------------------------------------------------------- Philox
 __device__ __forceinline__ void philox4x64_10(const unsigned long long ctr[4], const unsigned long long key[2],
@@ -224,22 +225,17 @@ __device__ __forceinline__ bool cta_last_item(uint32_t* done, uint32_t n_items, 
 }
 
 // ---------------------------------------------------------------- stage b
-// done (may be null): per-cluster completion counters; the CTA that scores a
-// cluster's last item then runs stage c for it.
 template <int R>
 __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                               const uint32_t* __restrict__ item_off,
                                               const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
                                               int H, int T, const float4* __restrict__ hyp,
-                                              uint32_t* __restrict__ counts, uint32_t* __restrict__ queue, float eps,
-                                              const uint8_t* __restrict__ valid, FitCluster* __restrict__ cl,
-                                              uint32_t* __restrict__ done) {
+                                              uint32_t* __restrict__ counts, uint32_t* __restrict__ queue, float eps) {
     pdl_wait();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];                // T staged points
     uint32_t* red = reinterpret_cast<uint32_t*>(sp + T);  // [P][G*R]
-    __shared__ uint32_t s_item, s_last;
-    __shared__ unsigned long long wbest[kT / 32];
+    __shared__ uint32_t s_item;
     const int G = (H + R - 1) / R;                // threads per point subset
     const int P = kT / G;                         // point subsets
     const int g = threadIdx.x / G, j = threadIdx.x % G;
@@ -286,8 +282,6 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
             for (int q = 0; q < P; ++q) s += red[q * (G * R) + h];
             if (s) atomicAdd(&counts[(size_t)c * H + h], s);
         }
-        if (done && cta_last_item(done + 3 * (size_t)c, item_off[c + 1] - item_off[c], &s_last))
-            select_cta(c, pts, off, H, hyp, valid, counts, cl, wbest);
     }
 }
 
@@ -481,8 +475,24 @@ __device__ __forceinline__ void centroid_cta(uint32_t c, const uint32_t* __restr
     __syncthreads();  // shared partials reused next
 }
 
+// After an extraction item of cluster c: the CTA that completes the cluster's
+// last item computes its centroid (out of line: the item loop keeps its
+// registers).
+__device__ __noinline__ void extract_tail(uint32_t c, const uint32_t* __restrict__ off,
+                                          const uint32_t* __restrict__ item_off, int T,
+                                          const float* __restrict__ part, FitCluster* __restrict__ cl,
+                                          float* __restrict__ cen, uint32_t* __restrict__ done) {
+    __shared__ df2 sh[3 * (kT / 32)];
+    __shared__ uint32_t shn[kT / 32], s_last;
+    if (cta_last_item(done + 3 * (size_t)c + 1, item_off[c + 1] - item_off[c], &s_last))
+        centroid_cta(c, off, item_off, T, part, cl, cen, sh, shn);
+}
+
 // Inliers, centroid partials (relative to the origin) and the extreme inliers
 // along the 16 filter directions (reduced per warp, then atomicMax).
+// kTail: the CTA that completes a cluster's last item computes its centroid
+// (done: the per-cluster completion counters).
+template <bool kTail>
 __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                                 const uint32_t* __restrict__ item_off,
                                                 const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
@@ -492,8 +502,6 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
     pdl_gate();
     const uint32_t k = *kp;
     __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 4];
-    __shared__ df2 sh[3 * (kT / 32)];
-    __shared__ uint32_t shn[kT / 32], s_last;
     const uint32_t n_items = item_off[k];
     const uint32_t cpt = (uint32_t)T / kChunk;  // chunks per work item
     for (uint32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -545,8 +553,7 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
             if ((threadIdx.x & 31) == 0 && m) atomicMax(&cl[c].ext[d], m);
         }
         __syncthreads();
-        if (cta_last_item(done + 3 * (size_t)c + 1, item_off[c + 1] - item_off[c], &s_last))
-            centroid_cta(c, off, item_off, T, part, cl, cen, sh, shn);
+        if constexpr (kTail) extract_tail(c, off, item_off, T, part, cl, cen, done);
     }
 }
 
@@ -558,12 +565,25 @@ __device__ __forceinline__ void refit_cta(uint32_t c, const uint32_t* __restrict
                                           const uint32_t* __restrict__ item_off, int T, const float* __restrict__ part,
                                           const float* __restrict__ cen, FitCluster* __restrict__ cl, df2* sh);
 
+// After a filter item of cluster c: the CTA that completes the cluster's last
+// item refits its plane (out of line).
+__device__ __noinline__ void filter_tail(uint32_t c, const uint32_t* __restrict__ off,
+                                         const uint32_t* __restrict__ item_off, int T, const float* __restrict__ part,
+                                         const float* __restrict__ cen, FitCluster* __restrict__ cl,
+                                         uint32_t* __restrict__ done) {
+    __shared__ df2 sh[6 * (kT / 32)];
+    __shared__ uint32_t s_last;
+    if (cta_last_item(done + 3 * (size_t)c + 2, item_off[c + 1] - item_off[c], &s_last))
+        refit_cta(c, off, item_off, T, part, cen, cl, sh);
+}
+
 // Covariance partials about the centroid, and the 16-gon filter: inliers
 // strictly inside the polygon through the 16 extreme inliers cannot be hull
 // vertices; the others are appended to the cluster's survivor list.  Each
 // warp gathers its survivors in shared memory and reserves room in the list
 // with one atomic per kSurvBuf survivors (usually one per work item) instead
 // of one returned atomic per chunk on the loop's critical path.
+template <bool kTail>
 __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                                const uint32_t* __restrict__ item_off,
                                                const uint32_t* __restrict__ item_cl, const uint32_t* __restrict__ kp,
@@ -573,8 +593,6 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
     pdl_gate();
     const uint32_t k = *kp;
     constexpr int kSurvBuf = 128;
-    __shared__ df2 sh[6 * (kT / 32)];
-    __shared__ uint32_t s_last;
     __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 6];
     __shared__ int2 poly[kFiltDirs + 1];
     __shared__ int npoly;
@@ -650,8 +668,7 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
         }
         if (cnt) flush();
         chunks_out<6>(wp, j, part + (size_t)it * cpt * 10, 4);
-        if (cta_last_item(done + 3 * (size_t)c + 2, item_off[c + 1] - item_off[c], &s_last))
-            refit_cta(c, off, item_off, T, part, cen, cl, sh);
+        if constexpr (kTail) filter_tail(c, off, item_off, T, part, cen, cl, done);
     }
 }
 
@@ -744,6 +761,29 @@ __device__ __forceinline__ void refit_cta(uint32_t c, const uint32_t* __restrict
         }
     }
     __syncthreads();  // shared partials reused next
+}
+
+// The centroid and the refit of every cluster as kernels of their own (a CTA
+// per cluster), for fits too large for the per-cluster completion counters
+// to pay (launch_fit).
+__global__ void __launch_bounds__(kT) k_centroid(const uint32_t* __restrict__ off,
+                                                 const uint32_t* __restrict__ item_off, const uint32_t* __restrict__ kp,
+                                                 int T, const float* __restrict__ part, FitCluster* __restrict__ cl,
+                                                 float* __restrict__ cen) {
+    pdl_gate();
+    const uint32_t k = *kp;
+    __shared__ df2 sh[3 * (kT / 32)];
+    __shared__ uint32_t shn[kT / 32];
+    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) centroid_cta(c, off, item_off, T, part, cl, cen, sh, shn);
+}
+
+__global__ void __launch_bounds__(kT) k_refit(const uint32_t* __restrict__ off, const uint32_t* __restrict__ item_off,
+                                              const uint32_t* __restrict__ kp, int T, const float* __restrict__ part,
+                                              const float* __restrict__ cen, FitCluster* __restrict__ cl) {
+    pdl_gate();
+    const uint32_t k = *kp;
+    __shared__ df2 sh[6 * (kT / 32)];
+    for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) refit_cta(c, off, item_off, T, part, cen, cl, sh);
 }
 
 __device__ __forceinline__ unsigned long long xy_key(int2 p) {
@@ -1140,9 +1180,7 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
                                                    const uint32_t* __restrict__ item_cl,
                                                    const uint32_t* __restrict__ kp, int H, int T,
                                                    const float4* __restrict__ hyp, uint32_t* __restrict__ counts,
-                                                   uint32_t* __restrict__ queue, float eps,
-                                                   const uint8_t* __restrict__ valid, FitCluster* __restrict__ cl,
-                                                   uint32_t* __restrict__ done) {
+                                                   uint32_t* __restrict__ queue, float eps) {
     pdl_wait();
     const uint32_t k = *kp;
     extern __shared__ float4 sp[];  // [kT / 32][T]
@@ -1201,17 +1239,6 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
                 if (h < H && acc[r]) atomicAdd(&counts[(size_t)c * H + h], acc[r]);
             }
         }
-        if (done) {  // the warp that scores a cluster's last item runs stage c for it
-            __threadfence();
-            __syncwarp();
-            uint32_t last = 0;
-            if (lane == 0) last = atomicAdd(done + 3 * (size_t)c, 1u) + 1u == item_off[c + 1] - item_off[c];
-            if (__shfl_sync(0xffffffffu, last, 0)) {
-                __threadfence();
-                const unsigned long long best = best_key(c, lane, 32, H, valid, counts);
-                if (lane == 0) select_record(c, best, pts, off, H, hyp, cl);
-            }
-        }
     }
 }
 
@@ -1228,9 +1255,6 @@ struct ScoreArgs {
     uint32_t* queue;
     float eps;
     int grid;
-    const uint8_t* valid;     // stage c after the last item of each cluster: with done non-null
-    FitCluster* cl;
-    uint32_t* done;
 };
 
 template <int R>
@@ -1239,7 +1263,7 @@ cudaError_t launch_score(const ScoreArgs& a, cudaStream_t s) {
     const int P = kT / G;
     const size_t smem = (size_t)a.T * sizeof(float4) + (size_t)P * G * R * sizeof(uint32_t);
     launch_full(k_score<R>, dim3(a.grid), dim3(kT), smem, s, a.pts, a.off, a.item_off, a.item_cl, a.kp, a.H, a.T,
-                a.hyp, a.counts, a.queue, a.eps, a.valid, a.cl, a.done);
+                a.hyp, a.counts, a.queue, a.eps);
     return cudaGetLastError();
 }
 
@@ -1247,7 +1271,7 @@ template <int R>
 cudaError_t launch_score_warp(const ScoreArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)(kT / 32) * a.T * sizeof(float4);
     launch_full(k_score_warp<R>, dim3(a.grid), dim3(kT), smem, s, a.pts, a.off, a.item_off, a.item_cl, a.kp, a.H,
-                a.T, a.hyp, a.counts, a.queue, a.eps, a.valid, a.cl, a.done);
+                a.T, a.hyp, a.counts, a.queue, a.eps);
     return cudaGetLastError();
 }
 
@@ -1358,9 +1382,15 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     int R;
     bool warp;
     score_variant(t, H, R, warp);
+    // Small fits (a map's segmentation) compute each cluster's centroid and
+    // refit in the kernel before them, triggered by per-cluster completion
+    // counters: that removes two dependent launches.  In large batches the
+    // counters' fences wait, per work item, for the item's contended atomics,
+    // which costs more than the launches; they take the separate kernels.
+    // Results are the same.
+    uint32_t* done = fb.npts_cap <= kFusedFitPoints ? fb.done : nullptr;
     VM_STAGE_BEGIN(hk, kStScore, s);
-    const ScoreArgs sa{pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid,
-                       fb.hyp_valid, fb.cl, fb.done};
+    const ScoreArgs sa{pts, off, fb.item_off, fb.item_cl, kp, H, T, fb.hyp, fb.counts, fb.queue, p.eps, grid};
     if (warp) {
         switch (R) {
             case 1: e = launch_score_warp<1>(sa, s); break;
@@ -1383,14 +1413,24 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     // centroid runs in the extraction kernel, the refit in the filter kernel
     const unsigned cgrid = kcap < (uint32_t)sms * 8 ? kcap : (uint32_t)sms * 8;
     VM_STAGE_BEGIN(hk, kStExtract, s);
+    launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
+    count_launch(1);
     const unsigned igrid = (unsigned)sms * 8;
-    launch_full(k_extract, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier,
-                fb.part, p.eps, fb.err, fb.done, fb.cen);
-    launch_full(k_filter, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off, fb.item_cl, kp, T, fb.cl, fb.inlier,
-                fb.cen, fb.part, fb.surv, fb.done);
+    launch_full(done ? k_extract<true> : k_extract<false>, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off,
+                fb.item_cl, kp, T, fb.cl, fb.inlier, fb.part, p.eps, fb.err, done, fb.cen);
+    if (!done) {
+        launch_k(k_centroid, dim3(cgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cl, fb.cen);
+        count_launch(1);
+    }
+    launch_full(done ? k_filter<true> : k_filter<false>, dim3(igrid), dim3(kT), 0, s, pts, off, fb.item_off,
+                fb.item_cl, kp, T, fb.cl, fb.inlier, fb.cen, fb.part, fb.surv, done);
     VM_STAGE_END(hk, kStExtract, s);
     count_launch(2);
     VM_STAGE_BEGIN(hk, kStHull, s);
+    if (!done) {
+        launch_k(k_refit, dim3(cgrid), dim3(kT), 0, s, off, fb.item_off, kp, T, fb.part, fb.cen, fb.cl);
+        count_launch(1);
+    }
     launch_k(k_hull, dim3(cgrid), dim3(kT), fit_hull_smem(), s, off, kp, fb.cl, fb.surv, fb.hull, fb.hull_cnt, fb.err,
              fb.queue + 3);
     VM_STAGE_END(hk, kStHull, s);
@@ -1542,8 +1582,7 @@ extern "C" vm_status vm_ransac_static(const float* xyz, const uint32_t* off, con
     bool warp;
     score_variant(tc, H, R, warp);
     const int grid = sms * t.ctas_per_sm;
-    const ScoreArgs sa{xyz, off, item_off, nullptr, kdev, H, t.tile, hyp, counts, queue, params->eps, grid,
-                       valid, cl, nullptr};
+    const ScoreArgs sa{xyz, off, item_off, nullptr, kdev, H, t.tile, hyp, counts, queue, params->eps, grid};
     switch (R) {
         case 1: e = launch_score<1>(sa, s); break;
         case 2: e = launch_score<2>(sa, s); break;
