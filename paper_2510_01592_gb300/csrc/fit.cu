@@ -63,6 +63,21 @@ __device__ __forceinline__ float plane_dist(float nx, float ny, float nz, float 
     return fabsf(__fmaf_rn(nz, pz, __fmaf_rn(ny, py, __fmaf_rn(nx, px, d))));
 }
 
+// Stage b for one point against a thread's R hypotheses: acc[r] += 1 when
+// |n_r . p + d_r| <= eps (the fma chain of plane_dist).  The comparison is a
+// set to all-ones / zero subtracted from the count: two instructions a test
+// after the three fused multiply-adds.
+template <int R>
+__device__ __forceinline__ void count_point(const float4 (&pl)[R], float4 p, float eps, uint32_t (&acc)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float dist = plane_dist(pl[r].x, pl[r].y, pl[r].z, pl[r].w, p.x, p.y, p.z);
+        uint32_t t;
+        asm("set.le.u32.f32 %0, %1, %2;" : "=r"(t) : "f"(dist), "f"(eps));
+        acc[r] -= t;
+    }
+}
+
 // The cluster of work item it: one load from the item -> cluster table k_hyp
 // writes (item_cl), else a binary search over the item offsets.
 __device__ __forceinline__ uint32_t find_cluster(const uint32_t* __restrict__ item_cl,
@@ -267,12 +282,7 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0;
         if (active) {
-            for (int q = g; q < cnt; q += P) {
-                const float4 p = sp[q];
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    acc[r] += plane_dist(pl[r].x, pl[r].y, pl[r].z, pl[r].w, p.x, p.y, p.z) <= eps;
-            }
+            for (int q = g; q < cnt; q += P) count_point<R>(pl, sp[q], eps, acc);
 #pragma unroll
             for (int r = 0; r < R; ++r) red[g * (G * R) + j * R + r] = acc[r];
         }
@@ -1216,14 +1226,8 @@ __global__ void __launch_bounds__(kT) k_score_warp(const float* __restrict__ pts
         uint32_t acc[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] = 0;
-        if (active) {
-            for (int q = g; q < cnt; q += P) {
-                const float4 p = wp[q];
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    acc[r] += plane_dist(pl[r].x, pl[r].y, pl[r].z, pl[r].w, p.x, p.y, p.z) <= eps;
-            }
-        }
+        if (active)
+            for (int q = g; q < cnt; q += P) count_point<R>(pl, wp[q], eps, acc);
         for (int q = 1; q < P; ++q) {
             const int src = j + q * G;  // < 32 since P * G <= 32
 #pragma unroll
