@@ -313,7 +313,7 @@ uint64_t map_footprint(const vm_map_params& p, const vm_segment_params& sp) {
     const uint64_t kcap = nv / mc > 256 ? nv / mc : 256;
     const uint64_t hcap = 65536 + kcap * 16;
     const uint64_t out = 256 + kcap * sizeof(vm_plane) + hcap * 20 + 1024;
-    const uint64_t stage = 16ull << 20;  // host-input staging for frames of up to ~1.4 M points
+    const uint64_t stage = 22ull << 20;  // host-input staging and deferred indices for frames of up to ~1.4 M points
     return pool + bricks + (uint64_t)dry.off * 5 / 4 + out + stage;
 }
 
@@ -863,6 +863,7 @@ vm_status vm_destroy(vm_map* m) {
     if (m->stream) cudaStreamSynchronize(m->stream);
     release(m->pool);
     release(m->stage);
+    release(m->deferred);
     release(m->brick_mem);
     release(m->vox_mem);
     release(m->round_mem);
@@ -902,8 +903,10 @@ vm_status vm_integrate_ex(vm_map* m, const float* xyz, uint32_t n, const float p
         VM_CUDA(launch_clear(d, n, P, m->g, m->brick_table, m->S, m->C, m->mark, m->ctr, m->capacity, m->stream));
         VM_STAGE_END(hk, kStClear, m->stream);
     }
+    VM_TRY(ensure(m->deferred, (size_t)n * sizeof(uint32_t)));
     VM_STAGE_BEGIN(hk, kStIntegrate, m->stream);
-    VM_CUDA(launch_integrate(d, n, P, m->g, m->brick_table, m->slot_key, m->S, m->C, m->ctr, m->capacity, m->stream));
+    VM_CUDA(launch_integrate(d, n, P, m->g, m->brick_table, m->slot_key, m->S, m->C,
+                             static_cast<uint32_t*>(m->deferred.p), m->ctr, m->capacity, m->stream));
     VM_STAGE_END(hk, kStIntegrate, m->stream);
     return VM_OK;
 }

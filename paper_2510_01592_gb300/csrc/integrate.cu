@@ -13,14 +13,14 @@
 // robot): the window moves in whole bricks (launch_scroll), so a voxel keeps
 // its key, its points and its exact sums for as long as it stays inside.
 //
-// Two launches per frame, both reading the frame's points (the second read is
-// served from L2):
-//  1. k_claim: a point whose brick is unallocated claims it with a CAS on the
-//     table entry; the winner takes a pool slot.  No thread ever waits on
-//     another.
-//  2. k_accum: each warp reduces runs of consecutive points that fall in the
-//     same voxel (a segmented shuffle scan) and the last lane of each run
-//     issues one 64-bit atomic per axis plus one 32-bit count atomic.
+// One pass over a frame's points (k_accum): a point whose brick is
+// unallocated claims it with a CAS on the table entry (the winner takes a
+// pool slot); each warp groups its points by voxel (a match over the voxel
+// key, wherever the points sit in the warp), reduces each group's integer
+// sums, and the group's lowest lane issues one 64-bit atomic per axis plus
+// one 32-bit count atomic.  The few points whose brick another thread was
+// claiming at that moment are deferred to a second, small kernel
+// (k_accum_deferred), so no thread ever waits on another.
 #include "vm_internal.cuh"
 
 namespace vmx {
@@ -65,30 +65,54 @@ __device__ __forceinline__ Keyed key_point(const float* __restrict__ xyz, uint32
     return k;
 }
 
-__global__ void __launch_bounds__(kThreads) k_claim(const float* __restrict__ xyz, uint32_t n, Pose P, Grid g,
-                                                   int32_t* __restrict__ table, int32_t* __restrict__ slot_key,
-                                                   MapCounters* __restrict__ ctr, uint32_t capacity) {
-    pdl_gate();
-    for (uint32_t i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
-        Keyed k = key_point(xyz, i, P, g);
-        if (!k.ok) continue;
-        if (table[k.brick] != -1) continue;  // allocated, being claimed, or refused
-        if (atomicCAS(&table[k.brick], -1, -2) != -1) continue;
-        const uint32_t slot = atomicAdd(&ctr->n_bricks, 1u);
-        if (slot < capacity) {
-            slot_key[slot] = (int32_t)k.brick;
-            table[k.brick] = (int32_t)slot;
-        } else {
-            table[k.brick] = -3;  // pool full: the brick's points are dropped and counted
-            atomicOr(&ctr->err, kErrCapacity);
-        }
+// Adds a warp's points to their voxels: lanes with equal keys (kNone: no
+// point) form a group wherever they sit in the warp (a raster camera gives
+// runs of consecutive lanes, a spinning LiDAR's beams interleave); each
+// group's integer sums are reduced and its lowest lane issues the group's
+// atomics (64-bit sums sign-extended: a group's sum is negative when its
+// points lie a quantum below the window's anchor).
+__device__ __forceinline__ void accumulate_warp(uint32_t key, int32_t v0, int32_t v1, int32_t v2,
+                                                unsigned long long* __restrict__ S, uint32_t* __restrict__ C) {
+    if (!__any_sync(0xffffffffu, key != kNone)) return;  // nothing in this warp lands in the map
+    const uint32_t grp = __match_any_sync(0xffffffffu, key);
+    const int32_t s0 = __reduce_add_sync(grp, v0), s1 = __reduce_add_sync(grp, v1), s2 = __reduce_add_sync(grp, v2);
+    if (key != kNone && (int)(threadIdx.x & 31) == __ffs(grp) - 1) {
+        const uint32_t slot = key / kBrickVox, l = key % kBrickVox;
+        unsigned long long* s = S + (size_t)slot * 3 * kBrickVox + l;
+        atomicAdd(s, (unsigned long long)(long long)s0);
+        atomicAdd(s + kBrickVox, (unsigned long long)(long long)s1);
+        atomicAdd(s + 2 * kBrickVox, (unsigned long long)(long long)s2);
+        atomicAdd(C + key, (uint32_t)__popc(grp));
     }
 }
 
+// Per-warp totals of accepted / dropped points into the map's counters.
+__device__ __forceinline__ void count_points(uint32_t n_ok, uint32_t n_bad, uint32_t n_full,
+                                             MapCounters* __restrict__ ctr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_ok += __shfl_xor_sync(0xffffffffu, n_ok, o);
+        n_bad += __shfl_xor_sync(0xffffffffu, n_bad, o);
+        n_full += __shfl_xor_sync(0xffffffffu, n_full, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n_ok) atomicAdd(&ctr->integrated, (unsigned long long)n_ok);
+        if (n_bad) atomicAdd(&ctr->dropped, (unsigned long long)n_bad);
+        if (n_full) atomicAdd(&ctr->no_capacity, (unsigned long long)n_full);
+    }
+}
+
+// One pass over the frame's points: a point whose brick is unallocated
+// claims it (a CAS on the table entry from -1 to -2; the winner takes a pool
+// slot and publishes it), a point whose brick has a slot is accumulated, and
+// a point whose brick another thread is claiming right now is put on the
+// deferred list (one atomic; no thread ever waits on another) for
+// k_accum_deferred, after which every claim is published.
 __global__ void __launch_bounds__(kThreads) k_accum(const float* __restrict__ xyz, uint32_t n, Pose P, Grid g,
-                                                   const int32_t* __restrict__ table,
+                                                   int32_t* __restrict__ table, int32_t* __restrict__ slot_key,
                                                    unsigned long long* __restrict__ S, uint32_t* __restrict__ C,
-                                                   MapCounters* __restrict__ ctr) {
+                                                   uint32_t* __restrict__ deferred, MapCounters* __restrict__ ctr,
+                                                   uint32_t capacity) {
     pdl_gate();
     const int lane = threadIdx.x & 31;
     const uint32_t warp_global = (blockIdx.x * kThreads + threadIdx.x) >> 5;
@@ -101,11 +125,29 @@ __global__ void __launch_bounds__(kThreads) k_accum(const float* __restrict__ xy
         if (i < n) {
             Keyed k = key_point(xyz, i, P, g);
             if (k.ok) {
-                const int32_t slot = table[k.brick];
+                int32_t slot = table[k.brick];
+                if (slot == -1) {  // unallocated: claim it, or find another thread claiming it
+                    if (atomicCAS(&table[k.brick], -1, -2) == -1) {
+                        const uint32_t sl = atomicAdd(&ctr->n_bricks, 1u);
+                        if (sl < capacity) {
+                            slot_key[sl] = (int32_t)k.brick;
+                            table[k.brick] = (int32_t)sl;
+                            slot = (int32_t)sl;
+                        } else {
+                            table[k.brick] = -3;  // pool full: the brick's points are dropped and counted
+                            atomicOr(&ctr->err, kErrCapacity);
+                            slot = -3;
+                        }
+                    } else {
+                        slot = -2;
+                    }
+                }
                 if (slot >= 0) {
                     key = (uint32_t)slot * kBrickVox + k.local;
                     v0 = k.F[0]; v1 = k.F[1]; v2 = k.F[2];
                     ++n_ok;
+                } else if (slot == -2) {
+                    deferred[atomicAdd(&ctr->n_deferred, 1u)] = i;
                 } else {
                     ++n_full;
                 }
@@ -113,41 +155,50 @@ __global__ void __launch_bounds__(kThreads) k_accum(const float* __restrict__ xy
                 ++n_bad;
             }
         }
-        // segmented inclusive scan over runs of equal keys in consecutive lanes
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-        const bool head = (lane == 0) || (key != prev);
-        const uint32_t heads = __ballot_sync(0xffffffffu, head);
-        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t t0 = __shfl_up_sync(0xffffffffu, v0, o);
-            const int32_t t1 = __shfl_up_sync(0xffffffffu, v1, o);
-            const int32_t t2 = __shfl_up_sync(0xffffffffu, v2, o);
-            if (lane - o >= start) { v0 += t0; v1 += t1; v2 += t2; }
-        }
-        const bool tail = (lane == 31) || ((heads >> (lane + 1)) & 1u);
-        if (tail && key != kNone) {
-            const uint32_t slot = key / kBrickVox, l = key % kBrickVox;
-            unsigned long long* s = S + (size_t)slot * 3 * kBrickVox + l;
-            // sign-extended: a run sum is negative when its points lie a
-            // quantum below the window's anchor (reading of the scrolled sums)
-            atomicAdd(s, (unsigned long long)(long long)v0);
-            atomicAdd(s + kBrickVox, (unsigned long long)(long long)v1);
-            atomicAdd(s + 2 * kBrickVox, (unsigned long long)(long long)v2);
-            atomicAdd(C + key, (uint32_t)(lane - start + 1));
-        }
+        accumulate_warp(key, v0, v1, v2, S, C);
     }
-    // per-warp totals of accepted / dropped points
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        n_ok += __shfl_xor_sync(0xffffffffu, n_ok, o);
-        n_bad += __shfl_xor_sync(0xffffffffu, n_bad, o);
-        n_full += __shfl_xor_sync(0xffffffffu, n_full, o);
+    count_points(n_ok, n_bad, n_full, ctr);
+}
+
+// The deferred points, their bricks' claims now published; the last CTA to
+// finish clears the list for the next frame.
+__global__ void __launch_bounds__(kThreads) k_accum_deferred(const float* __restrict__ xyz, Pose P, Grid g,
+                                                            const int32_t* __restrict__ table,
+                                                            unsigned long long* __restrict__ S,
+                                                            uint32_t* __restrict__ C,
+                                                            const uint32_t* __restrict__ deferred,
+                                                            MapCounters* __restrict__ ctr) {
+    pdl_gate();
+    __shared__ uint32_t s_last;
+    const uint32_t nd = ctr->n_deferred;
+    const uint32_t warp_global = (blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const uint32_t n_warps = (gridDim.x * kThreads) >> 5;
+    uint32_t n_ok = 0, n_full = 0;
+    for (uint32_t base = warp_global * 32u; base < nd; base += n_warps * 32u) {
+        const uint32_t j = base + (threadIdx.x & 31);
+        uint32_t key = kNone;
+        int32_t v0 = 0, v1 = 0, v2 = 0;
+        if (j < nd) {
+            const Keyed k = key_point(xyz, deferred[j], P, g);
+            const int32_t slot = table[k.brick];
+            if (slot >= 0) {
+                key = (uint32_t)slot * kBrickVox + k.local;
+                v0 = k.F[0]; v1 = k.F[1]; v2 = k.F[2];
+                ++n_ok;
+            } else {
+                ++n_full;
+            }
+        }
+        accumulate_warp(key, v0, v1, v2, S, C);
     }
-    if (lane == 0) {
-        if (n_ok) atomicAdd(&ctr->integrated, (unsigned long long)n_ok);
-        if (n_bad) atomicAdd(&ctr->dropped, (unsigned long long)n_bad);
-        if (n_full) atomicAdd(&ctr->no_capacity, (unsigned long long)n_full);
+    count_points(n_ok, 0, n_full, ctr);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctr->deferred_done, 1u) + 1u == gridDim.x;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        ctr->n_deferred = 0;
+        ctr->deferred_done = 0;
     }
 }
 
@@ -461,16 +512,18 @@ cudaError_t launch_clear(const float* xyz, uint32_t n, const Pose& pose, const G
 }
 
 cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, int32_t* brick_table,
-                             int32_t* slot_key, unsigned long long* S, uint32_t* C, MapCounters* ctr,
-                             uint32_t capacity, cudaStream_t s) {
+                             int32_t* slot_key, unsigned long long* S, uint32_t* C, uint32_t* deferred,
+                             MapCounters* ctr, uint32_t capacity, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint32_t want = (n + kThreads - 1) / kThreads;
     const uint32_t grid = want < (uint32_t)(sms * 8) ? want : (uint32_t)(sms * 8);
-    launch_k(k_claim, dim3(grid), dim3(kThreads), 0, s, xyz, n, pose, g, brick_table, slot_key, ctr, capacity);
-    launch_k(k_accum, dim3(grid), dim3(kThreads), 0, s, xyz, n, pose, g, brick_table, S, C, ctr);
+    launch_k(k_accum, dim3(grid), dim3(kThreads), 0, s, xyz, n, pose, g, brick_table, slot_key, S, C, deferred, ctr,
+             capacity);
+    launch_k(k_accum_deferred, dim3(grid < (uint32_t)sms ? grid : (uint32_t)sms), dim3(kThreads), 0, s, xyz, pose, g,
+             brick_table, S, C, deferred, ctr);
     count_launch(2);
     return cudaGetLastError();
 }

@@ -141,6 +141,7 @@ struct vm_map {
     float* po_dev = nullptr;         // position origin of the window, read by the segmentation
     vmx::DevBuf pool;
     vmx::DevBuf stage;             // host points staged on the device
+    vmx::DevBuf deferred;          // point indices deferred by the integration pass
     // segmentation
     vmx::DevBuf brick_mem;         // brick-level arrays (fixed size)
     vmx::DevBuf vox_mem;           // rank-dense voxel arrays (grow with the brick count)

@@ -105,6 +105,8 @@ struct MapCounters {
     uint32_t err;        // error bits
     unsigned long long cleared;  // voxels cleared by ray casting (Eq. 2)
     unsigned long long evicted;  // occupied voxels evicted by scrolling the window
+    uint32_t n_deferred;         // points of the frame waiting for their brick's claim (k_accum_deferred)
+    uint32_t deferred_done;      // CTAs of k_accum_deferred finished
 };
 
 // Counters produced by one segmentation, read back by the host.
@@ -318,9 +320,11 @@ size_t scroll_tmp_words(uint32_t capacity);
 cudaError_t launch_scroll(const Grid& g, const Grid& g2, const int32_t shift[3], const float po2[3],
                           int32_t* brick_table, uint32_t nb_total, int32_t* slot_key, unsigned long long* S,
                           uint32_t* C, MapCounters* ctr, uint32_t capacity, uint32_t* tmp, cudaStream_t s);
+// deferred: room for n point indices (the frame's points whose brick another
+// thread was claiming); the map counters' deferred words are zero between calls.
 cudaError_t launch_integrate(const float* xyz, uint32_t n, const Pose& pose, const Grid& g, int32_t* brick_table,
-                             int32_t* slot_key, unsigned long long* S, uint32_t* C, MapCounters* ctr,
-                             uint32_t capacity, cudaStream_t s);
+                             int32_t* slot_key, unsigned long long* S, uint32_t* C, uint32_t* deferred,
+                             MapCounters* ctr, uint32_t capacity, cudaStream_t s);
 // Voxel information clearing (Sec. III.B, Eq. 2): marks every occupied voxel
 // that a point's ray from the sensor passes through before the point's own
 // voxel (mark: one bit per voxel slot, capacity * 16 words, zero between
