@@ -470,6 +470,13 @@ uint64_t vm_launch_count(void);
  * re-allocates and re-captures; both should stay flat in a steady state). */
 uint64_t vm_capture_count(void);
 uint64_t vm_allocation_count(void);
+/* Shape of the map's captured segmentation graph (zeros before the first
+ * graph segmentation, or for a map created with VM_MAP_EAGER): its kernel and
+ * memcpy nodes, its dependency edges, and how many of those edges are
+ * programmatic -- kernel-to-kernel dependencies that, like the programmatic
+ * stream launches they were captured from, let the next kernel launch before
+ * the one it depends on has finished.  Any pointer may be NULL. */
+vm_status vm_graph_shape(vm_map* map, uint32_t* nodes, uint32_t* edges, uint32_t* programmatic);
 
 /* Thread-local message describing the last error of this thread. */
 const char* vm_last_error(void);

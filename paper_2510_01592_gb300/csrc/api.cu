@@ -465,6 +465,28 @@ cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk
     return cudaGetLastError();
 }
 
+// Nodes, edges and programmatic edges (a kernel launched with programmatic
+// stream serialization keeps that dependency type when captured) of a graph.
+static void graph_shape(cudaGraph_t graph, uint32_t& nodes, uint32_t& edges, uint32_t& prog) {
+    nodes = edges = prog = 0;
+    size_t nn = 0, ne = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess ||
+        cudaGraphGetEdges(graph, nullptr, nullptr, nullptr, &ne) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    nodes = (uint32_t)nn;
+    edges = (uint32_t)ne;
+    if (!ne) return;
+    std::vector<cudaGraphNode_t> from(ne), to(ne);
+    std::vector<cudaGraphEdgeData> data(ne);
+    if (cudaGraphGetEdges(graph, from.data(), to.data(), data.data(), &ne) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    for (size_t i = 0; i < ne; ++i) prog += data[i].type == cudaGraphDependencyTypeProgrammatic;
+}
+
 vm_status capture_segment(vm_map* m, const vm_segment_params& p) {
     if (m->gexec) {
         cudaGraphExecDestroy(m->gexec);
@@ -482,6 +504,7 @@ vm_status capture_segment(vm_map* m, const vm_segment_params& p) {
         return cuda_status(e, "segment capture");
     }
     if (e2 != cudaSuccess) return cuda_status(e2, "cudaStreamEndCapture");
+    graph_shape(graph, m->gnodes, m->gedges, m->gprog);
     e = cudaGraphInstantiate(&m->gexec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
@@ -1222,6 +1245,14 @@ vm_status vm_stage_times(vm_map* map, double* ms, uint64_t* calls, uint32_t cap,
 const char* vm_stage_name(uint32_t stage) { return stage < (uint32_t)kNumStages ? kStageNames[stage] : ""; }
 
 uint64_t vm_launch_count(void) { return g_launches.load(); }
+
+vm_status vm_graph_shape(vm_map* m, uint32_t* nodes, uint32_t* edges, uint32_t* programmatic) {
+    VM_TRY(check_map(m));
+    if (nodes) *nodes = m->gexec ? m->gnodes : 0;
+    if (edges) *edges = m->gexec ? m->gedges : 0;
+    if (programmatic) *programmatic = m->gexec ? m->gprog : 0;
+    return VM_OK;
+}
 uint64_t vm_capture_count(void) { return capture_total(); }
 uint64_t vm_allocation_count(void) { return alloc_total(); }
 

@@ -843,6 +843,7 @@ __device__ __forceinline__ bool jarvis_better(int2 cur, int2 a, bool a_ok, int2 
 // it lies in the convex hull of the polygon's vertices and is not an extreme
 // point); the directions only decide how much it removes.
 constexpr int kHullDirs = 128;
+constexpr int kSmallHull = kT;  // candidates ranked and tested in parallel, one a thread
 
 // Per cluster hull of the first filter's survivors: (1) extreme survivors along
 // kHullDirs directions; (2) survivors strictly inside the polygon they span
@@ -867,7 +868,9 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
     int2* ssv = reinterpret_cast<int2*>(st_hi + kHullCap);  // kSurvCap staged survivors
     __shared__ uint32_t wsum[kT / 32];
     __shared__ int s_klo, s_khi, s_m, s_cnt;
-    __shared__ int2 poly[kHullDirs + 1];
+    __shared__ int2 poly[kHullDirs + 1];   // the extreme point of each direction
+    __shared__ int2 hpoly[kHullDirs + 1];  // the filter polygon
+    __shared__ long long warea[kT / 32];
     __shared__ int2 sdir[kHullDirs];
     __shared__ int2 jcand[kT];
     __shared__ int jok[kT];
@@ -890,19 +893,27 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
             sv = ssv;
             __syncthreads();
         }
-        // (1) extreme points along kHullDirs directions: warp w takes 16 of them
+        // (1) extreme points along kHullDirs directions, warp w taking 16 of
+        // them.  The projections are FP32: any closed polygon through input
+        // points serves the filter below (which is exact), so an extreme point
+        // only has to be an input point, not the exact maximiser.
         {
             constexpr int kPer = kHullDirs / (kT / 32);
-            long long bv[kPer];
+            float dxq[kPer], dyq[kPer], bv[kPer];
             int bi[kPer];
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) { bv[q] = LLONG_MIN; bi[q] = -1; }
+            for (int q = 0; q < kPer; ++q) {
+                dxq[q] = (float)sdir[kPer * w + q].x;
+                dyq[q] = (float)sdir[kPer * w + q].y;
+                bv[q] = -INFINITY;
+                bi[q] = -1;
+            }
             for (int i = lane; i < s; i += 32) {
                 const int2 p = sv[i];
+                const float fx = (float)p.x, fy = (float)p.y;
 #pragma unroll
                 for (int q = 0; q < kPer; ++q) {
-                    const int2 dv = sdir[kPer * w + q];
-                    const long long v = (long long)dv.x * p.x + (long long)dv.y * p.y;
+                    const float v = fmaf(dxq[q], fx, dyq[q] * fy);
                     if (v > bv[q]) { bv[q] = v; bi[q] = i; }
                 }
             }
@@ -910,29 +921,53 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
             for (int q = 0; q < kPer; ++q) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const long long ov = __shfl_xor_sync(0xffffffffu, bv[q], o);
+                    const float ov = __shfl_xor_sync(0xffffffffu, bv[q], o);
                     const int oi = __shfl_xor_sync(0xffffffffu, bi[q], o);
-                    if (ov > bv[q] || (ov == bv[q] && oi < bi[q])) { bv[q] = ov; bi[q] = oi; }
+                    if (ov > bv[q] || (ov == bv[q] && oi >= 0 && (bi[q] < 0 || oi < bi[q]))) { bv[q] = ov; bi[q] = oi; }
                 }
                 if (lane == 0) poly[kPer * w + q] = (bi[q] >= 0) ? sv[bi[q]] : make_int2(INT_MIN, INT_MIN);
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {  // polygon through the extremes, consecutive duplicates removed
-            int m = 0;
-            for (int j = 0; j < kHullDirs; ++j) {
-                const int2 p = poly[j];
-                if (p.x == INT_MIN && p.y == INT_MIN) continue;
-                if (m && poly[m - 1].x == p.x && poly[m - 1].y == p.y) continue;
-                poly[m++] = p;
+        // The polygon through the extremes, consecutive duplicates removed (and
+        // the last vertex when it repeats the first), in parallel: a direction's
+        // extreme is kept unless it repeats the previous direction's; a ballot
+        // places the kept ones.  Every direction has an extreme when s > 0.
+        {
+            const bool valid = s > 0 && threadIdx.x < kHullDirs;
+            int2 p = make_int2(0, 0);
+            bool keep = false;
+            if (valid) {
+                p = poly[threadIdx.x];
+                const int2 q = poly[threadIdx.x ? threadIdx.x - 1 : 0];
+                keep = threadIdx.x == 0 || p.x != q.x || p.y != q.y;
             }
-            if (m > 1 && poly[m - 1].x == poly[0].x && poly[m - 1].y == poly[0].y) --m;
-            long long area2 = 0;
-            for (int i = 0; i < m; ++i) {
-                const int2 a = poly[i], b = poly[(i + 1) % m];
-                area2 += (long long)a.x * b.y - (long long)a.y * b.x;
+            const uint32_t b = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) wsum[w] = __popc(b);
+            __syncthreads();
+            uint32_t pos = __popc(b & ((1u << lane) - 1u)), m0 = 0;
+            for (int q = 0; q < kT / 32; ++q) {
+                pos += q < w ? wsum[q] : 0u;
+                m0 += wsum[q];
             }
-            s_m = (m >= 3 && area2 > 0) ? m : 0;
+            if (keep) hpoly[pos] = p;
+            __syncthreads();
+            if (m0 > 1 && hpoly[m0 - 1].x == hpoly[0].x && hpoly[m0 - 1].y == hpoly[0].y) --m0;
+            // twice the signed area: a degenerate (zero-area) polygon filters nothing
+            long long a2 = 0;
+            if (threadIdx.x < m0) {
+                const int2 a = hpoly[threadIdx.x], bb = hpoly[threadIdx.x + 1 < m0 ? threadIdx.x + 1 : 0];
+                a2 = (long long)a.x * bb.y - (long long)a.y * bb.x;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            if (lane == 0) warea[w] = a2;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                long long area2 = 0;
+                for (int q = 0; q < kT / 32; ++q) area2 += warea[q];
+                s_m = (m0 >= 3 && area2 > 0) ? (int)m0 : 0;
+            }
         }
         __syncthreads();
         const int m = s_m;
@@ -945,7 +980,7 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
                 p = sv[i];
                 keep = (m == 0);
                 for (int e = 0; e < m; ++e) {
-                    if (cross3(poly[e], poly[e + 1 < m ? e + 1 : 0], p) <= 0) { keep = true; break; }
+                    if (cross3(hpoly[e], hpoly[e + 1 < m ? e + 1 : 0], p) <= 0) { keep = true; break; }
                 }
             }
             const uint32_t b = __ballot_sync(0xffffffffu, keep);
@@ -956,7 +991,86 @@ __global__ void __launch_bounds__(kT) k_hull(const uint32_t* __restrict__ off, c
         }
         __syncthreads();
         const int s2 = s_cnt;
-        if (s2 <= kHullCap) {
+        if (s2 <= kSmallHull) {
+            // (3') at most kT candidates: rank sort with duplicates removed --
+            // a candidate is kept if no earlier one has its key, and lands at
+            // the number of kept keys below it
+            const int i = threadIdx.x;
+            unsigned long long key = 0;
+            bool first = false;
+            if (i < s2) {
+                key = sk[i];
+                first = true;
+                for (int j = 0; j < i; ++j) first &= sk[j] != key;
+            }
+            st_lo[i] = first;  // kT flags
+            __syncthreads();
+            int rank = 0;
+            if (first)
+                for (int j = 0; j < s2; ++j) rank += (st_lo[j] != 0u) & (sk[j] < key);
+            const uint32_t b = __ballot_sync(0xffffffffu, first);
+            if (lane == 0) wsum[w] = __popc(b);
+            __syncthreads();
+            int u = 0;
+            for (int q = 0; q < kT / 32; ++q) u += (int)wsum[q];
+            if (first) uq[rank] = key;
+            __syncthreads();
+            if (u < 3) {
+                if (i < u) out[i] = key_xy(uq[i]);
+                if (i == 0) hull_cnt[c] = (uint32_t)u;
+            } else {
+                // (4') Andrew's chains by a test per candidate: in the sorted
+                // order, P_i is a vertex of the lower chain iff it is an end or
+                // cross(P_j, P_i, P_k) > 0 for every j < i < k -- the directions
+                // P_i - P_j lie in a half-plane (x >= 0, x = 0 only upwards) where
+                // cross orders them by angle, so it is enough that the most
+                // counter-clockwise of them turns left into the most clockwise of
+                // the P_k - P_i; the upper chain is the same over the reversed
+                // order.  Collinear points fail (cross = 0), as in the chains.
+                bool lo = false, hi = false;
+                if (i < u) {
+                    const int2 P = key_xy(uq[i]);
+                    if (i == 0 || i == u - 1) {
+                        lo = hi = true;
+                    } else {
+                        int2 D = make_int2(0, 0), E = make_int2(0, 0), D2 = make_int2(0, 0), E2 = make_int2(0, 0);
+                        for (int j = 0; j < i; ++j) {  // lower: P - P_j (most ccw); upper: P_j - P (most cw)
+                            const int2 Q = key_xy(uq[j]);
+                            const int2 d = make_int2(P.x - Q.x, P.y - Q.y), e2 = make_int2(Q.x - P.x, Q.y - P.y);
+                            if (j == 0 || cross3(make_int2(0, 0), D, d) > 0) D = d;
+                            if (j == 0 || cross3(make_int2(0, 0), e2, E2) > 0) E2 = e2;
+                        }
+                        for (int k2 = i + 1; k2 < u; ++k2) {  // lower: P_k - P (most cw); upper: P - P_k (most ccw)
+                            const int2 Q = key_xy(uq[k2]);
+                            const int2 e = make_int2(Q.x - P.x, Q.y - P.y), d2 = make_int2(P.x - Q.x, P.y - Q.y);
+                            if (k2 == i + 1 || cross3(make_int2(0, 0), e, E) > 0) E = e;
+                            if (k2 == i + 1 || cross3(make_int2(0, 0), D2, d2) > 0) D2 = d2;
+                        }
+                        lo = cross3(make_int2(0, 0), D, E) > 0;
+                        hi = cross3(make_int2(0, 0), D2, E2) > 0;
+                    }
+                    lo &= i < u - 1;  // the lower chain's last point opens the upper chain
+                    hi &= i > 0;      // and the upper chain's last point is the first of the lower
+                }
+                // lower vertices in increasing order, then upper vertices in decreasing order
+                const uint32_t bl = __ballot_sync(0xffffffffu, lo), bh = __ballot_sync(0xffffffffu, hi);
+                if (lane == 0) {
+                    wsum[w] = __popc(bl);
+                    st_hi[w] = __popc(bh);
+                }
+                __syncthreads();
+                int klo = 0, khi = 0, plo = __popc(bl & ((1u << lane) - 1u)), phi = __popc(bh >> lane) - (hi ? 1 : 0);
+                for (int q = 0; q < kT / 32; ++q) {
+                    klo += (int)wsum[q];
+                    khi += (int)st_hi[q];
+                    plo += q < w ? (int)wsum[q] : 0;
+                    phi += q > w ? (int)st_hi[q] : 0;
+                }
+                if (lo) out[plo] = key_xy(uq[i]);
+                if (hi) out[klo + phi] = key_xy(uq[i]);
+                if (i == 0) hull_cnt[c] = (uint32_t)(klo + khi);
+            }
+        } else if (s2 <= kHullCap) {
             int n2 = 1;
             while (n2 < s2) n2 <<= 1;
             for (int i = s2 + threadIdx.x; i < n2; i += kT) sk[i] = ~0ull;

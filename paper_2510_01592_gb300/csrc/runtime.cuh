@@ -171,6 +171,7 @@ struct vm_map {
     uint64_t ggen = ~0ull;
     vm_segment_params gprm{};
     unsigned long long glaunches = 0;
+    uint32_t gnodes = 0, gedges = 0, gprog = 0;  // the captured graph's nodes, edges and programmatic edges
     // captured front half (brick order .. cluster points), for batched serving
     cudaGraphExec_t fexec = nullptr;
     uint64_t fgen = ~0ull;

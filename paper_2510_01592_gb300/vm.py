@@ -147,6 +147,7 @@ _SIGS = {
     "vm_stage_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint32, C.POINTER(C.c_uint32)]),
     "vm_stage_name": (C.c_char_p, [C.c_uint32]),
     "vm_launch_count": (C.c_uint64, []),
+    "vm_graph_shape": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]),
     "vm_capture_count": (C.c_uint64, []),
     "vm_allocation_count": (C.c_uint64, []),
     "vm_last_error": (C.c_char_p, []),
@@ -354,6 +355,12 @@ class VoxelMap:
         if st not in (VM_OK, VM_ERR_CAPACITY):
             _check(st)
         return {f: getattr(s, f) for f, _ in vm_stats._fields_} | {"status": st}
+
+    def graph_shape(self):
+        """Nodes, edges and programmatic edges of the captured segmentation graph."""
+        n, e, p = C.c_uint32(), C.c_uint32(), C.c_uint32()
+        _check(load().vm_graph_shape(self._h, C.byref(n), C.byref(e), C.byref(p)))
+        return {"nodes": n.value, "edges": e.value, "programmatic": p.value}
 
     def stage_times(self):
         """{stage: (ms, calls)} accumulated since the previous call."""

@@ -125,6 +125,7 @@ def test_parameter_and_handle_checks_need_no_gpu():
     assert L.vm_scroll_target(None, ctr, sh) == vm.VM_ERR_INVALID_ARG
     assert L.vm_get_window(None, sh, ctr) == vm.VM_ERR_INVALID_ARG
     assert L.vm_integrate(None, None, 0, None, 0) == vm.VM_ERR_INVALID_ARG
+    assert L.vm_graph_shape(None, None, None, None) == vm.VM_ERR_INVALID_ARG
     assert L.vm_destroy(None) == vm.VM_OK  # like free(NULL)
 
 

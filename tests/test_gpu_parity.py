@@ -260,3 +260,24 @@ def test_graph_and_eager_launches_agree_on_a_growing_map(orc, vmmod):
         for key in ("planes", "hull_xy", "hull_xyz"):
             assert np.array_equal(rg[key], re_[key]), key
     compare_planes(rg, om.segment(op), mg.export_clusters())
+
+
+def test_captured_graph_keeps_programmatic_edges(vmmod):
+    """The segmentation graph is captured from programmatic stream launches:
+    its kernel-to-kernel edges keep the programmatic type (the next kernel may
+    launch before the one it depends on finishes), as in the stream."""
+    import os
+    spec, pts, pose = synth.config1()
+    m = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size)
+    m.integrate(pts, pose)
+    m.segment(vmmod.segment_params(n_hyp=64))
+    g = m.graph_shape()
+    assert g["nodes"] >= 20 and g["edges"] >= g["nodes"] - 1
+    if os.environ.get("VOXMPS_PDL", "1") != "0":
+        # every launch but the plain ones (the grid-filling fit passes) and
+        # the memcpy-free chain's first node is captured programmatic
+        assert g["programmatic"] >= g["edges"] // 2, g
+    eager = vmmod.VoxelMap(spec.dims, spec.origin, spec.voxel_size, eager=True)
+    eager.integrate(pts, pose)
+    eager.segment(vmmod.segment_params(n_hyp=64))
+    assert eager.graph_shape() == {"nodes": 0, "edges": 0, "programmatic": 0}
