@@ -810,6 +810,7 @@ def run_gpu(args):
         torch.distributed.barrier()
     launches = vm.launch_count() - launches0
     clocks = sampler.stop()
+    graph = m.graph_shape()
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     # the GPU's idle time between steps: the host reads a step's result and
     # enqueues the next step (a synchronous segment call per frame)
@@ -1018,6 +1019,7 @@ def run_gpu(args):
         "config": bench_config(args.steps, args.warmup, ws),
         "fit_tuning": dict(tuning, autotune_candidates=tune_n, autotune_ms=round(tune_ms, 4)),
         "host_gap_ms": round(host_gap_ms, 4),
+        "segment_graph": graph,
         "p50_ms": round(statistics.median(per_step), 4),
         "p99_ms": round(sorted(per_step)[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)], 4),
         "gpu_launches": int(launches),

@@ -396,9 +396,76 @@ __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const uint32_t* in
     }
 }
 
+// Two arrays of the same length scanned by one CTA (as k_scan_small, both at once).
+__global__ void __launch_bounds__(kSmallThreads) k_scan2_small(const uint32_t* in0, uint32_t* out0, uint32_t* total0,
+                                                               const uint32_t* in1, uint32_t* out1, uint32_t* total1,
+                                                               size_t n_cap, const uint32_t* __restrict__ n_dev) {
+    pdl_gate();
+    __shared__ uint32_t ws[2][kSmallThreads / 32];
+    __shared__ uint32_t round_total[2];
+    const size_t n = dev_count(n_cap, n_dev);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t carry0 = 0, carry1 = 0;
+    for (size_t base = 0; base < n; base += (size_t)kSmallThreads * kSmallItems) {
+        const size_t j0 = base + (size_t)threadIdx.x * kSmallItems;
+        uint32_t v0[kSmallItems], v1[kSmallItems], sum0 = 0, sum1 = 0;
+#pragma unroll
+        for (int i = 0; i < kSmallItems; ++i) {
+            v0[i] = (j0 + i < n) ? in0[j0 + i] : 0u;
+            v1[i] = (j0 + i < n) ? in1[j0 + i] : 0u;
+            sum0 += v0[i];
+            sum1 += v1[i];
+        }
+        const uint32_t inc0 = warp_incl_scan(sum0), inc1 = warp_incl_scan(sum1);
+        if (lane == 31) {
+            ws[0][w] = inc0;
+            ws[1][w] = inc1;
+        }
+        __syncthreads();
+        if (w < 2) {
+            const uint32_t t = ws[w][lane];
+            const uint32_t ti = warp_incl_scan(t);
+            ws[w][lane] = ti - t;
+            if (lane == 31) round_total[w] = ti;
+        }
+        __syncthreads();
+        uint32_t ex0 = carry0 + ws[0][w] + (inc0 - sum0), ex1 = carry1 + ws[1][w] + (inc1 - sum1);
+#pragma unroll
+        for (int i = 0; i < kSmallItems; ++i) {
+            if (j0 + i < n) {
+                out0[j0 + i] = ex0;
+                out1[j0 + i] = ex1;
+            }
+            ex0 += v0[i];
+            ex1 += v1[i];
+        }
+        carry0 += round_total[0];
+        carry1 += round_total[1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (total0) *total0 = carry0;
+        if (total1) *total1 = carry1;
+    }
+}
+
 }  // namespace
 
 static_assert((size_t)kScanTile == kScanTileElems, "scan_tmp_words assumes the scan's tile size");
+
+cudaError_t exclusive_scan2_dev(const uint32_t* in0, uint32_t* out0, uint32_t* total0, const uint32_t* in1,
+                                uint32_t* out1, uint32_t* total1, const uint32_t* n_dev, size_t n_cap, uint32_t* tmp,
+                                cudaStream_t s, uint32_t* err) {
+    if (n_cap > 0 && n_cap <= kSmallMax) {
+        launch_k(k_scan2_small, dim3(1), dim3(kSmallThreads), 0, s, in0, out0, total0, in1, out1, total1, n_cap,
+                 n_dev);
+        count_launch(1);
+        return cudaGetLastError();
+    }
+    cudaError_t e = exclusive_scan_dev(in0, out0, total0, n_dev, n_cap, tmp, s, err);
+    if (e != cudaSuccess) return e;
+    return exclusive_scan_dev(in1, out1, total1, n_dev, n_cap, tmp, s, err);
+}
 
 cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
                                uint32_t* tmp, cudaStream_t s, uint32_t* err, bool end) {

@@ -746,6 +746,103 @@ __global__ void __launch_bounds__(kBrickVox) k_brick_clusters(const uint32_t* __
 
 
 
+// Cluster formation when every cluster number fits one byte (at most 256
+// clusters): the kept (cluster, index) pairs, in index order, are counted per
+// tile of 2048 and cluster; the counts are scanned cluster-major (each tile's
+// first slot in each cluster, and at tile 0 each cluster's offset); each pair
+// then goes, stably, straight to its slot with its mean position and voxel
+// id.  This is one pass of a stable radix sort whose scatter writes the
+// cluster point lists themselves, so the pairs are neither sorted first nor
+// gathered after, and the cluster offsets come from the same scan.
+constexpr int kClT = 256, kClWarps = kClT / 32, kClIt = 8, kClTile = kClT * kClIt;
+
+__global__ void __launch_bounds__(kClT) k_cl_hist(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ np,
+                                                  uint32_t* __restrict__ ghist, uint32_t* __restrict__ cnt) {
+    pdl_gate();
+    __shared__ uint32_t h[256];
+    const uint32_t n = *np;
+    const uint32_t ntu = (n + kClTile - 1) / kClTile;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *cnt = 256u * ntu;  // the scan's length
+    if (blockIdx.x >= ntu) return;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kClTile;
+    for (int i = 0; i < kClIt; ++i) {
+        const uint32_t j = base + i * kClT + threadIdx.x;
+        if (j < n) atomicAdd(&h[keys[j] & 255u], 1u);
+    }
+    __syncthreads();
+    ghist[(size_t)threadIdx.x * ntu + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable within a tile: warp w owns pairs [w * 256, w * 256 + 256) of it, in order.
+__global__ void __launch_bounds__(kClT) k_cl_scatter(const uint32_t* __restrict__ keys,
+                                                     const uint32_t* __restrict__ vals,
+                                                     const uint32_t* __restrict__ np, const uint32_t* __restrict__ kp,
+                                                     const uint32_t* __restrict__ goff,
+                                                     const float4* __restrict__ rec,
+                                                     const int32_t* __restrict__ sorted_key,
+                                                     float* __restrict__ pts, uint32_t* __restrict__ pt_vid,
+                                                     uint32_t* __restrict__ cl_off, SegCounters* __restrict__ ctr) {
+    pdl_gate();
+    __shared__ uint32_t wc[kClWarps][256];
+    const uint32_t n = *np;
+    const uint32_t ntu = (n + kClTile - 1) / kClTile;
+    if (blockIdx.x == 0) {  // the cluster offsets, closed by the number of clustered points
+        const uint32_t k = *kp;
+        for (uint32_t c = threadIdx.x; c < k; c += kClT) cl_off[c] = ntu ? goff[(size_t)c * ntu] : 0u;
+        if (threadIdx.x == 0) {
+            cl_off[k] = n;
+            ctr->tot = n;
+        }
+    }
+    if (blockIdx.x >= ntu) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kClWarps * 256; d += kClT) (&wc[0][0])[d] = 0;
+    __syncthreads();
+    const uint32_t base = blockIdx.x * kClTile + (uint32_t)w * (32 * kClIt);
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t rank[kClIt], dig[kClIt];
+#pragma unroll
+    for (int i = 0; i < kClIt; ++i) {
+        const uint32_t j = base + i * 32 + lane;
+        const uint32_t d = (j < n) ? (keys[j] & 255u) : 256u;
+        dig[i] = d;
+        const uint32_t m = __match_any_sync(0xffffffffu, d);
+        const uint32_t r = __popc(m & lt);
+        const uint32_t b = (d < 256u) ? wc[w][d] : 0u;
+        __syncwarp();
+        if (d < 256u && r == 0) wc[w][d] = b + __popc(m);
+        __syncwarp();
+        rank[i] = b + r;
+    }
+    __syncthreads();
+    {   // exclusive offsets of each warp per cluster
+        const int d = threadIdx.x;  // kClT == 256 clusters
+        uint32_t run = 0;
+        for (int q = 0; q < kClWarps; ++q) {
+            const uint32_t t = wc[q][d];
+            wc[q][d] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kClIt; ++i) {
+        const uint32_t j = base + i * 32 + lane;
+        if (j < n) {
+            const uint32_t d = dig[i];
+            const uint32_t pos = goff[(size_t)d * ntu + blockIdx.x] + wc[w][d] + rank[i];
+            const uint32_t v = vals[j];
+            const float4 a = rec[v];  // the mean position, as k_moments formed it
+            pts[3 * (size_t)pos + 0] = a.x;
+            pts[3 * (size_t)pos + 1] = a.y;
+            pts[3 * (size_t)pos + 2] = a.z;
+            pt_vid[pos] = vid_of(v, sorted_key);
+        }
+    }
+}
+
 // Cluster points in cluster order: mean positions and voxel ids.
 __global__ void k_gather(const uint32_t* __restrict__ np, const uint32_t* __restrict__ vals_main,
                          const uint32_t* __restrict__ vals_alt, const uint32_t* __restrict__ kp, int bits,
@@ -827,12 +924,25 @@ cudaError_t seg_run(const Grid& g, const unsigned long long* S, const uint32_t* 
     const unsigned bgrid = clampg(cap_b, sms * 4);
     launch_k(k_brick_tally, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nvert, nroot,
              rmask);
-    cudaError_t e = exclusive_scan_dev(nroot, nroot, &b.ctr->k, nsp, cap_b, b.scan_tmp, s, err);
-    if (e != cudaSuccess) return e;
-    e = exclusive_scan_dev(nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp, s, err);
+    cudaError_t e = exclusive_scan2_dev(nroot, nroot, &b.ctr->k, nvert, nvert, &b.ctr->n_kept, nsp, cap_b, b.scan_tmp,
+                                        s, err);
     if (e != cudaSuccess) return e;
     launch_k(k_brick_clusters, dim3(bgrid), dim3(kBrickVox), 0, s, nsp, cap_b, b.parent, b.count, min_cl, nroot, nvert,
              rmask, b.sorted_key, b.cl_size, b.cl_label, kcap, b.keys, b.vals, b.ctr);
+    if (kcap <= 256) {  // one byte a cluster number: one scatter pass writes the cluster points
+        const size_t nt = (b.nv + kClTile - 1) / kClTile;
+        uint32_t* ghist = b.sort_tmp;
+        uint32_t* cnt = b.sort_tmp + 256 * nt;
+        uint32_t* stmp = b.sort_tmp + 256 * nt + 64;
+        launch_k(k_cl_hist, dim3((unsigned)nt), dim3(kClT), 0, s, b.keys, &b.ctr->n_kept, ghist, cnt);
+        e = exclusive_scan_dev(ghist, ghist, nullptr, cnt, 256 * nt, stmp, s, err);
+        if (e != cudaSuccess) return e;
+        launch_k(k_cl_scatter, dim3((unsigned)nt), dim3(kClT), 0, s, b.keys, b.vals, &b.ctr->n_kept, &b.ctr->k, ghist,
+                 b.rec, b.sorted_key, b.pts, b.pt_vid, b.cl_off, b.ctr);
+        VM_STAGE_END(hk, kStClusters, s);
+        count_launch(5);
+        return cudaGetLastError();
+    }
     int bits = 1;
     while ((1ull << bits) < kcap && bits < 32) ++bits;
     e = stable_sort_pairs_dev(b.keys, b.vals, b.keys_alt, b.vals_alt, &b.ctr->n_kept, b.nv, bits, b.sort_tmp, s, err,

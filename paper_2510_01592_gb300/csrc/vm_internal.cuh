@@ -283,6 +283,11 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, uint32_t* tota
 // then holds n_cap + 1 words), the closing offset of an offsets array.
 cudaError_t exclusive_scan_dev(const uint32_t* in, uint32_t* out, uint32_t* total, const uint32_t* n_dev, size_t n_cap,
                                uint32_t* tmp, cudaStream_t s, uint32_t* err, bool end = false);
+// Two arrays of the same length scanned as exclusive_scan_dev does (one
+// launch when n_cap is small).
+cudaError_t exclusive_scan2_dev(const uint32_t* in0, uint32_t* out0, uint32_t* total0, const uint32_t* in1,
+                                uint32_t* out1, uint32_t* total1, const uint32_t* n_dev, size_t n_cap, uint32_t* tmp,
+                                cudaStream_t s, uint32_t* err);
 // key_bound (device, may be null): every key is below *key_bound; passes whose
 // digit no key reaches are skipped on the device, and the result then lies in
 // (keys, vals) after an even number of executed passes and in the alt buffers
