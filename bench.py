@@ -18,6 +18,7 @@ frames of all ranks / the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -658,6 +659,8 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.times = []
+        self.t_mark = None
 
     def start(self):
         try:
@@ -672,6 +675,19 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.times.append(time.perf_counter())
+
+    def mark(self):
+        """Samples before this call are left out of the record (set-up work)."""
+        self.t_mark = time.perf_counter()
+
+    def wait_first(self, timeout_s=10.0):
+        """Blocks until the sampler has printed its first line: nvidia-smi's own
+        start-up (driver and NVML initialisation) then lies before the timed
+        region instead of inside it."""
+        t_end = time.perf_counter() + timeout_s
+        while self.proc and not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def stop(self):
         if not self.proc:
@@ -683,7 +699,10 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        if self.t_mark is not None and len(self.times) == len(self.lines):
+            lines = [ln for ln, t in zip(self.lines, self.times) if t >= self.t_mark] or self.lines[-1:]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -754,6 +773,10 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    # the clock sampler starts here, its own start-up overlapping the set-up
+    # work; its record keeps only the samples taken from the first timed pass on
+    sampler = ClockSampler(local)
+    sampler.start()
     spec = synth.config2_spec()
     pts, poses = make_frames(dev)
     first, sched = frame_schedule(args.steps, args.warmup)
@@ -785,39 +808,80 @@ def run_gpu(args):
     # one more segmentation of the same map (it does not change the map): the
     # scratch the chosen schedule needs is sized, and its graph captured, here
     m.segment(params)
+    sampler.wait_first()
+    # no cyclic garbage collection inside the timed passes (a full collection
+    # over torch's objects takes milliseconds of host time between two steps)
+    gc.collect()
+    gc.disable()
+    # one untimed pass of the warm-up and timed steps on a throwaway map: in a
+    # fresh process the first such pass runs some 6% slower than every later
+    # one (segmenting an unchanged map again does not take that away); the
+    # timed map is not touched by it
+    mw = fresh_map()
+    for j, f in enumerate(sched[:args.warmup + min(args.steps, 100)]):
+        if f == 0 and j:
+            mw.reset()
+        mw.integrate(pts[f], poses[f])
+        mw.segment(params)
+    mw.close()
+    # then the timed map's own graph, segmenting the unchanged map for a tenth of a second
+    t_warm = time.perf_counter()
+    while time.perf_counter() - t_warm < 0.1:
+        m.segment(params)
     torch.cuda.synchronize()
+    sampler.mark()
     if ws > 1:
         torch.distributed.barrier()
-    sampler = ClockSampler(local)
-    sampler.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]  # where each step's GPU work begins
-    launches0 = vm.launch_count()
+    # throughput: the K steps bracketed by two events only (an event recorded
+    # between two steps would stand between one step's last kernel and the
+    # next step's first, as in the plain arm below, which records none)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0, captures0 = vm.launch_count(), vm.capture_count()
     torch.cuda.synchronize()
-    ev[0].record(stream)
+    e0.record(stream)
     n_planes = []
     for i in range(args.steps):
         f = sched[args.warmup + i]
         if f == 0 and (args.warmup + i):
             m.reset()
-        evs[i].record(stream)
         m.integrate(pts[f], poses[f])
         r = m.segment(params)
         n_planes.append(len(r["planes"]))
-        ev[i + 1].record(stream)
+    e1.record(stream)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     launches = vm.launch_count() - launches0
-    clocks = sampler.stop()
-    graph = m.graph_shape()
+    graph = dict(m.graph_shape(), captures_in_timed_steps=int(vm.capture_count() - captures0))
+    total_ms = e0.elapsed_time(e1)
+    st = m.stats()
+    m.close()
+    # ---------------- per-step latency: the same steps on a fresh map, an event around each step
+    ml = fresh_map()
+    for i in range(args.warmup):
+        f = sched[i]
+        if f == 0 and i:
+            ml.reset()
+        ml.integrate(pts[f], poses[f])
+        ml.segment(params)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]  # where each step's GPU work begins
+    ev[0].record(stream)
+    for i in range(args.steps):
+        f = sched[args.warmup + i]
+        if f == 0 and (args.warmup + i):
+            ml.reset()
+        evs[i].record(stream)
+        ml.integrate(pts[f], poses[f])
+        ml.segment(params)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    ml.close()
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     # the GPU's idle time between steps: the host reads a step's result and
     # enqueues the next step (a synchronous segment call per frame)
     host_gap_ms = statistics.median(ev[i].elapsed_time(evs[i]) for i in range(1, args.steps)) if args.steps > 1 else 0.0
-    total_ms = ev[0].elapsed_time(ev[-1])
-    st = m.stats()
-    m.close()
     # ---------------- plain per-frame launches (kernel by kernel, no graph), same frames
     mp = vm.VoxelMap(spec.dims, spec.origin, spec.voxel_size, stream=stream, eager=True)
     mp.set_fit_tuning(tuning)
@@ -1008,6 +1072,8 @@ def run_gpu(args):
                              "bricks before every frame (vm_scroll_to: eviction, pool compaction, re-anchoring), "
                              "then integrate + segment; graph replay"}
     mr.close()
+    clocks = sampler.stop()
+    gc.enable()
 
     total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev)
     frames = args.steps * ws
@@ -1020,6 +1086,8 @@ def run_gpu(args):
         "fit_tuning": dict(tuning, autotune_candidates=tune_n, autotune_ms=round(tune_ms, 4)),
         "host_gap_ms": round(host_gap_ms, 4),
         "segment_graph": graph,
+        "latency_pass": "p50_ms, p99_ms and host_gap_ms: the same steps again on a fresh map, an event pair around "
+                        "each step; value and ms_per_step: the steps bracketed by two events",
         "p50_ms": round(statistics.median(per_step), 4),
         "p99_ms": round(sorted(per_step)[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)], 4),
         "gpu_launches": int(launches),

@@ -55,3 +55,23 @@ def test_clock_record_from_samples():
     assert rec == {"sm_mhz": 2032.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     c2 = bench.ClockSampler(0)
     assert c2.stop() is None  # never started: no record
+
+
+def test_clock_record_keeps_the_samples_after_the_mark():
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c = bench.ClockSampler(0)
+    c.proc = Done()
+    c.lines = ["1200, 2070, 300.0, Not Active, Not Active, Not Active, Not Active",
+               "2070, 2070, 900.5, Not Active, Not Active, Not Active, Not Active",
+               "2040, 2070, 950.0, Not Active, Not Active, Not Active, Active"]
+    c.times = [1.0, 2.0, 3.0]
+    c.t_mark = 1.5  # the idle set-up sample is left out
+    assert c.stop() == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 2}
+    c.t_mark = 9.0  # nothing after the mark: the last sample stands in
+    assert c.stop()["samples"] == 1
