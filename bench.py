@@ -65,7 +65,8 @@ def parse():
                     help="profiling driver: integrate frames 1..F, segment --profile-segments times, no timing")
     ap.add_argument("--profile-segments", type=int, default=3)
     ap.add_argument("--profile-tuning", default="auto", metavar="TILE,R,CTAS,cta|warp",
-                    help="fit schedule of the profiling driver: 'auto' runs the autotuner first")
+                    help="fit schedule of the profiling drivers: 'auto' runs the autotuner first "
+                         "(--profile-case; --profile-fit keeps its default schedule)")
     ap.add_argument("--no-batching", action="store_true", help="skip the batched-fit and cluster-parallel variants")
     ap.add_argument("--no-serving", action="store_true", help="skip the 16-stream serving variant")
     ap.add_argument("--serve-seconds", type=float, default=20.0, help="Poisson-arrival serving run length")
@@ -106,14 +107,18 @@ def profile_case(frames, segments, tuning="auto"):
                       "fit_tuning": tuning, "stats": {k: v for k, v in m.stats().items() if isinstance(v, int)}}))
 
 
-def profile_fit(k):
+def profile_fit(k, tuning="default"):
     """A small, fixed batched fit for profiler captures: the first k clusters of
-    the config-3 recipe, H = 256, three runs of one plan (default schedule)."""
+    the config-3 recipe, H = 256, three runs of one plan (the default schedule,
+    or a given one: TILE,R,CTAS,cta|warp)."""
     import torch
     from paper_2510_01592_gb300 import vm
     import synth
     xyz, off, _ = synth.config3_clusters_device(n_clusters=k, device="cuda")
     plan = vm.FitPlan(k, xyz.shape[0], vm.segment_params(n_hyp=256, seed=7))
+    if tuning not in ("default", "auto"):
+        t, r, c, sched = tuning.split(",")
+        plan.set_tuning(int(t), int(r), int(c), sched)
     for _ in range(3):
         r = plan.run(xyz, off)
     torch.cuda.synchronize()
@@ -1380,7 +1385,7 @@ def main():
         profile_case(args.profile_case, args.profile_segments, args.profile_tuning)
         return
     if args.profile_fit:
-        profile_fit(args.profile_fit)
+        profile_fit(args.profile_fit, args.profile_tuning)
         return
     if args.impl == "reference":
         res, rank = run_reference(args)

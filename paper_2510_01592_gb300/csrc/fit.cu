@@ -295,17 +295,26 @@ __global__ void __launch_bounds__(kT) k_score(const float* __restrict__ pts, con
     }
 }
 
-// Quantised in-plane coordinates (units of 2^-16 m) relative to the origin.
-__device__ __forceinline__ int2 quantise(const FitCluster& f, float px, float py, float pz) {
+// In-plane coordinates relative to the origin in units of 2^-16 m, before
+// rounding: quantise() rounds exactly these values, so each lies within half
+// a unit of its quantised coordinate.
+__device__ __forceinline__ float2 plane_coords(const FitCluster& f, float px, float py, float pz) {
     const float qx = __fsub_rn(px, f.o[0]), qy = __fsub_rn(py, f.o[1]), qz = __fsub_rn(pz, f.o[2]);
     const float a = __fmaf_rn(qz, f.u[2], __fmaf_rn(qy, f.u[1], __fmul_rn(qx, f.u[0])));
     const float b = __fmaf_rn(qz, f.v[2], __fmaf_rn(qy, f.v[1], __fmul_rn(qx, f.v[0])));
-    return make_int2(__float2int_rn(__fmul_rn(a, 65536.0f)), __float2int_rn(__fmul_rn(b, 65536.0f)));
+    return make_float2(__fmul_rn(a, 65536.0f), __fmul_rn(b, 65536.0f));
+}
+
+// Quantised in-plane coordinates (units of 2^-16 m) relative to the origin.
+__device__ __forceinline__ int2 quantise(const FitCluster& f, float px, float py, float pz) {
+    const float2 w = plane_coords(f, px, py, pz);
+    return make_int2(__float2int_rn(w.x), __float2int_rn(w.y));
 }
 
 // The 16 filter directions, counter-clockwise: (1,0) (2,1) (1,1) (1,2) (0,1)
-// (-1,2) (-1,1) (-2,1) (-1,0) (-2,-1) (-1,-1) (-1,-2) (0,-1) (1,-2) (1,-1) (2,-1).
-// With |X|, |Y| < 2^28 every value fits in int32.
+// (-1,2) (-1,1) (-2,1) (-1,0) (-2,-1) (-1,-1) (-1,-2) (0,-1) (1,-2) (1,-1) (2,-1);
+// direction d + 8 is direction d negated.  With |X|, |Y| < 2^28 every value
+// fits in int32.
 constexpr int kFiltDirs = 16;
 __device__ __forceinline__ int32_t dir_value(int dir, int2 p) {
     const int a = (dir == 0 || dir == 2 || dir == 3 || dir == 14 || dir == 13) ? 1
@@ -348,15 +357,38 @@ constexpr uint32_t kChunk = kT;
 // then thread j adds chunk j's eight warp results in warp order.
 constexpr int kMaxChunksPerItem = 16384 / (int)kChunk;
 
+// The warp tree is the butterfly over lane offsets 16, 8, 4, 2, 1 for every
+// value, transposed: at each of the first levels a lane keeps half of its
+// values and sends the other half to its partner, which keeps the opposite
+// half, so NV values (padded to P = 4 or 8) take 2 + 1 + 3 (P = 4) or
+// 4 + 2 + 1 + 2 (P = 8) shuffles instead of 5 NV.  Each partial sum is
+// the one the plain butterfly forms at that level (a + b = b + a exactly),
+// so the totals are bit-identical to it.  Value e ends in the lanes whose top
+// log2(P) lane bits equal e.
 template <int NV>
 __device__ __forceinline__ void warp_park(float (&v)[NV], float* wp, uint32_t j) {
+    static_assert(NV == 4 || NV == 6, "4 or 6 values");
+    constexpr int P = NV == 4 ? 4 : 8;
+    constexpr int L = NV == 4 ? 2 : 3;  // log2(P): halving levels at offsets 16 .. 32 >> L
+    const int lane = threadIdx.x & 31;
+    float x[P];
 #pragma unroll
-    for (int e = 0; e < NV; ++e)
+    for (int e = 0; e < P; ++e) x[e] = e < NV ? v[e] : 0.0f;
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) v[e] += __shfl_xor_sync(0xffffffffu, v[e], s);
-    if ((threadIdx.x & 31) == 0)
+    for (int lv = 0; lv < L; ++lv) {
+        const int s = 16 >> lv, h = P >> (lv + 1);
+        const bool up = (lane & s) != 0;
 #pragma unroll
-        for (int e = 0; e < NV; ++e) wp[(j * (kT / 32) + (threadIdx.x >> 5)) * NV + e] = v[e];
+        for (int i = 0; i < h; ++i) {
+            const float keep = up ? x[h + i] : x[i];
+            const float send = up ? x[i] : x[h + i];
+            x[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+#pragma unroll
+    for (int s = 16 >> L; s > 0; s >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], s);
+    const int e = (lane >> (5 - L)) & (P - 1);
+    if ((lane & ((32 >> L) - 1)) == 0 && e < NV) wp[(j * (kT / 32) + (threadIdx.x >> 5)) * NV + e] = x[0];
 }
 
 template <int NV>
@@ -519,9 +551,17 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
         const FitCluster f = cl[c];
         const uint32_t start = off[c] + (it - item_off[c]) * (uint32_t)T;
         const uint32_t end = min(off[c + 1], start + (uint32_t)T);
-        unsigned long long ext[kFiltDirs];
+        // per thread and direction d < 8: the largest value and its point (the
+        // last one, i.e. the largest index, among equal values: points come in
+        // index order), and the smallest value and its point; direction d + 8
+        // is direction d negated, so its key is (-smallest, index)
+        int vmax[kFiltDirs / 2], imax[kFiltDirs / 2], vmin[kFiltDirs / 2], imin[kFiltDirs / 2];
 #pragma unroll
-        for (int d = 0; d < kFiltDirs; ++d) ext[d] = 0;
+        for (int d = 0; d < kFiltDirs / 2; ++d) {
+            vmax[d] = INT_MIN;
+            vmin[d] = INT_MAX;
+            imax[d] = imin[d] = 0;
+        }
         bool big = false;
         // chunk within the item; its slot is it * cpt + j (item_off[c] * cpt + its chunk in the cluster)
         uint32_t j = 0;
@@ -540,11 +580,12 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
                     v[3] = __fsub_rn(pz, f.o[2]);
                     const int2 xy = quantise(f, px, py, pz);
                     big |= (abs(xy.x) >= (1 << 28)) | (abs(xy.y) >= (1 << 28));
-                    const uint32_t idx = q - off[c];
+                    const int idx = (int)(q - off[c]);
 #pragma unroll
-                    for (int d = 0; d < kFiltDirs; ++d) {
-                        const unsigned long long key = ext_key(dir_value(d, xy), idx);
-                        ext[d] = key > ext[d] ? key : ext[d];
+                    for (int d = 0; d < kFiltDirs / 2; ++d) {
+                        const int val = dir_value(d, xy);
+                        if (val >= vmax[d]) { vmax[d] = val; imax[d] = idx; }
+                        if (val <= vmin[d]) { vmin[d] = val; imin[d] = idx; }
                     }
                 }
             }
@@ -552,15 +593,17 @@ __global__ void __launch_bounds__(kT) k_extract(const float* __restrict__ pts, c
         }
         chunks_out<4>(wp, j, part + (size_t)it * cpt * 10, 0);  // slot 0 holds the count (at most 256: exact)
         if (big) atomicOr(err, kErrOverflow);
+        // the warp's largest key per direction: the extreme value, then the
+        // largest index among the lanes that hold it
+        const bool lane0 = (threadIdx.x & 31) == 0;
 #pragma unroll
-        for (int d = 0; d < kFiltDirs; ++d) {
-            unsigned long long m = ext[d];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
-                m = t > m ? t : m;
-            }
-            if ((threadIdx.x & 31) == 0 && m) atomicMax(&cl[c].ext[d], m);
+        for (int d = 0; d < kFiltDirs / 2; ++d) {
+            const int wmax = __reduce_max_sync(0xffffffffu, vmax[d]);
+            const int wimax = __reduce_max_sync(0xffffffffu, vmax[d] == wmax ? imax[d] : 0);
+            const int wmin = __reduce_min_sync(0xffffffffu, vmin[d]);
+            const int wimin = __reduce_max_sync(0xffffffffu, vmin[d] == wmin ? imin[d] : 0);
+            if (lane0 && wmax != INT_MIN) atomicMax(&cl[c].ext[d], ext_key(wmax, (uint32_t)wimax));
+            if (lane0 && wmin != INT_MAX) atomicMax(&cl[c].ext[d + 8], ext_key(-wmin, (uint32_t)wimin));
         }
         __syncthreads();
         if constexpr (kTail) extract_tail(c, off, item_off, T, part, cl, cen, done);
@@ -593,6 +636,19 @@ __device__ __noinline__ void filter_tail(uint32_t c, const uint32_t* __restrict_
 // warp gathers its survivors in shared memory and reserves room in the list
 // with one atomic per kSurvBuf survivors (usually one per work item) instead
 // of one returned atomic per chunk on the loop's critical path.
+//
+// The polygon test runs in FP32 on the unrounded plane coordinates (af, bf)
+// against each edge's line scaled by a bound E on the test's own error: with
+// A -> B an edge (quantised ints, ex = B - A), c = ex A.y - ey A.x and the
+// cluster's inliers within |X|, |Y| <= M - 1 (their extremes along +-x, +-y),
+//   F = (ex bf - ey af - c) / E,  E = 2 (0.5 (|ex| + |ey|) + 2^-21 ((|ex| + |ey|) M + |c|) + 1),
+// differs from the exact cross product (ex Y - ey X - c) / E by less than 0.5:
+// af, bf lie within half a unit of X, Y, and the conversions, the divisions
+// and the two fused multiply-adds add at most 2^-22 ((|ex| + |ey|) M + |c|).
+// So min over the edges F > 1 means strictly inside every edge (the point is
+// dropped) and F < -1 on some edge means outside it (a survivor); the few
+// points in between take the exact integer test.  The edges' coefficients are
+// read from shared memory once per kBatch chunks.
 template <bool kTail>
 __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, const uint32_t* __restrict__ off,
                                                const uint32_t* __restrict__ item_off,
@@ -603,9 +659,13 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
     pdl_gate();
     const uint32_t k = *kp;
     constexpr int kSurvBuf = 128;
+    constexpr int kBatch = 4;  // chunks a thread tests against the edges together
     __shared__ float wp[kMaxChunksPerItem * (kT / 32) * 6];
+    __shared__ int2 sxy[kFiltDirs];
     __shared__ int2 poly[kFiltDirs + 1];
+    __shared__ float4 edge[kFiltDirs];  // (ex / E, -ey / E, -c / E): F = x bf + y af + z
     __shared__ int npoly;
+    __shared__ float sM;
     __shared__ int2 sbuf[kT / 32][kSurvBuf];
     int2* sb = sbuf[threadIdx.x >> 5];
     const uint32_t n_items = item_off[k];
@@ -618,14 +678,23 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
         const uint32_t start = base + (it - item_off[c]) * (uint32_t)T;
         const uint32_t end = min(off[c + 1], start + (uint32_t)T);
         __syncthreads();
+        if (threadIdx.x < kFiltDirs) {  // the extreme points, one direction a thread
+            const int d = threadIdx.x;
+            const unsigned long long key = cl[c].ext[d];  // not f.ext[d]: an indexed copy would live on the stack
+            int2 xy = make_int2(INT_MIN, INT_MIN);  // none
+            if (key) {
+                const float* p = pts + 3 * ((size_t)base + (uint32_t)(key & 0xffffffffu));
+                xy = quantise(f, p[0], p[1], p[2]);
+            }
+            sxy[d] = xy;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
             // polygon through the extreme points, counter-clockwise, duplicates removed
             int m = 0;
             for (int d = 0; d < kFiltDirs; ++d) {
-                if (!f.ext[d]) continue;
-                const uint32_t idx = (uint32_t)(f.ext[d] & 0xffffffffu);
-                const float* p = pts + 3 * ((size_t)base + idx);
-                const int2 xy = quantise(f, p[0], p[1], p[2]);
+                const int2 xy = sxy[d];
+                if (xy.x == INT_MIN && xy.y == INT_MIN) continue;
                 if (m && poly[m - 1].x == xy.x && poly[m - 1].y == xy.y) continue;
                 poly[m++] = xy;
             }
@@ -637,9 +706,30 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
                 area2 += (long long)a.x * b.y - (long long)a.y * b.x;
             }
             npoly = (m >= 3 && area2 > 0) ? m : 0;
+            // |X|, |Y| of every inlier: at most the extremes along +-x (directions 0, 8), +-y (4, 12)
+            int mx = 0;
+            for (int d = 0; d < kFiltDirs; d += 4)
+                if (f.ext[d]) mx = max(mx, abs((int)((uint32_t)(f.ext[d] >> 32) ^ 0x80000000u)));
+            sM = (float)mx + 1.0f;
         }
         __syncthreads();
         const int m = npoly;
+        if (threadIdx.x < kFiltDirs) {  // the edges' scaled lines, one edge a thread; padding never decides
+            const int i = threadIdx.x;
+            float4 e = make_float4(0.0f, 0.0f, 2.0f, 0.0f);
+            if (i < m) {
+                const int2 A = poly[i], B = poly[(i + 1) % m];
+                const long long ex = (long long)B.x - A.x, ey = (long long)B.y - A.y;
+                const long long cc = (long long)((unsigned long long)ex * (unsigned long long)(long long)A.y -
+                                                 (unsigned long long)ey * (unsigned long long)(long long)A.x);
+                const float exf = (float)ex, eyf = (float)ey, cf = (float)cc;
+                const float sum = fabsf(exf) + fabsf(eyf);
+                const float E = 2.0f * (0.5f * sum + 4.76837158203125e-7f * (sum * sM + fabsf(cf)) + 1.0f);
+                e = make_float4(__fdiv_rn(exf, E), -__fdiv_rn(eyf, E), -__fdiv_rn(cf, E), 0.0f);
+            }
+            edge[i] = e;
+        }
+        __syncthreads();
         const float cx = cen[6 * c], cy = cen[6 * c + 2], cz = cen[6 * c + 4];  // nearest floats of the centroid
         int cnt = 0;  // survivors in this warp's buffer (warp-uniform)
         auto flush = [&]() {
@@ -651,30 +741,60 @@ __global__ void __launch_bounds__(kT) k_filter(const float* __restrict__ pts, co
             cnt = 0;
         };
         uint32_t j = 0;
-#pragma unroll 4
-        for (uint32_t q0 = start; q0 < end; q0 += kChunk, ++j) {  // unrolled: later chunks' loads go out early
-            const uint32_t q = q0 + threadIdx.x;
-            bool keep = false;
-            int2 xy = make_int2(0, 0);
-            float v[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // centred second moments
-            if (q < end && inlier[q]) {
-                const float px = pts[3 * (size_t)q], py = pts[3 * (size_t)q + 1], pz = pts[3 * (size_t)q + 2];
-                const float rx = __fsub_rn(px, cx), ry = __fsub_rn(py, cy), rz = __fsub_rn(pz, cz);
-                v[0] = __fmul_rn(rx, rx); v[1] = __fmul_rn(ry, ry); v[2] = __fmul_rn(rz, rz);
-                v[3] = __fmul_rn(rx, ry); v[4] = __fmul_rn(rx, rz); v[5] = __fmul_rn(ry, rz);
-                xy = quantise(f, px, py, pz);
-                keep = true;
-                for (int i = 0; i < m; ++i) {  // strictly inside every edge -> not a hull vertex
-                    if (cross3(poly[i], poly[(i + 1) % m], xy) <= 0) break;
-                    if (i == m - 1) keep = false;
+        for (uint32_t qb = start; qb < end; qb += kBatch * kChunk) {
+            float px[kBatch], py[kBatch], pz[kBatch], af[kBatch], bf[kBatch], fmin[kBatch];
+            bool live[kBatch];
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                const uint32_t q = qb + u * kChunk + threadIdx.x;
+                live[u] = q < end && inlier[q];
+                px[u] = py[u] = pz[u] = af[u] = bf[u] = 0.0f;
+                if (live[u]) {
+                    px[u] = pts[3 * (size_t)q]; py[u] = pts[3 * (size_t)q + 1]; pz[u] = pts[3 * (size_t)q + 2];
+                    const float2 w = plane_coords(f, px[u], py[u], pz[u]);
+                    af[u] = w.x;
+                    bf[u] = w.y;
+                }
+                fmin[u] = 2.0f;
+            }
+            if (m) {
+#pragma unroll
+                for (int i = 0; i < kFiltDirs; ++i) {
+                    const float4 e = edge[i];
+#pragma unroll
+                    for (int u = 0; u < kBatch; ++u)
+                        fmin[u] = fminf(fmin[u], __fmaf_rn(e.x, bf[u], __fmaf_rn(e.y, af[u], e.z)));
                 }
             }
-            const uint32_t b = __ballot_sync(0xffffffffu, keep);
-            if (cnt + __popc(b) > kSurvBuf) flush();
-            if (keep) sb[cnt + __popc(b & ((1u << lane) - 1u))] = xy;
-            cnt += __popc(b);
-            __syncwarp();
-            warp_park<6>(v, wp, j);
+#pragma unroll
+            for (int u = 0; u < kBatch; ++u) {
+                if (qb + u * kChunk >= end) continue;  // uniform: past the item's last chunk
+                bool keep = false;
+                int2 xy = make_int2(0, 0);
+                float v[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};  // centred second moments
+                if (live[u]) {
+                    const float rx = __fsub_rn(px[u], cx), ry = __fsub_rn(py[u], cy), rz = __fsub_rn(pz[u], cz);
+                    v[0] = __fmul_rn(rx, rx); v[1] = __fmul_rn(ry, ry); v[2] = __fmul_rn(rz, rz);
+                    v[3] = __fmul_rn(rx, ry); v[4] = __fmul_rn(rx, rz); v[5] = __fmul_rn(ry, rz);
+                    keep = !m || !(fmin[u] > 1.0f);
+                    if (keep) {
+                        xy = make_int2(__float2int_rn(af[u]), __float2int_rn(bf[u]));
+                        if (m && !(fmin[u] < -1.0f)) {  // within the error band of an edge: the exact test
+                            for (int i = 0; i < m; ++i) {  // strictly inside every edge -> not a hull vertex
+                                if (cross3(poly[i], poly[(i + 1) % m], xy) <= 0) break;
+                                if (i == m - 1) keep = false;
+                            }
+                        }
+                    }
+                }
+                const uint32_t b = __ballot_sync(0xffffffffu, keep);
+                if (cnt + __popc(b) > kSurvBuf) flush();
+                if (keep) sb[cnt + __popc(b & ((1u << lane) - 1u))] = xy;
+                cnt += __popc(b);
+                __syncwarp();
+                warp_park<6>(v, wp, j);
+                ++j;
+            }
         }
         if (cnt) flush();
         chunks_out<6>(wp, j, part + (size_t)it * cpt * 10, 4);
