@@ -603,7 +603,22 @@ void scheduler(Server* S) {
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 const size_t n = S->open_order.size();
-                for (size_t j = 0; j < n && st.reqs.size() < per_step; ++j) {
+                // Batched: a step takes at most its share of the streams with work
+                // (running or not) over the steps that may be in flight, so that
+                // when every stream is busy the next step's integrate and front
+                // halves overlap the previous step's fit instead of all streams
+                // forming one step that nothing overlaps.
+                size_t take = per_step;
+                if (batched && max_steps > 1) {
+                    size_t waiting = 0;
+                    for (uint32_t id : S->open_order) {
+                        const auto& s = S->streams[id];
+                        waiting += s.state == 1 && s.map && (s.busy || !s.q.empty());
+                    }
+                    const size_t share = (waiting + max_steps - 1) / max_steps;
+                    if (share >= 1 && share < take) take = share;
+                }
+                for (size_t j = 0; j < n && st.reqs.size() < take; ++j) {
                     const uint32_t id = S->open_order[(S->rr + j) % n];
                     auto& s = S->streams[id];
                     if (s.state != 1 || !s.map || s.busy || s.q.empty()) continue;
