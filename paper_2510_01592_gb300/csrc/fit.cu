@@ -1647,8 +1647,9 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
     if (e != cudaSuccess) return e;
     VM_STAGE_END(hk, kStScore, s);
     count_launch(1);
-    // stage c ran in the scoring kernel (the last item of each cluster), the
-    // centroid runs in the extraction kernel, the refit in the filter kernel
+    // stage c (k_select, a CTA per cluster), then the extraction; with the
+    // completion counters the centroid runs in the extraction kernel and the
+    // refit in the filter kernel, otherwise as kernels of their own
     const unsigned cgrid = kcap < (uint32_t)sms * 8 ? kcap : (uint32_t)sms * 8;
     VM_STAGE_BEGIN(hk, kStExtract, s);
     launch_k(k_select, dim3(cgrid), dim3(kT), 0, s, pts, off, kp, H, fb.hyp, fb.hyp_valid, fb.counts, fb.cl);
