@@ -403,19 +403,9 @@ vm_status plan_capacity(vm_map* m, const vm_segment_params& p, bool with_fit) {
 
 // The result header; rounds (null for one plane per cluster): the record and
 // hull-vertex totals of the extraction rounds.
-__global__ void k_header(const SegCounters* __restrict__ ctr, const uint32_t* __restrict__ hull_off,
-                         const uint32_t* __restrict__ rounds, const uint32_t* __restrict__ fit_err,
-                         const MapCounters* __restrict__ mc, const uint32_t* __restrict__ seg_err,
-                         SegCounters* __restrict__ out) {
+__global__ void k_header(HeaderArgs a) {
     pdl_gate();
-    SegCounters h = *ctr;
-    h.n_hull = rounds ? rounds[kWordHullTot] : hull_off[h.k];
-    h.n_planes = rounds ? rounds[kWordRec] : h.k;
-    h.fit_err = *fit_err;
-    h.n_bricks = mc->n_bricks;
-    h.map_err = mc->err;
-    h.err |= *seg_err;
-    *out = h;
+    write_header(a);
 }
 
 // The whole segmentation as one fixed launch sequence (every count is read on
@@ -443,24 +433,29 @@ cudaError_t enqueue_segment(vm_map* m, const vm_segment_params& p, StageHook* hk
     vm_plane* planes = reinterpret_cast<vm_plane*>(d + out_planes_off());
     int32_t* hull_xy = reinterpret_cast<int32_t*>(d + out_xy_off(m->out_kcap));
     float* hull_xyz = reinterpret_cast<float*>(d + out_xyz_off(m->out_kcap, m->out_hcap));
-    const uint32_t* rounds = nullptr;
+    HeaderArgs ha{b.ctr, fb.hull_cnt, nullptr, fb.err, m->ctr, m->err, reinterpret_cast<SegCounters*>(d)};
     if (p.planes_per_cluster > 1) {
         e = launch_rounds(b, m->kcap, p, fb, m->rounds, m->tune, sms, b.scan_tmp, planes, m->out_kcap, hull_xy,
                           hull_xyz, m->out_hcap, s, hk);
         if (e != cudaSuccess) return e;
-        rounds = m->rounds.word;
+        ha.rounds = m->rounds.word;
         VM_STAGE_BEGIN(hk, kStPack, s);
+        launch_k(k_header, dim3(1), dim3(1), 0, s, ha);
+        count_launch(1);
     } else {
         if ((e = launch_fit(b.pts, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, p, fb, m->tune, sms, s, hk)) !=
             cudaSuccess)
             return e;
         VM_STAGE_BEGIN(hk, kStPack, s);
-        e = launch_pack(fb, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, planes, hull_xy, hull_xyz, m->out_hcap, s);
-        if (e != cudaSuccess) return e;
+        if (m->kcap) {  // the pack kernel writes the header too
+            e = launch_pack(fb, b.cl_off, b.cl_label, &b.ctr->k, m->kcap, planes, hull_xy, hull_xyz, m->out_hcap, s,
+                            &ha);
+            if (e != cudaSuccess) return e;
+        } else {
+            launch_k(k_header, dim3(1), dim3(1), 0, s, ha);
+            count_launch(1);
+        }
     }
-    launch_k(k_header, dim3(1), dim3(1), 0, s, b.ctr, fb.hull_cnt, rounds, fb.err, m->ctr, m->err,
-             reinterpret_cast<SegCounters*>(d));
-    count_launch(1);
     VM_STAGE_END(hk, kStPack, s);
     return cudaGetLastError();
 }

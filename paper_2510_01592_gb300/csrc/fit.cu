@@ -1403,9 +1403,10 @@ __global__ void k_pack(const uint32_t* __restrict__ off, const uint32_t* __restr
                        const uint32_t* __restrict__ kp, const FitCluster* __restrict__ cl,
                        const int2* __restrict__ hull, const uint32_t* __restrict__ hull_off,
                        vm_plane* __restrict__ planes, int32_t* __restrict__ hull_xy, float* __restrict__ hull_xyz,
-                       uint32_t hull_cap) {
+                       uint32_t hull_cap, HeaderArgs ha) {
     pdl_gate();
     const uint32_t k = *kp;
+    if (ha.out && blockIdx.x == 0 && threadIdx.x == 0) write_header(ha);
     for (uint32_t c = blockIdx.x; c < k; c += gridDim.x) {
         const uint32_t ho = hull_off[c];
         pack_cluster(cl[c], labels ? labels[c] : c, off[c + 1] - off[c], hull + off[c], ho, hull_off[c + 1] - ho,
@@ -1679,10 +1680,11 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
 
 cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
                         uint32_t kcap, vm_plane* planes, int32_t* hull_xy, float* hull_xyz, uint32_t hull_cap,
-                        cudaStream_t s) {
+                        cudaStream_t s, const HeaderArgs* header) {
     if (kcap == 0) return cudaSuccess;
+    const HeaderArgs ha = header ? *header : HeaderArgs{};
     launch_k(k_pack, dim3(kcap < 4096 ? kcap : 4096), dim3(128), 0, s, off, labels, kp, fb.cl, fb.hull, fb.hull_cnt,
-             planes, hull_xy, hull_xyz, hull_cap);
+             planes, hull_xy, hull_xyz, hull_cap, ha);
     count_launch(1);
     return cudaGetLastError();
 }

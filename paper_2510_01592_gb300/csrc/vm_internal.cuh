@@ -437,11 +437,27 @@ cudaError_t launch_fit(const float* pts, const uint32_t* off, const uint32_t* la
                        uint32_t kcap, const vm_segment_params& p, FitBuffers& fb, const FitTuning& t, int num_sms,
                        cudaStream_t s, StageHook* hk, uint32_t round = 0);
 
+// A segmentation's result header: the segmentation counters, the hull-vertex
+// and record totals (from the hull offsets' total, or, with several extraction
+// rounds, from the rounds' words), the fit's and the map's error words and the
+// map's brick count.
+struct HeaderArgs {
+    const SegCounters* ctr;
+    const uint32_t* hull_off;  // [k + 1]: the total at [k]
+    const uint32_t* rounds;    // null for one plane per cluster
+    const uint32_t* fit_err;
+    const MapCounters* mc;
+    const uint32_t* seg_err;
+    SegCounters* out;
+};
+
 // Packs vm_plane records and hull arrays (at most hull_cap vertices) for the
-// *kp clusters; the destinations may be mapped host memory.
+// *kp clusters; the destinations may be mapped host memory.  header (may be
+// null): the kernel's first thread also writes this result header (its inputs
+// all come from earlier kernels; the host reads it after the stream is done).
 cudaError_t launch_pack(const FitBuffers& fb, const uint32_t* off, const uint32_t* labels, const uint32_t* kp,
                         uint32_t kcap, vm_plane* planes, int32_t* hull_xy, float* hull_xyz, uint32_t hull_cap,
-                        cudaStream_t s);
+                        cudaStream_t s, const HeaderArgs* header = nullptr);
 
 // ---------------------------------------------------------------- rounds.cu
 // Sequential multi-plane extraction (planes_per_cluster P > 1): round r + 1
@@ -475,6 +491,17 @@ constexpr int kWordK = 0;                        // [kMaxRounds] clusters in rou
 constexpr int kWordHull = 8;                     // [kMaxRounds + 1] staged hull base of round r
 constexpr int kWordNpts = 20, kWordKeep = 21;    // round points, kept points
 constexpr int kWordRec = 22, kWordHullTot = 23;  // output records, output hull vertices
+
+__device__ __forceinline__ void write_header(const HeaderArgs& a) {
+    SegCounters h = *a.ctr;
+    h.n_hull = a.rounds ? a.rounds[kWordHullTot] : a.hull_off[h.k];
+    h.n_planes = a.rounds ? a.rounds[kWordRec] : h.k;
+    h.fit_err = *a.fit_err;
+    h.n_bricks = a.mc->n_bricks;
+    h.map_err = a.mc->err;
+    h.err |= *a.seg_err;
+    *a.out = h;
+}
 size_t rounds_bytes(size_t nv, size_t kcap, size_t hcap);
 void rounds_layout(char* base, RoundBuffers& rb, size_t nv, size_t kcap, size_t hcap);
 // Runs every round on the clusters of b (count b.ctr->k) and writes the
