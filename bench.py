@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--ref-budget-s", type=float, default=150.0)
     ap.add_argument("--stages", action="store_true", help="print the per-stage breakdown to stderr")
+    ap.add_argument("--no-clock-sampler", action="store_true",
+                    help="for profiler runs: no nvidia-smi clock sampling (the line then carries no clocks)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="F",
                     help="profiling driver: integrate frames 1..F, segment --profile-segments times, no timing")
     ap.add_argument("--profile-segments", type=int, default=3)
@@ -781,7 +783,8 @@ def run_gpu(args):
     # the clock sampler starts here, its own start-up overlapping the set-up
     # work; its record keeps only the samples taken from the first timed pass on
     sampler = ClockSampler(local)
-    sampler.start()
+    if not args.no_clock_sampler:
+        sampler.start()
     spec = synth.config2_spec()
     pts, poses = make_frames(dev)
     first, sched = frame_schedule(args.steps, args.warmup)
