@@ -985,7 +985,7 @@ vm_status vm_autotune_segment(vm_map* m, const vm_segment_params* params, uint32
     const int tiles_cta[] = {512, 1024, 2048, 4096};
     const int tiles_warp[] = {256, 512, 1024};
     const int rs[] = {2, 4, 8};
-    const int ctas[] = {2, 4, 8};
+    const int ctas[] = {2, 3, 4, 6, 8};
     for (int sched = 0; sched < 2; ++sched) {
         const int* tiles = sched ? tiles_warp : tiles_cta;
         const int nt = sched ? 3 : 4;

@@ -435,7 +435,7 @@ vm_status vm_fit_plan_autotune(vm_fit_plan* f, const float* xyz, const uint32_t*
     const int tiles_cta[] = {1024, 2048, 4096, 8192};
     const int tiles_warp[] = {256, 512, 768, 1024};
     const int rs[] = {2, 4, 8};
-    const int ctas[] = {1, 2, 4, 8};
+    const int ctas[] = {1, 2, 3, 4, 6, 8};
     for (int sched = 0; sched < 2; ++sched) {
         for (int ti = 0; ti < 4; ++ti) {
             for (int r : rs) {
