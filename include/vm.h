@@ -376,7 +376,10 @@ typedef struct vm_server vm_server; /* opaque, library-owned */
 
 typedef struct {
     uint32_t mode;             /* VM_SERVE_BATCHED or VM_SERVE_STREAMS                       */
-    uint32_t max_batch;        /* requests per step at most, 1..64                           */
+    uint32_t max_batch;        /* requests per step at most, 1..64; VM_SERVE_BATCHED also
+                                  caps a step at ceil(streams with work / max_inflight), so
+                                  that with every stream busy the steps in flight share the
+                                  streams and one step's front halves overlap another's fit */
     uint32_t max_inflight;     /* steps on the GPU at once, 1..4 (VM_SERVE_STREAMS: requests
                                   in flight at once is max_batch * max_inflight)              */
     uint32_t device;           /* CUDA device ordinal the server runs on                     */
